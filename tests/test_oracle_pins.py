@@ -1,0 +1,306 @@
+"""Pins of the CPU FP64 oracle against facts that do not come from the oracle itself:
+library routines (numpy, scipy), closed forms, exact quadrature of monomials, the analytic
+sphere series, Green's-identity special solutions and convergence under mesh refinement.
+Each test names the passage of the paper whose reading it checks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import analytic_sphere as an
+from workloads import octa_sphere, ico_sphere, shell_points, gaussian_pulse
+
+D = np.array([0.0, 0.0, 1.0])
+
+
+# ---------------- quadrature and shape functions (Sec. 3: quadratic elements, Gauss rules) ----
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 9, 16])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = oracle.gauss_legendre01(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    np.testing.assert_allclose(x, (xr + 1) / 2, atol=2e-15)
+    np.testing.assert_allclose(w, wr / 2, atol=2e-15)
+
+
+def _monomial(a, b):  # exact integral of xi^a eta^b over the reference triangle
+    return math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_std_rule_exact_for_polynomials(n):
+    xi, eta, w = oracle.rule_std(n)
+    assert len(w) == n * n and np.all(w > 0)
+    for a in range(2 * n - 1):
+        for b in range(2 * n - 1 - a):
+            np.testing.assert_allclose(np.sum(w * xi ** a * eta ** b), _monomial(a, b), rtol=1e-13)
+
+
+@pytest.mark.parametrize("node", range(6))
+def test_near_rule_exact_and_collapsed_on_node(node):
+    n = 6
+    xi, eta, w = oracle.rule_near(n, node)
+    assert len(w) == (n * n if node < 3 else 2 * n * n)
+    ref = [(0, 0), (1, 0), (0, 1), (0.5, 0), (0.5, 0.5), (0, 0.5)][node]
+    # every point strictly inside, none on the collocation node
+    assert np.all(np.hypot(xi - ref[0], eta - ref[1]) > 1e-3)
+    for a in range(2 * n - 1):
+        for b in range(2 * n - 1 - a):
+            np.testing.assert_allclose(np.sum(w * xi ** a * eta ** b), _monomial(a, b), rtol=1e-12)
+
+
+def test_shape_functions_kronecker_and_quadratic_reproduction():
+    ref = [(0, 0), (1, 0), (0, 1), (0.5, 0), (0.5, 0.5), (0, 0.5)]
+    for b, (x, y) in enumerate(ref):
+        N, _, _ = oracle.shape6(x, y)
+        np.testing.assert_allclose(N, np.eye(6)[b], atol=1e-15)
+    rng = np.random.default_rng(0)
+    f = lambda x, y: 1.3 - 0.7 * x + 2.1 * y + 0.4 * x * x - 1.1 * x * y + 0.9 * y * y
+    fx = lambda x, y: -0.7 + 0.8 * x - 1.1 * y
+    fy = lambda x, y: 2.1 - 1.1 * x + 1.8 * y
+    fv = np.array([f(*p) for p in ref])
+    for _ in range(20):
+        x, y = rng.random(2) * 0.5
+        N, dx, dy = oracle.shape6(x, y)
+        assert abs(N.sum() - 1) < 1e-15
+        assert abs(N @ fv - f(x, y)) < 1e-14
+        assert abs(dx @ fv - fx(x, y)) < 1e-13 and abs(dy @ fv - fy(x, y)) < 1e-13
+
+
+# ---------------- App. B: the surface at infinity (reading: I1 = +4 pi, I2 = 0) ----------------
+@pytest.mark.parametrize("k,R", [(1.0, 7.0), (2.5, 31.0)])
+def test_appendix_b_surface_at_infinity(k, R):
+    """Integrate [dg/dn G - dG/dn g] and the f analogue over a sphere of radius R about x0
+    (outward normal) with scipy-free midpoint/Gauss quadrature: the g integral equals +4 pi
+    for every R by Green's identity for the regular g, the f integral vanishes."""
+    nt = 400
+    ct, wt = np.polynomial.legendre.leggauss(nt)  # u = cos(theta) in [-1, 1]
+    # g, f depend only on u (k.n0 along the polar axis), so the azimuth integral is 2 pi
+    s = k * R * ct
+    g, f = np.cos(s), np.sin(s) / k
+    dg = -k * np.sin(s) * ct          # grad g . n with n = r/R
+    df = np.cos(s) * ct
+    G = np.exp(1j * k * R) / R
+    dG = np.exp(1j * k * R) * (1j * k * R - 1) / R ** 2
+    I1 = 2 * np.pi * R ** 2 * np.sum(wt * (dg * G - dG * g))
+    I2 = 2 * np.pi * R ** 2 * np.sum(wt * (df * G - dG * f))
+    assert abs(I1 - 4 * np.pi) < 1e-9
+    assert abs(I2) < 1e-9
+
+
+# ---------------- Eq. BRIEF assembly: identities that fix every term -------------------------
+def _residuals(mesh, k, u, du, with_4pi):
+    H, Gm, al, be = oracle.assemble_raw(mesh, k)
+    c = 4 * np.pi if with_4pi else 0.0
+    res = H @ u - (c + al) * u - Gm @ du - be * du
+    return np.linalg.norm(res) / (4 * np.pi * np.linalg.norm(u))
+
+
+@pytest.mark.parametrize("k", [1.0, 3.0])
+def test_entire_solution_identity_converges(k):
+    """u = exp(i k d.x) is regular inside the body, so the row equation without the S_inf term
+    must vanish up to discretisation error, at better than second order."""
+    errs = []
+    for L in (1, 2, 3):
+        m = octa_sphere(L)
+        u = np.exp(1j * k * m.nodes @ D)
+        du = 1j * k * (m.normals @ D) * u
+        errs.append(_residuals(m, k, u, du, with_4pi=False))
+    assert errs[2] < 2e-4
+    assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
+
+
+@pytest.mark.parametrize("k", [1.0, 3.0])
+def test_interior_point_source_fixes_infinity_term(k):
+    """A point source inside the body is a radiating exterior solution: the full row equation,
+    with +4 pi P(x_i) from S_inf, must vanish; with -4 pi it is off by 8 pi P."""
+    s = np.array([0.2, -0.1, 0.3])
+    errs = []
+    for L in (1, 2, 3):
+        m = octa_sphere(L)
+        r = m.nodes - s
+        R = np.linalg.norm(r, axis=1)
+        u = np.exp(1j * k * R) / R
+        du = np.exp(1j * k * R) * (1j * k * R - 1) * np.einsum("ij,ij->i", r, m.normals) / R ** 3
+        errs.append(_residuals(m, k, u, du, with_4pi=True))
+        if L == 2:
+            H, Gm, al, be = oracle.assemble_raw(m, k)
+            wrong = H @ u - (-4 * np.pi + al) * u - Gm @ du - be * du
+            assert np.linalg.norm(wrong) / (4 * np.pi * np.linalg.norm(u)) > 1.5
+    assert errs[2] < 1e-4
+    assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
+
+
+def test_two_body_point_sources():
+    """Two spheres, one interior source in each: still a radiating exterior solution."""
+    from workloads import merge_meshes, scale_translate
+    s0 = ico_sphere(2)
+    m = merge_meshes([scale_translate(s0, 1.0, (0, 0, -1.05)), scale_translate(s0, 1.0, (0, 0, 1.05))])
+    k = 1.5
+    src = [np.array([0.1, 0.0, -1.0]), np.array([-0.2, 0.1, 1.2])]
+    u = np.zeros(m.N, complex)
+    du = np.zeros(m.N, complex)
+    for s, amp in zip(src, (1.0, 0.5 - 0.3j)):
+        r = m.nodes - s
+        R = np.linalg.norm(r, axis=1)
+        u += amp * np.exp(1j * k * R) / R
+        du += amp * np.exp(1j * k * R) * (1j * k * R - 1) * np.einsum("ij,ij->i", r, m.normals) / R ** 3
+    assert _residuals(m, k, u, du, with_4pi=True) < 5e-3
+
+
+# ---------------- full solve vs the analytic sphere series (Sec. 4, last paragraph) -----------
+@pytest.mark.parametrize("k", [0.5, 1.0, 2.0])
+@pytest.mark.parametrize("hard", [True, False])
+def test_sphere_series_and_refinement(k, hard):
+    errs = []
+    for L in (1, 2, 3):
+        m = octa_sphere(L, bc=0 if hard else 1)
+        P, Pn = oracle.solve_frequency(m, k, D)
+        if hard:
+            ex, got = an.scattered(m.nodes, k, hard=True), P
+        else:
+            ex, got = an.surface_normal_derivative(m.nodes, k, hard=False), Pn
+        errs.append(np.linalg.norm(got - ex) / np.linalg.norm(ex))
+    assert errs[1] < 5e-3      # 258 nodes: "better than 2 significant figures"
+    assert errs[2] < 4e-4
+    assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
+
+
+def test_soft_sphere_low_frequency_limit():
+    """k -> 0 soft sphere: P_scat -> -a/r."""
+    m = octa_sphere(2, bc=1)
+    k = 1e-3
+    P, Pn = oracle.solve_frequency(m, k, D)
+    pts = shell_points(20, 1.5, 3.0, seed=3)
+    T = oracle.field(m, k, P, Pn, pts)
+    np.testing.assert_allclose(T, -1.0 / np.linalg.norm(pts, axis=1), rtol=5e-3, atol=2e-3)
+
+
+# ---------------- Eq. BRIEFdmn field evaluation ------------------------------------------------
+def test_field_reproduces_interior_point_source():
+    k = 2.0
+    s = np.array([0.2, -0.1, 0.3])
+    pts = shell_points(30, 1.05, 3.0, seed=7)
+    errs = []
+    for L in (1, 2, 3):
+        m = octa_sphere(L)
+        r = m.nodes - s
+        R = np.linalg.norm(r, axis=1)
+        G = np.exp(1j * k * R) / R
+        dG = np.exp(1j * k * R) * (1j * k * R - 1) * np.einsum("ij,ij->i", r, m.normals) / R ** 3
+        T = oracle.field(m, k, G, dG, pts)
+        Rp = np.linalg.norm(pts - s, axis=1)
+        ex = np.exp(1j * k * Rp) / Rp
+        errs.append(np.linalg.norm(T - ex) / np.linalg.norm(ex))
+    assert errs[2] < 5e-4 and errs[0] / errs[1] > 5 and errs[1] / errs[2] > 5
+
+
+def test_field_vs_series_after_solve():
+    k = 1.0
+    pts = shell_points(30, 1.05, 3.0, seed=8)
+    m = octa_sphere(3)
+    P, Pn = oracle.solve_frequency(m, k, D)
+    T = oracle.field(m, k, P, Pn, pts)
+    ex = an.scattered(pts, k, hard=True)
+    assert np.linalg.norm(T - ex) / np.linalg.norm(ex) < 1e-3
+
+
+def test_foot_points_on_sphere():
+    m = octa_sphere(2)
+    pts = shell_points(50, 1.02, 4.0, seed=5)
+    fe, fx, fy = oracle.foot_points(m, pts)
+    assert np.all(fe >= 0)
+    for p, e, x, y in zip(pts, fe, fx, fy):
+        N, dx, dy = oracle.shape6(x, y)
+        X = m.nodes[m.elems[e]]
+        x0 = N @ X
+        t1, t2 = dx @ X, dy @ X
+        # the quadratic surface is within O(h^3) of the sphere; the foot point is nearly radial
+        assert abs(np.linalg.norm(x0) - 1.0) < 2e-3
+        assert abs(np.linalg.norm(p - x0) - (np.linalg.norm(p) - 1.0)) < 3e-3
+        if x > 1e-9 and y > 1e-9 and x + y < 1 - 1e-9:  # interior stationary point
+            r = p - x0
+            assert abs(r @ t1) < 1e-9 * np.linalg.norm(t1) and abs(r @ t2) < 1e-9 * np.linalg.norm(t2)
+
+
+# ---------------- direct solver ------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 7, 64, 200])
+def test_lu_against_numpy(n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 3 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x = oracle.solve(A, b)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-11, atol=1e-12)
+    be = np.linalg.norm(A @ x - b) / (np.linalg.norm(A, 1) * np.linalg.norm(x) + np.linalg.norm(b))
+    assert be < 10 * n * np.finfo(float).eps
+
+
+def test_lu_pivot_order_and_singular():
+    A = np.array([[1.0, 2.0], [3.0, 4.0]], complex)
+    LU, piv = oracle.lu_factor(A)
+    assert list(piv) == [1, 1]
+    with pytest.raises(RuntimeError):
+        oracle.lu_factor(np.zeros((3, 3), complex))
+
+
+# ---------------- transforms (Eq. inverseFourier convention, Sec. 4 sampling) ------------------
+def test_dft_matches_numpy_and_parseval():
+    rng = np.random.default_rng(1)
+    s = rng.standard_normal(256)
+    S = oracle.dft(s)
+    np.testing.assert_allclose(S, 256 * np.fft.ifft(s), rtol=1e-12, atol=1e-11)
+    assert abs(np.sum(s ** 2) - np.sum(np.abs(S) ** 2) / 256) < 1e-10 * np.sum(s ** 2)
+
+
+def test_gaussian_spectrum_closed_form():
+    Nt, dk, sigma, tc = 256, 1 / 8, 0.5, 8.0
+    T = 2 * np.pi / dk
+    dt = T / Nt
+    S = oracle.dft(gaussian_pulse(Nt, T, sigma, tc))
+    w = 2 * np.pi * np.arange(Nt // 2 + 1) / T
+    ref = sigma * np.sqrt(2 * np.pi) / dt * np.exp(-(sigma * w) ** 2 / 2) * np.exp(1j * w * tc)
+    np.testing.assert_allclose(S[: Nt // 2 + 1], ref, atol=1e-11 * np.abs(ref).max())
+
+
+def test_synthesis_inverts_and_shifts():
+    Nt = 128
+    T = 2 * np.pi / 0.25
+    s = gaussian_pulse(Nt, T, 1.0, 6.0) - 0.3 * gaussian_pulse(Nt, T, 0.7, 12.0)
+    S = oracle.dft(s)
+    midx = np.arange(Nt // 2 + 1)
+    k = 2 * np.pi * midx / T
+    # T_m = 1 at all frequencies reproduces the pulse; T_m = exp(i k_m z) delays it by z (c = 1)
+    one = np.ones((len(midx), 1), complex)
+    np.testing.assert_allclose(oracle.synthesize(one, midx, S, Nt)[0, 0], s, atol=1e-12)
+    j = 5
+    z = j * T / Nt
+    shift = np.exp(1j * k * z)[:, None]
+    np.testing.assert_allclose(oracle.synthesize(shift, midx, S, Nt)[0, 0], np.roll(s, j), atol=1e-12)
+
+
+def test_causality_of_scattered_pulse():
+    """Sec. 4: no scattered field reaches an observation point before the incident pulse has
+    touched the body and travelled there.  With the analytic spectra the only leak is the
+    spectral truncation at k = 8 (Gaussian spectrum e^-8 there); with the 258-node BIE the
+    interior-resonance wavenumbers (j_n zeros near 4.49, 5.76, 6.99) add a ringing tail."""
+    Nk, Nt, sigma, tc = 64, 256, 0.5, 8.0
+    dk = 1 / 8
+    T = 2 * np.pi / dk
+    m = octa_sphere(2)
+    x = np.array([[0.0, 0.0, -2.5], [1.8, 0.0, 0.5]])
+    spectra = np.zeros((Nk, 2), complex)
+    for i in range(Nk):
+        k = dk * (i + 1)
+        P, Pn = oracle.solve_frequency(m, k, D)
+        spectra[i] = oracle.field(m, k, P, Pn, x)
+    series = np.array([an.scattered(x, dk * (i + 1)) for i in range(Nk)])
+    S = oracle.dft(gaussian_pulse(Nt, T, sigma, tc))
+    t = np.arange(Nt) * T / Nt
+    for spec, bound in ((series, 2e-4), (spectra, 1e-2)):
+        p = oracle.synthesize(spec, np.arange(1, Nk + 1), S, Nt)[0]
+        for ip, xp in enumerate(x):
+            # earliest arrival: the pulse peak reaches z = -1 at t = tc - 1, then travels >= |x| - 1
+            t_arr = tc - 1.0 + (np.linalg.norm(xp) - 1.0)
+            early = t < t_arr - 6 * sigma
+            assert np.abs(p[ip][early]).max() < bound * np.abs(p[ip]).max()
+            assert np.abs(p[ip]).max() > 1e-2

@@ -1,0 +1,20 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and the benchmark.
+
+This package only *generates inputs*: surface meshes of the test bodies (quadratic 6-node
+triangles with their analytic node normals), observation points, wavenumber grids and
+sampled incident pulses.  It holds none of the boundary-integral method's arithmetic
+(no quadrature, no Green's function, no assembly, no transform), so the oracle and the
+GPU library can both consume its arrays without sharing any of the method's code.
+"""
+from .meshes import (Mesh, octa_sphere, ico_sphere, scale_translate, merge_meshes,
+                     ellipsoid_from_sphere)
+from .pulses import gaussian_pulse, ricker_pulse, modulated_gaussian, paper_sine_pulse
+from .configs import (config_sphere_fp64, config_two_spheres_mixed, shell_points,
+                      plane_grid_points, Workload)
+
+__all__ = [
+    "Mesh", "octa_sphere", "ico_sphere", "scale_translate", "merge_meshes",
+    "ellipsoid_from_sphere", "gaussian_pulse", "ricker_pulse", "modulated_gaussian",
+    "paper_sine_pulse", "config_sphere_fp64", "config_two_spheres_mixed", "shell_points",
+    "plane_grid_points", "Workload",
+]
