@@ -1,0 +1,153 @@
+/* bie.h -- C ABI of the GB300 library for the space-time boundary-regularised (non-singular)
+ * boundary integral method of Klaseboer, Sepehrirahnama & Chan, "Space-time domain solutions of
+ * the wave equation by a non-singular boundary integral method and Fourier transform"
+ * (arXiv 1706.07919).
+ *
+ * Problem statement (Sec. 4): scatterers bounded by surfaces S, meshed with quadratic 6-node
+ * triangles (Sec. 3), sound-hard or sound-soft, are hit by a plane-wave pulse train.  For every
+ * wavenumber k the library solves the frequency-domain boundary integral equation Eq. (BRIEF)
+ * -- kernels regularised by the functions g and f of App. A, the surface at infinity evaluated
+ * analytically (App. B) -- for the scattered surface pressure P or dP/dn, evaluates the scattered
+ * field at observation points by Eq. (BRIEFdmn), and synthesises p_scat(x, t) for any number of
+ * incident pulses by the inverse discrete Fourier transform (Eq. inverseFourier, Sec. 3 end).
+ *
+ * Conventions, used by every entry point:
+ *   units a = c = 1; time dependence exp(-i omega t); G(x, y) = exp(ik|x-y|)/|x-y|;
+ *   complex values are interleaved (re, im) doubles ("c128") unless stated;
+ *   node normals point out of the scatterer into the fluid;
+ *   element node order v0 v1 v2 m01 m12 m20, counter-clockwise seen from the fluid;
+ *   bc[j] = 0: sound-hard node (dp/dn = 0), 1: sound-soft node (p = 0);
+ *   the incident field per unit amplitude at wavenumber k is exp(i k d.x) (unit vector d).
+ * Memory: pointers documented "host" are read (or written) during the call only; pointers
+ * documented "device" must be device memory of the context's GPU, are used on the context's
+ * stream, and stay owned by the caller.  Calls are stream-ordered: they return once their work
+ * is enqueued (except where stated), and device outputs are valid after the stream completes.
+ * Errors: every function returns BIE_OK (0) or a negative BIE_ERR_* code and then leaves a
+ * message in bie_last_error() (thread-local).  No C++ exception crosses this interface and the
+ * library never traps the device.
+ */
+#ifndef BIE_H
+#define BIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIE_OK 0
+#define BIE_ERR_INVALID_ARG (-1)
+#define BIE_ERR_CUDA (-2)
+#define BIE_ERR_OOM (-3)
+#define BIE_ERR_SINGULAR (-4)
+#define BIE_ERR_NOT_CONVERGED (-5)
+#define BIE_ERR_TIMEOUT (-6)
+#define BIE_ERR_STATE (-7)
+
+/* Precision modes of bie_solve_frequencies. */
+#define BIE_MODE_FP64 0   /* FP64 assembly, FP64 LU with partial pivoting, FP64 solve */
+#define BIE_MODE_MIXED 1  /* FP32 assembly (float-float distance/phase), TF32 tcgen05 LU,
+                             iterative refinement with float-float residuals */
+
+/* Report flags (bie_report.flags). */
+#define BIE_FLAG_NOT_CONVERGED 1u   /* refinement stopped at its iteration cap */
+#define BIE_FLAG_FALLBACK_FP64 2u   /* the frequency was re-solved by the FP64 path */
+#define BIE_FLAG_ZERO_PIVOT 4u      /* an exactly zero pivot was met */
+
+typedef struct bie_ctx bie_ctx;
+
+/* Per-frequency outcome of bie_solve_frequencies (host array, valid when that call returns). */
+typedef struct {
+  int32_t iters;        /* refinement iterations (0 for the FP64 path) */
+  int32_t path;         /* BIE_MODE_* that produced the result */
+  uint32_t flags;       /* BIE_FLAG_* bits */
+  int32_t reserved;
+  double backward_err;  /* ||b - A x|| / (||A||_inf ||x|| + ||b||), infinity norms */
+} bie_report;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* bie_last_error(void);
+
+/* Library version string. */
+const char* bie_version(void);
+
+/* Creates a context on CUDA device `cuda_device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.  The context owns
+ * its device scratch (allocated on demand, released by bie_destroy).  Errors: INVALID_ARG for a
+ * bad device index or NULL out, CUDA if the device cannot be used. */
+int bie_create(bie_ctx** out, int cuda_device, void* cuda_stream);
+
+/* Synchronises the context's stream and frees everything it owns. NULL is accepted. */
+int bie_destroy(bie_ctx* ctx);
+
+/* Quadrature of Sec. 3 ("simple"/"standard Gauss" quadrature): ng x ng collapsed Gauss-Legendre
+ * points per element (default 4), and ng_near x ng_near per sub-triangle for elements that
+ * contain the collocation node (default 6), which are split at that node and collapsed onto it.
+ * Must precede bie_set_geometry to take effect on it.  Errors: INVALID_ARG unless
+ * 1 <= ng <= 8 and 1 <= ng_near <= 12. */
+int bie_set_quadrature(bie_ctx* ctx, int ng, int ng_near);
+
+/* Surface mesh of all scatterers (Sec. 3 and 4).
+ *   nodes   host f64 [N][3]  node positions
+ *   elems   host i32 [E][6]  element nodes, order above, 0 <= index < N
+ *   normals host f64 [N][3]  unit node normals into the fluid (used for f, g of App. A at
+ *                            collocation nodes and for dP/dn); NULL: the normalised mean of the
+ *                            adjacent elements' normals at the node
+ *   bc      host u8  [N]     0 hard, 1 soft
+ * Copied to the device; the geometry precompute (quadrature points, element colouring, near
+ * lists) runs once here.  Errors: INVALID_ARG for N < 3, E < 1, an index out of range, a
+ * non-finite coordinate, a zero-area element or a zero normal; CUDA/OOM on device failures. */
+int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc);
+
+/* Direction d (host f64[3], normalised here) of the incident plane wave exp(i k d.x) (Sec. 4).
+ * Default (0, 0, 1).  Errors: INVALID_ARG for a zero or non-finite vector. */
+int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
+
+/* Assembles the FP64 system of one wavenumber k > 0: Eq. (BRIEF) at every node with the App. B
+ * term 4 pi P(x_i), unknown P at hard nodes and dP/dn at soft nodes, known values from the
+ * scattered-field boundary conditions of Sec. 4 (p_scat = -p_inc soft, dp_scat/dn = -dp_inc/dn
+ * hard) moved to the right-hand side.
+ *   A_out device c128 [N][N] row-major, b_out device c128 [N].
+ * Errors: INVALID_ARG (k <= 0 or not finite, NULL pointer), STATE (no geometry). */
+int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
+
+/* Frequency solves (the per-k hot path): for each k[m] > 0 assemble, factor and solve.
+ *   k        host f64 [Nk]
+ *   mode     BIE_MODE_FP64 or BIE_MODE_MIXED
+ *   surf_out device c128 [Nk][2][N]: scattered P and dP/dn at every node, per k
+ *   rep      host bie_report [Nk] or NULL
+ * Synchronises the stream before returning (the reports are read back).  Errors: INVALID_ARG,
+ * STATE, OOM (scratch larger than free device memory), CUDA. */
+int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, void* surf_out,
+                          bie_report* rep);
+
+/* Scattered field at M observation points (Eq. BRIEFdmn with the closest surface point x0 of
+ * each point, Sec. 3), for every k:
+ *   xobs  device f64 [M][3] points in the fluid
+ *   k     host f64 [Nk]; surf device c128 [Nk][2][N] as written by bie_solve_frequencies
+ *   T_out device c128 [Nk][M]
+ *   mode  BIE_MODE_FP64 (FP64 arithmetic) or BIE_MODE_MIXED (FP32 with float-float phases)
+ * Foot points are computed on the device at every call.  Errors: INVALID_ARG, STATE, CUDA. */
+int bie_eval_field(bie_ctx* ctx, const double* xobs, int64_t M, const double* k, int64_t Nk,
+                   const void* surf, int mode, void* T_out);
+
+/* Spectra of sampled pulses with the sign of Eq. (inverseFourier):
+ *   S[p][m] = sum_n s[p][n] exp(+2 pi i m n / Nt), m = 0 .. Nt/2.
+ *   s device f64 [P][Nt], S_out device c128 [P][Nt/2+1].  Nt even, 2 <= Nt <= 65536. */
+int bie_pulse_spectrum(bie_ctx* ctx, const double* s, int64_t P, int64_t Nt, void* S_out);
+
+/* Space-time scattered field (Sec. 3 end, Sec. 4): for each pulse p, point x and time sample n
+ *   out[p][x][n] = (1/Nt) sum_r w_m Re( S[p][m] T[r][x] exp(-2 pi i m n / Nt) ),  m = midx[r],
+ * w_m = 1 for m = 0 or Nt/2, else 2 (real signals); frequencies not listed contribute zero.
+ *   T device c128 [Nk][M]; midx host i64 [Nk], strictly increasing, 0 <= m <= Nt/2
+ *   S device c128 [P][Nt/2+1]; out device, f64 (out_dtype 0) or f32 (out_dtype 1), [P][M][Nt]
+ * Errors: INVALID_ARG (sizes, ordering, Nt not a power of two in [2, 65536]). */
+int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk, int64_t M,
+                   const void* S, int64_t P, int64_t Nt, void* out, int out_dtype);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,159 @@
+"""Thin ctypes binding of include/bie.h.
+
+Module-level functions carry the C names (bie_create, bie_set_geometry, ...) and only marshal
+arguments: torch tensors give device pointers and the stream, numpy arrays give host pointers.
+Every computation runs in libbie.so; there is no fallback.  Importing this module on a machine
+without the built library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbie.so")
+
+BIE_OK = 0
+BIE_ERR_INVALID_ARG = -1
+BIE_ERR_CUDA = -2
+BIE_ERR_OOM = -3
+BIE_ERR_SINGULAR = -4
+BIE_ERR_NOT_CONVERGED = -5
+BIE_ERR_TIMEOUT = -6
+BIE_ERR_STATE = -7
+BIE_MODE_FP64 = 0
+BIE_MODE_MIXED = 1
+BIE_FLAG_NOT_CONVERGED = 1
+BIE_FLAG_FALLBACK_FP64 = 2
+BIE_FLAG_ZERO_PIVOT = 4
+
+EXPORTED = ["bie_last_error", "bie_version", "bie_create", "bie_destroy", "bie_set_quadrature",
+            "bie_set_geometry", "bie_set_incident_plane_wave", "bie_assemble", "bie_solve_frequencies",
+            "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize"]
+
+
+class BieReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("path", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double)]
+
+
+class BieError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbie.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(p)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sigs = {
+        "bie_last_error": ([], ctypes.c_char_p),
+        "bie_version": ([], ctypes.c_char_p),
+        "bie_create": ([ctypes.POINTER(vp), i32, vp], i32),
+        "bie_destroy": ([vp], i32),
+        "bie_set_quadrature": ([vp, i32, i32], i32),
+        "bie_set_geometry": ([vp, vp, i64, vp, i64, vp, vp], i32),
+        "bie_set_incident_plane_wave": ([vp, vp], i32),
+        "bie_assemble": ([vp, dbl, vp, vp], i32),
+        "bie_solve_frequencies": ([vp, vp, i64, i32, vp, vp], i32),
+        "bie_eval_field": ([vp, vp, i64, vp, i64, vp, i32, vp], i32),
+        "bie_pulse_spectrum": ([vp, vp, i64, i64, vp], i32),
+        "bie_synthesize": ([vp, vp, vp, i64, i64, vp, i64, i64, vp, i32], i32),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != BIE_OK:
+        raise BieError(rc, load().bie_last_error().decode())
+
+
+def _hp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dp(t) -> int:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- C names, marshalling only ----
+def bie_last_error() -> str:
+    return load().bie_last_error().decode()
+
+
+def bie_version() -> str:
+    return load().bie_version().decode()
+
+
+def bie_create(device: int = 0, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().bie_create(ctypes.byref(h), device, stream))
+    return h.value
+
+
+def bie_destroy(ctx: int) -> None:
+    _check(load().bie_destroy(ctx))
+
+
+def bie_set_quadrature(ctx: int, ng: int, ng_near: int) -> None:
+    _check(load().bie_set_quadrature(ctx, ng, ng_near))
+
+
+def bie_set_geometry(ctx: int, nodes, elems, normals, bc) -> None:
+    nodes = np.ascontiguousarray(nodes, np.float64)
+    elems = np.ascontiguousarray(elems, np.int32)
+    bc = np.ascontiguousarray(bc, np.uint8)
+    nrm = None if normals is None else np.ascontiguousarray(normals, np.float64)
+    _check(load().bie_set_geometry(ctx, _hp(nodes), nodes.shape[0], _hp(elems), elems.shape[0],
+                                   None if nrm is None else _hp(nrm), _hp(bc)))
+
+
+def bie_set_incident_plane_wave(ctx: int, direction) -> None:
+    d = np.ascontiguousarray(direction, np.float64)
+    _check(load().bie_set_incident_plane_wave(ctx, _hp(d)))
+
+
+def bie_assemble(ctx: int, k: float, A, b) -> None:
+    _check(load().bie_assemble(ctx, float(k), _dp(A), _dp(b)))
+
+
+def bie_solve_frequencies(ctx: int, k, mode: int, surf_out, reports: bool = True):
+    k = np.ascontiguousarray(k, np.float64)
+    rep = (BieReport * max(1, k.shape[0]))() if reports else None
+    _check(load().bie_solve_frequencies(ctx, _hp(k), k.shape[0], mode, _dp(surf_out),
+                                        ctypes.cast(rep, ctypes.c_void_p) if rep is not None else None))
+    return list(rep)[: k.shape[0]] if rep is not None else None
+
+
+def bie_eval_field(ctx: int, xobs, k, surf, mode: int, T_out) -> None:
+    k = np.ascontiguousarray(k, np.float64)
+    _check(load().bie_eval_field(ctx, _dp(xobs), xobs.shape[0], _hp(k), k.shape[0], _dp(surf), mode, _dp(T_out)))
+
+
+def bie_pulse_spectrum(ctx: int, s, S_out) -> None:
+    _check(load().bie_pulse_spectrum(ctx, _dp(s), s.shape[0], s.shape[1], _dp(S_out)))
+
+
+def bie_synthesize(ctx: int, T, midx, S, Nt: int, out, out_dtype: int) -> None:
+    midx = np.ascontiguousarray(midx, np.int64)
+    _check(load().bie_synthesize(ctx, _dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
+                                 _dp(out), out_dtype))

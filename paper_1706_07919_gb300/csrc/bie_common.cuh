@@ -1,0 +1,185 @@
+// bie_common.cuh -- internal types and device helpers shared by the library's translation units.
+// Not part of the public interface (include/bie.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/bie.h"
+
+namespace bie {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ------------------------------------------------------------------------------------------
+// Error plumbing: every entry point funnels failures through set_error() and returns a code.
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define BIE_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::bie::cuda_fail(_e, #expr); \
+  } while (0)
+
+#define BIE_TRY(expr)          \
+  do {                         \
+    int _rc = (expr);          \
+    if (_rc != BIE_OK) return _rc; \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Quadrature tables (host-built, uploaded once per geometry).
+// Standard rule: Q points per element.  Near rule for local node a: nnear[a] points, stored
+// with stride QN (= 2 * ng_near^2) per (element, local node).
+// ------------------------------------------------------------------------------------------
+struct QuadRule {
+  int ng = 4, ng_near = 6;
+  int Q = 0, QN = 0;
+  int nnear[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<double> xi, eta, w;           // [Q]
+  std::vector<double> nxi, neta, nw;        // [6][QN]
+};
+void build_quad_rule(QuadRule& r, int ng, int ng_near);
+void gauss_legendre_unit(int n, double* x, double* w);
+
+// Per-point geometry record layout in the device tables (structure of arrays, FP64):
+// x, y, z, nx, ny, nz, wJ  -> 7 arrays of length npts.
+enum { GX = 0, GY, GZ, GNX, GNY, GNZ, GWJ, GCOUNT };
+
+// ------------------------------------------------------------------------------------------
+// The context.
+// ------------------------------------------------------------------------------------------
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace bie
+
+struct bie_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int ng = 4, ng_near = 6;
+  double dir[3] = {0.0, 0.0, 1.0};
+
+  // geometry (device)
+  bool has_geom = false;
+  int64_t N = 0, E = 0;
+  double* nodes = nullptr;     // [N][3]
+  int32_t* elems = nullptr;    // [E][6]
+  double* normals = nullptr;   // [N][3]
+  uint8_t* bc = nullptr;       // [N]
+  std::vector<double> h_nodes, h_normals;
+  std::vector<int32_t> h_elems;
+  std::vector<uint8_t> h_bc;
+  bie::QuadRule rule;
+  double* qgeo = nullptr;      // standard points: GCOUNT x [E*Q]
+  double* ngeo = nullptr;      // near points:     GCOUNT x [E*6*QN]
+  double* qshape = nullptr;    // [Q][6] shape values at the standard points
+  double* nshape = nullptr;    // [6][QN][6] shape values at the near points
+  float* qgeo32 = nullptr;     // mixed path standard points: see asm32.cu for the layout
+  float* qshape32 = nullptr;   // [Q][6]
+  int ncolors = 0;
+  std::vector<int32_t> h_color_off;  // [ncolors+1]
+  int32_t* color_off = nullptr;
+  int32_t* elem_perm = nullptr;      // [E] elements ordered by colour
+  int32_t* n2e_off = nullptr;        // [N+1] CSR: elements containing node i
+  int32_t* n2e = nullptr;            // element * 8 + local index
+  int max_n2e = 0;
+  int* d_nnear = nullptr;            // [6] near-rule point counts
+
+  // workspace (device), grown on demand
+  bie::DeviceBuf work;   // per-call systems / factors
+  bie::DeviceBuf work2;  // FFT twiddles
+  bie::DeviceBuf work3;  // foot points, field scratch, synthesis indices
+};
+
+namespace bie {
+
+int ensure_buf(DeviceBuf& b, size_t bytes);
+void free_buf(DeviceBuf& b);
+
+// ------------------------------------------------------------------------------------------
+// Device helpers.
+// ------------------------------------------------------------------------------------------
+struct cd {  // complex double
+  double re, im;
+};
+struct cf {  // complex float
+  float re, im;
+};
+
+__host__ __device__ __forceinline__ cd cmul(cd a, cd b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cd cadd(cd a, cd b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cd csub(cd a, cd b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cd cscale(cd a, double s) { return {a.re * s, a.im * s}; }
+
+// ---- float-float ("double-float") arithmetic: value = hi + lo, |lo| <= ulp(hi)/2 ----------
+// Error-free transforms after Knuth (TwoSum) and Dekker/FMA (TwoProd); renormalisation by
+// Fast2Sum.  About 48 significant bits.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return ff_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+  float p = __fmul_rn(a.hi, a.hi);
+  float e = __fmaf_rn(a.hi, a.hi, -p);
+  e = __fmaf_rn(2.0f * a.hi, a.lo, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {  // a > 0
+  float y = sqrtf(a.hi);
+  float r = __fmaf_rn(-y, y, a.hi);  // exact residual of y^2 vs a.hi
+  r = __fadd_rn(r, a.lo);
+  return ff_fast_two_sum(y, __fdividef(r, 2.0f * y));
+}
+__host__ __device__ __forceinline__ ff ff_from_double(double x) {
+  float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// Compensated (Kahan-Babuska/Neumaier) running sum in FP32.
+struct ksum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    ff t = ff_two_sum(s, x);
+    s = t.hi;
+    c = __fadd_rn(c, t.lo);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+}  // namespace bie

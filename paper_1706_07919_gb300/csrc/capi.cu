@@ -1,0 +1,322 @@
+// capi.cu -- the C ABI of include/bie.h: argument checks, device buffers, and the order in which
+// the kernels of the other translation units run.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "bie_common.cuh"
+
+namespace bie {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? BIE_ERR_OOM : BIE_ERR_CUDA;
+}
+
+int ensure_buf(DeviceBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return BIE_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BIE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return BIE_OK;
+}
+void free_buf(DeviceBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// translation-unit entry points
+int upload_geometry_tables(bie_ctx* c);
+int build_colouring(bie_ctx* c);
+int host_geometry_checks(bie_ctx* c, bool make_normals);
+void build_quad_rule(QuadRule& r, int ng, int ng_near);
+int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot);
+int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch);
+int lu_factor64(bie_ctx* c, cd* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
+int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cd* b,
+               int64_t bstride_b);
+int field64(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
+            const int32_t* foot_elem, const double* foot, cd* T, void* scratch);
+int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout);
+int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t M, const cd* Sp, int64_t P, int n,
+               void* out, int out_dtype);
+int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
+int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
+                const int32_t* foot_elem, const double* foot, cd* T, void* scratch, size_t scratch_bytes);
+
+static void free_geometry(bie_ctx* c) {
+  void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
+                  c->qshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
+  c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
+  c->qgeo32 = nullptr; c->qshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
+  c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr;
+  c->has_geom = false;
+}
+
+// P, P' at every node from the solution vector and the known boundary values.
+__global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, const cd* __restrict__ x,
+                                 const cd* __restrict__ known, cd* __restrict__ surf) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int kk = blockIdx.y;
+  if (j >= N) return;
+  cd xv = x[(int64_t)kk * N + j], kv = known[(int64_t)kk * N + j];
+  cd* s = surf + (int64_t)kk * 2 * N;
+  if (bc[j] == 0) { s[j] = xv; s[N + j] = kv; }
+  else { s[j] = kv; s[N + j] = xv; }
+}
+
+static int check_ctx(bie_ctx* c, bool need_geom) {
+  if (!c) return fail(BIE_ERR_INVALID_ARG, "NULL context");
+  if (need_geom && !c->has_geom) return fail(BIE_ERR_STATE, "no geometry: call bie_set_geometry first");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return BIE_OK;
+}
+
+static int check_k(const double* k, int64_t Nk) {
+  if (Nk < 0) return fail(BIE_ERR_INVALID_ARG, "Nk < 0");
+  if (Nk > 0 && !k) return fail(BIE_ERR_INVALID_ARG, "NULL k");
+  for (int64_t i = 0; i < Nk; ++i)
+    if (!(k[i] > 0.0) || !std::isfinite(k[i]))
+      return fail(BIE_ERR_INVALID_ARG, "k[" + std::to_string(i) + "] must be finite and > 0");
+  return BIE_OK;
+}
+
+int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep) {
+  const int64_t N = c->N;
+  const size_t perk = (size_t)N * N * sizeof(cd) + (size_t)N * sizeof(cd) * 6 + (size_t)N * 4 + 64;
+  size_t free_b = 0, total_b = 0;
+  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
+  if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "one FP64 system of N = " + std::to_string(N) + " does not fit in device memory");
+  BIE_TRY(ensure_buf(c->work, kb * perk + 4096));
+  char* base = (char*)c->work.p;
+  cd* A = (cd*)base;
+  cd* b = A + kb * N * N;
+  cd* scratch = b + kb * N;  // known [kb][N], rowsum [kb][N][3]
+  int32_t* piv = (int32_t*)(scratch + kb * N * 4);
+  int32_t* info = piv + kb * N;
+  double* kdev = (double*)(((uintptr_t)(info + kb) + 15) & ~(uintptr_t)15);
+  std::vector<int32_t> hinfo(kb);
+  for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
+    const int nk = (int)std::min<int64_t>(kb, Nk - k0);
+    BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
+    BIE_TRY(assemble64(c, kdev, nk, A, b, scratch));
+    BIE_TRY(lu_factor64(c, A, nk, (int)N, (int)N, N * N, piv, info));
+    BIE_TRY(lu_solve64(c, A, nk, (int)N, (int)N, N * N, piv, b, N));
+    dim3 g((unsigned)((N + 255) / 256), nk);
+    k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, b, scratch, surf_out + k0 * 2 * N);
+    BIE_CUDA_TRY(cudaGetLastError());
+    if (rep) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+      BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      for (int i = 0; i < nk; ++i) {
+        rep[k0 + i] = bie_report{0, BIE_MODE_FP64, hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u, 0, 0.0};
+      }
+    }
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+}  // namespace bie
+
+using namespace bie;
+
+extern "C" {
+
+const char* bie_last_error(void) { return g_last_error.c_str(); }
+
+const char* bie_version(void) { return "bie-gb300 0.1 (sm_103a)"; }
+
+int bie_create(bie_ctx** out, int cuda_device, void* cuda_stream) {
+  if (!out) return fail(BIE_ERR_INVALID_ARG, "NULL out");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (cuda_device < 0 || cuda_device >= n)
+    return fail(BIE_ERR_INVALID_ARG, "device " + std::to_string(cuda_device) + " out of range (" + std::to_string(n) + " devices)");
+  e = cudaSetDevice(cuda_device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  bie_ctx* c = new (std::nothrow) bie_ctx();
+  if (!c) return fail(BIE_ERR_OOM, "host allocation failed");
+  c->device = cuda_device;
+  c->stream = (cudaStream_t)cuda_stream;
+  *out = c;
+  return BIE_OK;
+}
+
+int bie_destroy(bie_ctx* c) {
+  if (!c) return BIE_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_geometry(c);
+  free_buf(c->work);
+  free_buf(c->work2);
+  free_buf(c->work3);
+  delete c;
+  return BIE_OK;
+}
+
+int bie_set_quadrature(bie_ctx* c, int ng, int ng_near) {
+  BIE_TRY(check_ctx(c, false));
+  if (ng < 1 || ng > 8 || ng_near < 1 || ng_near > 12)
+    return fail(BIE_ERR_INVALID_ARG, "quadrature orders must satisfy 1 <= ng <= 8, 1 <= ng_near <= 12");
+  c->ng = ng;
+  c->ng_near = ng_near;
+  return BIE_OK;
+}
+
+int bie_set_incident_plane_wave(bie_ctx* c, const double* dir) {
+  BIE_TRY(check_ctx(c, false));
+  if (!dir) return fail(BIE_ERR_INVALID_ARG, "NULL direction");
+  double n = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  if (!(n > 0.0) || !std::isfinite(n)) return fail(BIE_ERR_INVALID_ARG, "direction must be finite and non-zero");
+  for (int d = 0; d < 3; ++d) c->dir[d] = dir[d] / n;
+  return BIE_OK;
+}
+
+int bie_set_geometry(bie_ctx* c, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc) {
+  BIE_TRY(check_ctx(c, false));
+  if (!nodes || !elems || !bc) return fail(BIE_ERR_INVALID_ARG, "NULL nodes, elems or bc");
+  if (N < 3 || E < 1) return fail(BIE_ERR_INVALID_ARG, "need N >= 3 and E >= 1");
+  if (N > (int64_t)1 << 30 || E > (int64_t)1 << 28) return fail(BIE_ERR_INVALID_ARG, "mesh too large");
+  cudaStreamSynchronize(c->stream);
+  free_geometry(c);
+  c->N = N;
+  c->E = E;
+  c->h_nodes.assign(nodes, nodes + 3 * N);
+  c->h_elems.assign(elems, elems + 6 * E);
+  c->h_bc.assign(bc, bc + N);
+  for (int64_t i = 0; i < N; ++i)
+    if (c->h_bc[i] > 1) return fail(BIE_ERR_INVALID_ARG, "bc values must be 0 (hard) or 1 (soft)");
+  if (normals) c->h_normals.assign(normals, normals + 3 * N);
+  BIE_TRY(host_geometry_checks(c, normals == nullptr));
+  build_quad_rule(c->rule, c->ng, c->ng_near);
+  BIE_CUDA_TRY(cudaMalloc(&c->nodes, 3 * N * sizeof(double)));
+  BIE_CUDA_TRY(cudaMalloc(&c->normals, 3 * N * sizeof(double)));
+  BIE_CUDA_TRY(cudaMalloc(&c->elems, 6 * E * sizeof(int32_t)));
+  BIE_CUDA_TRY(cudaMalloc(&c->bc, N));
+  BIE_CUDA_TRY(cudaMalloc(&c->d_nnear, 6 * sizeof(int)));
+  BIE_CUDA_TRY(cudaMemcpy(c->nodes, c->h_nodes.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+  BIE_CUDA_TRY(cudaMemcpy(c->normals, c->h_normals.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+  BIE_CUDA_TRY(cudaMemcpy(c->elems, c->h_elems.data(), 6 * E * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BIE_CUDA_TRY(cudaMemcpy(c->bc, c->h_bc.data(), N, cudaMemcpyHostToDevice));
+  BIE_CUDA_TRY(cudaMemcpy(c->d_nnear, c->rule.nnear, 6 * sizeof(int), cudaMemcpyHostToDevice));
+  BIE_TRY(build_colouring(c));
+  BIE_TRY(upload_geometry_tables(c));
+  c->has_geom = true;
+  return BIE_OK;
+}
+
+int bie_assemble(bie_ctx* c, double k, void* A_out, void* b_out) {
+  BIE_TRY(check_ctx(c, true));
+  if (!A_out || !b_out) return fail(BIE_ERR_INVALID_ARG, "NULL output");
+  BIE_TRY(check_k(&k, 1));
+  const int64_t N = c->N;
+  BIE_TRY(ensure_buf(c->work, (size_t)N * 4 * sizeof(cd) + 64));
+  double* kdev = (double*)((char*)c->work.p + (size_t)N * 4 * sizeof(cd));
+  BIE_CUDA_TRY(cudaMemcpyAsync(kdev, &k, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  BIE_TRY(assemble64(c, kdev, 1, (cd*)A_out, (cd*)b_out, c->work.p));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, void* surf_out, bie_report* rep) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, Nk));
+  if (Nk == 0) return BIE_OK;
+  if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
+  if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
+  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep);
+  return fail(BIE_ERR_INVALID_ARG, "unknown mode " + std::to_string(mode));
+}
+
+int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, int64_t Nk, const void* surf,
+                   int mode, void* T_out) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, Nk));
+  if (M < 0) return fail(BIE_ERR_INVALID_ARG, "M < 0");
+  if (M == 0 || Nk == 0) return BIE_OK;
+  if (!xobs || !surf || !T_out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  if (mode != BIE_MODE_FP64 && mode != BIE_MODE_MIXED) return fail(BIE_ERR_INVALID_ARG, "unknown mode");
+  const int64_t EQ = c->E * c->rule.Q;
+  // foot points (k independent) then batches of k
+  const size_t foot_bytes = (size_t)M * (8 * sizeof(double) + sizeof(int32_t)) + 256;
+  const size_t perk = 2 * (size_t)EQ * sizeof(cd) + 16;
+  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, 64));
+  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + 4096));
+  double* foot = (double*)c->work3.p;
+  int32_t* foot_elem = (int32_t*)(foot + 8 * M);
+  char* after = (char*)(((uintptr_t)(foot_elem + M) + 255) & ~(uintptr_t)255);
+  double* kdev = (double*)after;
+  void* scratch = (void*)(after + 256 * sizeof(double));
+  if (kb > 256) kb = 256;
+  BIE_TRY(launch_foot_points(c, xobs, M, foot_elem, foot));
+  for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
+    const int nk = (int)std::min<int64_t>(kb, Nk - k0);
+    BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const cd* s = (const cd*)surf + k0 * 2 * c->N;
+    cd* T = (cd*)T_out + k0 * M;
+    if (mode == BIE_MODE_FP64)
+      BIE_TRY(field64(c, kdev, nk, s, xobs, M, foot_elem, foot, T, scratch));
+    else
+      BIE_TRY(field_mixed(c, kdev, nk, s, xobs, M, foot_elem, foot, T, scratch, kb * perk));
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+int bie_pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int64_t Nt, void* S_out) {
+  BIE_TRY(check_ctx(c, false));
+  if (P < 0 || Nt < 2 || Nt > 4096 || (Nt & (Nt - 1)))
+    return fail(BIE_ERR_INVALID_ARG, "Nt must be a power of two in [2, 4096] and P >= 0");
+  if (P == 0) return BIE_OK;
+  if (!s || !S_out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  BIE_TRY(pulse_spectrum(c, s, P, (int)Nt, (cd*)S_out));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+int bie_synthesize(bie_ctx* c, const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S, int64_t P,
+                   int64_t Nt, void* out, int out_dtype) {
+  BIE_TRY(check_ctx(c, false));
+  if (P < 0 || M < 0 || Nk < 0 || Nt < 2 || Nt > 4096 || (Nt & (Nt - 1)))
+    return fail(BIE_ERR_INVALID_ARG, "need P, M, Nk >= 0 and Nt a power of two in [2, 4096]");
+  if (out_dtype != 0 && out_dtype != 1) return fail(BIE_ERR_INVALID_ARG, "out_dtype must be 0 (f64) or 1 (f32)");
+  if (P > 65535) return fail(BIE_ERR_INVALID_ARG, "P > 65535");
+  if (P == 0 || M == 0) return BIE_OK;
+  if ((Nk > 0 && (!T || !midx)) || !S || !out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  for (int64_t r = 0; r < Nk; ++r) {
+    if (midx[r] < 0 || midx[r] > Nt / 2) return fail(BIE_ERR_INVALID_ARG, "midx out of [0, Nt/2]");
+    if (r > 0 && midx[r] <= midx[r - 1]) return fail(BIE_ERR_INVALID_ARG, "midx must be strictly increasing");
+  }
+  BIE_TRY(ensure_buf(c->work3, (size_t)std::max<int64_t>(Nk, 1) * sizeof(int64_t)));
+  int64_t* md = (int64_t*)c->work3.p;
+  if (Nk > 0) BIE_CUDA_TRY(cudaMemcpyAsync(md, midx, Nk * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_TRY(synthesize(c, (const cd*)T, md, (int)Nk, M, (const cd*)S, P, (int)Nt, out, out_dtype));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+}  // extern "C"

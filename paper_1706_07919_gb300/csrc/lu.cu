@@ -1,0 +1,270 @@
+// lu.cu -- batched dense complex LU with partial pivoting and triangular solves ("solved using a
+// direct method", Sec. 4), right-looking and blocked:
+//   for each panel of width nb:  factor the panel (pivot = largest modulus, lowest row on ties),
+//   apply its row swaps to the other columns, U12 = L11^{-1} A12, A22 -= L21 U12.
+// Matrices are row-major with leading dimension ld, batched with stride `bstride` elements.
+// This file holds the panel, swap/TRSM and SIMT-GEMM kernels in FP64 and FP32; the tensor-core
+// (tcgen05, TF32) trailing update lives in lu_tc.cu.
+#include "bie_common.cuh"
+
+namespace bie {
+
+template <class S> struct Cx { S re, im; };
+template <class S> __device__ __forceinline__ Cx<S> cx_mul(Cx<S> a, Cx<S> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class S> __device__ __forceinline__ Cx<S> cx_div(Cx<S> a, Cx<S> b) {
+  S d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// ---- panel factorisation: one CTA per matrix, columns p0 .. p0+nb-1, rows p0 .. n-1 ----------
+template <class S>
+__global__ void __launch_bounds__(512) k_panel(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                               int nb, int32_t* __restrict__ piv, int32_t* __restrict__ info) {
+  Cx<S>* M = A + (int64_t)blockIdx.x * bstride;
+  int32_t* pv = piv + (int64_t)blockIdx.x * n;
+  __shared__ S red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int pend = min(p0 + nb, n);
+  for (int c = p0; c < pend; ++c) {
+    // pivot: largest |a_rc|^2 over r >= c, lowest row on ties
+    S best = -1;
+    int bi = n;
+    for (int r = c + tid; r < n; r += nt) {
+      Cx<S> v = M[(int64_t)r * ld + c];
+      S m = v.re * v.re + v.im * v.im;
+      if (m > best) { best = m; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      S ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nw ? red_v[lane] : (S)-1;
+      bi = lane < nw ? red_i[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        S ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        s_piv = bi;
+        pv[c] = bi;
+        if (!(best > 0) && info) atomicOr(info + blockIdx.x, 1);
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != c && p < n)  // swap rows c and p inside the panel columns
+      for (int j = p0 + tid; j < pend; j += nt) {
+        Cx<S> t = M[(int64_t)c * ld + j];
+        M[(int64_t)c * ld + j] = M[(int64_t)p * ld + j];
+        M[(int64_t)p * ld + j] = t;
+      }
+    __syncthreads();
+    const Cx<S> d = M[(int64_t)c * ld + c];
+    const bool ok = (d.re != 0 || d.im != 0);
+    // scale the column and update the rest of the panel (rank-1), one row per thread
+    for (int r = c + 1 + tid; r < n; r += nt) {
+      Cx<S> l = M[(int64_t)r * ld + c];
+      if (ok) l = cx_div(l, d);
+      M[(int64_t)r * ld + c] = l;
+      for (int j = c + 1; j < pend; ++j) {
+        Cx<S> u = M[(int64_t)c * ld + j];
+        Cx<S> a = M[(int64_t)r * ld + j];
+        a.re -= l.re * u.re - l.im * u.im;
+        a.im -= l.re * u.im + l.im * u.re;
+        M[(int64_t)r * ld + j] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- row swaps outside the panel, then U12 = L11^{-1} A12 ----------------------------------
+// grid: (ceil(n / 128), batch), block 128: one column per thread.
+template <class S>
+__global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                                   int nb, const int32_t* __restrict__ piv) {
+  Cx<S>* M = A + (int64_t)blockIdx.y * bstride;
+  const int32_t* pv = piv + (int64_t)blockIdx.y * n;
+  extern __shared__ unsigned char smem_raw[];
+  Cx<S>* L11 = reinterpret_cast<Cx<S>*>(smem_raw);  // [nb][nb]
+  const int pend = min(p0 + nb, n);
+  const int w = pend - p0;
+  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+    int r = t / w, cc = t % w;
+    L11[t] = M[(int64_t)(p0 + r) * ld + p0 + cc];
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || (j >= p0 && j < pend)) return;
+  for (int s = p0; s < pend; ++s) {
+    int p = pv[s];
+    if (p != s) {
+      Cx<S> t = M[(int64_t)s * ld + j];
+      M[(int64_t)s * ld + j] = M[(int64_t)p * ld + j];
+      M[(int64_t)p * ld + j] = t;
+    }
+  }
+  if (j < pend) return;  // columns left of the panel only get the swaps
+  Cx<S> x[64];
+  for (int s = 0; s < w; ++s) {
+    Cx<S> v = M[(int64_t)(p0 + s) * ld + j];
+    for (int t = 0; t < s; ++t) {
+      Cx<S> l = L11[s * w + t];
+      v.re -= l.re * x[t].re - l.im * x[t].im;
+      v.im -= l.re * x[t].im + l.im * x[t].re;
+    }
+    x[s] = v;
+    M[(int64_t)(p0 + s) * ld + j] = v;
+  }
+}
+
+// ---- SIMT trailing update A22 -= L21 U12 (64 x 64 complex tile per CTA, 256 threads) ---------
+template <class S>
+__global__ void __launch_bounds__(256) k_gemm_update(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld,
+                                                     int p0, int nb) {
+  Cx<S>* M = A + (int64_t)blockIdx.z * bstride;
+  const int r0 = p0 + nb + blockIdx.y * 64, c0 = p0 + nb + blockIdx.x * 64;
+  if (r0 >= n || c0 >= n) return;
+  __shared__ Cx<S> Ls[16][64 + 1];  // [k][row]
+  __shared__ Cx<S> Us[16][64 + 1];  // [k][col]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  Cx<S> acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = {0, 0};
+  for (int k0 = p0; k0 < p0 + nb; k0 += 16) {
+    for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+      int kk = t & 15, rr = t >> 4;
+      int gr = r0 + rr, gk = k0 + kk;
+      Ls[kk][rr] = (gr < n && gk < p0 + nb) ? M[(int64_t)gr * ld + gk] : Cx<S>{0, 0};
+      int cc = t & 63, k2 = t >> 6;
+      int gc = c0 + cc, gk2 = k0 + k2;
+      Us[k2][cc] = (gc < n && gk2 < p0 + nb) ? M[(int64_t)gk2 * ld + gc] : Cx<S>{0, 0};
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; ++kk) {
+      Cx<S> l[4], u[4];
+      for (int a = 0; a < 4; ++a) l[a] = Ls[kk][ty + 16 * a];
+      for (int b = 0; b < 4; ++b) u[b] = Us[kk][tx + 16 * b];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b].re += l[a].re * u[b].re - l[a].im * u[b].im;
+          acc[a][b].im += l[a].re * u[b].im + l[a].im * u[b].re;
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      int gr = r0 + ty + 16 * a, gc = c0 + tx + 16 * b;
+      if (gr < n && gc < n) {
+        Cx<S>& m = M[(int64_t)gr * ld + gc];
+        m.re -= acc[a][b].re;
+        m.im -= acc[a][b].im;
+      }
+    }
+}
+
+// ---- solves with the factor: x = U^{-1} L^{-1} P b; one CTA per (matrix) -------------------
+template <class S, class SB>
+__global__ void __launch_bounds__(256) k_lu_solve(const Cx<S>* __restrict__ LU, int64_t bstride, int n, int ld,
+                                                  const int32_t* __restrict__ piv, Cx<SB>* __restrict__ b,
+                                                  int64_t bstride_b) {
+  const Cx<S>* M = LU + (int64_t)blockIdx.x * bstride;
+  const int32_t* pv = piv + (int64_t)blockIdx.x * n;
+  Cx<SB>* x = b + (int64_t)blockIdx.x * bstride_b;
+  __shared__ SB red[2][8];
+  __shared__ Cx<SB> xr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0)
+    for (int s = 0; s < n; ++s) {
+      int p = pv[s];
+      if (p != s) { Cx<SB> t = x[s]; x[s] = x[p]; x[p] = t; }
+    }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int ii = 0; ii < n; ++ii) {
+      const int r = pass == 0 ? ii : n - 1 - ii;
+      SB sr = 0, si = 0;
+      const int lo = pass == 0 ? 0 : r + 1, hi = pass == 0 ? r : n;
+      for (int cc = lo + tid; cc < hi; cc += blockDim.x) {
+        Cx<S> l = M[(int64_t)r * ld + cc];
+        Cx<SB> v = x[cc];
+        sr += (SB)l.re * v.re - (SB)l.im * v.im;
+        si += (SB)l.re * v.im + (SB)l.im * v.re;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+      __syncthreads();
+      if (tid == 0) {
+        SB tr = 0, ti = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += red[0][w]; ti += red[1][w]; }
+        Cx<SB> v = {x[r].re - tr, x[r].im - ti};
+        if (pass == 1) {
+          Cx<S> d = M[(int64_t)r * ld + r];
+          Cx<SB> dd = {(SB)d.re, (SB)d.im};
+          SB den = dd.re * dd.re + dd.im * dd.im;
+          v = {(v.re * dd.re + v.im * dd.im) / den, (v.im * dd.re - v.re * dd.im) / den};
+        }
+        x[r] = v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---- host drivers -----------------------------------------------------------------------------
+template <class S>
+int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
+                   int nb) {
+  if (nb > 64) nb = 64;
+  for (int p0 = 0; p0 < n; p0 += nb) {
+    const int w = std::min(nb, n - p0);
+    k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info);
+    dim3 gs((unsigned)((n + 127) / 128), batch);
+    k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv);
+    const int rem = n - p0 - w;
+    if (rem > 0) {
+      dim3 gg((unsigned)((rem + 63) / 64), (unsigned)((rem + 63) / 64), batch);
+      k_gemm_update<S><<<gg, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w);
+    }
+  }
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int lu_factor64(bie_ctx* c, cd* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info) {
+  return lu_factor_simt<double>(c, reinterpret_cast<Cx<double>*>(A), batch, n, ld, bstride, piv, info, 32);
+}
+int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cd* b,
+               int64_t bstride_b) {
+  k_lu_solve<double, double><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<double>*>(LU), bstride, n, ld,
+                                                           piv, reinterpret_cast<Cx<double>*>(b), bstride_b);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info) {
+  return lu_factor_simt<float>(c, reinterpret_cast<Cx<float>*>(A), batch, n, ld, bstride, piv, info, 32);
+}
+int lu_solve32(bie_ctx* c, const cf* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cf* b,
+               int64_t bstride_b) {
+  k_lu_solve<float, float><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<float>*>(LU), bstride, n, ld, piv,
+                                                         reinterpret_cast<Cx<float>*>(b), bstride_b);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+}  // namespace bie

@@ -1,0 +1,75 @@
+"""Convenience wrapper: one bie_ctx plus torch-allocated device outputs.
+
+Each method calls exactly one entry point of the C ABI (same argument meaning as include/bie.h).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class Solver:
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.ctx = B.bie_create(device, self.stream.cuda_stream)
+        self.N = 0
+
+    def close(self):
+        if self.ctx:
+            B.bie_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return torch.device("cuda", self.device)
+
+    def set_quadrature(self, ng: int = 4, ng_near: int = 6):
+        B.bie_set_quadrature(self.ctx, ng, ng_near)
+
+    def set_geometry(self, nodes, elems, normals, bc):
+        B.bie_set_geometry(self.ctx, nodes, elems, normals, bc)
+        self.N = int(np.asarray(nodes).shape[0])
+
+    def set_incident_plane_wave(self, direction):
+        B.bie_set_incident_plane_wave(self.ctx, direction)
+
+    def assemble(self, k: float):
+        A = torch.empty((self.N, self.N), dtype=torch.complex128, device=self._dev())
+        b = torch.empty((self.N,), dtype=torch.complex128, device=self._dev())
+        B.bie_assemble(self.ctx, k, A, b)
+        return A, b
+
+    def solve_frequencies(self, k, mode: int = B.BIE_MODE_FP64, out=None):
+        k = np.ascontiguousarray(k, np.float64)
+        surf = out if out is not None else torch.empty((k.shape[0], 2, self.N), dtype=torch.complex128,
+                                                       device=self._dev())
+        rep = B.bie_solve_frequencies(self.ctx, k, mode, surf)
+        return surf, rep
+
+    def eval_field(self, xobs: torch.Tensor, k, surf: torch.Tensor, mode: int = B.BIE_MODE_FP64, out=None):
+        k = np.ascontiguousarray(k, np.float64)
+        T = out if out is not None else torch.empty((k.shape[0], xobs.shape[0]), dtype=torch.complex128,
+                                                    device=self._dev())
+        B.bie_eval_field(self.ctx, xobs, k, surf, mode, T)
+        return T
+
+    def pulse_spectrum(self, s: torch.Tensor, out=None):
+        S = out if out is not None else torch.empty((s.shape[0], s.shape[1] // 2 + 1), dtype=torch.complex128,
+                                                    device=self._dev())
+        B.bie_pulse_spectrum(self.ctx, s, S)
+        return S
+
+    def synthesize(self, T: torch.Tensor, midx, S: torch.Tensor, Nt: int, out_dtype=torch.float64, out=None):
+        code = 0 if out_dtype == torch.float64 else 1
+        o = out if out is not None else torch.empty((S.shape[0], T.shape[1], Nt), dtype=out_dtype,
+                                                    device=self._dev())
+        B.bie_synthesize(self.ctx, T, midx, S, Nt, o, code)
+        return o
