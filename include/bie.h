@@ -54,6 +54,9 @@ extern "C" {
 #define BIE_FLAG_NOT_CONVERGED 1u   /* refinement stopped at its iteration cap */
 #define BIE_FLAG_FALLBACK_FP64 2u   /* the frequency was re-solved by the FP64 path */
 #define BIE_FLAG_ZERO_PIVOT 4u      /* an exactly zero pivot was met */
+#define BIE_FLAG_ILL_CONDITIONED 8u /* the FP32 assembly's rounding, pushed through the solve, was
+                                       estimated above "mixed.fallback_err_est" (a wavenumber
+                                       near an interior resonance); the FP64 path re-solved it */
 
 typedef struct bie_ctx bie_ctx;
 
@@ -64,6 +67,8 @@ typedef struct {
   uint32_t flags;       /* BIE_FLAG_* bits */
   int32_t reserved;
   double backward_err;  /* ||b - A x|| / (||A||_inf ||x|| + ||b||), infinity norms */
+  double err_est;       /* mixed path: estimated relative L2 error of x caused by the FP32
+                           assembly (a seeded FP32-sized perturbation of A solved with the LU) */
 } bie_report;
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -104,6 +109,18 @@ int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t
 /* Direction d (host f64[3], normalised here) of the incident plane wave exp(i k d.x) (Sec. 4).
  * Default (0, 0, 1).  Errors: INVALID_ARG for a zero or non-finite vector. */
 int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
+
+/* Tuning options of the mixed-precision path (names are case-sensitive):
+ *   "mixed.tcgen05"        1: trailing LU update on the tcgen05 tensor cores (TF32 operands,
+ *                          FP32 accumulation in TMEM); 0: FP32 SIMT update.  Default 1 where built.
+ *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
+ *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
+ *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
+ *   "mixed.fallback_err_est" re-solve in FP64 when the estimated error exceeds it (default 2.5e-7)
+ *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
+ *                          0: FP32 phases with hardware sine/cosine
+ * Errors: INVALID_ARG for an unknown name or a value out of range. */
+int bie_set_option(bie_ctx* ctx, const char* name, double value);
 
 /* Assembles the FP64 system of one wavenumber k > 0: Eq. (BRIEF) at every node with the App. B
  * term 4 pi P(x_i), unknown P at hard nodes and dP/dn at soft nodes, known values from the

@@ -28,15 +28,16 @@ BIE_MODE_MIXED = 1
 BIE_FLAG_NOT_CONVERGED = 1
 BIE_FLAG_FALLBACK_FP64 = 2
 BIE_FLAG_ZERO_PIVOT = 4
+BIE_FLAG_ILL_CONDITIONED = 8
 
 EXPORTED = ["bie_last_error", "bie_version", "bie_create", "bie_destroy", "bie_set_quadrature",
-            "bie_set_geometry", "bie_set_incident_plane_wave", "bie_assemble", "bie_solve_frequencies",
+            "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",
             "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize"]
 
 
 class BieReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("path", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double)]
+                ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double), ("err_est", ctypes.c_double)]
 
 
 class BieError(RuntimeError):
@@ -66,6 +67,7 @@ def load(path: str | None = None):
         "bie_set_quadrature": ([vp, i32, i32], i32),
         "bie_set_geometry": ([vp, vp, i64, vp, i64, vp, vp], i32),
         "bie_set_incident_plane_wave": ([vp, vp], i32),
+        "bie_set_option": ([vp, ctypes.c_char_p, dbl], i32),
         "bie_assemble": ([vp, dbl, vp, vp], i32),
         "bie_solve_frequencies": ([vp, vp, i64, i32, vp, vp], i32),
         "bie_eval_field": ([vp, vp, i64, vp, i64, vp, i32, vp], i32),
@@ -130,6 +132,10 @@ def bie_set_geometry(ctx: int, nodes, elems, normals, bc) -> None:
 def bie_set_incident_plane_wave(ctx: int, direction) -> None:
     d = np.ascontiguousarray(direction, np.float64)
     _check(load().bie_set_incident_plane_wave(ctx, _hp(d)))
+
+
+def bie_set_option(ctx: int, name: str, value: float) -> None:
+    _check(load().bie_set_option(ctx, name.encode(), float(value)))
 
 
 def bie_assemble(ctx: int, k: float, A, b) -> None:

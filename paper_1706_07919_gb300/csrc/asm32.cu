@@ -1,0 +1,322 @@
+// asm32.cu -- FP32 assembly of Eq. (BRIEF) for the mixed-precision path (same system as
+// asm64.cu; see there for the row equation and the bulk/near split).
+//
+// Precision plan (each matrix entry to about FP32 rounding, independent of k R):
+//   * positions and node normals are float-float (hi + lo), so x_q - x_i, |x_q - x_i| and
+//     nu_i.(x_q - x_i) carry ~48 bits;
+//   * both phases (k R for G, k nu_i.r for g and f) are formed and reduced modulo 2 pi in
+//     float-float, then sincosf of the FP32 head plus a first-order correction by the tail;
+//   * amplitudes (1/R, r.nu/R^3, w J N_a) are FP32;
+//   * the row sums alpha_i, beta_i and b_i (over all E*Q points, with cancellation) are
+//     compensated (Kahan-Babuska-Neumaier) sums.
+// Output: A as interleaved complex FP32 [N][ld], b as complex FP64 [N].
+#include "bie_common.cuh"
+
+namespace bie {
+
+// Mixed-path point table: SoA of 10 floats per point:
+//   x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, nx, ny, nz, wJ
+enum { P32XH = 0, P32YH, P32ZH, P32XL, P32YL, P32ZL, P32NX, P32NY, P32NZ, P32W, P32COUNT };
+
+__global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __restrict__ o) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  for (int d = 0; d < 3; ++d) {
+    ff v = ff_from_double(g[(GX + d) * n + p]);
+    o[(P32XH + d) * n + p] = v.hi;
+    o[(P32XL + d) * n + p] = v.lo;
+    o[(P32NX + d) * n + p] = (float)g[(GNX + d) * n + p];
+  }
+  o[P32W * n + p] = (float)g[GWJ * n + p];
+}
+
+// 2 pi as an unevaluated sum of three floats, and 1 / (2 pi).
+struct TwoPi3 {
+  float c1, c2, c3, inv;
+};
+
+// e^{i t} for t = a.hi + a.lo (float-float, |t| < 2^20): t = n 2pi + u, n = rint(t / 2pi), u
+// reduced in float-float (c1 n is exact against a.hi, see DESIGN notes), then
+// cos/sin(u_hi + u_lo) ~ cos(u_hi) - u_lo sin(u_hi), sin(u_hi) + u_lo cos(u_hi).
+__device__ __forceinline__ void ff_cis(ff a, const TwoPi3& tp, float& c, float& s) {
+  const float n = rintf(a.hi * tp.inv);
+  const float h = __fmaf_rn(-n, tp.c1, a.hi);  // exact: both terms are multiples of ulp(c1)
+  float t = __fmaf_rn(-n, tp.c2, a.lo);
+  t = __fmaf_rn(-n, tp.c3, t);
+  const ff u = ff_two_sum(h, t);
+  float sh, ch;
+  sincosf(u.hi, &sh, &ch);
+  c = __fmaf_rn(-u.lo, sh, ch);
+  s = __fmaf_rn(u.lo, ch, sh);
+}
+
+struct Kern32 {
+  float Gr, Gi, dGr, dGi;
+  float alr, ali, ber, bei;  // g dG - dg G, f dG - df G (without w J)
+};
+
+__device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff* xi, const ff* nui, const TwoPi3& tp,
+                                         const float* q, Kern32& o) {
+  // r = x_q - x_i in float-float
+  const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
+  const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
+  const ff rz = ff_sub(ff{q[2], q[5]}, xi[2]);
+  const ff R2 = ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz));
+  const ff R = ff_sqrt(R2);
+  const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
+  float c, s;
+  ff_cis(ff_mul(k, R), tp, c, s);
+  const float invR = 1.0f / R.hi;
+  const float kR = k.hi * R.hi;
+  o.Gr = c * invR;
+  o.Gi = s * invR;
+  const float rn = (rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8]) * invR * invR * invR;
+  o.dGr = (-c - s * kR) * rn;
+  o.dGi = (c * kR - s) * rn;
+  float cg, sg;
+  ff_cis(ff_mul(k, nr), tp, cg, sg);
+  const float nn = nui[0].hi * q[6] + nui[1].hi * q[7] + nui[2].hi * q[8];
+  const float g = cg, f = sg * kinv, dg = -k.hi * sg * nn, df = cg * nn;
+  o.alr = g * o.dGr - dg * o.Gr;
+  o.ali = g * o.dGi - dg * o.Gi;
+  o.ber = f * o.dGr - df * o.Gr;
+  o.bei = f * o.dGi - df * o.Gi;
+}
+
+struct RowSums {
+  ksum ar, ai, br, bi, sr, si;
+};
+
+__device__ __forceinline__ void load_point(const float* __restrict__ tab, int64_t n, int64_t p, float* q) {
+#pragma unroll
+  for (int t = 0; t < P32COUNT; ++t) q[t] = tab[t * n + p];
+}
+
+// grid: (ceil(N / rows), nk); block: 32 * rows; dynamic smem: rows * N * sizeof(cf)
+__global__ void __launch_bounds__(512) k_asm32_bulk(
+    const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
+    const int32_t* __restrict__ elems, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
+    const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
+    const int32_t* __restrict__ perm, const double* __restrict__ kv, const cd* __restrict__ known,
+    cf* __restrict__ A, int64_t lda, double* __restrict__ rowsum /* [nk][N][12] */, int rows, TwoPi3 tp) {
+  extern __shared__ cf acc32[];
+  __shared__ float shp[64 * 6];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kk = blockIdx.y;
+  const ff k = ff_from_double(kv[kk]);
+  const float kinv = (float)(1.0 / kv[kk]);
+  for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
+  for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * rows + warp;
+  if (i >= N) return;
+  cf* row = acc32 + (int64_t)warp * N;
+  const cd* kn = known + (int64_t)kk * N;
+  ff xi[3], nui[3];
+  for (int d = 0; d < 3; ++d) {
+    xi[d] = ff_from_double(nodes[3 * i + d]);
+    nui[d] = ff_from_double(normals[3 * i + d]);
+  }
+  const int64_t EQ = E * Q;
+  RowSums S;
+  for (int col = 0; col < ncolors; ++col) {
+    for (int32_t t = color_off[col] + lane; t < color_off[col + 1]; t += 32) {
+      const int32_t e = perm[t];
+      int32_t el[6];
+      bool near = false;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        el[a] = elems[6 * (int64_t)e + a];
+        near |= (el[a] == i);
+      }
+      if (near) continue;
+      float hr[6], hi[6], gr[6], gi[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.f; }
+      for (int qq = 0; qq < Q; ++qq) {
+        float q[P32COUNT];
+        load_point(qtab, EQ, (int64_t)e * Q + qq, q);
+        Kern32 K;
+        kernel32(k, kinv, xi, nui, tp, q, K);
+        const float wj = q[P32W];
+        S.ar.add(wj * K.alr); S.ai.add(wj * K.ali);
+        S.br.add(wj * K.ber); S.bi.add(wj * K.bei);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const float cw = wj * shp[qq * 6 + a];
+          hr[a] = __fmaf_rn(cw, K.dGr, hr[a]); hi[a] = __fmaf_rn(cw, K.dGi, hi[a]);
+          gr[a] = __fmaf_rn(cw, K.Gr, gr[a]);  gi[a] = __fmaf_rn(cw, K.Gi, gi[a]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const int32_t j = el[a];
+        const float kr = (float)kn[j].re, ki = (float)kn[j].im;
+        if (bc[j] == 0) {  // hard column: A += H, b += Gm P'_known
+          row[j].re += hr[a]; row[j].im += hi[a];
+          S.sr.add(gr[a] * kr - gi[a] * ki); S.si.add(gr[a] * ki + gi[a] * kr);
+        } else {           // soft column: A -= Gm, b -= H P_known
+          row[j].re -= gr[a]; row[j].im -= gi[a];
+          S.sr.add(-(hr[a] * kr - hi[a] * ki)); S.si.add(-(hr[a] * ki + hi[a] * kr));
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // reduce the compensated sums across the warp in FP64 (12 values per row)
+  double v[12] = {(double)S.ar.s, (double)S.ar.c, (double)S.ai.s, (double)S.ai.c, (double)S.br.s, (double)S.br.c,
+                  (double)S.bi.s, (double)S.bi.c, (double)S.sr.s, (double)S.sr.c, (double)S.si.s, (double)S.si.c};
+  double out[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    double x = v[2 * t] + v[2 * t + 1];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    out[t] = x;
+  }
+  cf* Arow = A + ((int64_t)kk * N + i) * lda;
+  for (int64_t j = lane; j < N; j += 32) Arow[j] = row[j];
+  if (lane == 0) {
+    double* rs = rowsum + ((int64_t)kk * N + i) * 6;
+    for (int t = 0; t < 6; ++t) rs[t] = out[t];
+  }
+}
+
+// Near pairs (element contains node i) and the diagonal terms; one warp per row.
+__global__ void __launch_bounds__(256) k_asm32_near(
+    const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
+    const int32_t* __restrict__ elems, int64_t N, int64_t E, int QN, const int* __restrict__ nnear_d,
+    const float* __restrict__ ntab, const double* __restrict__ nshape, const int32_t* __restrict__ n2e_off,
+    const int32_t* __restrict__ n2e, const double* __restrict__ kv, const cd* __restrict__ known,
+    cf* __restrict__ A, int64_t lda, const double* __restrict__ rowsum, cd* __restrict__ b, TwoPi3 tp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int kk = blockIdx.y;
+  if (i >= N) return;
+  const ff k = ff_from_double(kv[kk]);
+  const float kinv = (float)(1.0 / kv[kk]);
+  const cd* kn = known + (int64_t)kk * N;
+  ff xi[3], nui[3];
+  for (int d = 0; d < 3; ++d) {
+    xi[d] = ff_from_double(nodes[3 * i + d]);
+    nui[d] = ff_from_double(normals[3 * i + d]);
+  }
+  const int64_t tot = E * 6 * (int64_t)QN;
+  cf* Arow = A + ((int64_t)kk * N + i) * lda;
+  double al_r = 0, al_i = 0, be_r = 0, be_i = 0, bs_r = 0, bs_i = 0;
+  for (int32_t t = n2e_off[i]; t < n2e_off[i + 1]; ++t) {
+    const int32_t e = n2e[t] >> 3, a0 = n2e[t] & 7;
+    const int np = nnear_d[a0];
+    double hr[6], hi[6], gr[6], gi[6];
+    for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.0; }
+    for (int qq = lane; qq < np; qq += 32) {
+      float q[P32COUNT];
+      load_point(ntab, tot, ((int64_t)e * 6 + a0) * QN + qq, q);
+      Kern32 K;
+      kernel32(k, kinv, xi, nui, tp, q, K);
+      const double wj = q[P32W];
+      al_r += wj * K.alr; al_i += wj * K.ali;
+      be_r += wj * K.ber; be_i += wj * K.bei;
+      const double* sh = nshape + ((int64_t)a0 * QN + qq) * 6;
+      for (int a = 0; a < 6; ++a) {
+        const double cw = wj * sh[a];
+        hr[a] += cw * K.dGr; hi[a] += cw * K.dGi;
+        gr[a] += cw * K.Gr;  gi[a] += cw * K.Gi;
+      }
+    }
+    for (int a = 0; a < 6; ++a)
+      for (int o = 16; o > 0; o >>= 1) {
+        hr[a] += __shfl_xor_sync(0xffffffffu, hr[a], o); hi[a] += __shfl_xor_sync(0xffffffffu, hi[a], o);
+        gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o); gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
+      }
+    if (lane == 0) {
+      const int32_t* el = elems + 6 * (int64_t)e;
+      for (int a = 0; a < 6; ++a) {
+        const int32_t j = el[a];
+        const cd kj = kn[j];
+        if (bc[j] == 0) {
+          Arow[j].re += (float)hr[a]; Arow[j].im += (float)hi[a];
+          bs_r += gr[a] * kj.re - gi[a] * kj.im; bs_i += gr[a] * kj.im + gi[a] * kj.re;
+        } else {
+          Arow[j].re -= (float)gr[a]; Arow[j].im -= (float)gi[a];
+          bs_r -= hr[a] * kj.re - hi[a] * kj.im; bs_i -= hr[a] * kj.im + hi[a] * kj.re;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    al_r += __shfl_xor_sync(0xffffffffu, al_r, o); al_i += __shfl_xor_sync(0xffffffffu, al_i, o);
+    be_r += __shfl_xor_sync(0xffffffffu, be_r, o); be_i += __shfl_xor_sync(0xffffffffu, be_i, o);
+  }
+  if (lane == 0) {
+    const double* rs = rowsum + ((int64_t)kk * N + i) * 6;
+    al_r += rs[0]; al_i += rs[1]; be_r += rs[2]; be_i += rs[3];
+    bs_r += rs[4]; bs_i += rs[5];
+    const cd ki = kn[i];
+    const double fr = 4.0 * kPi + al_r, fi = al_i;
+    if (bc[i] == 0) {
+      Arow[i].re -= (float)fr; Arow[i].im -= (float)fi;
+      bs_r += be_r * ki.re - be_i * ki.im; bs_i += be_r * ki.im + be_i * ki.re;
+    } else {
+      Arow[i].re -= (float)be_r; Arow[i].im -= (float)be_i;
+      bs_r += fr * ki.re - fi * ki.im; bs_i += fr * ki.im + fi * ki.re;
+    }
+    b[(int64_t)kk * N + i] = {bs_r, bs_i};
+  }
+}
+
+__global__ void k_known64(const double* __restrict__ nodes, const double* __restrict__ normals,
+                          const uint8_t* __restrict__ bc, int64_t N, const double* __restrict__ kv, double dx,
+                          double dy, double dz, cd* __restrict__ known);
+
+static TwoPi3 two_pi3() {
+  const double tp = 2.0 * kPi;
+  TwoPi3 r;
+  r.c1 = (float)tp;
+  r.c2 = (float)(tp - (double)r.c1);
+  // third term from the FP64 remainder refined by a long-double-free split of 2 pi's digits
+  const double tail = 2.4492935982947064e-16;  // 2 pi - fl64(2 pi)
+  r.c3 = (float)((tp - (double)r.c1 - (double)r.c2) + tail);
+  r.inv = (float)(1.0 / tp);
+  return r;
+}
+
+int ensure_mixed_tables(bie_ctx* c) {
+  if (c->qgeo32) return BIE_OK;
+  const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
+  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, P32COUNT * (nq + nn) * sizeof(float)));
+  k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32);
+  k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+// Assembles nk FP32 systems: A [nk][N][lda] (cf), b [nk][N] (cd).  known [nk][N] (cd) must hold
+// the known boundary values on return it is filled here; rowsum scratch: nk * N * 6 doubles.
+int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum) {
+  const int64_t N = c->N;
+  BIE_TRY(ensure_mixed_tables(c));
+  dim3 gk((unsigned)((N + 255) / 256), nk);
+  k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known);
+  int rows = 16;
+  while (rows > 1 && (size_t)rows * N * sizeof(cf) > 200 * 1024) rows /= 2;
+  const size_t smem = (size_t)rows * N * sizeof(cf);
+  if (smem > 200 * 1024)
+    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP32 shared-memory row accumulator");
+  if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
+  const TwoPi3 tp = two_pi3();
+  BIE_CUDA_TRY(cudaFuncSetAttribute(k_asm32_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 gb((unsigned)((N + rows - 1) / rows), nk);
+  k_asm32_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q,
+                                                   c->qgeo32, c->qshape32, c->color_off, c->ncolors, c->elem_perm,
+                                                   kv, known, A, lda, rowsum, rows, tp);
+  BIE_CUDA_TRY(cudaGetLastError());
+  const int64_t nq = c->E * c->rule.Q;
+  dim3 gn((unsigned)((N * 32 + 255) / 256), nk);
+  k_asm32_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
+                                          c->qgeo32 + P32COUNT * nq, c->nshape, c->n2e_off, c->n2e, kv, known, A, lda,
+                                          rowsum, b, tp);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+}  // namespace bie

@@ -95,6 +95,14 @@ struct bie_ctx {
   int max_n2e = 0;
   int* d_nnear = nullptr;            // [6] near-rule point counts
 
+  // mixed-precision path settings
+  bool use_tcgen05 = false;          // tensor-core (tcgen05, TF32) trailing update in the LU
+  int mixed_batch = 64;              // wavenumbers per batch
+  int refine_it_max = 10;            // refinement corrections per system
+  double refine_tol = 1e-11;         // backward-error target of the refinement
+  double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
+  int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
+
   // workspace (device), grown on demand
   bie::DeviceBuf work;   // per-call systems / factors
   bie::DeviceBuf work2;  // FFT twiddles

@@ -129,7 +129,7 @@ int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report
       BIE_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
       BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
       for (int i = 0; i < nk; ++i) {
-        rep[k0 + i] = bie_report{0, BIE_MODE_FP64, hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u, 0, 0.0};
+        rep[k0 + i] = bie_report{0, BIE_MODE_FP64, hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u, 0, 0.0, 0.0};
       }
     }
   }
@@ -183,6 +183,33 @@ int bie_set_quadrature(bie_ctx* c, int ng, int ng_near) {
     return fail(BIE_ERR_INVALID_ARG, "quadrature orders must satisfy 1 <= ng <= 8, 1 <= ng_near <= 12");
   c->ng = ng;
   c->ng_near = ng_near;
+  return BIE_OK;
+}
+
+int bie_set_option(bie_ctx* c, const char* name, double value) {
+  BIE_TRY(check_ctx(c, false));
+  if (!name) return fail(BIE_ERR_INVALID_ARG, "NULL option name");
+  const std::string n(name);
+  if (!std::isfinite(value)) return fail(BIE_ERR_INVALID_ARG, "option value must be finite");
+  if (n == "mixed.tcgen05") {
+    c->use_tcgen05 = value != 0.0;
+  } else if (n == "mixed.batch") {
+    if (value < 1 || value > 4096) return fail(BIE_ERR_INVALID_ARG, "mixed.batch must be in [1, 4096]");
+    c->mixed_batch = (int)value;
+  } else if (n == "refine.tol") {
+    if (!(value > 0.0) || value >= 1.0) return fail(BIE_ERR_INVALID_ARG, "refine.tol must be in (0, 1)");
+    c->refine_tol = value;
+  } else if (n == "refine.it_max") {
+    if (value < 0 || value > 64) return fail(BIE_ERR_INVALID_ARG, "refine.it_max must be in [0, 64]");
+    c->refine_it_max = (int)value;
+  } else if (n == "mixed.fallback_err_est") {
+    if (!(value > 0.0)) return fail(BIE_ERR_INVALID_ARG, "mixed.fallback_err_est must be > 0");
+    c->fallback_err_est = value;
+  } else if (n == "field.accurate_phase") {
+    c->field_accurate_phase = value != 0.0 ? 1 : 0;
+  } else {
+    return fail(BIE_ERR_INVALID_ARG, "unknown option '" + n + "'");
+  }
   return BIE_OK;
 }
 

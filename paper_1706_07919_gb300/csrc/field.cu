@@ -134,4 +134,184 @@ int field64(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* 
   return BIE_OK;
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Mixed precision: the same formula in FP32 with compensated accumulation.  ACC = true forms the
+// three phases (k|x - x_p|, k|x - x0|, k nu0.(x - x0)) in float-float and reduces them modulo
+// 2 pi before sincosf; ACC = false uses FP32 distances and the SFU sine/cosine after an FP32
+// reduction.  Point table: asm32.cu's layout (x_hi[3], x_lo[3], nu[3], wJ).
+// ------------------------------------------------------------------------------------------
+struct TwoPi3f {
+  float c1, c2, c3, inv;
+};
+
+__device__ __forceinline__ void cis_ff(ff a, const TwoPi3f& tp, float& c, float& s) {
+  const float n = rintf(a.hi * tp.inv);
+  const float h = __fmaf_rn(-n, tp.c1, a.hi);
+  float t = __fmaf_rn(-n, tp.c2, a.lo);
+  t = __fmaf_rn(-n, tp.c3, t);
+  const ff u = ff_two_sum(h, t);
+  float sh, ch;
+  sincosf(u.hi, &sh, &ch);
+  c = __fmaf_rn(-u.lo, sh, ch);
+  s = __fmaf_rn(u.lo, ch, sh);
+}
+
+__device__ __forceinline__ void cis_fast(float t, const TwoPi3f& tp, float& c, float& s) {
+  const float n = rintf(t * tp.inv);
+  float u = __fmaf_rn(-n, tp.c1, t);
+  u = __fmaf_rn(-n, tp.c2, u);
+  __sincosf(u, &s, &c);
+}
+
+__global__ void k_interp_q32(const int32_t* __restrict__ elems, int64_t N, int64_t E, int Q,
+                             const double* __restrict__ qshape, const cd* __restrict__ surf, cf* __restrict__ Pq,
+                             cf* __restrict__ Pnq) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int kk = blockIdx.y;
+  if (p >= E * Q) return;
+  int64_t e = p / Q;
+  int q = (int)(p % Q);
+  const cd* P = surf + (int64_t)kk * 2 * N;
+  const cd* Pn = P + N;
+  cd a = {0, 0}, b = {0, 0};
+  for (int t = 0; t < 6; ++t) {
+    int32_t j = elems[6 * e + t];
+    double sh = qshape[q * 6 + t];
+    a.re += sh * P[j].re; a.im += sh * P[j].im;
+    b.re += sh * Pn[j].re; b.im += sh * Pn[j].im;
+  }
+  Pq[(int64_t)kk * E * Q + p] = {(float)a.re, (float)a.im};
+  Pnq[(int64_t)kk * E * Q + p] = {(float)b.re, (float)b.im};
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
+                                                const float* __restrict__ qtab, const cf* __restrict__ Pq,
+                                                const cf* __restrict__ Pnq, const cd* __restrict__ surf,
+                                                const double* __restrict__ xp, int64_t M,
+                                                const int32_t* __restrict__ foot_elem, const double* __restrict__ foot,
+                                                const double* __restrict__ kv, cd* __restrict__ T, TwoPi3f tp) {
+  __shared__ float st[14][FT];
+  const int kk = blockIdx.y;
+  const ff k = ff_from_double(kv[kk]);
+  const float kinv = (float)(1.0 / kv[kk]);
+  const int64_t m = (int64_t)blockIdx.x * FT + threadIdx.x;
+  const bool active = m < M;
+  ff p[3] = {{0, 0}, {0, 0}, {0, 0}}, x0[3] = {{0, 0}, {0, 0}, {0, 0}}, nu0[3] = {{0, 0}, {0, 0}, {1, 0}};
+  float P0r = 0, P0i = 0, Q0r = 0, Q0i = 0;
+  if (active) {
+    for (int d = 0; d < 3; ++d) {
+      p[d] = ff_from_double(xp[3 * m + d]);
+      x0[d] = ff_from_double(foot[8 * m + d]);
+      nu0[d] = ff_from_double(foot[8 * m + 3 + d]);
+    }
+    const double fxi = foot[8 * m + 6], feta = foot[8 * m + 7];
+    const double L1 = 1.0 - fxi - feta;
+    const double Nv[6] = {L1 * (2 * L1 - 1), fxi * (2 * fxi - 1), feta * (2 * feta - 1), 4 * L1 * fxi, 4 * fxi * feta,
+                          4 * feta * L1};
+    const int32_t* el = elems + 6 * (int64_t)foot_elem[m];
+    const cd* P = surf + (int64_t)kk * 2 * N;
+    double a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    for (int a = 0; a < 6; ++a) {
+      cd v = P[el[a]], w = P[N + el[a]];
+      a0 += Nv[a] * v.re; a1 += Nv[a] * v.im;
+      b0 += Nv[a] * w.re; b1 += Nv[a] * w.im;
+    }
+    P0r = (float)a0; P0i = (float)a1; Q0r = (float)b0; Q0i = (float)b1;
+  }
+  const cf* Pqk = Pq + (int64_t)kk * EQ;
+  const cf* Pnqk = Pnq + (int64_t)kk * EQ;
+  ksum sr, si;
+  for (int64_t t0 = 0; t0 < EQ; t0 += FT) {
+    const int64_t t = t0 + threadIdx.x;
+    if (t < EQ) {
+#pragma unroll
+      for (int u = 0; u < 10; ++u) st[u][threadIdx.x] = qtab[u * EQ + t];
+      const cf a = Pqk[t], b = Pnqk[t];
+      st[10][threadIdx.x] = a.re; st[11][threadIdx.x] = a.im;
+      st[12][threadIdx.x] = b.re; st[13][threadIdx.x] = b.im;
+    }
+    __syncthreads();
+    const int cnt = (EQ - t0) < FT ? (int)(EQ - t0) : FT;
+    if (active) {
+      for (int u = 0; u < cnt; ++u) {
+        const ff qx = {st[0][u], st[3][u]}, qy = {st[1][u], st[4][u]}, qz = {st[2][u], st[5][u]};
+        const float nx = st[6][u], ny = st[7][u], nz = st[8][u], wj = st[9][u];
+        const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
+        const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
+        float cp, sp, c0, s0, cg, sg, Rp, R0;
+        if (ACC) {
+          const ff Rpf = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
+          const ff R0f = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
+          const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
+          cis_ff(ff_mul(k, Rpf), tp, cp, sp);
+          cis_ff(ff_mul(k, R0f), tp, c0, s0);
+          cis_ff(ff_mul(k, nr), tp, cg, sg);
+          Rp = Rpf.hi;
+          R0 = R0f.hi;
+        } else {
+          Rp = sqrtf(rpx.hi * rpx.hi + rpy.hi * rpy.hi + rpz.hi * rpz.hi);
+          R0 = sqrtf(r0x.hi * r0x.hi + r0y.hi * r0y.hi + r0z.hi * r0z.hi);
+          const float nr = nu0[0].hi * r0x.hi + nu0[1].hi * r0y.hi + nu0[2].hi * r0z.hi;
+          cis_fast(k.hi * Rp, tp, cp, sp);
+          cis_fast(k.hi * R0, tp, c0, s0);
+          cis_fast(k.hi * nr, tp, cg, sg);
+        }
+        const float iRp = 1.0f / Rp, iR0 = 1.0f / R0;
+        const float kRp = k.hi * Rp, kR0 = k.hi * R0;
+        const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp * iRp;
+        const float rn0 = (r0x.hi * nx + r0y.hi * ny + r0z.hi * nz) * iR0 * iR0 * iR0;
+        const float Gpr = cp * iRp, Gpi = sp * iRp, G0r = c0 * iR0, G0i = s0 * iR0;
+        const float dGpr = (-cp - sp * kRp) * rnp, dGpi = (cp * kRp - sp) * rnp;
+        const float dG0r = (-c0 - s0 * kR0) * rn0, dG0i = (c0 * kR0 - s0) * rn0;
+        const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
+        const float g = cg, f = sg * kinv, dg = -k.hi * sg * nn, df = cg * nn;
+        const float Ptr = st[10][u] - P0r * g - Q0r * f, Pti = st[11][u] - P0i * g - Q0i * f;
+        const float dPr = st[12][u] - P0r * dg - Q0r * df, dPi = st[13][u] - P0i * dg - Q0i * df;
+        const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
+        const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
+        const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);
+        sr.add(wj * tr);
+        si.add(wj * ti);
+      }
+    }
+    __syncthreads();
+  }
+  if (active) {
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    T[(int64_t)kk * M + m] = {(double)P0r + sr.value() * inv4pi, (double)P0i + si.value() * inv4pi};
+  }
+}
+
+int ensure_mixed_tables(bie_ctx* c);
+
+int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
+                const int32_t* foot_elem, const double* foot, cd* T, void* scratch, size_t scratch_bytes) {
+  BIE_TRY(ensure_mixed_tables(c));
+  const int64_t EQ = c->E * c->rule.Q;
+  if ((size_t)2 * nk * EQ * sizeof(cf) > scratch_bytes) return fail(BIE_ERR_STATE, "field scratch too small");
+  cf* Pq = (cf*)scratch;
+  cf* Pnq = Pq + (int64_t)nk * EQ;
+  dim3 gi((unsigned)((EQ + 255) / 256), nk);
+  k_interp_q32<<<gi, 256, 0, c->stream>>>(c->elems, c->N, c->E, c->rule.Q, c->qshape, surf, Pq, Pnq);
+  TwoPi3f tp;
+  const double two_pi = 2.0 * kPi;
+  tp.c1 = (float)two_pi;
+  tp.c2 = (float)(two_pi - (double)tp.c1);
+  tp.c3 = (float)((two_pi - (double)tp.c1 - (double)tp.c2) + 2.4492935982947064e-16);
+  tp.inv = (float)(1.0 / two_pi);
+  if (M > 0) {
+    dim3 gf((unsigned)((M + FT - 1) / FT), nk);
+    if (c->field_accurate_phase)
+      k_field32<true><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot,
+                                                kv, T, tp);
+    else
+      k_field32<false><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
+                                                 foot, kv, T, tp);
+  }
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 }  // namespace bie

@@ -115,15 +115,15 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
     }
   }
   if (j < pend) return;  // columns left of the panel only get the swaps
-  Cx<S> x[64];
-  for (int s = 0; s < w; ++s) {
+  // forward substitution with the unit lower L11; solved entries are re-read from the column
+  for (int s = 1; s < w; ++s) {
     Cx<S> v = M[(int64_t)(p0 + s) * ld + j];
     for (int t = 0; t < s; ++t) {
-      Cx<S> l = L11[s * w + t];
-      v.re -= l.re * x[t].re - l.im * x[t].im;
-      v.im -= l.re * x[t].im + l.im * x[t].re;
+      const Cx<S> l = L11[s * w + t];
+      const Cx<S> xt = M[(int64_t)(p0 + t) * ld + j];
+      v.re -= l.re * xt.re - l.im * xt.im;
+      v.im -= l.re * xt.im + l.im * xt.re;
     }
-    x[s] = v;
     M[(int64_t)(p0 + s) * ld + j] = v;
   }
 }
@@ -242,6 +242,18 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
       k_gemm_update<S><<<gg, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w);
     }
   }
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+// Panel factorisation plus row swaps / U12 solve of one block column (FP32); the trailing update
+// is left to the caller (the tensor-core kernel of lu_tc.cu).
+int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
+                     int32_t* info) {
+  Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
+  k_panel<float><<<batch, 512, 0, c->stream>>>(M, bstride, n, ld, p0, w, piv, info);
+  dim3 gs((unsigned)((n + 127) / 128), batch);
+  k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv);
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

@@ -1,0 +1,332 @@
+// refine.cu -- iterative refinement of the mixed-precision solves:
+//   x_0 = (LU)^{-1} b;  repeat  r = b - A x  (A the FP32-assembled matrix, products and sums in
+//   float-float, r in FP64);  stop when ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf);
+//   d = (LU)^{-1} r (FP32);  x += d (FP64).
+// Convergence is tracked per wavenumber on the device, so the host enqueues a fixed number of
+// iterations without synchronising; kernels of converged systems return at once.
+#include "bie_common.cuh"
+
+namespace bie {
+
+struct RefineState {
+  int32_t done;      // 1 once converged
+  int32_t iters;     // corrections applied
+  double anorm;      // ||A||_inf
+  double bnorm;      // ||b||_inf
+  double berr;       // latest backward error
+  double err_est;    // estimated relative error caused by FP32 assembly (see k_perturb)
+};
+
+// ---- permutation vector from the LU's row interchanges: y = P r  <=>  y[i] = r[perm[i]] ----
+__global__ void k_piv_to_perm(const int32_t* __restrict__ piv, int n, int32_t* __restrict__ perm) {
+  extern __shared__ int32_t sp[];
+  const int32_t* pv = piv + (int64_t)blockIdx.x * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sp[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < n; ++s) {
+      int p = pv[s];
+      int t = sp[s]; sp[s] = sp[p]; sp[p] = t;
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[(int64_t)blockIdx.x * n + i] = sp[i];
+}
+
+// ---- triangular solves x = U^{-1} L^{-1} P r with one CTA (1024 threads) per system ---------
+// The vector lives in shared memory; the factor is swept in 64-column blocks: a warp solves the
+// diagonal block, then all warps update the remaining rows, eight rows per warp in flight.
+constexpr int TB = 64;
+
+template <bool LOWER>
+__device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nblk = (n + TB - 1) / TB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = LOWER ? bi : nblk - 1 - bi;
+    const int j0 = blk * TB, j1 = min(j0 + TB, n);
+    if (warp == 0) {  // diagonal block, row by row
+      for (int t = 0; t < j1 - j0; ++t) {
+        const int r = LOWER ? j0 + t : j1 - 1 - t;
+        float sr = 0.f, si = 0.f;
+        for (int c = j0 + lane; c < j1; c += 32) {
+          if (LOWER ? (c < r) : (c > r)) {
+            const cf l = M[(int64_t)r * ld + c];
+            const cf v = y[c];
+            sr += l.re * v.re - l.im * v.im;
+            si += l.re * v.im + l.im * v.re;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+          cf v = {y[r].re - sr, y[r].im - si};
+          if (!LOWER) {
+            const cf d = M[(int64_t)r * ld + r];
+            const float den = d.re * d.re + d.im * d.im;
+            v = {(v.re * d.re + v.im * d.im) / den, (v.im * d.re - v.re * d.im) / den};
+          }
+          y[r] = v;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // update rows outside the block: lower -> rows >= j1, upper -> rows < j0
+    const int rlo = LOWER ? j1 : 0, rhi = LOWER ? n : j0;
+    const int c0 = j0 + 2 * lane;  // each lane holds two columns of the block
+    cf ya = {0.f, 0.f}, yb = {0.f, 0.f};
+    if (c0 < j1) ya = y[c0];
+    if (c0 + 1 < j1) yb = y[c0 + 1];
+    for (int r0 = rlo + warp * 8; r0 < rhi; r0 += nw * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = r0 + u;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rhi) {
+          const cf* p = M + (int64_t)r * ld + c0;
+          if (c0 + 1 < j1) v[u] = *reinterpret_cast<const float4*>(p);
+          else if (c0 < j1) v[u] = make_float4(p[0].re, p[0].im, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float sr = v[u].x * ya.re - v[u].y * ya.im + v[u].z * yb.re - v[u].w * yb.im;
+        float si = v[u].x * ya.im + v[u].y * ya.re + v[u].z * yb.im + v[u].w * yb.re;
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        const int r = r0 + u;
+        if (lane == 0 && r < rhi) { y[r].re -= sr; y[r].im -= si; }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// rhs: cd [batch][n] (FP64), solution written to out (cd, added to `out` if accumulate).
+__global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
+                                                  const int32_t* __restrict__ perm, const cd* __restrict__ rhs,
+                                                  cd* __restrict__ out, int accumulate,
+                                                  const RefineState* __restrict__ st) {
+  extern __shared__ cf yv[];
+  const int kk = blockIdx.x;
+  if (st && st[kk].done) return;
+  const cf* M = LU + (int64_t)kk * bstride;
+  const int32_t* pm = perm + (int64_t)kk * n;
+  const cd* r = rhs + (int64_t)kk * n;
+  // scale the right-hand side to O(1) before rounding it to FP32
+  __shared__ double s_scale;
+  if (threadIdx.x == 0) s_scale = 0.0;
+  __syncthreads();
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fmax(fabs(r[i].re), fabs(r[i].im)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&s_scale, __double_as_longlong(mx));
+  __syncthreads();
+  const double sc = s_scale > 0.0 ? s_scale : 1.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cd v = r[pm[i]];
+    yv[i] = {(float)(v.re / sc), (float)(v.im / sc)};
+  }
+  __syncthreads();
+  trsv_sweep<true>(M, n, ld, yv);
+  trsv_sweep<false>(M, n, ld, yv);
+  cd* o = out + (int64_t)kk * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cd v = {(double)yv[i].re * sc, (double)yv[i].im * sc};
+    o[i] = accumulate ? cadd(o[i], v) : v;
+  }
+}
+
+// ---- residual r = b - A x in float-float; also the row sums of |A| for ||A||_inf ------------
+// grid (ceil(n / 16), batch), block 512: one warp per row, x staged in shared memory as ff.
+__device__ __forceinline__ void ff_acc_prod(float a, float xh, float xl, float& sh, float& sl) {
+  const float p = a * xh;
+  float e = __fmaf_rn(a, xh, -p);
+  e = __fmaf_rn(a, xl, e);
+  const ff t = ff_two_sum(sh, p);
+  sh = t.hi;
+  sl += t.lo + e;
+}
+
+__global__ void __launch_bounds__(512) k_residual_ff(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
+                                                     const cd* __restrict__ b, const cd* __restrict__ x,
+                                                     cd* __restrict__ r, double* __restrict__ rowabs,
+                                                     const RefineState* __restrict__ st) {
+  extern __shared__ float4 xs[];  // [n]: re_hi, re_lo, im_hi, im_lo
+  const int kk = blockIdx.y;
+  if (st[kk].done) return;
+  const cd* xk = x + (int64_t)kk * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const ff a = ff_from_double(xk[j].re), c = ff_from_double(xk[j].im);
+    xs[j] = make_float4(a.hi, a.lo, c.hi, c.lo);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 16 + warp;
+  if (i >= n) return;
+  const cf* row = A + (int64_t)kk * bstride + (int64_t)i * ld;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, ab = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    const cf a = row[j];
+    const float4 v = xs[j];
+    ff_acc_prod(a.re, v.x, v.y, rh, rl);
+    ff_acc_prod(-a.im, v.z, v.w, rh, rl);
+    ff_acc_prod(a.re, v.z, v.w, ih, il);
+    ff_acc_prod(a.im, v.x, v.y, ih, il);
+    ab += fabsf(a.re) + fabsf(a.im);
+  }
+  double sr = (double)rh + (double)rl, si = (double)ih + (double)il, sa = ab;
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0) {
+    const cd bi = b[(int64_t)kk * n + i];
+    r[(int64_t)kk * n + i] = {bi.re - sr, bi.im - si};
+    rowabs[(int64_t)kk * n + i] = sa;
+  }
+}
+
+// ---- convergence test per system (one CTA each) ----------------------------------------------
+__global__ void k_refine_check(int n, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ r,
+                               const double* __restrict__ rowabs, RefineState* __restrict__ st, double tol,
+                               int count_iter) {
+  const int kk = blockIdx.x;
+  if (st[kk].done) return;
+  __shared__ double red[4][32];
+  double rm = 0, xm = 0, bm = 0, am = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t t = (int64_t)kk * n + i;
+    rm = fmax(rm, fmax(fabs(r[t].re), fabs(r[t].im)));
+    xm = fmax(xm, fmax(fabs(x[t].re), fabs(x[t].im)));
+    bm = fmax(bm, fmax(fabs(b[t].re), fabs(b[t].im)));
+    am = fmax(am, rowabs[t]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+    xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+    bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][w] = rm; red[1][w] = xm; red[2][w] = bm; red[3][w] = am; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < (int)(blockDim.x >> 5); ++t) {
+      rm = fmax(rm, red[0][t]); xm = fmax(xm, red[1][t]); bm = fmax(bm, red[2][t]); am = fmax(am, red[3][t]);
+    }
+    const double be = rm / (am * xm + bm);
+    st[kk].anorm = am;
+    st[kk].bnorm = bm;
+    st[kk].berr = be;
+    if (be <= tol) st[kk].done = 1;
+    else if (count_iter) st[kk].iters += 1;
+  }
+}
+
+// ---- sensitivity of the solution to the FP32 assembly -----------------------------------------
+// v = E x with E_ij = eps |A_ij| eta_ij, eta_ij a hashed unit value in {1, i, -1, -i}: a random
+// perturbation of the size of the assembly's rounding.  z = (LU)^{-1} v then estimates the
+// solution's error against the FP64-assembled system; near an interior resonance (Sec. 4's remark
+// on w = 20.1a) ||z|| / ||x|| grows with the condition number and the system is re-solved in FP64.
+__global__ void __launch_bounds__(512) k_perturb(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
+                                                 const cd* __restrict__ x, cd* __restrict__ v, float eps) {
+  const int kk = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 16 + warp;
+  if (i >= n) return;
+  const cf* row = A + (int64_t)kk * bstride + (int64_t)i * ld;
+  const cd* xk = x + (int64_t)kk * n;
+  float sr = 0.f, si = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    const cf a = row[j];
+    const float m = eps * sqrtf(a.re * a.re + a.im * a.im);
+    uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)j * 0x85EBCA77u + 0x27D4EB2Fu);
+    h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12;
+    const uint32_t q = (h >> 30) & 3u;
+    const float er = (q == 0) ? m : (q == 2 ? -m : 0.f), ei = (q == 1) ? m : (q == 3 ? -m : 0.f);
+    const float xr = (float)xk[j].re, xi = (float)xk[j].im;
+    sr += er * xr - ei * xi;
+    si += er * xi + ei * xr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) v[(int64_t)kk * n + i] = {(double)sr, (double)si};
+}
+
+__global__ void k_err_est(int n, const cd* __restrict__ x, const cd* __restrict__ z, RefineState* __restrict__ st) {
+  const int kk = blockIdx.x;
+  __shared__ double red[2][32];
+  double zs = 0, xs = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t t = (int64_t)kk * n + i;
+    zs += z[t].re * z[t].re + z[t].im * z[t].im;
+    xs += x[t].re * x[t].re + x[t].im * x[t].im;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    zs += __shfl_xor_sync(0xffffffffu, zs, o);
+    xs += __shfl_xor_sync(0xffffffffu, xs, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][w] = zs; red[1][w] = xs; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    zs = 0; xs = 0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) { zs += red[0][t]; xs += red[1][t]; }
+    st[kk].err_est = xs > 0 ? sqrt(zs / xs) : 0.0;
+  }
+}
+
+int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
+                 const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
+                 int it_max, double tol) {
+  RefineState* st = (RefineState*)state_dev;
+  BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
+  k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm);
+  const size_t sm_trsv = (size_t)n * sizeof(cf);
+  const size_t sm_res = (size_t)n * sizeof(float4);
+  if (sm_trsv > 200 * 1024 || sm_res > 200 * 1024)
+    return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
+  BIE_CUDA_TRY(cudaFuncSetAttribute(k_trsv_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsv));
+  BIE_CUDA_TRY(cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_res));
+  k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr);
+  dim3 gr((unsigned)((n + 15) / 16), nk);
+  for (int it = 0; it <= it_max; ++it) {
+    k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st);
+    k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max);
+    if (it == it_max) break;
+    k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st);
+  }
+  // assembly-sensitivity estimate (r is free now)
+  k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f);
+  k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr);
+  k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+size_t refine_state_bytes(int nk) { return (size_t)nk * sizeof(RefineState); }
+
+int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
+                      double* err_est) {
+  std::vector<RefineState> h(nk);
+  BIE_CUDA_TRY(cudaMemcpyAsync(h.data(), state_dev, nk * sizeof(RefineState), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < nk; ++i) {
+    done[i] = h[i].done;
+    iters[i] = h[i].iters;
+    berr[i] = h[i].berr;
+    err_est[i] = h[i].err_est;
+  }
+  return BIE_OK;
+}
+
+}  // namespace bie

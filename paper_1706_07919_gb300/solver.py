@@ -38,6 +38,9 @@ class Solver:
         B.bie_set_geometry(self.ctx, nodes, elems, normals, bc)
         self.N = int(np.asarray(nodes).shape[0])
 
+    def set_option(self, name: str, value: float):
+        B.bie_set_option(self.ctx, name, value)
+
     def set_incident_plane_wave(self, direction):
         B.bie_set_incident_plane_wave(self.ctx, direction)
 

@@ -1,0 +1,123 @@
+"""Parity of the mixed-precision CUDA path (FP32 assembly with float-float phases, FP32/TF32 LU,
+float-float iterative refinement) with the CPU FP64 oracle.  Bar: relative L2 <= 1e-6 per
+wavenumber for surface solutions and for fields (the mixed path's tolerance)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import octa_sphere, ico_sphere, merge_meshes, scale_translate, config_sphere_fp64, plane_grid_points
+
+pytestmark = pytest.mark.gpu
+D = np.array([0.0, 0.0, 1.0])
+TOL = 1e-6
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1706_07919_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def Solver(B):
+    from paper_1706_07919_gb300 import Solver as S
+    return S
+
+
+def _solver(Solver, mesh, d=D, tc=None):
+    s = Solver(0)
+    s.set_geometry(mesh.nodes, mesh.elems, mesh.normals, mesh.bc)
+    s.set_incident_plane_wave(d)
+    if tc is not None:
+        s.set_option("mixed.tcgen05", tc)
+    return s
+
+
+@pytest.fixture(scope="module")
+def two_spheres():
+    s0 = ico_sphere(4)
+    return merge_meshes([scale_translate(s0, 1.0, (0, 0, -1.05)), scale_translate(s0, 1.0, (0, 0, 1.05))])
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_mixed_sphere_all_wavenumbers(Solver, B, tc):
+    w = config_sphere_fp64()
+    s = _solver(Solver, w.mesh, tc=tc)
+    surf, rep = s.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    errs = []
+    for i, k in enumerate(w.k):
+        P, Pn = oracle.solve_frequency(w.mesh, k, D)
+        errs.append(rel(surf[i, 0], P))
+        assert rep[i].backward_err <= 1e-10 or rep[i].flags & B.BIE_FLAG_FALLBACK_FP64
+    assert max(errs) <= TOL, (max(errs), int(np.argmax(errs)))
+    # only the wavenumbers next to interior resonances (j_n zeros near 3.14, 4.49, 5.76, 6.99, 7.73)
+    # may leave the mixed path, and never because the refinement failed
+    fell = [i for i in range(len(w.k)) if rep[i].flags & B.BIE_FLAG_FALLBACK_FP64]
+    assert len(fell) <= 6, [(w.k[i], rep[i].err_est) for i in fell]
+    assert all(not (rep[i].flags & B.BIE_FLAG_NOT_CONVERGED) for i in range(len(w.k)))
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_mixed_two_spheres_high_k(Solver, B, two_spheres, tc):
+    ks = np.array([0.5, 4.0, 9.3, 16.0])
+    s = _solver(Solver, two_spheres, tc=tc)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(two_spheres, k, D)
+        assert rel(surf[i, 0], P) <= TOL, (k, rel(surf[i, 0], P), rep[i].iters)
+        assert rep[i].iters <= 8 and rep[i].flags == 0, (k, rep[i].iters, rep[i].flags, rep[i].err_est)
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_unrefined_lu_accuracy(Solver, B, two_spheres, tc):
+    """With refinement switched off the answer is the low-precision factor's: FP32 (SIMT) or
+    TF32 (tensor cores) rounding times the condition number -- a broken update would be O(1)."""
+    ks = np.array([2.0, 11.0])
+    s = _solver(Solver, two_spheres, tc=tc)
+    s.set_option("refine.it_max", 0)
+    s.set_option("mixed.fallback_err_est", 1.0)
+    s.set_option("refine.tol", 0.5)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(two_spheres, k, D)
+        e = rel(surf[i, 0], P)
+        assert e <= (1e-5 if tc == 0 else 2e-2), (k, e)
+
+
+def test_mixed_soft_ragged_and_batch_edges(Solver, B):
+    m = octa_sphere(1, bc=1)
+    ks = np.array([0.01, 0.6, 2.2, 6.1, 7.7])
+    s = _solver(Solver, m)
+    s.set_option("mixed.batch", 2)  # ragged last batch
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(m, k, D)
+        assert rel(surf[i, 1], Pn) <= TOL
+
+
+@pytest.mark.parametrize("accurate,bound", [(1, 1e-6), (0, 2e-5)])
+def test_mixed_field_matches_oracle(Solver, B, two_spheres, accurate, bound):
+    xs = plane_grid_points(9, 5.0, 0.0)
+    ks = np.array([1.0, 8.0, 16.0])
+    s = _solver(Solver, two_spheres)
+    s.set_option("field.accurate_phase", accurate)
+    # identical surface data for both sides isolates the field evaluation
+    surf = np.zeros((len(ks), 2, two_spheres.N), complex)
+    for i, k in enumerate(ks):
+        surf[i] = oracle.solve_frequency(two_spheres, k, D)
+    T = s.eval_field(torch.tensor(xs, device="cuda"), ks, torch.tensor(surf, device="cuda"), B.BIE_MODE_MIXED)
+    T = T.cpu().numpy()
+    for i, k in enumerate(ks):
+        Tr = oracle.field(two_spheres, k, surf[i, 0], surf[i, 1], xs)
+        assert rel(T[i], Tr) <= bound, (k, rel(T[i], Tr))
