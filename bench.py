@@ -1,0 +1,384 @@
+"""Benchmark of the hot path: per-frequency boundary-regularised BIE solves followed by the field
+evaluation and Fourier synthesis of the space-time scattered field.
+
+Workload (one step): two sound-hard unit spheres, 720 quadratic elements / 1442 nodes each
+(N = 2884), surface gap 0.1, incident Gaussian plane-wave pulse along the axis; 512 wavenumbers
+k_m = m/32 (ka in (0, 16]) solved in mixed precision (FP32 assembly with float-float phases,
+tcgen05 TF32 LU, float-float iterative refinement, FP64 re-solve of flagged wavenumbers), field on
+a 128 x 128 grid of the plane z = 0 over [-5, 5]^2, synthesis of 1024 time samples.
+
+Metric: frequency solves per second of the whole path (each solve carries its share of the field
+evaluation and synthesis), with space-time points per second and the per-phase times alongside;
+accuracy of the solves against the FP64 GPU path on sampled wavenumbers (the FP64 path itself is
+parity-tested against the CPU oracle).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BEM freq solves/s & space-time pts/s at rel err <=1e-6 vs FP64; roofline frac"
+UNIT = "freq_solves/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    from workloads import config_two_spheres_mixed
+    return config_two_spheres_mixed()
+
+
+# ----------------------------------------------------------------------------- GPU arm ----
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+
+    w = build_workload()
+    Nk, M, Nt, P = len(w.k), w.xobs.shape[0], w.Nt, w.pulses.shape[0]
+    stream = torch.cuda.Stream(dev)
+    sol = Solver(local, stream)
+    sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    sol.set_incident_plane_wave(w.direction)
+    sol.set_option("mixed.tcgen05", 1)
+    sol.set_option("mixed.batch", args.batch)
+    midx = np.arange(1, Nk + 1, dtype=np.int64)
+
+    with torch.cuda.stream(stream):
+        xo = torch.tensor(w.xobs, dtype=torch.float64, device=dev)
+        pulses = torch.tensor(w.pulses, dtype=torch.float64, device=dev)
+        surf = torch.empty((Nk, 2, w.mesh.N), dtype=torch.complex128, device=dev)
+        T = torch.empty((Nk, M), dtype=torch.complex128, device=dev)
+        S = torch.empty((P, Nt // 2 + 1), dtype=torch.complex128, device=dev)
+        out = torch.empty((P, M, Nt), dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    reports = {}
+
+    def step(record=False):
+        if record:
+            ev[0].record(stream)
+        reports["rep"] = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED, out=surf)[1]
+        if record:
+            ev[1].record(stream)
+        sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED, out=T)
+        if record:
+            ev[2].record(stream)
+        sol.pulse_spectrum(pulses, out=S)
+        sol.synthesize(T, midx, S, Nt, torch.float32, out=out)
+        if record:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # kernel launches of one step, from the CUDA activity trace
+    launches_per_step = None
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step()
+            torch.cuda.synchronize(dev)
+        launches_per_step = sum(1 for e in prof.events() if e.device_type.name == "CUDA"
+                                and (e.name.startswith("bie::") or e.name.startswith("void bie::")
+                                     or "tc::" in e.name))
+    except Exception:
+        launches_per_step = None
+
+    phase = np.zeros(3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+            torch.cuda.synchronize(dev)
+            phase += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    t_ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    rep = reports["rep"]
+
+    # ---- accuracy on sampled wavenumbers against the FP64 GPU path (outside the timed region) ----
+    rng = np.random.Generator(np.random.PCG64(2001))
+    sample = np.sort(rng.choice(Nk, size=args.check, replace=False))
+    ks = w.k[sample]
+    s64, _ = sol.solve_frequencies(ks, B.BIE_MODE_FP64)
+    errs = [(torch.linalg.norm(surf[i] - s64[j]) / torch.linalg.norm(s64[j])).item() for j, i in enumerate(sample)]
+    T64 = sol.eval_field(xo, ks, s64, B.BIE_MODE_FP64)
+    ferrs = [(torch.linalg.norm(T[i] - T64[j]) / torch.linalg.norm(T64[j])).item() for j, i in enumerate(sample)]
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
+    e2e = run_e2e(args, w, sol, B, dev, stream)
+
+    # ---- roofline of the dominant kernel (measured live on its stream) ----
+    roof = roofline_live(args, w, sol, B, dev, stream, surf, xo)
+
+    units = Nk * world * args.steps
+    value = units / (t_ms / 1e3)
+    pts = M * Nt * P * world * args.steps / (t_ms / 1e3)
+    nfall = sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded meshes/points/pulse)",
+        "config": {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "E": int(w.mesh.E),
+                   "Nk": Nk, "ka_max": float(w.k[-1]), "M": M, "Nt": Nt, "pulses": P,
+                   "parallelism": f"{world} independent replica(s), one per GPU",
+                   "l2": "working set (64 x 133 MB systems per batch) larger than L2; no flush needed",
+                   "mixed_batch": args.batch},
+        "space_time_pts_per_s": pts,
+        "phase_ms_per_step": {"solve": phase[0] / args.steps, "field": phase[1] / args.steps,
+                              "spectrum_synthesis": phase[2] / args.steps},
+        "accuracy": {"sampled_k": [float(x) for x in ks], "max_rel_err_surface_vs_fp64": max(errs),
+                     "max_rel_err_field_vs_fp64": max(ferrs), "fp64_fallbacks": nfall,
+                     "max_refine_iters": max(r.iters for r in rep)},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "roofline": roof,
+        "gpu_launches": None if launches_per_step is None else launches_per_step * args.steps,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
+        print(json.dumps(line))
+    sol.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, w, sol, B, dev, stream):
+    """Same step through the public API with host buffers: host->device copies of the step's inputs
+    (wavenumber list travels as a host argument; observation points and pulse samples from pinned
+    host memory) and device->host copies of the surface solutions and the space-time field."""
+    import torch
+
+    Nk, M, Nt, P = len(w.k), w.xobs.shape[0], w.Nt, w.pulses.shape[0]
+    hx = torch.tensor(w.xobs, dtype=torch.float64).pin_memory()
+    hp = torch.tensor(w.pulses, dtype=torch.float64).pin_memory()
+    hsurf = torch.empty((Nk, 2, w.mesh.N), dtype=torch.complex128).pin_memory()
+    hout = torch.empty((P, M, Nt), dtype=torch.float32).pin_memory()
+    midx = np.arange(1, Nk + 1, dtype=np.int64)
+    steps = max(1, min(args.steps, 2))
+
+    def one():
+        with torch.cuda.stream(stream):
+            xo = hx.to(dev, non_blocking=True)
+            pl = hp.to(dev, non_blocking=True)
+        surf, _ = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+        T = sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
+        S = sol.pulse_spectrum(pl)
+        o = sol.synthesize(T, midx, S, Nt, torch.float32)
+        with torch.cuda.stream(stream):
+            hsurf.copy_(surf, non_blocking=True)
+            hout.copy_(o, non_blocking=True)
+        stream.synchronize()
+
+    one()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t
+    return {"value": Nk * steps / dt, "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": int(hx.numel() * 8 + hp.numel() * 8 + Nk * 8),
+            "d2h_bytes_per_step": int(hsurf.numel() * 16 + hout.numel() * 4)}
+
+
+def roofline_live(args, w, sol, B, dev, stream, surf, xo):
+    """The dominant kernel of the step is the field evaluation (Eq. BRIEFdmn), an FP32-ALU-bound
+    kernel: algorithmic flops per (point, quadrature point, k) x evaluations / launch time."""
+    import torch
+
+    ks = w.k[-8:]
+    EQ = w.mesh.E * 16
+    M = xo.shape[0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sol.eval_field(xo, ks, surf[-8:], B.BIE_MODE_MIXED)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    sol.eval_field(xo, ks, surf[-8:], B.BIE_MODE_MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / len(ks)
+    flops_per_eval = FIELD_FLOPS_PER_EVAL
+    achieved = flops_per_eval * M * EQ / (ms * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 FFMA, 152 SMs x 128 lanes x 2 flops at 2.07 GHz
+    return {"kernel": "k_field32 (Eq. BRIEFdmn, float-float phases)", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "evals_per_s": M * EQ / (ms * 1e-3), "flops_per_eval": flops_per_eval,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)"}
+
+
+# algorithmic flops of one field evaluation (one observation point, one quadrature point, one k),
+# counted on the FP64 formula: 2 distances (3 sub, 3 mul, 2 add, sqrt, div = 10 each), the
+# foot-point projection nu0.r and nu.nu0 (5 each), 3 complex exponentials (sin, cos, 1 mul = 3
+# each), G and dG for both sources (2 + 8 each), g, f, dg, df (5), Pt and dPt (16), the integrand
+# (2 complex mul + 3 complex sub = 14) and the accumulation (4)
+FIELD_FLOPS_PER_EVAL = 10 * 2 + 5 * 2 + 3 * 3 + 10 * 2 + 5 + 16 + 14 + 4
+
+
+def cpu_baseline(args, w):
+    """The CPU FP64 oracle on a bounded sample of the same workload, all host cores."""
+    import oracle
+
+    oracle.build()
+    cores = oracle.num_threads()
+    rng = np.random.Generator(np.random.PCG64(2002))
+    kidx = rng.choice(len(w.k), size=1, replace=False)
+    pts = w.xobs[rng.choice(w.xobs.shape[0], size=args.cpu_points, replace=False)]
+    t = time.perf_counter()
+    for i in kidx:
+        P, Pn = oracle.solve_frequency(w.mesh, w.k[i], w.direction)
+    t_solve = (time.perf_counter() - t) / len(kidx)
+    t = time.perf_counter()
+    oracle.field(w.mesh, w.k[kidx[0]], P, Pn, pts)
+    t_field = (time.perf_counter() - t) * (w.xobs.shape[0] / len(pts))
+    per_k = t_solve + t_field
+    return {"value": 1.0 / per_k, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(kidx)} wavenumber solve(s) (assembly+LU+solve, N={w.mesh.N}) and the field at "
+                      f"{len(pts)} of {w.xobs.shape[0]} points scaled to all points; synthesis not counted",
+            "seconds_per_frequency": per_k}
+
+
+# ------------------------------------------------------------------------- reference arm ----
+def run_reference(args):
+    """The oracle as the reference arm, timed on the host cores on bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = build_workload()
+    args.cpu_points = max(8, args.cpu_points // 2)
+    vals = []
+    for _ in range(args.warmup):      # warm-up samples (page-in, thread pool start), untimed
+        cpu_baseline(args, w)
+    t = time.perf_counter()
+    cb = None
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(args, w)
+        vals.append(cb["value"])
+    dt = time.perf_counter() - t
+    value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded meshes/points/pulse)", "impl": "reference",
+            "config": {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "Nk": len(w.k),
+                       "M": int(w.xobs.shape[0]), "Nt": w.Nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": dt}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--check", type=int, default=4)
+    ap.add_argument("--cpu-points", dest="cpu_points", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -14,9 +14,11 @@
 
 namespace bie {
 
-// Mixed-path point table: SoA of 10 floats per point:
-//   x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, nx, ny, nz, wJ
-enum { P32XH = 0, P32YH, P32ZH, P32XL, P32YL, P32ZL, P32NX, P32NY, P32NZ, P32W, P32COUNT };
+// Mixed-path point table: SoA of 13 floats per point:
+//   x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, nx, ny, nz, wJ, nx_lo, ny_lo, nz_lo
+// (the normal's low parts let r.nu, a second-order small quantity for nearby points on one smooth
+// surface, be formed in float-float).
+enum { P32XH = 0, P32YH, P32ZH, P32XL, P32YL, P32ZL, P32NX, P32NY, P32NZ, P32W, P32NXL, P32NYL, P32NZL, P32COUNT };
 
 __global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __restrict__ o) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -25,7 +27,9 @@ __global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __
     ff v = ff_from_double(g[(GX + d) * n + p]);
     o[(P32XH + d) * n + p] = v.hi;
     o[(P32XL + d) * n + p] = v.lo;
-    o[(P32NX + d) * n + p] = (float)g[(GNX + d) * n + p];
+    ff nv = ff_from_double(g[(GNX + d) * n + p]);
+    o[(P32NX + d) * n + p] = nv.hi;
+    o[(P32NXL + d) * n + p] = nv.lo;
   }
   o[P32W * n + p] = (float)g[GWJ * n + p];
 }
@@ -70,7 +74,8 @@ __device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff*
   const float kR = k.hi * R.hi;
   o.Gr = c * invR;
   o.Gi = s * invR;
-  const float rn = (rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8]) * invR * invR * invR;
+  const ff rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]}));
+  const float rn = rnu.hi * invR * invR * invR;
   o.dGr = (-c - s * kR) * rn;
   o.dGi = (c * kR - s) * rn;
   float cg, sg;

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
                                                 const double* __restrict__ xp, int64_t M,
                                                 const int32_t* __restrict__ foot_elem, const double* __restrict__ foot,
                                                 const double* __restrict__ kv, cd* __restrict__ T, TwoPi3f tp) {
-  __shared__ float st[14][FT];
+  __shared__ float st[17][FT];
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
   const float kinv = (float)(1.0 / kv[kk]);
@@ -227,10 +227,10 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
     const int64_t t = t0 + threadIdx.x;
     if (t < EQ) {
 #pragma unroll
-      for (int u = 0; u < 10; ++u) st[u][threadIdx.x] = qtab[u * EQ + t];
+      for (int u = 0; u < 13; ++u) st[u][threadIdx.x] = qtab[u * EQ + t];
       const cf a = Pqk[t], b = Pnqk[t];
-      st[10][threadIdx.x] = a.re; st[11][threadIdx.x] = a.im;
-      st[12][threadIdx.x] = b.re; st[13][threadIdx.x] = b.im;
+      st[13][threadIdx.x] = a.re; st[14][threadIdx.x] = a.im;
+      st[15][threadIdx.x] = b.re; st[16][threadIdx.x] = b.im;
     }
     __syncthreads();
     const int cnt = (EQ - t0) < FT ? (int)(EQ - t0) : FT;
@@ -240,8 +240,11 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
         const float nx = st[6][u], ny = st[7][u], nz = st[8][u], wj = st[9][u];
         const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
         const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
-        float cp, sp, c0, s0, cg, sg, Rp, R0;
+        float cp, sp, c0, s0, cg, sg, Rp, R0, rnp, rn0;
         if (ACC) {
+          const ff nux = {nx, st[10][u]}, nuy = {ny, st[11][u]}, nuz = {nz, st[12][u]};
+          rnp = ff_add(ff_add(ff_mul(rpx, nux), ff_mul(rpy, nuy)), ff_mul(rpz, nuz)).hi;
+          rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi;
           const ff Rpf = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
           const ff R0f = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
           const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
@@ -257,18 +260,20 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
           cis_fast(k.hi * Rp, tp, cp, sp);
           cis_fast(k.hi * R0, tp, c0, s0);
           cis_fast(k.hi * nr, tp, cg, sg);
+          rnp = rpx.hi * nx + rpy.hi * ny + rpz.hi * nz;
+          rn0 = r0x.hi * nx + r0y.hi * ny + r0z.hi * nz;
         }
         const float iRp = 1.0f / Rp, iR0 = 1.0f / R0;
         const float kRp = k.hi * Rp, kR0 = k.hi * R0;
-        const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp * iRp;
-        const float rn0 = (r0x.hi * nx + r0y.hi * ny + r0z.hi * nz) * iR0 * iR0 * iR0;
+        rnp *= iRp * iRp * iRp;
+        rn0 *= iR0 * iR0 * iR0;
         const float Gpr = cp * iRp, Gpi = sp * iRp, G0r = c0 * iR0, G0i = s0 * iR0;
         const float dGpr = (-cp - sp * kRp) * rnp, dGpi = (cp * kRp - sp) * rnp;
         const float dG0r = (-c0 - s0 * kR0) * rn0, dG0i = (c0 * kR0 - s0) * rn0;
         const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
         const float g = cg, f = sg * kinv, dg = -k.hi * sg * nn, df = cg * nn;
-        const float Ptr = st[10][u] - P0r * g - Q0r * f, Pti = st[11][u] - P0i * g - Q0i * f;
-        const float dPr = st[12][u] - P0r * dg - Q0r * df, dPi = st[13][u] - P0i * dg - Q0i * df;
+        const float Ptr = st[13][u] - P0r * g - Q0r * f, Pti = st[14][u] - P0i * g - Q0i * f;
+        const float dPr = st[15][u] - P0r * dg - Q0r * df, dPi = st[16][u] - P0i * dg - Q0i * df;
         const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
         const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
         const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);

@@ -88,6 +88,174 @@ __global__ void __launch_bounds__(512) k_panel(Cx<S>* __restrict__ A, int64_t bs
   }
 }
 
+// ---- leaf-recursive panel: a leaf of `lw` columns factored in shared memory ------------------
+// One CTA (1024 threads) per matrix holds rows c0..n-1 of columns c0..c0+lw-1, factors them with
+// partial pivoting (largest modulus, lowest row on ties), writes them back, applies the leaf's
+// row swaps to the other columns of the panel [p0, p0+w) and solves the leaf's U block for the
+// panel columns right of the leaf.
+template <class S>
+__global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w,
+                                               int c0, int lw, int32_t* __restrict__ piv, int32_t* __restrict__ info) {
+  extern __shared__ unsigned char smem_raw[];
+  Cx<S>* L = reinterpret_cast<Cx<S>*>(smem_raw);  // [rows][lw]
+  __shared__ S red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_piv[16];
+  Cx<S>* M = A + (int64_t)blockIdx.x * bstride;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int rows = n - c0;
+  for (int t = tid; t < rows * lw; t += nt) {
+    const int r = t / lw, c = t - r * lw;
+    L[t] = M[(int64_t)(c0 + r) * ld + c0 + c];
+  }
+  __syncthreads();
+  for (int c = 0; c < lw; ++c) {
+    S best = -1;
+    int bi = rows;
+    for (int r = c + tid; r < rows; r += nt) {
+      const Cx<S> v = L[r * lw + c];
+      const S m = v.re * v.re + v.im * v.im;
+      if (m > best) { best = m; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const S ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nw ? red_v[lane] : (S)-1;
+      bi = lane < nw ? red_i[lane] : rows;
+      for (int o = 16; o > 0; o >>= 1) {
+        const S ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (bi >= rows) bi = c;
+        s_piv[c] = bi;
+        piv[(int64_t)blockIdx.x * n + c0 + c] = c0 + bi;
+        if (!(best > 0) && info) atomicOr(info + blockIdx.x, 1);
+      }
+    }
+    __syncthreads();
+    const int p = s_piv[c];
+    if (p != c && tid < lw) {
+      const Cx<S> t = L[c * lw + tid];
+      L[c * lw + tid] = L[p * lw + tid];
+      L[p * lw + tid] = t;
+    }
+    __syncthreads();
+    const Cx<S> d = L[c * lw + c];
+    const bool ok = (d.re != 0 || d.im != 0);
+    for (int r = c + 1 + tid; r < rows; r += nt) {
+      Cx<S> l = L[r * lw + c];
+      if (ok) l = cx_div(l, d);
+      L[r * lw + c] = l;
+      for (int j = c + 1; j < lw; ++j) {
+        const Cx<S> u = L[c * lw + j];
+        Cx<S> a = L[r * lw + j];
+        a.re -= l.re * u.re - l.im * u.im;
+        a.im -= l.re * u.im + l.im * u.re;
+        L[r * lw + j] = a;
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < rows * lw; t += nt) {
+    const int r = t / lw, c = t - r * lw;
+    M[(int64_t)(c0 + r) * ld + c0 + c] = L[t];
+  }
+  // other panel columns: the leaf's swaps (in order), then the U-block solve right of the leaf
+  const int pend = min(p0 + w, n);
+  for (int j = p0 + tid; j < pend; j += nt) {
+    if (j >= c0 && j < c0 + lw) continue;
+    for (int s = 0; s < lw; ++s) {
+      const int p = c0 + s_piv[s];
+      if (p != c0 + s) {
+        const Cx<S> t = M[(int64_t)(c0 + s) * ld + j];
+        M[(int64_t)(c0 + s) * ld + j] = M[(int64_t)p * ld + j];
+        M[(int64_t)p * ld + j] = t;
+      }
+    }
+    if (j >= c0 + lw)
+      for (int s = 1; s < lw; ++s) {
+        Cx<S> v = M[(int64_t)(c0 + s) * ld + j];
+        for (int t = 0; t < s; ++t) {
+          const Cx<S> l = L[s * lw + t];
+          const Cx<S> xt = M[(int64_t)(c0 + t) * ld + j];
+          v.re -= l.re * xt.re - l.im * xt.im;
+          v.im -= l.re * xt.im + l.im * xt.re;
+        }
+        M[(int64_t)(c0 + s) * ld + j] = v;
+      }
+  }
+}
+
+// Rows below the leaf, panel columns right of it: A -= L_leaf U_leaf (K = lw <= 16).
+// grid (ceil(rows / 256), batch), block 256.
+template <class S>
+__global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                                     int w, int c0, int lw) {
+  __shared__ Cx<S> U[16 * 64];
+  Cx<S>* M = A + (int64_t)blockIdx.y * bstride;
+  const int cs = c0 + lw, ce = min(p0 + w, n), wr = ce - cs;
+  if (wr <= 0) return;
+  for (int t = threadIdx.x; t < lw * wr; t += blockDim.x) {
+    const int s = t / wr, j = t - s * wr;
+    U[s * 64 + j] = M[(int64_t)(c0 + s) * ld + cs + j];
+  }
+  __syncthreads();
+  const int r = c0 + lw + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  Cx<S> l[16];
+  for (int s = 0; s < lw; ++s) l[s] = M[(int64_t)r * ld + c0 + s];
+  for (int j = 0; j < wr; ++j) {
+    S ar = 0, ai = 0;
+    for (int s = 0; s < lw; ++s) {
+      const Cx<S> u = U[s * 64 + j];
+      ar += l[s].re * u.re - l[s].im * u.im;
+      ai += l[s].re * u.im + l[s].im * u.re;
+    }
+    Cx<S>& m = M[(int64_t)r * ld + cs + j];
+    m.re -= ar;
+    m.im -= ai;
+  }
+}
+
+// Leaf width for a panel whose rows start at p0: the widest power of two <= 8 whose leaf fits in
+// 200 KB of shared memory; 0 if even one column does not fit (then the global-memory panel runs).
+template <class S>
+static int leaf_width(int n, int p0) {
+  const size_t rows = (size_t)(n - p0);
+  for (int lw = 8; lw >= 1; lw >>= 1)
+    if (rows * lw * sizeof(Cx<S>) <= 200 * 1024) return lw;
+  return 0;
+}
+
+template <class S>
+static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstride, int p0, int w,
+                        int32_t* piv, int32_t* info) {
+  const int lw = leaf_width<S>(n, p0);
+  if (lw == 0 || w > 64) {
+    k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info);
+    return BIE_OK;
+  }
+  BIE_CUDA_TRY(cudaFuncSetAttribute(k_leaf<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  for (int c0 = p0; c0 < p0 + w; c0 += lw) {
+    const int l = std::min(lw, p0 + w - c0);
+    const size_t smem = (size_t)(n - c0) * l * sizeof(Cx<S>);
+    k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info);
+    const int rows = n - c0 - l;
+    if (rows > 0 && c0 + l < p0 + w) {
+      dim3 g((unsigned)((rows + 255) / 256), batch);
+      k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l);
+    }
+  }
+  return BIE_OK;
+}
+
 // ---- row swaps outside the panel, then U12 = L11^{-1} A12 ----------------------------------
 // grid: (ceil(n / 128), batch), block 128: one column per thread.
 template <class S>
@@ -233,7 +401,7 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
   if (nb > 64) nb = 64;
   for (int p0 = 0; p0 < n; p0 += nb) {
     const int w = std::min(nb, n - p0);
-    k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info);
+    BIE_TRY(panel_factor<S>(c, A, batch, n, ld, bstride, p0, w, piv, info));
     dim3 gs((unsigned)((n + 127) / 128), batch);
     k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv);
     const int rem = n - p0 - w;
@@ -251,7 +419,7 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
                      int32_t* info) {
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
-  k_panel<float><<<batch, 512, 0, c->stream>>>(M, bstride, n, ld, p0, w, piv, info);
+  BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
   dim3 gs((unsigned)((n + 127) / 128), batch);
   k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv);
   BIE_CUDA_TRY(cudaGetLastError());
