@@ -164,6 +164,23 @@ int bie_pulse_spectrum(bie_ctx* ctx, const double* s, int64_t P, int64_t Nt, voi
 int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk, int64_t M,
                    const void* S, int64_t P, int64_t Nt, void* out, int out_dtype);
 
+/* Allocation-free variant of bie_synthesize.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run -- a host framework that
+ * hands out a fixed device-memory budget through its own pool, or a latency-bound pipeline in
+ * which cudaMalloc/cudaFree would synchronise the device.  It needs no context and allocates
+ * nothing: its scratch (the FFT twiddle table and the device copy of midx) lives in one
+ * file-scope device array of 64 KB that every GPU loading the library holds until the process
+ * exits.  Arguments and the result are those of bie_synthesize, on the caller's current device
+ * and on `stream` (a cudaStream_t, NULL = legacy default stream); the call returns after the
+ * stream has completed.
+ * Limits: Nt a power of two in [2, 4096] and Nk <= 4096 (midx entries are in [0, Nt/2] anyway);
+ * larger sizes return BIE_ERR_INVALID_ARG with a message.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  All calls share the one array and every call rewrites the parts it uses, so
+ * calls whose work overlaps on the GPU (different streams or threads) race. */
+int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
+                           int64_t P, int64_t Nt, void* out, int out_dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

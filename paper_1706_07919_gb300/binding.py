@@ -32,7 +32,7 @@ BIE_FLAG_ILL_CONDITIONED = 8
 
 EXPORTED = ["bie_last_error", "bie_version", "bie_create", "bie_destroy", "bie_set_quadrature",
             "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",
-            "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize"]
+            "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc"]
 
 
 class BieReport(ctypes.Structure):
@@ -73,6 +73,7 @@ def load(path: str | None = None):
         "bie_eval_field": ([vp, vp, i64, vp, i64, vp, i32, vp], i32),
         "bie_pulse_spectrum": ([vp, vp, i64, i64, vp], i32),
         "bie_synthesize": ([vp, vp, vp, i64, i64, vp, i64, i64, vp, i32], i32),
+        "bie_synthesize_noalloc": ([vp, vp, i64, i64, vp, i64, i64, vp, i32, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -163,3 +164,10 @@ def bie_synthesize(ctx: int, T, midx, S, Nt: int, out, out_dtype: int) -> None:
     midx = np.ascontiguousarray(midx, np.int64)
     _check(load().bie_synthesize(ctx, _dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
                                  _dp(out), out_dtype))
+
+
+def bie_synthesize_noalloc(T, midx, S, Nt: int, out, out_dtype: int, stream: int | None = None) -> None:
+    """Allocation-free synthesis for callers that cannot allocate device memory (see bie.h)."""
+    midx = np.ascontiguousarray(midx, np.int64)
+    _check(load().bie_synthesize_noalloc(_dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
+                                         _dp(out), out_dtype, stream))

@@ -5,6 +5,8 @@
 //   synthesis: out[p][x][n] = (1/Nt) Re sum_m c_m exp(-2 pi i m n / Nt),  c_m = w_m S[p][m] T[m][x],
 //              w_0 = w_{Nt/2} = 1, else 2 (the m > Nt/2 half is the complex conjugate).
 // One CTA transforms one signal in shared memory with a Stockham (self-sorting) radix-2 FFT.
+#include <mutex>
+
 #include "bie_common.cuh"
 
 namespace bie {
@@ -121,4 +123,75 @@ int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t
   return BIE_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Allocation-free synthesis.  Some callers cannot allocate device memory while they run: a host
+// framework that hands out a fixed device-memory budget through its own pool, or a latency-bound
+// pipeline in which cudaMalloc/cudaFree would synchronise the device.  For them the synthesis's
+// scratch (the FFT twiddle table and the device copy of the frequency indices) lives in one
+// file-scope device array instead of context buffers, and no context is needed.
+// ------------------------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;  // twiddles <= 32 KB (Nt <= 4096) + indices <= 32 KB
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device (the host-side
+// name of a __device__ variable is not a device address).
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  BIE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(BIE_ERR_INVALID_ARG, "device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return BIE_OK;
+}
+
 }  // namespace bie
+
+extern "C" int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
+                                      int64_t P, int64_t Nt, void* out, int out_dtype, void* stream) {
+  using namespace bie;
+  if (P < 0 || M < 0 || Nk < 0 || Nt < 2 || Nt > 4096 || (Nt & (Nt - 1)))
+    return fail(BIE_ERR_INVALID_ARG, "need P, M, Nk >= 0 and Nt a power of two in [2, 4096]");
+  if (out_dtype != 0 && out_dtype != 1) return fail(BIE_ERR_INVALID_ARG, "out_dtype must be 0 (f64) or 1 (f32)");
+  if (P > 65535) return fail(BIE_ERR_INVALID_ARG, "P > 65535");
+  if ((size_t)Nk * sizeof(int64_t) > kNoAllocScratchBytes / 2)
+    return fail(BIE_ERR_INVALID_ARG, "Nk = " + std::to_string(Nk) + " exceeds the fixed scratch (at most " +
+                                         std::to_string(kNoAllocScratchBytes / 2 / sizeof(int64_t)) + ")");
+  if (P == 0 || M == 0) return BIE_OK;
+  if ((Nk > 0 && (!T || !midx)) || !S || !out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  for (int64_t r = 0; r < Nk; ++r) {
+    if (midx[r] < 0 || midx[r] > Nt / 2) return fail(BIE_ERR_INVALID_ARG, "midx out of [0, Nt/2]");
+    if (r > 0 && midx[r] <= midx[r - 1]) return fail(BIE_ERR_INVALID_ARG, "midx must be strictly increasing");
+  }
+  void* base = nullptr;
+  BIE_TRY(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = (int)Nt;
+  double2* tw = (double2*)base;  // n/2 entries, rewritten by every call
+  int64_t* md = (int64_t*)((char*)base + kNoAllocScratchBytes / 2);
+  if (Nk > 0) BIE_CUDA_TRY(cudaMemcpyAsync(md, midx, Nk * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  k_twiddles<<<(n / 2 + 255) / 256, 256, 0, st>>>(n, tw);
+  dim3 g((unsigned)M, (unsigned)P);
+  const int threads = std::min(512, std::max(32, n / 2));
+  if (out_dtype == 0) {
+    const size_t smem = 2 * (size_t)n * sizeof(C2<double>);
+    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_synth<double, double><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (double*)out);
+  } else {
+    const size_t smem = 2 * (size_t)n * sizeof(C2<float>);
+    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_synth<float, float><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (float*)out);
+  }
+  BIE_CUDA_TRY(cudaGetLastError());
+  // the host index array must outlive its asynchronous copy
+  BIE_CUDA_TRY(cudaStreamSynchronize(st));
+  return BIE_OK;
+}
