@@ -151,23 +151,11 @@ def run_ours(args):
         step()
     torch.cuda.synchronize(dev)
 
-    # kernel launches of one step, from the CUDA activity trace
-    launches_per_step = None
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            step()
-            torch.cuda.synchronize(dev)
-        launches_per_step = sum(1 for e in prof.events() if e.device_type.name == "CUDA"
-                                and (e.name.startswith("bie::") or e.name.startswith("void bie::")
-                                     or "tc::" in e.name))
-    except Exception:
-        launches_per_step = None
-
     phase = np.zeros(3)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    launches0 = B.bie_kernel_launches()
     with ClockSampler(local) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -181,6 +169,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
     t_ms = t0.elapsed_time(t1)
+    launches = B.bie_kernel_launches() - launches0
     if dist is not None:
         tt = torch.tensor([t_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -206,6 +195,7 @@ def run_ours(args):
     value = units / (t_ms / 1e3)
     pts = M * Nt * P * world * args.steps / (t_ms / 1e3)
     nfall = sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64)
+    nre64 = sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -220,12 +210,12 @@ def run_ours(args):
         "phase_ms_per_step": {"solve": phase[0] / args.steps, "field": phase[1] / args.steps,
                               "spectrum_synthesis": phase[2] / args.steps},
         "accuracy": {"sampled_k": [float(x) for x in ks], "max_rel_err_surface_vs_fp64": max(errs),
-                     "max_rel_err_field_vs_fp64": max(ferrs), "fp64_fallbacks": nfall,
+                     "max_rel_err_field_vs_fp64": max(ferrs), "fp64_reassembled": nre64, "fp64_full_solves": nfall,
                      "max_refine_iters": max(r.iters for r in rep)},
         "clocks": clk.summary(),
         "e2e": e2e,
         "roofline": roof,
-        "gpu_launches": None if launches_per_step is None else launches_per_step * args.steps,
+        "gpu_launches": int(launches),
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None

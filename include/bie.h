@@ -56,7 +56,10 @@ extern "C" {
 #define BIE_FLAG_ZERO_PIVOT 4u      /* an exactly zero pivot was met */
 #define BIE_FLAG_ILL_CONDITIONED 8u /* the FP32 assembly's rounding, pushed through the solve, was
                                        estimated above "mixed.fallback_err_est" (a wavenumber
-                                       near an interior resonance); the FP64 path re-solved it */
+                                       near an interior resonance) */
+#define BIE_FLAG_FP64_ASSEMBLY 16u  /* re-assembled in FP64 and refined against that system with
+                                       the low-precision factor (after ILL_CONDITIONED or a stalled
+                                       refinement); FALLBACK_FP64 is added if that also stalled */
 
 typedef struct bie_ctx bie_ctx;
 
@@ -76,6 +79,10 @@ const char* bie_last_error(void);
 
 /* Library version string. */
 const char* bie_version(void);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded (all contexts and
+ * threads); a diagnostic for counting launches in a region of interest. */
+uint64_t bie_kernel_launches(void);
 
 /* Creates a context on CUDA device `cuda_device` that enqueues on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  *out receives the handle.  The context owns
@@ -116,7 +123,7 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
- *   "mixed.fallback_err_est" re-solve in FP64 when the estimated error exceeds it (default 2.5e-7)
+ *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
  * Errors: INVALID_ARG for an unknown name or a value out of range. */

@@ -29,8 +29,9 @@ BIE_FLAG_NOT_CONVERGED = 1
 BIE_FLAG_FALLBACK_FP64 = 2
 BIE_FLAG_ZERO_PIVOT = 4
 BIE_FLAG_ILL_CONDITIONED = 8
+BIE_FLAG_FP64_ASSEMBLY = 16
 
-EXPORTED = ["bie_last_error", "bie_version", "bie_create", "bie_destroy", "bie_set_quadrature",
+EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create", "bie_destroy", "bie_set_quadrature",
             "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",
             "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc"]
 
@@ -62,6 +63,7 @@ def load(path: str | None = None):
     sigs = {
         "bie_last_error": ([], ctypes.c_char_p),
         "bie_version": ([], ctypes.c_char_p),
+        "bie_kernel_launches": ([], ctypes.c_uint64),
         "bie_create": ([ctypes.POINTER(vp), i32, vp], i32),
         "bie_destroy": ([vp], i32),
         "bie_set_quadrature": ([vp, i32, i32], i32),
@@ -105,6 +107,10 @@ def bie_last_error() -> str:
 
 def bie_version() -> str:
     return load().bie_version().decode()
+
+
+def bie_kernel_launches() -> int:
+    return int(load().bie_kernel_launches())
 
 
 def bie_create(device: int = 0, stream: int | None = None) -> int:

@@ -34,24 +34,47 @@ __global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __
   o[P32W * n + p] = (float)g[GWJ * n + p];
 }
 
+// The bulk kernel's copy of the same table, re-ordered for coalesced loads: elements in colour
+// order (position t of the colour-sorted list) and point-major, index (f * Q + q) * E + t, so
+// that the lanes of a warp -- consecutive elements of one colour -- read consecutive floats.
+// Element connectivity in the same order: esort[a * E + t].
+__global__ void k_points_to32_sorted(const double* __restrict__ g, const int32_t* __restrict__ perm,
+                                     const int32_t* __restrict__ elems, int64_t E, int Q, float* __restrict__ o,
+                                     int32_t* __restrict__ esort) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= E * Q) return;
+  const int64_t t = idx % E;
+  const int q = (int)(idx / E);
+  const int64_t e = perm[t];
+  const int64_t n = E * Q, src = e * Q + q;
+  float v[P32COUNT];
+  for (int d = 0; d < 3; ++d) {
+    const ff x = ff_from_double(g[(GX + d) * n + src]);
+    const ff nv = ff_from_double(g[(GNX + d) * n + src]);
+    v[P32XH + d] = x.hi; v[P32XL + d] = x.lo;
+    v[P32NX + d] = nv.hi; v[P32NXL + d] = nv.lo;
+  }
+  v[P32W] = (float)g[GWJ * n + src];
+  for (int f = 0; f < P32COUNT; ++f) o[((int64_t)f * Q + q) * E + t] = v[f];
+  if (q == 0)
+    for (int a = 0; a < 6; ++a) esort[a * E + t] = elems[6 * e + a];
+}
+
 // 2 pi as an unevaluated sum of three floats, and 1 / (2 pi).
 struct TwoPi3 {
   float c1, c2, c3, inv;
 };
 
 // e^{i t} for t = a.hi + a.lo (float-float, |t| < 2^20): t = n 2pi + u, n = rint(t / 2pi), u
-// reduced in float-float (c1 n is exact against a.hi, see DESIGN notes), then
-// cos/sin(u_hi + u_lo) ~ cos(u_hi) - u_lo sin(u_hi), sin(u_hi) + u_lo cos(u_hi).
+// reduced in float-float (the product n c1 cancels exactly against a.hi: both are multiples of
+// ulp(c1) and the difference is below pi), then cos/sin of u_hi + u_lo by cis_reduced.
 __device__ __forceinline__ void ff_cis(ff a, const TwoPi3& tp, float& c, float& s) {
   const float n = rintf(a.hi * tp.inv);
   const float h = __fmaf_rn(-n, tp.c1, a.hi);  // exact: both terms are multiples of ulp(c1)
   float t = __fmaf_rn(-n, tp.c2, a.lo);
   t = __fmaf_rn(-n, tp.c3, t);
   const ff u = ff_two_sum(h, t);
-  float sh, ch;
-  sincosf(u.hi, &sh, &ch);
-  c = __fmaf_rn(-u.lo, sh, ch);
-  s = __fmaf_rn(u.lo, ch, sh);
+  cis_reduced(u.hi, u.lo, c, s);
 }
 
 struct Kern32 {
@@ -97,41 +120,44 @@ __device__ __forceinline__ void load_point(const float* __restrict__ tab, int64_
   for (int t = 0; t < P32COUNT; ++t) q[t] = tab[t * n + p];
 }
 
-// grid: (ceil(N / rows), nk); block: 32 * rows; dynamic smem: rows * N * sizeof(cf)
+// grid: (ceil(N / rows), nk); block: 32 * rows * W (W warps share a row: the elements of one
+// colour share no node, so they can scatter into the row concurrently; colours are separated by
+// block barriers); dynamic smem: rows * N * sizeof(cf)
+constexpr int ASM_W = 2;
 __global__ void __launch_bounds__(512) k_asm32_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
-    const int32_t* __restrict__ elems, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
+    const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
     const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
-    const int32_t* __restrict__ perm, const double* __restrict__ kv, const cd* __restrict__ known,
-    cf* __restrict__ A, int64_t lda, double* __restrict__ rowsum /* [nk][N][12] */, int rows, TwoPi3 tp) {
+    const double* __restrict__ kv, const cd* __restrict__ known,
+    cf* __restrict__ A, int64_t lda, double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp) {
   extern __shared__ cf acc32[];
   __shared__ float shp[64 * 6];
+  __shared__ double part[16][ASM_W][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw = warp / ASM_W, sub = warp % ASM_W;
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
   const float kinv = (float)(1.0 / kv[kk]);
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
   for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * rows + warp;
-  if (i >= N) return;
-  cf* row = acc32 + (int64_t)warp * N;
+  const int64_t i = (int64_t)blockIdx.x * rows + rw;
+  const bool valid = i < N;
+  cf* row = acc32 + (int64_t)rw * N;
   const cd* kn = known + (int64_t)kk * N;
   ff xi[3], nui[3];
   for (int d = 0; d < 3; ++d) {
-    xi[d] = ff_from_double(nodes[3 * i + d]);
-    nui[d] = ff_from_double(normals[3 * i + d]);
+    xi[d] = ff_from_double(valid ? nodes[3 * i + d] : 0.0);
+    nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
   }
-  const int64_t EQ = E * Q;
   RowSums S;
   for (int col = 0; col < ncolors; ++col) {
-    for (int32_t t = color_off[col] + lane; t < color_off[col + 1]; t += 32) {
-      const int32_t e = perm[t];
+    for (int32_t t = color_off[col] + sub * 32 + lane; valid && t < color_off[col + 1]; t += 32 * ASM_W) {
       int32_t el[6];
       bool near = false;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        el[a] = elems[6 * (int64_t)e + a];
+        el[a] = esort[a * E + t];  // `elems` in colour order (k_points_to32_sorted)
         near |= (el[a] == i);
       }
       if (near) continue;
@@ -140,7 +166,8 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
       for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.f; }
       for (int qq = 0; qq < Q; ++qq) {
         float q[P32COUNT];
-        load_point(qtab, EQ, (int64_t)e * Q + qq, q);
+#pragma unroll
+        for (int f = 0; f < P32COUNT; ++f) q[f] = qtab[((int64_t)f * Q + qq) * E + t];
         Kern32 K;
         kernel32(k, kinv, xi, nui, tp, q, K);
         const float wj = q[P32W];
@@ -166,7 +193,7 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
         }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
   // reduce the compensated sums across the warp in FP64 (12 values per row)
   double v[12] = {(double)S.ar.s, (double)S.ar.c, (double)S.ai.s, (double)S.ai.c, (double)S.br.s, (double)S.br.c,
@@ -178,11 +205,19 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     out[t] = x;
   }
+  if (lane == 0)
+    for (int t = 0; t < 6; ++t) part[rw][sub][t] = out[t];
+  __syncthreads();
+  if (!valid) return;
   cf* Arow = A + ((int64_t)kk * N + i) * lda;
-  for (int64_t j = lane; j < N; j += 32) Arow[j] = row[j];
-  if (lane == 0) {
+  for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASM_W) Arow[j] = row[j];
+  if (sub == 0 && lane == 0) {
     double* rs = rowsum + ((int64_t)kk * N + i) * 6;
-    for (int t = 0; t < 6; ++t) rs[t] = out[t];
+    for (int t = 0; t < 6; ++t) {
+      double v = 0.0;
+      for (int w = 0; w < ASM_W; ++w) v += part[rw][w][t];
+      rs[t] = v;
+    }
   }
 }
 
@@ -285,12 +320,25 @@ static TwoPi3 two_pi3() {
   return r;
 }
 
+// Layout of c->qgeo32: standard points [P32COUNT][E*Q] (element-major, used by the field kernels),
+// near points [P32COUNT][E*6*QN], the colour-sorted standard points [P32COUNT][Q][E], then the
+// colour-sorted connectivity as int32 [6][E].
+static float* sorted_table(bie_ctx* c) {
+  const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
+  return c->qgeo32 + P32COUNT * (nq + nn);
+}
+static int32_t* sorted_elems(bie_ctx* c) {
+  return reinterpret_cast<int32_t*>(sorted_table(c) + P32COUNT * c->E * c->rule.Q);
+}
+
 int ensure_mixed_tables(bie_ctx* c) {
   if (c->qgeo32) return BIE_OK;
   const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
-  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, P32COUNT * (nq + nn) * sizeof(float)));
-  k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32);
-  k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq);
+  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (P32COUNT * (2 * nq + nn) + 6 * c->E) * sizeof(float)));
+  BIE_LAUNCH(k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32));
+  BIE_LAUNCH(k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq));
+  BIE_LAUNCH(k_points_to32_sorted<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(
+      c->qgeo, c->elem_perm, c->elems, c->E, c->rule.Q, sorted_table(c), sorted_elems(c)));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -301,8 +349,8 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
   const int64_t N = c->N;
   BIE_TRY(ensure_mixed_tables(c));
   dim3 gk((unsigned)((N + 255) / 256), nk);
-  k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known);
-  int rows = 16;
+  BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known));
+  int rows = 16 / ASM_W;
   while (rows > 1 && (size_t)rows * N * sizeof(cf) > 200 * 1024) rows /= 2;
   const size_t smem = (size_t)rows * N * sizeof(cf);
   if (smem > 200 * 1024)
@@ -311,15 +359,16 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
   const TwoPi3 tp = two_pi3();
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_asm32_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
-  k_asm32_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q,
-                                                   c->qgeo32, c->qshape32, c->color_off, c->ncolors, c->elem_perm,
-                                                   kv, known, A, lda, rowsum, rows, tp);
+  BIE_LAUNCH(k_asm32_bulk<<<gb, 32 * rows * ASM_W, smem, c->stream>>>(c->nodes, c->normals, c->bc, sorted_elems(c), N,
+                                                                      c->E, c->rule.Q, sorted_table(c), c->qshape32,
+                                                                      c->color_off, c->ncolors, kv, known, A, lda,
+                                                                      rowsum, rows, tp));
   BIE_CUDA_TRY(cudaGetLastError());
   const int64_t nq = c->E * c->rule.Q;
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);
-  k_asm32_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
+  BIE_LAUNCH(k_asm32_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
                                           c->qgeo32 + P32COUNT * nq, c->nshape, c->n2e_off, c->n2e, kv, known, A, lda,
-                                          rowsum, b, tp);
+                                          rowsum, b, tp));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

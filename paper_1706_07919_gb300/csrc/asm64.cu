@@ -233,7 +233,7 @@ int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch
   cd* known = (cd*)scratch;
   cd* rowsum = known + (int64_t)nk * N;
   dim3 gk((unsigned)((N + 255) / 256), nk);
-  k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known);
+  BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known));
   int rows = 16;
   while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
   size_t smem = (size_t)rows * N * sizeof(cd);
@@ -242,13 +242,13 @@ int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_asm64_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
-  k_asm64_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q, c->qgeo,
+  BIE_LAUNCH(k_asm64_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q, c->qgeo,
                                                    c->qshape, c->color_off, c->ncolors, c->elem_perm, kv, known, A,
-                                                   rowsum, rows);
+                                                   rowsum, rows));
   BIE_CUDA_TRY(cudaGetLastError());
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);
-  k_asm64_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
-                                          c->ngeo, c->nshape, c->n2e_off, c->n2e, kv, known, A, rowsum, b);
+  BIE_LAUNCH(k_asm64_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
+                                          c->ngeo, c->nshape, c->n2e_off, c->n2e, kv, known, A, rowsum, b));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

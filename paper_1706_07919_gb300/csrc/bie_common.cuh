@@ -28,6 +28,10 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::bie::cuda_fail(_e, #expr); \
   } while (0)
 
+// Every kernel launch of the library goes through BIE_LAUNCH, which counts it (bie_kernel_launches).
+void count_launch();
+#define BIE_LAUNCH(...) (::bie::count_launch(), __VA_ARGS__)
+
 #define BIE_TRY(expr)          \
   do {                         \
     int _rc = (expr);          \
@@ -99,6 +103,8 @@ struct bie_ctx {
   bool use_tcgen05 = false;          // tensor-core (tcgen05, TF32) trailing update in the LU
   int mixed_batch = 64;              // wavenumbers per batch
   int refine_it_max = 10;            // refinement corrections per system
+  int refine64_it_max = 30;          // corrections against the FP64 re-assembly of flagged systems
+  double refine64_tol = 1e-13;       // backward-error target against the FP64 re-assembly
   double refine_tol = 1e-11;         // backward-error target of the refinement
   double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
@@ -178,6 +184,34 @@ __host__ __device__ __forceinline__ ff ff_from_double(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 __host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// cos and sin of v = vh + vl, |v| <= pi (plus rounding), to about FP32 rounding: quadrant
+// reduction q = rint(v 2/pi) with pi/2 split in two floats (Cody-Waite), then the Taylor series
+// of sin (through v^9) and cos (through v^10) on |v'| <= pi/4, whose truncation errors are below
+// 2e-9 and 2e-10; the quadrant selects and negates.  Written from the series, not from a
+// library's polynomial.
+__device__ __forceinline__ void cis_reduced(float vh, float vl, float& c, float& s) {
+  const float kTwoOverPi = 0.636619772367581343f;
+  const float kPio2Hi = 1.57079637050628662f;        // fl32(pi/2)
+  const float kPio2Lo = -4.37113900018624284e-8f;    // pi/2 - fl32(pi/2)
+  const float q = rintf(vh * kTwoOverPi);
+  float v = __fmaf_rn(-q, kPio2Hi, vh);
+  v = __fmaf_rn(-q, kPio2Lo, v) + vl;
+  const float v2 = v * v;
+  float ps = __fmaf_rn(v2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);  // 1/9!, -1/7!
+  ps = __fmaf_rn(v2, ps, 8.33333333333333333e-3f);                              // 1/5!
+  ps = __fmaf_rn(v2, ps, -1.66666666666666667e-1f);                             // -1/3!
+  const float sv = __fmaf_rn(v * v2, ps, v);
+  float pc = __fmaf_rn(v2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+  pc = __fmaf_rn(v2, pc, -1.38888888888888889e-3f);                             // -1/6!
+  pc = __fmaf_rn(v2, pc, 4.16666666666666667e-2f);                              // 1/4!
+  pc = __fmaf_rn(v2, pc, -0.5f);
+  const float cv = __fmaf_rn(v2, pc, 1.0f);
+  const int qi = ((int)q) & 3;
+  const float a = (qi & 1) ? sv : cv, b = (qi & 1) ? cv : sv;
+  c = (qi == 1 || qi == 2) ? -a : a;
+  s = (qi >= 2) ? -b : b;
+}
 
 // Compensated (Kahan-Babuska/Neumaier) running sum in FP32.
 struct ksum {

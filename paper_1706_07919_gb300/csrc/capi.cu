@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI of include/bie.h: argument checks, device buffers, and the order in which
 // the kernels of the other translation units run.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -9,6 +10,9 @@
 namespace bie {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
@@ -123,7 +127,7 @@ int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report
     BIE_TRY(lu_factor64(c, A, nk, (int)N, (int)N, N * N, piv, info));
     BIE_TRY(lu_solve64(c, A, nk, (int)N, (int)N, N * N, piv, b, N));
     dim3 g((unsigned)((N + 255) / 256), nk);
-    k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, b, scratch, surf_out + k0 * 2 * N);
+    BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, b, scratch, surf_out + k0 * 2 * N));
     BIE_CUDA_TRY(cudaGetLastError());
     if (rep) {
       BIE_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -146,6 +150,8 @@ extern "C" {
 const char* bie_last_error(void) { return g_last_error.c_str(); }
 
 const char* bie_version(void) { return "bie-gb300 0.1 (sm_103a)"; }
+
+uint64_t bie_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int bie_create(bie_ctx** out, int cuda_device, void* cuda_stream) {
   if (!out) return fail(BIE_ERR_INVALID_ARG, "NULL out");

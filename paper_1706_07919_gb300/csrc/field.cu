@@ -125,10 +125,10 @@ int field64(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* 
   cd* Pq = (cd*)scratch;
   cd* Pnq = Pq + (int64_t)nk * EQ;
   dim3 gi((unsigned)((EQ + 255) / 256), nk);
-  k_interp_q64<<<gi, 256, 0, c->stream>>>(c->elems, c->N, c->E, c->rule.Q, c->qshape, surf, Pq, Pnq);
+  BIE_LAUNCH(k_interp_q64<<<gi, 256, 0, c->stream>>>(c->elems, c->N, c->E, c->rule.Q, c->qshape, surf, Pq, Pnq));
   if (M > 0) {
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
-    k_field64<<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, T);
+    BIE_LAUNCH(k_field64<<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, T));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -289,6 +289,130 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
   }
 }
 
+// k-batched variant of the float-float kernel: each (point, quadrature point) pair's geometry --
+// the float-float distances to x_p and x0, nu0.(x - x0), r.nu -- is formed once and reused for FKB
+// wavenumbers; per wavenumber only the three phases (float-float product and 2 pi reduction,
+// then cis_reduced) and the FP32 integrand remain.
+constexpr int FKB = 8;
+
+__device__ __forceinline__ void cis_ffk(ff a, const TwoPi3f& tp, float& c, float& s) {
+  const float n = rintf(a.hi * tp.inv);
+  const float h = __fmaf_rn(-n, tp.c1, a.hi);
+  float t = __fmaf_rn(-n, tp.c2, a.lo);
+  t = __fmaf_rn(-n, tp.c3, t);
+  const ff u = ff_two_sum(h, t);
+  cis_reduced(u.hi, u.lo, c, s);
+}
+
+__global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
+                                                 const float* __restrict__ qtab, const cf* __restrict__ Pq,
+                                                 const cf* __restrict__ Pnq, const cd* __restrict__ surf,
+                                                 const double* __restrict__ xp, int64_t M,
+                                                 const int32_t* __restrict__ foot_elem,
+                                                 const double* __restrict__ foot, const double* __restrict__ kv,
+                                                 int nk, cd* __restrict__ T, TwoPi3f tp) {
+  __shared__ float sg[13][FT];        // quadrature geometry tile
+  __shared__ float sq[FKB][4][FT];    // Pq, Pnq (re, im) of the tile for each wavenumber
+  __shared__ float s0[FKB][4][FT];    // P0, P0' (re, im) of each thread's point for each wavenumber
+  __shared__ float sk[FKB][3];        // k (hi, lo), 1/k
+  const int kbase = blockIdx.y * FKB;
+  const int nkb = min(FKB, nk - kbase);
+  const int tid = threadIdx.x;
+  const int64_t m = (int64_t)blockIdx.x * FT + tid;
+  const bool active = m < M;
+  if (tid < nkb) {
+    const ff k = ff_from_double(kv[kbase + tid]);
+    sk[tid][0] = k.hi;
+    sk[tid][1] = k.lo;
+    sk[tid][2] = (float)(1.0 / kv[kbase + tid]);
+  }
+  ff p[3] = {{0, 0}, {0, 0}, {0, 0}}, x0[3] = {{0, 0}, {0, 0}, {0, 0}}, nu0[3] = {{0, 0}, {0, 0}, {1, 0}};
+  if (active) {
+    for (int d = 0; d < 3; ++d) {
+      p[d] = ff_from_double(xp[3 * m + d]);
+      x0[d] = ff_from_double(foot[8 * m + d]);
+      nu0[d] = ff_from_double(foot[8 * m + 3 + d]);
+    }
+    const double fxi = foot[8 * m + 6], feta = foot[8 * m + 7];
+    const double L1 = 1.0 - fxi - feta;
+    const double Nv[6] = {L1 * (2 * L1 - 1), fxi * (2 * fxi - 1), feta * (2 * feta - 1), 4 * L1 * fxi, 4 * fxi * feta,
+                          4 * feta * L1};
+    const int32_t* el = elems + 6 * (int64_t)foot_elem[m];
+    for (int j = 0; j < nkb; ++j) {
+      const cd* P = surf + (int64_t)(kbase + j) * 2 * N;
+      double a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+      for (int a = 0; a < 6; ++a) {
+        const cd v = P[el[a]], w = P[N + el[a]];
+        a0 += Nv[a] * v.re; a1 += Nv[a] * v.im;
+        b0 += Nv[a] * w.re; b1 += Nv[a] * w.im;
+      }
+      s0[j][0][tid] = (float)a0; s0[j][1][tid] = (float)a1;
+      s0[j][2][tid] = (float)b0; s0[j][3][tid] = (float)b1;
+    }
+  }
+  ksum accr[FKB], acci[FKB];
+  for (int64_t t0 = 0; t0 < EQ; t0 += FT) {
+    const int64_t t = t0 + tid;
+    __syncthreads();
+    if (t < EQ) {
+#pragma unroll
+      for (int u = 0; u < 13; ++u) sg[u][tid] = qtab[u * EQ + t];
+      for (int j = 0; j < nkb; ++j) {
+        const cf a = Pq[(int64_t)(kbase + j) * EQ + t], b = Pnq[(int64_t)(kbase + j) * EQ + t];
+        sq[j][0][tid] = a.re; sq[j][1][tid] = a.im;
+        sq[j][2][tid] = b.re; sq[j][3][tid] = b.im;
+      }
+    }
+    __syncthreads();
+    const int cnt = (EQ - t0) < FT ? (int)(EQ - t0) : FT;
+    if (!active) continue;
+    for (int u = 0; u < cnt; ++u) {
+      const ff qx = {sg[0][u], sg[3][u]}, qy = {sg[1][u], sg[4][u]}, qz = {sg[2][u], sg[5][u]};
+      const float nx = sg[6][u], ny = sg[7][u], nz = sg[8][u], wj = sg[9][u];
+      const ff nux = {nx, sg[10][u]}, nuy = {ny, sg[11][u]}, nuz = {nz, sg[12][u]};
+      const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
+      const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
+      const ff Rp = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
+      const ff R0 = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
+      const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
+      const float iRp = 1.0f / Rp.hi, iR0 = 1.0f / R0.hi;
+      const float rnp = ff_add(ff_add(ff_mul(rpx, nux), ff_mul(rpy, nuy)), ff_mul(rpz, nuz)).hi * iRp * iRp * iRp;
+      const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0 * iR0;
+      const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
+#pragma unroll
+      for (int j = 0; j < FKB; ++j) {
+        if (j < nkb) {
+          const ff k = {sk[j][0], sk[j][1]};
+          const float kinv = sk[j][2];
+          float cp, spp, c0, s0v, cg, sgv;
+          cis_ffk(ff_mul(k, Rp), tp, cp, spp);
+          cis_ffk(ff_mul(k, R0), tp, c0, s0v);
+          cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+          const float kRp = k.hi * Rp.hi, kR0 = k.hi * R0.hi;
+          const float Gpr = cp * iRp, Gpi = spp * iRp, G0r = c0 * iR0, G0i = s0v * iR0;
+          const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
+          const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
+          const float g = cg, f = sgv * kinv, dg = -k.hi * sgv * nn, df = cg * nn;
+          const float P0r = s0[j][0][tid], P0i = s0[j][1][tid], Q0r = s0[j][2][tid], Q0i = s0[j][3][tid];
+          const float Ptr = sq[j][0][u] - P0r * g - Q0r * f, Pti = sq[j][1][u] - P0i * g - Q0i * f;
+          const float dPr = sq[j][2][u] - P0r * dg - Q0r * df, dPi = sq[j][3][u] - P0i * dg - Q0i * df;
+          const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
+          const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
+          const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);
+          accr[j].add(wj * tr);
+          acci[j].add(wj * ti);
+        }
+      }
+    }
+  }
+  if (active) {
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    for (int j = 0; j < nkb; ++j)
+      T[(int64_t)(kbase + j) * M + m] = {(double)s0[j][0][tid] + accr[j].value() * inv4pi,
+                                         (double)s0[j][1][tid] + acci[j].value() * inv4pi};
+  }
+}
+
 int ensure_mixed_tables(bie_ctx* c);
 
 int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
@@ -299,7 +423,7 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
   cf* Pq = (cf*)scratch;
   cf* Pnq = Pq + (int64_t)nk * EQ;
   dim3 gi((unsigned)((EQ + 255) / 256), nk);
-  k_interp_q32<<<gi, 256, 0, c->stream>>>(c->elems, c->N, c->E, c->rule.Q, c->qshape, surf, Pq, Pnq);
+  BIE_LAUNCH(k_interp_q32<<<gi, 256, 0, c->stream>>>(c->elems, c->N, c->E, c->rule.Q, c->qshape, surf, Pq, Pnq));
   TwoPi3f tp;
   const double two_pi = 2.0 * kPi;
   tp.c1 = (float)two_pi;
@@ -308,12 +432,14 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
   tp.inv = (float)(1.0 / two_pi);
   if (M > 0) {
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
-    if (c->field_accurate_phase)
-      k_field32<true><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot,
-                                                kv, T, tp);
+    if (c->field_accurate_phase) {
+      dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
+      BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot, kv,
+                                           nk, T, tp));
+    }
     else
-      k_field32<false><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
-                                                 foot, kv, T, tp);
+      BIE_LAUNCH(k_field32<false><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
+                                                 foot, kv, T, tp));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -187,10 +187,10 @@ int upload_geometry_tables(bie_ctx* c) {
   int64_t totq = E * r.Q, totn = E * 6 * r.QN;
   BIE_CUDA_TRY(cudaMalloc(&c->qgeo, GCOUNT * totq * sizeof(double)));
   BIE_CUDA_TRY(cudaMalloc(&c->ngeo, GCOUNT * totn * sizeof(double)));
-  k_geom_points<<<(unsigned)((totq + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, r.Q, r.Q, sxi, seta,
-                                                                        sw, 0, d_cnt, c->qgeo, totq);
-  k_geom_points<<<(unsigned)((totn + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, 0, r.QN, nxi, neta,
-                                                                        nw, 1, d_cnt, c->ngeo, totn);
+  BIE_LAUNCH(k_geom_points<<<(unsigned)((totq + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, r.Q, r.Q, sxi, seta,
+                                                                        sw, 0, d_cnt, c->qgeo, totq));
+  BIE_LAUNCH(k_geom_points<<<(unsigned)((totn + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, 0, r.QN, nxi, neta,
+                                                                        nw, 1, d_cnt, c->ngeo, totn));
   BIE_CUDA_TRY(cudaGetLastError());
 
   // shape-value tables
@@ -416,8 +416,8 @@ __global__ void k_foot_points(const double* __restrict__ nodes, int64_t N, const
 
 int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot) {
   if (M == 0) return BIE_OK;
-  k_foot_points<<<(unsigned)((M + 127) / 128), 128, 0, c->stream>>>(c->nodes, c->N, c->elems, c->n2e_off, c->n2e, xp,
-                                                                     M, foot_elem, foot);
+  BIE_LAUNCH(k_foot_points<<<(unsigned)((M + 127) / 128), 128, 0, c->stream>>>(c->nodes, c->N, c->elems, c->n2e_off, c->n2e, xp,
+                                                                     M, foot_elem, foot));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

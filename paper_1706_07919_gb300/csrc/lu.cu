@@ -239,18 +239,18 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
                         int32_t* piv, int32_t* info) {
   const int lw = leaf_width<S>(n, p0);
   if (lw == 0 || w > 64) {
-    k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info);
+    BIE_LAUNCH(k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info));
     return BIE_OK;
   }
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_leaf<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   for (int c0 = p0; c0 < p0 + w; c0 += lw) {
     const int l = std::min(lw, p0 + w - c0);
     const size_t smem = (size_t)(n - c0) * l * sizeof(Cx<S>);
-    k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info);
+    BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info));
     const int rows = n - c0 - l;
     if (rows > 0 && c0 + l < p0 + w) {
       dim3 g((unsigned)((rows + 255) / 256), batch);
-      k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l);
+      BIE_LAUNCH(k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l));
     }
   }
   return BIE_OK;
@@ -403,11 +403,11 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
     const int w = std::min(nb, n - p0);
     BIE_TRY(panel_factor<S>(c, A, batch, n, ld, bstride, p0, w, piv, info));
     dim3 gs((unsigned)((n + 127) / 128), batch);
-    k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv);
+    BIE_LAUNCH(k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv));
     const int rem = n - p0 - w;
     if (rem > 0) {
       dim3 gg((unsigned)((rem + 63) / 64), (unsigned)((rem + 63) / 64), batch);
-      k_gemm_update<S><<<gg, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w);
+      BIE_LAUNCH(k_gemm_update<S><<<gg, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w));
     }
   }
   BIE_CUDA_TRY(cudaGetLastError());
@@ -421,7 +421,7 @@ int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstrid
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
   dim3 gs((unsigned)((n + 127) / 128), batch);
-  k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv);
+  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -431,8 +431,8 @@ int lu_factor64(bie_ctx* c, cd* A, int batch, int n, int ld, int64_t bstride, in
 }
 int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cd* b,
                int64_t bstride_b) {
-  k_lu_solve<double, double><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<double>*>(LU), bstride, n, ld,
-                                                           piv, reinterpret_cast<Cx<double>*>(b), bstride_b);
+  BIE_LAUNCH(k_lu_solve<double, double><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<double>*>(LU), bstride, n, ld,
+                                                           piv, reinterpret_cast<Cx<double>*>(b), bstride_b));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -441,8 +441,8 @@ int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, in
 }
 int lu_solve32(bie_ctx* c, const cf* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cf* b,
                int64_t bstride_b) {
-  k_lu_solve<float, float><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<float>*>(LU), bstride, n, ld, piv,
-                                                         reinterpret_cast<Cx<float>*>(b), bstride_b);
+  BIE_LAUNCH(k_lu_solve<float, float><<<batch, 256, 0, c->stream>>>(reinterpret_cast<const Cx<float>*>(LU), bstride, n, ld, piv,
+                                                         reinterpret_cast<Cx<float>*>(b), bstride_b));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

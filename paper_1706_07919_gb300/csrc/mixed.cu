@@ -1,8 +1,10 @@
 // mixed.cu -- the mixed-precision frequency solves (BIE_MODE_MIXED):
 //   FP32 assembly with float-float phases (asm32.cu) -> FP32 copy factored by the blocked LU
-//   (trailing update on the tensor cores, lu_tc.cu, or SIMT FP32 where tcgen05 is not used) ->
-//   iterative refinement against the assembled matrix with float-float residuals (refine.cu).
-// Frequencies whose refinement does not converge are re-solved by the FP64 path and flagged.
+//   (trailing update on the tcgen05 tensor cores, lu_tc.cu, or SIMT FP32) -> iterative refinement
+//   against the assembled matrix with float-float residuals (refine.cu).
+// Wavenumbers whose estimated sensitivity to the FP32 assembly is too high (next to an interior
+// resonance) or whose refinement stalled are re-assembled in FP64 and refined against that system
+// with the same low-precision factor; only if that also stalls does the full FP64 path run.
 #include <algorithm>
 
 #include "bie_common.cuh"
@@ -10,6 +12,7 @@
 namespace bie {
 
 int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum);
+int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch);
 int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
                  void* scratch, size_t scratch_bytes);
@@ -17,6 +20,9 @@ size_t lu_tc_scratch_bytes(int batch, int n);
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
                  int it_max, double tol);
+int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
+                       const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
+                       double* rowabs, void* state_dev, int it_max, double tol);
 size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est);
@@ -26,6 +32,8 @@ __global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, cons
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr int kFallbackGroup = 8;  // FP64 systems re-assembled at once
+
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep) {
   const int64_t N = c->N;
   const int64_t ld = (N + 63) / 64 * 64;
@@ -33,13 +41,17 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   const size_t vec = align256((size_t)N * sizeof(cd));
   const size_t perk = 2 * mat + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
                       2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
+  // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel
+  const size_t fb = (size_t)kFallbackGroup *
+                        (align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024) + 4096;
   size_t free_b = 0, total_b = 0;
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(c->mixed_batch, (int64_t)((free_b / 2) / perk))));
+  const size_t avail = free_b > fb ? free_b - fb : 0;
+  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(c->mixed_batch, (int64_t)((avail / 2) / perk))));
   size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N);
-  if ((size_t)kb * perk + tc_scratch > free_b)
+  if ((size_t)kb * perk + tc_scratch + fb > free_b)
     return fail(BIE_ERR_OOM, "mixed-precision workspace for N = " + std::to_string(N) + " does not fit");
-  BIE_TRY(ensure_buf(c->work, kb * perk + tc_scratch + 8192));
+  BIE_TRY(ensure_buf(c->work, kb * perk + tc_scratch + fb + 16384));
   char* p = (char*)c->work.p;
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);
@@ -56,11 +68,23 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   int32_t* info = (int32_t*)take((size_t)kb * 4);
   double* kdev = (double*)take((size_t)kb * 8);
   void* tcs = take(tc_scratch);
+  const int G = kFallbackGroup;
+  cd* A64 = (cd*)take((size_t)G * N * N * sizeof(cd));
+  cd* b64 = (cd*)take((size_t)G * vec);
+  cd* s64 = (cd*)take((size_t)G * 4 * vec);  // known + rowsum of the FP64 assembly
+  cd* xg = (cd*)take((size_t)G * vec);
+  cd* rg = (cd*)take((size_t)G * vec);
+  double* rowabs_g = (double*)take((size_t)G * N * sizeof(double));
+  void* state_g = take(refine_state_bytes(G));
+  double* kg = (double*)take(G * sizeof(double));
+  int32_t* sel_g = (int32_t*)take(G * sizeof(int32_t));
   const int64_t bstride = (int64_t)(mat / sizeof(cf));
   std::vector<int32_t> done(kb), iters(kb), hinfo(kb);
   std::vector<double> berr(kb), est(kb);
-  std::vector<double> fallback;
-  std::vector<int64_t> fallback_idx;
+  std::vector<int32_t> gd(G), gi(G);
+  std::vector<double> gb(G), ge(G);
+  std::vector<double> full64;
+  std::vector<int64_t> full64_idx;
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -73,35 +97,63 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
                          c->refine_tol));
-    dim3 g((unsigned)((N + 255) / 256), nk);
-    k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, surf_out + k0 * 2 * N);
-    BIE_CUDA_TRY(cudaGetLastError());
     BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
     BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> flagged;
     for (int i = 0; i < nk; ++i) {
-      const bool conv = done[i] && !hinfo[i] && std::isfinite(berr[i]);
+      const bool conv = done[i] && std::isfinite(berr[i]);
       const bool sensitive = !(est[i] <= c->fallback_err_est);
-      const bool ok = conv && !sensitive;
       if (rep)
         rep[k0 + i] = bie_report{iters[i], BIE_MODE_MIXED,
                                  (conv ? 0u : BIE_FLAG_NOT_CONVERGED) | (hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u) |
                                      (sensitive ? BIE_FLAG_ILL_CONDITIONED : 0u),
                                  0, berr[i], est[i]};
-      if (!ok) {
-        fallback.push_back(k[k0 + i]);
-        fallback_idx.push_back(k0 + i);
+      if (hinfo[i]) {  // singular low-precision factor: nothing to refine with
+        full64.push_back(k[k0 + i]);
+        full64_idx.push_back(k0 + i);
+      } else if (!conv || sensitive) {
+        flagged.push_back(i);
       }
     }
+    // FP64 re-assembly and refinement with the existing factor, in groups
+    for (size_t f0 = 0; f0 < flagged.size(); f0 += G) {
+      const int ng = (int)std::min<size_t>(G, flagged.size() - f0);
+      std::vector<double> kv(ng);
+      for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
+      BIE_CUDA_TRY(cudaMemcpyAsync(kg, kv.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+      BIE_TRY(assemble64(c, kg, ng, A64, b64, s64));
+      BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
+                                 c->refine64_it_max, c->refine64_tol));
+      BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
+      for (int g = 0; g < ng; ++g) {
+        const int64_t idx = k0 + flagged[f0 + g];
+        if (rep) {
+          rep[idx].flags |= BIE_FLAG_FP64_ASSEMBLY;
+          rep[idx].iters += gi[g];
+          rep[idx].backward_err = gb[g];
+          if (gd[g]) rep[idx].flags &= ~BIE_FLAG_NOT_CONVERGED;
+        }
+        if (!gd[g] || !std::isfinite(gb[g])) {
+          full64.push_back(k[idx]);
+          full64_idx.push_back(idx);
+        }
+      }
+    }
+    dim3 g((unsigned)((N + 255) / 256), nk);
+    BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, surf_out + k0 * 2 * N));
+    BIE_CUDA_TRY(cudaGetLastError());
   }
-  // frequencies the mixed path could not settle (near an interior resonance, zero pivot): FP64
-  for (size_t f = 0; f < fallback.size(); ++f) {
+  // last resort: the full FP64 path
+  for (size_t f = 0; f < full64.size(); ++f) {
     bie_report r64;
-    BIE_TRY(solve_fp64(c, &fallback[f], 1, surf_out + fallback_idx[f] * 2 * N, &r64));
+    BIE_TRY(solve_fp64(c, &full64[f], 1, surf_out + full64_idx[f] * 2 * N, &r64));
     if (rep) {
-      rep[fallback_idx[f]].flags |= BIE_FLAG_FALLBACK_FP64;
-      rep[fallback_idx[f]].path = BIE_MODE_FP64;
+      rep[full64_idx[f]].flags |= BIE_FLAG_FALLBACK_FP64;
+      rep[full64_idx[f]].path = BIE_MODE_FP64;
     }
   }
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }
 

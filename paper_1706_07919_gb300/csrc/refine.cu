@@ -108,15 +108,18 @@ __device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y) {
 }
 
 // rhs: cd [batch][n] (FP64), solution written to out (cd, added to `out` if accumulate).
+// sel (optional): system blockIdx.x uses factor sel[blockIdx.x] (vectors stay indexed by blockIdx.x).
 __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
                                                   const int32_t* __restrict__ perm, const cd* __restrict__ rhs,
                                                   cd* __restrict__ out, int accumulate,
-                                                  const RefineState* __restrict__ st) {
+                                                  const RefineState* __restrict__ st,
+                                                  const int32_t* __restrict__ sel = nullptr) {
   extern __shared__ cf yv[];
   const int kk = blockIdx.x;
   if (st && st[kk].done) return;
-  const cf* M = LU + (int64_t)kk * bstride;
-  const int32_t* pm = perm + (int64_t)kk * n;
+  const int fk = sel ? sel[kk] : kk;
+  const cf* M = LU + (int64_t)fk * bstride;
+  const int32_t* pm = perm + (int64_t)fk * n;
   const cd* r = rhs + (int64_t)kk * n;
   // scale the right-hand side to O(1) before rounding it to FP32
   __shared__ double s_scale;
@@ -290,30 +293,94 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
                  int it_max, double tol) {
   RefineState* st = (RefineState*)state_dev;
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
-  k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm);
+  BIE_LAUNCH(k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm));
   const size_t sm_trsv = (size_t)n * sizeof(cf);
   const size_t sm_res = (size_t)n * sizeof(float4);
   if (sm_trsv > 200 * 1024 || sm_res > 200 * 1024)
     return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_trsv_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsv));
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_res));
-  k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr);
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int it = 0; it <= it_max; ++it) {
-    k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st);
-    k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max);
+    BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st));
+    BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st);
+    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st));
   }
   // assembly-sensitivity estimate (r is free now)
-  k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f);
-  k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr);
-  k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st);
+  BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f));
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr));
+  BIE_LAUNCH(k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
 
 size_t refine_state_bytes(int nk) { return (size_t)nk * sizeof(RefineState); }
+
+// ---- refinement against the FP64-assembled system (wavenumbers flagged by the estimate) ------
+// r = b64 - A64 x in FP64; corrections still come from the low-precision factor of the FP32
+// system, which remains a good preconditioner while cond(A) * (its error) < 1.
+__global__ void __launch_bounds__(512) k_residual64(const cd* __restrict__ A, int n, const cd* __restrict__ b,
+                                                    const cd* __restrict__ x, cd* __restrict__ r,
+                                                    double* __restrict__ rowabs, const RefineState* __restrict__ st) {
+  const int g = blockIdx.y;
+  if (st[g].done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 16 + warp;
+  if (i >= n) return;
+  const cd* row = A + ((int64_t)g * n + i) * n;
+  const cd* xg = x + (int64_t)g * n;
+  double sr = 0, si = 0, sa = 0;
+  for (int j = lane; j < n; j += 32) {
+    const cd a = row[j], v = xg[j];
+    sr = fma(a.re, v.re, fma(-a.im, v.im, sr));
+    si = fma(a.re, v.im, fma(a.im, v.re, si));
+    sa += fabs(a.re) + fabs(a.im);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0) {
+    const cd bi = b[(int64_t)g * n + i];
+    r[(int64_t)g * n + i] = {bi.re - sr, bi.im - si};
+    rowabs[(int64_t)g * n + i] = sa;
+  }
+}
+
+__global__ void k_gather_scatter(cd* __restrict__ xb, cd* __restrict__ xg, const int32_t* __restrict__ sel, int n,
+                                 int to_group) {
+  const int g = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cd* src = to_group ? xb + (int64_t)sel[g] * n : xg + (int64_t)g * n;
+  cd* dst = to_group ? xg + (int64_t)g * n : xb + (int64_t)sel[g] * n;
+  dst[i] = src[i];
+}
+
+// Refines x[sel[g]] (g < ng) against A64/b64 [ng] with factors LU[sel[g]].  Scratch: xg, r [ng][n],
+// rowabs [ng][n], state [ng].
+int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
+                       const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
+                       double* rowabs, void* state_dev, int it_max, double tol) {
+  RefineState* st = (RefineState*)state_dev;
+  BIE_CUDA_TRY(cudaMemsetAsync(st, 0, ng * sizeof(RefineState), c->stream));
+  dim3 gv((unsigned)((n + 255) / 256), ng);
+  BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 1));
+  const size_t sm_trsv = (size_t)n * sizeof(cf);
+  dim3 gr((unsigned)((n + 15) / 16), ng);
+  for (int it = 0; it <= it_max; ++it) {
+    BIE_LAUNCH(k_residual64<<<gr, 512, 0, c->stream>>>(A64, n, b64, xg, r, rowabs, st));
+    BIE_LAUNCH(k_refine_check<<<ng, 256, 0, c->stream>>>(n, b64, xg, r, rowabs, st, tol, it < it_max));
+    if (it == it_max) break;
+    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev));
+  }
+  BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 0));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
 
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est) {

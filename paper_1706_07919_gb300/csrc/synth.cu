@@ -89,7 +89,7 @@ __global__ void k_synth(const cd* __restrict__ T, const int64_t* __restrict__ mi
 static int twiddle_table(bie_ctx* c, int n, double2** tw) {
   BIE_TRY(ensure_buf(c->work2, (size_t)(n / 2 + 1) * sizeof(double2)));
   *tw = (double2*)c->work2.p;
-  k_twiddles<<<(n / 2 + 255) / 256, 256, 0, c->stream>>>(n, *tw);
+  BIE_LAUNCH(k_twiddles<<<(n / 2 + 255) / 256, 256, 0, c->stream>>>(n, *tw));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -99,7 +99,7 @@ int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout) {
   BIE_TRY(twiddle_table(c, n, &tw));
   size_t smem = 2 * (size_t)n * sizeof(C2<double>);
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_pulse_spectrum<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_pulse_spectrum<double><<<(unsigned)P, std::min(512, n / 2), smem, c->stream>>>(s, n, tw, Sout);
+  BIE_LAUNCH(k_pulse_spectrum<double><<<(unsigned)P, std::min(512, n / 2), smem, c->stream>>>(s, n, tw, Sout));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -113,11 +113,11 @@ int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t
   if (out_dtype == 0) {
     size_t smem = 2 * (size_t)n * sizeof(C2<double>);
     BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_synth<double, double><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (double*)out);
+    BIE_LAUNCH(k_synth<double, double><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (double*)out));
   } else {
     size_t smem = 2 * (size_t)n * sizeof(C2<float>);
     BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_synth<float, float><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (float*)out);
+    BIE_LAUNCH(k_synth<float, float><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (float*)out));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -178,17 +178,17 @@ extern "C" int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_
   double2* tw = (double2*)base;  // n/2 entries, rewritten by every call
   int64_t* md = (int64_t*)((char*)base + kNoAllocScratchBytes / 2);
   if (Nk > 0) BIE_CUDA_TRY(cudaMemcpyAsync(md, midx, Nk * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  k_twiddles<<<(n / 2 + 255) / 256, 256, 0, st>>>(n, tw);
+  BIE_LAUNCH(k_twiddles<<<(n / 2 + 255) / 256, 256, 0, st>>>(n, tw));
   dim3 g((unsigned)M, (unsigned)P);
   const int threads = std::min(512, std::max(32, n / 2));
   if (out_dtype == 0) {
     const size_t smem = 2 * (size_t)n * sizeof(C2<double>);
     BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_synth<double, double><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (double*)out);
+    BIE_LAUNCH(k_synth<double, double><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (double*)out));
   } else {
     const size_t smem = 2 * (size_t)n * sizeof(C2<float>);
     BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_synth<float, float><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (float*)out);
+    BIE_LAUNCH(k_synth<float, float><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (float*)out));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   // the host index array must outlive its asynchronous copy

@@ -56,13 +56,13 @@ def test_mixed_sphere_all_wavenumbers(Solver, B, tc):
     for i, k in enumerate(w.k):
         P, Pn = oracle.solve_frequency(w.mesh, k, D)
         errs.append(rel(surf[i, 0], P))
-        assert rep[i].backward_err <= 1e-10 or rep[i].flags & B.BIE_FLAG_FALLBACK_FP64
+        assert rep[i].backward_err <= 1e-10 or rep[i].flags & B.BIE_FLAG_FALLBACK_FP64, (k, rep[i].backward_err)
     assert max(errs) <= TOL, (max(errs), int(np.argmax(errs)))
     # only the wavenumbers next to interior resonances (j_n zeros near 3.14, 4.49, 5.76, 6.99, 7.73)
     # may leave the mixed path, and never because the refinement failed
-    fell = [i for i in range(len(w.k)) if rep[i].flags & B.BIE_FLAG_FALLBACK_FP64]
+    fell = [i for i in range(len(w.k)) if rep[i].flags & B.BIE_FLAG_FP64_ASSEMBLY]
     assert len(fell) <= 6, [(w.k[i], rep[i].err_est) for i in fell]
-    assert all(not (rep[i].flags & B.BIE_FLAG_NOT_CONVERGED) for i in range(len(w.k)))
+    assert all(not (rep[i].flags & (B.BIE_FLAG_NOT_CONVERGED | B.BIE_FLAG_FALLBACK_FP64)) for i in range(len(w.k)))
 
 
 @pytest.mark.parametrize("tc", [0, 1])
@@ -121,3 +121,19 @@ def test_mixed_field_matches_oracle(Solver, B, two_spheres, accurate, bound):
     for i, k in enumerate(ks):
         Tr = oracle.field(two_spheres, k, surf[i, 0], surf[i, 1], xs)
         assert rel(T[i], Tr) <= bound, (k, rel(T[i], Tr))
+
+
+def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B):
+    """Forcing every wavenumber through the FP64 re-assembly (threshold below any estimate):
+    refinement with the TF32 factor against the FP64 system must reach the FP64 path's answer to
+    the refinement's FP64 stop (backward error 1e-13) times the condition number."""
+    w = config_sphere_fp64()
+    ks = w.k[[3, 30, 35, 60]]
+    s = _solver(Solver, w.mesh, tc=1)
+    s.set_option("mixed.fallback_err_est", 1e-15)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        assert rep[i].flags & B.BIE_FLAG_FP64_ASSEMBLY and not rep[i].flags & B.BIE_FLAG_FALLBACK_FP64
+        P, Pn = oracle.solve_frequency(w.mesh, k, D)
+        assert rel(surf[i, 0], P) <= 1e-8, (k, rel(surf[i, 0], P))
