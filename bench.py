@@ -119,7 +119,7 @@ def run_ours(args):
     sol = Solver(local, stream)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_incident_plane_wave(w.direction)
-    sol.set_option("mixed.tcgen05", 1)
+    sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.batch", args.batch)
     midx = np.arange(1, Nk + 1, dtype=np.int64)
 
@@ -357,7 +357,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--tc", type=int, default=2, help="LU trailing update: 2 TMA-fed tcgen05, 1 register-staged tcgen05, 0 SIMT")
     ap.add_argument("--check", type=int, default=4)
     ap.add_argument("--cpu-points", dest="cpu_points", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

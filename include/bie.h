@@ -118,8 +118,9 @@ int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t
 int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
 
 /* Tuning options of the mixed-precision path (names are case-sensitive):
- *   "mixed.tcgen05"        1: trailing LU update on the tcgen05 tensor cores (TF32 operands,
- *                          FP32 accumulation in TMEM); 0: FP32 SIMT update.  Default 1 where built.
+ *   "mixed.tcgen05"        trailing LU update: 2 (default) persistent TMA-fed tcgen05 kernel
+ *                          (TF32 operands, FP32 accumulation in TMEM), 1 the register-staged
+ *                          tcgen05 kernel, 0 FP32 on the CUDA cores.
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)

@@ -14,6 +14,9 @@
 // warps then read their 32 TMEM lanes each (tcgen05.ld 32x32b) and update A22 in place.
 // Shared memory 96 KB and TMEM 256 columns per CTA: two CTAs per SM, so one CTA's staging and
 // epilogue overlap the other's MMAs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "bie_common.cuh"
 
 namespace bie {
@@ -220,20 +223,328 @@ __global__ void __launch_bounds__(128, 2) k_update_tc(float* __restrict__ A, int
 
 }  // namespace tc
 
-size_t lu_tc_scratch_bytes(int batch, int n) { return 256; }
+size_t lu_tc_scratch_bytes(int batch, int n) {
+  return 256 + (size_t)batch * 2 * n * (2 * tc::NB) * sizeof(float);  // error flag + B^T of the real embedding
+}
+
+// ==============================================================================================
+// Version 2: persistent, warp-specialised, TMA-fed update with the complex product written as a
+// real GEMM on the interleaved storage (real embedding):
+//   C_int (m x 2n reals) -= L_int (m x 2K reals) * B,  B = [[ur, ui], [-ui, ur]] per complex u,
+// so L21 is consumed exactly as stored (re, im, re, im, ...) and B^T (2n x 2K, K-major) is built
+// once per panel by k_build_ub.  Roles: warp 0 lane 0 issues TMA loads of 128-row x 32-float boxes
+// (128-byte swizzle) into a 4-stage ring; warp 1 lane 0 issues tcgen05.mma (M = 128, N = 128,
+// K = 8, TF32) and commits each stage back to the producer and each finished tile to the
+// epilogue; warps 2-5 move the tile out of TMEM (double-buffered accumulators, 2 x 128 columns)
+// and subtract it from A22, overlapping the next tile's MMAs.  Every wait is bounded and sets an
+// error flag instead of hanging.
+// ==============================================================================================
+namespace tc2 {
+
+constexpr int BM = 128;                  // rows per tile
+constexpr int BNR = 128;                 // real columns per tile (64 complex)
+constexpr int KR = 2 * tc::NB;           // reals along K (128)
+constexpr int KCH = 32;                  // floats per 128-byte swizzle row
+constexpr int NCHK = KR / KCH;           // 4 chunks per tile
+constexpr int STAGES = 4;
+constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
+constexpr int B_STAGE = BNR * KCH * 4;   // 16 KB
+constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 2 * A_STAGE + 1024;  // ring + 2 epilogue boxes
+constexpr int TMEM_COLS = 256;
+constexpr int NTHREADS = 192;
+constexpr uint32_t SPIN = 1u << 22;
+
+struct alignas(8) Bars {
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  uint32_t tmem_slot;
+  uint32_t abort;  // set by an epilogue warp whose wait gave up
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+// bounded wait; returns false (and raises the error flag) when the limit is reached
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int32_t* err) {
+  for (uint32_t i = 0; i < SPIN; ++i)
+    if (tc::mbar_try_wait(a, parity)) return true;
+  atomicOr(err, 2);
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+// K-major operand in the 128-byte-swizzled canonical layout: 8-row atoms of 128 B, atoms 1024 B
+// apart (SBO), leading offset unused, descriptor version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__host__ __device__ constexpr uint32_t idesc_m128n128() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BNR >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// B^T of the real embedding for the current panel: rows 2c, 2c+1 for trailing column c
+// (relative to p0 + NB), 2K floats each: [ur, -ui, ...] and [ui, ur, ...].  grid (ceil(rem/32), batch)
+__global__ void __launch_bounds__(256) k_build_ub(const float* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                                  float* __restrict__ ub, int64_t ub_stride) {
+  __shared__ float2 t[tc::NB][33];
+  const int z = blockIdx.y;
+  const int rbase = p0 + tc::NB, c0 = blockIdx.x * 32;
+  const float* M = A + (int64_t)z * bstride * 2;
+  for (int e = threadIdx.x; e < tc::NB * 32; e += blockDim.x) {  // U12 rows k, columns c0..c0+31
+    const int k = e / 32, cc = e % 32;
+    const int gc = rbase + c0 + cc;
+    float2 u = make_float2(0.f, 0.f);
+    if (gc < n) u = *reinterpret_cast<const float2*>(M + 2 * ((int64_t)(p0 + k) * ld + gc));
+    t[k][cc] = u;
+  }
+  __syncthreads();
+  float* out = ub + (int64_t)z * ub_stride;
+  for (int e = threadIdx.x; e < 32 * tc::NB; e += blockDim.x) {
+    const int cc = e / tc::NB, k = e % tc::NB;
+    const float2 u = t[k][cc];
+    const int64_t r = 2 * (int64_t)(c0 + cc);
+    const float ur = tc::to_tf32(u.x), ui = tc::to_tf32(u.y);  // round to nearest TF32 once here
+    *reinterpret_cast<float2*>(out + r * KR + 2 * k) = make_float2(ur, -ui);
+    *reinterpret_cast<float2*>(out + (r + 1) * KR + 2 * k) = make_float2(ui, ur);
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB,
+                                                           float* __restrict__ A, int64_t bstride, int n, int ld,
+                                                           int p0, int batch, int ntm, int ntn,
+                                                           int32_t* __restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ Bars bar;
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  const uint32_t smA = tc::smem_u32(sm), smB = smA + STAGES * A_STAGE;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto baddr = [&](const uint64_t& b) { return tc::smem_u32(&b); };
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(baddr(bar.full[s]), 1);
+      mbar_init(baddr(bar.empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(baddr(bar.acc_full[a]), 1);
+      mbar_init(baddr(bar.acc_empty[a]), 4);
+    }
+    bar.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::smem_u32(&bar.tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = bar.tmem_slot;
+  const int ntiles = batch * ntm * ntn;
+  const int rbase = p0 + tc::NB;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer ----
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int z = tile / (ntm * ntn), rr = tile % (ntm * ntn), tm = rr / ntn, tn = rr % ntn;
+        for (int ch = 0; ch < NCHK && ok; ++ch, ++it) {
+          const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+          ok = mbar_wait(baddr(bar.empty[s]), ph ^ 1, err);
+          if (!ok) break;
+          mbar_expect_tx(baddr(bar.full[s]), A_STAGE + B_STAGE);
+          tma_load_3d(smA + s * A_STAGE, &tmA, 2 * p0 + ch * KCH, rbase + tm * BM, z, baddr(bar.full[s]));
+          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, tn * BNR, z, baddr(bar.full[s]));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer ----
+      const uint32_t idesc = idesc_m128n128();
+      uint32_t it = 0, ti = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
+        const uint32_t a = ti & 1, aph = (ti >> 1) & 1;
+        ok = mbar_wait(baddr(bar.acc_empty[a]), aph ^ 1, err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d = tmem + a * BNR;
+        for (int ch = 0; ch < NCHK && ok; ++ch, ++it) {
+          const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+          ok = mbar_wait(baddr(bar.full[s]), ph, err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+          for (int k = 0; k < KCH / 8; ++k)
+            tc::mma_tf32(d, desc_sw128(smA + s * A_STAGE + k * 32), desc_sw128(smB + s * B_STAGE + k * 32), idesc,
+                         (ch | k) ? 1u : 0u);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           baddr(bar.empty[s]))
+                       : "memory");
+        }
+        if (ok)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           baddr(bar.acc_full[a]))
+                       : "memory");
+      }
+    }
+  } else {  // ---- epilogue warps 2..5: TMEM lane quarter = warp % 4 ----
+    // Each 32-column chunk of the accumulator is negated into a 128-byte-swizzled staging box
+    // (two boxes, alternating) and added to A22 by a TMA reduction: the L2 performs the
+    // read-modify-write, the epilogue never waits on global loads.
+    const int q = warp & 3;
+    const int rt = q * 32 + lane;
+    const bool leader = (warp == 2 && lane == 0);
+    const uint32_t smD = smB + STAGES * B_STAGE;  // 2 x 16 KB, 1024-aligned
+    uint32_t ti = 0, nb = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ti) {
+      const int z = tile / (ntm * ntn), rr = tile % (ntm * ntn), tm = rr / ntn, tn = rr % ntn;
+      const uint32_t a = ti & 1, aph = (ti >> 1) & 1;
+      // every epilogue warp reaches the named barrier once per tile, then all leave together if
+      // any of them gave up waiting (no warp may be left alone at a later barrier)
+      if (!mbar_wait(baddr(bar.acc_full[a]), aph, err)) bar.abort = 1;
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+      if (*(volatile uint32_t*)&bar.abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int gr0 = rbase + tm * BM;
+      const int gc0 = 2 * (rbase + tn * (BNR / 2));  // first real column of the tile
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * BNR;
+#pragma unroll 1
+      for (int cc = 0; cc < BNR; cc += 32, ++nb) {
+        float v[32];
+        tmem_ld32(ta + cc, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        const uint32_t box = smD + (nb & 1) * A_STAGE;
+        // the reduction issued two chunks ago read this box: wait until it has
+        if (leader) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+#pragma unroll
+        for (int c4 = 0; c4 < 8; ++c4) {
+          const uint32_t off = (uint32_t)rt * 128 + (uint32_t)((c4 ^ (rt & 7)) * 16);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(box + off), "f"(-v[4 * c4]),
+                       "f"(-v[4 * c4 + 1]), "f"(-v[4 * c4 + 2]), "f"(-v[4 * c4 + 3])
+                       : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");
+        if (leader) {
+          asm volatile(
+              "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                  reinterpret_cast<uint64_t>(&tmA)),
+              "r"(gc0 + cc), "r"(gr0), "r"(z), "r"(box)
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(baddr(bar.acc_empty[a]));
+    }
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static int make_map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1_bytes,
+                       uint64_t s2_bytes) {
+  auto fn = encode_fn();
+  if (!fn) return fail(BIE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {s1_bytes, s2_bytes};
+  const cuuint32_t box[3] = {(cuuint32_t)KCH, (cuuint32_t)BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(BIE_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return BIE_OK;
+}
+
+}  // namespace tc2
 
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
                  void* scratch, size_t scratch_bytes) {
   using namespace tc;
-  if (ld % 2 != 0 || bstride % 2 != 0) return fail(BIE_ERR_INVALID_ARG, "tcgen05 LU needs even ld and batch stride");
+  if (ld % 64 != 0 || bstride % 2 != 0) return fail(BIE_ERR_INVALID_ARG, "tcgen05 LU needs ld % 64 == 0 and even batch stride");
   int32_t* err = (int32_t*)scratch;
   BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  const bool v2 = c->tc_version >= 2;
+  float* ub = reinterpret_cast<float*>((char*)scratch + 256);
+  const int64_t ub_stride = (int64_t)2 * n * tc2::KR;  // floats per matrix
+  CUtensorMap mA, mB;
+  int nsm = 148;
+  if (v2) {
+    if (scratch_bytes < 256 + (size_t)batch * ub_stride * sizeof(float))
+      return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
+    BIE_TRY(tc2::make_map_3d(&mA, A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)batch, (uint64_t)2 * ld * 4,
+                             (uint64_t)bstride * 8));
+    BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)tc2::KR, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)tc2::KR * 4,
+                             (uint64_t)ub_stride * 4));
+    BIE_CUDA_TRY(cudaFuncSetAttribute(tc2::k_update_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, tc2::SMEM_BYTES));
+    BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  } else {
+    BIE_CUDA_TRY(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  }
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int w = std::min(NB, n - p0);
     BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info));
     const int rem = n - p0 - w;
-    if (rem > 0) {
+    if (rem <= 0) continue;
+    if (v2) {
+      dim3 gb((unsigned)((rem + 31) / 32), (unsigned)batch);
+      BIE_LAUNCH(tc2::k_build_ub<<<gb, 256, 0, c->stream>>>(reinterpret_cast<const float*>(A), bstride, n, ld, p0, ub,
+                                                            ub_stride));
+      const int ntm = (rem + tc2::BM - 1) / tc2::BM, ntn = (rem + tc2::BNR / 2 - 1) / (tc2::BNR / 2);
+      const int ntiles = ntm * ntn * batch;
+      const int grid = std::min(ntiles, nsm);
+      BIE_LAUNCH(tc2::k_update_tc2<<<grid, tc2::NTHREADS, tc2::SMEM_BYTES, c->stream>>>(
+          mA, mB, reinterpret_cast<float*>(A), bstride, n, ld, p0, batch, ntm, ntn, err));
+    } else {
       dim3 g((unsigned)((rem + BN - 1) / BN), (unsigned)((rem + BM - 1) / BM), (unsigned)batch);
       BIE_LAUNCH(k_update_tc<<<g, 128, SMEM_BYTES, c->stream>>>(reinterpret_cast<float*>(A), bstride, n, ld, p0, err));
     }
