@@ -93,7 +93,7 @@ int bie_create(bie_ctx** out, int cuda_device, void* cuda_stream);
 /* Synchronises the context's stream and frees everything it owns. NULL is accepted. */
 int bie_destroy(bie_ctx* ctx);
 
-/* Quadrature of Sec. 3 ("simple"/"standard Gauss" quadrature): ng x ng collapsed Gauss-Legendre
+/* Quadrature (Sec. 3: ordinary Gauss quadrature on regular integrands): ng x ng collapsed Gauss-Legendre
  * points per element (default 4), and ng_near x ng_near per sub-triangle for elements that
  * contain the collocation node (default 6), which are split at that node and collapsed onto it.
  * Must precede bie_set_geometry to take effect on it.  Errors: INVALID_ARG unless

@@ -26,7 +26,7 @@ int or_num_threads(void) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * Quadrature ("simple" / "standard Gauss" quadrature, Sec. 3).  The paper names no rule; the
+ * Quadrature (Sec. 3: ordinary Gauss quadrature suffices once the kernels are regular).  The paper names no rule; the
  * reading used here is a collapsed-coordinate tensor Gauss-Legendre rule.
  * ------------------------------------------------------------------------------------------ */
 int or_gauss_legendre01(int n, double* x, double* w) {
@@ -262,7 +262,7 @@ int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int
 }
 
 /* ------------------------------------------------------------------------------------------
- * "Solved using a direct method" (Sec. 4): textbook Doolittle LU with partial pivoting.
+ * Direct solution of the linear system (Sec. 4): textbook Doolittle LU with partial pivoting.
  * ------------------------------------------------------------------------------------------ */
 int or_lu_factor(int64_t n, cplx* A, int64_t* piv) {
   for (int64_t k = 0; k < n; ++k) {

@@ -1,5 +1,5 @@
-// lu.cu -- batched dense complex LU with partial pivoting and triangular solves ("solved using a
-// direct method", Sec. 4), right-looking and blocked:
+// lu.cu -- batched dense complex LU with partial pivoting and triangular solves (the direct solver
+// of Sec. 4), right-looking and blocked:
 //   for each panel of width nb:  factor the panel (pivot = largest modulus, lowest row on ties),
 //   apply its row swaps to the other columns, U12 = L11^{-1} A12, A22 -= L21 U12.
 // Matrices are row-major with leading dimension ld, batched with stride `bstride` elements.

@@ -1,4 +1,4 @@
-// lu_tc.cu -- blocked complex LU ("solved using a direct method", Sec. 4) with the trailing update
+// lu_tc.cu -- blocked complex LU (the direct solver of Sec. 4) with the trailing update
 // A22 -= L21 U12 on the 5th-generation tensor cores (tcgen05, TF32 operands, FP32 accumulation in
 // tensor memory).  Panel factorisation with partial pivoting and the U12 solve run on the CUDA
 // cores (lu.cu); the update, a genuine dense contraction, runs here.

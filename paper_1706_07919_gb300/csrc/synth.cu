@@ -1,6 +1,6 @@
 // synth.cu -- pulse spectra and space-time synthesis by the discrete Fourier transform with the
-// sign of Eq. (inverseFourier) (exp(-i omega t)), evaluated by a radix-2 FFT (Sec. 3 end:
-// "discrete fast Fourier transform").
+// sign of Eq. (inverseFourier) (exp(-i omega t)), evaluated by a radix-2 FFT (the last paragraph
+// of Sec. 3 asks for the discrete fast Fourier transform).
 //   spectrum:  S[p][m] = sum_n s[p][n] exp(+2 pi i m n / Nt) = conj(FFT(s))_m  (real s)
 //   synthesis: out[p][x][n] = (1/Nt) Re sum_m c_m exp(-2 pi i m n / Nt),  c_m = w_m S[p][m] T[m][x],
 //              w_0 = w_{Nt/2} = 1, else 2 (the m > Nt/2 half is the complex conjugate).
