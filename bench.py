@@ -351,6 +351,36 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_case(args):
+    """Small cases for profiler captures (no timing, no output line): `lu` factors and refines four
+    two-sphere systems (k = 3.15 .. 3.25); `field` evaluates the field of eight wavenumbers at 2048
+    of the 16 384 plane points from a constant surface solution."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+
+    w = build_workload()
+    sol = Solver(0)
+    sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    sol.set_option("mixed.tcgen05", args.tc)
+    if args.case == "lu":
+        sol.set_option("mixed.fallback_err_est", 1.0)
+        surf, rep = sol.solve_frequencies(w.k[100:104], B.BIE_MODE_MIXED)
+        print("case lu: refinement corrections", [r.iters for r in rep])
+    else:
+        ks = w.k[496:504]
+        surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
+        xo = torch.tensor(w.xobs[::8], device="cuda")
+        T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
+        print("case field:", tuple(T.shape))
+    torch.cuda.synchronize()
+    sol.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,7 +392,12 @@ def main():
     ap.add_argument("--check", type=int, default=4)
     ap.add_argument("--cpu-points", dest="cpu_points", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", choices=["lu", "field"], default=None,
+                    help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
                                                  const double* __restrict__ xp, int64_t M,
                                                  const int32_t* __restrict__ foot_elem,
                                                  const double* __restrict__ foot, const double* __restrict__ kv,
-                                                 int nk, cd* __restrict__ T, TwoPi3f tp) {
+                                                 int nk, cd* __restrict__ T, TwoPi3f tp, int uniform,
+                                                 ff dk) {
   __shared__ float sg[13][FT];        // quadrature geometry tile
   __shared__ float sq[FKB][4][FT];    // Pq, Pnq (re, im) of the tile for each wavenumber
   __shared__ float s0[FKB][4][FT];    // P0, P0' (re, im) of each thread's point for each wavenumber
@@ -376,18 +377,44 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
       const ff R0 = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
       const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
       const float iRp = 1.0f / Rp.hi, iR0 = 1.0f / R0.hi;
-      const float rnp = ff_add(ff_add(ff_mul(rpx, nux), ff_mul(rpy, nuy)), ff_mul(rpz, nuz)).hi * iRp * iRp * iRp;
+      // x_p is off the surface (no cancellation in r.nu); x0 is on it, so r0.nu is second-order
+      // small for nearby quadrature points and is formed in float-float
+      const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp * iRp;
       const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0 * iR0;
       const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
+      // phase factors: on a uniform group k_j = k_0 + j dk, e^{i k_j R} = e^{i k_0 R} (e^{i dk R})^j with
+      // both factors accurate and the powers taken by FP32 rotation (drift <= nkb ulps)
+      float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
+      float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
+      if (uniform) {
+        const ff k0 = {sk[0][0], sk[0][1]};
+        cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
+        cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
+        cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
+        cis_ffk(ff_mul(dk, Rp), tp, dcp, dsp);
+        cis_ffk(ff_mul(dk, R0), tp, dc0, ds0);
+        cis_ffk(ff_mul(dk, nr), tp, dcg, dsg);
+      }
 #pragma unroll
       for (int j = 0; j < FKB; ++j) {
         if (j < nkb) {
           const ff k = {sk[j][0], sk[j][1]};
           const float kinv = sk[j][2];
-          float cp, spp, c0, s0v, cg, sgv;
-          cis_ffk(ff_mul(k, Rp), tp, cp, spp);
-          cis_ffk(ff_mul(k, R0), tp, c0, s0v);
-          cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+          if (!uniform) {
+            cis_ffk(ff_mul(k, Rp), tp, cp, spp);
+            cis_ffk(ff_mul(k, R0), tp, c0, s0v);
+            cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+          } else if (j > 0) {
+            float t = cp * dcp - spp * dsp;
+            spp = spp * dcp + cp * dsp;
+            cp = t;
+            t = c0 * dc0 - s0v * ds0;
+            s0v = s0v * dc0 + c0 * ds0;
+            c0 = t;
+            t = cg * dcg - sgv * dsg;
+            sgv = sgv * dcg + cg * dsg;
+            cg = t;
+          }
           const float kRp = k.hi * Rp.hi, kR0 = k.hi * R0.hi;
           const float Gpr = cp * iRp, Gpi = spp * iRp, G0r = c0 * iR0, G0i = s0v * iR0;
           const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
@@ -434,8 +461,18 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
     if (c->field_accurate_phase) {
       dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
+      // uniform spacing inside every group of FKB wavenumbers enables the phase recurrence
+      std::vector<double> hk(nk);
+      BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      int uniform = nk > 1 ? 1 : 0;
+      const double dkv = nk > 1 ? hk[1] - hk[0] : 0.0;
+      for (int j = 0; j < nk && uniform; ++j) {
+        const double expect = hk[(j / FKB) * FKB] + (j % FKB) * dkv;
+        if (std::fabs(hk[j] - expect) > 1e-12 * std::fabs(hk[j]) || !(dkv > 0.0)) uniform = 0;
+      }
       BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot, kv,
-                                           nk, T, tp));
+                                           nk, T, tp, uniform, ff_from_double(dkv)));
     }
     else
       BIE_LAUNCH(k_field32<false><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,

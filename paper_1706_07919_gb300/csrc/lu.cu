@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
 }
 
 // Rows below the leaf, panel columns right of it: A -= L_leaf U_leaf (K = lw <= 16).
-// grid (ceil(rows / 256), batch), block 256.
+// One warp per row, lanes over the (<= 64) columns so that the read-modify-write of A coalesces;
+// the row's lw entries of L are broadcast.  grid (ceil(rows / 64), batch), block 256 (8 warps, 8
+// rows each).
 template <class S>
 __global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
                                                      int w, int c0, int lw) {
@@ -207,20 +209,31 @@ __global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int6
     U[s * 64 + j] = M[(int64_t)(c0 + s) * ld + cs + j];
   }
   __syncthreads();
-  const int r = c0 + lw + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  Cx<S> l[16];
-  for (int s = 0; s < lw; ++s) l[s] = M[(int64_t)r * ld + c0 + s];
-  for (int j = 0; j < wr; ++j) {
-    S ar = 0, ai = 0;
-    for (int s = 0; s < lw; ++s) {
-      const Cx<S> u = U[s * 64 + j];
-      ar += l[s].re * u.re - l[s].im * u.im;
-      ai += l[s].re * u.im + l[s].im * u.re;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbeg = c0 + lw + blockIdx.x * 64;
+  for (int r = rbeg + warp; r < min(rbeg + 64, n); r += 8) {
+    const Cx<S>* lrow = M + (int64_t)r * ld + c0;
+    Cx<S> l[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s)
+      if (s < lw) l[s] = lrow[s];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j < wr) {
+        S ar = 0, ai = 0;
+#pragma unroll
+        for (int s = 0; s < 16; ++s)
+          if (s < lw) {
+            const Cx<S> u = U[s * 64 + j];
+            ar += l[s].re * u.re - l[s].im * u.im;
+            ai += l[s].re * u.im + l[s].im * u.re;
+          }
+        Cx<S>& m = M[(int64_t)r * ld + cs + j];
+        m.re -= ar;
+        m.im -= ai;
+      }
     }
-    Cx<S>& m = M[(int64_t)r * ld + cs + j];
-    m.re -= ar;
-    m.im -= ai;
   }
 }
 
@@ -249,7 +262,7 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
     BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info));
     const int rows = n - c0 - l;
     if (rows > 0 && c0 + l < p0 + w) {
-      dim3 g((unsigned)((rows + 255) / 256), batch);
+      dim3 g((unsigned)((rows + 63) / 64), batch);
       BIE_LAUNCH(k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l));
     }
   }
