@@ -15,6 +15,12 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   field                                   pinned: interior point source, conventional representation
   dft / synthesize                        pinned: numpy FFT, Gaussian closed form, Parseval
   full solve                              pinned: analytic rigid/soft sphere partial-wave series
+  mlp_features                            pinned: closed-form values at chosen nodes
+  mlp_forward / mlp_loss                  pinned: zero-weight and single-path closed forms
+  mlp_loss_grad                           pinned: central finite differences of mlp_loss
+  adam_step                               pinned: first step moves every parameter by lr*sign(g)
+(the mlp_* functions restate the learned warm start of the frequency sweep, which is not part of
+the paper's method; its definition is written out at the top of mlp.c)
 """
 from __future__ import annotations
 
@@ -31,12 +37,13 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (plain C11, OpenMP) into oracle/liboracle.so."""
-    src = os.path.join(_HERE, "oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
+    deps = srcs + [os.path.join(_HERE, "oracle.h")]
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            os.path.getmtime(f) for f in deps):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, src, "-lm"])
+                               "-o", tmp, *srcs, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,6 +68,11 @@ def _load():
             "or_field": [c_dp, i64, c_ip, i64, dbl, i32, c_dp, c_dp, c_dp, i64, c_ip, c_dp, c_dp, c_dp],
             "or_dft": [i64, c_dp, c_dp],
             "or_synthesize": [i64, i64, c_dp, c_ip, i64, i64, c_dp, c_dp],
+            "or_mlp_features": [c_dp, c_dp, i64, c_dp, i64, c_dp, c_dp, dbl, dbl, c_dp],
+            "or_mlp_forward": [c_dp, c_dp, i64, c_dp],
+            "or_mlp_loss_grad": [c_dp, c_dp, c_dp, i64, c_dp, c_dp],
+            "or_mlp_loss": [c_dp, c_dp, c_dp, i64, c_dp],
+            "or_adam_step": [i64, c_dp, c_dp, c_dp, c_dp, i64, dbl, dbl, dbl, dbl],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -69,6 +81,7 @@ def _load():
         lib.or_shape6.argtypes = [dbl, dbl, c_dp, c_dp, c_dp]
         lib.or_shape6.restype = None
         lib.or_num_threads.restype = ctypes.c_int
+        lib.or_mlp_param_count.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -225,3 +238,73 @@ def synthesize(T: np.ndarray, midx: np.ndarray, S: np.ndarray, Nt: int) -> np.nd
     out = np.zeros((P, M, Nt))
     _check(_load().or_synthesize(Nk, M, _p(T), _p(midx), P, Nt, _p(S), _p(out)), "synthesize")
     return out
+
+
+# ---- learned warm start (not part of the paper's method; defined at the top of mlp.c) --------
+MLP_IN, MLP_WIDTH, MLP_OUT = 64, 256, 2
+
+
+def mlp_param_count() -> int:
+    return int(_load().or_mlp_param_count())
+
+
+def mlp_param_slices() -> dict:
+    """Named views into the flat parameter vector: W1 b1 W2 b2 W3 b3 W4 b4."""
+    shapes = [("W1", (MLP_WIDTH, MLP_IN)), ("b1", (MLP_WIDTH,)), ("W2", (MLP_WIDTH, MLP_WIDTH)),
+              ("b2", (MLP_WIDTH,)), ("W3", (MLP_WIDTH, MLP_WIDTH)), ("b3", (MLP_WIDTH,)),
+              ("W4", (MLP_OUT, MLP_WIDTH)), ("b4", (MLP_OUT,))]
+    out, off = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        out[name] = (off, shp)
+        off += n
+    return out
+
+
+def mlp_features(nodes, normals, kv, direction, centre, scale: float, kmax: float) -> np.ndarray:
+    x = np.ascontiguousarray(nodes, np.float64)
+    nu = np.ascontiguousarray(normals, np.float64)
+    kv = np.ascontiguousarray(np.atleast_1d(kv), np.float64)
+    d = np.ascontiguousarray(direction, np.float64)
+    c = np.ascontiguousarray(centre, np.float64)
+    N, nk = x.shape[0], kv.shape[0]
+    phi = np.zeros((nk, N, MLP_IN))
+    _check(_load().or_mlp_features(_p(x), _p(nu), N, _p(kv), nk, _p(d), _p(c), float(scale), float(kmax),
+                                   _p(phi)), "mlp_features")
+    return phi
+
+
+def mlp_forward(theta, X) -> np.ndarray:
+    theta = np.ascontiguousarray(theta, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, MLP_IN)
+    Y = np.zeros((X.shape[0], MLP_OUT))
+    _check(_load().or_mlp_forward(_p(theta), _p(X), X.shape[0], _p(Y)), "mlp_forward")
+    return Y
+
+
+def mlp_loss(theta, X, T) -> float:
+    theta = np.ascontiguousarray(theta, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, MLP_IN)
+    T = np.ascontiguousarray(T, np.float64).reshape(-1, MLP_OUT)
+    L = np.zeros(1)
+    _check(_load().or_mlp_loss(_p(theta), _p(X), _p(T), X.shape[0], _p(L)), "mlp_loss")
+    return float(L[0])
+
+
+def mlp_loss_grad(theta, X, T):
+    theta = np.ascontiguousarray(theta, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, MLP_IN)
+    T = np.ascontiguousarray(T, np.float64).reshape(-1, MLP_OUT)
+    L = np.zeros(1)
+    g = np.zeros(theta.shape[0])
+    _check(_load().or_mlp_loss_grad(_p(theta), _p(X), _p(T), X.shape[0], _p(L), _p(g)), "mlp_loss_grad")
+    return float(L[0]), g
+
+
+def adam_step(theta, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """In place on theta, m, v (float64 arrays)."""
+    for a in (theta, grad, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(_load().or_adam_step(theta.shape[0], _p(theta), _p(grad), _p(m), _p(v), int(t), float(lr),
+                                float(beta1), float(beta2), float(eps)), "adam_step")

@@ -94,6 +94,23 @@ int or_dft(int64_t Nt, const double* s, double _Complex* S);
 int or_synthesize(int64_t Nk, int64_t M, const double _Complex* T, const int64_t* midx,
                   int64_t P, int64_t Nt, const double _Complex* S, double* p);
 
+/* ---- learned warm start of the frequency sweep (not part of the paper's method) -------------
+ * Feature map, network, loss and optimiser step are defined in full at the top of mlp.c; the
+ * parameter vector is W1 (256x64) | b1 | W2 (256x256) | b2 | W3 (256x256) | b3 | W4 (2x256) | b4. */
+int64_t or_mlp_param_count(void);
+/* phi[nk][N][64] for nodes x[N][3] with normals nu[N][3] at wavenumbers kv[nk]. */
+int or_mlp_features(const double* x, const double* nu, int64_t N, const double* kv, int64_t nk,
+                    const double* dir, const double* centre, double scale, double kmax, double* phi);
+/* Y[B][2] = network(X[B][64]). */
+int or_mlp_forward(const double* theta, const double* X, int64_t B, double* Y);
+/* loss = (1/B) sum |Y - T|^2 and its gradient with respect to theta (analytic backward). */
+int or_mlp_loss_grad(const double* theta, const double* X, const double* T, int64_t B, double* loss,
+                     double* grad);
+int or_mlp_loss(const double* theta, const double* X, const double* T, int64_t B, double* loss);
+/* One Adam step (step counter t >= 1) on P parameters, in place on theta, m, v. */
+int or_adam_step(int64_t P, double* theta, const double* grad, double* m, double* v, int64_t t, double lr,
+                 double beta1, double beta2, double eps);
+
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);
 
