@@ -180,13 +180,19 @@ def run_ours(args):
     rng = np.random.Generator(np.random.PCG64(2001))
     sample = np.sort(rng.choice(Nk, size=args.check, replace=False))
     ks = w.k[sample]
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
     s64, _ = sol.solve_frequencies(ks, B.BIE_MODE_FP64)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_solves_per_s = len(ks) / (f0.elapsed_time(f1) / 1e3)
     errs = [(torch.linalg.norm(surf[i] - s64[j]) / torch.linalg.norm(s64[j])).item() for j, i in enumerate(sample)]
     T64 = sol.eval_field(xo, ks, s64, B.BIE_MODE_FP64)
     ferrs = [(torch.linalg.norm(T[i] - T64[j]) / torch.linalg.norm(T64[j])).item() for j, i in enumerate(sample)]
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
     e2e = run_e2e(args, w, sol, B, dev, stream)
+    solve_rate = Nk * args.steps / (phase[0] / 1e3)
 
     # ---- roofline of the dominant kernel (measured live on its stream) ----
     roof = roofline_live(args, w, sol, B, dev, stream, surf, xo)
@@ -212,17 +218,80 @@ def run_ours(args):
         "accuracy": {"sampled_k": [float(x) for x in ks], "max_rel_err_surface_vs_fp64": max(errs),
                      "max_rel_err_field_vs_fp64": max(ferrs), "fp64_reassembled": nre64, "fp64_full_solves": nfall,
                      "max_refine_iters": max(r.iters for r in rep)},
+        "fp64_path": {"solves_per_s": fp64_solves_per_s, "sample": f"{len(ks)} wavenumbers, same N",
+                      "mixed_solve_phase_speedup": solve_rate / fp64_solves_per_s},
         "clocks": clk.summary(),
         "e2e": e2e,
         "roofline": roof,
         "gpu_launches": int(launches),
     }
+    sol.close()
+    if not args.no_learned:
+        line["learned"] = run_learned(args, dev, stream)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
         print(json.dumps(line))
-    sol.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_learned(args, dev, stream):
+    """The learned-warm-start sweep (BIE_MODE_LEARNED) on the spheroid workload: hard prolate
+    spheroid (1, 1, 2), N = 2562, 1024 wavenumbers over ka in (0, 20]; every 8th solved directly,
+    the network trained on those, the rest by GMRES from its prediction.  Timed next to the
+    mixed direct path on the same wavenumbers and to GMRES from a zero start; accuracy on sampled
+    GMRES-solved wavenumbers against the FP64 GPU path."""
+    import torch
+
+    from workloads import config_spheroid_learned
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+
+    w = config_spheroid_learned()
+    Nk = len(w.k)
+    sol = Solver(dev.index if dev.index is not None else 0, stream)
+    sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    sol.set_incident_plane_wave(w.direction)
+    sol.set_option("mixed.batch", args.batch)
+    sol.set_option("learned.epochs", args.epochs)
+    with torch.cuda.stream(stream):
+        surf = torch.empty((Nk, 2, w.mesh.N), dtype=torch.complex128, device=dev)
+        surf_d = torch.empty_like(surf)
+
+    def timed(mode, out):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        _, rep = sol.solve_frequencies(w.k, mode, out=out)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t, rep
+
+    sol.solve_frequencies(w.k[:64], B.BIE_MODE_LEARNED)  # warm-up (module load, graph paths)
+    t_l, rep_l = timed(B.BIE_MODE_LEARNED, surf)
+    info = sol.learned_info()
+    t_d, _ = timed(B.BIE_MODE_MIXED, surf_d)
+    sol.set_option("learned.x0", 0)
+    t_z, _ = timed(B.BIE_MODE_LEARNED, surf_d)
+    info_z = sol.learned_info()
+    sol.set_option("learned.x0", 1)
+    # accuracy: sampled wavenumbers that GMRES solved, against the FP64 path
+    rng = np.random.Generator(np.random.PCG64(3002))
+    gm = [i for i, r in enumerate(rep_l) if r.path == B.BIE_MODE_LEARNED]
+    sample = np.sort(rng.choice(gm, size=min(args.check, len(gm)), replace=False)) if gm else np.array([], int)
+    errs = []
+    if len(sample):
+        s64, _ = sol.solve_frequencies(w.k[sample], B.BIE_MODE_FP64)
+        errs = [(torch.linalg.norm(surf[i] - s64[j]) / torch.linalg.norm(s64[j])).item()
+                for j, i in enumerate(sample)]
+    sol.close()
+    return {"workload": "spheroid_1_1_2_N2562_Nk1024_ka20", "solves_per_s": Nk / t_l,
+            "mixed_direct_solves_per_s": Nk / t_d, "zero_start_solves_per_s": Nk / t_z,
+            "anchors": info["anchors"], "krylov": info["krylov"], "krylov_fallback": info["krylov_fallback"],
+            "epochs": info["epochs"], "train_ms": info["train_ms"], "first_loss": info["first_loss"],
+            "last_loss": info["last_loss"], "x0_rel_err": info["x0_rel_err"], "mean_arnoldi_steps": info["mean_iters"],
+            "zero_start_mean_arnoldi_steps": info_z["mean_iters"],
+            "zero_start_krylov_fallback": info_z["krylov_fallback"],
+            "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,
+            "timing": "wall clock around each synchronising call (host-side setup included)"}
 
 
 def run_e2e(args, w, sol, B, dev, stream):
@@ -392,6 +461,9 @@ def main():
     ap.add_argument("--check", type=int, default=4)
     ap.add_argument("--cpu-points", dest="cpu_points", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", dest="no_learned", action="store_true",
+                    help="skip the learned-warm-start sweep on the spheroid workload")
+    ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned warm start")
     ap.add_argument("--case", choices=["lu", "field"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()

@@ -49,6 +49,14 @@ extern "C" {
 #define BIE_MODE_FP64 0   /* FP64 assembly, FP64 LU with partial pivoting, FP64 solve */
 #define BIE_MODE_MIXED 1  /* FP32 assembly (float-float distance/phase), TF32 tcgen05 LU,
                              iterative refinement with float-float residuals */
+#define BIE_MODE_LEARNED 2 /* every "learned.stride"-th wavenumber ("anchor") solved as
+                             BIE_MODE_MIXED, keeping its low-precision factor; a network trained on
+                             the anchors' solutions predicts the others, which are solved by
+                             flexible GMRES from that guess, preconditioned by the nearest anchor's
+                             factor (see bie_set_option); not part of the paper's method */
+
+/* Parameter count of the learned warm start's network (see bie_mlp_set_params). */
+#define BIE_MLP_PARAMS 148738
 
 /* Report flags (bie_report.flags). */
 #define BIE_FLAG_NOT_CONVERGED 1u   /* refinement stopped at its iteration cap */
@@ -65,7 +73,8 @@ typedef struct bie_ctx bie_ctx;
 
 /* Per-frequency outcome of bie_solve_frequencies (host array, valid when that call returns). */
 typedef struct {
-  int32_t iters;        /* refinement iterations (0 for the FP64 path) */
+  int32_t iters;        /* refinement iterations (0 for the FP64 path); Arnoldi steps for
+                           wavenumbers solved by GMRES in BIE_MODE_LEARNED */
   int32_t path;         /* BIE_MODE_* that produced the result */
   uint32_t flags;       /* BIE_FLAG_* bits */
   int32_t reserved;
@@ -73,6 +82,19 @@ typedef struct {
   double err_est;       /* mixed path: estimated relative L2 error of x caused by the FP32
                            assembly (a seeded FP32-sized perturbation of A solved with the LU) */
 } bie_report;
+
+/* Summary of the last BIE_MODE_LEARNED call (bie_get_learned_info()). */
+typedef struct {
+  int32_t anchors;         /* wavenumbers solved directly */
+  int32_t krylov;          /* wavenumbers solved by GMRES */
+  int32_t krylov_fallback; /* of those, re-solved directly (GMRES did not converge) */
+  int32_t epochs;          /* training epochs run */
+  float first_loss;        /* mean minibatch loss of the first and last epoch (targets scaled to */
+  float last_loss;         /*   unit mean square) */
+  double train_ms;         /* wall time of the training */
+  double x0_rel_err;       /* mean over GMRES-solved wavenumbers of ||x0 - x|| / ||x|| */
+  double mean_iters;       /* mean Arnoldi steps per GMRES-solved wavenumber */
+} bie_learned_info;
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* bie_last_error(void);
@@ -127,6 +149,21 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
+ * Learned warm start and Krylov solve (BIE_MODE_LEARNED):
+ *   "learned.stride"       every stride-th wavenumber of the call is an anchor (>= 2, default 8;
+ *                          indices stride-1, 2 stride-1, ...; the last index if none)
+ *   "learned.x0"           initial guess of the GMRES solves: 1 the network (default), 0 zero,
+ *                          2 the nearest anchor's solution
+ *   "learned.epochs"       training epochs (0..100000, default 60)
+ *   "learned.batch"        rows per minibatch (128..1048576, rounded up to 128; default 8192)
+ *   "learned.lr", "learned.lr_min"  Adam step size, cosine-decayed to lr_min (default 2e-3, 1e-4)
+ *   "learned.seed"         initial weights and minibatch order (default 1234)
+ *   "learned.kmax"         wavenumber scale of the feature map (0: the largest training k)
+ *   "learned.graph"        1: replay each training epoch from a captured CUDA graph (default)
+ *   "gmres.m"              Arnoldi steps per cycle (1..62, default 30)
+ *   "gmres.cycles"         cycles, each from a float-float residual (1..100, default 6)
+ *   "gmres.inner_tol"      relative residual decrease that ends a cycle (default 1e-5)
+ * The refinement target "refine.tol" is also the GMRES backward-error target.
  * Errors: INVALID_ARG for an unknown name or a value out of range. */
 int bie_set_option(bie_ctx* ctx, const char* name, double value);
 
@@ -140,7 +177,8 @@ int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
 
 /* Frequency solves (the per-k hot path): for each k[m] > 0 assemble, factor and solve.
  *   k        host f64 [Nk]
- *   mode     BIE_MODE_FP64 or BIE_MODE_MIXED
+ *   mode     BIE_MODE_FP64, BIE_MODE_MIXED or BIE_MODE_LEARNED (which trains the context's
+ *            network on this call's anchors, replacing its parameters)
  *   surf_out device c128 [Nk][2][N]: scattered P and dP/dn at every node, per k
  *   rep      host bie_report [Nk] or NULL
  * Synchronises the stream before returning (the reports are read back).  Errors: INVALID_ARG,
@@ -188,6 +226,47 @@ int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk,
  * calls whose work overlaps on the GPU (different streams or threads) race. */
 int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
                            int64_t P, int64_t Nt, void* out, int out_dtype, void* stream);
+
+/* ---- learned warm start (BIE_MODE_LEARNED's network; not part of the paper's method) ---------
+ * Feature map of node x (normal nu) at wavenumber k, 64 values: (x - c)/s, nu, k/kmax, (k/kmax)^2,
+ * then cos and sin of k * sc_q * (b_j . (x - c)) for j = 0..6, q = 0..3 (value 8 + 2(4j+q) is the
+ * cosine, 9 + 2(4j+q) the sine), b = {d, e_x, e_y, e_z, (e_x+e_y)/sqrt2, (e_y+e_z)/sqrt2,
+ * (e_z+e_x)/sqrt2}, sc = {0.5, 1, 1.5, 2}; c = centroid of the nodes, s = largest node distance
+ * from c, kmax = "learned.kmax" or the largest wavenumber of the last training.
+ * Network: h1 = tanh(W1 phi + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3), y = W4 h3 + b4;
+ * parameters (FP32) in the order W1 [256][64], b1 [256], W2 [256][256], b2, W3 [256][256], b3,
+ * W4 [2][256], b4 [2] (row-major, BIE_MLP_PARAMS values).  Hidden layers run with BF16 operands
+ * and FP32 accumulation on the tensor cores.  Loss over B rows: (1/B) sum |y - t|^2.
+ * Targets when training on solutions: t = u exp(-i k d.x) / tau, u the node's unknown (P at
+ * hard, dP/dn at soft nodes), tau the root mean square of |u| over the training rows; the
+ * prediction is x0 = tau (y0 + i y1) exp(i k d.x). */
+
+/* Copies in (host f32 [BIE_MLP_PARAMS]) the network parameters and resets the optimiser. */
+int bie_mlp_set_params(bie_ctx* ctx, const float* theta);
+/* Copies out (host f32 [BIE_MLP_PARAMS]).  Errors: STATE before any parameters exist. */
+int bie_mlp_get_params(bie_ctx* ctx, float* theta);
+/* Features of every node at k[0..nk) (host f64), as fed to the network (rounded to BF16):
+ * phi_out device f32 [nk][N][64].  Errors: STATE without geometry or wavenumber scale. */
+int bie_mlp_features(bie_ctx* ctx, const double* k, int64_t nk, float* phi_out);
+/* Network outputs: X device f32 [B][64], Y_out device f32 [B][2].  Synchronises. */
+int bie_mlp_forward(bie_ctx* ctx, const float* X, int64_t B, float* Y_out);
+/* Loss and its gradient: X device f32 [B][64], T device f32 [B][2]; grad_out device f32
+ * [BIE_MLP_PARAMS], loss_out device f32 [1] (either may be NULL).  Synchronises. */
+int bie_mlp_loss_grad(bie_ctx* ctx, const float* X, const float* T, int64_t B, float* grad_out,
+                      float* loss_out);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step size lr) with the
+ * gradient grad (device f32 [BIE_MLP_PARAMS]) on the context's parameters and moments. */
+int bie_mlp_adam_step(bie_ctx* ctx, const float* grad, double lr);
+/* Trains on surface solutions: k host f64 [nk], surf device c128 [nk][2][N] (as written by
+ * bie_solve_frequencies); runs `epochs` epochs with the "learned.*" options, starting from the
+ * current parameters (or a seeded Glorot initialisation).  loss_hist host f32 [epochs] or NULL. */
+int bie_mlp_train(bie_ctx* ctx, const double* k, int64_t nk, const void* surf, int epochs,
+                  float* loss_hist);
+/* Predicted unknowns x0 = tau (y0 + i y1) exp(i k d.x) at every node: k host f64 [nk], x0_out
+ * device c128 [nk][N].  Synchronises. */
+int bie_mlp_predict(bie_ctx* ctx, const double* k, int64_t nk, void* x0_out);
+/* Summary of the last BIE_MODE_LEARNED solve (host out). */
+int bie_get_learned_info(bie_ctx* ctx, bie_learned_info* out);
 
 #ifdef __cplusplus
 }

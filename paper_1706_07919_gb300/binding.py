@@ -25,6 +25,8 @@ BIE_ERR_TIMEOUT = -6
 BIE_ERR_STATE = -7
 BIE_MODE_FP64 = 0
 BIE_MODE_MIXED = 1
+BIE_MODE_LEARNED = 2
+BIE_MLP_PARAMS = 148738
 BIE_FLAG_NOT_CONVERGED = 1
 BIE_FLAG_FALLBACK_FP64 = 2
 BIE_FLAG_ZERO_PIVOT = 4
@@ -33,12 +35,20 @@ BIE_FLAG_FP64_ASSEMBLY = 16
 
 EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create", "bie_destroy", "bie_set_quadrature",
             "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",
-            "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc"]
+            "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc", "bie_mlp_set_params",
+            "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
+            "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info"]
 
 
 class BieReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("path", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("reserved", ctypes.c_int32), ("backward_err", ctypes.c_double), ("err_est", ctypes.c_double)]
+
+
+class BieLearnedInfo(ctypes.Structure):
+    _fields_ = [("anchors", ctypes.c_int32), ("krylov", ctypes.c_int32), ("krylov_fallback", ctypes.c_int32),
+                ("epochs", ctypes.c_int32), ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float),
+                ("train_ms", ctypes.c_double), ("x0_rel_err", ctypes.c_double), ("mean_iters", ctypes.c_double)]
 
 
 class BieError(RuntimeError):
@@ -76,6 +86,15 @@ def load(path: str | None = None):
         "bie_pulse_spectrum": ([vp, vp, i64, i64, vp], i32),
         "bie_synthesize": ([vp, vp, vp, i64, i64, vp, i64, i64, vp, i32], i32),
         "bie_synthesize_noalloc": ([vp, vp, i64, i64, vp, i64, i64, vp, i32, vp], i32),
+        "bie_mlp_set_params": ([vp, vp], i32),
+        "bie_mlp_get_params": ([vp, vp], i32),
+        "bie_mlp_features": ([vp, vp, i64, vp], i32),
+        "bie_mlp_forward": ([vp, vp, i64, vp], i32),
+        "bie_mlp_loss_grad": ([vp, vp, vp, i64, vp, vp], i32),
+        "bie_mlp_adam_step": ([vp, vp, dbl], i32),
+        "bie_mlp_train": ([vp, vp, i64, vp, i32, vp], i32),
+        "bie_mlp_predict": ([vp, vp, i64, vp], i32),
+        "bie_get_learned_info": ([vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -177,3 +196,54 @@ def bie_synthesize_noalloc(T, midx, S, Nt: int, out, out_dtype: int, stream: int
     midx = np.ascontiguousarray(midx, np.int64)
     _check(load().bie_synthesize_noalloc(_dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
                                          _dp(out), out_dtype, stream))
+
+
+# ---- learned warm start (not part of the paper's method; see bie.h) ---------------------------
+def bie_mlp_set_params(ctx: int, theta) -> None:
+    th = np.ascontiguousarray(theta, np.float32)
+    if th.shape != (BIE_MLP_PARAMS,):
+        raise ValueError(f"expected {BIE_MLP_PARAMS} parameters")
+    _check(load().bie_mlp_set_params(ctx, _hp(th)))
+
+
+def bie_mlp_get_params(ctx: int) -> np.ndarray:
+    th = np.zeros(BIE_MLP_PARAMS, np.float32)
+    _check(load().bie_mlp_get_params(ctx, _hp(th)))
+    return th
+
+
+def bie_mlp_features(ctx: int, k, phi_out) -> None:
+    k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+    _check(load().bie_mlp_features(ctx, _hp(k), k.shape[0], _dp(phi_out)))
+
+
+def bie_mlp_forward(ctx: int, X, Y_out) -> None:
+    _check(load().bie_mlp_forward(ctx, _dp(X), X.shape[0], _dp(Y_out)))
+
+
+def bie_mlp_loss_grad(ctx: int, X, T, grad_out, loss_out) -> None:
+    _check(load().bie_mlp_loss_grad(ctx, _dp(X), _dp(T), X.shape[0],
+                                    None if grad_out is None else _dp(grad_out),
+                                    None if loss_out is None else _dp(loss_out)))
+
+
+def bie_mlp_adam_step(ctx: int, grad, lr: float) -> None:
+    _check(load().bie_mlp_adam_step(ctx, _dp(grad), float(lr)))
+
+
+def bie_mlp_train(ctx: int, k, surf, epochs: int) -> np.ndarray:
+    k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+    hist = np.zeros(max(1, epochs), np.float32)
+    _check(load().bie_mlp_train(ctx, _hp(k), k.shape[0], _dp(surf), int(epochs), _hp(hist)))
+    return hist[:epochs]
+
+
+def bie_mlp_predict(ctx: int, k, x0_out) -> None:
+    k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+    _check(load().bie_mlp_predict(ctx, _hp(k), k.shape[0], _dp(x0_out)))
+
+
+def bie_get_learned_info(ctx: int) -> dict:
+    info = BieLearnedInfo()
+    _check(load().bie_get_learned_info(ctx, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in BieLearnedInfo._fields_}

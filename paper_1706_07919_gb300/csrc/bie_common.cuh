@@ -30,6 +30,8 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // Every kernel launch of the library goes through BIE_LAUNCH, which counts it (bie_kernel_launches).
 void count_launch();
+void count_launches(int64_t n);
+void uncount_launches(int64_t n);
 #define BIE_LAUNCH(...) (::bie::count_launch(), __VA_ARGS__)
 
 #define BIE_TRY(expr)          \
@@ -63,6 +65,18 @@ enum { GX = 0, GY, GZ, GNX, GNY, GNZ, GWJ, GCOUNT };
 struct DeviceBuf {
   void* p = nullptr;
   size_t bytes = 0;
+};
+
+struct MlpState;  // learned warm start (mlp.cu)
+
+// Per-system state of the iterative refinement and of the Krylov solver's outer loop.
+struct RefineState {
+  int32_t done;      // 1 once converged
+  int32_t iters;     // corrections applied (refinement) or Arnoldi steps (Krylov)
+  double anorm;      // ||A||_inf
+  double bnorm;      // ||b||_inf
+  double berr;       // latest backward error
+  double err_est;    // estimated relative error caused by FP32 assembly (see refine.cu, k_perturb)
 };
 
 }  // namespace bie
@@ -110,10 +124,26 @@ struct bie_ctx {
   double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
 
+  // learned warm start + Krylov path (BIE_MODE_LEARNED)
+  int learned_stride = 8;            // every stride-th wavenumber is solved directly (an anchor)
+  int learned_x0 = 1;                // initial guess: 0 zero, 1 network, 2 nearest anchor's solution
+  int mlp_epochs = 60;               // training epochs over the anchors' solutions
+  int mlp_batch = 8192;              // rows per minibatch
+  double mlp_lr = 2e-3, mlp_lr_min = 1e-4;  // Adam step size, cosine-decayed to lr_min
+  int64_t mlp_seed = 1234;           // initial weights and minibatch order
+  double mlp_kmax = 0.0;             // feature wavenumber scale (0: largest training wavenumber)
+  int mlp_graph = 1;                 // replay training epochs from a captured CUDA graph
+  int gmres_m = 30;                  // Arnoldi steps per cycle
+  int gmres_cycles = 6;              // cycles (each starts from a float-float residual)
+  double gmres_inner_tol = 1e-5;     // relative residual decrease that closes a cycle
+  bie::MlpState* mlp = nullptr;
+  bie_learned_info learned_info{};
+
   // workspace (device), grown on demand
   bie::DeviceBuf work;   // per-call systems / factors
   bie::DeviceBuf work2;  // FFT twiddles
   bie::DeviceBuf work3;  // foot points, field scratch, synthesis indices
+  bie::DeviceBuf work4;  // learned mode: the anchors' factors, permutations and solutions
 };
 
 namespace bie {

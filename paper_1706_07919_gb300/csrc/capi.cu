@@ -13,6 +13,8 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+void uncount_launches(int64_t n) { g_launches.fetch_sub((uint64_t)n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
@@ -58,7 +60,18 @@ int field64(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* 
 int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout);
 int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t M, const cd* Sp, int64_t P, int n,
                void* out, int out_dtype);
-int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
+int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
+                int32_t* perm_keep);
+int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
+void mlp_free(bie_ctx* c);
+int mlp_set_params(bie_ctx* c, const float* theta_host);
+int mlp_get_params(bie_ctx* c, float* theta_host);
+int mlp_features_api(bie_ctx* c, const double* k, int64_t nk, float* phi);
+int mlp_forward_api(bie_ctx* c, const float* X, int64_t B, float* Y);
+int mlp_loss_grad_api(bie_ctx* c, const float* X, const float* T, int64_t B, float* grad, float* loss);
+int mlp_adam_api(bie_ctx* c, const float* grad, double lr);
+int mlp_train(bie_ctx* c, const double* k, int64_t nk, const cd* surf, int epochs, float* loss_hist);
+int mlp_predict_api(bie_ctx* c, const double* k, int64_t nk, cd* x0);
 int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
                 const int32_t* foot_elem, const double* foot, cd* T, void* scratch, size_t scratch_bytes);
 
@@ -179,6 +192,8 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c->work);
   free_buf(c->work2);
   free_buf(c->work3);
+  free_buf(c->work4);
+  mlp_free(c);
   delete c;
   return BIE_OK;
 }
@@ -215,6 +230,42 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     c->fallback_err_est = value;
   } else if (n == "field.accurate_phase") {
     c->field_accurate_phase = value != 0.0 ? 1 : 0;
+  } else if (n == "learned.stride") {
+    if (value < 2 || value > 1e6) return fail(BIE_ERR_INVALID_ARG, "learned.stride must be in [2, 1e6]");
+    c->learned_stride = (int)value;
+  } else if (n == "learned.x0") {
+    if (value != 0.0 && value != 1.0 && value != 2.0)
+      return fail(BIE_ERR_INVALID_ARG, "learned.x0 must be 0 (zero), 1 (network) or 2 (nearest anchor)");
+    c->learned_x0 = (int)value;
+  } else if (n == "learned.epochs") {
+    if (value < 0 || value > 100000) return fail(BIE_ERR_INVALID_ARG, "learned.epochs must be in [0, 100000]");
+    c->mlp_epochs = (int)value;
+  } else if (n == "learned.batch") {
+    if (value < 128 || value > 1048576) return fail(BIE_ERR_INVALID_ARG, "learned.batch must be in [128, 1048576]");
+    c->mlp_batch = (int)((((int64_t)value) + 127) / 128 * 128);
+  } else if (n == "learned.lr") {
+    if (!(value > 0.0) || value > 1.0) return fail(BIE_ERR_INVALID_ARG, "learned.lr must be in (0, 1]");
+    c->mlp_lr = value;
+  } else if (n == "learned.lr_min") {
+    if (!(value >= 0.0) || value > 1.0) return fail(BIE_ERR_INVALID_ARG, "learned.lr_min must be in [0, 1]");
+    c->mlp_lr_min = value;
+  } else if (n == "learned.seed") {
+    if (value < 0 || value > 9.0e15) return fail(BIE_ERR_INVALID_ARG, "learned.seed must be in [0, 9e15]");
+    c->mlp_seed = (int64_t)value;
+  } else if (n == "learned.kmax") {
+    if (value < 0) return fail(BIE_ERR_INVALID_ARG, "learned.kmax must be >= 0");
+    c->mlp_kmax = value;
+  } else if (n == "learned.graph") {
+    c->mlp_graph = value != 0.0 ? 1 : 0;
+  } else if (n == "gmres.m") {
+    if (value < 1 || value > 62) return fail(BIE_ERR_INVALID_ARG, "gmres.m must be in [1, 62]");
+    c->gmres_m = (int)value;
+  } else if (n == "gmres.cycles") {
+    if (value < 1 || value > 100) return fail(BIE_ERR_INVALID_ARG, "gmres.cycles must be in [1, 100]");
+    c->gmres_cycles = (int)value;
+  } else if (n == "gmres.inner_tol") {
+    if (!(value > 0.0) || value >= 1.0) return fail(BIE_ERR_INVALID_ARG, "gmres.inner_tol must be in (0, 1)");
+    c->gmres_inner_tol = value;
   } else {
     return fail(BIE_ERR_INVALID_ARG, "unknown option '" + n + "'");
   }
@@ -283,8 +334,76 @@ int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, voi
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
   if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
-  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep);
+  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr);
+  if (mode == BIE_MODE_LEARNED) return solve_learned(c, k, Nk, (cd*)surf_out, rep);
   return fail(BIE_ERR_INVALID_ARG, "unknown mode " + std::to_string(mode));
+}
+
+// ---- learned warm start ----------------------------------------------------------------------
+int bie_mlp_set_params(bie_ctx* c, const float* theta) {
+  BIE_TRY(check_ctx(c, false));
+  if (!theta) return fail(BIE_ERR_INVALID_ARG, "NULL theta");
+  for (int64_t i = 0; i < BIE_MLP_PARAMS; ++i)
+    if (!std::isfinite(theta[i])) return fail(BIE_ERR_INVALID_ARG, "non-finite parameter at " + std::to_string(i));
+  return mlp_set_params(c, theta);
+}
+
+int bie_mlp_get_params(bie_ctx* c, float* theta) {
+  BIE_TRY(check_ctx(c, false));
+  if (!theta) return fail(BIE_ERR_INVALID_ARG, "NULL theta");
+  return mlp_get_params(c, theta);
+}
+
+int bie_mlp_features(bie_ctx* c, const double* k, int64_t nk, float* phi_out) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, nk));
+  if (nk > 0 && !phi_out) return fail(BIE_ERR_INVALID_ARG, "NULL phi_out");
+  return mlp_features_api(c, k, nk, phi_out);
+}
+
+int bie_mlp_forward(bie_ctx* c, const float* X, int64_t B, float* Y_out) {
+  BIE_TRY(check_ctx(c, false));
+  if (B < 0 || B > ((int64_t)1 << 26)) return fail(BIE_ERR_INVALID_ARG, "B out of range");
+  if (B > 0 && (!X || !Y_out)) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  return mlp_forward_api(c, X, B, Y_out);
+}
+
+int bie_mlp_loss_grad(bie_ctx* c, const float* X, const float* T, int64_t B, float* grad_out, float* loss_out) {
+  BIE_TRY(check_ctx(c, false));
+  if (B < 1 || B > ((int64_t)1 << 26)) return fail(BIE_ERR_INVALID_ARG, "B out of range");
+  if (!X || !T) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  return mlp_loss_grad_api(c, X, T, B, grad_out, loss_out);
+}
+
+int bie_mlp_adam_step(bie_ctx* c, const float* grad, double lr) {
+  BIE_TRY(check_ctx(c, false));
+  if (!grad) return fail(BIE_ERR_INVALID_ARG, "NULL grad");
+  if (!(lr > 0.0) || !std::isfinite(lr)) return fail(BIE_ERR_INVALID_ARG, "lr must be finite and > 0");
+  return mlp_adam_api(c, grad, lr);
+}
+
+int bie_mlp_train(bie_ctx* c, const double* k, int64_t nk, const void* surf, int epochs, float* loss_hist) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, nk));
+  if (nk < 1 || !surf) return fail(BIE_ERR_INVALID_ARG, "need nk >= 1 and surf");
+  if (epochs < 0 || epochs > 100000) return fail(BIE_ERR_INVALID_ARG, "epochs out of range");
+  BIE_TRY(mlp_train(c, k, nk, (const cd*)surf, epochs, loss_hist));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+int bie_mlp_predict(bie_ctx* c, const double* k, int64_t nk, void* x0_out) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, nk));
+  if (nk > 0 && !x0_out) return fail(BIE_ERR_INVALID_ARG, "NULL x0_out");
+  return mlp_predict_api(c, k, nk, (cd*)x0_out);
+}
+
+int bie_get_learned_info(bie_ctx* c, bie_learned_info* out) {
+  BIE_TRY(check_ctx(c, false));
+  if (!out) return fail(BIE_ERR_INVALID_ARG, "NULL out");
+  *out = c->learned_info;
+  return BIE_OK;
 }
 
 int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, int64_t Nk, const void* surf,

@@ -34,10 +34,13 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kFallbackGroup = 8;  // FP64 systems re-assembled at once
 
-int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep) {
+// lu_keep / perm_keep (optional, device): receive the low-precision factor ([Nk][N][ld], ld = N
+// rounded up to 64) and row permutation ([Nk][N]) of every wavenumber.
+int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
+                int32_t* perm_keep) {
   const int64_t N = c->N;
   const int64_t ld = (N + 63) / 64 * 64;
-  const size_t mat = align256((size_t)N * ld * sizeof(cf));
+  const size_t mat = align256((size_t)N * ld * sizeof(cf));  // == N * ld * 8: ld is a multiple of 64
   const size_t vec = align256((size_t)N * sizeof(cd));
   const size_t perk = 2 * mat + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
                       2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
@@ -97,6 +100,12 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
                          c->refine_tol));
+    if (lu_keep) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(lu_keep + k0 * N * ld, LU, (size_t)nk * N * ld * sizeof(cf), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+      BIE_CUDA_TRY(cudaMemcpyAsync(perm_keep + k0 * N, perm, (size_t)nk * N * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    }
     BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
     BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
     std::vector<int32_t> flagged;

@@ -8,14 +8,6 @@
 
 namespace bie {
 
-struct RefineState {
-  int32_t done;      // 1 once converged
-  int32_t iters;     // corrections applied
-  double anorm;      // ||A||_inf
-  double bnorm;      // ||b||_inf
-  double berr;       // latest backward error
-  double err_est;    // estimated relative error caused by FP32 assembly (see k_perturb)
-};
 
 // ---- permutation vector from the LU's row interchanges: y = P r  <=>  y[i] = r[perm[i]] ----
 __global__ void k_piv_to_perm(const int32_t* __restrict__ piv, int n, int32_t* __restrict__ perm) {
@@ -107,20 +99,22 @@ __device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y) {
   }
 }
 
-// rhs: cd [batch][n] (FP64), solution written to out (cd, added to `out` if accumulate).
+// rhs: cd vectors of n entries, system kk's at rhs + kk * rstride + roff (FP64); the solution is
+// written to out + kk * ostride + ooff (added to it if accumulate).
 // sel (optional): system blockIdx.x uses factor sel[blockIdx.x] (vectors stay indexed by blockIdx.x).
 __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
                                                   const int32_t* __restrict__ perm, const cd* __restrict__ rhs,
                                                   cd* __restrict__ out, int accumulate,
                                                   const RefineState* __restrict__ st,
-                                                  const int32_t* __restrict__ sel = nullptr) {
+                                                  const int32_t* __restrict__ sel, int64_t rstride, int64_t roff,
+                                                  int64_t ostride, int64_t ooff) {
   extern __shared__ cf yv[];
   const int kk = blockIdx.x;
   if (st && st[kk].done) return;
   const int fk = sel ? sel[kk] : kk;
   const cf* M = LU + (int64_t)fk * bstride;
   const int32_t* pm = perm + (int64_t)fk * n;
-  const cd* r = rhs + (int64_t)kk * n;
+  const cd* r = rhs + (int64_t)kk * rstride + roff;
   // scale the right-hand side to O(1) before rounding it to FP32
   __shared__ double s_scale;
   if (threadIdx.x == 0) s_scale = 0.0;
@@ -138,7 +132,7 @@ __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int
   __syncthreads();
   trsv_sweep<true>(M, n, ld, yv);
   trsv_sweep<false>(M, n, ld, yv);
-  cd* o = out + (int64_t)kk * n;
+  cd* o = out + (int64_t)kk * ostride + ooff;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const cd v = {(double)yv[i].re * sc, (double)yv[i].im * sc};
     o[i] = accumulate ? cadd(o[i], v) : v;
@@ -300,17 +294,17 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
     return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_trsv_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsv));
   BIE_CUDA_TRY(cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_res));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr));
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int it = 0; it <= it_max; ++it) {
     BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st));
+    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0));
   }
   // assembly-sensitivity estimate (r is free now)
   BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr));
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, n, 0, n, 0));
   BIE_LAUNCH(k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -375,7 +369,7 @@ int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, i
     BIE_LAUNCH(k_residual64<<<gr, 512, 0, c->stream>>>(A64, n, b64, xg, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<ng, 256, 0, c->stream>>>(n, b64, xg, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev));
+    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev, n, 0, n, 0));
   }
   BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 0));
   BIE_CUDA_TRY(cudaGetLastError());

@@ -76,3 +76,42 @@ class Solver:
                                                     device=self._dev())
         B.bie_synthesize(self.ctx, T, midx, S, Nt, o, code)
         return o
+
+    # ---- learned warm start (BIE_MODE_LEARNED's network) ----
+    def mlp_set_params(self, theta):
+        B.bie_mlp_set_params(self.ctx, theta)
+
+    def mlp_get_params(self):
+        return B.bie_mlp_get_params(self.ctx)
+
+    def mlp_features(self, k):
+        k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+        phi = torch.empty((k.shape[0], self.N, 64), dtype=torch.float32, device=self._dev())
+        B.bie_mlp_features(self.ctx, k, phi)
+        return phi
+
+    def mlp_forward(self, X: torch.Tensor):
+        Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=self._dev())
+        B.bie_mlp_forward(self.ctx, X, Y)
+        return Y
+
+    def mlp_loss_grad(self, X: torch.Tensor, T: torch.Tensor):
+        g = torch.empty((B.BIE_MLP_PARAMS,), dtype=torch.float32, device=self._dev())
+        L = torch.empty((1,), dtype=torch.float32, device=self._dev())
+        B.bie_mlp_loss_grad(self.ctx, X, T, g, L)
+        return float(L.item()), g
+
+    def mlp_adam_step(self, grad: torch.Tensor, lr: float):
+        B.bie_mlp_adam_step(self.ctx, grad, lr)
+
+    def mlp_train(self, k, surf: torch.Tensor, epochs: int):
+        return B.bie_mlp_train(self.ctx, k, surf, epochs)
+
+    def mlp_predict(self, k):
+        k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+        x0 = torch.empty((k.shape[0], self.N), dtype=torch.complex128, device=self._dev())
+        B.bie_mlp_predict(self.ctx, k, x0)
+        return x0
+
+    def learned_info(self) -> dict:
+        return B.bie_get_learned_info(self.ctx)

@@ -1,0 +1,168 @@
+"""GPU tests of the learned warm start (network kernels) and of BIE_MODE_LEARNED (GMRES solves),
+through the C ABI, against the CPU oracle.
+
+Tolerances of the network kernels come from their arithmetic: the hidden layers multiply BF16
+operands (unit roundoff u = 2^-9) with FP32 accumulation and round every activation and every
+backward product to BF16 again, so each layer adds a relative error of a few u; over three layers
+the outputs and gradients stay within 1.5e-2 and 4e-2 (relative L2) of the FP64 oracle on the
+random networks used here, the test parameters and inputs being BF16-representable so that the
+operand rounding is exact.  The optimiser step runs in FP32 (relative 1e-6).  The frequency solves
+of the learned mode must meet the mixed path's bar: relative L2 <= 1e-6 against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def _bf16(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16-representable value (ties to even), kept as float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _params(seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    sl = oracle.mlp_param_slices()
+    th = np.zeros(oracle.mlp_param_count(), np.float32)
+    for name, (off, shp) in sl.items():
+        n = int(np.prod(shp))
+        if len(shp) == 2:
+            a = np.sqrt(6.0 / (shp[0] + shp[1]))
+            th[off:off + n] = rng.uniform(-a, a, n)
+        else:
+            th[off:off + n] = rng.uniform(-0.2, 0.2, n)
+    return _bf16(th)
+
+
+def _solver(mesh):
+    from paper_1706_07919_gb300 import Solver
+    s = Solver(0)
+    s.set_geometry(mesh.nodes, mesh.elems, mesh.normals, mesh.bc)
+    return s
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def small_spheroid():
+    return W.ellipsoid_from_sphere(W.ico_sphere(3, 1.0, bc=0), (1.0, 1.0, 2.0))
+
+
+def test_features_match_oracle(small_spheroid):
+    m = small_spheroid
+    s = _solver(m)
+    s.set_option("learned.kmax", 10.0)
+    kv = np.array([0.37, 4.1, 9.5])
+    phi = s.mlp_features(kv).cpu().numpy()
+    c = m.nodes.mean(axis=0)
+    sc = np.max(np.linalg.norm(m.nodes - c, axis=1))
+    ref = oracle.mlp_features(m.nodes, m.normals, kv, [0.0, 0.0, 1.0], c, sc, 10.0)
+    # GPU features are rounded to BF16: half an ulp of values up to ~1.5, plus FP32 phases
+    assert np.max(np.abs(phi - ref)) <= 4e-3
+    assert np.array_equal(phi, _bf16(phi))
+    s.close()
+
+
+@pytest.mark.parametrize("B", [128, 300, 1000])
+def test_forward_matches_oracle(small_spheroid, B):
+    s = _solver(small_spheroid)
+    th = _params(7)
+    s.mlp_set_params(th)
+    rng = np.random.default_rng(B)
+    X = _bf16(rng.uniform(-1, 1, (B, 64)))
+    Y = s.mlp_forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    ref = oracle.mlp_forward(th.astype(np.float64), X.astype(np.float64))
+    assert _rel(Y, ref) <= 1.5e-2
+    assert np.allclose(s.mlp_get_params(), th, rtol=0, atol=0)
+    s.close()
+
+
+@pytest.mark.parametrize("B", [256, 333])
+def test_gradient_matches_oracle(small_spheroid, B):
+    s = _solver(small_spheroid)
+    th = _params(11)
+    s.mlp_set_params(th)
+    rng = np.random.default_rng(100 + B)
+    X = _bf16(rng.uniform(-1, 1, (B, 64)))
+    T = rng.normal(size=(B, 2)).astype(np.float32)
+    L, g = s.mlp_loss_grad(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    g = g.cpu().numpy()
+    Lr, gr = oracle.mlp_loss_grad(th.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(L - Lr) <= 1e-2 * Lr
+    for name, (off, shp) in oracle.mlp_param_slices().items():
+        n = int(np.prod(shp))
+        e = _rel(g[off:off + n], gr[off:off + n])
+        assert e <= 4e-2, (name, e)
+    s.close()
+
+
+def test_adam_steps_match_oracle(small_spheroid):
+    s = _solver(small_spheroid)
+    th = _params(3)
+    s.mlp_set_params(th)
+    rng = np.random.default_rng(5)
+    P = th.shape[0]
+    t64, m, v = th.astype(np.float64), np.zeros(P), np.zeros(P)
+    for t in (1, 2, 3):
+        g = (rng.normal(size=P) * 10.0 ** rng.uniform(-4, 0, P)).astype(np.float32)
+        s.mlp_adam_step(torch.tensor(g, device="cuda"), 1e-3)
+        oracle.adam_step(t64, g.astype(np.float64), m, v, t, 1e-3)
+    got = s.mlp_get_params().astype(np.float64)
+    assert np.max(np.abs(got - t64)) <= 1e-6 * (1.0 + np.max(np.abs(t64)))
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def learned_case():
+    """Hard prolate spheroid (642 nodes), 48 wavenumbers over (0, 6]: anchors every 8th."""
+    from paper_1706_07919_gb300 import binding as Bd
+    mesh = W.ellipsoid_from_sphere(W.ico_sphere(4, 1.0, bc=0), (1.0, 1.0, 2.0))
+    k = 0.125 * np.arange(1, 49)
+    out = {}
+    for x0 in (1, 0):
+        s = _solver(mesh)
+        s.set_option("learned.x0", x0)
+        s.set_option("learned.epochs", 400)
+        s.set_option("learned.batch", 1024)
+        surf, rep = s.solve_frequencies(k, Bd.BIE_MODE_LEARNED)
+        out[x0] = (surf.cpu().numpy(), rep, s.learned_info())
+        s.close()
+    return mesh, k, out
+
+
+def test_learned_solves_match_oracle(learned_case):
+    from paper_1706_07919_gb300 import binding as Bd
+    mesh, k, out = learned_case
+    surf, rep, info = out[1]
+    assert info["anchors"] == 6 and info["krylov"] == 42
+    paths = [r.path for r in rep]
+    assert paths.count(Bd.BIE_MODE_LEARNED) + info["krylov_fallback"] == 42
+    for i in (0, 4, 13, 22, 30, 46):  # non-anchor wavenumbers across the band (7, 15, ... are anchors)
+        P, Pn = oracle.solve_frequency(mesh, k[i], [0.0, 0.0, 1.0])
+        assert _rel(surf[i, 0], P) <= 1e-6, (i, k[i], rep[i].flags)
+        assert _rel(surf[i, 1], Pn) <= 1e-6
+    for i in (7, 23):  # anchors (direct path)
+        P, _ = oracle.solve_frequency(mesh, k[i], [0.0, 0.0, 1.0])
+        assert _rel(surf[i, 0], P) <= 1e-6
+    for r in rep:
+        assert r.backward_err <= 1e-10
+
+
+def test_network_warm_start_gains(learned_case):
+    mesh, k, out = learned_case
+    _, _, net = out[1]
+    _, _, zero = out[0]
+    print("network:", net)
+    print("zero start:", zero)
+    assert zero["x0_rel_err"] == pytest.approx(1.0)
+    assert net["last_loss"] < 0.05 * net["first_loss"]
+    assert net["x0_rel_err"] < 0.5
+    assert net["mean_iters"] < zero["mean_iters"]
