@@ -96,6 +96,24 @@ typedef struct {
   double mean_iters;       /* mean Arnoldi steps per GMRES-solved wavenumber */
 } bie_learned_info;
 
+/* Result of bie_autotune. */
+typedef struct {
+  int32_t n_bucket;    /* N rounded up to a multiple of 64: the cache key */
+  int32_t batch;       /* wavenumbers per batch chosen ("mixed.batch") */
+  int32_t tcgen05;     /* trailing-update kernel chosen ("mixed.tcgen05") */
+  int32_t from_cache;  /* 1: read from the cache file, 0: measured now */
+  double us_per_k;     /* measured time per wavenumber of the chosen setting */
+} bie_tune_result;
+
+/* Statistics of bie_sched_run. */
+typedef struct {
+  int32_t jobs, workers;
+  double wall_ms;  /* wall time of the whole run */
+  double busy_ms;  /* sum over workers of the time spent inside jobs */
+} bie_sched_stats;
+
+typedef struct bie_sched bie_sched;
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* bie_last_error(void);
 
@@ -149,6 +167,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
+ *   "mixed.graph"          1: replay the device work of full batches from a captured CUDA graph
+ *                          (default), 0: launch every kernel directly
  * Learned warm start and Krylov solve (BIE_MODE_LEARNED):
  *   "learned.stride"       every stride-th wavenumber of the call is an anchor (>= 2, default 8;
  *                          indices stride-1, 2 stride-1, ...; the last index if none)
@@ -226,6 +246,35 @@ int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk,
  * calls whose work overlaps on the GPU (different streams or threads) race. */
 int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
                            int64_t P, int64_t Nt, void* out, int out_dtype, void* stream);
+
+/* Autotuner of the mixed path (not part of the paper's method, which fixes no launch parameters):
+ * for the context's geometry, times one batch of BIE_MODE_MIXED solves (sample wavenumbers
+ * k host f64 [nk], repeated to fill the batch) for every candidate of "mixed.batch" in
+ * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {2, 0},
+ * and sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
+ * file keyed by N rounded up to 64; an entry for this N is applied without measuring, a new
+ * measurement is added to it.  out (host, optional) receives the choice.  Synchronises.
+ * Errors: STATE without geometry, OOM if no candidate fits, INVALID_ARG if the cache cannot be
+ * written. */
+int bie_autotune(bie_ctx* ctx, const double* k, int64_t nk, const char* cache_path, bie_tune_result* out);
+
+/* Scheduler of many independent jobs (scatterer configurations, each with its own mesh and
+ * wavenumber list) on one GPU: jobs run largest-first on `workers` threads, each with its own
+ * context and CUDA stream, so that small configurations overlap large ones.  tune_cache (host
+ * string or NULL): autotuner cache applied to every job's N bucket (measured on first use).
+ * Not part of the paper's method.  Errors: INVALID_ARG (device, workers outside [1, 64]). */
+int bie_sched_create(bie_sched** out, int cuda_device, int workers, const char* tune_cache);
+int bie_sched_destroy(bie_sched* sched);
+/* Queues a job.  Mesh arguments as bie_set_geometry (copied now), dir as
+ * bie_set_incident_plane_wave (NULL: +z), k host f64 [Nk] (copied), mode and outputs as
+ * bie_solve_frequencies: surf_out device c128 [Nk][2][N] and rep host [Nk] (or NULL), both
+ * written during bie_sched_run.  job_id (optional) receives the job's index. */
+int bie_sched_add(bie_sched* sched, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                  const double* normals, const uint8_t* bc, const double* dir, const double* k, int64_t Nk,
+                  int mode, void* surf_out, bie_report* rep, int32_t* job_id);
+/* Runs every queued job and returns when all are done (the queue is then empty).  stats (host,
+ * optional).  Errors: the first failing job's code, with its message. */
+int bie_sched_run(bie_sched* sched, bie_sched_stats* stats);
 
 /* ---- learned warm start (BIE_MODE_LEARNED's network; not part of the paper's method) ---------
  * Feature map of node x (normal nu) at wavenumber k, 64 values: (x - c)/s, nu, k/kmax, (k/kmax)^2,

@@ -37,7 +37,8 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",
             "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc", "bie_mlp_set_params",
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
-            "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info"]
+            "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
+            "bie_sched_destroy", "bie_sched_add", "bie_sched_run"]
 
 
 class BieReport(ctypes.Structure):
@@ -49,6 +50,16 @@ class BieLearnedInfo(ctypes.Structure):
     _fields_ = [("anchors", ctypes.c_int32), ("krylov", ctypes.c_int32), ("krylov_fallback", ctypes.c_int32),
                 ("epochs", ctypes.c_int32), ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float),
                 ("train_ms", ctypes.c_double), ("x0_rel_err", ctypes.c_double), ("mean_iters", ctypes.c_double)]
+
+
+class BieTuneResult(ctypes.Structure):
+    _fields_ = [("n_bucket", ctypes.c_int32), ("batch", ctypes.c_int32), ("tcgen05", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("us_per_k", ctypes.c_double)]
+
+
+class BieSchedStats(ctypes.Structure):
+    _fields_ = [("jobs", ctypes.c_int32), ("workers", ctypes.c_int32), ("wall_ms", ctypes.c_double),
+                ("busy_ms", ctypes.c_double)]
 
 
 class BieError(RuntimeError):
@@ -95,6 +106,11 @@ def load(path: str | None = None):
         "bie_mlp_train": ([vp, vp, i64, vp, i32, vp], i32),
         "bie_mlp_predict": ([vp, vp, i64, vp], i32),
         "bie_get_learned_info": ([vp, vp], i32),
+        "bie_autotune": ([vp, vp, i64, ctypes.c_char_p, vp], i32),
+        "bie_sched_create": ([ctypes.POINTER(vp), i32, i32, ctypes.c_char_p], i32),
+        "bie_sched_destroy": ([vp], i32),
+        "bie_sched_add": ([vp, vp, i64, vp, i64, vp, vp, vp, vp, i64, i32, vp, vp, vp], i32),
+        "bie_sched_run": ([vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -247,3 +263,56 @@ def bie_get_learned_info(ctx: int) -> dict:
     info = BieLearnedInfo()
     _check(load().bie_get_learned_info(ctx, ctypes.byref(info)))
     return {name: getattr(info, name) for name, _ in BieLearnedInfo._fields_}
+
+
+# ---- autotuner and scheduler ------------------------------------------------------------------
+def bie_autotune(ctx: int, k, cache_path: str | None = None) -> dict:
+    k = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+    r = BieTuneResult()
+    _check(load().bie_autotune(ctx, _hp(k), k.shape[0], None if cache_path is None else cache_path.encode(),
+                               ctypes.byref(r)))
+    return {name: getattr(r, name) for name, _ in BieTuneResult._fields_}
+
+
+def bie_sched_create(device: int = 0, workers: int = 4, tune_cache: str | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().bie_sched_create(ctypes.byref(h), device, workers,
+                                   None if tune_cache is None else tune_cache.encode()))
+    return h.value
+
+
+def bie_sched_destroy(sched: int) -> None:
+    _check(load().bie_sched_destroy(sched))
+
+
+class SchedJob:
+    """Host arrays kept alive until bie_sched_run has consumed them; reports are read back here."""
+
+    def __init__(self, k):
+        self.k = np.ascontiguousarray(k, np.float64)
+        self.rep = (BieReport * max(1, self.k.shape[0]))()
+
+    def reports(self):
+        return list(self.rep)[: self.k.shape[0]]
+
+
+def bie_sched_add(sched: int, nodes, elems, normals, bc, direction, k, mode: int, surf_out) -> SchedJob:
+    nodes = np.ascontiguousarray(nodes, np.float64)
+    elems = np.ascontiguousarray(elems, np.int32)
+    bc = np.ascontiguousarray(bc, np.uint8)
+    nrm = None if normals is None else np.ascontiguousarray(normals, np.float64)
+    d = None if direction is None else np.ascontiguousarray(direction, np.float64)
+    job = SchedJob(k)
+    jid = ctypes.c_int32()
+    _check(load().bie_sched_add(sched, _hp(nodes), nodes.shape[0], _hp(elems), elems.shape[0],
+                                None if nrm is None else _hp(nrm), _hp(bc), None if d is None else _hp(d),
+                                _hp(job.k), job.k.shape[0], mode, _dp(surf_out),
+                                ctypes.cast(job.rep, ctypes.c_void_p), ctypes.byref(jid)))
+    job.id = jid.value
+    return job
+
+
+def bie_sched_run(sched: int) -> dict:
+    st = BieSchedStats()
+    _check(load().bie_sched_run(sched, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in BieSchedStats._fields_}

@@ -123,6 +123,9 @@ struct bie_ctx {
   double refine_tol = 1e-11;         // backward-error target of the refinement
   double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
+  int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
+  void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
+  size_t pinned_bytes = 0;
 
   // learned warm start + Krylov path (BIE_MODE_LEARNED)
   int learned_stride = 8;            // every stride-th wavenumber is solved directly (an anchor)
@@ -149,6 +152,7 @@ struct bie_ctx {
 namespace bie {
 
 int ensure_buf(DeviceBuf& b, size_t bytes);
+int ensure_pinned(bie_ctx* c, size_t bytes);
 void free_buf(DeviceBuf& b);
 
 // ------------------------------------------------------------------------------------------

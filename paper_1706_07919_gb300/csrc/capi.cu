@@ -39,6 +39,19 @@ int ensure_buf(DeviceBuf& b, size_t bytes) {
   b.bytes = bytes;
   return BIE_OK;
 }
+int ensure_pinned(bie_ctx* c, size_t bytes) {
+  if (c->pinned_bytes >= bytes) return BIE_OK;
+  if (c->pinned) {
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    c->pinned_bytes = 0;
+  }
+  BIE_CUDA_TRY(cudaMallocHost(&c->pinned, bytes));
+  c->pinned_bytes = bytes;
+  return BIE_OK;
+}
+
 void free_buf(DeviceBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -72,6 +85,7 @@ int mlp_loss_grad_api(bie_ctx* c, const float* X, const float* T, int64_t B, flo
 int mlp_adam_api(bie_ctx* c, const float* grad, double lr);
 int mlp_train(bie_ctx* c, const double* k, int64_t nk, const cd* surf, int epochs, float* loss_hist);
 int mlp_predict_api(bie_ctx* c, const double* k, int64_t nk, cd* x0);
+int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bie_tune_result* out);
 int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
                 const int32_t* foot_elem, const double* foot, cd* T, void* scratch, size_t scratch_bytes);
 
@@ -194,6 +208,7 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c->work3);
   free_buf(c->work4);
   mlp_free(c);
+  if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
   return BIE_OK;
 }
@@ -230,6 +245,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     c->fallback_err_est = value;
   } else if (n == "field.accurate_phase") {
     c->field_accurate_phase = value != 0.0 ? 1 : 0;
+  } else if (n == "mixed.graph") {
+    c->mixed_graph = value != 0.0 ? 1 : 0;
   } else if (n == "learned.stride") {
     if (value < 2 || value > 1e6) return fail(BIE_ERR_INVALID_ARG, "learned.stride must be in [2, 1e6]");
     c->learned_stride = (int)value;
@@ -397,6 +414,12 @@ int bie_mlp_predict(bie_ctx* c, const double* k, int64_t nk, void* x0_out) {
   BIE_TRY(check_k(k, nk));
   if (nk > 0 && !x0_out) return fail(BIE_ERR_INVALID_ARG, "NULL x0_out");
   return mlp_predict_api(c, k, nk, (cd*)x0_out);
+}
+
+int bie_autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bie_tune_result* out) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, nk));
+  return autotune(c, k, nk, cache_path, out);
 }
 
 int bie_get_learned_info(bie_ctx* c, bie_learned_info* out) {

@@ -88,9 +88,11 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   std::vector<double> gb(G), ge(G);
   std::vector<double> full64;
   std::vector<int64_t> full64_idx;
-  for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
-    const int nk = (int)std::min<int64_t>(kb, Nk - k0);
-    BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // The device part of a batch (assembly, factorisation, refinement) is stream-ordered and needs
+  // no host decision, so full batches after the first are captured once in a CUDA graph and
+  // replayed; the wavenumbers reach the graph through a pinned host buffer.
+  auto batch_core = [&](const double* ksrc, int nk) -> int {
+    BIE_CUDA_TRY(cudaMemcpyAsync(kdev, ksrc, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
     BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum));
     BIE_CUDA_TRY(cudaMemcpyAsync(LU, A, (size_t)nk * mat, cudaMemcpyDeviceToDevice, c->stream));
@@ -100,6 +102,54 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
                          c->refine_tol));
+    return BIE_OK;
+  };
+  bool use_graph = c->mixed_graph && Nk >= 2 * kb;
+  double* kpin = nullptr;
+  if (use_graph) {
+    BIE_TRY(ensure_pinned(c, (size_t)kb * sizeof(double)));
+    kpin = (double*)c->pinned;
+  }
+  cudaGraphExec_t gexec = nullptr;
+  int64_t gnodes = 0;
+  struct ExecGuard {
+    cudaGraphExec_t* e;
+    ~ExecGuard() { if (*e) cudaGraphExecDestroy(*e); }
+  } guard{&gexec};
+  for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
+    const int nk = (int)std::min<int64_t>(kb, Nk - k0);
+    if (use_graph && k0 > 0 && nk == kb) {
+      std::copy(k + k0, k + k0 + nk, kpin);  // the previous batch has completed (its state was read)
+      if (!gexec) {
+        const int64_t before = (int64_t)bie_kernel_launches();
+        cudaGraph_t graph = nullptr;
+        int rc = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess ? BIE_OK : BIE_ERR_CUDA;
+        if (rc == BIE_OK) {
+          rc = batch_core(kpin, nk);
+          const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+          if (rc == BIE_OK && ce == cudaSuccess && graph)
+            rc = cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess ? BIE_OK : BIE_ERR_CUDA;
+          else
+            rc = BIE_ERR_CUDA;
+          if (graph) cudaGraphDestroy(graph);
+        }
+        gnodes = (int64_t)bie_kernel_launches() - before;
+        uncount_launches(gnodes);  // captured, not launched: counted per replay
+        if (rc != BIE_OK) {  // capture unsupported here: run this call's batches directly
+          cudaGetLastError();
+          if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+          use_graph = false;
+        }
+      }
+      if (gexec) {
+        BIE_CUDA_TRY(cudaGraphLaunch(gexec, c->stream));
+        count_launches(gnodes);
+      } else {
+        BIE_TRY(batch_core(k + k0, nk));
+      }
+    } else {
+      BIE_TRY(batch_core(k + k0, nk));
+    }
     if (lu_keep) {
       BIE_CUDA_TRY(cudaMemcpyAsync(lu_keep + k0 * N * ld, LU, (size_t)nk * N * ld * sizeof(cf), cudaMemcpyDeviceToDevice,
                                    c->stream));

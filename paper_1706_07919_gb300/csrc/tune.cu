@@ -1,0 +1,131 @@
+// tune.cu -- autotuner of the mixed path's launch parameters per problem size.
+// For a geometry of N nodes the tuner times one batch of mixed-precision frequency solves for
+// every candidate (wavenumbers per batch x LU trailing-update kernel) and keeps the fastest per
+// wavenumber.  Results are cached per N bucket (N rounded up to a multiple of 64) in a small JSON
+// file:  {"bie_autotune": 1, "entries": {"2944": {"batch": 128, "tcgen05": 2, "us_per_k": ...}}}
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <map>
+#include <sstream>
+
+#include "bie_common.cuh"
+
+namespace bie {
+
+int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
+                int32_t* perm_keep);
+
+struct TuneEntry {
+  int batch = 0, tc = 0;
+  double us_per_k = 0.0;
+};
+
+static std::map<int, TuneEntry> load_cache(const char* path) {
+  std::map<int, TuneEntry> m;
+  if (!path) return m;
+  std::ifstream f(path);
+  if (!f) return m;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  for (size_t i = 0; i + 1 < s.size(); ++i) {
+    if (s[i] != '"' || !(s[i + 1] >= '0' && s[i + 1] <= '9')) continue;
+    int key = 0, b = 0, t = 0;
+    double us = 0.0;
+    if (std::sscanf(s.c_str() + i, "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"us_per_k\": %lf}", &key, &b, &t, &us) ==
+            4 &&
+        b >= 1 && (t == 0 || t == 1 || t == 2))
+      m[key] = TuneEntry{b, t, us};
+  }
+  return m;
+}
+
+static bool save_cache(const char* path, const std::map<int, TuneEntry>& m) {
+  std::ofstream f(std::string(path) + ".tmp");
+  if (!f) return false;
+  f << "{\"bie_autotune\": 1, \"entries\": {\n";
+  size_t i = 0;
+  for (const auto& kv : m) {
+    char line[160];
+    std::snprintf(line, sizeof(line), "  \"%d\": {\"batch\": %d, \"tcgen05\": %d, \"us_per_k\": %.3f}%s\n", kv.first,
+                  kv.second.batch, kv.second.tc, kv.second.us_per_k, (++i < m.size()) ? "," : "");
+    f << line;
+  }
+  f << "}}\n";
+  f.close();
+  return std::rename((std::string(path) + ".tmp").c_str(), path) == 0;
+}
+
+int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bie_tune_result* out) {
+  const int64_t N = c->N;
+  const int key = (int)((N + 63) / 64 * 64);
+  auto cache = load_cache(cache_path);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    c->mixed_batch = it->second.batch;
+    c->tc_version = it->second.tc;
+    if (out) *out = bie_tune_result{key, it->second.batch, it->second.tc, 1, it->second.us_per_k};
+    return BIE_OK;
+  }
+  if (nk < 1) return fail(BIE_ERR_INVALID_ARG, "autotune needs at least one sample wavenumber");
+  const int64_t ld = (N + 63) / 64 * 64;
+  const size_t perk = 2 * (size_t)N * ld * sizeof(cf) + 64 * (size_t)N;
+  size_t free_b = 0, total_b = 0;
+  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const int saved_batch = c->mixed_batch, saved_tc = c->tc_version, saved_graph = c->mixed_graph;
+  TuneEntry best;
+  best.us_per_k = 1e300;
+  std::vector<double> kk;
+  cd* surf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = BIE_OK;
+  const int batches[] = {8, 16, 32, 64, 128, 256};
+  const int tcs[] = {2, 0};
+  size_t surf_bytes = (size_t)256 * 2 * N * sizeof(cd);
+  if (cudaMalloc(&surf, surf_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = fail(BIE_ERR_OOM, "autotune scratch");
+  for (int tc : tcs) {
+    for (int b : batches) {
+      if (rc != BIE_OK) break;
+      if ((size_t)b * perk > free_b / 3) continue;
+      kk.resize((size_t)b);
+      for (int i = 0; i < b; ++i) kk[i] = k[i % nk];
+      c->mixed_batch = b;
+      c->tc_version = tc;
+      c->mixed_graph = 0;
+      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr);  // warm-up: workspace, tables
+      if (rc != BIE_OK) break;
+      cudaEventRecord(e0, c->stream);
+      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr);
+      if (rc != BIE_OK) break;
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double us = 1e3 * ms / b;
+      if (us < best.us_per_k) best = TuneEntry{b, tc, us};
+    }
+  }
+  if (surf) cudaFree(surf);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->mixed_graph = saved_graph;
+  if (rc != BIE_OK || best.batch == 0) {
+    c->mixed_batch = saved_batch;
+    c->tc_version = saved_tc;
+    return rc != BIE_OK ? rc : fail(BIE_ERR_OOM, "autotune: no candidate fits in device memory");
+  }
+  c->mixed_batch = best.batch;
+  c->tc_version = best.tc;
+  if (cache_path) {
+    cache = load_cache(cache_path);  // another process may have added entries meanwhile
+    cache[key] = best;
+    if (!save_cache(cache_path, cache)) return fail(BIE_ERR_INVALID_ARG, std::string("cannot write ") + cache_path);
+  }
+  if (out) *out = bie_tune_result{key, best.batch, best.tc, 0, best.us_per_k};
+  return BIE_OK;
+}
+
+}  // namespace bie

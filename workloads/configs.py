@@ -8,6 +8,12 @@
   face, mapped onto the exact spheroid), k_m = 20 m / 1024 (m = 1..1024), 256 observation points
   seeded (3001) in the shell between the spheroid scaled by 1.2 and by 2.5, Gaussian sigma = 0.2,
   2048 time samples.
+* uneven_batch: 64 configurations (seed 4001) of 1-8 sound-hard bodies each -- spheres or
+  ellipsoids with semi-axes r (1, U[.5, 1], U[.5, 1]) in a random orientation, r ~ U[0.3, 1.5],
+  placed without overlap (gap >= 0.1 between bounding spheres) in the box [0, 10]^3 -- meshed with
+  icosahedral grids of about 6 r divisions per face, coarsened so that N stays in [162, 8000];
+  256 wavenumbers over (0, 8], 256 seeded points outside the bodies, Gaussian sigma = 0.5,
+  512 time samples.
 * two_spheres_mixed: two sound-hard unit spheres, 720 elements / 1442 nodes each (N = 2884),
   centres (0, 0, +-1.05) (surface gap 0.1) on the propagation axis, k_m = m/32 (m = 1..512),
   128 x 128 observation grid on the plane z = 0 over [-5, 5]^2, Gaussian sigma = 0.25,
@@ -93,3 +99,62 @@ def config_spheroid_learned(Nk: int = 1024, kmax: float = 20.0, freq: int = 8, M
     xobs = spheroid_shell_points(M, axes, 1.2, 2.5, seed=3001)
     pulses = gaussian_pulse(Nt, T, sigma=0.2, tc=8.0)[None, :]
     return Workload("spheroid_learned", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs, pulses, Nt, T)
+
+
+def _random_rotation(rng) -> np.ndarray:
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def uneven_configuration(index: int, seed: int = 4001, n_max: int = 8000):
+    """Configuration `index` of the uneven batch: (mesh, body list) -- see the module docstring."""
+    rng = np.random.Generator(np.random.PCG64([seed, index]))
+    nb = int(rng.integers(1, 9))
+    bodies = []
+    for _ in range(nb):
+        r = float(rng.uniform(0.3, 1.5))
+        ell = bool(rng.random() < 0.5)
+        axes = (r, r * float(rng.uniform(0.5, 1.0)), r * float(rng.uniform(0.5, 1.0))) if ell else (r, r, r)
+        rot = _random_rotation(rng) if ell else np.eye(3)
+        for _attempt in range(1000):
+            c = rng.uniform(r, 10.0 - r, 3)
+            if all(np.linalg.norm(c - b["c"]) >= r + b["r"] + 0.1 for b in bodies):
+                bodies.append({"r": r, "axes": axes, "rot": rot, "c": c})
+                break
+    divs = [max(2, int(round(6.0 * b["r"]))) for b in bodies]
+    while sum(40 * n * n + 2 for n in divs) > n_max:
+        i = int(np.argmax(divs))
+        divs[i] -= 1
+    meshes = []
+    for b, n in zip(bodies, divs):
+        m = ellipsoid_from_sphere(ico_sphere(n, 1.0, bc=0), b["axes"])
+        meshes.append(scale_translate(m, 1.0, b["c"], rot=b["rot"]))
+    return merge_meshes(meshes), bodies
+
+
+def outside_points(M: int, bodies, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = []
+    while len(pts) < M:
+        p = rng.uniform(0.0, 10.0, 3)
+        if all(np.linalg.norm(p - b["c"]) > 1.1 * b["r"] + 0.05 for b in bodies):
+            pts.append(p)
+    return np.array(pts)
+
+
+def config_uneven_batch(n_configs: int = 64, Nk: int = 256, M: int = 256, Nt: int = 512):
+    """List of Workloads, one per configuration, sharing the wavenumber grid and the pulse."""
+    dk = 8.0 / Nk
+    T = 2.0 * np.pi / dk
+    k = dk * np.arange(1, Nk + 1, dtype=np.float64)
+    pulse = gaussian_pulse(Nt, T, sigma=0.5, tc=8.0)[None, :]
+    out = []
+    for i in range(n_configs):
+        mesh, bodies = uneven_configuration(i)
+        xobs = outside_points(M, bodies, seed=4001 * 1000 + i)
+        out.append(Workload(f"uneven_{i}", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs, pulse, Nt, T))
+    return out
