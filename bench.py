@@ -288,6 +288,9 @@ def run_learned(args, dev, stream):
             "anchors": info["anchors"], "krylov": info["krylov"], "krylov_fallback": info["krylov_fallback"],
             "epochs": info["epochs"], "train_ms": info["train_ms"], "first_loss": info["first_loss"],
             "last_loss": info["last_loss"], "x0_rel_err": info["x0_rel_err"], "mean_arnoldi_steps": info["mean_iters"],
+            "max_arnoldi_steps": info["max_iters"],
+            "phase_ms": {name: info[name] for name in ("anchors_ms", "train_ms", "assembly_ms", "predict_ms",
+                                                       "gmres_ms", "estimate_ms", "redo_ms")},
             "zero_start_mean_arnoldi_steps": info_z["mean_iters"],
             "zero_start_krylov_fallback": info_z["krylov_fallback"],
             "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,

@@ -94,6 +94,13 @@ typedef struct {
   double train_ms;         /* wall time of the training */
   double x0_rel_err;       /* mean over GMRES-solved wavenumbers of ||x0 - x|| / ||x|| */
   double mean_iters;       /* mean Arnoldi steps per GMRES-solved wavenumber */
+  double max_iters;        /* largest Arnoldi step count of a GMRES-solved wavenumber */
+  double anchors_ms;       /* device time of the anchors' direct solves */
+  double assembly_ms;      /* device time of the GMRES-solved wavenumbers' assembly */
+  double predict_ms;       /* device time of the initial guesses */
+  double gmres_ms;         /* device time of the GMRES solves */
+  double estimate_ms;      /* device time of the sensitivity estimates */
+  double redo_ms;          /* wall time of the direct re-solves of handed-back wavenumbers */
 } bie_learned_info;
 
 /* Result of bie_autotune. */
@@ -181,7 +188,7 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "learned.kmax"         wavenumber scale of the feature map (0: the largest training k)
  *   "learned.graph"        1: replay each training epoch from a captured CUDA graph (default)
  *   "gmres.m"              Arnoldi steps per cycle (1..62, default 30)
- *   "gmres.cycles"         cycles, each from a float-float residual (1..100, default 6)
+ *   "gmres.cycles"         cycles, each from a float-float residual (1..100, default 3)
  *   "gmres.inner_tol"      relative residual decrease that ends a cycle (default 1e-5)
  * The refinement target "refine.tol" is also the GMRES backward-error target.
  * Errors: INVALID_ARG for an unknown name or a value out of range. */

@@ -49,7 +49,10 @@ class BieReport(ctypes.Structure):
 class BieLearnedInfo(ctypes.Structure):
     _fields_ = [("anchors", ctypes.c_int32), ("krylov", ctypes.c_int32), ("krylov_fallback", ctypes.c_int32),
                 ("epochs", ctypes.c_int32), ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float),
-                ("train_ms", ctypes.c_double), ("x0_rel_err", ctypes.c_double), ("mean_iters", ctypes.c_double)]
+                ("train_ms", ctypes.c_double), ("x0_rel_err", ctypes.c_double), ("mean_iters", ctypes.c_double),
+                ("max_iters", ctypes.c_double), ("anchors_ms", ctypes.c_double), ("assembly_ms", ctypes.c_double),
+                ("predict_ms", ctypes.c_double), ("gmres_ms", ctypes.c_double), ("estimate_ms", ctypes.c_double),
+                ("redo_ms", ctypes.c_double)]
 
 
 class BieTuneResult(ctypes.Structure):

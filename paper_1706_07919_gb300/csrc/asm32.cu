@@ -357,7 +357,7 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
     return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP32 shared-memory row accumulator");
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
   const TwoPi3 tp = two_pi3();
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_asm32_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BIE_TRY((set_smem_max(k_asm32_bulk)));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   BIE_LAUNCH(k_asm32_bulk<<<gb, 32 * rows * ASM_W, smem, c->stream>>>(c->nodes, c->normals, c->bc, sorted_elems(c), N,
                                                                       c->E, c->rule.Q, sorted_table(c), c->qshape32,

@@ -240,7 +240,7 @@ int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch
   if (smem > 200 * 1024)
     return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP64 shared-memory row accumulator");
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_asm64_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BIE_TRY((set_smem_max(k_asm64_bulk)));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   BIE_LAUNCH(k_asm64_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q, c->qgeo,
                                                    c->qshape, c->color_off, c->ncolors, c->elem_perm, kv, known, A,

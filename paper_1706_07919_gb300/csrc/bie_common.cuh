@@ -77,6 +77,7 @@ struct RefineState {
   double bnorm;      // ||b||_inf
   double berr;       // latest backward error
   double err_est;    // estimated relative error caused by FP32 assembly (see refine.cu, k_perturb)
+  double scale;      // ||A||_inf ||x||_inf + ||b||_inf at the latest check
 };
 
 }  // namespace bie
@@ -125,6 +126,7 @@ struct bie_ctx {
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
+  cudaStream_t cap_stream = nullptr; // private stream on which CUDA graphs are captured
   size_t pinned_bytes = 0;
 
   // learned warm start + Krylov path (BIE_MODE_LEARNED)
@@ -137,7 +139,7 @@ struct bie_ctx {
   double mlp_kmax = 0.0;             // feature wavenumber scale (0: largest training wavenumber)
   int mlp_graph = 1;                 // replay training epochs from a captured CUDA graph
   int gmres_m = 30;                  // Arnoldi steps per cycle
-  int gmres_cycles = 6;              // cycles (each starts from a float-float residual)
+  int gmres_cycles = 3;              // cycles (each starts from a float-float residual)
   double gmres_inner_tol = 1e-5;     // relative residual decrease that closes a cycle
   bie::MlpState* mlp = nullptr;
   bie_learned_info learned_info{};
@@ -152,6 +154,24 @@ struct bie_ctx {
 namespace bie {
 
 int ensure_buf(DeviceBuf& b, size_t bytes);
+// The device's per-block shared-memory opt-in limit.  Kernels with dynamic shared memory get
+// this limit once (never a launch-specific size), so that contexts on other threads launching
+// the same kernel with other sizes cannot lower it between another thread's set and launch.
+int smem_optin();
+template <typename F>
+inline int set_smem_max(F* f) {  // dynamic limit = opt-in limit minus the kernel's static shared memory
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, (const void*)f) != cudaSuccess) return fail(BIE_ERR_CUDA, "cudaFuncGetAttributes");
+  const cudaError_t e = cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_optin() - (int)a.sharedSizeBytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+  return BIE_OK;
+}
+// Graph capture: work enqueued on c->stream between begin and end is recorded (not run) on the
+// context's private capture stream -- the caller's stream may be the legacy default stream, which
+// cannot be captured -- and returned as a graph to be launched on c->stream.
+int capture_begin(bie_ctx* c, cudaStream_t* saved);
+int capture_end(bie_ctx* c, cudaStream_t saved, cudaGraph_t* graph);
 int ensure_pinned(bie_ctx* c, size_t bytes);
 void free_buf(DeviceBuf& b);
 

@@ -39,6 +39,34 @@ int ensure_buf(DeviceBuf& b, size_t bytes) {
   b.bytes = bytes;
   return BIE_OK;
 }
+int smem_optin() {
+  static std::atomic<int> v{0};
+  int x = v.load();
+  if (x == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || x <= 0)
+      x = 48 * 1024;
+    v.store(x);
+  }
+  return x;
+}
+
+int capture_begin(bie_ctx* c, cudaStream_t* saved) {
+  if (!c->cap_stream) BIE_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  BIE_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+  *saved = c->stream;
+  c->stream = c->cap_stream;
+  return BIE_OK;
+}
+
+int capture_end(bie_ctx* c, cudaStream_t saved, cudaGraph_t* graph) {
+  c->stream = saved;
+  *graph = nullptr;
+  BIE_CUDA_TRY(cudaStreamEndCapture(c->cap_stream, graph));
+  return BIE_OK;
+}
+
 int ensure_pinned(bie_ctx* c, size_t bytes) {
   if (c->pinned_bytes >= bytes) return BIE_OK;
   if (c->pinned) {
@@ -209,6 +237,7 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c->work4);
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return BIE_OK;
 }

@@ -26,6 +26,7 @@ struct GmresState {
   int32_t iters;    // total Arnoldi steps
   double beta;      // ||r|| at the start of the cycle
   double resid;     // current residual estimate |g_{j}|
+  double target;    // absolute residual at which the outer backward-error target is met
 };
 
 // ---- block reductions (1024 threads) -------------------------------------------------------------
@@ -41,9 +42,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // start of a cycle: beta = ||r||_2, v_0 = r / beta, g = (beta, 0, ...); gate = converged
+// The cycle also stops once |g| falls below target = tol (||A|| ||x|| + ||b||) / 2 (infinity
+// norms, from the latest check; |g| bounds the 2-norm and so the infinity norm of the residual):
+// a close initial guess then saves the Arnoldi steps of the last decades.
 __global__ void __launch_bounds__(1024) k_gm_start(int n, int m, const cd* __restrict__ r, cd* __restrict__ V,
                                                    cd* __restrict__ g, GmresState* __restrict__ gs,
-                                                   const RefineState* __restrict__ rs, RefineState* __restrict__ gate) {
+                                                   const RefineState* __restrict__ rs, RefineState* __restrict__ gate,
+                                                   double tol) {
   __shared__ double red[32];
   const int kk = blockIdx.x;
   if (rs[kk].done) {
@@ -61,6 +66,7 @@ __global__ void __launch_bounds__(1024) k_gm_start(int n, int m, const cd* __res
     gs[kk].j = 0;
     gs[kk].beta = beta;
     gs[kk].resid = beta;
+    gs[kk].target = 0.5 * tol * rs[kk].scale;
     g[(int64_t)kk * (m + 1)] = {beta, 0.0};
     gate[kk].done = beta > 0.0 ? 0 : 1;
   }
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(1024) k_gm_arnoldi(int n, int m, int j, cd* __
     gs[kk].j = j + 1;
     gs[kk].iters += 1;
     gs[kk].resid = res;
-    if (res <= inner_tol * gs[kk].beta || j + 1 >= m || hn == 0.0) gate[kk].done = 1;
+    if (res <= fmax(inner_tol * gs[kk].beta, gs[kk].target) || j + 1 >= m || hn == 0.0) gate[kk].done = 1;
   }
 }
 
@@ -260,15 +266,15 @@ int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstr
   BIE_CUDA_TRY(cudaMemsetAsync(gs, 0, nk * sizeof(GmresState), c->stream));
   const size_t sm_trsv = (size_t)n * sizeof(cf), sm_res = (size_t)n * sizeof(float4), sm_mv = (size_t)n * sizeof(float2);
   if (sm_res > 200 * 1024) return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory Krylov kernels");
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_trsv_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsv));
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_res));
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_gm_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mv));
+  BIE_TRY((set_smem_max(k_trsv_lu)));
+  BIE_TRY((set_smem_max(k_residual_ff)));
+  BIE_TRY((set_smem_max(k_gm_matvec)));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int cy = 0; cy <= cycles; ++cy) {
     BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, rs));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, rs, tol, 0));
     if (cy == cycles) break;
-    BIE_LAUNCH(k_gm_start<<<nk, 1024, 0, c->stream>>>(n, m, r, V, g, gs, rs, gate));
+    BIE_LAUNCH(k_gm_start<<<nk, 1024, 0, c->stream>>>(n, m, r, V, g, gs, rs, gate, tol));
     for (int j = 0; j < m; ++j) {
       // z_j = M^{-1} v_j
       BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, lu_bstride, perm, V, Z, 0, gate, sel,

@@ -157,7 +157,22 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   std::vector<double> ka((size_t)na);
   for (int64_t a = 0; a < na; ++a) ka[a] = k[anc[a]];
   std::vector<bie_report> rep_a((size_t)na);
+  cudaEvent_t ev[5];
+  for (auto& e : ev) BIE_CUDA_TRY(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); }
+  } evg{ev};
+  auto elapsed = [&](int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[a], ev[b]);
+    return (double)ms;
+  };
+  BIE_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
   BIE_TRY(solve_mixed(c, ka.data(), na, surf_a, rep_a.data(), LUk, permk));
+  BIE_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
+  BIE_CUDA_TRY(cudaEventSynchronize(ev[1]));
+  info.anchors_ms = elapsed(0, 1);
   {
     std::vector<int32_t> dst(anc.begin(), anc.end());
     BIE_CUDA_TRY(cudaMemcpyAsync(idx_dev, dst.data(), na * 4, cudaMemcpyHostToDevice, c->stream));
@@ -236,7 +251,9 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, kv.data(), nk * 8, cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemcpyAsync(sel, hs.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemcpyAsync(dst, hd.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
+    BIE_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
     BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum));
+    BIE_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
     if (c->learned_x0 == 1) {
       BIE_TRY(mlp_predict_dev(c, kdev, nk, x));
     } else if (c->learned_x0 == 2) {
@@ -246,8 +263,10 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
       BIE_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nk * N * sizeof(cd), c->stream));
     }
     BIE_CUDA_TRY(cudaMemcpyAsync(x0, x, (size_t)nk * N * sizeof(cd), cudaMemcpyDeviceToDevice, c->stream));
+    BIE_CUDA_TRY(cudaEventRecord(ev[2], c->stream));
     BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, b, x, LUk, lu_bstride, permk, sel, m, c->gmres_cycles,
                         c->gmres_inner_tol, c->refine_tol, gscr, state));
+    BIE_CUDA_TRY(cudaEventRecord(ev[3], c->stream));
     BIE_LAUNCH(k_rel_diff<<<nk, 256, 0, c->stream>>>(x0, x, N, rel));  // error of the initial guess
     // sensitivity to the FP32 assembly: z = A^{-1} (E x), E a seeded FP32-sized perturbation,
     // by a short GMRES solve; err_est = ||z|| / ||x||
@@ -257,6 +276,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, x0, z, LUk, lu_bstride, permk, sel, std::min(m, 20), 1, 1e-2,
                         0.0, gscr, state_e));
     BIE_LAUNCH(k_norm_ratio<<<nk, 256, 0, c->stream>>>(z, x, N, rel + kb));
+    BIE_CUDA_TRY(cudaEventRecord(ev[4], c->stream));
     {
       dim3 g((unsigned)((N + 255) / 256), (unsigned)nk);
       BIE_LAUNCH(k_surface_fields_to<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, dst, surf_out));
@@ -264,6 +284,10 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_CUDA_TRY(cudaGetLastError());
     BIE_CUDA_TRY(cudaMemcpyAsync(hrel.data(), rel, 2 * kb * 8, cudaMemcpyDeviceToHost, c->stream));
     BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
+    info.assembly_ms += elapsed(0, 1);
+    info.predict_ms += elapsed(1, 2);
+    info.gmres_ms += elapsed(2, 3);
+    info.estimate_ms += elapsed(3, 4);
     for (int i = 0; i < nk; ++i) {
       const int64_t gi = others[o0 + i];
       const bool conv = done[i] && std::isfinite(berr[i]);
@@ -271,6 +295,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
       const bool sensitive = !(e <= c->fallback_err_est);
       sum_rel += hrel[i];
       sum_it += iters[i];
+      info.max_iters = std::max(info.max_iters, (double)iters[i]);
       if (rep)
         rep[gi] = bie_report{iters[i], BIE_MODE_LEARNED,
                              (conv ? 0u : BIE_FLAG_NOT_CONVERGED) | (sensitive ? BIE_FLAG_ILL_CONDITIONED : 0u), 0,
@@ -286,6 +311,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   info.x0_rel_err = sum_rel / (double)nothers;
   info.mean_iters = sum_it / (double)nothers;
   // ---- 4. direct solves of the wavenumbers the Krylov path handed back ------------------------
+  const auto t_redo = std::chrono::steady_clock::now();
   if (!redo.empty()) {
     const int64_t nr = (int64_t)redo.size();
     void* tmp = nullptr;
@@ -312,6 +338,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_TRY(rc);
   }
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  info.redo_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_redo).count();
   c->learned_info = info;
   return BIE_OK;
 }

@@ -255,7 +255,7 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
     BIE_LAUNCH(k_panel<S><<<batch, 512, 0, c->stream>>>(A, bstride, n, ld, p0, w, piv, info));
     return BIE_OK;
   }
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_leaf<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  BIE_TRY((set_smem_max(k_leaf<S>)));
   for (int c0 = p0; c0 < p0 + w; c0 += lw) {
     const int l = std::min(lw, p0 + w - c0);
     const size_t smem = (size_t)(n - c0) * l * sizeof(Cx<S>);

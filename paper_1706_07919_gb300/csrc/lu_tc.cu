@@ -525,10 +525,10 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
                              (uint64_t)bstride * 8));
     BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)tc2::KR, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)tc2::KR * 4,
                              (uint64_t)ub_stride * 4));
-    BIE_CUDA_TRY(cudaFuncSetAttribute(tc2::k_update_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, tc2::SMEM_BYTES));
+    BIE_TRY((set_smem_max(tc2::k_update_tc2)));
     BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   } else {
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    BIE_TRY((set_smem_max(k_update_tc)));
   }
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int w = std::min(NB, n - p0);

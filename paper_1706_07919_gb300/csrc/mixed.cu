@@ -123,11 +123,12 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       if (!gexec) {
         const int64_t before = (int64_t)bie_kernel_launches();
         cudaGraph_t graph = nullptr;
-        int rc = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess ? BIE_OK : BIE_ERR_CUDA;
+        cudaStream_t saved = nullptr;
+        int rc = capture_begin(c, &saved);
         if (rc == BIE_OK) {
           rc = batch_core(kpin, nk);
-          const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
-          if (rc == BIE_OK && ce == cudaSuccess && graph)
+          const int re = capture_end(c, saved, &graph);
+          if (rc == BIE_OK && re == BIE_OK && graph)
             rc = cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess ? BIE_OK : BIE_ERR_CUDA;
           else
             rc = BIE_ERR_CUDA;

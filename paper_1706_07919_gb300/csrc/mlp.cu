@@ -954,13 +954,16 @@ int mlp_train(bie_ctx* c, const double* k, int64_t nk, const cd* surf, int epoch
       if (!exec) {
         cudaGraph_t graph = nullptr;
         const int64_t before = bie_kernel_launches();
-        rc = cuda_ok(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaStream_t saved = nullptr;
+        rc = capture_begin(c, &saved);
         if (rc != BIE_OK) break;
         const int body = epoch_body();
-        const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
-        if (body != BIE_OK) { rc = body; if (graph) cudaGraphDestroy(graph); break; }
-        rc = cuda_ok(ce, "end capture");
-        if (rc != BIE_OK) break;
+        const int re = capture_end(c, saved, &graph);
+        if (body != BIE_OK || re != BIE_OK) {
+          rc = body != BIE_OK ? body : re;
+          if (graph) cudaGraphDestroy(graph);
+          break;
+        }
         graph_nodes = (int)(bie_kernel_launches() - before);
         rc = cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
         cudaGraphDestroy(graph);

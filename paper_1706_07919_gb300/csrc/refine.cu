@@ -222,6 +222,7 @@ __global__ void k_refine_check(int n, const cd* __restrict__ b, const cd* __rest
     st[kk].anorm = am;
     st[kk].bnorm = bm;
     st[kk].berr = be;
+    st[kk].scale = am * xm + bm;
     if (be <= tol) st[kk].done = 1;
     else if (count_iter) st[kk].iters += 1;
   }
@@ -292,8 +293,8 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
   const size_t sm_res = (size_t)n * sizeof(float4);
   if (sm_trsv > 200 * 1024 || sm_res > 200 * 1024)
     return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_trsv_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsv));
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_residual_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_res));
+  BIE_TRY((set_smem_max(k_trsv_lu)));
+  BIE_TRY((set_smem_max(k_residual_ff)));
   BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int it = 0; it <= it_max; ++it) {

@@ -98,7 +98,7 @@ int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout) {
   double2* tw;
   BIE_TRY(twiddle_table(c, n, &tw));
   size_t smem = 2 * (size_t)n * sizeof(C2<double>);
-  BIE_CUDA_TRY(cudaFuncSetAttribute(k_pulse_spectrum<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BIE_TRY((set_smem_max(k_pulse_spectrum<double>)));
   BIE_LAUNCH(k_pulse_spectrum<double><<<(unsigned)P, std::min(512, n / 2), smem, c->stream>>>(s, n, tw, Sout));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -112,11 +112,11 @@ int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t
   int threads = std::min(512, std::max(32, n / 2));
   if (out_dtype == 0) {
     size_t smem = 2 * (size_t)n * sizeof(C2<double>);
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_TRY((set_smem_max(k_synth<double, double>)));
     BIE_LAUNCH(k_synth<double, double><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (double*)out));
   } else {
     size_t smem = 2 * (size_t)n * sizeof(C2<float>);
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_TRY((set_smem_max(k_synth<float, float>)));
     BIE_LAUNCH(k_synth<float, float><<<g, threads, smem, c->stream>>>(T, midx_dev, nk, M, Sp, n, tw, (float*)out));
   }
   BIE_CUDA_TRY(cudaGetLastError());
@@ -183,11 +183,11 @@ extern "C" int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_
   const int threads = std::min(512, std::max(32, n / 2));
   if (out_dtype == 0) {
     const size_t smem = 2 * (size_t)n * sizeof(C2<double>);
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_TRY((set_smem_max(k_synth<double, double>)));
     BIE_LAUNCH(k_synth<double, double><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (double*)out));
   } else {
     const size_t smem = 2 * (size_t)n * sizeof(C2<float>);
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_synth<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_TRY((set_smem_max(k_synth<float, float>)));
     BIE_LAUNCH(k_synth<float, float><<<g, threads, smem, st>>>((const cd*)T, md, (int)Nk, M, (const cd*)S, n, tw, (float*)out));
   }
   BIE_CUDA_TRY(cudaGetLastError());

@@ -6,8 +6,13 @@
 #include <algorithm>
 #include <cstdio>
 #include <fstream>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <sstream>
+#include <thread>
+
+#include <unistd.h>
 
 #include "bie_common.cuh"
 
@@ -41,8 +46,14 @@ static std::map<int, TuneEntry> load_cache(const char* path) {
   return m;
 }
 
+static std::mutex g_cache_mu;  // read-modify-write of cache files within this process
+
 static bool save_cache(const char* path, const std::map<int, TuneEntry>& m) {
-  std::ofstream f(std::string(path) + ".tmp");
+  static std::atomic<uint64_t> seq{0};
+  const std::string tmp = std::string(path) + "." + std::to_string((long)getpid()) + "." +
+                          std::to_string((uint64_t)std::hash<std::thread::id>()(
+                              std::this_thread::get_id())) + "." + std::to_string(seq.fetch_add(1)) + ".tmp";
+  std::ofstream f(tmp);
   if (!f) return false;
   f << "{\"bie_autotune\": 1, \"entries\": {\n";
   size_t i = 0;
@@ -54,7 +65,7 @@ static bool save_cache(const char* path, const std::map<int, TuneEntry>& m) {
   }
   f << "}}\n";
   f.close();
-  return std::rename((std::string(path) + ".tmp").c_str(), path) == 0;
+  return std::rename(tmp.c_str(), path) == 0;
 }
 
 int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bie_tune_result* out) {
@@ -120,7 +131,8 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   c->mixed_batch = best.batch;
   c->tc_version = best.tc;
   if (cache_path) {
-    cache = load_cache(cache_path);  // another process may have added entries meanwhile
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    cache = load_cache(cache_path);  // another thread or process may have added entries meanwhile
     cache[key] = best;
     if (!save_cache(cache_path, cache)) return fail(BIE_ERR_INVALID_ARG, std::string("cannot write ") + cache_path);
   }

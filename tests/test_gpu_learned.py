@@ -48,7 +48,7 @@ def _solver(mesh):
 
 
 def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
 
 
 @pytest.fixture(scope="module")
@@ -122,10 +122,11 @@ def test_adam_steps_match_oracle(small_spheroid):
 
 @pytest.fixture(scope="module")
 def learned_case():
-    """Hard prolate spheroid (642 nodes), 48 wavenumbers over (0, 6]: anchors every 8th."""
+    """Hard prolate spheroid (642 nodes), 96 wavenumbers k_m = 0.02 m: anchors every 8th
+    (spacing 0.16, as on the 1024-wavenumber spheroid workload)."""
     from paper_1706_07919_gb300 import binding as Bd
     mesh = W.ellipsoid_from_sphere(W.ico_sphere(4, 1.0, bc=0), (1.0, 1.0, 2.0))
-    k = 0.125 * np.arange(1, 49)
+    k = 0.02 * np.arange(1, 97)
     out = {}
     for x0 in (1, 0):
         s = _solver(mesh)
@@ -142,14 +143,14 @@ def test_learned_solves_match_oracle(learned_case):
     from paper_1706_07919_gb300 import binding as Bd
     mesh, k, out = learned_case
     surf, rep, info = out[1]
-    assert info["anchors"] == 6 and info["krylov"] == 42
+    assert info["anchors"] == 12 and info["krylov"] == 84
     paths = [r.path for r in rep]
-    assert paths.count(Bd.BIE_MODE_LEARNED) + info["krylov_fallback"] == 42
-    for i in (0, 4, 13, 22, 30, 46):  # non-anchor wavenumbers across the band (7, 15, ... are anchors)
+    assert paths.count(Bd.BIE_MODE_LEARNED) + info["krylov_fallback"] == 84
+    for i in (0, 4, 13, 22, 50, 94):  # non-anchor wavenumbers across the band (7, 15, ... are anchors)
         P, Pn = oracle.solve_frequency(mesh, k[i], [0.0, 0.0, 1.0])
         assert _rel(surf[i, 0], P) <= 1e-6, (i, k[i], rep[i].flags)
         assert _rel(surf[i, 1], Pn) <= 1e-6
-    for i in (7, 23):  # anchors (direct path)
+    for i in (7, 95):  # anchors (direct path)
         P, _ = oracle.solve_frequency(mesh, k[i], [0.0, 0.0, 1.0])
         assert _rel(surf[i, 0], P) <= 1e-6
     for r in rep:
@@ -164,5 +165,5 @@ def test_network_warm_start_gains(learned_case):
     print("zero start:", zero)
     assert zero["x0_rel_err"] == pytest.approx(1.0)
     assert net["last_loss"] < 0.05 * net["first_loss"]
-    assert net["x0_rel_err"] < 0.5
+    assert net["x0_rel_err"] < 0.1
     assert net["mean_iters"] < zero["mean_iters"]

@@ -90,7 +90,7 @@ def test_scheduler_uneven_configurations(tmp_path):
         s.close()
         assert _rel(surf.cpu().numpy(), ref.cpu().numpy()) <= 1e-7
         assert all(r.backward_err <= 1e-10 for r in job.reports())
-    m = min(picks, key=lambda x: x.N)
-    i = picks.index(m)
+    i = int(np.argmin([x.N for x in picks]))
+    m = picks[i]
     P, _ = oracle.solve_frequency(m, k[3], [0.0, 0.0, 1.0])
     assert _rel(surfs[i].cpu().numpy()[3, 0], P) <= 1e-6
