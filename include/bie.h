@@ -174,6 +174,9 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
+ *   "field.variant"        shape of the mixed field kernel: wavenumbers per group x points per CTA,
+ *                          0 (8 x 128, FP32 compensated sums per term), 1 (8 x 128), 2 (4 x 128),
+ *                          3 (8 x 64), 4 (16 x 64, default), 5 (16 x 32), 6 (16 x 128), 7 (12 x 64)
  *   "mixed.graph"          1: replay the device work of full batches from a captured CUDA graph
  *                          (default), 0: launch every kernel directly
  * Learned warm start and Krylov solve (BIE_MODE_LEARNED):

@@ -274,6 +274,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     c->fallback_err_est = value;
   } else if (n == "field.accurate_phase") {
     c->field_accurate_phase = value != 0.0 ? 1 : 0;
+  } else if (n == "field.variant") {
+    if (value < 0 || value > 7 || value != (int)value) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0..7");
+    c->field_variant = (int)value;
   } else if (n == "mixed.graph") {
     c->mixed_graph = value != 0.0 ? 1 : 0;
   } else if (n == "learned.stride") {

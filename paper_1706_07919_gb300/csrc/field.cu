@@ -440,6 +440,179 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
   }
 }
 
+// Variant of k_field32b with the wavenumber-group size KB, the points per CTA TP and the minimum
+// resident CTAs MINB as template parameters: terms are summed in FP32 over runs of 32 quadrature
+// points and each run is added to a compensated sum kept in shared memory, so only 2 KB partial
+// sums stay in registers; the phase step e^{i dk R} takes its phase from an FMA-split product
+// (no 2 pi reduction in float-float: dk R is small).
+template <int KB, int TP, int MINB>
+__global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
+                                                       const float* __restrict__ qtab, const cf* __restrict__ Pq,
+                                                       const cf* __restrict__ Pnq, const cd* __restrict__ surf,
+                                                       const double* __restrict__ xp, int64_t M,
+                                                       const int32_t* __restrict__ foot_elem,
+                                                       const double* __restrict__ foot, const double* __restrict__ kv,
+                                                       int nk, cd* __restrict__ T, TwoPi3f tp, int uniform, ff dk) {
+  __shared__ float sg[13][TP];
+  __shared__ float sq[KB][4][TP];
+  __shared__ float s0[KB][4][TP];
+  __shared__ float sacc[KB][4][TP];  // compensated sums: re (s, c), im (s, c)
+  __shared__ float sk[KB][3];
+  const int kbase = blockIdx.y * KB;
+  const int nkb = min(KB, nk - kbase);
+  const int tid = threadIdx.x;
+  const int64_t m = (int64_t)blockIdx.x * TP + tid;
+  const bool active = m < M;
+  if (tid < nkb) {
+    const ff k = ff_from_double(kv[kbase + tid]);
+    sk[tid][0] = k.hi;
+    sk[tid][1] = k.lo;
+    sk[tid][2] = (float)(1.0 / kv[kbase + tid]);
+  }
+#pragma unroll
+  for (int j = 0; j < KB; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sacc[j][q][tid] = 0.f;
+  ff p[3] = {{0, 0}, {0, 0}, {0, 0}}, x0[3] = {{0, 0}, {0, 0}, {0, 0}}, nu0[3] = {{0, 0}, {0, 0}, {1, 0}};
+  if (active) {
+    for (int d = 0; d < 3; ++d) {
+      p[d] = ff_from_double(xp[3 * m + d]);
+      x0[d] = ff_from_double(foot[8 * m + d]);
+      nu0[d] = ff_from_double(foot[8 * m + 3 + d]);
+    }
+    const double fxi = foot[8 * m + 6], feta = foot[8 * m + 7];
+    const double L1 = 1.0 - fxi - feta;
+    const double Nv[6] = {L1 * (2 * L1 - 1), fxi * (2 * fxi - 1), feta * (2 * feta - 1), 4 * L1 * fxi, 4 * fxi * feta,
+                          4 * feta * L1};
+    const int32_t* el = elems + 6 * (int64_t)foot_elem[m];
+    for (int j = 0; j < nkb; ++j) {
+      const cd* P = surf + (int64_t)(kbase + j) * 2 * N;
+      double a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+      for (int a = 0; a < 6; ++a) {
+        const cd v = P[el[a]], w = P[N + el[a]];
+        a0 += Nv[a] * v.re; a1 += Nv[a] * v.im;
+        b0 += Nv[a] * w.re; b1 += Nv[a] * w.im;
+      }
+      s0[j][0][tid] = (float)a0; s0[j][1][tid] = (float)a1;
+      s0[j][2][tid] = (float)b0; s0[j][3][tid] = (float)b1;
+    }
+  }
+  float pr[KB], pim[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) pr[j] = pim[j] = 0.f;
+  for (int64_t t0 = 0; t0 < EQ; t0 += TP) {
+    const int64_t t = t0 + tid;
+    __syncthreads();
+    if (t < EQ) {
+#pragma unroll
+      for (int u = 0; u < 13; ++u) sg[u][tid] = qtab[u * EQ + t];
+      for (int j = 0; j < nkb; ++j) {
+        const cf a = Pq[(int64_t)(kbase + j) * EQ + t], b = Pnq[(int64_t)(kbase + j) * EQ + t];
+        sq[j][0][tid] = a.re; sq[j][1][tid] = a.im;
+        sq[j][2][tid] = b.re; sq[j][3][tid] = b.im;
+      }
+    }
+    __syncthreads();
+    const int cnt = (EQ - t0) < TP ? (int)(EQ - t0) : TP;
+    if (!active) continue;
+    for (int u = 0; u < cnt; ++u) {
+      const ff qx = {sg[0][u], sg[3][u]}, qy = {sg[1][u], sg[4][u]}, qz = {sg[2][u], sg[5][u]};
+      const float nx = sg[6][u], ny = sg[7][u], nz = sg[8][u], wj = sg[9][u];
+      const ff nux = {nx, sg[10][u]}, nuy = {ny, sg[11][u]}, nuz = {nz, sg[12][u]};
+      const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
+      const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
+      const ff Rp = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
+      const ff R0 = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
+      const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
+      const float iRp = 1.0f / Rp.hi, iR0 = 1.0f / R0.hi;
+      const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp * iRp;
+      const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0 * iR0;
+      const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
+      float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
+      float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
+      if (uniform) {
+        const ff k0 = {sk[0][0], sk[0][1]};
+        cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
+        cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
+        cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
+        // step phases dk R: FP32 head plus its exact FMA error and the cross terms as the tail
+        float h = dk.hi * Rp.hi;
+        cis_reduced(h, __fmaf_rn(dk.hi, Rp.hi, -h) + (dk.hi * Rp.lo + dk.lo * Rp.hi), dcp, dsp);
+        h = dk.hi * R0.hi;
+        cis_reduced(h, __fmaf_rn(dk.hi, R0.hi, -h) + (dk.hi * R0.lo + dk.lo * R0.hi), dc0, ds0);
+        h = dk.hi * nr.hi;
+        cis_reduced(h, __fmaf_rn(dk.hi, nr.hi, -h) + (dk.hi * nr.lo + dk.lo * nr.hi), dcg, dsg);
+      }
+#pragma unroll
+      for (int j = 0; j < KB; ++j) {
+        if (j < nkb) {
+          const float khi = sk[j][0], kinv = sk[j][2];
+          if (!uniform) {
+            const ff k = {khi, sk[j][1]};
+            cis_ffk(ff_mul(k, Rp), tp, cp, spp);
+            cis_ffk(ff_mul(k, R0), tp, c0, s0v);
+            cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+          } else if (j > 0) {
+            float t = cp * dcp - spp * dsp;
+            spp = spp * dcp + cp * dsp;
+            cp = t;
+            t = c0 * dc0 - s0v * ds0;
+            s0v = s0v * dc0 + c0 * ds0;
+            c0 = t;
+            t = cg * dcg - sgv * dsg;
+            sgv = sgv * dcg + cg * dsg;
+            cg = t;
+          }
+          const float kRp = khi * Rp.hi, kR0 = khi * R0.hi;
+          const float Gpr = cp * iRp, Gpi = spp * iRp, G0r = c0 * iR0, G0i = s0v * iR0;
+          const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
+          const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
+          const float g = cg, f = sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
+          const float P0r = s0[j][0][tid], P0i = s0[j][1][tid], Q0r = s0[j][2][tid], Q0i = s0[j][3][tid];
+          const float Ptr = sq[j][0][u] - P0r * g - Q0r * f, Pti = sq[j][1][u] - P0i * g - Q0i * f;
+          const float dPr = sq[j][2][u] - P0r * dg - Q0r * df, dPi = sq[j][3][u] - P0i * dg - Q0i * df;
+          const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
+          const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
+          const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);
+          pr[j] = __fmaf_rn(wj, tr, pr[j]);
+          pim[j] = __fmaf_rn(wj, ti, pim[j]);
+        }
+      }
+      if ((u & 31) == 31 || u == cnt - 1) {  // add the run to the compensated sums
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+          if (j < nkb) {
+            ff a = ff_two_sum(sacc[j][0][tid], pr[j]);
+            sacc[j][0][tid] = a.hi;
+            sacc[j][1][tid] += a.lo;
+            a = ff_two_sum(sacc[j][2][tid], pim[j]);
+            sacc[j][2][tid] = a.hi;
+            sacc[j][3][tid] += a.lo;
+          }
+          pr[j] = pim[j] = 0.f;
+        }
+      }
+    }
+  }
+  if (active) {
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    for (int j = 0; j < nkb; ++j) {
+      const double sr = (double)sacc[j][0][tid] + (double)sacc[j][1][tid];
+      const double si = (double)sacc[j][2][tid] + (double)sacc[j][3][tid];
+      T[(int64_t)(kbase + j) * M + m] = {(double)s0[j][0][tid] + sr * inv4pi, (double)s0[j][1][tid] + si * inv4pi};
+    }
+  }
+}
+
+template <int KB, int TP, int MINB>
+static void launch_field32c(bie_ctx* c, int64_t EQ, const cf* Pq, const cf* Pnq, const cd* surf, const double* xp,
+                            int64_t M, const int32_t* foot_elem, const double* foot, const double* kv, int nk, cd* T,
+                            TwoPi3f tp, int uniform, ff dk) {
+  dim3 gb((unsigned)((M + TP - 1) / TP), (unsigned)((nk + KB - 1) / KB));
+  BIE_LAUNCH(k_field32c<KB, TP, MINB><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M,
+                                                              foot_elem, foot, kv, nk, T, tp, uniform, dk));
+}
+
 int ensure_mixed_tables(bie_ctx* c);
 
 int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* xp, int64_t M,
@@ -460,19 +633,39 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
   if (M > 0) {
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
     if (c->field_accurate_phase) {
-      dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
-      // uniform spacing inside every group of FKB wavenumbers enables the phase recurrence
+      const int v = c->field_variant;
+      static const int kKB[8] = {FKB, 8, 4, 8, 16, 16, 16, 12};
+      const int KBv = kKB[v & 7];
+      // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
       int uniform = nk > 1 ? 1 : 0;
       const double dkv = nk > 1 ? hk[1] - hk[0] : 0.0;
       for (int j = 0; j < nk && uniform; ++j) {
-        const double expect = hk[(j / FKB) * FKB] + (j % FKB) * dkv;
+        const double expect = hk[(j / KBv) * KBv] + (j % KBv) * dkv;
         if (std::fabs(hk[j] - expect) > 1e-12 * std::fabs(hk[j]) || !(dkv > 0.0)) uniform = 0;
       }
-      BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot, kv,
-                                           nk, T, tp, uniform, ff_from_double(dkv)));
+      const ff dkf = ff_from_double(dkv);
+      if (v == 1) {
+        launch_field32c<8, 128, 4>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 2) {
+        launch_field32c<4, 128, 6>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 3) {
+        launch_field32c<8, 64, 8>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 4) {
+        launch_field32c<16, 64, 4>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 5) {
+        launch_field32c<16, 32, 8>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 6) {
+        launch_field32c<16, 128, 2>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 7) {
+        launch_field32c<12, 64, 5>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else {
+        dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
+        BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
+                                                        foot, kv, nk, T, tp, uniform, dkf));
+      }
     }
     else
       BIE_LAUNCH(k_field32<false><<<gf, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
