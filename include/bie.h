@@ -177,6 +177,9 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "field.variant"        shape of the mixed field kernel: wavenumbers per group x points per CTA,
  *                          0 (8 x 128, FP32 compensated sums per term), 1 (8 x 128), 2 (4 x 128),
  *                          3 (8 x 64), 4 (16 x 64, default), 5 (16 x 32), 6 (16 x 128), 7 (12 x 64)
+ *   "mixed.reassembly"     system of the flagged wavenumbers: 1 (default) bulk pairs in float-float
+ *                          (~48-bit, FP32 pipes), 0 in FP64; near pairs and diagonal are FP64
+ *   "assemble.bulk_ff"     bie_assemble's bulk pairs in float-float (1) or FP64 (0, default)
  *   "mixed.graph"          1: replay the device work of full batches from a captured CUDA graph
  *                          (default), 0: launch every kernel directly
  * Learned warm start and Krylov solve (BIE_MODE_LEARNED):

@@ -331,6 +331,9 @@ static int32_t* sorted_elems(bie_ctx* c) {
   return reinterpret_cast<int32_t*>(sorted_table(c) + P32COUNT * c->E * c->rule.Q);
 }
 
+const float* sorted_table_ptr(bie_ctx* c) { return sorted_table(c); }
+const int32_t* sorted_elems_ptr(bie_ctx* c) { return sorted_elems(c); }
+
 int ensure_mixed_tables(bie_ctx* c) {
   if (c->qgeo32) return BIE_OK;
   const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;

@@ -226,14 +226,20 @@ __global__ void __launch_bounds__(256) k_asm64_near(
   }
 }
 
+int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* known, cd* rowsum);
+
 // Assembles nk systems (FP64) for the device wavenumbers kv[0..nk): A [nk][N][N], b [nk][N].
-// scratch: >= nk * N * (sizeof(cd) * 4) bytes.
-int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch) {
+// scratch: >= nk * N * (sizeof(cd) * 4) bytes.  ff_bulk: the bulk pairs in float-float on the
+// FP32 pipes (asmff.cu) instead of FP64; the near pairs and the diagonal are FP64 either way.
+int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch, bool ff_bulk) {
   const int64_t N = c->N;
   cd* known = (cd*)scratch;
   cd* rowsum = known + (int64_t)nk * N;
   dim3 gk((unsigned)((N + 255) / 256), nk);
   BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known));
+  if (ff_bulk) {
+    BIE_TRY(assemble_ff_bulk(c, kv, nk, A, known, rowsum));
+  } else {
   int rows = 16;
   while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
   size_t smem = (size_t)rows * N * sizeof(cd);
@@ -246,6 +252,7 @@ int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch
                                                    c->qshape, c->color_off, c->ncolors, c->elem_perm, kv, known, A,
                                                    rowsum, rows));
   BIE_CUDA_TRY(cudaGetLastError());
+  }
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);
   BIE_LAUNCH(k_asm64_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
                                           c->ngeo, c->nshape, c->n2e_off, c->n2e, kv, known, A, rowsum, b));

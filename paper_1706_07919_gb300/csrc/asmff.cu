@@ -1,0 +1,258 @@
+// asmff.cu -- float-float assembly of Eq. (BRIEF) for the wavenumbers that need the FP64 system
+// (those flagged near an interior resonance, see mixed.cu): the bulk (row, element) pairs of
+// asm64.cu computed with every quantity carried as an unevaluated sum of two floats (about 48
+// significant bits) on the FP32 pipes, which on this GPU run ~70x faster than the FP64 pipe.
+// Output is the FP64 system of asm64.cu (entries rounded to double from float-float); the pairs
+// whose element contains the collocation node stay with k_asm64_near.
+//
+// e^{i phi} to ~1e-14: phi (float-float) is reduced by n pi/2 with pi/2 split into three floats
+// whose first two products with n are exact, then sin and cos of the reduced v, |v| <= pi/4, by
+// their Taylor series written from the series: the leading terms in float-float by Horner's rule
+// and the terms below 4e-9 in FP32 (truncation after v^15 and v^16: < 1e-16).
+#include "bie_common.cuh"
+
+namespace bie {
+
+__device__ __forceinline__ ff ffx_add_f(ff a, float b) {  // ff + float
+  const ff s = ff_two_sum(a.hi, b);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ffx_mul_f(ff a, float b) {  // ff * float
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return ff_fast_two_sum(p, e);
+}
+// acc += a * b (ff * ff), accumulated with a two-sum on the heads
+__device__ __forceinline__ void ffx_mac(ff& acc, ff a, ff b) { acc = ff_add(acc, ff_mul(a, b)); }
+__device__ __forceinline__ ff ffx_recip(ff a) {  // 1 / a by one Newton step on the FP32 reciprocal
+  const float y = 1.0f / a.hi;
+  const ff e = ff_sub(ff{1.0f, 0.0f}, ffx_mul_f(a, y));  // 1 - a y, small
+  return ffx_add_f(ffx_mul_f(e, y), y);
+}
+
+struct FFConst {
+  float p1, p2, p3;            // pi/2 = p1 + p2 + p3, p1 and p2 with 16 significant bits
+  float two_over_pi;
+  ff s3, s5, s7, s9;           // -1/3!, 1/5!, -1/7!, 1/9!
+  float s11, s13, s15;         // -1/11!, 1/13!, -1/15!
+  ff c2, c4, c6, c8;           // -1/2!, 1/4!, -1/6!, 1/8!
+  float c10, c12, c14, c16;    // -1/10!, 1/12!, -1/14!, 1/16!
+};
+
+__device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
+  const float n = rintf(phi.hi * K.two_over_pi);
+  const float h = __fmaf_rn(-n, K.p1, phi.hi);  // exact (n p1 exact, result within the ulp grid)
+  ff u = ff_two_sum(h, -n * K.p2);              // n p2 exact
+  u = ffx_add_f(u, __fmaf_rn(-n, K.p3, phi.lo));
+  const ff z = ff_sqr(u);
+  // sin u = u + u z S(z)
+  const float ts = __fmaf_rn(z.hi, __fmaf_rn(z.hi, K.s15, K.s13), K.s11);  // -1/11! + z/13! - z^2/15!
+  ff S = ffx_add_f(K.s9, z.hi * ts);
+  S = ff_add(K.s7, ff_mul(z, S));
+  S = ff_add(K.s5, ff_mul(z, S));
+  S = ff_add(K.s3, ff_mul(z, S));
+  const ff sv = ff_add(u, ff_mul(ff_mul(u, z), S));
+  // cos u = 1 + z C(z)
+  const float tc = __fmaf_rn(z.hi, __fmaf_rn(z.hi, __fmaf_rn(z.hi, K.c16, K.c14), K.c12), K.c10);
+  ff C = ffx_add_f(K.c8, z.hi * tc);
+  C = ff_add(K.c6, ff_mul(z, C));
+  C = ff_add(K.c4, ff_mul(z, C));
+  C = ff_add(K.c2, ff_mul(z, C));
+  const ff cv = ffx_add_f(ff_mul(z, C), 1.0f);
+  const int q = ((int)n) & 3;
+  const ff a = (q & 1) ? sv : cv, b = (q & 1) ? cv : sv;
+  c = (q == 1 || q == 2) ? ff_neg(a) : a;
+  s = (q >= 2) ? ff_neg(b) : b;
+}
+
+// Same outputs and launch shape as k_asm32_bulk (rows per CTA x ASMF_W warps per row, colours
+// separated by block barriers), with an FP64 shared-memory row accumulator [rows][N] and FP64 A.
+constexpr int ASMF_W = 2;
+__global__ void __launch_bounds__(256) k_asmff_bulk(
+    const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
+    const int32_t* __restrict__ esort, const int32_t* __restrict__ eperm, int64_t N, int64_t E, int Q,
+    const float* __restrict__ qtab /* colour-sorted float-float points, 13 x [Q][E] */,
+    const double* __restrict__ qgeo /* FP64 points (weights) */, const double* __restrict__ qshape,
+    const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv, const cd* __restrict__ known,
+    cd* __restrict__ A, cd* __restrict__ rowsum /* [nk][N][3] */, int rows, FFConst K) {
+  extern __shared__ cd accd[];
+  __shared__ ff shp[64 * 6];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw = warp / ASMF_W, sub = warp % ASMF_W;
+  const int kk = blockIdx.y;
+  const ff k = ff_from_double(kv[kk]);
+  const ff kinv = ff_from_double(1.0 / kv[kk]);
+  for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = ff_from_double(qshape[t]);
+  for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accd[t] = {0.0, 0.0};
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * rows + rw;
+  const bool valid = i < N;
+  cd* row = accd + (int64_t)rw * N;
+  const cd* kn = known + (int64_t)kk * N;
+  ff xi[3], nui[3];
+  for (int d = 0; d < 3; ++d) {
+    xi[d] = ff_from_double(valid ? nodes[3 * i + d] : 0.0);
+    nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
+  }
+  const int64_t EQ = E * Q;
+  ff alr = {0, 0}, ali = {0, 0}, ber = {0, 0}, bei = {0, 0}, bsr = {0, 0}, bsi = {0, 0};
+  for (int col = 0; col < ncolors; ++col) {
+    for (int32_t t = color_off[col] + sub * 32 + lane; valid && t < color_off[col + 1]; t += 32 * ASMF_W) {
+      int32_t el[6];
+      bool near = false;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        el[a] = esort[a * E + t];
+        near |= (el[a] == i);
+      }
+      if (near) continue;
+      const int64_t e = eperm[t];
+      ff hr[6], hi[6], gr[6], gi[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) hr[a] = hi[a] = gr[a] = gi[a] = ff{0.f, 0.f};
+      for (int qq = 0; qq < Q; ++qq) {
+        auto tab = [&](int f) { return qtab[((int64_t)f * Q + qq) * E + t]; };
+        const ff qx = {tab(0), tab(3)}, qy = {tab(1), tab(4)}, qz = {tab(2), tab(5)};
+        const ff nx = {tab(6), tab(10)}, ny = {tab(7), tab(11)}, nz = {tab(8), tab(12)};
+        const ff wj = ff_from_double(qgeo[GWJ * EQ + e * Q + qq]);
+        const ff rx = ff_sub(qx, xi[0]), ry = ff_sub(qy, xi[1]), rz = ff_sub(qz, xi[2]);
+        const ff R = ff_sqrt(ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz)));
+        const ff invR = ffx_recip(R);
+        const ff kR = ff_mul(k, R);
+        ff c, s;
+        cis_ff(kR, K, c, s);
+        const ff Gr = ff_mul(c, invR), Gi = ff_mul(s, invR);
+        const ff rnu = ff_add(ff_add(ff_mul(rx, nx), ff_mul(ry, ny)), ff_mul(rz, nz));
+        const ff rn = ff_mul(rnu, ff_mul(invR, ff_sqr(invR)));
+        // (c + i s)(i kR - 1) = (-c - s kR) + i (c kR - s)
+        const ff dGr = ff_mul(ff_neg(ff_add(c, ff_mul(s, kR))), rn);
+        const ff dGi = ff_mul(ff_sub(ff_mul(c, kR), s), rn);
+        const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
+        ff cg, sg;
+        cis_ff(ff_mul(k, nr), K, cg, sg);
+        const ff nn = ff_add(ff_add(ff_mul(nui[0], nx), ff_mul(nui[1], ny)), ff_mul(nui[2], nz));
+        const ff f = ff_mul(sg, kinv), dg = ff_neg(ff_mul(ff_mul(k, sg), nn)), df = ff_mul(cg, nn);
+        // row sums: w J [g dG - dg G], w J [f dG - df G]
+        ffx_mac(alr, wj, ff_sub(ff_mul(cg, dGr), ff_mul(dg, Gr)));
+        ffx_mac(ali, wj, ff_sub(ff_mul(cg, dGi), ff_mul(dg, Gi)));
+        ffx_mac(ber, wj, ff_sub(ff_mul(f, dGr), ff_mul(df, Gr)));
+        ffx_mac(bei, wj, ff_sub(ff_mul(f, dGi), ff_mul(df, Gi)));
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const ff cw = ff_mul(wj, shp[qq * 6 + a]);
+          ffx_mac(hr[a], cw, dGr);
+          ffx_mac(hi[a], cw, dGi);
+          ffx_mac(gr[a], cw, Gr);
+          ffx_mac(gi[a], cw, Gi);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const int32_t j = el[a];
+        const cd kvj = kn[j];
+        const cd H = {ff_to_double(hr[a]), ff_to_double(hi[a])}, G = {ff_to_double(gr[a]), ff_to_double(gi[a])};
+        if (bc[j] == 0) {  // hard column: A += H, b += Gm P'_known
+          row[j].re += H.re;
+          row[j].im += H.im;
+          const cd t2 = cmul(G, kvj);
+          bsr = ffx_add_f(ffx_add_f(bsr, (float)t2.re), (float)(t2.re - (double)(float)t2.re));
+          bsi = ffx_add_f(ffx_add_f(bsi, (float)t2.im), (float)(t2.im - (double)(float)t2.im));
+        } else {           // soft column: A -= Gm, b -= H P_known
+          row[j].re -= G.re;
+          row[j].im -= G.im;
+          const cd t2 = cmul(H, kvj);
+          bsr = ffx_add_f(ffx_add_f(bsr, -(float)t2.re), -(float)(t2.re - (double)(float)t2.re));
+          bsi = ffx_add_f(ffx_add_f(bsi, -(float)t2.im), -(float)(t2.im - (double)(float)t2.im));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // combine the lanes' and the row's warps' sums in FP64
+  double v[6] = {ff_to_double(alr), ff_to_double(ali), ff_to_double(ber), ff_to_double(bei), ff_to_double(bsr),
+                 ff_to_double(bsi)};
+#pragma unroll
+  for (int u = 0; u < 6; ++u)
+    for (int o = 16; o > 0; o >>= 1) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+  __shared__ double part[8][ASMF_W][6];
+  if (lane == 0)
+    for (int u = 0; u < 6; ++u) part[rw][sub][u] = v[u];
+  __syncthreads();
+  if (valid) {
+    cd* Arow = A + ((int64_t)kk * N + i) * N;
+    for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) Arow[j] = row[j];
+    if (sub == 0 && lane == 0) {
+      double w[6] = {0, 0, 0, 0, 0, 0};
+      for (int s2 = 0; s2 < ASMF_W; ++s2)
+        for (int u = 0; u < 6; ++u) w[u] += part[rw][s2][u];
+      cd* rs = rowsum + ((int64_t)kk * N + i) * 3;
+      rs[0] = {w[0], w[1]};
+      rs[1] = {w[2], w[3]};
+      rs[2] = {w[4], w[5]};
+    }
+  }
+}
+
+static FFConst make_ffconst() {
+  FFConst K;
+  const double pio2 = 1.57079632679489661923132169163975144;
+  auto round_bits = [](double x, int bits) {  // x rounded to `bits` significant bits
+    int ex;
+    const double m = std::frexp(x, &ex);
+    return std::ldexp(std::nearbyint(std::ldexp(m, bits)), ex - bits);
+  };
+  const double p1 = round_bits(pio2, 16);
+  const double p2 = round_bits(pio2 - p1, 16);
+  K.p1 = (float)p1;
+  K.p2 = (float)p2;
+  K.p3 = (float)(pio2 - p1 - p2);
+  K.two_over_pi = (float)(1.0 / pio2);
+  double fact[17];
+  fact[0] = 1.0;
+  for (int n = 1; n <= 16; ++n) fact[n] = fact[n - 1] * n;
+  auto sgn = [](int n) { return ((n / 2) % 2) ? -1.0 : 1.0; };  // sign of the x^n term of sin / cos
+  K.s3 = ff_from_double(sgn(3) / fact[3]);
+  K.s5 = ff_from_double(sgn(5) / fact[5]);
+  K.s7 = ff_from_double(sgn(7) / fact[7]);
+  K.s9 = ff_from_double(sgn(9) / fact[9]);
+  K.s11 = (float)(sgn(11) / fact[11]);
+  K.s13 = (float)(sgn(13) / fact[13]);
+  K.s15 = (float)(sgn(15) / fact[15]);
+  K.c2 = ff_from_double(sgn(2) / fact[2]);
+  K.c4 = ff_from_double(sgn(4) / fact[4]);
+  K.c6 = ff_from_double(sgn(6) / fact[6]);
+  K.c8 = ff_from_double(sgn(8) / fact[8]);
+  K.c10 = (float)(sgn(10) / fact[10]);
+  K.c12 = (float)(sgn(12) / fact[12]);
+  K.c14 = (float)(sgn(14) / fact[14]);
+  K.c16 = (float)(sgn(16) / fact[16]);
+  return K;
+}
+
+int ensure_mixed_tables(bie_ctx* c);
+const float* sorted_table_ptr(bie_ctx* c);
+const int32_t* sorted_elems_ptr(bie_ctx* c);
+
+// Bulk part of the FP64 system in float-float (the replacement of k_asm64_bulk in assemble64).
+int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* known, cd* rowsum) {
+  const int64_t N = c->N;
+  BIE_TRY(ensure_mixed_tables(c));
+  int rows = 8 / ASMF_W * 2;  // 8 rows x 2 warps = 512 threads at most; shrink to fit shared memory
+  while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
+  const size_t smem = (size_t)rows * N * sizeof(cd);
+  if (smem > 200 * 1024)
+    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP64 shared-memory row accumulator");
+  if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
+  rows = std::min(rows, 4);  // 256 threads per CTA (launch bound)
+  BIE_TRY((set_smem_max(k_asmff_bulk)));
+  static const FFConst K = make_ffconst();
+  dim3 gb((unsigned)((N + rows - 1) / rows), nk);
+  BIE_LAUNCH(k_asmff_bulk<<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
+      c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c), c->qgeo,
+      c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+}  // namespace bie

@@ -126,6 +126,8 @@ struct bie_ctx {
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
   int field_variant = 4;             // mixed field kernel shape: 0 k_field32b (8 wavenumbers per
                                      // group), 1-7 k_field32c shapes; 4 = 16 per group, 64 points/CTA
+  int assemble_ff = 0;               // bie_assemble: bulk pairs in float-float (1) or FP64 (0)
+  int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
   cudaStream_t cap_stream = nullptr; // private stream on which CUDA graphs are captured

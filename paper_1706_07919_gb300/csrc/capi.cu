@@ -92,7 +92,7 @@ int build_colouring(bie_ctx* c);
 int host_geometry_checks(bie_ctx* c, bool make_normals);
 void build_quad_rule(QuadRule& r, int ng, int ng_near);
 int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot);
-int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch);
+int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch, bool ff_bulk);
 int lu_factor64(bie_ctx* c, cd* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
 int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cd* b,
                int64_t bstride_b);
@@ -178,7 +178,7 @@ int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
-    BIE_TRY(assemble64(c, kdev, nk, A, b, scratch));
+    BIE_TRY(assemble64(c, kdev, nk, A, b, scratch, false));
     BIE_TRY(lu_factor64(c, A, nk, (int)N, (int)N, N * N, piv, info));
     BIE_TRY(lu_solve64(c, A, nk, (int)N, (int)N, N * N, piv, b, N));
     dim3 g((unsigned)((N + 255) / 256), nk);
@@ -277,6 +277,11 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   } else if (n == "field.variant") {
     if (value < 0 || value > 7 || value != (int)value) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0..7");
     c->field_variant = (int)value;
+  } else if (n == "assemble.bulk_ff") {
+    c->assemble_ff = value != 0.0 ? 1 : 0;
+  } else if (n == "mixed.reassembly") {
+    if (value != 0.0 && value != 1.0) return fail(BIE_ERR_INVALID_ARG, "mixed.reassembly must be 0 (FP64) or 1 (float-float)");
+    c->reassembly_ff = (int)value;
   } else if (n == "mixed.graph") {
     c->mixed_graph = value != 0.0 ? 1 : 0;
   } else if (n == "learned.stride") {
@@ -372,7 +377,7 @@ int bie_assemble(bie_ctx* c, double k, void* A_out, void* b_out) {
   BIE_TRY(ensure_buf(c->work, (size_t)N * 4 * sizeof(cd) + 64));
   double* kdev = (double*)((char*)c->work.p + (size_t)N * 4 * sizeof(cd));
   BIE_CUDA_TRY(cudaMemcpyAsync(kdev, &k, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  BIE_TRY(assemble64(c, kdev, 1, (cd*)A_out, (cd*)b_out, c->work.p));
+  BIE_TRY(assemble64(c, kdev, 1, (cd*)A_out, (cd*)b_out, c->work.p, c->assemble_ff != 0));
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }

@@ -12,7 +12,7 @@
 namespace bie {
 
 int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum);
-int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch);
+int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch, bool ff_bulk);
 int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
                  void* scratch, size_t scratch_bytes);
@@ -182,7 +182,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
       BIE_CUDA_TRY(cudaMemcpyAsync(kg, kv.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-      BIE_TRY(assemble64(c, kg, ng, A64, b64, s64));
+      BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
       BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
                                  c->refine64_it_max, c->refine64_tol));
       BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));

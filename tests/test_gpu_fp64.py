@@ -50,6 +50,22 @@ def test_assembly_matches_oracle(Solver, L, k):
     assert rel(b.cpu().numpy(), br) <= 1e-12
 
 
+@pytest.mark.parametrize("L,k", [(1, 0.5), (2, 7.875), (3, 15.9)])
+def test_float_float_bulk_assembly_matches_oracle(Solver, L, k):
+    """The float-float bulk assembly (used to re-assemble flagged wavenumbers) meets the FP64 bar."""
+    m = octa_sphere(L)
+    s = _solver(Solver, m)
+    s.set_option("assemble.bulk_ff", 1)
+    A, b = s.assemble(k)
+    s.set_option("assemble.bulk_ff", 0)
+    A64, b64 = s.assemble(k)
+    Ar, br = oracle.assemble_system(m, k, D)
+    A, A64 = A.cpu().numpy(), A64.cpu().numpy()
+    assert np.abs(A - Ar).max() <= 1e-12 * np.abs(Ar).max()
+    assert rel(b.cpu().numpy(), br) <= 1e-12
+    assert np.abs(A - A64).max() <= 1e-12 * np.abs(Ar).max()
+
+
 def test_assembly_mixed_bc_two_bodies_and_custom_rule(Solver):
     s0 = ico_sphere(2)
     m = merge_meshes([scale_translate(s0, 0.8, (0, 0, -1.0), bc=1), scale_translate(s0, 1.1, (0.3, 0, 1.3), bc=0)])

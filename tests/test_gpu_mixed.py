@@ -123,7 +123,8 @@ def test_mixed_field_matches_oracle(Solver, B, two_spheres, accurate, bound):
         assert rel(T[i], Tr) <= bound, (k, rel(T[i], Tr))
 
 
-def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B):
+@pytest.mark.parametrize("ff", [0, 1])
+def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B, ff):
     """Forcing every wavenumber through the FP64 re-assembly (threshold below any estimate):
     refinement with the TF32 factor against the FP64 system must reach the FP64 path's answer to
     the refinement's FP64 stop (backward error 1e-13) times the condition number."""
@@ -131,6 +132,7 @@ def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B):
     ks = w.k[[3, 30, 35, 60]]
     s = _solver(Solver, w.mesh, tc=1)
     s.set_option("mixed.fallback_err_est", 1e-15)
+    s.set_option("mixed.reassembly", ff)
     surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
     surf = surf.cpu().numpy()
     for i, k in enumerate(ks):
