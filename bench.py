@@ -418,7 +418,8 @@ def run_reference(args):
 def run_case(args):
     """Small cases for profiler captures (no timing, no output line): `lu` factors and refines four
     two-sphere systems (k = 3.15 .. 3.25); `field` evaluates the field of eight wavenumbers at 2048
-    of the 16 384 plane points from a constant surface solution."""
+    of the 16 384 plane points from a constant surface solution; `batch` runs one batch of the
+    benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points)."""
     import torch
 
     import __graft_entry__
@@ -431,7 +432,13 @@ def run_case(args):
     sol = Solver(0)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_option("mixed.tcgen05", args.tc)
-    if args.case == "lu":
+    if args.case == "batch":
+        ks = w.k[256:384]
+        surf, rep = sol.solve_frequencies(ks, B.BIE_MODE_MIXED)
+        xo = torch.tensor(w.xobs, device="cuda")
+        T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
+        print("case batch: flagged", sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY), tuple(T.shape))
+    elif args.case == "lu":
         sol.set_option("mixed.fallback_err_est", 1.0)
         surf, rep = sol.solve_frequencies(w.k[100:104], B.BIE_MODE_MIXED)
         print("case lu: refinement corrections", [r.iters for r in rep])
@@ -459,7 +466,7 @@ def main():
     ap.add_argument("--no-learned", dest="no_learned", action="store_true",
                     help="skip the learned-warm-start sweep on the spheroid workload")
     ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned warm start")
-    ap.add_argument("--case", choices=["lu", "field"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "batch"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -32,7 +32,7 @@ __global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, cons
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int kFallbackGroup = 8;  // FP64 systems re-assembled at once
+constexpr int kFallbackGroupMax = 32;  // FP64 systems re-assembled and refined together (at most)
 
 // lu_keep / perm_keep (optional, device): receive the low-precision factor ([Nk][N][ld], ld = N
 // rounded up to 64) and row permutation ([Nk][N]) of every wavenumber.
@@ -44,11 +44,14 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   const size_t vec = align256((size_t)N * sizeof(cd));
   const size_t perk = 2 * mat + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
                       2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
-  // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel
-  const size_t fb = (size_t)kFallbackGroup *
-                        (align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024) + 4096;
+  // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel.  One
+  // group refines its systems in the same launches (one CTA per system in the triangular
+  // solves), so a larger group fills more of the GPU; it is capped at an eighth of free memory.
+  const size_t fb1 = align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024;
   size_t free_b = 0, total_b = 0;
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const int G = (int)std::max<size_t>(1, std::min<size_t>(kFallbackGroupMax, (free_b / 8) / fb1));
+  const size_t fb = (size_t)G * fb1 + 4096;
   const size_t avail = free_b > fb ? free_b - fb : 0;
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(c->mixed_batch, (int64_t)((avail / 2) / perk))));
   size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N);
@@ -71,7 +74,6 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   int32_t* info = (int32_t*)take((size_t)kb * 4);
   double* kdev = (double*)take((size_t)kb * 8);
   void* tcs = take(tc_scratch);
-  const int G = kFallbackGroup;
   cd* A64 = (cd*)take((size_t)G * N * N * sizeof(cd));
   cd* b64 = (cd*)take((size_t)G * vec);
   cd* s64 = (cd*)take((size_t)G * 4 * vec);  // known + rowsum of the FP64 assembly
