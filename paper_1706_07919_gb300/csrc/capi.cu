@@ -102,7 +102,7 @@ int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout);
 int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t M, const cd* Sp, int64_t P, int n,
                void* out, int out_dtype);
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep);
+                int32_t* perm_keep, cf* d_keep);
 int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
 void mlp_free(bie_ctx* c);
 int mlp_set_params(bie_ctx* c, const float* theta_host);
@@ -388,7 +388,7 @@ int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, voi
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
   if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
-  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr);
+  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr);
   if (mode == BIE_MODE_LEARNED) return solve_learned(c, k, Nk, (cd*)surf_out, rep);
   return fail(BIE_ERR_INVALID_ARG, "unknown mode " + std::to_string(mode));
 }

@@ -13,7 +13,8 @@ namespace bie {
 __global__ void k_trsv_lu(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride, const int32_t* __restrict__ perm,
                           const cd* __restrict__ rhs, cd* __restrict__ out, int accumulate,
                           const RefineState* __restrict__ st, const int32_t* __restrict__ sel, int64_t rstride,
-                          int64_t roff, int64_t ostride, int64_t ooff);
+                          int64_t roff, int64_t ostride, int64_t ooff, const cf* __restrict__ Dinv, int64_t dstride);
+int64_t diag_inv_stride(int n);
 __global__ void k_residual_ff(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride, const cd* __restrict__ b,
                               const cd* __restrict__ x, cd* __restrict__ r, double* __restrict__ rowabs,
                               const RefineState* __restrict__ st);
@@ -243,11 +244,13 @@ size_t gmres_scratch_bytes(int nk, int n, int m) {
 }
 
 // Solves A_kk x_kk = b_kk for kk < nk (A: FP32 systems with pitch ld, batch stride bstride),
-// starting from x (in/out), preconditioned by factor sel[kk] of LU/perm.  state_dev receives a
+// starting from x (in/out), preconditioned by factor sel[kk] of LU/perm (with the factors'
+// diagonal-block inverses Dinv, or NULL).  state_dev receives a
 // RefineState per system (done, iters = Arnoldi steps, backward error).
 int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstride, const cd* b, cd* x,
-                const cf* LU, int64_t lu_bstride, const int32_t* perm, const int32_t* sel, int m, int cycles,
-                double inner_tol, double tol, void* scratch, void* state_dev) {
+                const cf* LU, int64_t lu_bstride, const int32_t* perm, const cf* Dinv, const int32_t* sel, int m,
+                int cycles, double inner_tol, double tol, void* scratch, void* state_dev) {
+  const int64_t dstride = diag_inv_stride(n);
   if (m < 1 || m > 62) return fail(BIE_ERR_INVALID_ARG, "gmres.m must be in [1, 62]");
   char* p = (char*)scratch;
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
@@ -279,7 +282,7 @@ int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstr
       // z_j = M^{-1} v_j
       BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, lu_bstride, perm, V, Z, 0, gate, sel,
                                                              (int64_t)(m + 1) * n, (int64_t)j * n, (int64_t)m * n,
-                                                             (int64_t)j * n));
+                                                             (int64_t)j * n, Dinv, dstride));
       BIE_LAUNCH(k_gm_matvec<<<gr, 512, sm_mv, c->stream>>>(A, n, ld, bstride, Z, V, m, j, gate));
       BIE_LAUNCH(k_gm_arnoldi<<<nk, 1024, 0, c->stream>>>(n, m, j, V, H, cs, sn, g, gs, gate, inner_tol));
     }

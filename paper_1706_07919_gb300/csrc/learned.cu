@@ -19,11 +19,12 @@
 namespace bie {
 
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep);
+                int32_t* perm_keep, cf* d_keep);
 int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum);
 int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstride, const cd* b, cd* x, const cf* LU,
-                int64_t lu_bstride, const int32_t* perm, const int32_t* sel, int m, int cycles, double inner_tol,
-                double tol, void* scratch, void* state_dev);
+                int64_t lu_bstride, const int32_t* perm, const cf* Dinv, const int32_t* sel, int m, int cycles,
+                double inner_tol, double tol, void* scratch, void* state_dev);
+int64_t diag_inv_stride(int n);
 size_t gmres_scratch_bytes(int nk, int n, int m);
 size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
@@ -146,13 +147,16 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   }
   // ---- 1. anchors: direct solves that keep their factors -----------------------------------
   const size_t lu_bytes = align256((size_t)na * N * ld * sizeof(cf));
-  const size_t keep_bytes = lu_bytes + align256((size_t)na * N * 4) + align256((size_t)na * 2 * N * sizeof(cd)) +
-                            align256((size_t)Nk * 4) + 4096;
+  const int64_t dstride = diag_inv_stride((int)N);
+  const size_t d_bytes = align256((size_t)na * dstride * sizeof(cf));
+  const size_t keep_bytes = lu_bytes + d_bytes + align256((size_t)na * N * 4) +
+                            align256((size_t)na * 2 * N * sizeof(cd)) + align256((size_t)Nk * 4) + 4096;
   BIE_TRY(ensure_buf(c->work4, keep_bytes));
   char* kp = (char*)c->work4.p;
   cf* LUk = (cf*)kp;
-  int32_t* permk = (int32_t*)(kp + lu_bytes);
-  cd* surf_a = (cd*)(kp + lu_bytes + align256((size_t)na * N * 4));
+  cf* Dk = (cf*)(kp + lu_bytes);
+  int32_t* permk = (int32_t*)(kp + lu_bytes + d_bytes);
+  cd* surf_a = (cd*)(kp + lu_bytes + d_bytes + align256((size_t)na * N * 4));
   int32_t* idx_dev = (int32_t*)((char*)surf_a + align256((size_t)na * 2 * N * sizeof(cd)));
   std::vector<double> ka((size_t)na);
   for (int64_t a = 0; a < na; ++a) ka[a] = k[anc[a]];
@@ -169,7 +173,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     return (double)ms;
   };
   BIE_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
-  BIE_TRY(solve_mixed(c, ka.data(), na, surf_a, rep_a.data(), LUk, permk));
+  BIE_TRY(solve_mixed(c, ka.data(), na, surf_a, rep_a.data(), LUk, permk, Dk));
   BIE_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
   BIE_CUDA_TRY(cudaEventSynchronize(ev[1]));
   info.anchors_ms = elapsed(0, 1);
@@ -264,7 +268,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     }
     BIE_CUDA_TRY(cudaMemcpyAsync(x0, x, (size_t)nk * N * sizeof(cd), cudaMemcpyDeviceToDevice, c->stream));
     BIE_CUDA_TRY(cudaEventRecord(ev[2], c->stream));
-    BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, b, x, LUk, lu_bstride, permk, sel, m, c->gmres_cycles,
+    BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, b, x, LUk, lu_bstride, permk, Dk, sel, m, c->gmres_cycles,
                         c->gmres_inner_tol, c->refine_tol, gscr, state));
     BIE_CUDA_TRY(cudaEventRecord(ev[3], c->stream));
     BIE_LAUNCH(k_rel_diff<<<nk, 256, 0, c->stream>>>(x0, x, N, rel));  // error of the initial guess
@@ -273,8 +277,8 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     dim3 gr((unsigned)((N + 15) / 16), (unsigned)nk);
     BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, (int)N, ld, bstride, x, x0, 6e-8f));
     BIE_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)nk * N * sizeof(cd), c->stream));
-    BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, x0, z, LUk, lu_bstride, permk, sel, std::min(m, 20), 1, 1e-2,
-                        0.0, gscr, state_e));
+    BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, x0, z, LUk, lu_bstride, permk, Dk, sel, std::min(m, 20), 1,
+                        1e-2, 0.0, gscr, state_e));
     BIE_LAUNCH(k_norm_ratio<<<nk, 256, 0, c->stream>>>(z, x, N, rel + kb));
     BIE_CUDA_TRY(cudaEventRecord(ev[4], c->stream));
     {
@@ -319,7 +323,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     cd* surf_r = (cd*)tmp;
     int32_t* ridx = (int32_t*)((char*)tmp + (size_t)nr * 2 * N * sizeof(cd));
     std::vector<bie_report> rr((size_t)nr);
-    int rc = solve_mixed(c, redo.data(), nr, surf_r, rr.data(), nullptr, nullptr);
+    int rc = solve_mixed(c, redo.data(), nr, surf_r, rr.data(), nullptr, nullptr, nullptr);
     if (rc == BIE_OK) {
       std::vector<int32_t> hi(redo_idx.begin(), redo_idx.end());
       rc = cudaMemcpyAsync(ridx, hi.data(), nr * 4, cudaMemcpyHostToDevice, c->stream) == cudaSuccess ? BIE_OK

@@ -19,10 +19,11 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
 size_t lu_tc_scratch_bytes(int batch, int n);
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
-                 int it_max, double tol);
+                 int it_max, double tol, cf* D);
+int64_t diag_inv_stride(int n);
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol);
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D);
 size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est);
@@ -34,15 +35,18 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kFallbackGroupMax = 32;  // FP64 systems re-assembled and refined together (at most)
 
-// lu_keep / perm_keep (optional, device): receive the low-precision factor ([Nk][N][ld], ld = N
-// rounded up to 64) and row permutation ([Nk][N]) of every wavenumber.
+// lu_keep / perm_keep / d_keep (optional, device): receive the low-precision factor ([Nk][N][ld],
+// ld = N rounded up to 64), row permutation ([Nk][N]) and diagonal-block inverses
+// ([Nk][diag_inv_stride(N)]) of every wavenumber.
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep) {
+                int32_t* perm_keep, cf* d_keep) {
   const int64_t N = c->N;
   const int64_t ld = (N + 63) / 64 * 64;
   const size_t mat = align256((size_t)N * ld * sizeof(cf));  // == N * ld * 8: ld is a multiple of 64
   const size_t vec = align256((size_t)N * sizeof(cd));
-  const size_t perk = 2 * mat + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
+  const int64_t dstride = diag_inv_stride((int)N);
+  const size_t dsz = align256((size_t)dstride * sizeof(cf));
+  const size_t perk = 2 * mat + dsz + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
                       2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
   // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel.  One
   // group refines its systems in the same launches (one CTA per system in the triangular
@@ -62,6 +66,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);
   cf* LU = (cf*)take(kb * mat);
+  cf* Dinv = (cf*)take(kb * dsz);
   cd* b = (cd*)take(kb * vec);
   cd* x = (cd*)take(kb * vec);
   cd* r = (cd*)take(kb * vec);
@@ -103,7 +108,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     else
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
-                         c->refine_tol));
+                         c->refine_tol, Dinv));
     return BIE_OK;
   };
   bool use_graph = c->mixed_graph && Nk >= 2 * kb;
@@ -158,6 +163,9 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
                                    c->stream));
       BIE_CUDA_TRY(cudaMemcpyAsync(perm_keep + k0 * N, perm, (size_t)nk * N * sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                    c->stream));
+      if (d_keep)
+        BIE_CUDA_TRY(cudaMemcpyAsync(d_keep + k0 * dstride, Dinv, (size_t)nk * dstride * sizeof(cf),
+                                     cudaMemcpyDeviceToDevice, c->stream));
     }
     BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
     BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -186,7 +194,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
       BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
       BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
-                                 c->refine64_it_max, c->refine64_tol));
+                                 c->refine64_it_max, c->refine64_tol, Dinv));
       BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
       for (int g = 0; g < ng; ++g) {
         const int64_t idx = k0 + flagged[f0 + g];

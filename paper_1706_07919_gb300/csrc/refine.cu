@@ -25,18 +25,87 @@ __global__ void k_piv_to_perm(const int32_t* __restrict__ piv, int n, int32_t* _
 }
 
 // ---- triangular solves x = U^{-1} L^{-1} P r with one CTA (1024 threads) per system ---------
-// The vector lives in shared memory; the factor is swept in 64-column blocks: a warp solves the
-// diagonal block, then all warps update the remaining rows, eight rows per warp in flight.
+// The vector lives in shared memory; the factor is swept in 64-column blocks: the diagonal block
+// is applied as a product with its precomputed inverse (all warps; k_diag_inv), or solved row by
+// row by one warp when no inverse is given, then all warps update the remaining rows, eight rows
+// per warp in flight.
 constexpr int TB = 64;
 
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower) and U of every factor, by column-wise
+// substitution in shared memory (thread j computes column j).  D: [nk][nblk][2][64][64] (L, U),
+// rows and columns beyond the matrix are zero.  grid (nblk, nk, 2), block 64.
+__global__ void __launch_bounds__(64) k_diag_inv(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
+                                                 cf* __restrict__ D, int64_t dstride) {
+  extern __shared__ cf smi[];
+  cf* Ms = smi;            // [64][65]
+  cf* X = smi + 64 * 65;   // [64][65]
+  const int blk = blockIdx.x, kk = blockIdx.y, upper = blockIdx.z, j = threadIdx.x;
+  const int j0 = blk * TB, bs = min(TB, n - j0);
+  const cf* Mg = LU + (int64_t)kk * bstride + (int64_t)j0 * ld + j0;
+  for (int idx = j; idx < TB * TB; idx += TB) {
+    const int r = idx / TB, cc = idx % TB;
+    Ms[r * 65 + cc] = (r < bs && cc < bs) ? Mg[(int64_t)r * ld + cc] : cf{0.f, 0.f};
+  }
+  __syncthreads();
+  if (!upper) {
+    for (int i = 0; i < TB; ++i) {
+      float xr = (i == j) ? 1.f : 0.f, xi = 0.f;
+      for (int m = j; m < i; ++m) {
+        const cf a = Ms[i * 65 + m], b = X[m * 65 + j];
+        xr -= a.re * b.re - a.im * b.im;
+        xi -= a.re * b.im + a.im * b.re;
+      }
+      X[i * 65 + j] = (i < bs && j < bs) ? cf{xr, xi} : cf{0.f, 0.f};
+    }
+  } else {
+    for (int i = TB - 1; i >= 0; --i) {
+      float xr = (i == j) ? 1.f : 0.f, xi = 0.f;
+      if (i < bs && j < bs) {
+        for (int m = i + 1; m <= j; ++m) {
+          const cf a = Ms[i * 65 + m], b = X[m * 65 + j];
+          xr -= a.re * b.re - a.im * b.im;
+          xi -= a.re * b.im + a.im * b.re;
+        }
+        const cf d = Ms[i * 65 + i];
+        const float den = d.re * d.re + d.im * d.im;
+        X[i * 65 + j] = {(xr * d.re + xi * d.im) / den, (xi * d.re - xr * d.im) / den};
+      } else {
+        X[i * 65 + j] = {0.f, 0.f};
+      }
+    }
+  }
+  __syncthreads();
+  cf* Db = D + (int64_t)kk * dstride + ((int64_t)blk * 2 + upper) * TB * TB;
+  for (int idx = j; idx < TB * TB; idx += TB) Db[idx] = X[(idx / TB) * 65 + idx % TB];
+}
+
 template <bool LOWER>
-__device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y) {
+__device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y, const cf* __restrict__ D, cf* ytmp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nblk = (n + TB - 1) / TB;
   for (int bi = 0; bi < nblk; ++bi) {
     const int blk = LOWER ? bi : nblk - 1 - bi;
     const int j0 = blk * TB, j1 = min(j0 + TB, n);
-    if (warp == 0) {  // diagonal block, row by row
+    if (D) {  // diagonal block: y_blk = inv(block) y_blk, one warp per row
+      const cf* Db = D + ((int64_t)blk * 2 + (LOWER ? 0 : 1)) * TB * TB;
+      const int bs = j1 - j0;
+      for (int r = warp; r < bs; r += nw) {
+        float sr = 0.f, si = 0.f;
+        for (int cc = lane; cc < bs; cc += 32) {
+          const cf d = Db[r * TB + cc];
+          const cf v = y[j0 + cc];
+          sr += d.re * v.re - d.im * v.im;
+          si += d.re * v.im + d.im * v.re;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) ytmp[r] = {sr, si};
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < bs) y[j0 + threadIdx.x] = ytmp[threadIdx.x];
+    } else if (warp == 0) {  // diagonal block, row by row
       for (int t = 0; t < j1 - j0; ++t) {
         const int r = LOWER ? j0 + t : j1 - 1 - t;
         float sr = 0.f, si = 0.f;
@@ -107,8 +176,10 @@ __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int
                                                   cd* __restrict__ out, int accumulate,
                                                   const RefineState* __restrict__ st,
                                                   const int32_t* __restrict__ sel, int64_t rstride, int64_t roff,
-                                                  int64_t ostride, int64_t ooff) {
+                                                  int64_t ostride, int64_t ooff, const cf* __restrict__ Dinv,
+                                                  int64_t dstride) {
   extern __shared__ cf yv[];
+  __shared__ cf ytmp[TB];
   const int kk = blockIdx.x;
   if (st && st[kk].done) return;
   const int fk = sel ? sel[kk] : kk;
@@ -130,8 +201,9 @@ __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int
     yv[i] = {(float)(v.re / sc), (float)(v.im / sc)};
   }
   __syncthreads();
-  trsv_sweep<true>(M, n, ld, yv);
-  trsv_sweep<false>(M, n, ld, yv);
+  const cf* Df = Dinv ? Dinv + (int64_t)fk * dstride : nullptr;
+  trsv_sweep<true>(M, n, ld, yv, Df, ytmp);
+  trsv_sweep<false>(M, n, ld, yv, Df, ytmp);
   cd* o = out + (int64_t)kk * ostride + ooff;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const cd v = {(double)yv[i].re * sc, (double)yv[i].im * sc};
@@ -283,29 +355,42 @@ __global__ void k_err_est(int n, const cd* __restrict__ x, const cd* __restrict_
   }
 }
 
+int64_t diag_inv_stride(int n) { return (int64_t)((n + TB - 1) / TB) * 2 * TB * TB; }
+
+// Inverses of the diagonal blocks of nk factors (D: [nk][diag_inv_stride(n)] cf).
+int diag_inverses(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t bstride, cf* D) {
+  BIE_TRY((set_smem_max(k_diag_inv)));
+  dim3 g((unsigned)((n + TB - 1) / TB), (unsigned)nk, 2);
+  BIE_LAUNCH(k_diag_inv<<<g, TB, 2 * 64 * 65 * sizeof(cf), c->stream>>>(LU, n, ld, bstride, D, diag_inv_stride(n)));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
-                 int it_max, double tol) {
+                 int it_max, double tol, cf* D) {
   RefineState* st = (RefineState*)state_dev;
+  const int64_t dstride = diag_inv_stride(n);
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
   BIE_LAUNCH(k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm));
+  if (D) BIE_TRY(diag_inverses(c, LU, nk, n, ld, bstride, D));
   const size_t sm_trsv = (size_t)n * sizeof(cf);
   const size_t sm_res = (size_t)n * sizeof(float4);
   if (sm_trsv > 200 * 1024 || sm_res > 200 * 1024)
     return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
   BIE_TRY((set_smem_max(k_trsv_lu)));
   BIE_TRY((set_smem_max(k_residual_ff)));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0));
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int it = 0; it <= it_max; ++it) {
     BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0));
+    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0, D, dstride));
   }
   // assembly-sensitivity estimate (r is free now)
   BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, n, 0, n, 0));
+  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
   BIE_LAUNCH(k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -359,7 +444,8 @@ __global__ void k_gather_scatter(cd* __restrict__ xb, cd* __restrict__ xg, const
 // rowabs [ng][n], state [ng].
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol) {
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D) {
+  const int64_t dstride = diag_inv_stride(n);
   RefineState* st = (RefineState*)state_dev;
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, ng * sizeof(RefineState), c->stream));
   dim3 gv((unsigned)((n + 255) / 256), ng);
@@ -370,7 +456,7 @@ int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, i
     BIE_LAUNCH(k_residual64<<<gr, 512, 0, c->stream>>>(A64, n, b64, xg, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<ng, 256, 0, c->stream>>>(n, b64, xg, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev, n, 0, n, 0));
+    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev, n, 0, n, 0, D, dstride));
   }
   BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 0));
   BIE_CUDA_TRY(cudaGetLastError());

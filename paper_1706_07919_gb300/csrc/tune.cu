@@ -19,7 +19,7 @@
 namespace bie {
 
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep);
+                int32_t* perm_keep, cf* d_keep);
 
 struct TuneEntry {
   int batch = 0, tc = 0;
@@ -106,10 +106,10 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
       c->mixed_batch = b;
       c->tc_version = tc;
       c->mixed_graph = 0;
-      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr);  // warm-up: workspace, tables
+      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr);  // warm-up: workspace, tables
       if (rc != BIE_OK) break;
       cudaEventRecord(e0, c->stream);
-      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr);
+      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr);
       if (rc != BIE_OK) break;
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);
