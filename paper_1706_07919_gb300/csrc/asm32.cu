@@ -10,6 +10,8 @@
 //   * the row sums alpha_i, beta_i and b_i (over all E*Q points, with cancellation) are
 //     compensated (Kahan-Babuska-Neumaier) sums.
 // Output: A as interleaved complex FP32 [N][ld], b as complex FP64 [N].
+#include <algorithm>
+
 #include "bie_common.cuh"
 
 namespace bie {
@@ -82,8 +84,10 @@ struct Kern32 {
   float alr, ali, ber, bei;  // g dG - dg G, f dG - df G (without w J)
 };
 
+// far_r2: beyond R^2 > far_r2 (a few element sizes) r.nu_q is formed in FP32: its absolute error
+// eps R then perturbs dG by eps / R^2, the entry's own rounding.
 __device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff* xi, const ff* nui, const TwoPi3& tp,
-                                         const float* q, Kern32& o) {
+                                         const float* q, Kern32& o, float far_r2 = 3.0e38f) {
   // r = x_q - x_i in float-float
   const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
   const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
@@ -97,8 +101,12 @@ __device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff*
   const float kR = k.hi * R.hi;
   o.Gr = c * invR;
   o.Gi = s * invR;
-  const ff rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]}));
-  const float rn = rnu.hi * invR * invR * invR;
+  float rnu;
+  if (R2.hi > far_r2)
+    rnu = rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8];
+  else
+    rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]})).hi;
+  const float rn = rnu * invR * invR * invR;
   o.dGr = (-c - s * kR) * rn;
   o.dGi = (c * kR - s) * rn;
   float cg, sg;
@@ -129,7 +137,8 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
     const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
     const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
     const double* __restrict__ kv, const cd* __restrict__ known,
-    cf* __restrict__ A, int64_t lda, double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp) {
+    cf* __restrict__ A, int64_t lda, double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp,
+    float far_r2) {
   extern __shared__ cf acc32[];
   __shared__ float shp[64 * 6];
   __shared__ double part[16][ASM_W][6];
@@ -164,15 +173,17 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
       float hr[6], hi[6], gr[6], gi[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.f; }
+      // the element's share of the row sums in FP32 (Q terms), then one compensated addition each
+      float ear = 0.f, eai = 0.f, ebr = 0.f, ebi = 0.f;
       for (int qq = 0; qq < Q; ++qq) {
         float q[P32COUNT];
 #pragma unroll
         for (int f = 0; f < P32COUNT; ++f) q[f] = qtab[((int64_t)f * Q + qq) * E + t];
         Kern32 K;
-        kernel32(k, kinv, xi, nui, tp, q, K);
+        kernel32(k, kinv, xi, nui, tp, q, K, far_r2);
         const float wj = q[P32W];
-        S.ar.add(wj * K.alr); S.ai.add(wj * K.ali);
-        S.br.add(wj * K.ber); S.bi.add(wj * K.bei);
+        ear = __fmaf_rn(wj, K.alr, ear); eai = __fmaf_rn(wj, K.ali, eai);
+        ebr = __fmaf_rn(wj, K.ber, ebr); ebi = __fmaf_rn(wj, K.bei, ebi);
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
           const float cw = wj * shp[qq * 6 + a];
@@ -180,6 +191,8 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
           gr[a] = __fmaf_rn(cw, K.Gr, gr[a]);  gi[a] = __fmaf_rn(cw, K.Gi, gi[a]);
         }
       }
+      S.ar.add(ear); S.ai.add(eai);
+      S.br.add(ebr); S.bi.add(ebi);
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
         const int32_t j = el[a];
@@ -360,12 +373,26 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
     return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP32 shared-memory row accumulator");
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
   const TwoPi3 tp = two_pi3();
+  if (!(c->far_r2 > 0.0)) {  // (3 x longest element edge)^2, once per geometry
+    double h2 = 0.0;
+    for (int64_t e = 0; e < c->E; ++e)
+      for (int a = 0; a < 3; ++a) {
+        const int32_t p = c->h_elems[6 * e + a], q = c->h_elems[6 * e + (a + 1) % 3];
+        double d2 = 0.0;
+        for (int x = 0; x < 3; ++x) {
+          const double d = c->h_nodes[3 * p + x] - c->h_nodes[3 * q + x];
+          d2 += d * d;
+        }
+        h2 = std::max(h2, d2);
+      }
+    c->far_r2 = 9.0 * h2;
+  }
   BIE_TRY((set_smem_max(k_asm32_bulk)));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   BIE_LAUNCH(k_asm32_bulk<<<gb, 32 * rows * ASM_W, smem, c->stream>>>(c->nodes, c->normals, c->bc, sorted_elems(c), N,
                                                                       c->E, c->rule.Q, sorted_table(c), c->qshape32,
                                                                       c->color_off, c->ncolors, kv, known, A, lda,
-                                                                      rowsum, rows, tp));
+                                                                      rowsum, rows, tp, (float)c->far_r2));
   BIE_CUDA_TRY(cudaGetLastError());
   const int64_t nq = c->E * c->rule.Q;
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);

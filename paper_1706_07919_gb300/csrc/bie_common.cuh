@@ -112,6 +112,7 @@ struct bie_ctx {
   int32_t* n2e_off = nullptr;        // [N+1] CSR: elements containing node i
   int32_t* n2e = nullptr;            // element * 8 + local index
   int max_n2e = 0;
+  double far_r2 = 0.0;               // (3 x longest element edge)^2, set on first mixed assembly
   int* d_nnear = nullptr;            // [6] near-rule point counts
 
   // mixed-precision path settings

@@ -126,6 +126,7 @@ static void free_geometry(bie_ctx* c) {
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
   c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr;
+  c->far_r2 = 0.0;
   c->has_geom = false;
 }
 
