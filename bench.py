@@ -92,20 +92,60 @@ def build_workload():
     return config_two_spheres_mixed()
 
 
+class RankGroup:
+    """One process per GPU, launched by torchrun (RANK, WORLD_SIZE, LOCAL_RANK, MASTER_* from the
+    environment).  The frequency sweep shards into independent replicas, so there is no
+    data-path collective: the group only brackets the timed region with barriers, takes the
+    maximum of the ranks' times, and lets rank 0 report."""
+
+    def __init__(self, backend: str = "nccl", device=None):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if backend == "nccl" and device is not None else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    @property
+    def is_root(self) -> bool:
+        return self.rank == 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x: float, device=None) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device if self.backend == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_throughput(units_per_rank_step: int, world: int, steps: int, t_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank_step * world * steps / (t_ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- GPU arm ----
 def run_ours(args):
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    grp = RankGroup("nccl", dev)
+    rank, world = grp.rank, grp.world
 
     import __graft_entry__
 
@@ -152,8 +192,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     phase = np.zeros(3)
-    if dist is not None:
-        dist.barrier()
+    grp.barrier()
     torch.cuda.synchronize(dev)
     launches0 = B.bie_kernel_launches()
     with ClockSampler(local) as clk:
@@ -166,14 +205,9 @@ def run_ours(args):
             phase += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
         t1.record(stream)
         torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-    t_ms = t0.elapsed_time(t1)
+        grp.barrier()
+    t_ms = grp.max_over_ranks(t0.elapsed_time(t1), dev)
     launches = B.bie_kernel_launches() - launches0
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
     rep = reports["rep"]
 
     # ---- accuracy on sampled wavenumbers against the FP64 GPU path (outside the timed region) ----
@@ -197,9 +231,8 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: the field phase of the timed steps ----
     roof = roofline_field(w, phase[1] / args.steps, M, Nk)
 
-    units = Nk * world * args.steps
-    value = units / (t_ms / 1e3)
-    pts = M * Nt * P * world * args.steps / (t_ms / 1e3)
+    value = job_throughput(Nk, world, args.steps, t_ms)
+    pts = job_throughput(M * Nt * P, world, args.steps, t_ms)
     nfall = sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64)
     nre64 = sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY)
     line = {
@@ -228,11 +261,10 @@ def run_ours(args):
     sol.close()
     if not args.no_learned:
         line["learned"] = run_learned(args, dev, stream)
-    if rank == 0:
+    if grp.is_root:
         line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
         print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+    grp.close()
 
 
 def run_learned(args, dev, stream):
