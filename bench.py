@@ -261,6 +261,8 @@ def run_ours(args):
     sol.close()
     if not args.no_learned:
         line["learned"] = run_learned(args, dev, stream)
+    if not args.no_uneven:
+        line["uneven"] = run_uneven(args, dev)
     if grp.is_root:
         line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
         print(json.dumps(line))
@@ -327,6 +329,43 @@ def run_learned(args, dev, stream):
             "zero_start_krylov_fallback": info_z["krylov_fallback"],
             "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,
             "timing": "wall clock around each synchronising call (host-side setup included)"}
+
+
+def run_uneven(args, dev):
+    """The uneven batch (64 seeded configurations of 1-8 spheres and ellipsoids, N 162 .. 7976)
+    through the scheduler: a bounded sample of `--uneven-nk` wavenumbers over (0, 8] per
+    configuration (the full workload has 256), run with 4 workers (one context and stream each,
+    largest job first) and with 1 worker; wall clock around each synchronising run."""
+    import torch
+
+    from workloads import uneven_configuration
+    from paper_1706_07919_gb300 import binding as B
+
+    nk = args.uneven_nk
+    k = (8.0 / nk) * np.arange(1, nk + 1, dtype=np.float64)
+    meshes = [uneven_configuration(i)[0] for i in range(64)]
+    outs = [torch.empty((nk, 2, m.N), dtype=torch.complex128, device=dev) for m in meshes]
+    res = {}
+    for workers in (4, 1):
+        sched = B.bie_sched_create(dev.index if dev.index is not None else 0, workers, None)
+        jobs = [B.bie_sched_add(sched, m.nodes, m.elems, m.normals, m.bc, [0.0, 0.0, 1.0], k, B.BIE_MODE_MIXED, o)
+                for m, o in zip(meshes, outs)]
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        st = B.bie_sched_run(sched)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t
+        B.bie_sched_destroy(sched)
+        res[workers] = (dt, st, jobs)
+    dt4, st4, jobs4 = res[4]
+    flagged = sum(1 for j in jobs4 for r in j.reports() if r.flags & B.BIE_FLAG_FP64_ASSEMBLY)
+    worst = max(r.backward_err for j in jobs4 for r in j.reports())
+    Ns = [m.N for m in meshes]
+    return {"workload": "uneven_64_configs_N162_to_7976", "wavenumbers_per_config": nk,
+            "solves": 64 * nk, "solves_per_s": 64 * nk / dt4, "solves_per_s_one_worker": 64 * nk / res[1][0],
+            "workers": 4, "wall_s": dt4, "busy_s": st4["busy_ms"] / 1e3, "sum_N": int(sum(Ns)),
+            "max_N": int(max(Ns)), "fp64_reassembled": flagged, "max_backward_err": worst,
+            "timing": "wall clock around bie_sched_run (mesh set-up of every job included)"}
 
 
 def run_e2e(args, w, sol, B, dev, stream):
@@ -498,6 +537,10 @@ def main():
     ap.add_argument("--no-learned", dest="no_learned", action="store_true",
                     help="skip the learned-warm-start sweep on the spheroid workload")
     ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned warm start")
+    ap.add_argument("--no-uneven", dest="no_uneven", action="store_true",
+                    help="skip the uneven multi-configuration batch through the scheduler")
+    ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
+                    help="wavenumbers per configuration of the uneven batch sample")
     ap.add_argument("--case", choices=["lu", "field", "batch"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
