@@ -68,6 +68,7 @@ def _load():
             "or_field": [c_dp, i64, c_ip, i64, dbl, i32, c_dp, c_dp, c_dp, i64, c_ip, c_dp, c_dp, c_dp],
             "or_dft": [i64, c_dp, c_dp],
             "or_synthesize": [i64, i64, c_dp, c_ip, i64, i64, c_dp, c_dp],
+            "or_assemble_rows": [c_dp, i64, c_ip, i64, c_dp, c_ip, dbl, c_dp, i32, i32, c_dp, i64, c_dp, c_dp],
             "or_mlp_features": [c_dp, c_dp, i64, c_dp, i64, c_dp, c_dp, dbl, dbl, c_dp],
             "or_mlp_forward": [c_dp, c_dp, i64, c_dp],
             "or_mlp_loss_grad": [c_dp, c_dp, c_dp, i64, c_dp, c_dp],
@@ -152,6 +153,19 @@ def assemble_system(mesh, k: float, direction, ng: int = 4, ng_near: int = 6):
     b = np.zeros(N, np.complex128)
     _check(_load().or_assemble_system(_p(nodes), N, _p(elems), E, _p(normals), _p(bc), float(k), _p(d),
                                       ng, ng_near, _p(A), _p(b)), "assemble_system")
+    return A, b
+
+
+def assemble_rows(mesh, k: float, direction, rows, ng: int = 4, ng_near: int = 6):
+    """Selected rows of the system of assemble_system (same arithmetic, row by row)."""
+    nodes, elems, normals, bc = _mesh_arrays(mesh)
+    d = np.ascontiguousarray(direction, np.float64)
+    rows = np.ascontiguousarray(rows, np.int64)
+    N, E = nodes.shape[0], elems.shape[0]
+    A = np.zeros((rows.shape[0], N), np.complex128)
+    b = np.zeros(rows.shape[0], np.complex128)
+    _check(_load().or_assemble_rows(_p(nodes), N, _p(elems), E, _p(normals), _p(bc), float(k), _p(d), ng, ng_near,
+                                    _p(rows), rows.shape[0], _p(A), _p(b)), "assemble_rows")
     return A, b
 
 

@@ -159,65 +159,137 @@ static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1]
 /* ------------------------------------------------------------------------------------------
  * Eq. BRIEF assembly (Sec. 3, App. A): every node x_i is a collocation point.
  * ------------------------------------------------------------------------------------------ */
-int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                    const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
-                    cplx* alpha, cplx* beta) {
+/* The rules of one assembly: standard points, and near points per local node. */
+typedef struct {
+  int nstd;
+  double sxi[256], seta[256], sw[256];
+  int nnear[6];
+  double nxi[6][512], neta[6][512], nw[6][512];
+} rules_t;
+
+static void make_rules(int ng, int ng_near, rules_t* r) {
+  r->nstd = or_rule_std(ng, r->sxi, r->seta, r->sw);
+  for (int a = 0; a < 6; ++a) r->nnear[a] = or_rule_near(ng_near, a, r->nxi[a], r->neta[a], r->nw[a]);
+}
+
+/* Row i: Hrow[j], Gmrow[j] (accumulated) and alpha_i, beta_i. */
+static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                          const double* normals, double k, const rules_t* ru, int64_t i, cplx* Hrow,
+                          cplx* Gmrow, cplx* alpha_i, cplx* beta_i) {
+  (void)N;
+  const double* xi0 = nodes + 3 * i;   /* collocation point x_i */
+  const double* nu0 = normals + 3 * i; /* its normal nu_i */
+  cplx al = 0.0, be = 0.0;
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t* el = elems + 6 * e;
+    int own = -1; /* local index of node i in element e, if any */
+    for (int a = 0; a < 6; ++a)
+      if (el[a] == i) own = a;
+    const double *qx = ru->sxi, *qe = ru->seta, *qw = ru->sw;
+    int nq = ru->nstd;
+    if (own >= 0) {
+      qx = ru->nxi[own];
+      qe = ru->neta[own];
+      qw = ru->nw[own];
+      nq = ru->nnear[own];
+    }
+    for (int q = 0; q < nq; ++q) {
+      double x[3], nu[3], J, Nv[6];
+      elem_point(nodes, el, qx[q], qe[q], x, nu, &J, Nv);
+      double r[3] = {x[0] - xi0[0], x[1] - xi0[1], x[2] - xi0[2]};
+      double R = sqrt(dot3(r, r));
+      cplx eikr = cexp(I * k * R);
+      cplx G = eikr / R;                                           /* Eq. Green_func */
+      cplx dG = eikr * (I * k * R - 1.0) * dot3(r, nu) / (R * R * R); /* dG/dnu at x */
+      double s = k * dot3(nu0, r);
+      double g = cos(s), f = sin(s) / k;                           /* Eqs. g_function, f_function */
+      double dg = -k * sin(s) * dot3(nu0, nu), df = cos(s) * dot3(nu0, nu);
+      double wJ = qw[q] * J;
+      for (int a = 0; a < 6; ++a) {
+        Hrow[el[a]] += wJ * Nv[a] * dG;
+        Gmrow[el[a]] += wJ * Nv[a] * G;
+      }
+      al += wJ * (g * dG - dg * G);
+      be += wJ * (f * dG - df * G);
+    }
+  }
+  *alpha_i = al;
+  *beta_i = be;
+}
+
+static int check_mesh(int64_t N, const int32_t* elems, int64_t E, double k, int ng, int ng_near) {
   if (N < 1 || E < 1 || !(k > 0.0) || ng < 1 || ng > 16 || ng_near < 1 || ng_near > 16) return -1;
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 6; ++a)
       if (elems[6 * e + a] < 0 || elems[6 * e + a] >= N) return -1;
+  return 0;
+}
 
-  double sxi[256], seta[256], sw[256];
-  int nstd = or_rule_std(ng, sxi, seta, sw);
-  double nxi[6][512], neta[6][512], nw[6][512];
-  int nnear[6];
-  for (int a = 0; a < 6; ++a) nnear[a] = or_rule_near(ng_near, a, nxi[a], neta[a], nw[a]);
-
+int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                    const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
+                    cplx* alpha, cplx* beta) {
+  if (check_mesh(N, elems, E, k, ng, ng_near)) return -1;
+  rules_t* ru = (rules_t*)malloc(sizeof(rules_t));
+  if (!ru) return -3;
+  make_rules(ng, ng_near, ru);
   memset(H, 0, sizeof(cplx) * N * N);
   memset(Gm, 0, sizeof(cplx) * N * N);
-
 #pragma omp parallel for schedule(dynamic, 4)
-  for (int64_t i = 0; i < N; ++i) {
-    const double* xi0 = nodes + 3 * i;   /* collocation point x_i */
-    const double* nu0 = normals + 3 * i; /* its normal nu_i */
-    cplx al = 0.0, be = 0.0;
-    for (int64_t e = 0; e < E; ++e) {
-      const int32_t* el = elems + 6 * e;
-      int own = -1; /* local index of node i in element e, if any */
-      for (int a = 0; a < 6; ++a)
-        if (el[a] == i) own = a;
-      const double *qx = sxi, *qe = seta, *qw = sw;
-      int nq = nstd;
-      if (own >= 0) {
-        qx = nxi[own];
-        qe = neta[own];
-        qw = nw[own];
-        nq = nnear[own];
-      }
-      for (int q = 0; q < nq; ++q) {
-        double x[3], nu[3], J, Nv[6];
-        elem_point(nodes, el, qx[q], qe[q], x, nu, &J, Nv);
-        double r[3] = {x[0] - xi0[0], x[1] - xi0[1], x[2] - xi0[2]};
-        double R = sqrt(dot3(r, r));
-        cplx eikr = cexp(I * k * R);
-        cplx G = eikr / R;                                           /* Eq. Green_func */
-        cplx dG = eikr * (I * k * R - 1.0) * dot3(r, nu) / (R * R * R); /* dG/dnu at x */
-        double s = k * dot3(nu0, r);
-        double g = cos(s), f = sin(s) / k;                           /* Eqs. g_function, f_function */
-        double dg = -k * sin(s) * dot3(nu0, nu), df = cos(s) * dot3(nu0, nu);
-        double wJ = qw[q] * J;
-        for (int a = 0; a < 6; ++a) {
-          H[i * N + el[a]] += wJ * Nv[a] * dG;
-          Gm[i * N + el[a]] += wJ * Nv[a] * G;
-        }
-        al += wJ * (g * dG - dg * G);
-        be += wJ * (f * dG - df * G);
-      }
-    }
-    alpha[i] = al;
-    beta[i] = be;
-  }
+  for (int64_t i = 0; i < N; ++i)
+    row_integrals(nodes, N, elems, E, normals, k, ru, i, H + i * N, Gm + i * N, alpha + i, beta + i);
+  free(ru);
   return 0;
+}
+
+/* Rows rows[0..nrows) of the system of or_assemble_system: A_rows [nrows][N], b_rows [nrows]. */
+int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc, double k, const double* dir, int ng,
+                     int ng_near, const int64_t* rows, int64_t nrows, cplx* A_rows, cplx* b_rows) {
+  if (check_mesh(N, elems, E, k, ng, ng_near)) return -1;
+  for (int64_t t = 0; t < nrows; ++t)
+    if (rows[t] < 0 || rows[t] >= N) return -1;
+  rules_t* ru = (rules_t*)malloc(sizeof(rules_t));
+  cplx* known = (cplx*)malloc(sizeof(cplx) * N);
+  if (!ru || !known) {
+    free(ru); free(known);
+    return -3;
+  }
+  make_rules(ng, ng_near, ru);
+  for (int64_t j = 0; j < N; ++j) {
+    cplx pinc = cexp(I * k * dot3(dir, nodes + 3 * j));
+    known[j] = bc[j] ? -pinc : -(I * k * dot3(dir, normals + 3 * j)) * pinc;
+  }
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < nrows; ++t) {
+    const int64_t i = rows[t];
+    cplx* H = (cplx*)calloc(N, sizeof(cplx));
+    cplx* Gm = (cplx*)calloc(N, sizeof(cplx));
+    if (!H || !Gm) {
+      rc = -3;
+    } else {
+      cplx al, be;
+      row_integrals(nodes, N, elems, E, normals, k, ru, i, H, Gm, &al, &be);
+      cplx bi = 0.0;
+      for (int64_t j = 0; j < N; ++j) {
+        cplx C = H[j] - (i == j ? 4.0 * PI + al : 0.0); /* multiplies P_j  */
+        cplx D = -(Gm[j] + (i == j ? be : 0.0));        /* multiplies P'_j */
+        if (bc[j] == 0) {
+          A_rows[t * N + j] = C;
+          bi -= D * known[j];
+        } else {
+          A_rows[t * N + j] = D;
+          bi -= C * known[j];
+        }
+      }
+      b_rows[t] = bi;
+    }
+    free(H);
+    free(Gm);
+  }
+  free(ru);
+  free(known);
+  return rc;
 }
 
 int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int64_t E,

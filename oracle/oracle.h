@@ -56,6 +56,13 @@ int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int
                        const double* normals, const uint8_t* bc, double k, const double* dir,
                        int ng, int ng_near, double _Complex* A, double _Complex* b);
 
+/* The rows rows[0..nrows) of that system (the same arithmetic, row by row): A_rows [nrows][N],
+ * b_rows [nrows]; for checks at sizes where the whole system does not fit. */
+int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc, double k, const double* dir, int ng,
+                     int ng_near, const int64_t* rows, int64_t nrows, double _Complex* A_rows,
+                     double _Complex* b_rows);
+
 /* Dense complex LU with partial pivoting (largest modulus, ties to the lowest row), in place;
  * piv[k] = row swapped with row k.  Returns 0, or -4 on an exactly zero pivot. */
 int or_lu_factor(int64_t n, double _Complex* A, int64_t* piv);

@@ -67,7 +67,9 @@ __device__ __forceinline__ void kernel64(double k, const double* xi, const doubl
   o.be = {f * o.dG.re - df * o.G.re, f * o.dG.im - df * o.G.im};
 }
 
-// grid: (ceil(N / ROWS), nk); block: 32 * ROWS; dynamic smem: ROWS * N * sizeof(cd)
+// grid: (ceil(N / ROWS), nk); block: 32 * ROWS; dynamic smem: ROWS * N * sizeof(cd), or none
+// with GROW (large N), where each warp accumulates straight into its row of A.
+template <bool GROW>
 __global__ void __launch_bounds__(512) k_asm64_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ elems, int64_t N, int64_t E, int Q, const double* __restrict__ qgeo,
@@ -80,11 +82,16 @@ __global__ void __launch_bounds__(512) k_asm64_bulk(
   const int kk = blockIdx.y;
   const double k = kv[kk];
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
-  for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) acc[t] = {0.0, 0.0};
-  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * rows + warp;
+  if constexpr (GROW) {
+    if (i < N)
+      for (int64_t j = lane; j < N; j += 32) A[((int64_t)kk * N + i) * N + j] = {0.0, 0.0};
+  } else {
+    for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) acc[t] = {0.0, 0.0};
+  }
+  __syncthreads();
   if (i < N) {
-    cd* row = acc + (int64_t)warp * N;
+    cd* row = GROW ? A + ((int64_t)kk * N + i) * N : acc + (int64_t)warp * N;
     const cd* kn = known + (int64_t)kk * N;
     const double xi[3] = {nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2]};
     const double nui[3] = {normals[3 * i], normals[3 * i + 1], normals[3 * i + 2]};
@@ -136,8 +143,10 @@ __global__ void __launch_bounds__(512) k_asm64_bulk(
       be.re += __shfl_xor_sync(0xffffffffu, be.re, o); be.im += __shfl_xor_sync(0xffffffffu, be.im, o);
       bsum.re += __shfl_xor_sync(0xffffffffu, bsum.re, o); bsum.im += __shfl_xor_sync(0xffffffffu, bsum.im, o);
     }
-    cd* Arow = A + ((int64_t)kk * N + i) * N;
-    for (int64_t j = lane; j < N; j += 32) Arow[j] = row[j];
+    if constexpr (!GROW) {
+      cd* Arow = A + ((int64_t)kk * N + i) * N;
+      for (int64_t j = lane; j < N; j += 32) Arow[j] = row[j];
+    }
     if (lane == 0) {
       cd* rs = rowsum + ((int64_t)kk * N + i) * 3;
       rs[0] = al; rs[1] = be; rs[2] = bsum;
@@ -242,15 +251,23 @@ int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch
   } else {
   int rows = 16;
   while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
-  size_t smem = (size_t)rows * N * sizeof(cd);
-  if (smem > 200 * 1024)
-    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP64 shared-memory row accumulator");
+  const bool grow = (size_t)rows * N * sizeof(cd) > 200 * 1024;
+  if (grow) rows = 8;
+  size_t smem = grow ? 0 : (size_t)rows * N * sizeof(cd);
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
-  BIE_TRY((set_smem_max(k_asm64_bulk)));
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
-  BIE_LAUNCH(k_asm64_bulk<<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.Q, c->qgeo,
-                                                   c->qshape, c->color_off, c->ncolors, c->elem_perm, kv, known, A,
-                                                   rowsum, rows));
+  if (grow) {
+    BIE_LAUNCH(k_asm64_bulk<true><<<gb, 32 * rows, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E,
+                                                                   c->rule.Q, c->qgeo, c->qshape, c->color_off,
+                                                                   c->ncolors, c->elem_perm, kv, known, A, rowsum,
+                                                                   rows));
+  } else {
+    BIE_TRY((set_smem_max(k_asm64_bulk<false>)));
+    BIE_LAUNCH(k_asm64_bulk<false><<<gb, 32 * rows, smem, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N,
+                                                                       c->E, c->rule.Q, c->qgeo, c->qshape,
+                                                                       c->color_off, c->ncolors, c->elem_perm, kv,
+                                                                       known, A, rowsum, rows));
+  }
   BIE_CUDA_TRY(cudaGetLastError());
   }
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);

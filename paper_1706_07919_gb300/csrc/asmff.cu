@@ -67,8 +67,11 @@ __device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
 }
 
 // Same outputs and launch shape as k_asm32_bulk (rows per CTA x ASMF_W warps per row, colours
-// separated by block barriers), with an FP64 shared-memory row accumulator [rows][N] and FP64 A.
+// separated by block barriers), with an FP64 row accumulator [rows][N] in shared memory, or for
+// large N (GROW) the output rows of A themselves (each row belongs to one CTA; the elements of a
+// colour share no node, so the row's warps never touch the same entry between barriers).
 constexpr int ASMF_W = 2;
+template <bool GROW>
 __global__ void __launch_bounds__(256) k_asmff_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ esort, const int32_t* __restrict__ eperm, int64_t N, int64_t E, int Q,
@@ -84,11 +87,18 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
   const ff k = ff_from_double(kv[kk]);
   const ff kinv = ff_from_double(1.0 / kv[kk]);
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = ff_from_double(qshape[t]);
-  for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accd[t] = {0.0, 0.0};
-  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * rows + rw;
   const bool valid = i < N;
-  cd* row = accd + (int64_t)rw * N;
+  cd* row;
+  if constexpr (GROW) {
+    row = A + ((int64_t)kk * N + (valid ? i : 0)) * N;
+    if (valid)
+      for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) row[j] = {0.0, 0.0};
+  } else {
+    for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accd[t] = {0.0, 0.0};
+    row = accd + (int64_t)rw * N;
+  }
+  __syncthreads();
   const cd* kn = known + (int64_t)kk * N;
   ff xi[3], nui[3];
   for (int d = 0; d < 3; ++d) {
@@ -180,8 +190,10 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
     for (int u = 0; u < 6; ++u) part[rw][sub][u] = v[u];
   __syncthreads();
   if (valid) {
-    cd* Arow = A + ((int64_t)kk * N + i) * N;
-    for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) Arow[j] = row[j];
+    if constexpr (!GROW) {
+      cd* Arow = A + ((int64_t)kk * N + i) * N;
+      for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) Arow[j] = row[j];
+    }
     if (sub == 0 && lane == 0) {
       double w[6] = {0, 0, 0, 0, 0, 0};
       for (int s2 = 0; s2 < ASMF_W; ++s2)
@@ -238,19 +250,24 @@ const int32_t* sorted_elems_ptr(bie_ctx* c);
 int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* known, cd* rowsum) {
   const int64_t N = c->N;
   BIE_TRY(ensure_mixed_tables(c));
-  int rows = 8 / ASMF_W * 2;  // 8 rows x 2 warps = 512 threads at most; shrink to fit shared memory
+  int rows = 4;  // 4 rows x 2 warps = 256 threads (launch bound); shrink to fit shared memory
   while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
-  const size_t smem = (size_t)rows * N * sizeof(cd);
-  if (smem > 200 * 1024)
-    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP64 shared-memory row accumulator");
+  const bool grow = (size_t)rows * N * sizeof(cd) > 200 * 1024;  // rows accumulate in A itself
+  if (grow) rows = 4;
+  const size_t smem = grow ? 0 : (size_t)rows * N * sizeof(cd);
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
-  rows = std::min(rows, 4);  // 256 threads per CTA (launch bound)
-  BIE_TRY((set_smem_max(k_asmff_bulk)));
   static const FFConst K = make_ffconst();
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
-  BIE_LAUNCH(k_asmff_bulk<<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
-      c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c), c->qgeo,
-      c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+  if (grow) {
+    BIE_LAUNCH(k_asmff_bulk<true><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+  } else {
+    BIE_TRY((set_smem_max(k_asmff_bulk<false>)));
+    BIE_LAUNCH(k_asmff_bulk<false><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+  }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

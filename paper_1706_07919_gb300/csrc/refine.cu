@@ -222,19 +222,23 @@ __device__ __forceinline__ void ff_acc_prod(float a, float xh, float xl, float& 
   sl += t.lo + e;
 }
 
+// stage: x split into float-float once per CTA in shared memory (n * 16 bytes); otherwise (large n)
+// every lane splits the FP64 entries it reads.
 __global__ void __launch_bounds__(512) k_residual_ff(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
                                                      const cd* __restrict__ b, const cd* __restrict__ x,
                                                      cd* __restrict__ r, double* __restrict__ rowabs,
-                                                     const RefineState* __restrict__ st) {
+                                                     const RefineState* __restrict__ st, int stage) {
   extern __shared__ float4 xs[];  // [n]: re_hi, re_lo, im_hi, im_lo
   const int kk = blockIdx.y;
   if (st[kk].done) return;
   const cd* xk = x + (int64_t)kk * n;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const ff a = ff_from_double(xk[j].re), c = ff_from_double(xk[j].im);
-    xs[j] = make_float4(a.hi, a.lo, c.hi, c.lo);
+  if (stage) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const ff a = ff_from_double(xk[j].re), c = ff_from_double(xk[j].im);
+      xs[j] = make_float4(a.hi, a.lo, c.hi, c.lo);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * 16 + warp;
   if (i >= n) return;
@@ -242,7 +246,13 @@ __global__ void __launch_bounds__(512) k_residual_ff(const cf* __restrict__ A, i
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f, ab = 0.f;
   for (int j = lane; j < n; j += 32) {
     const cf a = row[j];
-    const float4 v = xs[j];
+    float4 v;
+    if (stage) {
+      v = xs[j];
+    } else {
+      const ff p = ff_from_double(xk[j].re), q = ff_from_double(xk[j].im);
+      v = make_float4(p.hi, p.lo, q.hi, q.lo);
+    }
     ff_acc_prod(a.re, v.x, v.y, rh, rl);
     ff_acc_prod(-a.im, v.z, v.w, rh, rl);
     ff_acc_prod(a.re, v.z, v.w, ih, il);
@@ -372,18 +382,21 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
   RefineState* st = (RefineState*)state_dev;
   const int64_t dstride = diag_inv_stride(n);
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
+  if ((size_t)n * sizeof(int32_t) > 200 * 1024) return fail(BIE_ERR_INVALID_ARG, "N too large for the permutation kernel");
+  BIE_TRY((set_smem_max(k_piv_to_perm)));
   BIE_LAUNCH(k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm));
   if (D) BIE_TRY(diag_inverses(c, LU, nk, n, ld, bstride, D));
   const size_t sm_trsv = (size_t)n * sizeof(cf);
-  const size_t sm_res = (size_t)n * sizeof(float4);
-  if (sm_trsv > 200 * 1024 || sm_res > 200 * 1024)
-    return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory refinement kernels");
+  const int stage = (size_t)n * sizeof(float4) <= 200 * 1024 ? 1 : 0;
+  const size_t sm_res = stage ? (size_t)n * sizeof(float4) : 0;
+  if (sm_trsv > 200 * 1024)
+    return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory triangular solves (N <= 25600)");
   BIE_TRY((set_smem_max(k_trsv_lu)));
   BIE_TRY((set_smem_max(k_residual_ff)));
   BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int it = 0; it <= it_max; ++it) {
-    BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st));
+    BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st, stage));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
     BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0, D, dstride));

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import analytic_sphere as an
-from workloads import octa_sphere, ico_sphere, shell_points, gaussian_pulse
+from workloads import octa_sphere, ico_sphere, shell_points, gaussian_pulse, merge_meshes, scale_translate
 
 D = np.array([0.0, 0.0, 1.0])
 
@@ -304,3 +304,13 @@ def test_causality_of_scattered_pulse():
             early = t < t_arr - 6 * sigma
             assert np.abs(p[ip][early]).max() < bound * np.abs(p[ip]).max()
             assert np.abs(p[ip]).max() > 1e-2
+
+
+def test_assemble_rows_equals_the_system_rows():
+    """The row-by-row assembly used for checks at large N is the system's arithmetic, row by row."""
+    m = merge_meshes([scale_translate(ico_sphere(2), 0.8, (0, 0, -1.0), bc=1),
+                      scale_translate(ico_sphere(2), 1.1, (0.3, 0, 1.3), bc=0)])
+    A, b = oracle.assemble_system(m, 2.3, [0.0, 0.0, 1.0])
+    rows = np.array([0, 5, 161, m.N - 1])
+    Ar, br = oracle.assemble_rows(m, 2.3, [0.0, 0.0, 1.0], rows)
+    assert np.array_equal(Ar, A[rows]) and np.array_equal(br, b[rows])

@@ -14,6 +14,10 @@
   icosahedral grids of about 6 r divisions per face, coarsened so that N stays in [162, 8000];
   256 wavenumbers over (0, 8], 256 seeded points outside the bodies, Gaussian sigma = 0.5,
   512 time samples.
+* lattice_large: a 4 x 4 x 2 lattice of sound-soft spheres of radius 0.5 (320 elements / 642 nodes
+  each, N = 20544), centres 1.2 (i - 1.5, j - 1.5, l - 0.5), k_m = 24 m / 2048 (ka <= 12), 256 x 256
+  observation grid on z = 0 over [-4, 4]^2, eight pulses (Gaussian, Ricker, three Gaussian-modulated
+  sinusoids, three seeded random band-limited), 4096 time samples.
 * two_spheres_mixed: two sound-hard unit spheres, 720 elements / 1442 nodes each (N = 2884),
   centres (0, 0, +-1.05) (surface gap 0.1) on the propagation axis, k_m = m/32 (m = 1..512),
   128 x 128 observation grid on the plane z = 0 over [-5, 5]^2, Gaussian sigma = 0.25,
@@ -158,3 +162,37 @@ def config_uneven_batch(n_configs: int = 64, Nk: int = 256, M: int = 256, Nt: in
         xobs = outside_points(M, bodies, seed=4001 * 1000 + i)
         out.append(Workload(f"uneven_{i}", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs, pulse, Nt, T))
     return out
+
+
+def config_lattice_large(Nk: int = 2048, grid: int = 256, Nt: int = 4096, freq: int = 4) -> Workload:
+    s = ico_sphere(freq, 1.0, bc=1)
+    bodies = []
+    for i in range(4):
+        for j in range(4):
+            for l in range(2):
+                c = (1.2 * (i - 1.5), 1.2 * (j - 1.5), 1.2 * (l - 0.5))
+                bodies.append(scale_translate(s, 0.5, c, bc=1))
+    mesh = merge_meshes(bodies)
+    kmax = 24.0
+    dk = kmax / Nk
+    T = 2.0 * np.pi / dk
+    k = dk * np.arange(1, Nk + 1, dtype=np.float64)
+    xobs = plane_grid_points(grid, 4.0, 0.0)
+    from .pulses import gaussian_pulse as gp, ricker_pulse, modulated_gaussian
+    sig = 1.0 / 12.0
+    rows = [gp(Nt, T, sigma=2.0 * sig, tc=4.0), ricker_pulse(Nt, T, kp=8.0, tc=4.0)]
+    for kc in (6.0, 12.0, 18.0):
+        rows.append(modulated_gaussian(Nt, T, kc=kc, sigma=0.5, tc=4.0))
+    # seeded random band-limited signals: sums of the window's harmonics up to angular frequency
+    # 20 with normal amplitudes and phases under a cos^2 taper
+    rng = np.random.Generator(np.random.PCG64(5001))
+    t = np.arange(Nt, dtype=np.float64) * (T / Nt)
+    m = np.arange(1, int(20.0 * T / (2.0 * np.pi)) + 1)
+    w = 2.0 * np.pi * m / T
+    taper = np.cos(0.5 * np.pi * w / 20.0) ** 2
+    for _ in range(3):
+        amp = rng.standard_normal(m.size) * taper
+        ph = rng.uniform(0.0, 2.0 * np.pi, m.size)
+        rows.append(np.cos(np.outer(t, w) + ph) @ amp / np.sqrt(m.size))
+    pulses = np.stack(rows)
+    return Workload("lattice_large", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs, pulses, Nt, T)
