@@ -263,6 +263,8 @@ def run_ours(args):
         line["learned"] = run_learned(args, dev, stream)
     if not args.no_uneven:
         line["uneven"] = run_uneven(args, dev)
+    if not args.no_large:
+        line["large"] = run_large(args, dev, stream)
     if grp.is_root:
         line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
         print(json.dumps(line))
@@ -329,6 +331,50 @@ def run_learned(args, dev, stream):
             "zero_start_krylov_fallback": info_z["krylov_fallback"],
             "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,
             "timing": "wall clock around each synchronising call (host-side setup included)"}
+
+
+def run_large(args, dev, stream):
+    """The lattice workload (4 x 4 x 2 sound-soft spheres, N = 20 544) on a bounded sample: one
+    batch of `--large-nk` wavenumbers spread over (0, 24] solved in mixed precision, their field on
+    the full 256 x 256 plane and the synthesis of the eight pulses at 4096 samples (the full
+    workload has 2048 wavenumbers).  CUDA events on the library's stream around each phase."""
+    import torch
+
+    from workloads import config_lattice_large
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+
+    w = config_lattice_large()
+    nk = args.large_nk
+    idx = np.linspace(0, len(w.k) - 1, nk).round().astype(np.int64)
+    ks = w.k[idx]
+    midx = idx + 1  # frequency index m of each wavenumber (k_m = m dk)
+    M, Nt, P = w.xobs.shape[0], w.Nt, w.pulses.shape[0]
+    sol = Solver(dev.index if dev.index is not None else 0, stream)
+    sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    sol.set_incident_plane_wave(w.direction)
+    with torch.cuda.stream(stream):
+        xo = torch.tensor(w.xobs, dtype=torch.float64, device=dev)
+        pulses = torch.tensor(w.pulses, dtype=torch.float64, device=dev)
+        out = torch.empty((P, M, Nt), dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    surf, rep = sol.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    ev[1].record(stream)
+    T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
+    ev[2].record(stream)
+    S = sol.pulse_spectrum(pulses)
+    sol.synthesize(T, midx, S, Nt, torch.float32, out=out)
+    ev[3].record(stream)
+    torch.cuda.synchronize(dev)
+    t_solve, t_field, t_syn = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
+    sol.close()
+    return {"workload": "lattice_4x4x2_soft_N20544", "N": int(w.mesh.N), "wavenumbers": nk,
+            "k": [float(x) for x in ks], "solves_per_s": nk / (t_solve / 1e3),
+            "field_evals_per_s": M * w.mesh.E * 16 * nk / (t_field / 1e3), "points": M, "pulses": P, "Nt": Nt,
+            "phase_ms": {"solve": t_solve, "field": t_field, "spectrum_synthesis": t_syn},
+            "fp64_reassembled": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
+            "max_backward_err": max(r.backward_err for r in rep)}
 
 
 def run_uneven(args, dev):
@@ -537,6 +583,10 @@ def main():
     ap.add_argument("--no-learned", dest="no_learned", action="store_true",
                     help="skip the learned-warm-start sweep on the spheroid workload")
     ap.add_argument("--epochs", type=int, default=60, help="training epochs of the learned warm start")
+    ap.add_argument("--no-large", dest="no_large", action="store_true",
+                    help="skip the lattice (N = 20544) sample")
+    ap.add_argument("--large-nk", dest="large_nk", type=int, default=8,
+                    help="wavenumbers of the lattice sample")
     ap.add_argument("--no-uneven", dest="no_uneven", action="store_true",
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
