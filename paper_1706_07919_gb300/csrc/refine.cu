@@ -152,16 +152,34 @@ __device__ void trsv_sweep(const cf* __restrict__ M, int n, int64_t ld, cf* y, c
           else if (c0 < j1) v[u] = make_float4(p[0].re, p[0].im, 0.f, 0.f);
         }
       }
+      // the 16 partial sums (8 rows x re, im) are reduced across the warp by halving exchanges:
+      // at offset 16, 8, 4, 2 each lane keeps half of its values and adds its partner's copy of
+      // them (8 + 4 + 2 + 1 shuffles), then one exchange at offset 1 completes the sums; lane L
+      // ends with value 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of L) = row (that >> 1), part (& 1)
+      float t[16];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        float sr = v[u].x * ya.re - v[u].y * ya.im + v[u].z * yb.re - v[u].w * yb.im;
-        float si = v[u].x * ya.im + v[u].y * ya.re + v[u].z * yb.im + v[u].w * yb.re;
-        for (int o = 16; o > 0; o >>= 1) {
-          sr += __shfl_xor_sync(0xffffffffu, sr, o);
-          si += __shfl_xor_sync(0xffffffffu, si, o);
+        t[2 * u] = v[u].x * ya.re - v[u].y * ya.im + v[u].z * yb.re - v[u].w * yb.im;
+        t[2 * u + 1] = v[u].x * ya.im + v[u].y * ya.re + v[u].z * yb.im + v[u].w * yb.re;
+      }
+#pragma unroll
+      for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+          const float send = up ? t[j] : t[j + h];
+          const float keep = up ? t[j + h] : t[j];
+          t[j] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
         }
-        const int r = r0 + u;
-        if (lane == 0 && r < rhi) { y[r].re -= sr; y[r].im -= si; }
+      }
+      t[0] += __shfl_xor_sync(0xffffffffu, t[0], 1);
+      if ((lane & 1) == 0) {
+        const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        const int r = r0 + (idx >> 1);
+        if (r < rhi) {
+          if (idx & 1) y[r].im -= t[0];
+          else y[r].re -= t[0];
+        }
       }
     }
     __syncthreads();
