@@ -536,7 +536,8 @@ def run_case(args):
     """Small cases for profiler captures (no timing, no output line): `lu` factors and refines four
     two-sphere systems (k = 3.15 .. 3.25); `field` evaluates the field of eight wavenumbers at 2048
     of the 16 384 plane points from a constant surface solution; `batch` runs one batch of the
-    benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points)."""
+    benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points); `learned`
+    runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs)."""
     import torch
 
     import __graft_entry__
@@ -549,7 +550,16 @@ def run_case(args):
     sol = Solver(0)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_option("mixed.tcgen05", args.tc)
-    if args.case == "batch":
+    if args.case == "learned":
+        from workloads import config_spheroid_learned
+        ws = config_spheroid_learned()
+        s2 = Solver(0)
+        s2.set_geometry(ws.mesh.nodes, ws.mesh.elems, ws.mesh.normals, ws.mesh.bc)
+        s2.set_option("learned.epochs", 20)
+        surf, rep = s2.solve_frequencies(ws.k[256:384], B.BIE_MODE_LEARNED)
+        print("case learned:", s2.learned_info())
+        s2.close()
+    elif args.case == "batch":
         ks = w.k[256:384]
         surf, rep = sol.solve_frequencies(ks, B.BIE_MODE_MIXED)
         xo = torch.tensor(w.xobs, device="cuda")
@@ -591,7 +601,7 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "batch"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "batch", "learned"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case:
