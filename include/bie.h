@@ -174,9 +174,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
- *   "field.variant"        shape of the mixed field kernel: wavenumbers per group x points per CTA,
- *                          0 (8 x 128, FP32 compensated sums per term), 1 (8 x 128), 2 (4 x 128),
- *                          3 (8 x 64), 4 (16 x 64, default), 5 (16 x 32), 6 (16 x 128), 7 (12 x 64)
+ *   "field.variant"        mixed field kernel: 1 (default) groups of 16 wavenumbers, 64 points per
+ *                          CTA, FP32 run sums; 0 groups of 8, 128 points, compensated sums per term
  *   "mixed.reassembly"     system of the flagged wavenumbers: 1 (default) bulk pairs in float-float
  *                          (~48-bit, FP32 pipes), 0 in FP64; near pairs and diagonal are FP64
  *   "assemble.bulk_ff"     bie_assemble's bulk pairs in float-float (1) or FP64 (0, default)

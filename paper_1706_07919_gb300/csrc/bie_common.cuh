@@ -125,8 +125,8 @@ struct bie_ctx {
   double refine_tol = 1e-11;         // backward-error target of the refinement
   double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
-  int field_variant = 4;             // mixed field kernel shape: 0 k_field32b (8 wavenumbers per
-                                     // group), 1-7 k_field32c shapes; 4 = 16 per group, 64 points/CTA
+  int field_variant = 1;             // mixed field kernel: 1 k_field32c (16 wavenumbers per group,
+                                     // 64 points per CTA), 0 k_field32b (8 per group, 128 points)
   int assemble_ff = 0;               // bie_assemble: bulk pairs in float-float (1) or FP64 (0)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph

@@ -276,7 +276,7 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   } else if (n == "field.accurate_phase") {
     c->field_accurate_phase = value != 0.0 ? 1 : 0;
   } else if (n == "field.variant") {
-    if (value < 0 || value > 7 || value != (int)value) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0..7");
+    if (value != 0.0 && value != 1.0) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0 or 1");
     c->field_variant = (int)value;
   } else if (n == "assemble.bulk_ff") {
     c->assemble_ff = value != 0.0 ? 1 : 0;

@@ -634,8 +634,7 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
     if (c->field_accurate_phase) {
       const int v = c->field_variant;
-      static const int kKB[8] = {FKB, 8, 4, 8, 16, 16, 16, 12};
-      const int KBv = kKB[v & 7];
+      const int KBv = (v == 1) ? 16 : FKB;
       // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -648,19 +647,7 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
       }
       const ff dkf = ff_from_double(dkv);
       if (v == 1) {
-        launch_field32c<8, 128, 4>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 2) {
-        launch_field32c<4, 128, 6>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 3) {
-        launch_field32c<8, 64, 8>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 4) {
         launch_field32c<16, 64, 4>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 5) {
-        launch_field32c<16, 32, 8>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 6) {
-        launch_field32c<16, 128, 2>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 7) {
-        launch_field32c<12, 64, 5>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
       } else {
         dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
         BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,

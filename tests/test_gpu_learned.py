@@ -167,3 +167,54 @@ def test_network_warm_start_gains(learned_case):
     assert net["last_loss"] < 0.05 * net["first_loss"]
     assert net["x0_rel_err"] < 0.1
     assert net["mean_iters"] < zero["mean_iters"]
+
+
+def test_learned_soft_hard_ragged_and_single_anchor():
+    """Mixed boundary conditions (a soft and a hard body, the unknown is dP/dnu on the soft one),
+    a wavenumber count that is not a multiple of the stride, and a call with fewer wavenumbers
+    than the stride (one anchor: the last wavenumber), started from the anchor's solution."""
+    from paper_1706_07919_gb300 import binding as Bd
+    s0 = W.ico_sphere(2)
+    m = W.merge_meshes([W.scale_translate(s0, 0.8, (0, 0, -1.1), bc=1), W.scale_translate(s0, 1.0, (0.2, 0, 1.2), bc=0)])
+    d = np.array([0.0, 0.0, 1.0])
+    k = 0.1 * np.arange(1, 12)  # 11 wavenumbers, stride 4: anchors at indices 3 and 7
+    s = _solver(m)
+    s.set_option("learned.stride", 4)
+    s.set_option("learned.epochs", 30)
+    s.set_option("learned.batch", 256)
+    surf, rep = s.solve_frequencies(k, Bd.BIE_MODE_LEARNED)
+    info = s.learned_info()
+    assert info["anchors"] == 2 and info["krylov"] == 9
+    surf = surf.cpu().numpy()
+    for i in (0, 5, 10):
+        P, Pn = oracle.solve_frequency(m, k[i], d)
+        assert _rel(surf[i, 0], P) <= 1e-6 and _rel(surf[i, 1], Pn) <= 1e-6
+    s.set_option("learned.x0", 2)
+    surf2, rep2 = s.solve_frequencies(k[:3], Bd.BIE_MODE_LEARNED)
+    assert s.learned_info()["anchors"] == 1 and rep2[2].path == Bd.BIE_MODE_MIXED
+    P, Pn = oracle.solve_frequency(m, k[0], d)
+    assert _rel(surf2.cpu().numpy()[0, 1], Pn) <= 1e-6
+    s.close()
+
+
+def test_network_entry_points_report_errors(small_spheroid):
+    from paper_1706_07919_gb300 import binding as Bd
+    s = _solver(small_spheroid)
+    with pytest.raises(Bd.BieError) as e:
+        s.mlp_get_params()
+    assert e.value.code == Bd.BIE_ERR_STATE
+    with pytest.raises(Bd.BieError) as e:
+        s.mlp_features([1.0])  # no wavenumber scale yet
+    assert e.value.code == Bd.BIE_ERR_STATE
+    with pytest.raises(ValueError):
+        s.mlp_set_params(np.zeros(10, np.float32))
+    th = _params(1)
+    th[5] = np.nan
+    with pytest.raises(Bd.BieError) as e:
+        s.mlp_set_params(th)
+    assert e.value.code == Bd.BIE_ERR_INVALID_ARG
+    with pytest.raises(Bd.BieError):
+        s.set_option("gmres.m", 100)
+    with pytest.raises(Bd.BieError):
+        s.set_option("learned.x0", 3)
+    s.close()

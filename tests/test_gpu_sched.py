@@ -94,3 +94,32 @@ def test_scheduler_uneven_configurations(tmp_path):
     m = picks[i]
     P, _ = oracle.solve_frequency(m, k[3], [0.0, 0.0, 1.0])
     assert _rel(surfs[i].cpu().numpy()[3, 0], P) <= 1e-6
+
+
+def test_scheduler_reports_a_failing_job(tmp_path):
+    from paper_1706_07919_gb300 import binding as B
+    good = W.octa_sphere(1)
+    bad = W.octa_sphere(1)
+    bad_elems = bad.elems.copy()
+    bad_elems[3, 2] = bad.N + 5  # node index out of range
+    sched = B.bie_sched_create(0, 2, None)
+    k = np.array([1.0, 2.0])
+    o1 = torch.empty((2, 2, good.N), dtype=torch.complex128, device="cuda")
+    o2 = torch.empty((2, 2, bad.N), dtype=torch.complex128, device="cuda")
+    B.bie_sched_add(sched, good.nodes, good.elems, good.normals, good.bc, None, k, B.BIE_MODE_MIXED, o1)
+    B.bie_sched_add(sched, bad.nodes, bad_elems, bad.normals, bad.bc, None, k, B.BIE_MODE_MIXED, o2)
+    with pytest.raises(B.BieError) as e:
+        B.bie_sched_run(sched)
+    assert e.value.code == B.BIE_ERR_INVALID_ARG and "scheduler job failed" in str(e.value)
+    B.bie_sched_destroy(sched)
+
+
+def test_autotune_ignores_a_corrupt_cache(tmp_path):
+    from paper_1706_07919_gb300 import binding as B
+    cache = tmp_path / "tune.json"
+    cache.write_text('{"bie_autotune": 1, "entries": {"320": {"batch": -4, "tcgen05": 9}, garbage')
+    s = _solver(W.octa_sphere(2))
+    r = B.bie_autotune(s.ctx, [2.0], str(cache))
+    assert r["from_cache"] == 0 and r["batch"] >= 8
+    assert json.load(open(cache))["entries"]["320"]["batch"] == r["batch"]
+    s.close()
