@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(512) k_panel(Cx<S>* __restrict__ A, int64_t bs
 // One CTA (1024 threads) per matrix holds rows c0..n-1 of columns c0..c0+lw-1, factors them with
 // partial pivoting (largest modulus, lowest row on ties), writes them back, applies the leaf's
 // row swaps to the other columns of the panel [p0, p0+w) and solves the leaf's U block for the
-// panel columns right of the leaf.
+// panel columns right of the leaf.  The leaf is stored column by column in shared memory
+// (element (r, c) at c * rows + r), so that threads walking the rows touch consecutive words.
 template <class S>
 __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w,
                                                int c0, int lw, int32_t* __restrict__ piv, int32_t* __restrict__ info) {
   extern __shared__ unsigned char smem_raw[];
-  Cx<S>* L = reinterpret_cast<Cx<S>*>(smem_raw);  // [rows][lw]
+  Cx<S>* L = reinterpret_cast<Cx<S>*>(smem_raw);  // [lw][rows]
   __shared__ S red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv[16];
@@ -106,14 +107,14 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   const int rows = n - c0;
   for (int t = tid; t < rows * lw; t += nt) {
     const int r = t / lw, c = t - r * lw;
-    L[t] = M[(int64_t)(c0 + r) * ld + c0 + c];
+    L[c * rows + r] = M[(int64_t)(c0 + r) * ld + c0 + c];
   }
   __syncthreads();
   for (int c = 0; c < lw; ++c) {
     S best = -1;
     int bi = rows;
     for (int r = c + tid; r < rows; r += nt) {
-      const Cx<S> v = L[r * lw + c];
+      const Cx<S> v = L[c * rows + r];
       const S m = v.re * v.re + v.im * v.im;
       if (m > best) { best = m; bi = r; }
     }
@@ -142,30 +143,30 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
     __syncthreads();
     const int p = s_piv[c];
     if (p != c && tid < lw) {
-      const Cx<S> t = L[c * lw + tid];
-      L[c * lw + tid] = L[p * lw + tid];
-      L[p * lw + tid] = t;
+      const Cx<S> t = L[tid * rows + c];
+      L[tid * rows + c] = L[tid * rows + p];
+      L[tid * rows + p] = t;
     }
     __syncthreads();
-    const Cx<S> d = L[c * lw + c];
+    const Cx<S> d = L[c * rows + c];
     const bool ok = (d.re != 0 || d.im != 0);
     for (int r = c + 1 + tid; r < rows; r += nt) {
-      Cx<S> l = L[r * lw + c];
+      Cx<S> l = L[c * rows + r];
       if (ok) l = cx_div(l, d);
-      L[r * lw + c] = l;
+      L[c * rows + r] = l;
       for (int j = c + 1; j < lw; ++j) {
-        const Cx<S> u = L[c * lw + j];
-        Cx<S> a = L[r * lw + j];
+        const Cx<S> u = L[j * rows + c];
+        Cx<S> a = L[j * rows + r];
         a.re -= l.re * u.re - l.im * u.im;
         a.im -= l.re * u.im + l.im * u.re;
-        L[r * lw + j] = a;
+        L[j * rows + r] = a;
       }
     }
     __syncthreads();
   }
   for (int t = tid; t < rows * lw; t += nt) {
     const int r = t / lw, c = t - r * lw;
-    M[(int64_t)(c0 + r) * ld + c0 + c] = L[t];
+    M[(int64_t)(c0 + r) * ld + c0 + c] = L[c * rows + r];
   }
   // other panel columns: the leaf's swaps (in order), then the U-block solve right of the leaf
   const int pend = min(p0 + w, n);
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
       for (int s = 1; s < lw; ++s) {
         Cx<S> v = M[(int64_t)(c0 + s) * ld + j];
         for (int t = 0; t < s; ++t) {
-          const Cx<S> l = L[s * lw + t];
+          const Cx<S> l = L[t * rows + s];
           const Cx<S> xt = M[(int64_t)(c0 + t) * ld + j];
           v.re -= l.re * xt.re - l.im * xt.im;
           v.im -= l.re * xt.im + l.im * xt.re;
