@@ -464,11 +464,17 @@ def roofline_field(w, field_ms, M, Nk):
     peak = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 FFMA, 152 SMs x 128 lanes x 2 flops at 2.07 GHz
     launches = (Nk + 63) // 64
     return {"kernel": "k_field32c<16,64,4> (Eq. BRIEFdmn, float-float phases)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": FIELD_LAUNCH_DRAM_BYTES, "traffic_unit": "bytes per launch",
             "evals_per_s": evals / (field_ms * 1e-3), "flops_per_eval": flops_per_eval,
             "launches_per_step": launches, "ms_per_launch": field_ms / launches,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)"}
 
+
+# DRAM bytes (read + write) of one launch of the field kernel in this configuration (64
+# wavenumbers x 16 384 points), from an ncu capture of exactly that launch: 28.30 MB read,
+# 0.18 MB written -- the kernel is ALU-bound and its traffic is the tables and surface values.
+FIELD_LAUNCH_DRAM_BYTES = 28_295_680 + 179_200
 
 # algorithmic flops of one field evaluation (one observation point, one quadrature point, one k),
 # counted on the FP64 formula: 2 distances (3 sub, 3 mul, 2 add, sqrt, div = 10 each), the
