@@ -543,7 +543,8 @@ def run_case(args):
     two-sphere systems (k = 3.15 .. 3.25); `field` evaluates the field of eight wavenumbers at 2048
     of the 16 384 plane points from a constant surface solution; `batch` runs one batch of the
     benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points); `learned`
-    runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs)."""
+    runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs);
+    `step` runs one benchmark step once (cold: the geometry tables are built inside it)."""
     import torch
 
     import __graft_entry__
@@ -556,7 +557,17 @@ def run_case(args):
     sol = Solver(0)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_option("mixed.tcgen05", args.tc)
-    if args.case == "learned":
+    if args.case == "step":
+        sol.set_incident_plane_wave(w.direction)
+        sol.set_option("mixed.batch", args.batch)
+        xo = torch.tensor(w.xobs, dtype=torch.float64, device="cuda")
+        pulses = torch.tensor(w.pulses, dtype=torch.float64, device="cuda")
+        surf, _ = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+        T = sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
+        S = sol.pulse_spectrum(pulses)
+        sol.synthesize(T, np.arange(1, len(w.k) + 1, dtype=np.int64), S, w.Nt, torch.float32)
+        print("case step: one benchmark step")
+    elif args.case == "learned":
         from workloads import config_spheroid_learned
         ws = config_spheroid_learned()
         s2 = Solver(0)
@@ -607,7 +618,7 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "batch", "learned"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "batch", "learned", "step"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case:
