@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(512) k_panel(Cx<S>* __restrict__ A, int64_t bs
 // One CTA (1024 threads) per matrix holds rows c0..n-1 of columns c0..c0+lw-1, factors them with
 // partial pivoting (largest modulus, lowest row on ties), writes them back, applies the leaf's
 // row swaps to the other columns of the panel [p0, p0+w) and solves the leaf's U block for the
-// panel columns right of the leaf.  The leaf is stored column by column in shared memory
-// (element (r, c) at c * rows + r), so that threads walking the rows touch consecutive words.
+// panel columns right of the leaf, then updates the panel columns right of the leaf in the rows
+// below it.  The leaf is stored column by column in shared memory (element (r, c) at
+// c * rows + r), so that threads walking the rows touch consecutive words.
 template <class S>
 __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w,
                                                int c0, int lw, int32_t* __restrict__ piv, int32_t* __restrict__ info) {
@@ -192,59 +193,40 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
         M[(int64_t)(c0 + s) * ld + j] = v;
       }
   }
-}
-
-// Rows below the leaf, panel columns right of it: A -= L_leaf U_leaf (K = lw <= 16).
-// One warp per row, lanes over the (<= 64) columns so that the read-modify-write of A coalesces;
-// the row's lw entries of L are broadcast.  grid (ceil(rows / 64), batch), block 256 (8 warps, 8
-// rows each).
-template <class S>
-__global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
-                                                     int w, int c0, int lw) {
-  __shared__ Cx<S> U[16 * 64];
-  Cx<S>* M = A + (int64_t)blockIdx.y * bstride;
-  const int cs = c0 + lw, ce = min(p0 + w, n), wr = ce - cs;
-  if (wr <= 0) return;
-  for (int t = threadIdx.x; t < lw * wr; t += blockDim.x) {
-    const int s = t / wr, j = t - s * wr;
-    U[s * 64 + j] = M[(int64_t)(c0 + s) * ld + cs + j];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rbeg = c0 + lw + blockIdx.x * 64;
-  for (int r = rbeg + warp; r < min(rbeg + 64, n); r += 8) {
-    const Cx<S>* lrow = M + (int64_t)r * ld + c0;
-    Cx<S> l[16];
-#pragma unroll
-    for (int s = 0; s < 16; ++s)
-      if (s < lw) l[s] = lrow[s];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = lane + 32 * h;
-      if (j < wr) {
-        S ar = 0, ai = 0;
-#pragma unroll
-        for (int s = 0; s < 16; ++s)
-          if (s < lw) {
-            const Cx<S> u = U[s * 64 + j];
-            ar += l[s].re * u.re - l[s].im * u.im;
-            ai += l[s].re * u.im + l[s].im * u.re;
-          }
-        Cx<S>& m = M[(int64_t)r * ld + cs + j];
-        m.re -= ar;
-        m.im -= ai;
+  // rows below the leaf, panel columns right of it: A -= L_leaf U_leaf, with the leaf's L from
+  // shared memory and its just-solved U block read once into shared memory after it; consecutive
+  // threads take consecutive columns of a row (coalesced read-modify-write)
+  const int cs = c0 + lw, wr = pend - cs;
+  if (wr > 0 && rows > lw) {
+    __syncthreads();  // this CTA's U-block writes above are complete
+    Cx<S>* U = L + (size_t)rows * lw;  // [lw][wr]
+    for (int t = tid; t < lw * wr; t += nt) {
+      const int s = t / wr, j = t - s * wr;
+      U[t] = M[(int64_t)(c0 + s) * ld + cs + j];
+    }
+    __syncthreads();
+    for (int t = tid; t < (rows - lw) * wr; t += nt) {
+      const int rr = t / wr, j = t - rr * wr, r = lw + rr;
+      Cx<S>& m = M[(int64_t)(c0 + r) * ld + cs + j];
+      Cx<S> a = m;
+      for (int s2 = 0; s2 < lw; ++s2) {
+        const Cx<S> l = L[s2 * rows + r], u = U[s2 * wr + j];
+        a.re -= l.re * u.re - l.im * u.im;
+        a.im -= l.re * u.im + l.im * u.re;
       }
+      m = a;
     }
   }
 }
 
-// Leaf width for a panel whose rows start at p0: the widest power of two <= 8 whose leaf fits in
-// 200 KB of shared memory; 0 if even one column does not fit (then the global-memory panel runs).
+// Leaf width for a panel whose rows start at p0: the widest power of two <= 8 whose leaf and U
+// block (lw x 64) fit in 200 KB of shared memory; 0 if even one column does not fit (then the
+// global-memory panel runs).
 template <class S>
 static int leaf_width(int n, int p0) {
   const size_t rows = (size_t)(n - p0);
   for (int lw = 8; lw >= 1; lw >>= 1)
-    if (rows * lw * sizeof(Cx<S>) <= 200 * 1024) return lw;
+    if ((rows + 64) * lw * sizeof(Cx<S>) <= 200 * 1024) return lw;
   return 0;
 }
 
@@ -259,13 +241,9 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
   BIE_TRY((set_smem_max(k_leaf<S>)));
   for (int c0 = p0; c0 < p0 + w; c0 += lw) {
     const int l = std::min(lw, p0 + w - c0);
-    const size_t smem = (size_t)(n - c0) * l * sizeof(Cx<S>);
+    const int wr = std::max(0, std::min(p0 + w, n) - c0 - l);  // panel columns right of the leaf
+    const size_t smem = ((size_t)(n - c0) * l + (size_t)l * wr) * sizeof(Cx<S>);
     BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info));
-    const int rows = n - c0 - l;
-    if (rows > 0 && c0 + l < p0 + w) {
-      dim3 g((unsigned)((rows + 63) / 64), batch);
-      BIE_LAUNCH(k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l));
-    }
   }
   return BIE_OK;
 }
