@@ -130,7 +130,7 @@ __device__ __forceinline__ void load_point(const float* __restrict__ tab, int64_
 
 // grid: (ceil(N / rows), nk); block: 32 * rows * W (W warps share a row: the elements of one
 // colour share no node, so they can scatter into the row concurrently; colours are separated by
-// block barriers); dynamic smem: rows * N * sizeof(cf)
+// a barrier of the row's warps); dynamic smem: rows * N * sizeof(cf)
 constexpr int ASM_W = 2;
 __global__ void __launch_bounds__(512) k_asm32_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
         }
       }
     }
-    __syncthreads();
+    bar_named(1 + rw, 32 * ASM_W);  // the row's warps finish the colour (rows <= 8: ids 1..8)
   }
   // reduce the compensated sums across the warp in FP64 (12 values per row)
   double v[12] = {(double)S.ar.s, (double)S.ar.c, (double)S.ai.s, (double)S.ai.c, (double)S.br.s, (double)S.br.c,

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
         }
       }
     }
-    __syncthreads();
+    bar_named(1 + rw, 32 * ASMF_W);  // the row's warps finish the colour (rows <= 8: ids 1..8)
   }
   // combine the lanes' and the row's warps' sums in FP64
   double v[6] = {ff_to_double(alr), ff_to_double(ali), ff_to_double(ber), ff_to_double(bei), ff_to_double(bsr),

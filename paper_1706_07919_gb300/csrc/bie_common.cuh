@@ -273,6 +273,12 @@ __device__ __forceinline__ void cis_reduced(float vh, float vl, float& c, float&
   s = (qi >= 2) ? -b : b;
 }
 
+// Barrier of the nthreads threads (whole warps) that use barrier `id` (1..15; 0 is
+// __syncthreads); orders their shared- and global-memory accesses like __syncthreads.
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Compensated (Kahan-Babuska/Neumaier) running sum in FP32.
 struct ksum {
   float s = 0.0f, c = 0.0f;

@@ -212,27 +212,48 @@ int upload_geometry_tables(bie_ctx* c) {
   return BIE_OK;
 }
 
-// Greedy colouring of the element/node incidence: elements of one colour share no node, so a
-// warp can scatter one collocation row's contributions of a whole colour without conflicts.
+// Equitable colouring of the element/node incidence: elements of one colour share no node, so the
+// lanes working on one collocation row can scatter a whole colour's contributions into the row
+// without conflicts.  The bulk assembly kernels give one row 64 lanes (two warps; the FP64 kernel
+// one warp), so colours hold at most kColourCap = 64 elements and as few colours as possible are
+// used: then every pass over a colour keeps (nearly) all lanes busy.  Greedy: each element takes
+// the least-filled colour among those that are neither full nor used by an element sharing a node
+// with it.  With C colours, at most ceil(E / cap) of them full and at most D (the most elements
+// one element shares a node with) in conflict, a colour is always free once C > E / cap + D, so
+// the retry loop (C + 1 after a failure) ends.
+constexpr int kColourCap = 64;
 int build_colouring(bie_ctx* c) {
   const int64_t N = c->N, E = c->E;
   std::vector<std::vector<int32_t>> n2e(N);
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 6; ++a) n2e[c->h_elems[6 * e + a]].push_back((int32_t)(e * 8 + a));
   std::vector<int> colour(E, -1);
-  int ncol = 0;
-  std::vector<char> used;
-  for (int64_t e = 0; e < E; ++e) {
-    used.assign(ncol + 1, 0);
-    for (int a = 0; a < 6; ++a)
-      for (int32_t ea : n2e[c->h_elems[6 * e + a]]) {
-        int cc = colour[ea / 8];
-        if (cc >= 0) used[cc] = 1;
+  int ncol = (int)std::max<int64_t>(1, (E + kColourCap - 1) / kColourCap);
+  std::vector<int> fill_count, used;
+  for (;;) {
+    std::fill(colour.begin(), colour.end(), -1);
+    fill_count.assign(ncol, 0);
+    used.assign(ncol, -1);
+    bool ok = true;
+    for (int64_t e = 0; e < E && ok; ++e) {
+      for (int a = 0; a < 6; ++a)
+        for (int32_t ea : n2e[c->h_elems[6 * e + a]]) {
+          const int cc = colour[ea / 8];
+          if (cc >= 0) used[cc] = (int)e;
+        }
+      int best = -1;
+      for (int cc = 0; cc < ncol; ++cc)
+        if (used[cc] != (int)e && fill_count[cc] < kColourCap && (best < 0 || fill_count[cc] < fill_count[best]))
+          best = cc;
+      if (best < 0) {
+        ok = false;
+        break;
       }
-    int cc = 0;
-    while (cc < ncol && used[cc]) ++cc;
-    colour[e] = cc;
-    if (cc == ncol) ++ncol;
+      colour[e] = best;
+      ++fill_count[best];
+    }
+    if (ok) break;
+    ++ncol;
   }
   std::vector<int32_t> off(ncol + 1, 0), perm(E);
   for (int64_t e = 0; e < E; ++e) off[colour[e] + 1]++;
