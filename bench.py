@@ -603,7 +603,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=128)
-    ap.add_argument("--tc", type=int, default=2, help="LU trailing update: 2 TMA-fed tcgen05, 1 register-staged tcgen05, 0 SIMT")
+    ap.add_argument("--tc", type=int, default=3,
+                    help="LU trailing update: 3 TMA-fed tcgen05 deferred over 256 columns, 2 after every 64-column "
+                         "panel, 1 register-staged tcgen05, 0 SIMT")
     ap.add_argument("--check", type=int, default=4)
     ap.add_argument("--cpu-points", dest="cpu_points", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

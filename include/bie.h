@@ -165,9 +165,11 @@ int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t
 int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
 
 /* Tuning options of the mixed-precision path (names are case-sensitive):
- *   "mixed.tcgen05"        trailing LU update: 2 (default) persistent TMA-fed tcgen05 kernel
- *                          (TF32 operands, FP32 accumulation in TMEM), 1 the register-staged
- *                          tcgen05 kernel, 0 FP32 on the CUDA cores.
+ *   "mixed.tcgen05"        trailing LU update: 3 (default) persistent TMA-fed tcgen05 kernel
+ *                          (TF32 operands, FP32 accumulation in TMEM) with the update of the
+ *                          trailing matrix deferred over 256-column blocks (four 64-column
+ *                          panels), 2 the same kernel after every 64-column panel, 1 the
+ *                          register-staged tcgen05 kernel, 0 FP32 on the CUDA cores.
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
@@ -262,7 +264,7 @@ int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64
 /* Autotuner of the mixed path (not part of the paper's method, which fixes no launch parameters):
  * for the context's geometry, times one batch of BIE_MODE_MIXED solves (sample wavenumbers
  * k host f64 [nk], repeated to fill the batch) for every candidate of "mixed.batch" in
- * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {2, 0},
+ * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {3, 2},
  * and sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
  * file keyed by N rounded up to 64; an entry for this N is applied without measuring, a new
  * measurement is added to it.  out (host, optional) receives the choice.  Synchronises.

@@ -258,8 +258,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   const std::string n(name);
   if (!std::isfinite(value)) return fail(BIE_ERR_INVALID_ARG, "option value must be finite");
   if (n == "mixed.tcgen05") {
-    if (value != 0.0 && value != 1.0 && value != 2.0)
-      return fail(BIE_ERR_INVALID_ARG, "mixed.tcgen05 must be 0 (SIMT), 1 or 2 (tensor-core kernels)");
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+      return fail(BIE_ERR_INVALID_ARG, "mixed.tcgen05 must be 0 (SIMT), 1, 2 or 3 (tensor-core kernels)");
     c->tc_version = (int)value;
   } else if (n == "mixed.batch") {
     if (value < 1 || value > 4096) return fail(BIE_ERR_INVALID_ARG, "mixed.batch must be in [1, 4096]");

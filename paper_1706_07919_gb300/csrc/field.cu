@@ -453,11 +453,12 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
                                                        const int32_t* __restrict__ foot_elem,
                                                        const double* __restrict__ foot, const double* __restrict__ kv,
                                                        int nk, cd* __restrict__ T, TwoPi3f tp, int uniform, ff dk) {
-  __shared__ float sg[13][TP];
-  __shared__ float sq[KB][4][TP];
-  __shared__ float s0[KB][4][TP];
+  __shared__ float4 sg[TP][4];  // the quadrature point's 13 table values (P32 order), padded to 16
+  __shared__ float4 sq[KB][TP];  // surface values at the quadrature points: P re, im, dP re, im
+  __shared__ float4 s0[KB][TP];  // surface values at the foot points, same order
   __shared__ float sacc[KB][4][TP];  // compensated sums: re (s, c), im (s, c)
-  __shared__ float sk[KB][3];
+  __shared__ float2 sk[KB];  // k (FP32 head), 1 / k
+  __shared__ float sklo[KB];  // k - head
   const int kbase = blockIdx.y * KB;
   const int nkb = min(KB, nk - kbase);
   const int tid = threadIdx.x;
@@ -465,9 +466,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   const bool active = m < M;
   if (tid < nkb) {
     const ff k = ff_from_double(kv[kbase + tid]);
-    sk[tid][0] = k.hi;
-    sk[tid][1] = k.lo;
-    sk[tid][2] = (float)(1.0 / kv[kbase + tid]);
+    sk[tid] = make_float2(k.hi, (float)(1.0 / kv[kbase + tid]));
+    sklo[tid] = k.lo;
   }
 #pragma unroll
   for (int j = 0; j < KB; ++j)
@@ -493,8 +493,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
         a0 += Nv[a] * v.re; a1 += Nv[a] * v.im;
         b0 += Nv[a] * w.re; b1 += Nv[a] * w.im;
       }
-      s0[j][0][tid] = (float)a0; s0[j][1][tid] = (float)a1;
-      s0[j][2][tid] = (float)b0; s0[j][3][tid] = (float)b1;
+      s0[j][tid] = make_float4((float)a0, (float)a1, (float)b0, (float)b1);
     }
   }
   float pr[KB], pim[KB];
@@ -504,21 +503,22 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
     const int64_t t = t0 + tid;
     __syncthreads();
     if (t < EQ) {
+      float* g = reinterpret_cast<float*>(sg[tid]);
 #pragma unroll
-      for (int u = 0; u < 13; ++u) sg[u][tid] = qtab[u * EQ + t];
+      for (int u = 0; u < 13; ++u) g[u] = qtab[u * EQ + t];
       for (int j = 0; j < nkb; ++j) {
         const cf a = Pq[(int64_t)(kbase + j) * EQ + t], b = Pnq[(int64_t)(kbase + j) * EQ + t];
-        sq[j][0][tid] = a.re; sq[j][1][tid] = a.im;
-        sq[j][2][tid] = b.re; sq[j][3][tid] = b.im;
+        sq[j][tid] = make_float4(a.re, a.im, b.re, b.im);
       }
     }
     __syncthreads();
     const int cnt = (EQ - t0) < TP ? (int)(EQ - t0) : TP;
     if (!active) continue;
     for (int u = 0; u < cnt; ++u) {
-      const ff qx = {sg[0][u], sg[3][u]}, qy = {sg[1][u], sg[4][u]}, qz = {sg[2][u], sg[5][u]};
-      const float nx = sg[6][u], ny = sg[7][u], nz = sg[8][u], wj = sg[9][u];
-      const ff nux = {nx, sg[10][u]}, nuy = {ny, sg[11][u]}, nuz = {nz, sg[12][u]};
+      const float4 g0 = sg[u][0], g1 = sg[u][1], g2 = sg[u][2], g3 = sg[u][3];
+      const ff qx = {g0.x, g0.w}, qy = {g0.y, g1.x}, qz = {g0.z, g1.y};
+      const float nx = g1.z, ny = g1.w, nz = g2.x, wj = g2.y;
+      const ff nux = {nx, g2.z}, nuy = {ny, g2.w}, nuz = {nz, g3.x};
       const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
       const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
       const ff Rp = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
       float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
       if (uniform) {
-        const ff k0 = {sk[0][0], sk[0][1]};
+        const ff k0 = {sk[0].x, sklo[0]};
         cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
         cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
         cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
@@ -546,9 +546,10 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
 #pragma unroll
       for (int j = 0; j < KB; ++j) {
         if (j < nkb) {
-          const float khi = sk[j][0], kinv = sk[j][2];
+          const float2 kj = sk[j];
+          const float khi = kj.x, kinv = kj.y;
           if (!uniform) {
-            const ff k = {khi, sk[j][1]};
+            const ff k = {khi, sklo[j]};
             cis_ffk(ff_mul(k, Rp), tp, cp, spp);
             cis_ffk(ff_mul(k, R0), tp, c0, s0v);
             cis_ffk(ff_mul(k, nr), tp, cg, sgv);
@@ -568,9 +569,10 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
           const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
           const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
           const float g = cg, f = sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
-          const float P0r = s0[j][0][tid], P0i = s0[j][1][tid], Q0r = s0[j][2][tid], Q0i = s0[j][3][tid];
-          const float Ptr = sq[j][0][u] - P0r * g - Q0r * f, Pti = sq[j][1][u] - P0i * g - Q0i * f;
-          const float dPr = sq[j][2][u] - P0r * dg - Q0r * df, dPi = sq[j][3][u] - P0i * dg - Q0i * df;
+          const float4 p0 = s0[j][tid], pq = sq[j][u];
+          const float P0r = p0.x, P0i = p0.y, Q0r = p0.z, Q0i = p0.w;
+          const float Ptr = pq.x - P0r * g - Q0r * f, Pti = pq.y - P0i * g - Q0i * f;
+          const float dPr = pq.z - P0r * dg - Q0r * df, dPi = pq.w - P0i * dg - Q0i * df;
           const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
           const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
           const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
     for (int j = 0; j < nkb; ++j) {
       const double sr = (double)sacc[j][0][tid] + (double)sacc[j][1][tid];
       const double si = (double)sacc[j][2][tid] + (double)sacc[j][3][tid];
-      T[(int64_t)(kbase + j) * M + m] = {(double)s0[j][0][tid] + sr * inv4pi, (double)s0[j][1][tid] + si * inv4pi};
+      T[(int64_t)(kbase + j) * M + m] = {(double)s0[j][tid].x + sr * inv4pi, (double)s0[j][tid].y + si * inv4pi};
     }
   }
 }

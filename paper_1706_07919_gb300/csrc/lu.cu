@@ -249,10 +249,13 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
 }
 
 // ---- row swaps outside the panel, then U12 = L11^{-1} A12 ----------------------------------
-// grid: (ceil(n / 128), batch), block 128: one column per thread.
+// grid: (ceil((n - jlo) / 128), batch), block 128: one column j >= jlo per thread.  With swaps != 0
+// the panel's row swaps are applied (in order) to every column outside the panel; the forward
+// substitution with the unit lower L11 runs for the columns in [p0 + nb, tend).
 template <class S>
 __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
-                                                   int nb, const int32_t* __restrict__ piv) {
+                                                   int nb, const int32_t* __restrict__ piv, int jlo, int tend,
+                                                   int swaps) {
   Cx<S>* M = A + (int64_t)blockIdx.y * bstride;
   const int32_t* pv = piv + (int64_t)blockIdx.y * n;
   extern __shared__ unsigned char smem_raw[];
@@ -264,17 +267,18 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
     L11[t] = M[(int64_t)(p0 + r) * ld + p0 + cc];
   }
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = jlo + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n || (j >= p0 && j < pend)) return;
-  for (int s = p0; s < pend; ++s) {
-    int p = pv[s];
-    if (p != s) {
-      Cx<S> t = M[(int64_t)s * ld + j];
-      M[(int64_t)s * ld + j] = M[(int64_t)p * ld + j];
-      M[(int64_t)p * ld + j] = t;
+  if (swaps)
+    for (int s = p0; s < pend; ++s) {
+      int p = pv[s];
+      if (p != s) {
+        Cx<S> t = M[(int64_t)s * ld + j];
+        M[(int64_t)s * ld + j] = M[(int64_t)p * ld + j];
+        M[(int64_t)p * ld + j] = t;
+      }
     }
-  }
-  if (j < pend) return;  // columns left of the panel only get the swaps
+  if (j < pend || j >= tend) return;  // columns left of the panel (or past tend) only get the swaps
   // forward substitution with the unit lower L11; solved entries are re-read from the column
   for (int s = 1; s < w; ++s) {
     Cx<S> v = M[(int64_t)(p0 + s) * ld + j];
@@ -395,7 +399,8 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
     const int w = std::min(nb, n - p0);
     BIE_TRY(panel_factor<S>(c, A, batch, n, ld, bstride, p0, w, piv, info));
     dim3 gs((unsigned)((n + 127) / 128), batch);
-    BIE_LAUNCH(k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv));
+    BIE_LAUNCH(k_swap_trsm<S><<<gs, 128, (size_t)w * w * sizeof(Cx<S>), c->stream>>>(A, bstride, n, ld, p0, w, piv,
+                                                                                     0, n, 1));
     const int rem = n - p0 - w;
     if (rem > 0) {
       dim3 gg((unsigned)((rem + 63) / 64), (unsigned)((rem + 63) / 64), batch);
@@ -406,14 +411,28 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
   return BIE_OK;
 }
 
-// Panel factorisation plus row swaps / U12 solve of one block column (FP32); the trailing update
-// is left to the caller (the tensor-core kernel of lu_tc.cu).
+// Panel factorisation plus row swaps (all columns) and the U12 solve of the columns in
+// [p0 + w, tend) for one block column (FP32); the trailing update is left to the caller (the
+// tensor-core kernels of lu_tc.cu).
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info) {
+                     int32_t* info, int tend) {
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
   dim3 gs((unsigned)((n + 127) / 128), batch);
-  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv));
+  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv,
+                                                                                          0, tend, 1));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+// U = L11^{-1} A for rows [p0, p0 + w) and the columns [jlo, n), L11 the unit lower diagonal block
+// at (p0, p0) (FP32; no swaps).
+int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo) {
+  if (jlo >= n) return BIE_OK;
+  Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
+  dim3 gs((unsigned)((n - jlo + 127) / 128), batch);
+  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
+                                                                                          nullptr, jlo, n, 0));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

@@ -22,7 +22,8 @@
 namespace bie {
 
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info);
+                     int32_t* info, int tend);
+int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo);
 
 namespace tc {
 
@@ -223,10 +224,6 @@ __global__ void __launch_bounds__(128, 2) k_update_tc(float* __restrict__ A, int
 
 }  // namespace tc
 
-size_t lu_tc_scratch_bytes(int batch, int n) {
-  return 256 + (size_t)batch * 2 * n * (2 * tc::NB) * sizeof(float);  // error flag + B^T of the real embedding
-}
-
 // ==============================================================================================
 // Version 2: persistent, warp-specialised, TMA-fed update with the complex product written as a
 // real GEMM on the interleaved storage (real embedding):
@@ -309,38 +306,48 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// B^T of the real embedding for the current panel: rows 2c, 2c+1 for trailing column c
-// (relative to p0 + NB), 2K floats each: [ur, -ui, ...] and [ui, ur, ...].  grid (ceil(rem/32), batch)
-__global__ void __launch_bounds__(256) k_build_ub(const float* __restrict__ A, int64_t bstride, int n, int ld, int p0,
-                                                  float* __restrict__ ub, int64_t ub_stride) {
+// B^T of the real embedding for 64 rows of U (rows u0 .. u0+63 of A, row k = u0 + kk): for
+// column c in [cb, cend), B^T rows 2 (c - cb) and 2 (c - cb) + 1 get, at floats koff + 2 kk,
+// [ur, -ui] and [ui, ur] (rows `krow` floats long).  Columns at or past n are zero.
+// grid (ceil((cend - cb) / 32), batch)
+__global__ void __launch_bounds__(256) k_build_ub(const float* __restrict__ A, int64_t bstride, int n, int ld, int u0,
+                                                  int cb, int cend, float* __restrict__ ub, int64_t ub_stride,
+                                                  int krow, int koff) {
   __shared__ float2 t[tc::NB][33];
   const int z = blockIdx.y;
-  const int rbase = p0 + tc::NB, c0 = blockIdx.x * 32;
+  const int c0 = blockIdx.x * 32;
   const float* M = A + (int64_t)z * bstride * 2;
-  for (int e = threadIdx.x; e < tc::NB * 32; e += blockDim.x) {  // U12 rows k, columns c0..c0+31
+  for (int e = threadIdx.x; e < tc::NB * 32; e += blockDim.x) {  // U rows k, columns cb + c0 .. +31
     const int k = e / 32, cc = e % 32;
-    const int gc = rbase + c0 + cc;
+    const int gc = cb + c0 + cc;
     float2 u = make_float2(0.f, 0.f);
-    if (gc < n) u = *reinterpret_cast<const float2*>(M + 2 * ((int64_t)(p0 + k) * ld + gc));
+    if (gc < n && gc < cend) u = *reinterpret_cast<const float2*>(M + 2 * ((int64_t)(u0 + k) * ld + gc));
     t[k][cc] = u;
   }
   __syncthreads();
   float* out = ub + (int64_t)z * ub_stride;
   for (int e = threadIdx.x; e < 32 * tc::NB; e += blockDim.x) {
     const int cc = e / tc::NB, k = e % tc::NB;
+    if (cb + c0 + cc >= cend) continue;
     const float2 u = t[k][cc];
     const int64_t r = 2 * (int64_t)(c0 + cc);
     const float ur = tc::to_tf32(u.x), ui = tc::to_tf32(u.y);  // round to nearest TF32 once here
-    *reinterpret_cast<float2*>(out + r * KR + 2 * k) = make_float2(ur, -ui);
-    *reinterpret_cast<float2*>(out + (r + 1) * KR + 2 * k) = make_float2(ui, ur);
+    *reinterpret_cast<float2*>(out + r * krow + koff + 2 * k) = make_float2(ur, -ui);
+    *reinterpret_cast<float2*>(out + (r + 1) * krow + koff + 2 * k) = make_float2(ui, ur);
   }
 }
 
+// One update region: rows [r0, r1), complex columns [c0, c1) of every matrix get
+//   A -= L U,  L = A[rows][kc0 .. kc0 + 16 nchk),  U from the B^T map (row 2 (c - ub_c0)),
+// in tiles of 128 rows x 64 complex columns.  Rows at or past r1 inside the last row tile are
+// left unchanged (their share of the tile is zeroed before the reduction).
+struct Region {
+  int r0, r1, c0, c1, kc0, nchk, ub_c0, ntm, ntn;
+};
+
 __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constant__ CUtensorMap tmA,
-                                                           const __grid_constant__ CUtensorMap tmB,
-                                                           float* __restrict__ A, int64_t bstride, int n, int ld,
-                                                           int p0, int batch, int ntm, int ntn,
-                                                           int32_t* __restrict__ err) {
+                                                           const __grid_constant__ CUtensorMap tmB, int batch,
+                                                           const Region rg, int32_t* __restrict__ err) {
   extern __shared__ unsigned char smraw[];
   __shared__ Bars bar;
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -368,8 +375,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = bar.tmem_slot;
+  const int ntm = rg.ntm, ntn = rg.ntn, nchk = rg.nchk;
   const int ntiles = batch * ntm * ntn;
-  const int rbase = p0 + tc::NB;
 
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer ----
@@ -377,13 +384,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int z = tile / (ntm * ntn), rr = tile % (ntm * ntn), tm = rr / ntn, tn = rr % ntn;
-        for (int ch = 0; ch < NCHK && ok; ++ch, ++it) {
+        for (int ch = 0; ch < nchk && ok; ++ch, ++it) {
           const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
           ok = mbar_wait(baddr(bar.empty[s]), ph ^ 1, err);
           if (!ok) break;
           mbar_expect_tx(baddr(bar.full[s]), A_STAGE + B_STAGE);
-          tma_load_3d(smA + s * A_STAGE, &tmA, 2 * p0 + ch * KCH, rbase + tm * BM, z, baddr(bar.full[s]));
-          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, tn * BNR, z, baddr(bar.full[s]));
+          tma_load_3d(smA + s * A_STAGE, &tmA, 2 * rg.kc0 + ch * KCH, rg.r0 + tm * BM, z, baddr(bar.full[s]));
+          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, 2 * (rg.c0 - rg.ub_c0) + tn * BNR, z, baddr(bar.full[s]));
         }
       }
     }
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d = tmem + a * BNR;
-        for (int ch = 0; ch < NCHK && ok; ++ch, ++it) {
+        for (int ch = 0; ch < nchk && ok; ++ch, ++it) {
           const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
           ok = mbar_wait(baddr(bar.full[s]), ph, err);
           if (!ok) break;
@@ -435,8 +442,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
       asm volatile("bar.sync 1, 128;\n" ::: "memory");
       if (*(volatile uint32_t*)&bar.abort) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int gr0 = rbase + tm * BM;
-      const int gc0 = 2 * (rbase + tn * (BNR / 2));  // first real column of the tile
+      const int gr0 = rg.r0 + tm * BM;
+      const int gc0 = 2 * (rg.c0 + tn * (BNR / 2));  // first real column of the tile
+      const bool keep = gr0 + rt < rg.r1;             // rows past r1 add zero
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * BNR;
 #pragma unroll 1
       for (int cc = 0; cc < BNR; cc += 32, ++nb) {
@@ -450,8 +458,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
 #pragma unroll
         for (int c4 = 0; c4 < 8; ++c4) {
           const uint32_t off = (uint32_t)rt * 128 + (uint32_t)((c4 ^ (rt & 7)) * 16);
-          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(box + off), "f"(-v[4 * c4]),
-                       "f"(-v[4 * c4 + 1]), "f"(-v[4 * c4 + 2]), "f"(-v[4 * c4 + 3])
+          const float4 o = keep ? make_float4(-v[4 * c4], -v[4 * c4 + 1], -v[4 * c4 + 2], -v[4 * c4 + 3])
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(box + off), "f"(o.x), "f"(o.y), "f"(o.z),
+                       "f"(o.w)
                        : "memory");
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -507,43 +517,100 @@ static int make_map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d
 
 }  // namespace tc2
 
+// Version 3 (the default): the update of version 2, with the trailing update deferred over an
+// outer block of NBO = 256 columns (four 64-column panels), so that A22 is read and written once
+// per 256 columns instead of once per 64 (intensity 8 x 256 / 16 = 128 flop per byte of A22):
+//   for each outer block [P0, E):
+//     for each panel [p0, p0 + 64): factor it; swap rows in every column; U = L11^{-1} A for the
+//       block's columns right of the panel; update rows below the panel in the block's columns
+//       right of it (K = 64).  Columns at or past E get only the swaps.
+//     U12 (block rows, columns >= E) by block forward substitution: for each 64-row block b,
+//       A_b -= L_b,<b U_<b (K = 64 b), then U_b = L_bb^{-1} A_b.
+//     A22 (rows and columns >= E) -= L21 U12 with K = 256.
+constexpr int NBO = 256;
+
+size_t lu_tc_scratch_bytes(int batch, int n) {
+  // error flag, B^T for one 64-row panel (128 floats per row) and for one outer block (512)
+  return 256 + (size_t)batch * 2 * n * (2 * tc::NB + 2 * NBO) * sizeof(float);
+}
+
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
                  void* scratch, size_t scratch_bytes) {
   using namespace tc;
   if (ld % 64 != 0 || bstride % 2 != 0) return fail(BIE_ERR_INVALID_ARG, "tcgen05 LU needs ld % 64 == 0 and even batch stride");
   int32_t* err = (int32_t*)scratch;
   BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
-  const bool v2 = c->tc_version >= 2;
+  const int ver = c->tc_version;
   float* ub = reinterpret_cast<float*>((char*)scratch + 256);
-  const int64_t ub_stride = (int64_t)2 * n * tc2::KR;  // floats per matrix
-  CUtensorMap mA, mB;
+  const int64_t ub_stride = (int64_t)2 * n * tc2::KR;  // floats per matrix, 64-row panel
+  float* ubo = ub + (int64_t)batch * ub_stride;
+  const int64_t ubo_stride = (int64_t)2 * n * (2 * NBO);  // floats per matrix, outer block
+  const float* Af = reinterpret_cast<const float*>(A);
+  CUtensorMap mA, mB, mBo;
   int nsm = 148;
-  if (v2) {
-    if (scratch_bytes < 256 + (size_t)batch * ub_stride * sizeof(float))
-      return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
+  if (ver >= 2) {
+    if (scratch_bytes < lu_tc_scratch_bytes(batch, n)) return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
     BIE_TRY(tc2::make_map_3d(&mA, A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)batch, (uint64_t)2 * ld * 4,
                              (uint64_t)bstride * 8));
     BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)tc2::KR, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)tc2::KR * 4,
                              (uint64_t)ub_stride * 4));
+    BIE_TRY(tc2::make_map_3d(&mBo, ubo, (uint64_t)2 * NBO, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)2 * NBO * 4,
+                             (uint64_t)ubo_stride * 4));
     BIE_TRY((set_smem_max(tc2::k_update_tc2)));
     BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   } else {
     BIE_TRY((set_smem_max(k_update_tc)));
   }
+  // B^T of U rows u0 .. u0+63, columns [cb, cend), into the panel (o = 0) or outer-block buffer
+  auto build = [&](int u0, int cb, int cend, bool outer, int koff) -> int {
+    if (cend <= cb) return BIE_OK;
+    dim3 gb((unsigned)((cend - cb + 31) / 32), (unsigned)batch);
+    BIE_LAUNCH(tc2::k_build_ub<<<gb, 256, 0, c->stream>>>(Af, bstride, n, ld, u0, cb, cend, outer ? ubo : ub,
+                                                          outer ? ubo_stride : ub_stride, outer ? 2 * NBO : tc2::KR,
+                                                          koff));
+    return BIE_OK;
+  };
+  auto update = [&](int r0, int r1, int c0, int c1, int kc0, int kcols, bool outer, int ub_c0) -> int {
+    if (r1 <= r0 || c1 <= c0 || kcols <= 0) return BIE_OK;
+    tc2::Region rg{r0, r1, c0, c1, kc0, 2 * kcols / tc2::KCH, ub_c0, (r1 - r0 + tc2::BM - 1) / tc2::BM,
+                   (c1 - c0 + tc2::BNR / 2 - 1) / (tc2::BNR / 2)};
+    const int ntiles = rg.ntm * rg.ntn * batch;
+    const int grid = std::min(ntiles, nsm);
+    BIE_LAUNCH(tc2::k_update_tc2<<<grid, tc2::NTHREADS, tc2::SMEM_BYTES, c->stream>>>(mA, outer ? mBo : mB, batch, rg,
+                                                                                     err));
+    return BIE_OK;
+  };
+  if (ver >= 3) {
+    for (int P0 = 0; P0 < n; P0 += NBO) {
+      const int E = std::min(n, P0 + NBO);
+      for (int p0 = P0; p0 < E; p0 += NB) {
+        const int w = std::min(NB, E - p0), q = p0 + w;
+        BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E));
+        if (q < E) {  // then w == 64 (E - P0 is a multiple of 64 unless E == n)
+          BIE_TRY(build(p0, q, E, false, 0));
+          BIE_TRY(update(q, n, q, E, p0, w, false, q));
+        }
+      }
+      if (E >= n) continue;  // E - P0 == NBO from here on
+      for (int b = 0; b < NBO / NB; ++b) {
+        const int Rb = P0 + b * NB;
+        BIE_TRY(update(Rb, Rb + NB, E, n, P0, b * NB, true, E));
+        BIE_TRY(lu_trsm_rows32(c, A, batch, n, ld, bstride, Rb, NB, E));
+        BIE_TRY(build(Rb, E, n, true, 2 * NB * b));
+      }
+      BIE_TRY(update(E, n, E, n, P0, NBO, true, E));
+    }
+    BIE_CUDA_TRY(cudaGetLastError());
+    return BIE_OK;
+  }
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int w = std::min(NB, n - p0);
-    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info));
+    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n));
     const int rem = n - p0 - w;
     if (rem <= 0) continue;
-    if (v2) {
-      dim3 gb((unsigned)((rem + 31) / 32), (unsigned)batch);
-      BIE_LAUNCH(tc2::k_build_ub<<<gb, 256, 0, c->stream>>>(reinterpret_cast<const float*>(A), bstride, n, ld, p0, ub,
-                                                            ub_stride));
-      const int ntm = (rem + tc2::BM - 1) / tc2::BM, ntn = (rem + tc2::BNR / 2 - 1) / (tc2::BNR / 2);
-      const int ntiles = ntm * ntn * batch;
-      const int grid = std::min(ntiles, nsm);
-      BIE_LAUNCH(tc2::k_update_tc2<<<grid, tc2::NTHREADS, tc2::SMEM_BYTES, c->stream>>>(
-          mA, mB, reinterpret_cast<float*>(A), bstride, n, ld, p0, batch, ntm, ntn, err));
+    if (ver == 2) {
+      BIE_TRY(build(p0, p0 + NB, n, false, 0));
+      BIE_TRY(update(p0 + NB, n, p0 + NB, n, p0, NB, false, p0 + NB));
     } else {
       dim3 g((unsigned)((rem + BN - 1) / BN), (unsigned)((rem + BM - 1) / BM), (unsigned)batch);
       BIE_LAUNCH(k_update_tc<<<g, 128, SMEM_BYTES, c->stream>>>(reinterpret_cast<float*>(A), bstride, n, ld, p0, err));

@@ -40,7 +40,7 @@ static std::map<int, TuneEntry> load_cache(const char* path) {
     double us = 0.0;
     if (std::sscanf(s.c_str() + i, "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"us_per_k\": %lf}", &key, &b, &t, &us) ==
             4 &&
-        b >= 1 && (t == 0 || t == 1 || t == 2))
+        b >= 1 && t >= 0 && t <= 3)
       m[key] = TuneEntry{b, t, us};
   }
   return m;
@@ -92,7 +92,7 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = BIE_OK;
   const int batches[] = {8, 16, 32, 64, 128, 256};
-  const int tcs[] = {2, 0};
+  const int tcs[] = {3, 2};
   size_t surf_bytes = (size_t)256 * 2 * N * sizeof(cd);
   if (cudaMalloc(&surf, surf_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)

@@ -46,7 +46,7 @@ def two_spheres():
     return merge_meshes([scale_translate(s0, 1.0, (0, 0, -1.05)), scale_translate(s0, 1.0, (0, 0, 1.05))])
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_mixed_sphere_all_wavenumbers(Solver, B, tc):
     w = config_sphere_fp64()
     s = _solver(Solver, w.mesh, tc=tc)
@@ -65,7 +65,7 @@ def test_mixed_sphere_all_wavenumbers(Solver, B, tc):
     assert all(not (rep[i].flags & (B.BIE_FLAG_NOT_CONVERGED | B.BIE_FLAG_FALLBACK_FP64)) for i in range(len(w.k)))
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_mixed_two_spheres_high_k(Solver, B, two_spheres, tc):
     ks = np.array([0.5, 4.0, 9.3, 16.0])
     s = _solver(Solver, two_spheres, tc=tc)
@@ -77,7 +77,7 @@ def test_mixed_two_spheres_high_k(Solver, B, two_spheres, tc):
         assert rep[i].iters <= 8 and rep[i].flags == 0, (k, rep[i].iters, rep[i].flags, rep[i].err_est)
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_unrefined_lu_accuracy(Solver, B, two_spheres, tc):
     """With refinement switched off the answer is the low-precision factor's: FP32 (SIMT) or
     TF32 (tensor cores) rounding times the condition number -- a broken update would be O(1)."""
