@@ -262,11 +262,13 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
   Cx<S>* L11 = reinterpret_cast<Cx<S>*>(smem_raw);  // [nb][nb]
   const int pend = min(p0 + nb, n);
   const int w = pend - p0;
-  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-    int r = t / w, cc = t % w;
-    L11[t] = M[(int64_t)(p0 + r) * ld + p0 + cc];
+  if (tend > pend) {  // some column is solved: stage L11
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int r = t / w, cc = t % w;
+      L11[t] = M[(int64_t)(p0 + r) * ld + p0 + cc];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int j = jlo + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n || (j >= p0 && j < pend)) return;
   if (swaps)
@@ -290,6 +292,42 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
     }
     M[(int64_t)(p0 + s) * ld + j] = v;
   }
+}
+
+// ---- U = L11^{-1} A for a full 64-row panel, FP32: the column lives in registers -------------
+// grid (ceil((j1 - j0) / 128), batch), block 128, static smem 32 KB: one column j in [j0, j1) per
+// thread.  The 64 entries of the column are loaded once, solved in registers (the loops are fully
+// unrolled, so x[] never leaves the register file) and stored once: no solved entry is re-read
+// from global memory, where each re-read would wait on the L2.  L11 is read from shared memory as
+// pairs of entries (16-byte broadcasts).  Same operations, in the same order, as k_swap_trsm.
+__global__ void __launch_bounds__(128) k_trsm64(Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                                int j0, int j1) {
+  __shared__ __align__(16) Cx<float> L11[64 * 64];
+  Cx<float>* M = A + (int64_t)blockIdx.y * bstride;
+  for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) L11[t] = M[(int64_t)(p0 + (t >> 6)) * ld + p0 + (t & 63)];
+  __syncthreads();
+  const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j1 || j >= n) return;
+  Cx<float> x[64];
+#pragma unroll
+  for (int s = 0; s < 64; ++s) x[s] = M[(int64_t)(p0 + s) * ld + j];
+#pragma unroll
+  for (int s = 1; s < 64; ++s) {
+    Cx<float> v = x[s];
+#pragma unroll
+    for (int t = 0; t < s; t += 2) {
+      const float4 l2 = *reinterpret_cast<const float4*>(&L11[s * 64 + t]);  // entries t, t+1
+      v.re -= l2.x * x[t].re - l2.y * x[t].im;
+      v.im -= l2.x * x[t].im + l2.y * x[t].re;
+      if (t + 1 < s) {
+        v.re -= l2.z * x[t + 1].re - l2.w * x[t + 1].im;
+        v.im -= l2.z * x[t + 1].im + l2.w * x[t + 1].re;
+      }
+    }
+    x[s] = v;
+  }
+#pragma unroll
+  for (int s = 1; s < 64; ++s) M[(int64_t)(p0 + s) * ld + j] = x[s];
 }
 
 // ---- SIMT trailing update A22 -= L21 U12 (64 x 64 complex tile per CTA, 256 threads) ---------
@@ -419,8 +457,16 @@ int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstrid
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
   dim3 gs((unsigned)((n + 127) / 128), batch);
-  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w, piv,
-                                                                                          0, tend, 1));
+  if (w == 64) {  // swaps here, the solve with the register-resident kernel
+    BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, 0, c->stream>>>(M, bstride, n, ld, p0, w, piv, 0, p0 + w, 1));
+    if (tend > p0 + w) {
+      dim3 gt((unsigned)((tend - p0 - w + 127) / 128), batch);
+      BIE_LAUNCH(k_trsm64<<<gt, 128, 0, c->stream>>>(M, bstride, n, ld, p0, p0 + w, tend));
+    }
+  } else {
+    BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
+                                                                                            piv, 0, tend, 1));
+  }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -431,8 +477,11 @@ int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride,
   if (jlo >= n) return BIE_OK;
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   dim3 gs((unsigned)((n - jlo + 127) / 128), batch);
-  BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
-                                                                                          nullptr, jlo, n, 0));
+  if (w == 64)
+    BIE_LAUNCH(k_trsm64<<<gs, 128, 0, c->stream>>>(M, bstride, n, ld, p0, jlo, n));
+  else
+    BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
+                                                                                            nullptr, jlo, n, 0));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
