@@ -243,7 +243,7 @@ constexpr int BNR = 128;                 // real columns per tile (64 complex)
 constexpr int KR = 2 * tc::NB;           // reals along K (128)
 constexpr int KCH = 32;                  // floats per 128-byte swizzle row
 constexpr int NCHK = KR / KCH;           // 4 chunks per tile
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
 constexpr int B_STAGE = BNR * KCH * 4;   // 16 KB
 constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 2 * A_STAGE + 1024;  // ring + 2 epilogue boxes
