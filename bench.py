@@ -160,6 +160,7 @@ def run_ours(args):
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_incident_plane_wave(w.direction)
     sol.set_option("mixed.tcgen05", args.tc)
+    sol.set_option("mixed.asm_kb", args.asm_kb)
     sol.set_option("mixed.batch", args.batch)
     midx = np.arange(1, Nk + 1, dtype=np.int64)
 
@@ -557,6 +558,7 @@ def run_case(args):
     sol = Solver(0)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_option("mixed.tcgen05", args.tc)
+    sol.set_option("mixed.asm_kb", args.asm_kb)
     if args.case == "step":
         sol.set_incident_plane_wave(w.direction)
         sol.set_option("mixed.batch", args.batch)
@@ -603,6 +605,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--asm-kb", type=int, default=2,
+                    help="FP32 bulk assembly: wavenumbers per thread (2, 1) or 0 for the general kernel")
     ap.add_argument("--tc", type=int, default=3,
                     help="LU trailing update: 3 TMA-fed tcgen05 deferred over 256 columns, 2 after every 64-column "
                          "panel, 1 register-staged tcgen05, 0 SIMT")

@@ -234,6 +234,203 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
   }
 }
 
+// Known boundary values at the quadrature points of the colour-sorted elements:
+//   kq[k][qq][t] = sum_a N_a(q_qq) known[k][el_t[a]]  (FP32 complex)
+// so that an element whose six nodes share one boundary condition adds its right-hand-side share
+// as sum_q w_q K_q kq_q (K = G on a hard element, -dG/dnu on a soft one) instead of carrying the
+// six nodal sums of both kernels.  grid (ceil(E / 256), nk), block 256.
+__global__ void k_known_q32(const int32_t* __restrict__ esort, int64_t E, int Q, const float* __restrict__ qshape,
+                            const cd* __restrict__ known, int64_t N, cf* __restrict__ kq) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int kk = blockIdx.y;
+  if (t >= E) return;
+  cd kn[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) kn[a] = known[(int64_t)kk * N + esort[a * E + t]];
+  for (int qq = 0; qq < Q; ++qq) {
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const double sh = qshape[qq * 6 + a];
+      sr += sh * kn[a].re;
+      si += sh * kn[a].im;
+    }
+    kq[((int64_t)kk * Q + qq) * E + t] = {(float)sr, (float)si};
+  }
+}
+
+// Bulk assembly for meshes whose elements each carry one boundary condition on all six nodes
+// (every element of a sound-hard or sound-soft body), KB wavenumbers per thread: the geometry of
+// a (row, quadrature point) pair -- float-float r, R, nu_i.r, r.nu_q -- is formed once and used
+// for KB wavenumbers, each with its own float-float phases (no recurrence: every entry keeps the
+// accuracy of the one-wavenumber kernel).  Per element and wavenumber a lane carries the six nodal
+// sums of the one kernel that enters A (dG/dnu on a hard element, -G on a soft one), the
+// right-hand-side sum against the interpolated known values kq, and the two regularisation sums.
+// A row has ASM_W x QS warps: ASM_W warps take consecutive elements of a colour and, with QS = 2,
+// a second set of ASM_W warps takes the other half of the same elements' quadrature points, so
+// that the registers of KB = 2 fit 16 warps per SM; the halves add into the row one after the
+// other (barrier of the row's warps in between: fixed order, deterministic sums).
+// grid (ceil(N / rows), ceil(nk / KB)); block 32 * rows * ASM_W * QS; smem rows * KB * N cf.
+template <int KB, int QS>
+__global__ void __launch_bounds__(256) k_asm32_bulk_u(
+    const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
+    const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
+    const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
+    const double* __restrict__ kv, int nk, const cf* __restrict__ kq, cf* __restrict__ A, int64_t lda,
+    double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp, float far_r2) {
+  constexpr int WR = ASM_W * QS;  // warps per row
+  extern __shared__ cf acc32[];
+  __shared__ float shp[64 * 6];
+  __shared__ double part[8][WR][KB][6];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rw = warp / WR, wr = warp % WR, sub = wr % ASM_W, h = wr / ASM_W;
+  const int k0 = blockIdx.y * KB;
+  const int nkb = min(KB, nk - k0);
+  ff k[KB];
+  float kinv[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) {
+    const int kj = min(k0 + j, nk - 1);  // a ragged last group repeats its last wavenumber
+    k[j] = ff_from_double(kv[kj]);
+    kinv[j] = (float)(1.0 / kv[kj]);
+  }
+  for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
+  for (int64_t t = threadIdx.x; t < (int64_t)rows * KB * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * rows + rw;
+  const bool valid = i < N;
+  const int qlo = h * Q / QS, qhi = (h + 1) * Q / QS;
+  ff xi[3], nui[3];
+  for (int d = 0; d < 3; ++d) {
+    xi[d] = ff_from_double(valid ? nodes[3 * i + d] : 0.0);
+    nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
+  }
+  RowSums S[KB];
+  for (int col = 0; col < ncolors; ++col) {
+    const int32_t cbeg = color_off[col], cend = color_off[col + 1];
+    // the same trip count for all warps of the row (the barriers below are the row's)
+    const int iters = valid ? (cend - cbeg + 32 * ASM_W - 1) / (32 * ASM_W) : 0;
+    for (int it = 0; it < iters; ++it) {
+      const int32_t t = cbeg + it * 32 * ASM_W + sub * 32 + lane;
+      bool act = t < cend;
+      int32_t el[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        el[a] = act ? esort[a * E + t] : 0;
+        if (el[a] == i) act = false;  // near pair: the near kernel's
+      }
+      float ar[KB][6], ai[KB][6];
+#pragma unroll
+      for (int j = 0; j < KB; ++j)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) ar[j][a] = ai[j][a] = 0.f;
+      if (act) {
+        const bool soft = bc[el[0]] != 0;
+        float sr[KB], si[KB], ear[KB], eai[KB], ebr[KB], ebi[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) sr[j] = si[j] = ear[j] = eai[j] = ebr[j] = ebi[j] = 0.f;
+        for (int qq = qlo; qq < qhi; ++qq) {
+          float q[P32COUNT];
+#pragma unroll
+          for (int f = 0; f < P32COUNT; ++f) q[f] = qtab[((int64_t)f * Q + qq) * E + t];
+          // geometry, shared by the KB wavenumbers
+          const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
+          const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
+          const ff rz = ff_sub(ff{q[2], q[5]}, xi[2]);
+          const ff R2 = ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz));
+          const ff R = ff_sqrt(R2);
+          const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
+          const float invR = 1.0f / R.hi;
+          float rnu;
+          if (R2.hi > far_r2)
+            rnu = rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8];
+          else
+            rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]}))
+                      .hi;
+          const float rn = rnu * invR * invR * invR;
+          const float nn = nui[0].hi * q[6] + nui[1].hi * q[7] + nui[2].hi * q[8];
+          const float wj = q[P32W];
+          float sh[6];
+#pragma unroll
+          for (int a = 0; a < 6; ++a) sh[a] = shp[qq * 6 + a];
+#pragma unroll
+          for (int j = 0; j < KB; ++j) {
+            float c, s;
+            ff_cis(ff_mul(k[j], R), tp, c, s);
+            const float kR = k[j].hi * R.hi;
+            const float Gr = c * invR, Gi = s * invR;
+            const float dGr = (-c - s * kR) * rn, dGi = (c * kR - s) * rn;
+            float cg, sg;
+            ff_cis(ff_mul(k[j], nr), tp, cg, sg);
+            const float g = cg, f = sg * kinv[j], dg = -k[j].hi * sg * nn, df = cg * nn;
+            ear[j] = __fmaf_rn(wj, g * dGr - dg * Gr, ear[j]);
+            eai[j] = __fmaf_rn(wj, g * dGi - dg * Gi, eai[j]);
+            ebr[j] = __fmaf_rn(wj, f * dGr - df * Gr, ebr[j]);
+            ebi[j] = __fmaf_rn(wj, f * dGi - df * Gi, ebi[j]);
+            // into A: dG (hard) or -G (soft); into b: G kq (hard) or -dG kq (soft)
+            const float war = wj * (soft ? -Gr : dGr), wai = wj * (soft ? -Gi : dGi);
+            const float wbr = wj * (soft ? -dGr : Gr), wbi = wj * (soft ? -dGi : Gi);
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+              ar[j][a] = __fmaf_rn(sh[a], war, ar[j][a]);
+              ai[j][a] = __fmaf_rn(sh[a], wai, ai[j][a]);
+            }
+            const cf kqv = kq[((int64_t)min(k0 + j, nk - 1) * Q + qq) * E + t];
+            sr[j] = __fmaf_rn(wbr, kqv.re, __fmaf_rn(-wbi, kqv.im, sr[j]));
+            si[j] = __fmaf_rn(wbr, kqv.im, __fmaf_rn(wbi, kqv.re, si[j]));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+          S[j].ar.add(ear[j]); S[j].ai.add(eai[j]);
+          S[j].br.add(ebr[j]); S[j].bi.add(ebi[j]);
+          S[j].sr.add(sr[j]); S[j].si.add(si[j]);
+        }
+      }
+      // scatter into the row: the quadrature halves one after the other
+#pragma unroll
+      for (int hh = 0; hh < QS; ++hh) {
+        if (act && h == hh) {
+#pragma unroll
+          for (int j = 0; j < KB; ++j) {
+            cf* row = acc32 + ((int64_t)rw * KB + j) * N;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+              row[el[a]].re += ar[j][a];
+              row[el[a]].im += ai[j][a];
+            }
+          }
+        }
+        if (QS > 1) bar_named(1 + rw, 32 * WR);
+      }
+    }
+    if (QS == 1) bar_named(1 + rw, 32 * WR);  // the row's warps finish the colour (rows <= 8: ids 1..8)
+  }
+  // reduce the compensated sums across the warp in FP64 (6 values per row and wavenumber)
+#pragma unroll
+  for (int j = 0; j < KB; ++j) {
+    const ksum* v[6] = {&S[j].ar, &S[j].ai, &S[j].br, &S[j].bi, &S[j].sr, &S[j].si};
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      double x = (double)v[u]->s + (double)v[u]->c;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) part[rw][wr][j][u] = x;
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  for (int j = 0; j < nkb; ++j) {
+    const cf* row = acc32 + ((int64_t)rw * KB + j) * N;
+    cf* Arow = A + ((int64_t)(k0 + j) * N + i) * lda;
+    for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) Arow[c2] = row[c2];
+    if (wr == 0 && lane < 6) {
+      double x = 0.0;
+      for (int w = 0; w < WR; ++w) x += part[rw][w][j][lane];
+      rowsum[((int64_t)(k0 + j) * N + i) * 6 + lane] = x;
+    }
+  }
+}
+
 // Near pairs (element contains node i) and the diagonal terms; one warp per row.
 __global__ void __launch_bounds__(256) k_asm32_near(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
@@ -359,9 +556,10 @@ int ensure_mixed_tables(bie_ctx* c) {
   return BIE_OK;
 }
 
-// Assembles nk FP32 systems: A [nk][N][lda] (cf), b [nk][N] (cd).  known [nk][N] (cd) must hold
-// the known boundary values on return it is filled here; rowsum scratch: nk * N * 6 doubles.
-int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum) {
+// Assembles nk FP32 systems: A [nk][N][lda] (cf), b [nk][N] (cd).  known [nk][N] (cd) receives the
+// known boundary values; rowsum scratch: nk * N * 6 doubles; kq scratch: nk * E * Q cf (the known
+// values at the quadrature points, used by the uniform-condition bulk kernel; may be NULL).
+int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq) {
   const int64_t N = c->N;
   BIE_TRY(ensure_mixed_tables(c));
   dim3 gk((unsigned)((N + 255) / 256), nk);
@@ -387,12 +585,47 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
       }
     c->far_r2 = 9.0 * h2;
   }
-  BIE_TRY((set_smem_max(k_asm32_bulk)));
-  dim3 gb((unsigned)((N + rows - 1) / rows), nk);
-  BIE_LAUNCH(k_asm32_bulk<<<gb, 32 * rows * ASM_W, smem, c->stream>>>(c->nodes, c->normals, c->bc, sorted_elems(c), N,
-                                                                      c->E, c->rule.Q, sorted_table(c), c->qshape32,
-                                                                      c->color_off, c->ncolors, kv, known, A, lda,
-                                                                      rowsum, rows, tp, (float)c->far_r2));
+  if (c->uniform_bc < 0) {  // does every element carry one condition on its six nodes?
+    c->uniform_bc = 1;
+    for (int64_t e = 0; e < c->E && c->uniform_bc; ++e)
+      for (int a = 1; a < 6; ++a)
+        if (c->h_bc[c->h_elems[6 * e + a]] != c->h_bc[c->h_elems[6 * e]]) c->uniform_bc = 0;
+  }
+  // the uniform-condition kernel: KB = 2 wavenumbers per thread with the quadrature points of an
+  // element split over two warps (2 rows x 4 warps), or KB = 1 (4 rows x 2 warps); 256 threads
+  int kb = (kq && c->uniform_bc == 1) ? c->asm_kb : 0;
+  if (kb == 2 && (size_t)2 * 2 * N * sizeof(cf) > 100 * 1024) kb = 1;  // two CTAs per SM
+  int urows = 4;
+  if (kb == 1)
+    while (urows > 1 && (size_t)urows * N * sizeof(cf) > 200 * 1024) urows /= 2;
+  if (kb == 2) urows = 2;
+  if (kb == 1 && (size_t)urows * N * sizeof(cf) > 200 * 1024) kb = 0;
+  if (kb >= 1) {
+    const int64_t E = c->E;
+    dim3 gq((unsigned)((E + 255) / 256), nk);
+    BIE_LAUNCH(k_known_q32<<<gq, 256, 0, c->stream>>>(sorted_elems(c), E, c->rule.Q, c->qshape32, known, N, kq));
+    const size_t usmem = (size_t)urows * kb * N * sizeof(cf);
+    dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)((nk + kb - 1) / kb));
+    if (kb == 2) {
+      BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2>)));
+      BIE_LAUNCH(k_asm32_bulk_u<2, 2><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
+          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_table(c), c->qshape32, c->color_off,
+          c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+    } else {
+      BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1>)));
+      BIE_LAUNCH(k_asm32_bulk_u<1, 1><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
+          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_table(c), c->qshape32, c->color_off,
+          c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+    }
+  }
+  if (kb == 0) {
+    BIE_TRY((set_smem_max(k_asm32_bulk)));
+    dim3 gb((unsigned)((N + rows - 1) / rows), nk);
+    BIE_LAUNCH(k_asm32_bulk<<<gb, 32 * rows * ASM_W, smem, c->stream>>>(c->nodes, c->normals, c->bc, sorted_elems(c), N,
+                                                                        c->E, c->rule.Q, sorted_table(c), c->qshape32,
+                                                                        c->color_off, c->ncolors, kv, known, A, lda,
+                                                                        rowsum, rows, tp, (float)c->far_r2));
+  }
   BIE_CUDA_TRY(cudaGetLastError());
   const int64_t nq = c->E * c->rule.Q;
   dim3 gn((unsigned)((N * 32 + 255) / 256), nk);

@@ -129,6 +129,9 @@ struct bie_ctx {
   int field_variant = 1;             // mixed field kernel: 1 k_field32c (16 wavenumbers per group,
                                      // 64 points per CTA), 0 k_field32b (8 per group, 128 points)
   int assemble_ff = 0;               // bie_assemble: bulk pairs in float-float (1) or FP64 (0)
+  int uniform_bc = -1;               // every element has one condition on all nodes (1), not (0), unknown
+  int asm_kb = 2;                    // FP32 bulk assembly: wavenumbers per thread (1, 2), 0 = the
+                                     // general kernel (also taken when an element mixes conditions)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)

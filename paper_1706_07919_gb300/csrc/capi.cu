@@ -127,6 +127,7 @@ static void free_geometry(bie_ctx* c) {
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
   c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr;
   c->far_r2 = 0.0;
+  c->uniform_bc = -1;
   c->has_geom = false;
 }
 
@@ -278,6 +279,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   } else if (n == "field.variant") {
     if (value != 0.0 && value != 1.0) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0 or 1");
     c->field_variant = (int)value;
+  } else if (n == "mixed.asm_kb") {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(BIE_ERR_INVALID_ARG, "mixed.asm_kb must be 0, 1 or 2");
+    c->asm_kb = (int)value;
   } else if (n == "assemble.bulk_ff") {
     c->assemble_ff = value != 0.0 ? 1 : 0;
   } else if (n == "mixed.reassembly") {

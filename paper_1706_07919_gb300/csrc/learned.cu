@@ -20,7 +20,7 @@ namespace bie {
 
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
                 int32_t* perm_keep, cf* d_keep);
-int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum);
+int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq);
 int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstride, const cd* b, cd* x, const cf* LU,
                 int64_t lu_bstride, const int32_t* perm, const cf* Dinv, const int32_t* sel, int m, int cycles,
                 double inner_tol, double tol, void* scratch, void* state_dev);
@@ -210,8 +210,9 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   const int m = c->gmres_m;
   const size_t mat = align256((size_t)N * ld * sizeof(cf));
   const size_t vec = align256((size_t)N * sizeof(cd));
+  const size_t kqb = align256((size_t)c->E * c->rule.Q * sizeof(cf));  // known values at quadrature points
   const size_t perk = mat + 5 * vec + align256((size_t)N * 6 * sizeof(double)) + gmres_scratch_bytes(1, (int)N, m) +
-                      2 * align256(refine_state_bytes(1)) + 64;
+                      2 * align256(refine_state_bytes(1)) + kqb + 64;
   size_t free_b = 0, total_b = 0;
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t avail = free_b / 2 + c->work.bytes;  // the mixed path's workspace is reused
@@ -235,6 +236,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   int32_t* dst = (int32_t*)take((size_t)kb * 4);
   double* rel = (double*)take((size_t)kb * 2 * 8);
   void* gscr = take(gmres_scratch_bytes((int)kb, (int)N, m));
+  cf* kqs = (cf*)take(kb * kqb);
   const int64_t bstride = (int64_t)(mat / sizeof(cf));
   const int64_t lu_bstride = N * ld;
   std::vector<int32_t> done(kb), iters(kb), dd(kb), di(kb);
@@ -256,7 +258,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_CUDA_TRY(cudaMemcpyAsync(sel, hs.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemcpyAsync(dst, hd.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
-    BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum));
+    BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum, kqs));
     BIE_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
     if (c->learned_x0 == 1) {
       BIE_TRY(mlp_predict_dev(c, kdev, nk, x));

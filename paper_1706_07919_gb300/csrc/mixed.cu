@@ -11,7 +11,7 @@
 
 namespace bie {
 
-int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum);
+int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq);
 int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch, bool ff_bulk);
 int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
@@ -101,7 +101,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   auto batch_core = [&](const double* ksrc, int nk) -> int {
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, ksrc, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
-    BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum));
+    BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum, LU));  // LU is free until the copy below
     BIE_CUDA_TRY(cudaMemcpyAsync(LU, A, (size_t)nk * mat, cudaMemcpyDeviceToDevice, c->stream));
     if (c->tc_version > 0)
       BIE_TRY(lu_factor_tc(c, LU, nk, (int)N, (int)ld, bstride, piv, info, tcs, tc_scratch));

@@ -159,3 +159,38 @@ def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B, ff):
         assert rep[i].flags & B.BIE_FLAG_FP64_ASSEMBLY and not rep[i].flags & B.BIE_FLAG_FALLBACK_FP64
         P, Pn = oracle.solve_frequency(w.mesh, k, D)
         assert rel(surf[i, 0], P) <= 1e-8, (k, rel(surf[i, 0], P))
+
+
+@pytest.mark.parametrize("kb", [0, 1, 2])
+def test_bulk_assembly_variants_match_oracle(Solver, B, two_spheres, kb):
+    """The FP32 bulk assembly with one (general kernel, kb 0) or several wavenumbers per thread
+    (uniform-condition kernel, kb 1 and 2) gives the oracle's solution; five wavenumbers leave a
+    ragged last group of the two-wavenumber kernel, and soft and hard bodies are mixed."""
+    m = merge_meshes([scale_translate(ico_sphere(3, bc=1), 0.8, (0, 0, -1.0)),
+                      scale_translate(ico_sphere(3), 1.0, (0.1, 0, 1.2))])
+    ks = np.array([0.7, 3.3, 6.2, 9.1, 12.5])
+    s = _solver(Solver, m)
+    s.set_option("mixed.asm_kb", kb)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(m, k, D)
+        assert rel(surf[i, 0], P) <= TOL and rel(surf[i, 1], Pn) <= TOL, (k, rep[i].flags)
+        assert not (rep[i].flags & (B.BIE_FLAG_NOT_CONVERGED | B.BIE_FLAG_FALLBACK_FP64))
+
+
+def test_bulk_assembly_element_with_mixed_conditions(Solver, B):
+    """An element whose nodes carry different boundary conditions sends the assembly to the
+    general kernel even when the multi-wavenumber kernel is selected."""
+    m = octa_sphere(2)
+    bc = m.bc.copy()
+    bc[m.elems[0, :3]] = 1  # the three vertices of element 0 soft, its mid-edge nodes hard
+    m.bc = bc
+    ks = np.array([1.1, 4.4, 7.3])
+    s = _solver(Solver, m)
+    s.set_option("mixed.asm_kb", 2)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(m, k, D)
+        assert rel(surf[i, 0], P) <= TOL and rel(surf[i, 1], Pn) <= TOL, k
