@@ -525,8 +525,11 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
       const ff R0 = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
       const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
       const float iRp = 1.0f / Rp.hi, iR0 = 1.0f / R0.hi;
-      const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp * iRp;
-      const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0 * iR0;
+      // the recurrences below carry the weighted kernels Gp = w e^{ik Rp} / Rp and G0 (same for
+      // the foot point); then dG/dnu = G (ik R - 1) r.nu / R^2
+      const float ap = wj * iRp, a0 = wj * iR0;
+      const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp;
+      const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0;
       const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
       float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
@@ -542,6 +545,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
         cis_reduced(h, __fmaf_rn(dk.hi, R0.hi, -h) + (dk.hi * R0.lo + dk.lo * R0.hi), dc0, ds0);
         h = dk.hi * nr.hi;
         cis_reduced(h, __fmaf_rn(dk.hi, nr.hi, -h) + (dk.hi * nr.lo + dk.lo * nr.hi), dcg, dsg);
+        cp *= ap; spp *= ap;
+        c0 *= a0; s0v *= a0;
       }
 #pragma unroll
       for (int j = 0; j < KB; ++j) {
@@ -553,6 +558,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
             cis_ffk(ff_mul(k, Rp), tp, cp, spp);
             cis_ffk(ff_mul(k, R0), tp, c0, s0v);
             cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+            cp *= ap; spp *= ap;
+            c0 *= a0; s0v *= a0;
           } else if (j > 0) {
             float t = cp * dcp - spp * dsp;
             spp = spp * dcp + cp * dsp;
@@ -565,7 +572,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
             cg = t;
           }
           const float kRp = khi * Rp.hi, kR0 = khi * R0.hi;
-          const float Gpr = cp * iRp, Gpi = spp * iRp, G0r = c0 * iR0, G0i = s0v * iR0;
+          const float Gpr = cp, Gpi = spp, G0r = c0, G0i = s0v;  // weighted by w
           const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
           const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
           const float g = cg, f = sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
@@ -574,10 +581,15 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
           const float Ptr = pq.x - P0r * g - Q0r * f, Pti = pq.y - P0i * g - Q0i * f;
           const float dPr = pq.z - P0r * dg - Q0r * df, dPi = pq.w - P0i * dg - Q0i * df;
           const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
-          const float tr = (Ptr * ddr - Pti * ddi) - (gdr * dPr - gdi * dPi);
-          const float ti = (Ptr * ddi + Pti * ddr) - (gdr * dPi + gdi * dPr);
-          pr[j] = __fmaf_rn(wj, tr, pr[j]);
-          pim[j] = __fmaf_rn(wj, ti, pim[j]);
+          // run sums of w [P~ (dGp - dG0) - (Gp - G0) dP~]
+          float a = __fmaf_rn(Ptr, ddr, pr[j]);
+          a = __fmaf_rn(-Pti, ddi, a);
+          a = __fmaf_rn(-gdr, dPr, a);
+          pr[j] = __fmaf_rn(gdi, dPi, a);
+          a = __fmaf_rn(Ptr, ddi, pim[j]);
+          a = __fmaf_rn(Pti, ddr, a);
+          a = __fmaf_rn(-gdr, dPi, a);
+          pim[j] = __fmaf_rn(-gdi, dPr, a);
         }
       }
       if ((u & 31) == 31 || u == cnt - 1) {  // add the run to the compensated sums
