@@ -431,6 +431,19 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
   }
 }
 
+// One level of a warp's halving exchange: v[0 .. 2 HALF) per lane; the lane keeps the upper or
+// lower half (by `upper`), adds its partner's (lane ^ o) copy of that half and stores it in
+// v[0 .. HALF).
+template <int HALF>
+__device__ __forceinline__ void halving_exchange(double* v, int o, bool upper) {
+#pragma unroll
+  for (int m = 0; m < HALF; ++m) {
+    const double send = upper ? v[m] : v[m + HALF];
+    const double keep = upper ? v[m + HALF] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+
 // Near pairs (element contains node i) and the diagonal terms; one warp per row.
 __global__ void __launch_bounds__(256) k_asm32_near(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
@@ -452,47 +465,75 @@ __global__ void __launch_bounds__(256) k_asm32_near(
   }
   const int64_t tot = E * 6 * (int64_t)QN;
   cf* Arow = A + ((int64_t)kk * N + i) * lda;
-  double al_r = 0, al_i = 0, be_r = 0, be_i = 0, bs_r = 0, bs_i = 0;
+  // The regularisation sums per lane in compensated FP32 (they cancel against the bulk's) and the
+  // nodal sums per lane in FP32 (a lane holds a few points of one element); across the warp the
+  // nodal sums go to FP64 and are reduced by halving exchanges (36 FP64 additions per lane instead
+  // of 120 for six separate butterflies), so that each of six lanes ends with one node's four sums:
+  // the GB300's FP64 pipe is too narrow for per-point FP64 arithmetic here.
+  ksum sal_r, sal_i, sbe_r, sbe_i;
+  double bs_r = 0, bs_i = 0;
+  const int node = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   for (int32_t t = n2e_off[i]; t < n2e_off[i + 1]; ++t) {
     const int32_t e = n2e[t] >> 3, a0 = n2e[t] & 7;
     const int np = nnear_d[a0];
-    double hr[6], hi[6], gr[6], gi[6];
-    for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.0; }
+    float hr[6], hi[6], gr[6], gi[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.f; }
     for (int qq = lane; qq < np; qq += 32) {
       float q[P32COUNT];
       load_point(ntab, tot, ((int64_t)e * 6 + a0) * QN + qq, q);
       Kern32 K;
       kernel32(k, kinv, xi, nui, tp, q, K);
-      const double wj = q[P32W];
-      al_r += wj * K.alr; al_i += wj * K.ali;
-      be_r += wj * K.ber; be_i += wj * K.bei;
+      const float wj = q[P32W];
+      // w K enters exactly: the product's rounding error joins the compensation term
+      auto add_exact = [&](ksum& acc, float x) {
+        const float p = wj * x;
+        acc.add(p);
+        acc.c += __fmaf_rn(wj, x, -p);
+      };
+      add_exact(sal_r, K.alr); add_exact(sal_i, K.ali);
+      add_exact(sbe_r, K.ber); add_exact(sbe_i, K.bei);
       const double* sh = nshape + ((int64_t)a0 * QN + qq) * 6;
+#pragma unroll
       for (int a = 0; a < 6; ++a) {
-        const double cw = wj * sh[a];
-        hr[a] += cw * K.dGr; hi[a] += cw * K.dGi;
-        gr[a] += cw * K.Gr;  gi[a] += cw * K.Gi;
+        const float cw = wj * (float)sh[a];
+        hr[a] = __fmaf_rn(cw, K.dGr, hr[a]); hi[a] = __fmaf_rn(cw, K.dGi, hi[a]);
+        gr[a] = __fmaf_rn(cw, K.Gr, gr[a]);  gi[a] = __fmaf_rn(cw, K.Gi, gi[a]);
       }
     }
-    for (int a = 0; a < 6; ++a)
-      for (int o = 16; o > 0; o >>= 1) {
-        hr[a] += __shfl_xor_sync(0xffffffffu, hr[a], o); hi[a] += __shfl_xor_sync(0xffffffffu, hi[a], o);
-        gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o); gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
-      }
-    if (lane == 0) {
-      const int32_t* el = elems + 6 * (int64_t)e;
-      for (int a = 0; a < 6; ++a) {
-        const int32_t j = el[a];
-        const cd kj = kn[j];
-        if (bc[j] == 0) {
-          Arow[j].re += (float)hr[a]; Arow[j].im += (float)hi[a];
-          bs_r += gr[a] * kj.re - gi[a] * kj.im; bs_i += gr[a] * kj.im + gi[a] * kj.re;
-        } else {
-          Arow[j].re -= (float)gr[a]; Arow[j].im -= (float)gi[a];
-          bs_r -= hr[a] * kj.re - hi[a] * kj.im; bs_i -= hr[a] * kj.im + hi[a] * kj.re;
-        }
+    double v[32];  // node a: v[4a .. 4a+3] = h re, h im, g re, g im; nodes 6, 7 are padding
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      v[4 * a] = hr[a]; v[4 * a + 1] = hi[a]; v[4 * a + 2] = gr[a]; v[4 * a + 3] = gi[a];
+    }
+#pragma unroll
+    for (int m = 24; m < 32; ++m) v[m] = 0.0;
+    halving_exchange<16>(v, 16, (lane & 16) != 0);
+    halving_exchange<8>(v, 8, (lane & 8) != 0);
+    halving_exchange<4>(v, 4, (lane & 4) != 0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[m] += __shfl_xor_sync(0xffffffffu, v[m], 2);
+      v[m] += __shfl_xor_sync(0xffffffffu, v[m], 1);
+    }
+    if ((lane & 3) == 0 && node < 6) {  // this lane holds node `node`'s sums
+      const int32_t j = elems[6 * (int64_t)e + node];
+      const cd kj = kn[j];
+      if (bc[j] == 0) {
+        Arow[j].re += (float)v[0]; Arow[j].im += (float)v[1];
+        bs_r += v[2] * kj.re - v[3] * kj.im; bs_i += v[2] * kj.im + v[3] * kj.re;
+      } else {
+        Arow[j].re -= (float)v[2]; Arow[j].im -= (float)v[3];
+        bs_r -= v[0] * kj.re - v[1] * kj.im; bs_i -= v[0] * kj.im + v[1] * kj.re;
       }
     }
+    __syncwarp();  // the next element (sharing nodes with this one) updates after these writes
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    bs_r += __shfl_xor_sync(0xffffffffu, bs_r, o);
+    bs_i += __shfl_xor_sync(0xffffffffu, bs_i, o);
+  }
+  double al_r = sal_r.value(), al_i = sal_i.value(), be_r = sbe_r.value(), be_i = sbe_i.value();
   for (int o = 16; o > 0; o >>= 1) {
     al_r += __shfl_xor_sync(0xffffffffu, al_r, o); al_i += __shfl_xor_sync(0xffffffffu, al_i, o);
     be_r += __shfl_xor_sync(0xffffffffu, be_r, o); be_i += __shfl_xor_sync(0xffffffffu, be_i, o);
