@@ -434,21 +434,21 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
 // One level of a warp's halving exchange: v[0 .. 2 HALF) per lane; the lane keeps the upper or
 // lower half (by `upper`), adds its partner's (lane ^ o) copy of that half and stores it in
 // v[0 .. HALF).
-template <int HALF>
-__device__ __forceinline__ void halving_exchange(double* v, int o, bool upper) {
+template <int HALF, class T>
+__device__ __forceinline__ void halving_exchange(T* v, int o, bool upper) {
 #pragma unroll
   for (int m = 0; m < HALF; ++m) {
-    const double send = upper ? v[m] : v[m + HALF];
-    const double keep = upper ? v[m + HALF] : v[m];
+    const T send = upper ? v[m] : v[m + HALF];
+    const T keep = upper ? v[m + HALF] : v[m];
     v[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
   }
 }
 
 // Near pairs (element contains node i) and the diagonal terms; one warp per row.
-__global__ void __launch_bounds__(256) k_asm32_near(
+__global__ void __launch_bounds__(128) k_asm32_near(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ elems, int64_t N, int64_t E, int QN, const int* __restrict__ nnear_d,
-    const float* __restrict__ ntab, const double* __restrict__ nshape, const int32_t* __restrict__ n2e_off,
+    const float* __restrict__ ntab, const float* __restrict__ nshape, const int32_t* __restrict__ n2e_off,
     const int32_t* __restrict__ n2e, const double* __restrict__ kv, const cd* __restrict__ known,
     cf* __restrict__ A, int64_t lda, const double* __restrict__ rowsum, cd* __restrict__ b, TwoPi3 tp) {
   const int lane = threadIdx.x & 31;
@@ -493,23 +493,28 @@ __global__ void __launch_bounds__(256) k_asm32_near(
       };
       add_exact(sal_r, K.alr); add_exact(sal_i, K.ali);
       add_exact(sbe_r, K.ber); add_exact(sbe_i, K.bei);
-      const double* sh = nshape + ((int64_t)a0 * QN + qq) * 6;
+      const float* sh = nshape + ((int64_t)a0 * QN + qq) * 6;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        const float cw = wj * (float)sh[a];
+        const float cw = wj * sh[a];
         hr[a] = __fmaf_rn(cw, K.dGr, hr[a]); hi[a] = __fmaf_rn(cw, K.dGi, hi[a]);
         gr[a] = __fmaf_rn(cw, K.Gr, gr[a]);  gi[a] = __fmaf_rn(cw, K.Gi, gi[a]);
       }
     }
-    double v[32];  // node a: v[4a .. 4a+3] = h re, h im, g re, g im; nodes 6, 7 are padding
+    // node a: u[4a .. 4a+3] = h re, h im, g re, g im; nodes 6, 7 are padding.  The first two
+    // levels add partial sums of 2 and 4 lanes in FP32 (small against the total), the rest in FP64.
+    float u[32];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-      v[4 * a] = hr[a]; v[4 * a + 1] = hi[a]; v[4 * a + 2] = gr[a]; v[4 * a + 3] = gi[a];
+      u[4 * a] = hr[a]; u[4 * a + 1] = hi[a]; u[4 * a + 2] = gr[a]; u[4 * a + 3] = gi[a];
     }
 #pragma unroll
-    for (int m = 24; m < 32; ++m) v[m] = 0.0;
-    halving_exchange<16>(v, 16, (lane & 16) != 0);
-    halving_exchange<8>(v, 8, (lane & 8) != 0);
+    for (int m = 24; m < 32; ++m) u[m] = 0.f;
+    halving_exchange<16>(u, 16, (lane & 16) != 0);
+    halving_exchange<8>(u, 8, (lane & 8) != 0);
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = u[m];
     halving_exchange<4>(v, 4, (lane & 4) != 0);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -669,9 +674,9 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
   }
   BIE_CUDA_TRY(cudaGetLastError());
   const int64_t nq = c->E * c->rule.Q;
-  dim3 gn((unsigned)((N * 32 + 255) / 256), nk);
-  BIE_LAUNCH(k_asm32_near<<<gn, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
-                                          c->qgeo32 + P32COUNT * nq, c->nshape, c->n2e_off, c->n2e, kv, known, A, lda,
+  dim3 gn((unsigned)((N * 32 + 127) / 128), nk);
+  BIE_LAUNCH(k_asm32_near<<<gn, 128, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
+                                          c->qgeo32 + P32COUNT * nq, c->nshape32, c->n2e_off, c->n2e, kv, known, A, lda,
                                           rowsum, b, tp));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -103,6 +103,7 @@ struct bie_ctx {
   double* ngeo = nullptr;      // near points:     GCOUNT x [E*6*QN]
   double* qshape = nullptr;    // [Q][6] shape values at the standard points
   double* nshape = nullptr;    // [6][QN][6] shape values at the near points
+  float* nshape32 = nullptr;   // the same in FP32 (mixed path)
   float* qgeo32 = nullptr;     // mixed path standard points: see asm32.cu for the layout
   float* qshape32 = nullptr;   // [Q][6]
   int ncolors = 0;

@@ -119,12 +119,12 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
 
 static void free_geometry(bie_ctx* c) {
   void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
-                  c->qshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear};
+                  c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
-  c->qgeo32 = nullptr; c->qshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
+  c->qgeo32 = nullptr; c->qshape32 = nullptr; c->nshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
   c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr;
   c->far_r2 = 0.0;
   c->uniform_bc = -1;

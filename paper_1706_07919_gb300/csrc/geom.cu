@@ -199,13 +199,15 @@ int upload_geometry_tables(bie_ctx* c) {
   for (int a = 0; a < 6; ++a)
     for (int t = 0; t < r.nnear[a]; ++t)
       shape6(r.nxi[a * r.QN + t], r.neta[a * r.QN + t], &ns[(a * r.QN + t) * 6], nullptr, nullptr);
-  std::vector<float> qs32(qs.begin(), qs.end());
+  std::vector<float> qs32(qs.begin(), qs.end()), ns32(ns.begin(), ns.end());
   BIE_CUDA_TRY(cudaMalloc(&c->qshape, qs.size() * sizeof(double)));
   BIE_CUDA_TRY(cudaMalloc(&c->nshape, ns.size() * sizeof(double)));
   BIE_CUDA_TRY(cudaMalloc(&c->qshape32, qs32.size() * sizeof(float)));
+  BIE_CUDA_TRY(cudaMalloc(&c->nshape32, ns32.size() * sizeof(float)));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->qshape, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->nshape, ns.data(), ns.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->qshape32, qs32.data(), qs32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->nshape32, ns32.data(), ns32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   cudaFree(d_tab);
   cudaFree(d_cnt);
