@@ -473,9 +473,10 @@ def roofline_field(w, field_ms, M, Nk):
 
 
 # DRAM bytes (read + write) of one launch of the field kernel in this configuration (64
-# wavenumbers x 16 384 points), from an ncu capture of exactly that launch: 28.30 MB read,
-# 0.18 MB written -- the kernel is ALU-bound and its traffic is the tables and surface values.
-FIELD_LAUNCH_DRAM_BYTES = 28_295_680 + 179_200
+# wavenumbers x 16 384 points), from an ncu capture of a launch of exactly that shape
+# (`bench.py --case field64`): 28.31 MB read, 0.04 MB written -- the kernel is ALU-bound and its
+# traffic is the tables and surface values (the field it writes leaves L2 after the launch).
+FIELD_LAUNCH_DRAM_BYTES = 28_313_600 + 36_352
 
 # algorithmic flops of one field evaluation (one observation point, one quadrature point, one k),
 # counted on the FP64 formula: 2 distances (3 sub, 3 mul, 2 add, sqrt, div = 10 each), the
@@ -545,6 +546,8 @@ def run_case(args):
     of the 16 384 plane points from a constant surface solution; `batch` runs one batch of the
     benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points); `learned`
     runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs);
+    `field64` evaluates the field of the last 64 wavenumbers at all 16 384 points from a constant
+    surface solution (the shape of one field launch of the benchmark, without its solves);
     `step` runs one benchmark step once (cold: the geometry tables are built inside it)."""
     import torch
 
@@ -588,6 +591,12 @@ def run_case(args):
         sol.set_option("mixed.fallback_err_est", 1.0)
         surf, rep = sol.solve_frequencies(w.k[100:104], B.BIE_MODE_MIXED)
         print("case lu: refinement corrections", [r.iters for r in rep])
+    elif args.case == "field64":
+        ks = w.k[448:512]
+        surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
+        xo = torch.tensor(w.xobs, device="cuda")
+        T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
+        print("case field64:", tuple(T.shape))
     else:
         ks = w.k[496:504]
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -624,7 +633,7 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "batch", "learned", "step"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "field64", "batch", "learned", "step"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case:
