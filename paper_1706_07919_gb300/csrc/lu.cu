@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   Cx<S>* M = A + (int64_t)blockIdx.x * bstride;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int rows = n - c0;
+  // global-memory loops are unrolled so that several loads per thread are in flight
+#pragma unroll 4
   for (int t = tid; t < rows * lw; t += nt) {
     const int r = t / lw, c = t - r * lw;
     L[c * rows + r] = M[(int64_t)(c0 + r) * ld + c0 + c];
@@ -200,11 +202,13 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   if (wr > 0 && rows > lw) {
     __syncthreads();  // this CTA's U-block writes above are complete
     Cx<S>* U = L + (size_t)rows * lw;  // [lw][wr]
+#pragma unroll 4
     for (int t = tid; t < lw * wr; t += nt) {
       const int s = t / wr, j = t - s * wr;
       U[t] = M[(int64_t)(c0 + s) * ld + cs + j];
     }
     __syncthreads();
+#pragma unroll 4
     for (int t = tid; t < (rows - lw) * wr; t += nt) {
       const int rr = t / wr, j = t - rr * wr, r = lw + rr;
       Cx<S>& m = M[(int64_t)(c0 + r) * ld + cs + j];
@@ -298,13 +302,21 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
 // grid (ceil((j1 - j0) / 128), batch), block 128, static smem 32 KB: one column j in [j0, j1) per
 // thread.  The 64 entries of the column are loaded once, solved in registers (the loops are fully
 // unrolled, so x[] never leaves the register file) and stored once: no solved entry is re-read
-// from global memory, where each re-read would wait on the L2.  L11 is read from shared memory as
-// pairs of entries (16-byte broadcasts).  Same operations, in the same order, as k_swap_trsm.
+// from global memory, where each re-read would wait on the L2.  The solve runs column by column
+// of L11 (x_s -= l_st x_t for all s > t once x_t is final): the up to 63 updates of a step are
+// independent, so the FMA latency is hidden inside the thread; each x_s still receives its
+// updates in increasing t, the order of the row-by-row substitution of k_swap_trsm.  L11 is
+// staged transposed (column t contiguous) and read by broadcast.
 __global__ void __launch_bounds__(128) k_trsm64(Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
                                                 int j0, int j1) {
-  __shared__ __align__(16) Cx<float> L11[64 * 64];
+  __shared__ __align__(16) Cx<float> LT[64 * 64];  // LT[t * 64 + s] = L11[s][t]
   Cx<float>* M = A + (int64_t)blockIdx.y * bstride;
-  for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) L11[t] = M[(int64_t)(p0 + (t >> 6)) * ld + p0 + (t & 63)];
+  // 32 independent loads per thread in flight (blockDim.x == 128)
+#pragma unroll
+  for (int e = threadIdx.x; e < 64 * 64; e += 128) {
+    const int r = e >> 6, c = e & 63;  // coalesced read of row r
+    LT[c * 64 + r] = M[(int64_t)(p0 + r) * ld + p0 + c];
+  }
   __syncthreads();
   const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= j1 || j >= n) return;
@@ -312,19 +324,14 @@ __global__ void __launch_bounds__(128) k_trsm64(Cx<float>* __restrict__ A, int64
 #pragma unroll
   for (int s = 0; s < 64; ++s) x[s] = M[(int64_t)(p0 + s) * ld + j];
 #pragma unroll
-  for (int s = 1; s < 64; ++s) {
-    Cx<float> v = x[s];
+  for (int t = 0; t < 63; ++t) {
+    const Cx<float> xt = x[t];
 #pragma unroll
-    for (int t = 0; t < s; t += 2) {
-      const float4 l2 = *reinterpret_cast<const float4*>(&L11[s * 64 + t]);  // entries t, t+1
-      v.re -= l2.x * x[t].re - l2.y * x[t].im;
-      v.im -= l2.x * x[t].im + l2.y * x[t].re;
-      if (t + 1 < s) {
-        v.re -= l2.z * x[t + 1].re - l2.w * x[t + 1].im;
-        v.im -= l2.z * x[t + 1].im + l2.w * x[t + 1].re;
-      }
+    for (int s = t + 1; s < 64; ++s) {
+      const Cx<float> l = LT[t * 64 + s];
+      x[s].re -= l.re * xt.re - l.im * xt.im;
+      x[s].im -= l.re * xt.im + l.im * xt.re;
     }
-    x[s] = v;
   }
 #pragma unroll
   for (int s = 1; s < 64; ++s) M[(int64_t)(p0 + s) * ld + j] = x[s];
