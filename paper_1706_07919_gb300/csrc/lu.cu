@@ -107,10 +107,24 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int rows = n - c0;
   // global-memory loops are unrolled so that several loads per thread are in flight
+  // 16-byte accesses need an even element index: even ld, batch stride, c0 and leaf width (the
+  // last also keeps the U block below, at element rows * lw of the shared array, 16-byte aligned)
+  const bool pairs = sizeof(S) == 4 && ((ld | bstride | c0 | lw) & 1) == 0;
+  if (pairs) {  // FP32: 16-byte loads of column pairs
+    const int hl = lw >> 1;
 #pragma unroll 4
-  for (int t = tid; t < rows * lw; t += nt) {
-    const int r = t / lw, c = t - r * lw;
-    L[c * rows + r] = M[(int64_t)(c0 + r) * ld + c0 + c];
+    for (int t = tid; t < rows * hl; t += nt) {
+      const int r = t / hl, c = 2 * (t - r * hl);
+      const float4 v = *reinterpret_cast<const float4*>(&M[(int64_t)(c0 + r) * ld + c0 + c]);
+      L[c * rows + r] = Cx<S>{(S)v.x, (S)v.y};
+      L[(c + 1) * rows + r] = Cx<S>{(S)v.z, (S)v.w};
+    }
+  } else {
+#pragma unroll 4
+    for (int t = tid; t < rows * lw; t += nt) {
+      const int r = t / lw, c = t - r * lw;
+      L[c * rows + r] = M[(int64_t)(c0 + r) * ld + c0 + c];
+    }
   }
   __syncthreads();
   for (int c = 0; c < lw; ++c) {
@@ -208,17 +222,37 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
       U[t] = M[(int64_t)(c0 + s) * ld + cs + j];
     }
     __syncthreads();
+    if (pairs && (wr & 1) == 0) {  // cs = c0 + lw is even too
+      // FP32: a thread takes two adjacent columns (one 16-byte load and store), several in flight
+      const int hw = wr >> 1;
 #pragma unroll 4
-    for (int t = tid; t < (rows - lw) * wr; t += nt) {
-      const int rr = t / wr, j = t - rr * wr, r = lw + rr;
-      Cx<S>& m = M[(int64_t)(c0 + r) * ld + cs + j];
-      Cx<S> a = m;
-      for (int s2 = 0; s2 < lw; ++s2) {
-        const Cx<S> l = L[s2 * rows + r], u = U[s2 * wr + j];
-        a.re -= l.re * u.re - l.im * u.im;
-        a.im -= l.re * u.im + l.im * u.re;
+      for (int t = tid; t < (rows - lw) * hw; t += nt) {
+        const int rr = t / hw, j = 2 * (t - rr * hw), r = lw + rr;
+        float4* mp = reinterpret_cast<float4*>(&M[(int64_t)(c0 + r) * ld + cs + j]);
+        float4 a = *mp;
+        for (int s2 = 0; s2 < lw; ++s2) {
+          const Cx<S> l = L[s2 * rows + r];
+          const float4 u = *reinterpret_cast<const float4*>(&U[s2 * wr + j]);
+          a.x -= l.re * u.x - l.im * u.y;
+          a.y -= l.re * u.y + l.im * u.x;
+          a.z -= l.re * u.z - l.im * u.w;
+          a.w -= l.re * u.w + l.im * u.z;
+        }
+        *mp = a;
       }
-      m = a;
+    } else {
+#pragma unroll 4
+      for (int t = tid; t < (rows - lw) * wr; t += nt) {
+        const int rr = t / wr, j = t - rr * wr, r = lw + rr;
+        Cx<S>& m = M[(int64_t)(c0 + r) * ld + cs + j];
+        Cx<S> a = m;
+        for (int s2 = 0; s2 < lw; ++s2) {
+          const Cx<S> l = L[s2 * rows + r], u = U[s2 * wr + j];
+          a.re -= l.re * u.re - l.im * u.im;
+          a.im -= l.re * u.im + l.im * u.re;
+        }
+        m = a;
+      }
     }
   }
 }
