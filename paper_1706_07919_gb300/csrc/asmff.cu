@@ -70,19 +70,23 @@ __device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
 // separated by block barriers), with an FP64 row accumulator [rows][N] in shared memory, or for
 // large N (GROW) the output rows of A themselves (each row belongs to one CTA; the elements of a
 // colour share no node, so the row's warps never touch the same entry between barriers).
+// With QS = 2 the quadrature points of an element are split over two sets of ASMF_W warps (four
+// warps per row), so that two rows fit one CTA of 256 threads and two CTAs an SM (16 warps); the
+// halves add into the row one after the other (a barrier of the row's warps in between).
 constexpr int ASMF_W = 2;
-template <bool GROW>
-__global__ void __launch_bounds__(256) k_asmff_bulk(
+template <bool GROW, int QS>
+__global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ esort, const int32_t* __restrict__ eperm, int64_t N, int64_t E, int Q,
     const float* __restrict__ qtab /* colour-sorted float-float points, 13 x [Q][E] */,
     const double* __restrict__ qgeo /* FP64 points (weights) */, const double* __restrict__ qshape,
     const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv, const cd* __restrict__ known,
     cd* __restrict__ A, cd* __restrict__ rowsum /* [nk][N][3] */, int rows, FFConst K) {
+  constexpr int WR = ASMF_W * QS;  // warps per row
   extern __shared__ cd accd[];
   __shared__ ff shp[64 * 6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rw = warp / ASMF_W, sub = warp % ASMF_W;
+  const int rw = warp / WR, wr = warp % WR, sub = wr % ASMF_W, h = wr / ASMF_W;
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
   const ff kinv = ff_from_double(1.0 / kv[kk]);
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
   if constexpr (GROW) {
     row = A + ((int64_t)kk * N + (valid ? i : 0)) * N;
     if (valid)
-      for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) row[j] = {0.0, 0.0};
+      for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) row[j] = {0.0, 0.0};
   } else {
     for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accd[t] = {0.0, 0.0};
     row = accd + (int64_t)rw * N;
@@ -106,22 +110,26 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
     nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
   }
   const int64_t EQ = E * Q;
+  const int qlo = h * Q / QS, qhi = (h + 1) * Q / QS;
   ff alr = {0, 0}, ali = {0, 0}, ber = {0, 0}, bei = {0, 0}, bsr = {0, 0}, bsi = {0, 0};
   for (int col = 0; col < ncolors; ++col) {
-    for (int32_t t = color_off[col] + sub * 32 + lane; valid && t < color_off[col + 1]; t += 32 * ASMF_W) {
+    const int32_t cbeg = color_off[col], cend = color_off[col + 1];
+    // the same trip count for all warps of the row (the barriers below are the row's)
+    const int iters = valid ? (cend - cbeg + 32 * ASMF_W - 1) / (32 * ASMF_W) : 0;
+    for (int it = 0; it < iters; ++it) {
+      const int32_t t = cbeg + it * 32 * ASMF_W + sub * 32 + lane;
+      bool act = t < cend;
       int32_t el[6];
-      bool near = false;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        el[a] = esort[a * E + t];
-        near |= (el[a] == i);
+        el[a] = act ? esort[a * E + t] : 0;
+        if (el[a] == i) act = false;  // near pair: the near kernel's
       }
-      if (near) continue;
-      const int64_t e = eperm[t];
+      const int64_t e = act ? eperm[t] : 0;
       ff hr[6], hi[6], gr[6], gi[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) hr[a] = hi[a] = gr[a] = gi[a] = ff{0.f, 0.f};
-      for (int qq = 0; qq < Q; ++qq) {
+      for (int qq = qlo; act && qq < qhi; ++qq) {
         auto tab = [&](int f) { return qtab[((int64_t)f * Q + qq) * E + t]; };
         const ff qx = {tab(0), tab(3)}, qy = {tab(1), tab(4)}, qz = {tab(2), tab(5)};
         const ff nx = {tab(6), tab(10)}, ny = {tab(7), tab(11)}, nz = {tab(8), tab(12)};
@@ -158,26 +166,32 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
         }
       }
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        const int32_t j = el[a];
-        const cd kvj = kn[j];
-        const cd H = {ff_to_double(hr[a]), ff_to_double(hi[a])}, G = {ff_to_double(gr[a]), ff_to_double(gi[a])};
-        if (bc[j] == 0) {  // hard column: A += H, b += Gm P'_known
-          row[j].re += H.re;
-          row[j].im += H.im;
-          const cd t2 = cmul(G, kvj);
-          bsr = ffx_add_f(ffx_add_f(bsr, (float)t2.re), (float)(t2.re - (double)(float)t2.re));
-          bsi = ffx_add_f(ffx_add_f(bsi, (float)t2.im), (float)(t2.im - (double)(float)t2.im));
-        } else {           // soft column: A -= Gm, b -= H P_known
-          row[j].re -= G.re;
-          row[j].im -= G.im;
-          const cd t2 = cmul(H, kvj);
-          bsr = ffx_add_f(ffx_add_f(bsr, -(float)t2.re), -(float)(t2.re - (double)(float)t2.re));
-          bsi = ffx_add_f(ffx_add_f(bsi, -(float)t2.im), -(float)(t2.im - (double)(float)t2.im));
+      for (int hh = 0; hh < QS; ++hh) {  // the quadrature halves add into the row in turn
+        if (act && h == hh) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            const int32_t j = el[a];
+            const cd kvj = kn[j];
+            const cd H = {ff_to_double(hr[a]), ff_to_double(hi[a])}, G = {ff_to_double(gr[a]), ff_to_double(gi[a])};
+            if (bc[j] == 0) {  // hard column: A += H, b += Gm P'_known
+              row[j].re += H.re;
+              row[j].im += H.im;
+              const cd t2 = cmul(G, kvj);
+              bsr = ffx_add_f(ffx_add_f(bsr, (float)t2.re), (float)(t2.re - (double)(float)t2.re));
+              bsi = ffx_add_f(ffx_add_f(bsi, (float)t2.im), (float)(t2.im - (double)(float)t2.im));
+            } else {           // soft column: A -= Gm, b -= H P_known
+              row[j].re -= G.re;
+              row[j].im -= G.im;
+              const cd t2 = cmul(H, kvj);
+              bsr = ffx_add_f(ffx_add_f(bsr, -(float)t2.re), -(float)(t2.re - (double)(float)t2.re));
+              bsi = ffx_add_f(ffx_add_f(bsi, -(float)t2.im), -(float)(t2.im - (double)(float)t2.im));
+            }
+          }
         }
+        if (QS > 1) bar_named(1 + rw, 32 * WR);
       }
     }
-    bar_named(1 + rw, 32 * ASMF_W);  // the row's warps finish the colour (rows <= 8: ids 1..8)
+    if (QS == 1) bar_named(1 + rw, 32 * WR);  // the row's warps finish the colour (rows <= 8: ids 1..8)
   }
   // combine the lanes' and the row's warps' sums in FP64
   double v[6] = {ff_to_double(alr), ff_to_double(ali), ff_to_double(ber), ff_to_double(bei), ff_to_double(bsr),
@@ -185,18 +199,18 @@ __global__ void __launch_bounds__(256) k_asmff_bulk(
 #pragma unroll
   for (int u = 0; u < 6; ++u)
     for (int o = 16; o > 0; o >>= 1) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
-  __shared__ double part[8][ASMF_W][6];
+  __shared__ double part[8][WR][6];
   if (lane == 0)
-    for (int u = 0; u < 6; ++u) part[rw][sub][u] = v[u];
+    for (int u = 0; u < 6; ++u) part[rw][wr][u] = v[u];
   __syncthreads();
   if (valid) {
     if constexpr (!GROW) {
       cd* Arow = A + ((int64_t)kk * N + i) * N;
-      for (int64_t j = sub * 32 + lane; j < N; j += 32 * ASMF_W) Arow[j] = row[j];
+      for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) Arow[j] = row[j];
     }
-    if (sub == 0 && lane == 0) {
+    if (wr == 0 && lane == 0) {
       double w[6] = {0, 0, 0, 0, 0, 0};
-      for (int s2 = 0; s2 < ASMF_W; ++s2)
+      for (int s2 = 0; s2 < WR; ++s2)
         for (int u = 0; u < 6; ++u) w[u] += part[rw][s2][u];
       cd* rs = rowsum + ((int64_t)kk * N + i) * 3;
       rs[0] = {w[0], w[1]};
@@ -250,21 +264,29 @@ const int32_t* sorted_elems_ptr(bie_ctx* c);
 int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* known, cd* rowsum) {
   const int64_t N = c->N;
   BIE_TRY(ensure_mixed_tables(c));
-  int rows = 4;  // 4 rows x 2 warps = 256 threads (launch bound); shrink to fit shared memory
-  while (rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
-  const bool grow = (size_t)rows * N * sizeof(cd) > 200 * 1024;  // rows accumulate in A itself
+  // 2 rows x 4 warps (quadrature halves) when two such CTAs fit an SM, else 4 rows x 2 warps
+  // shrunk to fit shared memory, else (large N) the rows accumulate in A itself
+  const bool split = (size_t)2 * N * sizeof(cd) <= 100 * 1024;
+  int rows = split ? 2 : 4;
+  while (!split && rows > 1 && (size_t)rows * N * sizeof(cd) > 200 * 1024) rows /= 2;
+  const bool grow = (size_t)rows * N * sizeof(cd) > 200 * 1024;
   if (grow) rows = 4;
   const size_t smem = grow ? 0 : (size_t)rows * N * sizeof(cd);
   if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
   static const FFConst K = make_ffconst();
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   if (grow) {
-    BIE_LAUNCH(k_asmff_bulk<true><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
+    BIE_LAUNCH(k_asmff_bulk<true, 1><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+  } else if (split) {
+    BIE_TRY((set_smem_max(k_asmff_bulk<false, 2>)));
+    BIE_LAUNCH(k_asmff_bulk<false, 2><<<gb, 32 * rows * ASMF_W * 2, smem, c->stream>>>(
         c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
         c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   } else {
-    BIE_TRY((set_smem_max(k_asmff_bulk<false>)));
-    BIE_LAUNCH(k_asmff_bulk<false><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
+    BIE_TRY((set_smem_max(k_asmff_bulk<false, 1>)));
+    BIE_LAUNCH(k_asmff_bulk<false, 1><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
         c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
         c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   }
