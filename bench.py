@@ -161,6 +161,7 @@ def run_ours(args):
     sol.set_incident_plane_wave(w.direction)
     sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.asm_kb", args.asm_kb)
+    sol.set_option("field.variant", args.field_variant)
     sol.set_option("mixed.batch", args.batch)
     midx = np.arange(1, Nk + 1, dtype=np.int64)
 
@@ -230,7 +231,7 @@ def run_ours(args):
     solve_rate = Nk * args.steps / (phase[0] / 1e3)
 
     # ---- roofline of the dominant kernel: the field phase of the timed steps ----
-    roof = roofline_field(w, phase[1] / args.steps, M, Nk)
+    roof = roofline_field(w, phase[1] / args.steps, M, Nk, args.field_variant)
 
     value = job_throughput(Nk, world, args.steps, t_ms)
     pts = job_throughput(M * Nt * P, world, args.steps, t_ms)
@@ -453,7 +454,7 @@ def run_e2e(args, w, sol, B, dev, stream):
             "d2h_bytes_per_step": int(hsurf.numel() * 16 + hout.numel() * 4)}
 
 
-def roofline_field(w, field_ms, M, Nk):
+def roofline_field(w, field_ms, M, Nk, variant):
     """The dominant kernel of the step is the field evaluation (Eq. BRIEFdmn), FP32-ALU-bound:
     algorithmic flops per (point, quadrature point, k) x evaluations / the field phase's device time
     in the timed steps (CUDA events on the library's stream; the phase also holds the foot-point
@@ -463,20 +464,23 @@ def roofline_field(w, field_ms, M, Nk):
     flops_per_eval = FIELD_FLOPS_PER_EVAL
     achieved = flops_per_eval * evals / (field_ms * 1e-3) / 1e12
     peak = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 FFMA, 152 SMs x 128 lanes x 2 flops at 2.07 GHz
-    launches = (Nk + 63) // 64
-    return {"kernel": "k_field32c<16,64,4> (Eq. BRIEFdmn, float-float phases)", "bound": "alu",
+    launches = (Nk + FIELD_BATCH - 1) // FIELD_BATCH
+    name = {1: "k_field32c<16,64,4,64>", 2: "k_field32c<16,128,3,32>"}.get(variant, "k_field32b")
+    return {"kernel": name + " (Eq. BRIEFdmn, float-float phases)", "bound": "alu",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": FIELD_LAUNCH_DRAM_BYTES, "traffic_unit": "bytes per launch",
+            "traffic": FIELD_LAUNCH_DRAM_BYTES.get(variant), "traffic_unit": "bytes per launch",
             "evals_per_s": evals / (field_ms * 1e-3), "flops_per_eval": flops_per_eval,
             "launches_per_step": launches, "ms_per_launch": field_ms / launches,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)"}
 
 
-# DRAM bytes (read + write) of one launch of the field kernel in this configuration (64
-# wavenumbers x 16 384 points), from an ncu capture of a launch of exactly that shape
-# (`bench.py --case field64`): 28.31 MB read, 0.04 MB written -- the kernel is ALU-bound and its
-# traffic is the tables and surface values (the field it writes leaves L2 after the launch).
-FIELD_LAUNCH_DRAM_BYTES = 28_313_600 + 36_352
+# wavenumbers per field launch of the library (bie_eval_field)
+FIELD_BATCH = 512
+
+# DRAM bytes (read + write) of one launch of the field kernel in this configuration (512
+# wavenumbers x 16 384 points) per kernel variant, from an ncu capture of a launch of exactly
+# that shape (`bench.py --case field512`); None: not captured for the current kernel.
+FIELD_LAUNCH_DRAM_BYTES = {}
 
 # algorithmic flops of one field evaluation (one observation point, one quadrature point, one k),
 # counted on the FP64 formula: 2 distances (3 sub, 3 mul, 2 add, sqrt, div = 10 each), the
@@ -546,8 +550,8 @@ def run_case(args):
     of the 16 384 plane points from a constant surface solution; `batch` runs one batch of the
     benchmark (128 wavenumbers, k = 8.03 .. 12.0: solves and the field at all points); `learned`
     runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs);
-    `field64` evaluates the field of the last 64 wavenumbers at all 16 384 points from a constant
-    surface solution (the shape of one field launch of the benchmark, without its solves);
+    `field512` evaluates the field of all 512 wavenumbers at all 16 384 points from a constant
+    surface solution (the shape of the benchmark's field launch, without its solves);
     `step` runs one benchmark step once (cold: the geometry tables are built inside it)."""
     import torch
 
@@ -562,6 +566,7 @@ def run_case(args):
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
     sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.asm_kb", args.asm_kb)
+    sol.set_option("field.variant", args.field_variant)
     if args.case == "step":
         sol.set_incident_plane_wave(w.direction)
         sol.set_option("mixed.batch", args.batch)
@@ -591,12 +596,12 @@ def run_case(args):
         sol.set_option("mixed.fallback_err_est", 1.0)
         surf, rep = sol.solve_frequencies(w.k[100:104], B.BIE_MODE_MIXED)
         print("case lu: refinement corrections", [r.iters for r in rep])
-    elif args.case == "field64":
-        ks = w.k[448:512]
+    elif args.case == "field512":
+        ks = w.k
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
         xo = torch.tensor(w.xobs, device="cuda")
         T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
-        print("case field64:", tuple(T.shape))
+        print("case field512:", tuple(T.shape))
     else:
         ks = w.k[496:504]
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -614,6 +619,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--field-variant", type=int, default=2,
+                    help="mixed field kernel: 2 (128 points per CTA, 32-point tiles), 1 (64 points), 0 (k_field32b)")
     ap.add_argument("--asm-kb", type=int, default=2,
                     help="FP32 bulk assembly: wavenumbers per thread (2, 1) or 0 for the general kernel")
     ap.add_argument("--tc", type=int, default=3,
@@ -633,7 +640,7 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "field64", "batch", "learned", "step"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case:

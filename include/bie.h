@@ -176,8 +176,10 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
- *   "field.variant"        mixed field kernel: 1 (default) groups of 16 wavenumbers, 64 points per
- *                          CTA, FP32 run sums; 0 groups of 8, 128 points, compensated sums per term
+ *   "field.variant"        mixed field kernel: 2 (default) groups of 16 wavenumbers, 128 points per
+ *                          CTA, tiles of 32 quadrature points, FP32 run sums; 1 the same with 64
+ *                          points per CTA and 64-point tiles; 0 groups of 8, 128 points,
+ *                          compensated sums per term
  *   "mixed.reassembly"     system of the flagged wavenumbers: 1 (default) bulk pairs in float-float
  *                          (~48-bit, FP32 pipes), 0 in FP64; near pairs and diagonal are FP64
  *   "assemble.bulk_ff"     bie_assemble's bulk pairs in float-float (1) or FP64 (0, default)

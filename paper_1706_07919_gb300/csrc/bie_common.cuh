@@ -127,8 +127,9 @@ struct bie_ctx {
   double refine_tol = 1e-11;         // backward-error target of the refinement
   double fallback_err_est = 2.5e-7;  // FP64 re-solve above this estimated assembly-induced error
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
-  int field_variant = 1;             // mixed field kernel: 1 k_field32c (16 wavenumbers per group,
-                                     // 64 points per CTA), 0 k_field32b (8 per group, 128 points)
+  int field_variant = 2;             // mixed field kernel: 2 k_field32c (16 wavenumbers per group,
+                                     // 128 points per CTA, 32-point tiles), 1 the same with 64
+                                     // points and 64-point tiles, 0 k_field32b (8 per group)
   int assemble_ff = 0;               // bie_assemble: bulk pairs in float-float (1) or FP64 (0)
   int uniform_bc = -1;               // every element has one condition on all nodes (1), not (0), unknown
   int asm_kb = 2;                    // FP32 bulk assembly: wavenumbers per thread (1, 2), 0 = the

@@ -277,7 +277,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   } else if (n == "field.accurate_phase") {
     c->field_accurate_phase = value != 0.0 ? 1 : 0;
   } else if (n == "field.variant") {
-    if (value != 0.0 && value != 1.0) return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0 or 1");
+    if (value != 0.0 && value != 1.0 && value != 2.0)
+      return fail(BIE_ERR_INVALID_ARG, "field.variant must be 0, 1 or 2");
     c->field_variant = (int)value;
   } else if (n == "mixed.asm_kb") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return fail(BIE_ERR_INVALID_ARG, "mixed.asm_kb must be 0, 1 or 2");
@@ -483,14 +484,16 @@ int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, i
   // foot points (k independent) then batches of k
   const size_t foot_bytes = (size_t)M * (8 * sizeof(double) + sizeof(int32_t)) + 256;
   const size_t perk = 2 * (size_t)EQ * sizeof(cd) + 16;
-  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, 64));
-  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + 4096));
+  // up to 512 wavenumbers per launch: the field kernel's grid (points x groups of 16 wavenumbers)
+  // then spans many waves of resident CTAs, so the last, partial wave costs little
+  constexpr int64_t kMaxFieldBatch = 512;
+  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, kMaxFieldBatch));
+  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + kMaxFieldBatch * sizeof(double) + 4096));
   double* foot = (double*)c->work3.p;
   int32_t* foot_elem = (int32_t*)(foot + 8 * M);
   char* after = (char*)(((uintptr_t)(foot_elem + M) + 255) & ~(uintptr_t)255);
   double* kdev = (double*)after;
-  void* scratch = (void*)(after + 256 * sizeof(double));
-  if (kb > 256) kb = 256;
+  void* scratch = (void*)(after + kMaxFieldBatch * sizeof(double));
   BIE_TRY(launch_foot_points(c, xobs, M, foot_elem, foot));
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);

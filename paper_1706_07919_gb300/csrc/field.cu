@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
 // points and each run is added to a compensated sum kept in shared memory, so only 2 KB partial
 // sums stay in registers; the phase step e^{i dk R} takes its phase from an FMA-split product
 // (no 2 pi reduction in float-float: dk R is small).
-template <int KB, int TP, int MINB>
+template <int KB, int TP, int MINB, int UT>
 __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
                                                        const float* __restrict__ qtab, const cf* __restrict__ Pq,
                                                        const cf* __restrict__ Pnq, const cd* __restrict__ surf,
@@ -453,8 +453,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
                                                        const int32_t* __restrict__ foot_elem,
                                                        const double* __restrict__ foot, const double* __restrict__ kv,
                                                        int nk, cd* __restrict__ T, TwoPi3f tp, int uniform, ff dk) {
-  __shared__ float4 sg[TP][4];  // the quadrature point's 13 table values (P32 order), padded to 16
-  __shared__ float4 sq[KB][TP];  // surface values at the quadrature points: P re, im, dP re, im
+  __shared__ float4 sg[UT][4];  // a tile of UT quadrature points: 13 table values (P32 order), padded
+  __shared__ float4 sq[KB][UT];  // surface values at the tile's points: P re, im, dP re, im
   __shared__ float4 s0[KB][TP];  // surface values at the foot points, same order
   __shared__ float sacc[KB][4][TP];  // compensated sums: re (s, c), im (s, c)
   __shared__ float2 sk[KB];  // k (FP32 head), 1 / k
@@ -499,20 +499,22 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   float pr[KB], pim[KB];
 #pragma unroll
   for (int j = 0; j < KB; ++j) pr[j] = pim[j] = 0.f;
-  for (int64_t t0 = 0; t0 < EQ; t0 += TP) {
-    const int64_t t = t0 + tid;
+  for (int64_t t0 = 0; t0 < EQ; t0 += UT) {
+    const int cnt = (EQ - t0) < UT ? (int)(EQ - t0) : UT;
     __syncthreads();
-    if (t < EQ) {
-      float* g = reinterpret_cast<float*>(sg[tid]);
-#pragma unroll
-      for (int u = 0; u < 13; ++u) g[u] = qtab[u * EQ + t];
-      for (int j = 0; j < nkb; ++j) {
+    for (int e = tid; e < 13 * UT; e += TP) {  // consecutive threads, consecutive points
+      const int f = e / UT, u = e - f * UT;
+      if (u < cnt) reinterpret_cast<float*>(sg[u])[f] = qtab[f * EQ + t0 + u];
+    }
+    for (int e = tid; e < KB * UT; e += TP) {
+      const int j = e / UT, u = e - j * UT;
+      if (j < nkb && u < cnt) {
+        const int64_t t = t0 + u;
         const cf a = Pq[(int64_t)(kbase + j) * EQ + t], b = Pnq[(int64_t)(kbase + j) * EQ + t];
-        sq[j][tid] = make_float4(a.re, a.im, b.re, b.im);
+        sq[j][u] = make_float4(a.re, a.im, b.re, b.im);
       }
     }
     __syncthreads();
-    const int cnt = (EQ - t0) < TP ? (int)(EQ - t0) : TP;
     if (!active) continue;
     for (int u = 0; u < cnt; ++u) {
       const float4 g0 = sg[u][0], g1 = sg[u][1], g2 = sg[u][2], g3 = sg[u][3];
@@ -618,12 +620,12 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   }
 }
 
-template <int KB, int TP, int MINB>
+template <int KB, int TP, int MINB, int UT>
 static void launch_field32c(bie_ctx* c, int64_t EQ, const cf* Pq, const cf* Pnq, const cd* surf, const double* xp,
                             int64_t M, const int32_t* foot_elem, const double* foot, const double* kv, int nk, cd* T,
                             TwoPi3f tp, int uniform, ff dk) {
   dim3 gb((unsigned)((M + TP - 1) / TP), (unsigned)((nk + KB - 1) / KB));
-  BIE_LAUNCH(k_field32c<KB, TP, MINB><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M,
+  BIE_LAUNCH(k_field32c<KB, TP, MINB, UT><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M,
                                                               foot_elem, foot, kv, nk, T, tp, uniform, dk));
 }
 
@@ -648,7 +650,7 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
     if (c->field_accurate_phase) {
       const int v = c->field_variant;
-      const int KBv = (v == 1) ? 16 : FKB;
+      const int KBv = (v >= 1) ? 16 : FKB;
       // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -661,7 +663,9 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
       }
       const ff dkf = ff_from_double(dkv);
       if (v == 1) {
-        launch_field32c<16, 64, 4>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+        launch_field32c<16, 64, 4, 64>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
+      } else if (v == 2) {
+        launch_field32c<16, 128, 3, 32>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
       } else {
         dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
         BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
