@@ -71,7 +71,7 @@ struct TwoPi3 {
 // reduced in float-float (the product n c1 cancels exactly against a.hi: both are multiples of
 // ulp(c1) and the difference is below pi), then cos/sin of u_hi + u_lo by cis_reduced.
 __device__ __forceinline__ void ff_cis(ff a, const TwoPi3& tp, float& c, float& s) {
-  const float n = rintf(a.hi * tp.inv);
+  const float n = round_small(__fmul_rn(a.hi, tp.inv));
   const float h = __fmaf_rn(-n, tp.c1, a.hi);  // exact: both terms are multiples of ulp(c1)
   float t = __fmaf_rn(-n, tp.c2, a.lo);
   t = __fmaf_rn(-n, tp.c3, t);

@@ -41,7 +41,8 @@ struct FFConst {
 };
 
 __device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
-  const float n = rintf(phi.hi * K.two_over_pi);
+  const float nm = __fadd_rn(__fmul_rn(phi.hi, K.two_over_pi), kRoundMagic);  // |phi 2/pi| < 2^22
+  const float n = __fsub_rn(nm, kRoundMagic);
   const float h = __fmaf_rn(-n, K.p1, phi.hi);  // exact (n p1 exact, result within the ulp grid)
   ff u = ff_two_sum(h, -n * K.p2);              // n p2 exact
   u = ffx_add_f(u, __fmaf_rn(-n, K.p3, phi.lo));
@@ -60,7 +61,7 @@ __device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
   C = ff_add(K.c4, ff_mul(z, C));
   C = ff_add(K.c2, ff_mul(z, C));
   const ff cv = ffx_add_f(ff_mul(z, C), 1.0f);
-  const int q = ((int)n) & 3;
+  const int q = __float_as_int(nm) & 3;
   const ff a = (q & 1) ? sv : cv, b = (q & 1) ? cv : sv;
   c = (q == 1 || q == 2) ? ff_neg(a) : a;
   s = (q >= 2) ? ff_neg(b) : b;

@@ -256,11 +256,20 @@ __host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a
 // of sin (through v^9) and cos (through v^10) on |v'| <= pi/4, whose truncation errors are below
 // 2e-9 and 2e-10; the quadrant selects and negates.  Written from the series, not from a
 // library's polynomial.
+// Nearest integer (ties to even) of an FP32 value of magnitude below 2^22, as two additions of
+// 1.5 * 2^23 on the FMA pipe instead of an instruction of the conversion unit; the sum's low
+// significand bits hold that integer modulo 2^22 (two's complement for negative values).
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float round_small(float x) {
+  return __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic);
+}
+
 __device__ __forceinline__ void cis_reduced(float vh, float vl, float& c, float& s) {
   const float kTwoOverPi = 0.636619772367581343f;
   const float kPio2Hi = 1.57079637050628662f;        // fl32(pi/2)
   const float kPio2Lo = -4.37113900018624284e-8f;    // pi/2 - fl32(pi/2)
-  const float q = rintf(vh * kTwoOverPi);
+  const float qm = __fadd_rn(__fmul_rn(vh, kTwoOverPi), kRoundMagic);  // |v 2/pi| < 2^22
+  const float q = __fsub_rn(qm, kRoundMagic);
   float v = __fmaf_rn(-q, kPio2Hi, vh);
   v = __fmaf_rn(-q, kPio2Lo, v) + vl;
   const float v2 = v * v;
@@ -273,7 +282,7 @@ __device__ __forceinline__ void cis_reduced(float vh, float vl, float& c, float&
   pc = __fmaf_rn(v2, pc, 4.16666666666666667e-2f);                              // 1/4!
   pc = __fmaf_rn(v2, pc, -0.5f);
   const float cv = __fmaf_rn(v2, pc, 1.0f);
-  const int qi = ((int)q) & 3;
+  const int qi = __float_as_int(qm) & 3;
   const float a = (qi & 1) ? sv : cv, b = (qi & 1) ? cv : sv;
   c = (qi == 1 || qi == 2) ? -a : a;
   s = (qi >= 2) ? -b : b;

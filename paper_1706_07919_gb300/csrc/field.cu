@@ -146,7 +146,7 @@ struct TwoPi3f {
 };
 
 __device__ __forceinline__ void cis_ff(ff a, const TwoPi3f& tp, float& c, float& s) {
-  const float n = rintf(a.hi * tp.inv);
+  const float n = round_small(__fmul_rn(a.hi, tp.inv));
   const float h = __fmaf_rn(-n, tp.c1, a.hi);
   float t = __fmaf_rn(-n, tp.c2, a.lo);
   t = __fmaf_rn(-n, tp.c3, t);
@@ -158,7 +158,7 @@ __device__ __forceinline__ void cis_ff(ff a, const TwoPi3f& tp, float& c, float&
 }
 
 __device__ __forceinline__ void cis_fast(float t, const TwoPi3f& tp, float& c, float& s) {
-  const float n = rintf(t * tp.inv);
+  const float n = round_small(__fmul_rn(t, tp.inv));
   float u = __fmaf_rn(-n, tp.c1, t);
   u = __fmaf_rn(-n, tp.c2, u);
   __sincosf(u, &s, &c);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
 constexpr int FKB = 8;
 
 __device__ __forceinline__ void cis_ffk(ff a, const TwoPi3f& tp, float& c, float& s) {
-  const float n = rintf(a.hi * tp.inv);
+  const float n = round_small(__fmul_rn(a.hi, tp.inv));
   const float h = __fmaf_rn(-n, tp.c1, a.hi);
   float t = __fmaf_rn(-n, tp.c2, a.lo);
   t = __fmaf_rn(-n, tp.c3, t);
