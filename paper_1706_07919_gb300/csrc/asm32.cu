@@ -42,7 +42,7 @@ __global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __
 // Element connectivity in the same order: esort[a * E + t].
 __global__ void k_points_to32_sorted(const double* __restrict__ g, const int32_t* __restrict__ perm,
                                      const int32_t* __restrict__ elems, int64_t E, int Q, float* __restrict__ o,
-                                     int32_t* __restrict__ esort) {
+                                     int32_t* __restrict__ esort, float4* __restrict__ aos) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= E * Q) return;
   const int64_t t = idx % E;
@@ -56,8 +56,15 @@ __global__ void k_points_to32_sorted(const double* __restrict__ g, const int32_t
     v[P32XH + d] = x.hi; v[P32XL + d] = x.lo;
     v[P32NX + d] = nv.hi; v[P32NXL + d] = nv.lo;
   }
-  v[P32W] = (float)g[GWJ * n + src];
+  const ff w = ff_from_double(g[GWJ * n + src]);
+  v[P32W] = w.hi;
   for (int f = 0; f < P32COUNT; ++f) o[((int64_t)f * Q + q) * E + t] = v[f];
+  // the same 13 values as one 64-byte record, then the weight's low part (float-float kernels)
+  float4* a = aos + ((int64_t)q * E + t) * 4;
+  a[0] = make_float4(v[0], v[1], v[2], v[3]);
+  a[1] = make_float4(v[4], v[5], v[6], v[7]);
+  a[2] = make_float4(v[8], v[9], v[10], v[11]);
+  a[3] = make_float4(v[12], w.lo, 0.f, 0.f);
   if (q == 0)
     for (int a = 0; a < 6; ++a) esort[a * E + t] = elems[6 * e + a];
 }
@@ -274,7 +281,7 @@ __global__ void k_known_q32(const int32_t* __restrict__ esort, int64_t E, int Q,
 template <int KB, int QS>
 __global__ void __launch_bounds__(256) k_asm32_bulk_u(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
-    const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float* __restrict__ qtab,
+    const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float4* __restrict__ qaos,
     const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
     const double* __restrict__ kv, int nk, const cf* __restrict__ kq, cf* __restrict__ A, int64_t lda,
     double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp, float far_r2) {
@@ -330,9 +337,10 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
 #pragma unroll
         for (int j = 0; j < KB; ++j) sr[j] = si[j] = ear[j] = eai[j] = ebr[j] = ebi[j] = 0.f;
         for (int qq = qlo; qq < qhi; ++qq) {
-          float q[P32COUNT];
-#pragma unroll
-          for (int f = 0; f < P32COUNT; ++f) q[f] = qtab[((int64_t)f * Q + qq) * E + t];
+          // the point's 64-byte record (colour-sorted, point-major): four 16-byte loads
+          const float4* qp = qaos + ((int64_t)qq * E + t) * 4;
+          const float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
+          const float q[P32COUNT] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x};
           // geometry, shared by the KB wavenumbers
           const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
           const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
@@ -586,6 +594,13 @@ static float* sorted_table(bie_ctx* c) {
 static int32_t* sorted_elems(bie_ctx* c) {
   return reinterpret_cast<int32_t*>(sorted_table(c) + P32COUNT * c->E * c->rule.Q);
 }
+// the colour-sorted points again as 64-byte records [Q][E][16 floats], 16-byte aligned
+static size_t sorted_aos_offset(bie_ctx* c) {
+  const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
+  return ((size_t)(P32COUNT * (2 * nq + nn) + 6 * c->E) + 63) / 64 * 64;
+}
+static float4* sorted_aos(bie_ctx* c) { return reinterpret_cast<float4*>(c->qgeo32 + sorted_aos_offset(c)); }
+const float4* sorted_aos_ptr(bie_ctx* c) { return sorted_aos(c); }
 
 const float* sorted_table_ptr(bie_ctx* c) { return sorted_table(c); }
 const int32_t* sorted_elems_ptr(bie_ctx* c) { return sorted_elems(c); }
@@ -593,11 +608,11 @@ const int32_t* sorted_elems_ptr(bie_ctx* c) { return sorted_elems(c); }
 int ensure_mixed_tables(bie_ctx* c) {
   if (c->qgeo32) return BIE_OK;
   const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
-  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (P32COUNT * (2 * nq + nn) + 6 * c->E) * sizeof(float)));
+  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (sorted_aos_offset(c) + 16 * (size_t)nq) * sizeof(float)));
   BIE_LAUNCH(k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32));
   BIE_LAUNCH(k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq));
   BIE_LAUNCH(k_points_to32_sorted<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(
-      c->qgeo, c->elem_perm, c->elems, c->E, c->rule.Q, sorted_table(c), sorted_elems(c)));
+      c->qgeo, c->elem_perm, c->elems, c->E, c->rule.Q, sorted_table(c), sorted_elems(c), sorted_aos(c)));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -655,12 +670,12 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
     if (kb == 2) {
       BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2>)));
       BIE_LAUNCH(k_asm32_bulk_u<2, 2><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
-          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_table(c), c->qshape32, c->color_off,
+          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
           c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
     } else {
       BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1>)));
       BIE_LAUNCH(k_asm32_bulk_u<1, 1><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
-          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_table(c), c->qshape32, c->color_off,
+          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
           c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
     }
   }

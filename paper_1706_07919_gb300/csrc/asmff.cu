@@ -79,7 +79,7 @@ template <bool GROW, int QS>
 __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ esort, const int32_t* __restrict__ eperm, int64_t N, int64_t E, int Q,
-    const float* __restrict__ qtab /* colour-sorted float-float points, 13 x [Q][E] */,
+    const float4* __restrict__ qaos /* colour-sorted float-float points, 64-byte records [Q][E] */,
     const double* __restrict__ qgeo /* FP64 points (weights) */, const double* __restrict__ qshape,
     const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv, const cd* __restrict__ known,
     cd* __restrict__ A, cd* __restrict__ rowsum /* [nk][N][3] */, int rows, FFConst K) {
@@ -110,7 +110,6 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     xi[d] = ff_from_double(valid ? nodes[3 * i + d] : 0.0);
     nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
   }
-  const int64_t EQ = E * Q;
   const int qlo = h * Q / QS, qhi = (h + 1) * Q / QS;
   ff alr = {0, 0}, ali = {0, 0}, ber = {0, 0}, bei = {0, 0}, bsr = {0, 0}, bsi = {0, 0};
   for (int col = 0; col < ncolors; ++col) {
@@ -126,15 +125,15 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
         el[a] = act ? esort[a * E + t] : 0;
         if (el[a] == i) act = false;  // near pair: the near kernel's
       }
-      const int64_t e = act ? eperm[t] : 0;
       ff hr[6], hi[6], gr[6], gi[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) hr[a] = hi[a] = gr[a] = gi[a] = ff{0.f, 0.f};
       for (int qq = qlo; act && qq < qhi; ++qq) {
-        auto tab = [&](int f) { return qtab[((int64_t)f * Q + qq) * E + t]; };
-        const ff qx = {tab(0), tab(3)}, qy = {tab(1), tab(4)}, qz = {tab(2), tab(5)};
-        const ff nx = {tab(6), tab(10)}, ny = {tab(7), tab(11)}, nz = {tab(8), tab(12)};
-        const ff wj = ff_from_double(qgeo[GWJ * EQ + e * Q + qq]);
+        const float4* qp = qaos + ((int64_t)qq * E + t) * 4;  // x hi, x lo, nu hi, w, nu lo, w lo
+        const float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
+        const ff qx = {v0.x, v0.w}, qy = {v0.y, v1.x}, qz = {v0.z, v1.y};
+        const ff nx = {v1.z, v2.z}, ny = {v1.w, v2.w}, nz = {v2.x, v3.x};
+        const ff wj = {v2.y, v3.y};
         const ff rx = ff_sub(qx, xi[0]), ry = ff_sub(qy, xi[1]), rz = ff_sub(qz, xi[2]);
         const ff R = ff_sqrt(ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz)));
         const ff invR = ffx_recip(R);
@@ -258,7 +257,7 @@ static FFConst make_ffconst() {
 }
 
 int ensure_mixed_tables(bie_ctx* c);
-const float* sorted_table_ptr(bie_ctx* c);
+const float4* sorted_aos_ptr(bie_ctx* c);
 const int32_t* sorted_elems_ptr(bie_ctx* c);
 
 // Bulk part of the FP64 system in float-float (the replacement of k_asm64_bulk in assemble64).
@@ -278,17 +277,17 @@ int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* know
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   if (grow) {
     BIE_LAUNCH(k_asmff_bulk<true, 1><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
         c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   } else if (split) {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 2>)));
     BIE_LAUNCH(k_asmff_bulk<false, 2><<<gb, 32 * rows * ASMF_W * 2, smem, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
         c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   } else {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 1>)));
     BIE_LAUNCH(k_asmff_bulk<false, 1><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_table_ptr(c),
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
         c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   }
   BIE_CUDA_TRY(cudaGetLastError());
