@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(512) k_panel(Cx<S>* __restrict__ A, int64_t bs
 // c * rows + r), so that threads walking the rows touch consecutive words.
 template <class S>
 __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w,
-                                               int c0, int lw, int32_t* __restrict__ piv, int32_t* __restrict__ info) {
+                                               int c0, int lw, int32_t* __restrict__ piv, int32_t* __restrict__ info,
+                                               int fuse) {
   extern __shared__ unsigned char smem_raw[];
   Cx<S>* L = reinterpret_cast<Cx<S>*>(smem_raw);  // [lw][rows]
   __shared__ S red_v[32];
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   // shared memory and its just-solved U block read once into shared memory after it; consecutive
   // threads take consecutive columns of a row (coalesced read-modify-write)
   const int cs = c0 + lw, wr = pend - cs;
-  if (wr > 0 && rows > lw) {
+  if (fuse && wr > 0 && rows > lw) {
     __syncthreads();  // this CTA's U-block writes above are complete
     Cx<S>* U = L + (size_t)rows * lw;  // [lw][wr]
 #pragma unroll 4
@@ -257,6 +258,50 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
   }
 }
 
+// Rows below the leaf, panel columns right of it: A -= L_leaf U_leaf (K = lw <= 16), as its own
+// launch for small batches (the leaf kernel has one CTA per matrix).  One warp per row, lanes over the (<= 64) columns so that the read-modify-write of A coalesces;
+// the row's lw entries of L are broadcast.  grid (ceil(rows / 64), batch), block 256 (8 warps, 8
+// rows each).
+template <class S>
+__global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                                     int w, int c0, int lw) {
+  __shared__ Cx<S> U[16 * 64];
+  Cx<S>* M = A + (int64_t)blockIdx.y * bstride;
+  const int cs = c0 + lw, ce = min(p0 + w, n), wr = ce - cs;
+  if (wr <= 0) return;
+  for (int t = threadIdx.x; t < lw * wr; t += blockDim.x) {
+    const int s = t / wr, j = t - s * wr;
+    U[s * 64 + j] = M[(int64_t)(c0 + s) * ld + cs + j];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbeg = c0 + lw + blockIdx.x * 64;
+  for (int r = rbeg + warp; r < min(rbeg + 64, n); r += 8) {
+    const Cx<S>* lrow = M + (int64_t)r * ld + c0;
+    Cx<S> l[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s)
+      if (s < lw) l[s] = lrow[s];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      if (j < wr) {
+        S ar = 0, ai = 0;
+#pragma unroll
+        for (int s = 0; s < 16; ++s)
+          if (s < lw) {
+            const Cx<S> u = U[s * 64 + j];
+            ar += l[s].re * u.re - l[s].im * u.im;
+            ai += l[s].re * u.im + l[s].im * u.re;
+          }
+        Cx<S>& m = M[(int64_t)r * ld + cs + j];
+        m.re -= ar;
+        m.im -= ai;
+      }
+    }
+  }
+}
+
 // Leaf width for a panel whose rows start at p0: the widest power of two <= 8 whose leaf and U
 // block (lw x 64) fit in 200 KB of shared memory; 0 if even one column does not fit (then the
 // global-memory panel runs).
@@ -277,11 +322,19 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
     return BIE_OK;
   }
   BIE_TRY((set_smem_max(k_leaf<S>)));
+  // With a large batch the leaf kernel (one CTA per matrix) also updates the panel right of the
+  // leaf; with a small one that update runs as its own launch over all rows of every matrix.
+  const int fuse = batch >= 64 ? 1 : 0;
   for (int c0 = p0; c0 < p0 + w; c0 += lw) {
     const int l = std::min(lw, p0 + w - c0);
     const int wr = std::max(0, std::min(p0 + w, n) - c0 - l);  // panel columns right of the leaf
-    const size_t smem = ((size_t)(n - c0) * l + (size_t)l * wr) * sizeof(Cx<S>);
-    BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info));
+    const size_t smem = ((size_t)(n - c0) * l + (fuse ? (size_t)l * wr : 0)) * sizeof(Cx<S>);
+    BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info, fuse));
+    const int rows = n - c0 - l;
+    if (!fuse && rows > 0 && wr > 0) {
+      dim3 g((unsigned)((rows + 63) / 64), batch);
+      BIE_LAUNCH(k_leaf_update<S><<<g, 256, 0, c->stream>>>(A, bstride, n, ld, p0, w, c0, l));
+    }
   }
   return BIE_OK;
 }

@@ -194,3 +194,18 @@ def test_bulk_assembly_element_with_mixed_conditions(Solver, B):
     for i, k in enumerate(ks):
         P, Pn = oracle.solve_frequency(m, k, D)
         assert rel(surf[i, 0], P) <= TOL and rel(surf[i, 1], Pn) <= TOL, k
+
+
+def test_mixed_large_batch_matches_oracle(Solver, B):
+    """A batch of 70 systems (at least 64: the LU leaf kernel then updates the panel itself instead
+    of a separate launch) gives the oracle's solutions."""
+    m = octa_sphere(2)
+    ks = 0.11 * np.arange(1, 71)
+    s = _solver(Solver, m)
+    s.set_option("mixed.batch", 128)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i in range(0, 70, 3):
+        P, Pn = oracle.solve_frequency(m, ks[i], D)
+        assert rel(surf[i, 0], P) <= TOL, (ks[i], rel(surf[i, 0], P))
+    assert all(not (r.flags & B.BIE_FLAG_NOT_CONVERGED) for r in rep)
