@@ -277,9 +277,11 @@ __global__ void k_known_q32(const int32_t* __restrict__ esort, int64_t E, int Q,
 // a second set of ASM_W warps takes the other half of the same elements' quadrature points, so
 // that the registers of KB = 2 fit 16 warps per SM; the halves add into the row one after the
 // other (barrier of the row's warps in between: fixed order, deterministic sums).
-// grid (ceil(N / rows), ceil(nk / KB)); block 32 * rows * ASM_W * QS; smem rows * KB * N cf.
-template <int KB, int QS>
-__global__ void __launch_bounds__(256) k_asm32_bulk_u(
+// grid (ceil(N / rows), ceil(nk / KB)); block 32 * rows * ASM_W * QS; smem rows * KB * N cf, or
+// (GROW, large N) none: the rows then accumulate in A itself, each row owned by one CTA and the
+// row's warps ordered by the same barriers.
+template <int KB, int QS, bool GROW>
+__global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float4* __restrict__ qaos,
     const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
@@ -302,10 +304,23 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
     kinv[j] = (float)(1.0 / kv[kj]);
   }
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
-  for (int64_t t = threadIdx.x; t < (int64_t)rows * KB * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
-  __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * rows + rw;
   const bool valid = i < N;
+  // row j of this CTA's row rw: in shared memory, or (GROW) row i of system k0 + j in A
+  auto row_of = [&](int j) -> cf* {
+    if constexpr (GROW) return A + ((int64_t)(k0 + j) * N + i) * lda;
+    else return acc32 + ((int64_t)rw * KB + j) * N;
+  };
+  if constexpr (GROW) {
+    if (valid)
+      for (int j = 0; j < nkb; ++j) {
+        cf* r = row_of(j);
+        for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) r[c2] = {0.f, 0.f};
+      }
+  } else {
+    for (int64_t t = threadIdx.x; t < (int64_t)rows * KB * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
+  }
+  __syncthreads();
   const int qlo = h * Q / QS, qhi = (h + 1) * Q / QS;
   ff xi[3], nui[3];
   for (int d = 0; d < 3; ++d) {
@@ -401,7 +416,8 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
         if (act && h == hh) {
 #pragma unroll
           for (int j = 0; j < KB; ++j) {
-            cf* row = acc32 + ((int64_t)rw * KB + j) * N;
+            if (GROW && j >= nkb) break;  // no system behind a ragged group's last slots
+            cf* row = row_of(j);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
               row[el[a]].re += ar[j][a];
@@ -428,9 +444,11 @@ __global__ void __launch_bounds__(256) k_asm32_bulk_u(
   __syncthreads();
   if (!valid) return;
   for (int j = 0; j < nkb; ++j) {
-    const cf* row = acc32 + ((int64_t)rw * KB + j) * N;
-    cf* Arow = A + ((int64_t)(k0 + j) * N + i) * lda;
-    for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) Arow[c2] = row[c2];
+    if constexpr (!GROW) {
+      const cf* row = row_of(j);
+      cf* Arow = A + ((int64_t)(k0 + j) * N + i) * lda;
+      for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) Arow[c2] = row[c2];
+    }
     if (wr == 0 && lane < 6) {
       double x = 0.0;
       for (int w = 0; w < WR; ++w) x += part[rw][w][j][lane];
@@ -653,30 +671,45 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
         if (c->h_bc[c->h_elems[6 * e + a]] != c->h_bc[c->h_elems[6 * e]]) c->uniform_bc = 0;
   }
   // the uniform-condition kernel: KB = 2 wavenumbers per thread with the quadrature points of an
-  // element split over two warps (2 rows x 4 warps), or KB = 1 (4 rows x 2 warps); 256 threads
+  // element split over two warps (2 rows x 4 warps, 256 threads); its rows in shared memory while
+  // two CTAs fit an SM, else (large N) in A itself; KB = 1 (4 rows x 2 warps) on request
   int kb = (kq && c->uniform_bc == 1) ? c->asm_kb : 0;
-  if (kb == 2 && (size_t)2 * 2 * N * sizeof(cf) > 100 * 1024) kb = 1;  // two CTAs per SM
-  int urows = 4;
-  if (kb == 1)
-    while (urows > 1 && (size_t)urows * N * sizeof(cf) > 200 * 1024) urows /= 2;
-  if (kb == 2) urows = 2;
-  if (kb == 1 && (size_t)urows * N * sizeof(cf) > 200 * 1024) kb = 0;
   if (kb >= 1) {
     const int64_t E = c->E;
     dim3 gq((unsigned)((E + 255) / 256), nk);
     BIE_LAUNCH(k_known_q32<<<gq, 256, 0, c->stream>>>(sorted_elems(c), E, c->rule.Q, c->qshape32, known, N, kq));
-    const size_t usmem = (size_t)urows * kb * N * sizeof(cf);
-    dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)((nk + kb - 1) / kb));
     if (kb == 2) {
-      BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2>)));
-      BIE_LAUNCH(k_asm32_bulk_u<2, 2><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
-          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-          c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      const int urows = 2;
+      const bool grow = (size_t)urows * 2 * N * sizeof(cf) > 100 * 1024;
+      const size_t usmem = grow ? 0 : (size_t)urows * 2 * N * sizeof(cf);
+      dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)((nk + 1) / 2));
+      if (grow) {
+        BIE_LAUNCH(k_asm32_bulk_u<2, 2, true><<<gu, 32 * urows * ASM_W * 2, 0, c->stream>>>(
+            c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      } else {
+        BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2, false>)));
+        BIE_LAUNCH(k_asm32_bulk_u<2, 2, false><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
+            c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      }
     } else {
-      BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1>)));
-      BIE_LAUNCH(k_asm32_bulk_u<1, 1><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
-          c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-          c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      int urows = 4;
+      while (urows > 1 && (size_t)urows * N * sizeof(cf) > 200 * 1024) urows /= 2;
+      const bool grow = (size_t)urows * N * sizeof(cf) > 200 * 1024;
+      if (grow) urows = 4;
+      const size_t usmem = grow ? 0 : (size_t)urows * N * sizeof(cf);
+      dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)nk);
+      if (grow) {
+        BIE_LAUNCH(k_asm32_bulk_u<1, 1, true><<<gu, 32 * urows * ASM_W, 0, c->stream>>>(
+            c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      } else {
+        BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1, false>)));
+        BIE_LAUNCH(k_asm32_bulk_u<1, 1, false><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
+            c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+      }
     }
   }
   if (kb == 0) {

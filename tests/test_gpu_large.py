@@ -23,7 +23,7 @@ def test_large_lattice_rows_and_field(lattice):
     w = lattice
     m = w.mesh
     assert m.N == 20544
-    ks = w.k[[255, 1023]]  # ka = 1.5, 6
+    ks = w.k[[255, 640, 1023]]  # ka = 1.5, 3.75, 6; three: the two-wavenumber assembly's last group is ragged
     s = Solver(0)
     s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
     surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
