@@ -385,43 +385,64 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
   }
 }
 
-// ---- U = L11^{-1} A for a full 64-row panel, FP32: the column lives in registers -------------
-// grid (ceil((j1 - j0) / 128), batch), block 128, static smem 32 KB: one column j in [j0, j1) per
-// thread.  The 64 entries of the column are loaded once, solved in registers (the loops are fully
-// unrolled, so x[] never leaves the register file) and stored once: no solved entry is re-read
-// from global memory, where each re-read would wait on the L2.  The solve runs column by column
-// of L11 (x_s -= l_st x_t for all s > t once x_t is final): the up to 63 updates of a step are
-// independent, so the FMA latency is hidden inside the thread; each x_s still receives its
-// updates in increasing t, the order of the row-by-row substitution of k_swap_trsm.  L11 is
-// staged transposed (column t contiguous) and read by broadcast.
-__global__ void __launch_bounds__(128) k_trsm64(Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
-                                                int j0, int j1) {
-  __shared__ __align__(16) Cx<float> LT[64 * 64];  // LT[t * 64 + s] = L11[s][t]
+// ---- U = L11^{-1} A for a full 64-row panel, FP32 --------------------------------------------
+// grid (ceil((j1 - j0) / 64), batch), block 64, dynamic smem 64 KB: one column j in [j0, j1) per
+// thread, solved in four blocks of 16 rows.  A block's 16 entries live in registers: first the
+// products with the solved entries of the earlier blocks (a loop over t that reads x_t from this
+// thread's shared-memory column and L11's column t as 16-byte broadcasts), then the solve inside
+// the block (unrolled).  Each x_s receives its updates in increasing t, the order of the row-by-row
+// substitution of k_swap_trsm.  (A fully unrolled 64-entry register version ran from the
+// instruction cache's misses.)
+constexpr size_t kTrsmSmem = 2 * 64 * 64 * sizeof(Cx<float>);  // L11^T and the solved columns
+__global__ void __launch_bounds__(64) k_trsm64(Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
+                                               int j0, int j1) {
+  extern __shared__ float4 trsm_smem[];
+  Cx<float>* LT = reinterpret_cast<Cx<float>*>(trsm_smem);  // LT[t * 64 + s] = L11[s][t]
+  Cx<float>(*X)[64] = reinterpret_cast<Cx<float>(*)[64]>(LT + 64 * 64);  // X[s][thread]: the solved column
   Cx<float>* M = A + (int64_t)blockIdx.y * bstride;
-  // 32 independent loads per thread in flight (blockDim.x == 128)
-#pragma unroll
-  for (int e = threadIdx.x; e < 64 * 64; e += 128) {
+  const int tid = threadIdx.x;
+#pragma unroll 8
+  for (int e = tid; e < 64 * 64; e += 64) {
     const int r = e >> 6, c = e & 63;  // coalesced read of row r
     LT[c * 64 + r] = M[(int64_t)(p0 + r) * ld + p0 + c];
   }
   __syncthreads();
-  const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= j1 || j >= n) return;
-  Cx<float> x[64];
+  const int j = j0 + blockIdx.x * blockDim.x + tid;
+  const bool act = j < j1 && j < n;
+#pragma unroll 1
+  for (int b0 = 0; b0 < 64; b0 += 16) {
+    Cx<float> xb[16];
 #pragma unroll
-  for (int s = 0; s < 64; ++s) x[s] = M[(int64_t)(p0 + s) * ld + j];
+    for (int r = 0; r < 16; ++r) xb[r] = act ? M[(int64_t)(p0 + b0 + r) * ld + j] : Cx<float>{0.f, 0.f};
+#pragma unroll 2
+    for (int t = 0; t < b0; ++t) {  // earlier blocks
+      const Cx<float> xt = X[t][tid];
+      const float4* l4 = reinterpret_cast<const float4*>(&LT[t * 64 + b0]);
 #pragma unroll
-  for (int t = 0; t < 63; ++t) {
-    const Cx<float> xt = x[t];
+      for (int r = 0; r < 16; r += 2) {
+        const float4 l = l4[r >> 1];  // L11[b0 + r][t], L11[b0 + r + 1][t]
+        xb[r].re -= l.x * xt.re - l.y * xt.im;
+        xb[r].im -= l.x * xt.im + l.y * xt.re;
+        xb[r + 1].re -= l.z * xt.re - l.w * xt.im;
+        xb[r + 1].im -= l.z * xt.im + l.w * xt.re;
+      }
+    }
 #pragma unroll
-    for (int s = t + 1; s < 64; ++s) {
-      const Cx<float> l = LT[t * 64 + s];
-      x[s].re -= l.re * xt.re - l.im * xt.im;
-      x[s].im -= l.re * xt.im + l.im * xt.re;
+    for (int t = 0; t < 15; ++t) {  // inside the block
+      const Cx<float> xt = xb[t];
+#pragma unroll
+      for (int r = t + 1; r < 16; ++r) {
+        const Cx<float> l = LT[(b0 + t) * 64 + b0 + r];
+        xb[r].re -= l.re * xt.re - l.im * xt.im;
+        xb[r].im -= l.re * xt.im + l.im * xt.re;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      X[b0 + r][tid] = xb[r];
+      if (act && (b0 + r) > 0) M[(int64_t)(p0 + b0 + r) * ld + j] = xb[r];
     }
   }
-#pragma unroll
-  for (int s = 1; s < 64; ++s) M[(int64_t)(p0 + s) * ld + j] = x[s];
 }
 
 // ---- SIMT trailing update A22 -= L21 U12 (64 x 64 complex tile per CTA, 256 threads) ---------
@@ -554,8 +575,9 @@ int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstrid
   if (w == 64) {  // swaps here, the solve with the register-resident kernel
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, 0, c->stream>>>(M, bstride, n, ld, p0, w, piv, 0, p0 + w, 1));
     if (tend > p0 + w) {
-      dim3 gt((unsigned)((tend - p0 - w + 127) / 128), batch);
-      BIE_LAUNCH(k_trsm64<<<gt, 128, 0, c->stream>>>(M, bstride, n, ld, p0, p0 + w, tend));
+      BIE_TRY((set_smem_max(k_trsm64)));
+      dim3 gt((unsigned)((tend - p0 - w + 63) / 64), batch);
+      BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, p0 + w, tend));
     }
   } else {
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
@@ -571,8 +593,11 @@ int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride,
   if (jlo >= n) return BIE_OK;
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   dim3 gs((unsigned)((n - jlo + 127) / 128), batch);
-  if (w == 64)
-    BIE_LAUNCH(k_trsm64<<<gs, 128, 0, c->stream>>>(M, bstride, n, ld, p0, jlo, n));
+  if (w == 64) {
+    BIE_TRY((set_smem_max(k_trsm64)));
+    dim3 gt((unsigned)((n - jlo + 63) / 64), batch);
+    BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, jlo, n));
+  }
   else
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
                                                                                             nullptr, jlo, n, 0));
