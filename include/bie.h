@@ -110,6 +110,7 @@ typedef struct {
   int32_t tcgen05;     /* trailing-update kernel chosen ("mixed.tcgen05") */
   int32_t from_cache;  /* 1: read from the cache file, 0: measured now */
   double us_per_k;     /* measured time per wavenumber of the chosen setting */
+  int32_t lu_block;    /* columns over which the deferred update runs ("mixed.lu_block") */
 } bie_tune_result;
 
 /* Statistics of bie_sched_run. */
@@ -167,9 +168,10 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
 /* Tuning options of the mixed-precision path (names are case-sensitive):
  *   "mixed.tcgen05"        trailing LU update: 3 (default) persistent TMA-fed tcgen05 kernel
  *                          (TF32 operands, FP32 accumulation in TMEM) with the update of the
- *                          trailing matrix deferred over 256-column blocks (four 64-column
- *                          panels), 2 the same kernel after every 64-column panel, 1 the
+ *                          trailing matrix deferred over blocks of "mixed.lu_block" columns,
+ *                          2 the same kernel after every 64-column panel, 1 the
  *                          register-staged tcgen05 kernel, 0 FP32 on the CUDA cores.
+ *   "mixed.lu_block"       columns of the deferred update of version 3: 128, 256 (default), 512
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
@@ -266,8 +268,9 @@ int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64
 /* Autotuner of the mixed path (not part of the paper's method, which fixes no launch parameters):
  * for the context's geometry, times one batch of BIE_MODE_MIXED solves (sample wavenumbers
  * k host f64 [nk], repeated to fill the batch) for every candidate of "mixed.batch" in
- * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {3, 2},
- * and sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
+ * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {3, 2}
+ * (with "mixed.lu_block" 256), then, if version 3 won, "mixed.lu_block" 128 and 512 at the chosen
+ * batch, and sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
  * file keyed by N rounded up to 64; an entry for this N is applied without measuring, a new
  * measurement is added to it.  out (host, optional) receives the choice.  Synchronises.
  * Errors: STATE without geometry, OOM if no candidate fits, INVALID_ARG if the cache cannot be

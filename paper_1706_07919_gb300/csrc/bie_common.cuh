@@ -120,6 +120,8 @@ struct bie_ctx {
   int tc_version = 3;                // LU trailing update: 0 SIMT FP32, 1 tcgen05 (register-staged),
                                      // 2 tcgen05 (persistent, TMA-fed, warp-specialised), 3 as 2
                                      // with the update deferred over 256-column blocks
+  int lu_block = 256;                // mixed.tcgen05 3: columns over which the trailing update is
+                                     // deferred (128, 256 or 512)
   int mixed_batch = 64;              // wavenumbers per batch
   int refine_it_max = 10;            // refinement corrections per system
   int refine64_it_max = 30;          // corrections against the FP64 re-assembly of flagged systems

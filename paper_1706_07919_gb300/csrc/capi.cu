@@ -262,6 +262,10 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
       return fail(BIE_ERR_INVALID_ARG, "mixed.tcgen05 must be 0 (SIMT), 1, 2 or 3 (tensor-core kernels)");
     c->tc_version = (int)value;
+  } else if (n == "mixed.lu_block") {
+    if (value != 128.0 && value != 256.0 && value != 512.0)
+      return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 128, 256 or 512");
+    c->lu_block = (int)value;
   } else if (n == "mixed.batch") {
     if (value < 1 || value > 4096) return fail(BIE_ERR_INVALID_ARG, "mixed.batch must be in [1, 4096]");
     c->mixed_batch = (int)value;

@@ -518,8 +518,9 @@ static int make_map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d
 }  // namespace tc2
 
 // Version 3 (the default): the update of version 2, with the trailing update deferred over an
-// outer block of NBO = 256 columns (four 64-column panels), so that A22 is read and written once
-// per 256 columns instead of once per 64 (intensity 8 x 256 / 16 = 128 flop per byte of A22):
+// outer block of NBO columns (c->lu_block: 128, 256 or 512, i.e. 2, 4 or 8 64-column panels), so
+// that A22 is read and written once per NBO columns instead of once per 64 (at NBO = 256 the
+// intensity is 8 x 256 / 16 = 128 flop per byte of A22):
 //   for each outer block [P0, E):
 //     for each panel [p0, p0 + 64): factor it; swap rows in every column; U = L11^{-1} A for the
 //       block's columns right of the panel; update rows below the panel in the block's columns
@@ -527,11 +528,12 @@ static int make_map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d
 //     U12 (block rows, columns >= E) by block forward substitution: for each 64-row block b,
 //       A_b -= L_b,<b U_<b (K = 64 b), then U_b = L_bb^{-1} A_b.
 //     A22 (rows and columns >= E) -= L21 U12 with K = 256.
-constexpr int NBO = 256;
+constexpr int kMaxLuBlock = 512;
 
-size_t lu_tc_scratch_bytes(int batch, int n) {
-  // error flag, B^T for one 64-row panel (128 floats per row) and for one outer block (512)
-  return 256 + (size_t)batch * 2 * n * (2 * tc::NB + 2 * NBO) * sizeof(float);
+size_t lu_tc_scratch_bytes(int batch, int n, int block) {
+  // error flag, B^T for one 64-row panel (128 floats per row) and for one outer block (2 NBO)
+  if (block < tc::NB || block > kMaxLuBlock) block = kMaxLuBlock;
+  return 256 + (size_t)batch * 2 * n * (2 * tc::NB + 2 * block) * sizeof(float);
 }
 
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
@@ -541,6 +543,8 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   int32_t* err = (int32_t*)scratch;
   BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
   const int ver = c->tc_version;
+  const int NBO = c->lu_block;
+  if (NBO % NB != 0 || NBO < NB || NBO > kMaxLuBlock) return fail(BIE_ERR_INVALID_ARG, "LU block must be 128, 256 or 512");
   float* ub = reinterpret_cast<float*>((char*)scratch + 256);
   const int64_t ub_stride = (int64_t)2 * n * tc2::KR;  // floats per matrix, 64-row panel
   float* ubo = ub + (int64_t)batch * ub_stride;
@@ -549,7 +553,8 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   CUtensorMap mA, mB, mBo;
   int nsm = 148;
   if (ver >= 2) {
-    if (scratch_bytes < lu_tc_scratch_bytes(batch, n)) return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
+    if (scratch_bytes < lu_tc_scratch_bytes(batch, n, ver >= 3 ? NBO : NB))
+      return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
     BIE_TRY(tc2::make_map_3d(&mA, A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)batch, (uint64_t)2 * ld * 4,
                              (uint64_t)bstride * 8));
     BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)tc2::KR, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)tc2::KR * 4,

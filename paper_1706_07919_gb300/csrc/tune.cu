@@ -1,8 +1,10 @@
 // tune.cu -- autotuner of the mixed path's launch parameters per problem size.
 // For a geometry of N nodes the tuner times one batch of mixed-precision frequency solves for
 // every candidate (wavenumbers per batch x LU trailing-update kernel) and keeps the fastest per
-// wavenumber.  Results are cached per N bucket (N rounded up to a multiple of 64) in a small JSON
-// file:  {"bie_autotune": 1, "entries": {"2944": {"batch": 128, "tcgen05": 2, "us_per_k": ...}}}
+// wavenumber, then for the deferred update (tcgen05 = 3) the block over which it is deferred
+// (128, 256, 512 columns) at the chosen batch.  Results are cached per N bucket (N rounded up to a
+// multiple of 64) in a small JSON file:
+//   {"bie_autotune": 1, "entries": {"2944": {"batch": 128, "tcgen05": 3, "lu_block": 256, "us_per_k": ...}}}
 #include <algorithm>
 #include <cstdio>
 #include <fstream>
@@ -22,7 +24,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
                 int32_t* perm_keep, cf* d_keep);
 
 struct TuneEntry {
-  int batch = 0, tc = 0;
+  int batch = 0, tc = 0, block = 256;
   double us_per_k = 0.0;
 };
 
@@ -36,12 +38,12 @@ static std::map<int, TuneEntry> load_cache(const char* path) {
   const std::string s = ss.str();
   for (size_t i = 0; i + 1 < s.size(); ++i) {
     if (s[i] != '"' || !(s[i + 1] >= '0' && s[i + 1] <= '9')) continue;
-    int key = 0, b = 0, t = 0;
+    int key = 0, b = 0, t = 0, blk = 0;
     double us = 0.0;
-    if (std::sscanf(s.c_str() + i, "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"us_per_k\": %lf}", &key, &b, &t, &us) ==
-            4 &&
-        b >= 1 && t >= 0 && t <= 3)
-      m[key] = TuneEntry{b, t, us};
+    if (std::sscanf(s.c_str() + i, "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %lf}", &key,
+                    &b, &t, &blk, &us) == 5 &&
+        b >= 1 && t >= 0 && t <= 3 && (blk == 128 || blk == 256 || blk == 512))
+      m[key] = TuneEntry{b, t, blk, us};
   }
   return m;
 }
@@ -58,9 +60,10 @@ static bool save_cache(const char* path, const std::map<int, TuneEntry>& m) {
   f << "{\"bie_autotune\": 1, \"entries\": {\n";
   size_t i = 0;
   for (const auto& kv : m) {
-    char line[160];
-    std::snprintf(line, sizeof(line), "  \"%d\": {\"batch\": %d, \"tcgen05\": %d, \"us_per_k\": %.3f}%s\n", kv.first,
-                  kv.second.batch, kv.second.tc, kv.second.us_per_k, (++i < m.size()) ? "," : "");
+    char line[192];
+    std::snprintf(line, sizeof(line), "  \"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %.3f}%s\n",
+                  kv.first, kv.second.batch, kv.second.tc, kv.second.block, kv.second.us_per_k,
+                  (++i < m.size()) ? "," : "");
     f << line;
   }
   f << "}}\n";
@@ -76,7 +79,8 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   if (it != cache.end()) {
     c->mixed_batch = it->second.batch;
     c->tc_version = it->second.tc;
-    if (out) *out = bie_tune_result{key, it->second.batch, it->second.tc, 1, it->second.us_per_k};
+    c->lu_block = it->second.block;
+    if (out) *out = bie_tune_result{key, it->second.batch, it->second.tc, 1, it->second.us_per_k, it->second.block};
     return BIE_OK;
   }
   if (nk < 1) return fail(BIE_ERR_INVALID_ARG, "autotune needs at least one sample wavenumber");
@@ -84,7 +88,8 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   const size_t perk = 2 * (size_t)N * ld * sizeof(cf) + 64 * (size_t)N;
   size_t free_b = 0, total_b = 0;
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-  const int saved_batch = c->mixed_batch, saved_tc = c->tc_version, saved_graph = c->mixed_graph;
+  const int saved_batch = c->mixed_batch, saved_tc = c->tc_version, saved_graph = c->mixed_graph,
+            saved_block = c->lu_block;
   TuneEntry best;
   best.us_per_k = 1e300;
   std::vector<double> kk;
@@ -97,28 +102,40 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   if (cudaMalloc(&surf, surf_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(BIE_ERR_OOM, "autotune scratch");
+  // one timed batch (after an untimed one that sizes the workspace and builds the tables)
+  auto measure = [&](int b, int tc, int block, double* us) -> int {
+    kk.resize((size_t)b);
+    for (int i = 0; i < b; ++i) kk[i] = k[i % nk];
+    c->mixed_batch = b;
+    c->tc_version = tc;
+    c->lu_block = block;
+    c->mixed_graph = 0;
+    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr));
+    cudaEventRecord(e0, c->stream);
+    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr));
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *us = 1e3 * ms / b;
+    return BIE_OK;
+  };
   for (int tc : tcs) {
     for (int b : batches) {
       if (rc != BIE_OK) break;
       if ((size_t)b * perk > free_b / 3) continue;
-      kk.resize((size_t)b);
-      for (int i = 0; i < b; ++i) kk[i] = k[i % nk];
-      c->mixed_batch = b;
-      c->tc_version = tc;
-      c->mixed_graph = 0;
-      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr);  // warm-up: workspace, tables
-      if (rc != BIE_OK) break;
-      cudaEventRecord(e0, c->stream);
-      rc = solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr);
-      if (rc != BIE_OK) break;
-      cudaEventRecord(e1, c->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double us = 1e3 * ms / b;
-      if (us < best.us_per_k) best = TuneEntry{b, tc, us};
+      double us = 0.0;
+      rc = measure(b, tc, 256, &us);
+      if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{b, tc, 256, us};
     }
   }
+  if (rc == BIE_OK && best.tc == 3)  // then the block of the deferred update at the chosen batch
+    for (int block : {128, 512}) {
+      double us = 0.0;
+      rc = measure(best.batch, 3, block, &us);
+      if (rc != BIE_OK) break;
+      if (us < best.us_per_k) best = TuneEntry{best.batch, 3, block, us};
+    }
   if (surf) cudaFree(surf);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -126,17 +143,19 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   if (rc != BIE_OK || best.batch == 0) {
     c->mixed_batch = saved_batch;
     c->tc_version = saved_tc;
+    c->lu_block = saved_block;
     return rc != BIE_OK ? rc : fail(BIE_ERR_OOM, "autotune: no candidate fits in device memory");
   }
   c->mixed_batch = best.batch;
   c->tc_version = best.tc;
+  c->lu_block = best.block;
   if (cache_path) {
     std::lock_guard<std::mutex> g(g_cache_mu);
     cache = load_cache(cache_path);  // another thread or process may have added entries meanwhile
     cache[key] = best;
     if (!save_cache(cache_path, cache)) return fail(BIE_ERR_INVALID_ARG, std::string("cannot write ") + cache_path);
   }
-  if (out) *out = bie_tune_result{key, best.batch, best.tc, 0, best.us_per_k};
+  if (out) *out = bie_tune_result{key, best.batch, best.tc, 0, best.us_per_k, best.block};
   return BIE_OK;
 }
 

@@ -209,3 +209,20 @@ def test_mixed_large_batch_matches_oracle(Solver, B):
         P, Pn = oracle.solve_frequency(m, ks[i], D)
         assert rel(surf[i, 0], P) <= TOL, (ks[i], rel(surf[i, 0], P))
     assert all(not (r.flags & B.BIE_FLAG_NOT_CONVERGED) for r in rep)
+
+
+@pytest.mark.parametrize("block", [128, 512])
+def test_mixed_lu_block_variants(Solver, B, two_spheres, block):
+    """The deferred tensor-core update over 128- or 512-column blocks (N = 1284: whole blocks and a
+    ragged last one) gives the oracle's solutions with few refinement corrections."""
+    ks = np.array([1.5, 8.0])
+    s = _solver(Solver, two_spheres, tc=3)
+    s.set_option("mixed.lu_block", block)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(two_spheres, k, D)
+        assert rel(surf[i, 0], P) <= TOL, (k, rel(surf[i, 0], P))
+        assert rep[i].iters <= 8 and not (rep[i].flags & B.BIE_FLAG_NOT_CONVERGED), (k, rep[i].iters)
+    with pytest.raises(B.BieError):
+        s.set_option("mixed.lu_block", 192)
