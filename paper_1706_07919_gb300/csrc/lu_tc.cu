@@ -239,15 +239,15 @@ __global__ void __launch_bounds__(128, 2) k_update_tc(float* __restrict__ A, int
 namespace tc2 {
 
 constexpr int BM = 128;                  // rows per tile
-constexpr int BNR = 128;                 // real columns per tile (64 complex)
+constexpr int BNR = 256;                 // real columns per tile (128 complex)
 constexpr int KR = 2 * tc::NB;           // reals along K (128)
 constexpr int KCH = 32;                  // floats per 128-byte swizzle row
 constexpr int NCHK = KR / KCH;           // 4 chunks per tile
-constexpr int STAGES = 6;
+constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
-constexpr int B_STAGE = BNR * KCH * 4;   // 16 KB
+constexpr int B_STAGE = BNR * KCH * 4;   // 32 KB (two 128-row TMA boxes)
 constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 2 * A_STAGE + 1024;  // ring + 2 epilogue boxes
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;           // two 256-column accumulators
 constexpr int NTHREADS = 192;
 constexpr uint32_t SPIN = 1u << 22;
 
@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
           if (!ok) break;
           mbar_expect_tx(baddr(bar.full[s]), A_STAGE + B_STAGE);
           tma_load_3d(smA + s * A_STAGE, &tmA, 2 * rg.kc0 + ch * KCH, rg.r0 + tm * BM, z, baddr(bar.full[s]));
-          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, 2 * (rg.c0 - rg.ub_c0) + tn * BNR, z, baddr(bar.full[s]));
+          const int yb = 2 * (rg.c0 - rg.ub_c0) + tn * BNR;  // B^T rows of the tile, two boxes of BM rows
+          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, yb, z, baddr(bar.full[s]));
+          tma_load_3d(smB + s * B_STAGE + BM * KCH * 4, &tmB, ch * KCH, yb + BM, z, baddr(bar.full[s]));
         }
       }
     }
@@ -444,10 +446,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int gr0 = rg.r0 + tm * BM;
       const int gc0 = 2 * (rg.c0 + tn * (BNR / 2));  // first real column of the tile
+      const int gc_end = 2 * rg.c1;                   // chunks at or past it are not reduced
       const bool keep = gr0 + rt < rg.r1;             // rows past r1 add zero
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * BNR;
 #pragma unroll 1
       for (int cc = 0; cc < BNR; cc += 32, ++nb) {
+        // chunks at or past the region's last column are neither staged nor reduced (the same
+        // decision in all four warps; nb counts only the chunks that commit a reduction, so the
+        // box written next was read by the reduction two commits back)
+        if (gc0 + cc >= gc_end) break;
         float v[32];
         tmem_ld32(ta + cc, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
