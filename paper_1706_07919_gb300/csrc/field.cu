@@ -574,15 +574,16 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
             cg = t;
           }
           const float kRp = khi * Rp.hi, kR0 = khi * R0.hi;
-          const float Gpr = cp, Gpi = spp, G0r = c0, G0i = s0v;  // weighted by w
-          const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
-          const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
+          // G weighted by w; dG/dnu = -(Gr + Gi kR) rn + i (Gr kR - Gi) rn, taken as the
+          // difference dGp - dG0 directly
+          const float gdr = cp - c0, gdi = spp - s0v;
+          const float ddr = __fmaf_rn(__fmaf_rn(s0v, kR0, c0), rn0, -(__fmaf_rn(spp, kRp, cp) * rnp));
+          const float ddi = __fmaf_rn(__fmaf_rn(cp, kRp, -spp), rnp, -(__fmaf_rn(c0, kR0, -s0v) * rn0));
           const float g = cg, f = sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
           const float4 p0 = s0[j][tid], pq = sq[j][u];
           const float P0r = p0.x, P0i = p0.y, Q0r = p0.z, Q0i = p0.w;
           const float Ptr = pq.x - P0r * g - Q0r * f, Pti = pq.y - P0i * g - Q0i * f;
           const float dPr = pq.z - P0r * dg - Q0r * df, dPi = pq.w - P0i * dg - Q0i * df;
-          const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
           // run sums of w [P~ (dGp - dG0) - (Gp - G0) dP~]
           float a = __fmaf_rn(Ptr, ddr, pr[j]);
           a = __fmaf_rn(-Pti, ddi, a);
