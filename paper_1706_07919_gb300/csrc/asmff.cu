@@ -78,9 +78,9 @@ constexpr int ASMF_W = 2;
 template <bool GROW, int QS>
 __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
-    const int32_t* __restrict__ esort, const int32_t* __restrict__ eperm, int64_t N, int64_t E, int Q,
+    const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q,
     const float4* __restrict__ qaos /* colour-sorted float-float points, 64-byte records [Q][E] */,
-    const double* __restrict__ qgeo /* FP64 points (weights) */, const double* __restrict__ qshape,
+    const double* __restrict__ qshape,
     const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv, const cd* __restrict__ known,
     cd* __restrict__ A, cd* __restrict__ rowsum /* [nk][N][3] */, int rows, FFConst K) {
   constexpr int WR = ASMF_W * QS;  // warps per row
@@ -277,18 +277,18 @@ int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* know
   dim3 gb((unsigned)((N + rows - 1) / rows), nk);
   if (grow) {
     BIE_LAUNCH(k_asmff_bulk<true, 1><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
+        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   } else if (split) {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 2>)));
     BIE_LAUNCH(k_asmff_bulk<false, 2><<<gb, 32 * rows * ASMF_W * 2, smem, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
+        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   } else {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 1>)));
     BIE_LAUNCH(k_asmff_bulk<false, 1><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
-        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), c->elem_perm, N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qgeo, c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
+        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -242,7 +242,6 @@ constexpr int BM = 128;                  // rows per tile
 constexpr int BNR = 256;                 // real columns per tile (128 complex)
 constexpr int KR = 2 * tc::NB;           // reals along K (128)
 constexpr int KCH = 32;                  // floats per 128-byte swizzle row
-constexpr int NCHK = KR / KCH;           // 4 chunks per tile
 constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
 constexpr int B_STAGE = BNR * KCH * 4;   // 32 KB (two 128-row TMA boxes)
@@ -500,7 +499,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }
