@@ -302,13 +302,13 @@ __global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int6
   }
 }
 
-// Leaf width for a panel whose rows start at p0: the widest power of two <= 8 whose leaf and U
-// block (lw x 64) fit in 200 KB of shared memory; 0 if even one column does not fit (then the
-// global-memory panel runs).
+// Leaf width for a panel whose rows start at p0: the widest power of two <= 16 whose leaf and U
+// block (lw x 64) fit in 200 KB of shared memory (fewer, wider leaves re-read the panel fewer
+// times); 0 if even one column does not fit (then the global-memory panel runs).
 template <class S>
 static int leaf_width(int n, int p0) {
   const size_t rows = (size_t)(n - p0);
-  for (int lw = 8; lw >= 1; lw >>= 1)
+  for (int lw = 16; lw >= 1; lw >>= 1)
     if ((rows + 64) * lw * sizeof(Cx<S>) <= 200 * 1024) return lw;
   return 0;
 }
