@@ -22,18 +22,27 @@ namespace bie {
 // surface, be formed in float-float).
 enum { P32XH = 0, P32YH, P32ZH, P32XL, P32YL, P32ZL, P32NX, P32NY, P32NZ, P32W, P32NXL, P32NYL, P32NZL, P32COUNT };
 
-__global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __restrict__ o) {
+// aos (optional): the same 13 values per point as one 64-byte record [n][16 floats].
+__global__ void k_points_to32(const double* __restrict__ g, int64_t n, float* __restrict__ o,
+                              float4* __restrict__ aos) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  float v[P32COUNT];
   for (int d = 0; d < 3; ++d) {
-    ff v = ff_from_double(g[(GX + d) * n + p]);
-    o[(P32XH + d) * n + p] = v.hi;
-    o[(P32XL + d) * n + p] = v.lo;
-    ff nv = ff_from_double(g[(GNX + d) * n + p]);
-    o[(P32NX + d) * n + p] = nv.hi;
-    o[(P32NXL + d) * n + p] = nv.lo;
+    const ff x = ff_from_double(g[(GX + d) * n + p]);
+    const ff nv = ff_from_double(g[(GNX + d) * n + p]);
+    v[P32XH + d] = x.hi; v[P32XL + d] = x.lo;
+    v[P32NX + d] = nv.hi; v[P32NXL + d] = nv.lo;
   }
-  o[P32W * n + p] = (float)g[GWJ * n + p];
+  v[P32W] = (float)g[GWJ * n + p];
+  for (int f = 0; f < P32COUNT; ++f) o[f * n + p] = v[f];
+  if (aos) {
+    float4* a = aos + p * 4;
+    a[0] = make_float4(v[0], v[1], v[2], v[3]);
+    a[1] = make_float4(v[4], v[5], v[6], v[7]);
+    a[2] = make_float4(v[8], v[9], v[10], v[11]);
+    a[3] = make_float4(v[12], 0.f, 0.f, 0.f);
+  }
 }
 
 // The bulk kernel's copy of the same table, re-ordered for coalesced loads: elements in colour
@@ -474,7 +483,7 @@ __device__ __forceinline__ void halving_exchange(T* v, int o, bool upper) {
 __global__ void __launch_bounds__(128) k_asm32_near(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ elems, int64_t N, int64_t E, int QN, const int* __restrict__ nnear_d,
-    const float* __restrict__ ntab, const float* __restrict__ nshape, const int32_t* __restrict__ n2e_off,
+    const float4* __restrict__ naos, const float* __restrict__ nshape, const int32_t* __restrict__ n2e_off,
     const int32_t* __restrict__ n2e, const double* __restrict__ kv, const cd* __restrict__ known,
     cf* __restrict__ A, int64_t lda, const double* __restrict__ rowsum, cd* __restrict__ b, TwoPi3 tp) {
   const int lane = threadIdx.x & 31;
@@ -489,7 +498,6 @@ __global__ void __launch_bounds__(128) k_asm32_near(
     xi[d] = ff_from_double(nodes[3 * i + d]);
     nui[d] = ff_from_double(normals[3 * i + d]);
   }
-  const int64_t tot = E * 6 * (int64_t)QN;
   cf* Arow = A + ((int64_t)kk * N + i) * lda;
   // The regularisation sums per lane in compensated FP32 (they cancel against the bulk's) and the
   // nodal sums per lane in FP32 (a lane holds a few points of one element); across the warp the
@@ -506,8 +514,9 @@ __global__ void __launch_bounds__(128) k_asm32_near(
 #pragma unroll
     for (int a = 0; a < 6; ++a) { hr[a] = hi[a] = gr[a] = gi[a] = 0.f; }
     for (int qq = lane; qq < np; qq += 32) {
-      float q[P32COUNT];
-      load_point(ntab, tot, ((int64_t)e * 6 + a0) * QN + qq, q);
+      const float4* qp = naos + (((int64_t)e * 6 + a0) * QN + qq) * 4;  // the point's 64-byte record
+      const float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
+      const float q[P32COUNT] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x};
       Kern32 K;
       kernel32(k, kinv, xi, nui, tp, q, K);
       const float wj = q[P32W];
@@ -618,6 +627,10 @@ static size_t sorted_aos_offset(bie_ctx* c) {
   return ((size_t)(P32COUNT * (2 * nq + nn) + 6 * c->E) + 63) / 64 * 64;
 }
 static float4* sorted_aos(bie_ctx* c) { return reinterpret_cast<float4*>(c->qgeo32 + sorted_aos_offset(c)); }
+// the near points as 64-byte records [E * 6 * QN][16 floats], after the sorted records
+static float4* near_aos(bie_ctx* c) {
+  return reinterpret_cast<float4*>(c->qgeo32 + sorted_aos_offset(c) + 16 * (size_t)c->E * c->rule.Q);
+}
 const float4* sorted_aos_ptr(bie_ctx* c) { return sorted_aos(c); }
 
 const float* sorted_table_ptr(bie_ctx* c) { return sorted_table(c); }
@@ -626,9 +639,10 @@ const int32_t* sorted_elems_ptr(bie_ctx* c) { return sorted_elems(c); }
 int ensure_mixed_tables(bie_ctx* c) {
   if (c->qgeo32) return BIE_OK;
   const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
-  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (sorted_aos_offset(c) + 16 * (size_t)nq) * sizeof(float)));
-  BIE_LAUNCH(k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32));
-  BIE_LAUNCH(k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq));
+  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (sorted_aos_offset(c) + 16 * (size_t)(nq + nn)) * sizeof(float)));
+  BIE_LAUNCH(k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32, nullptr));
+  BIE_LAUNCH(k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq,
+                                                                                near_aos(c)));
   BIE_LAUNCH(k_points_to32_sorted<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(
       c->qgeo, c->elem_perm, c->elems, c->E, c->rule.Q, sorted_table(c), sorted_elems(c), sorted_aos(c)));
   BIE_CUDA_TRY(cudaGetLastError());
@@ -721,10 +735,9 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
                                                                         rowsum, rows, tp, (float)c->far_r2));
   }
   BIE_CUDA_TRY(cudaGetLastError());
-  const int64_t nq = c->E * c->rule.Q;
   dim3 gn((unsigned)((N * 32 + 127) / 128), nk);
   BIE_LAUNCH(k_asm32_near<<<gn, 128, 0, c->stream>>>(c->nodes, c->normals, c->bc, c->elems, N, c->E, c->rule.QN, c->d_nnear,
-                                          c->qgeo32 + P32COUNT * nq, c->nshape32, c->n2e_off, c->n2e, kv, known, A, lda,
+                                          near_aos(c), c->nshape32, c->n2e_off, c->n2e, kv, known, A, lda,
                                           rowsum, b, tp));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
