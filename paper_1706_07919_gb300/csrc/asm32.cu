@@ -501,11 +501,11 @@ __global__ void __launch_bounds__(128) k_asm32_near(
   cf* Arow = A + ((int64_t)kk * N + i) * lda;
   // The regularisation sums per lane in compensated FP32 (they cancel against the bulk's) and the
   // nodal sums per lane in FP32 (a lane holds a few points of one element); across the warp the
-  // nodal sums go to FP64 and are reduced by halving exchanges (36 FP64 additions per lane instead
-  // of 120 for six separate butterflies), so that each of six lanes ends with one node's four sums:
-  // the GB300's FP64 pipe is too narrow for per-point FP64 arithmetic here.
+  // nodal sums are reduced by halving exchanges, so that each of six lanes ends with one node's
+  // four sums, and the right-hand side accumulates in float-float: the GB300's FP64 pipe is too
+  // narrow for per-point or per-element FP64 arithmetic here.
   ksum sal_r, sal_i, sbe_r, sbe_i;
-  double bs_r = 0, bs_i = 0;
+  ff bsr = {0.f, 0.f}, bsi = {0.f, 0.f};
   const int node = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   for (int32_t t = n2e_off[i]; t < n2e_off[i + 1]; ++t) {
     const int32_t e = n2e[t] >> 3, a0 = n2e[t] & 7;
@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(128) k_asm32_near(
       }
     }
     // node a: u[4a .. 4a+3] = h re, h im, g re, g im; nodes 6, 7 are padding.  The first two
-    // levels add partial sums of 2 and 4 lanes in FP32 (small against the total), the rest in FP64.
+    // levels add partial sums of 2 and 4 lanes in FP32 (small against the total), the rest in
+    // float-float (FP32 pipes: the FP64 pipe of the GB300 is too narrow for this reduction).
     float u[32];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
@@ -547,32 +548,42 @@ __global__ void __launch_bounds__(128) k_asm32_near(
     for (int m = 24; m < 32; ++m) u[m] = 0.f;
     halving_exchange<16>(u, 16, (lane & 16) != 0);
     halving_exchange<8>(u, 8, (lane & 8) != 0);
-    double v[8];
+    ff v[4];
+    {
+      const bool up = (lane & 4) != 0;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = u[m];
-    halving_exchange<4>(v, 4, (lane & 4) != 0);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      v[m] += __shfl_xor_sync(0xffffffffu, v[m], 2);
-      v[m] += __shfl_xor_sync(0xffffffffu, v[m], 1);
+      for (int m = 0; m < 4; ++m) {
+        const float send = up ? u[m] : u[m + 4], keep = up ? u[m + 4] : u[m];
+        v[m] = ff_two_sum(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+      }
     }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        const ff r = {__shfl_xor_sync(0xffffffffu, v[m].hi, o), __shfl_xor_sync(0xffffffffu, v[m].lo, o)};
+        v[m] = ff_add(v[m], r);
+      }
     if ((lane & 3) == 0 && node < 6) {  // this lane holds node `node`'s sums
       const int32_t j = elems[6 * (int64_t)e + node];
-      const cd kj = kn[j];
-      if (bc[j] == 0) {
-        Arow[j].re += (float)v[0]; Arow[j].im += (float)v[1];
-        bs_r += v[2] * kj.re - v[3] * kj.im; bs_i += v[2] * kj.im + v[3] * kj.re;
-      } else {
-        Arow[j].re -= (float)v[2]; Arow[j].im -= (float)v[3];
-        bs_r -= v[0] * kj.re - v[1] * kj.im; bs_i -= v[0] * kj.im + v[1] * kj.re;
+      const ff kr = ff_from_double(kn[j].re), ki = ff_from_double(kn[j].im);
+      if (bc[j] == 0) {  // hard column: A += H, b += G known
+        Arow[j].re += __fadd_rn(v[0].hi, v[0].lo); Arow[j].im += __fadd_rn(v[1].hi, v[1].lo);
+        bsr = ff_add(bsr, ff_sub(ff_mul(v[2], kr), ff_mul(v[3], ki)));
+        bsi = ff_add(bsi, ff_add(ff_mul(v[2], ki), ff_mul(v[3], kr)));
+      } else {           // soft column: A -= G, b -= H known
+        Arow[j].re -= __fadd_rn(v[2].hi, v[2].lo); Arow[j].im -= __fadd_rn(v[3].hi, v[3].lo);
+        bsr = ff_sub(bsr, ff_sub(ff_mul(v[0], kr), ff_mul(v[1], ki)));
+        bsi = ff_sub(bsi, ff_add(ff_mul(v[0], ki), ff_mul(v[1], kr)));
       }
     }
     __syncwarp();  // the next element (sharing nodes with this one) updates after these writes
   }
   for (int o = 16; o > 0; o >>= 1) {
-    bs_r += __shfl_xor_sync(0xffffffffu, bs_r, o);
-    bs_i += __shfl_xor_sync(0xffffffffu, bs_i, o);
+    bsr = ff_add(bsr, ff{__shfl_xor_sync(0xffffffffu, bsr.hi, o), __shfl_xor_sync(0xffffffffu, bsr.lo, o)});
+    bsi = ff_add(bsi, ff{__shfl_xor_sync(0xffffffffu, bsi.hi, o), __shfl_xor_sync(0xffffffffu, bsi.lo, o)});
   }
+  double bs_r = ff_to_double(bsr), bs_i = ff_to_double(bsi);
   double al_r = sal_r.value(), al_i = sal_i.value(), be_r = sbe_r.value(), be_i = sbe_i.value();
   for (int o = 16; o > 0; o >>= 1) {
     al_r += __shfl_xor_sync(0xffffffffu, al_r, o); al_i += __shfl_xor_sync(0xffffffffu, al_i, o);
