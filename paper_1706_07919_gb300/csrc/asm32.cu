@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
           const ff R2 = ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz));
           const ff R = ff_sqrt(R2);
           const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
-          const float invR = 1.0f / R.hi;
+          const float invR = __frcp_rn(R.hi);  // correctly rounded, as 1.0f / R.hi
           float rnu;
           if (R2.hi > far_r2)
             rnu = rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8];
