@@ -14,7 +14,8 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   foot_points                             pinned: sphere closest point is radial projection
   field                                   pinned: interior point source, conventional representation
   dft / synthesize                        pinned: numpy FFT, Gaussian closed form, Parseval
-  full solve                              pinned: analytic rigid/soft sphere partial-wave series
+  full solve                              pinned: analytic rigid/soft sphere partial-wave series;
+                                          k = 0: soft sphere -a/r, harmonic linear identity, limit k -> 0
   mlp_features                            pinned: closed-form values at chosen nodes
   mlp_forward / mlp_loss                  pinned: zero-weight and single-path closed forms
   mlp_loss_grad                           pinned: central finite differences of mlp_loss

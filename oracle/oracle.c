@@ -202,7 +202,9 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
       cplx G = eikr / R;                                           /* Eq. Green_func */
       cplx dG = eikr * (I * k * R - 1.0) * dot3(r, nu) / (R * R * R); /* dG/dnu at x */
       double s = k * dot3(nu0, r);
-      double g = cos(s), f = sin(s) / k;                           /* Eqs. g_function, f_function */
+      /* Eqs. g_function, f_function; at k = 0 (the zero-frequency term of Eq. inverseFourier) f
+       * takes its limit sin(k nu_i.r)/k -> nu_i.r, while g -> 1 and G -> 1/R need no change */
+      double g = cos(s), f = (k == 0.0) ? dot3(nu0, r) : sin(s) / k;
       double dg = -k * sin(s) * dot3(nu0, nu), df = cos(s) * dot3(nu0, nu);
       double wJ = qw[q] * J;
       for (int a = 0; a < 6; ++a) {
@@ -218,7 +220,7 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
 }
 
 static int check_mesh(int64_t N, const int32_t* elems, int64_t E, double k, int ng, int ng_near) {
-  if (N < 1 || E < 1 || !(k > 0.0) || ng < 1 || ng > 16 || ng_near < 1 || ng_near > 16) return -1;
+  if (N < 1 || E < 1 || !(k >= 0.0) || ng < 1 || ng > 16 || ng_near < 1 || ng_near > 16) return -1;
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 6; ++a)
       if (elems[6 * e + a] < 0 || elems[6 * e + a] >= N) return -1;
@@ -512,7 +514,7 @@ int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t
 int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
              const cplx* P, const cplx* Pn, const double* xp, int64_t M, const int32_t* foot_elem,
              const double* foot_xi, const double* foot_eta, cplx* T) {
-  if (N < 1 || E < 1 || !(k > 0.0) || ng < 1 || ng > 16) return -1;
+  if (N < 1 || E < 1 || !(k >= 0.0) || ng < 1 || ng > 16) return -1;
   double sxi[256], seta[256], sw[256];
   int nq = or_rule_std(ng, sxi, seta, sw);
 #pragma omp parallel for schedule(dynamic, 8)
@@ -539,7 +541,7 @@ int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, do
         cplx dGp = ep * (I * k * Rp - 1.0) * dot3(rp, nu) / (Rp * Rp * Rp);
         cplx dG0 = e0 * (I * k * R0 - 1.0) * dot3(r0, nu) / (R0 * R0 * R0);
         double s = k * dot3(nu0, r0);
-        double g = cos(s), f = sin(s) / k;
+        double g = cos(s), f = (k == 0.0) ? dot3(nu0, r0) : sin(s) / k; /* k = 0: the limit nu0.r0 */
         double dg = -k * sin(s) * dot3(nu0, nu), df = cos(s) * dot3(nu0, nu);
         cplx Pt = Pq - P0 * g - Pn0 * f;
         cplx dPt = Pnq - P0 * dg - Pn0 * df;

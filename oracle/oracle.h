@@ -42,6 +42,8 @@ int or_rule_near(int n, int a, double* xi, double* eta, double* w);
  *   Gm[i][j] = sum_{e,q} w J N_a G(x_i,x_q)
  *   alpha[i] = sum_{e,q} w J [g_i dG/dnu - dg_i/dnu G],  beta[i] = same with f_i
  * with g_i = cos(k nu_i.(x-x_i)), f_i = sin(k nu_i.(x-x_i))/k (Eqs. f_function, g_function).
+ * k >= 0: at k = 0 (the zero-frequency term of Eq. inverseFourier, the Laplace limit) the same
+ * formulas hold with f_i replaced by its limit nu_i.(x-x_i); G = 1/R, g = 1, dg = 0.
  * Elements that contain node i use the near rule (ng_near), the others the standard rule (ng). */
 int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
                     const double* normals, double k, int ng, int ng_near,
@@ -84,7 +86,8 @@ int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t
 /* Scattered field T(x_p) per unit incident amplitude from the surface solution, by the
  * boundary-regularised representation Eq. BRIEFdmn with its S_inf parts evaluated analytically
  * (App. B reasoning): 4 pi P(x_p) = 4 pi P0 + int_S Pt (dG_p - dG_0) - (G_p - G_0) dPt dS,
- * Pt = P - P0 g - P0' f about the foot point x0; standard rule on every element. */
+ * Pt = P - P0 g - P0' f about the foot point x0; standard rule on every element.  k >= 0, with
+ * f -> nu0.(x - x0) at k = 0 as in or_assemble_raw. */
 int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
              const double _Complex* P, const double _Complex* Pn, const double* xp, int64_t M,
              const int32_t* foot_elem, const double* foot_xi, const double* foot_eta,

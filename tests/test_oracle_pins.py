@@ -110,7 +110,7 @@ def test_entire_solution_identity_converges(k):
     assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
 
 
-@pytest.mark.parametrize("k", [1.0, 3.0])
+@pytest.mark.parametrize("k", [0.0, 1.0, 3.0])
 def test_interior_point_source_fixes_infinity_term(k):
     """A point source inside the body is a radiating exterior solution: the full row equation,
     with +4 pi P(x_i) from S_inf, must vanish; with -4 pi it is off by 8 pi P."""
@@ -129,6 +129,65 @@ def test_interior_point_source_fixes_infinity_term(k):
             assert np.linalg.norm(wrong) / (4 * np.pi * np.linalg.norm(u)) > 1.5
     assert errs[2] < 1e-4
     assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
+
+
+def test_laplace_limit_linear_solution_identity():
+    """k = 0 (the zero-frequency term of Eq. inverseFourier): u = c.x + u0 is harmonic and regular
+    inside the body, so the row equation without the S_inf term vanishes up to discretisation
+    error.  Its normal derivative c.nu enters through f's limit nu_i.(x - x_i): with f dropped the
+    residual stays at 0.27, with f negated at 0.55, at every refinement (measured)."""
+    c = np.array([0.3, -0.5, 0.8])
+    errs = []
+    for L in (1, 2, 3):
+        m = octa_sphere(L)
+        u = (m.nodes @ c + 0.4).astype(complex)
+        du = (m.normals @ c).astype(complex)
+        errs.append(_residuals(m, 0.0, u, du, with_4pi=False))
+    assert errs[2] < 2e-4
+    assert errs[0] / errs[1] > 7 and errs[1] / errs[2] > 7
+
+
+def test_laplace_limit_is_the_limit_of_the_wavenumber_system():
+    """The k = 0 system is the k -> 0 limit of the k > 0 system: every entry of A and b at
+    k = 1e-7 agrees with k = 0 to O(k R), for a soft and a hard body."""
+    for bc in (0, 1):
+        m = octa_sphere(1, bc=bc)
+        A0, b0 = oracle.assemble_system(m, 0.0, D)
+        A1, b1 = oracle.assemble_system(m, 1e-7, D)
+        assert np.abs(A1 - A0).max() <= 1e-6 * np.abs(A0).max()
+        if bc == 1:
+            assert np.abs(b1 - b0).max() <= 1e-6 * np.abs(b0).max()
+        else:
+            assert np.abs(b0).max() == 0.0 and np.abs(b1).max() < 1e-5
+
+
+@pytest.mark.parametrize("a", [1.0, 0.7])
+def test_soft_sphere_zero_frequency_closed_form(a):
+    """k = 0 exactly, soft sphere of radius a: P_scat = -a/r, so dP/dnu = 1/a on the surface and
+    the field is -a/r outside; the discrete solution converges to it under refinement."""
+    pts = shell_points(24, 1.3 * a, 3.0 * a, seed=5)
+    e_surf, e_field = [], []
+    for L in (1, 2, 3):
+        m = scale_translate(octa_sphere(L, bc=1), a, (0.0, 0.0, 0.0))
+        P, Pn = oracle.solve_frequency(m, 0.0, D)
+        np.testing.assert_array_equal(P, -np.ones(m.N))
+        e_surf.append(np.abs(Pn - 1.0 / a).max() * a)
+        T = oracle.field(m, 0.0, P, Pn, pts)
+        ex = -a / np.linalg.norm(pts, axis=1)
+        e_field.append(np.abs(T - ex).max() / np.abs(ex).max())
+    assert e_surf[1] < 2e-3 and e_field[1] < 1e-3    # measured 9.1e-4, 4.0e-4
+    assert e_surf[0] / e_surf[1] > 7 and e_surf[1] / e_surf[2] > 7
+    assert e_field[2] < 1e-4                          # measured 3.7e-5
+
+
+def test_hard_body_zero_frequency_scatters_nothing():
+    """k = 0, sound-hard body: the known normal derivative -d.nu ik exp(ik d.x) vanishes, so the
+    right-hand side and the scattered field are exactly zero."""
+    m = octa_sphere(1, bc=0)
+    A, b = oracle.assemble_system(m, 0.0, D)
+    assert np.abs(b).max() == 0.0
+    P, Pn = oracle.solve_frequency(m, 0.0, D)
+    assert np.abs(P).max() == 0.0 and np.abs(Pn).max() == 0.0
 
 
 def test_two_body_point_sources():
