@@ -205,16 +205,18 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  * Errors: INVALID_ARG for an unknown name or a value out of range. */
 int bie_set_option(bie_ctx* ctx, const char* name, double value);
 
-/* Assembles the FP64 system of one wavenumber k > 0: Eq. (BRIEF) at every node with the App. B
+/* Assembles the FP64 system of one wavenumber k >= 0: Eq. (BRIEF) at every node with the App. B
  * term 4 pi P(x_i), unknown P at hard nodes and dP/dn at soft nodes, known values from the
  * scattered-field boundary conditions of Sec. 4 (p_scat = -p_inc soft, dp_scat/dn = -dp_inc/dn
- * hard) moved to the right-hand side.
+ * hard) moved to the right-hand side.  k = 0 is the zero-frequency term of Eq. (inverseFourier): the
+ * kernels take their k -> 0 limit (G = 1/R, g = 1, f = nu_i.(x - x_i)), the Laplace problem.
  *   A_out device c128 [N][N] row-major, b_out device c128 [N].
- * Errors: INVALID_ARG (k <= 0 or not finite, NULL pointer), STATE (no geometry). */
+ * Errors: INVALID_ARG (k < 0, 0 < k < 1e-30 or not finite, NULL pointer), STATE (no geometry). */
 int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
 
-/* Frequency solves (the per-k hot path): for each k[m] > 0 assemble, factor and solve.
- *   k        host f64 [Nk]
+/* Frequency solves (the per-k hot path): for each k[m] assemble, factor and solve.
+ *   k        host f64 [Nk]: each 0 (the zero-frequency term, solved by the k -> 0 limit of the
+ *            same kernels, see bie_assemble; not in BIE_MODE_LEARNED) or >= 1e-30
  *   mode     BIE_MODE_FP64, BIE_MODE_MIXED or BIE_MODE_LEARNED (which trains the context's
  *            network on this call's anchors, replacing its parameters)
  *   surf_out device c128 [Nk][2][N]: scattered P and dP/dn at every node, per k
@@ -226,17 +228,20 @@ int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, v
 
 /* Scattered field at M observation points (Eq. BRIEFdmn with the closest surface point x0 of
  * each point, Sec. 3), for every k:
- *   xobs  device f64 [M][3] points in the fluid
- *   k     host f64 [Nk]; surf device c128 [Nk][2][N] as written by bie_solve_frequencies
+ *   xobs  device f64 [M][3] points in the fluid (a point behind its closest surface point, i.e.
+ *         inside a body, is rejected with INVALID_ARG naming the lowest such index)
+ *   k     host f64 [Nk] (k = 0 allowed, as in bie_solve_frequencies); surf device c128 [Nk][2][N]
+ *         as written by bie_solve_frequencies
  *   T_out device c128 [Nk][M]
  *   mode  BIE_MODE_FP64 (FP64 arithmetic) or BIE_MODE_MIXED (FP32 with float-float phases)
- * Foot points are computed on the device at every call.  Errors: INVALID_ARG, STATE, CUDA. */
+ * Foot points are computed on the device at every call (the inside test reads one word back).
+ * Errors: INVALID_ARG, STATE, CUDA. */
 int bie_eval_field(bie_ctx* ctx, const double* xobs, int64_t M, const double* k, int64_t Nk,
                    const void* surf, int mode, void* T_out);
 
 /* Spectra of sampled pulses with the sign of Eq. (inverseFourier):
  *   S[p][m] = sum_n s[p][n] exp(+2 pi i m n / Nt), m = 0 .. Nt/2.
- *   s device f64 [P][Nt], S_out device c128 [P][Nt/2+1].  Nt even, 2 <= Nt <= 65536. */
+ *   s device f64 [P][Nt], S_out device c128 [P][Nt/2+1].  Nt a power of two in [2, 4096]. */
 int bie_pulse_spectrum(bie_ctx* ctx, const double* s, int64_t P, int64_t Nt, void* S_out);
 
 /* Space-time scattered field (Sec. 3 end, Sec. 4): for each pulse p, point x and time sample n
@@ -244,7 +249,7 @@ int bie_pulse_spectrum(bie_ctx* ctx, const double* s, int64_t P, int64_t Nt, voi
  * w_m = 1 for m = 0 or Nt/2, else 2 (real signals); frequencies not listed contribute zero.
  *   T device c128 [Nk][M]; midx host i64 [Nk], strictly increasing, 0 <= m <= Nt/2
  *   S device c128 [P][Nt/2+1]; out device, f64 (out_dtype 0) or f32 (out_dtype 1), [P][M][Nt]
- * Errors: INVALID_ARG (sizes, ordering, Nt not a power of two in [2, 65536]). */
+ * Errors: INVALID_ARG (sizes, ordering, Nt not a power of two in [2, 4096]). */
 int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk, int64_t M,
                    const void* S, int64_t P, int64_t Nt, void* out, int out_dtype);
 
@@ -259,8 +264,9 @@ int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk,
  * stream has completed.
  * Limits: Nt a power of two in [2, 4096] and Nk <= 4096 (midx entries are in [0, Nt/2] anyway);
  * larger sizes return BIE_ERR_INVALID_ARG with a message.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture begins.  All calls share the one array and every call rewrites the parts it uses, so
+ * the array's device address (cudaGetSymbolAddress) and keeps it for the process; make that first
+ * call before any stream capture begins, and do not use this entry point after a cudaDeviceReset
+ * of that device (the kept address would be stale).  All calls share the one array and every call rewrites the parts it uses, so
  * calls whose work overlaps on the GPU (different streams or threads) race. */
 int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
                            int64_t P, int64_t Nt, void* out, int out_dtype, void* stream);

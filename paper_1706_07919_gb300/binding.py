@@ -197,15 +197,50 @@ def bie_solve_frequencies(ctx: int, k, mode: int, surf_out, reports: bool = True
 
 def bie_eval_field(ctx: int, xobs, k, surf, mode: int, T_out) -> None:
     k = np.ascontiguousarray(k, np.float64)
+    if len(xobs.shape) != 2 or xobs.shape[1] != 3 or _dtype_name(xobs) != "float64":
+        raise ValueError(f"xobs must be float64 [M][3], got {_dtype_name(xobs)} {tuple(xobs.shape)}")
+    if _dtype_name(T_out) != "complex128" or _numel(T_out) != k.shape[0] * xobs.shape[0]:
+        raise ValueError(f"T_out must be complex128 with Nk*M = {k.shape[0] * xobs.shape[0]} elements")
     _check(load().bie_eval_field(ctx, _dp(xobs), xobs.shape[0], _hp(k), k.shape[0], _dp(surf), mode, _dp(T_out)))
 
 
 def bie_pulse_spectrum(ctx: int, s, S_out) -> None:
+    if len(s.shape) != 2 or _dtype_name(s) != "float64":
+        raise ValueError(f"s must be float64 [P][Nt], got {_dtype_name(s)} {tuple(s.shape)}")
+    if _dtype_name(S_out) != "complex128" or _numel(S_out) != s.shape[0] * (s.shape[1] // 2 + 1):
+        raise ValueError("S_out must be complex128 [P][Nt/2+1]")
     _check(load().bie_pulse_spectrum(ctx, _dp(s), s.shape[0], s.shape[1], _dp(S_out)))
+
+
+def _dtype_name(t) -> str:
+    return str(t.dtype).split(".")[-1]
+
+
+def _numel(t) -> int:
+    return int(t.numel()) if callable(getattr(t, "numel", None)) else int(np.prod(t.shape))
+
+
+def _synth_shapes(T, midx, S, Nt: int, out, out_dtype: int) -> None:
+    """Argument checks of the synthesis calls (sizes and dtypes only): a short or mistyped output
+    would otherwise be written past its end on the device."""
+    Nk = midx.shape[0]
+    if out_dtype not in (0, 1):
+        raise ValueError("out_dtype must be 0 (float64) or 1 (float32)")
+    if Nk > 0 and (len(T.shape) != 2 or T.shape[0] != Nk or _dtype_name(T) != "complex128"):
+        raise ValueError(f"T must be complex128 [Nk={Nk}][M], got {_dtype_name(T)} {tuple(T.shape)}")
+    if len(S.shape) != 2 or S.shape[1] != Nt // 2 + 1 or _dtype_name(S) != "complex128":
+        raise ValueError(f"S must be complex128 [P][Nt/2+1={Nt // 2 + 1}], got {_dtype_name(S)} {tuple(S.shape)}")
+    want = "float64" if out_dtype == 0 else "float32"
+    if _dtype_name(out) != want:
+        raise ValueError(f"out must have dtype {want} for out_dtype={out_dtype}, got {_dtype_name(out)}")
+    P, M = S.shape[0], T.shape[1]
+    if _numel(out) != P * M * Nt:
+        raise ValueError(f"out must hold P*M*Nt = {P * M * Nt} elements, got {_numel(out)}")
 
 
 def bie_synthesize(ctx: int, T, midx, S, Nt: int, out, out_dtype: int) -> None:
     midx = np.ascontiguousarray(midx, np.int64)
+    _synth_shapes(T, midx, S, Nt, out, out_dtype)
     _check(load().bie_synthesize(ctx, _dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
                                  _dp(out), out_dtype))
 
@@ -213,6 +248,7 @@ def bie_synthesize(ctx: int, T, midx, S, Nt: int, out, out_dtype: int) -> None:
 def bie_synthesize_noalloc(T, midx, S, Nt: int, out, out_dtype: int, stream: int | None = None) -> None:
     """Allocation-free synthesis for callers that cannot allocate device memory (see bie.h)."""
     midx = np.ascontiguousarray(midx, np.int64)
+    _synth_shapes(T, midx, S, Nt, out, out_dtype)
     _check(load().bie_synthesize_noalloc(_dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
                                          _dp(out), out_dtype, stream))
 

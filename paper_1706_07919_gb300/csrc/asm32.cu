@@ -128,7 +128,7 @@ __device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff*
   float cg, sg;
   ff_cis(ff_mul(k, nr), tp, cg, sg);
   const float nn = nui[0].hi * q[6] + nui[1].hi * q[7] + nui[2].hi * q[8];
-  const float g = cg, f = sg * kinv, dg = -k.hi * sg * nn, df = cg * nn;
+  const float g = cg, f = kinv != 0.f ? sg * kinv : nr.hi, dg = -k.hi * sg * nn, df = cg * nn;
   o.alr = g * o.dGr - dg * o.Gr;
   o.ali = g * o.dGi - dg * o.Gi;
   o.ber = f * o.dGr - df * o.Gr;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(512) k_asm32_bulk(
   const int rw = warp / ASM_W, sub = warp % ASM_W;
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
-  const float kinv = (float)(1.0 / kv[kk]);
+  const float kinv = kinv32(kv[kk]);
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
   for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
   __syncthreads();
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
   for (int j = 0; j < KB; ++j) {
     const int kj = min(k0 + j, nk - 1);  // a ragged last group repeats its last wavenumber
     k[j] = ff_from_double(kv[kj]);
-    kinv[j] = (float)(1.0 / kv[kj]);
+    kinv[j] = kinv32(kv[kj]);
   }
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
   const int64_t i = (int64_t)blockIdx.x * rows + rw;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
             const float dGr = (-c - s * kR) * rn, dGi = (c * kR - s) * rn;
             float cg, sg;
             ff_cis(ff_mul(k[j], nr), tp, cg, sg);
-            const float g = cg, f = sg * kinv[j], dg = -k[j].hi * sg * nn, df = cg * nn;
+            const float g = cg, f = kinv[j] != 0.f ? sg * kinv[j] : nr.hi, dg = -k[j].hi * sg * nn, df = cg * nn;
             ear[j] = __fmaf_rn(wj, g * dGr - dg * Gr, ear[j]);
             eai[j] = __fmaf_rn(wj, g * dGi - dg * Gi, eai[j]);
             ebr[j] = __fmaf_rn(wj, f * dGr - df * Gr, ebr[j]);
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(128) k_asm32_near(
   const int kk = blockIdx.y;
   if (i >= N) return;
   const ff k = ff_from_double(kv[kk]);
-  const float kinv = (float)(1.0 / kv[kk]);
+  const float kinv = kinv32(kv[kk]);
   const cd* kn = known + (int64_t)kk * N;
   ff xi[3], nui[3];
   for (int d = 0; d < 3; ++d) {
@@ -503,7 +503,8 @@ __global__ void __launch_bounds__(128) k_asm32_near(
   // nodal sums per lane in FP32 (a lane holds a few points of one element); across the warp the
   // nodal sums are reduced by halving exchanges, so that each of six lanes ends with one node's
   // four sums, and the right-hand side accumulates in float-float: the GB300's FP64 pipe is too
-  // narrow for per-point or per-element FP64 arithmetic here.
+  // narrow for per-point FP64 arithmetic here (per element, six lanes split their node's known
+  // value into float-float: two FP64 conversions and subtractions each).
   ksum sal_r, sal_i, sbe_r, sbe_i;
   ff bsr = {0.f, 0.f}, bsi = {0.f, 0.f};
   const int node = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);

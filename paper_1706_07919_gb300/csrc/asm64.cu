@@ -58,11 +58,13 @@ __device__ __forceinline__ void kernel64(double k, const double* xi, const doubl
   double rn = (rx * nx + ry * ny + rz * nz) * invR * invR * invR;
   // (c + i s)(i kR - 1) = (-c - s kR) + i (c kR - s)
   o.dG = {(-c - s * kR) * rn, (c * kR - s) * rn};
-  double sa = k * (nui[0] * rx + nui[1] * ry + nui[2] * rz);
+  const double nr = nui[0] * rx + nui[1] * ry + nui[2] * rz;
+  double sa = k * nr;
   double sg, cg;
   sincos(sa, &sg, &cg);
   double nn = nui[0] * nx + nui[1] * ny + nui[2] * nz;
-  double g = cg, f = sg / k, dg = -k * sg * nn, df = cg * nn;
+  // f = sin(k nu_i.r)/k, and its limit nu_i.r at k = 0 (the zero-frequency term)
+  double g = cg, f = k > 0.0 ? sg / k : nr, dg = -k * sg * nn, df = cg * nn;
   o.al = {g * o.dG.re - dg * o.G.re, g * o.dG.im - dg * o.G.im};
   o.be = {f * o.dG.re - df * o.G.re, f * o.dG.im - df * o.G.im};
 }

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
   const int rw = warp / WR, wr = warp % WR, sub = wr % ASMF_W, h = wr / ASMF_W;
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
-  const ff kinv = ff_from_double(1.0 / kv[kk]);
+  const bool kzero = !(kv[kk] > 0.0);  // the zero-frequency term: f takes its limit nu_i.r
+  const ff kinv = ff_from_double(kzero ? 0.0 : 1.0 / kv[kk]);
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = ff_from_double(qshape[t]);
   const int64_t i = (int64_t)blockIdx.x * rows + rw;
   const bool valid = i < N;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
         ff cg, sg;
         cis_ff(ff_mul(k, nr), K, cg, sg);
         const ff nn = ff_add(ff_add(ff_mul(nui[0], nx), ff_mul(nui[1], ny)), ff_mul(nui[2], nz));
-        const ff f = ff_mul(sg, kinv), dg = ff_neg(ff_mul(ff_mul(k, sg), nn)), df = ff_mul(cg, nn);
+        const ff f = kzero ? nr : ff_mul(sg, kinv), dg = ff_neg(ff_mul(ff_mul(k, sg), nn)), df = ff_mul(cg, nn);
         // row sums: w J [g dG - dg G], w J [f dG - df G]
         ffx_mac(alr, wj, ff_sub(ff_mul(cg, dGr), ff_mul(dg, Gr)));
         ffx_mac(ali, wj, ff_sub(ff_mul(cg, dGi), ff_mul(dg, Gi)));

@@ -253,6 +253,10 @@ __host__ __device__ __forceinline__ ff ff_from_double(double x) {
 }
 __host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// 1/k for the FP32 kernels' f = sin(k nu.r)/k; 0 at k = 0, where f takes its limit nu.r (the
+// zero-frequency term): every FP32 kernel forms f = kinv != 0 ? sin(k nu.r) kinv : nu.r.
+__host__ __device__ __forceinline__ float kinv32(double k) { return k > 0.0 ? (float)(1.0 / k) : 0.f; }
+
 // cos and sin of v = vh + vl, |v| <= pi (plus rounding), to about FP32 rounding: quadrant
 // reduction q = rint(v 2/pi) with pi/2 split in two floats (Cody-Waite), then the Taylor series
 // of sin (through v^9) and cos (through v^10) on |v'| <= pi/4, whose truncation errors are below

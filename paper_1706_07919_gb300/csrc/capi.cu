@@ -91,7 +91,8 @@ int upload_geometry_tables(bie_ctx* c);
 int build_colouring(bie_ctx* c);
 int host_geometry_checks(bie_ctx* c, bool make_normals);
 void build_quad_rule(QuadRule& r, int ng, int ng_near);
-int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot);
+int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot,
+                       unsigned long long* first_inside);
 int assemble64(bie_ctx* c, const double* kv, int nk, cd* A, cd* b, void* scratch, bool ff_bulk);
 int lu_factor64(bie_ctx* c, cd* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info);
 int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstride, const int32_t* piv, cd* b,
@@ -151,12 +152,16 @@ static int check_ctx(bie_ctx* c, bool need_geom) {
   return BIE_OK;
 }
 
-static int check_k(const double* k, int64_t Nk) {
+// k = 0 is the zero-frequency term of Eq. (inverseFourier), solved by the k -> 0 limit of the same
+// kernels (f -> nu.r); positive k below 1e-30 would overflow 1/k in FP32 and are rejected.
+static int check_k(const double* k, int64_t Nk, bool allow_zero = true) {
   if (Nk < 0) return fail(BIE_ERR_INVALID_ARG, "Nk < 0");
   if (Nk > 0 && !k) return fail(BIE_ERR_INVALID_ARG, "NULL k");
-  for (int64_t i = 0; i < Nk; ++i)
-    if (!(k[i] > 0.0) || !std::isfinite(k[i]))
-      return fail(BIE_ERR_INVALID_ARG, "k[" + std::to_string(i) + "] must be finite and > 0");
+  for (int64_t i = 0; i < Nk; ++i) {
+    if (!std::isfinite(k[i]) || k[i] < 0.0 || (k[i] > 0.0 && k[i] < 1e-30) || (!allow_zero && k[i] == 0.0))
+      return fail(BIE_ERR_INVALID_ARG, "k[" + std::to_string(i) + "] must be finite and " +
+                                           (allow_zero ? "either 0 or >= 1e-30" : ">= 1e-30"));
+  }
   return BIE_OK;
 }
 
@@ -394,7 +399,7 @@ int bie_assemble(bie_ctx* c, double k, void* A_out, void* b_out) {
 
 int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, void* surf_out, bie_report* rep) {
   BIE_TRY(check_ctx(c, true));
-  BIE_TRY(check_k(k, Nk));
+  BIE_TRY(check_k(k, Nk, mode != BIE_MODE_LEARNED));
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
   if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
@@ -492,13 +497,22 @@ int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, i
   // then spans many waves of resident CTAs, so the last, partial wave costs little
   constexpr int64_t kMaxFieldBatch = 512;
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, kMaxFieldBatch));
-  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + kMaxFieldBatch * sizeof(double) + 4096));
+  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + kMaxFieldBatch * sizeof(double) + 4096 + 256));
   double* foot = (double*)c->work3.p;
   int32_t* foot_elem = (int32_t*)(foot + 8 * M);
   char* after = (char*)(((uintptr_t)(foot_elem + M) + 255) & ~(uintptr_t)255);
+  unsigned long long* first_inside = (unsigned long long*)after;
+  after += 256;
   double* kdev = (double*)after;
   void* scratch = (void*)(after + kMaxFieldBatch * sizeof(double));
-  BIE_TRY(launch_foot_points(c, xobs, M, foot_elem, foot));
+  BIE_CUDA_TRY(cudaMemsetAsync(first_inside, 0xff, sizeof(unsigned long long), c->stream));
+  BIE_TRY(launch_foot_points(c, xobs, M, foot_elem, foot, first_inside));
+  unsigned long long bad = ~0ull;
+  BIE_CUDA_TRY(cudaMemcpyAsync(&bad, first_inside, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (bad != ~0ull)
+    return fail(BIE_ERR_INVALID_ARG, "observation point " + std::to_string(bad) +
+                                         " lies inside a scatterer (Eq. BRIEFdmn needs points in the fluid)");
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));

@@ -99,10 +99,11 @@ __global__ void __launch_bounds__(FT) k_field64(const int32_t* __restrict__ elem
         rn = (rx * nx + ry * ny + rz * nz) * iR * iR * iR;
         cd G0 = {c * iR, s * iR}, dG0 = {(-c - s * kR) * rn, (c * kR - s) * rn};
         // g, f about x0
-        double sa = k * (nu0[0] * rx + nu0[1] * ry + nu0[2] * rz), sg, cg;
+        const double nr = nu0[0] * rx + nu0[1] * ry + nu0[2] * rz;
+        double sa = k * nr, sg, cg;
         sincos(sa, &sg, &cg);
         double nn = nu0[0] * nx + nu0[1] * ny + nu0[2] * nz;
-        double g = cg, f = sg / k, dg = -k * sg * nn, df = cg * nn;
+        double g = cg, f = k > 0.0 ? sg / k : nr, dg = -k * sg * nn, df = cg * nn;  // f -> nu0.r at k = 0
         cd Pt = {sP[u].re - P0.re * g - Pn0.re * f, sP[u].im - P0.im * g - Pn0.im * f};
         cd dPt = {sPn[u].re - P0.re * dg - Pn0.re * df, sPn[u].im - P0.im * dg - Pn0.im * df};
         cd a = cmul(Pt, csub(dGp, dG0)), b = cmul(csub(Gp, G0), dPt);
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
   __shared__ float st[17][FT];
   const int kk = blockIdx.y;
   const ff k = ff_from_double(kv[kk]);
-  const float kinv = (float)(1.0 / kv[kk]);
+  const float kinv = kinv32(kv[kk]);
   const int64_t m = (int64_t)blockIdx.x * FT + threadIdx.x;
   const bool active = m < M;
   ff p[3] = {{0, 0}, {0, 0}, {0, 0}}, x0[3] = {{0, 0}, {0, 0}, {0, 0}}, nu0[3] = {{0, 0}, {0, 0}, {1, 0}};
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
         const float nx = st[6][u], ny = st[7][u], nz = st[8][u], wj = st[9][u];
         const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
         const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
-        float cp, sp, c0, s0, cg, sg, Rp, R0, rnp, rn0;
+        float cp, sp, c0, s0, cg, sg, Rp, R0, rnp, rn0, nrh;
         if (ACC) {
           const ff nux = {nx, st[10][u]}, nuy = {ny, st[11][u]}, nuz = {nz, st[12][u]};
           rnp = ff_add(ff_add(ff_mul(rpx, nux), ff_mul(rpy, nuy)), ff_mul(rpz, nuz)).hi;
@@ -251,12 +252,14 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
           cis_ff(ff_mul(k, Rpf), tp, cp, sp);
           cis_ff(ff_mul(k, R0f), tp, c0, s0);
           cis_ff(ff_mul(k, nr), tp, cg, sg);
+          nrh = nr.hi;
           Rp = Rpf.hi;
           R0 = R0f.hi;
         } else {
           Rp = sqrtf(rpx.hi * rpx.hi + rpy.hi * rpy.hi + rpz.hi * rpz.hi);
           R0 = sqrtf(r0x.hi * r0x.hi + r0y.hi * r0y.hi + r0z.hi * r0z.hi);
           const float nr = nu0[0].hi * r0x.hi + nu0[1].hi * r0y.hi + nu0[2].hi * r0z.hi;
+          nrh = nr;
           cis_fast(k.hi * Rp, tp, cp, sp);
           cis_fast(k.hi * R0, tp, c0, s0);
           cis_fast(k.hi * nr, tp, cg, sg);
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
         const float dGpr = (-cp - sp * kRp) * rnp, dGpi = (cp * kRp - sp) * rnp;
         const float dG0r = (-c0 - s0 * kR0) * rn0, dG0i = (c0 * kR0 - s0) * rn0;
         const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
-        const float g = cg, f = sg * kinv, dg = -k.hi * sg * nn, df = cg * nn;
+        const float g = cg, f = kinv != 0.f ? sg * kinv : nrh, dg = -k.hi * sg * nn, df = cg * nn;
         const float Ptr = st[13][u] - P0r * g - Q0r * f, Pti = st[14][u] - P0i * g - Q0i * f;
         const float dPr = st[15][u] - P0r * dg - Q0r * df, dPi = st[16][u] - P0i * dg - Q0i * df;
         const float ddr = dGpr - dG0r, ddi = dGpi - dG0i, gdr = Gpr - G0r, gdi = Gpi - G0i;
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
     const ff k = ff_from_double(kv[kbase + tid]);
     sk[tid][0] = k.hi;
     sk[tid][1] = k.lo;
-    sk[tid][2] = (float)(1.0 / kv[kbase + tid]);
+    sk[tid][2] = kinv32(kv[kbase + tid]);
   }
   ff p[3] = {{0, 0}, {0, 0}, {0, 0}}, x0[3] = {{0, 0}, {0, 0}, {0, 0}}, nu0[3] = {{0, 0}, {0, 0}, {1, 0}};
   if (active) {
@@ -419,7 +422,7 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
           const float Gpr = cp * iRp, Gpi = spp * iRp, G0r = c0 * iR0, G0i = s0v * iR0;
           const float dGpr = (-cp - spp * kRp) * rnp, dGpi = (cp * kRp - spp) * rnp;
           const float dG0r = (-c0 - s0v * kR0) * rn0, dG0i = (c0 * kR0 - s0v) * rn0;
-          const float g = cg, f = sgv * kinv, dg = -k.hi * sgv * nn, df = cg * nn;
+          const float g = cg, f = kinv != 0.f ? sgv * kinv : nr.hi, dg = -k.hi * sgv * nn, df = cg * nn;
           const float P0r = s0[j][0][tid], P0i = s0[j][1][tid], Q0r = s0[j][2][tid], Q0i = s0[j][3][tid];
           const float Ptr = sq[j][0][u] - P0r * g - Q0r * f, Pti = sq[j][1][u] - P0i * g - Q0i * f;
           const float dPr = sq[j][2][u] - P0r * dg - Q0r * df, dPi = sq[j][3][u] - P0i * dg - Q0i * df;
@@ -457,8 +460,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   __shared__ float4 sq[KB][UT];  // surface values at the tile's points: P re, im, dP re, im
   __shared__ float4 s0[KB][TP];  // surface values at the foot points, same order
   __shared__ float sacc[KB][4][TP];  // compensated sums: re (s, c), im (s, c)
-  __shared__ float2 sk[KB];  // k (FP32 head), 1 / k
-  __shared__ float sklo[KB];  // k - head
+  __shared__ float4 sk[KB];  // k (FP32 head), 1 / k (0 at k = 0), 1 at k = 0 else 0, k - head
   const int kbase = blockIdx.y * KB;
   const int nkb = min(KB, nk - kbase);
   const int tid = threadIdx.x;
@@ -466,8 +468,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   const bool active = m < M;
   if (tid < nkb) {
     const ff k = ff_from_double(kv[kbase + tid]);
-    sk[tid] = make_float2(k.hi, (float)(1.0 / kv[kbase + tid]));
-    sklo[tid] = k.lo;
+    sk[tid] = make_float4(k.hi, kinv32(kv[kbase + tid]), kv[kbase + tid] > 0.0 ? 0.f : 1.f, k.lo);
   }
 #pragma unroll
   for (int j = 0; j < KB; ++j)
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
       float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
       if (uniform) {
-        const ff k0 = {sk[0].x, sklo[0]};
+        const ff k0 = {sk[0].x, sk[0].w};
         cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
         cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
         cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
@@ -553,10 +554,10 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
 #pragma unroll
       for (int j = 0; j < KB; ++j) {
         if (j < nkb) {
-          const float2 kj = sk[j];
-          const float khi = kj.x, kinv = kj.y;
+          const float4 kj = sk[j];
+          const float khi = kj.x, kinv = kj.y, kzero = kj.z;
           if (!uniform) {
-            const ff k = {khi, sklo[j]};
+            const ff k = {khi, kj.w};
             cis_ffk(ff_mul(k, Rp), tp, cp, spp);
             cis_ffk(ff_mul(k, R0), tp, c0, s0v);
             cis_ffk(ff_mul(k, nr), tp, cg, sgv);
@@ -579,7 +580,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
           const float gdr = cp - c0, gdi = spp - s0v;
           const float ddr = __fmaf_rn(__fmaf_rn(s0v, kR0, c0), rn0, -(__fmaf_rn(spp, kRp, cp) * rnp));
           const float ddi = __fmaf_rn(__fmaf_rn(cp, kRp, -spp), rnp, -(__fmaf_rn(c0, kR0, -s0v) * rn0));
-          const float g = cg, f = sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
+          // f = sin(k nu0.r)/k, or its limit nu0.r at k = 0 (kinv 0, kzero 1)
+          const float g = cg, f = __fmaf_rn(kzero, nr.hi, sgv * kinv), dg = -khi * sgv * nn, df = cg * nn;
           const float4 p0 = s0[j][tid], pq = sq[j][u];
           const float P0r = p0.x, P0i = p0.y, Q0r = p0.z, Q0i = p0.w;
           const float Ptr = pq.x - P0r * g - Q0r * f, Pti = pq.y - P0i * g - Q0i * f;

@@ -405,7 +405,7 @@ __device__ double newton_project(const double* X, const double* p, double& xi, d
 __global__ void k_foot_points(const double* __restrict__ nodes, int64_t N, const int32_t* __restrict__ elems,
                               const int32_t* __restrict__ n2e_off, const int32_t* __restrict__ n2e,
                               const double* __restrict__ xp, int64_t M, int32_t* __restrict__ foot_elem,
-                              double* __restrict__ foot) {
+                              double* __restrict__ foot, unsigned long long* __restrict__ first_inside) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= M) return;
   double p[3] = {xp[3 * m], xp[3 * m + 1], xp[3 * m + 2]};
@@ -435,12 +435,22 @@ __global__ void k_foot_points(const double* __restrict__ nodes, int64_t N, const
   o[0] = x0[0]; o[1] = x0[1]; o[2] = x0[2];
   o[3] = nu[0]; o[4] = nu[1]; o[5] = nu[2];
   o[6] = bxi; o[7] = beta;
+  // Eq. (BRIEFdmn) holds for x_p in the fluid: a point behind its closest surface point (relative
+  // to the normal, which points into the fluid) lies inside a body; the lowest such index is kept
+  if (first_inside && be >= 0) {
+    const double s = (p[0] - x0[0]) * nu[0] + (p[1] - x0[1]) * nu[1] + (p[2] - x0[2]) * nu[2];
+    const double tol = 1e-9 * (1.0 + fabs(x0[0]) + fabs(x0[1]) + fabs(x0[2]));
+    if (s < -tol) atomicMin(first_inside, (unsigned long long)m);
+  }
 }
 
-int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot) {
+// first_inside (device, optional): receives the lowest index of a point inside a body, and must
+// hold ~0ull beforehand.
+int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot,
+                       unsigned long long* first_inside) {
   if (M == 0) return BIE_OK;
   BIE_LAUNCH(k_foot_points<<<(unsigned)((M + 127) / 128), 128, 0, c->stream>>>(c->nodes, c->N, c->elems, c->n2e_off, c->n2e, xp,
-                                                                     M, foot_elem, foot));
+                                                                     M, foot_elem, foot, first_inside));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

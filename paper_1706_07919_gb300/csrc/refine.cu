@@ -318,7 +318,9 @@ __global__ void k_refine_check(int n, const cd* __restrict__ b, const cd* __rest
     for (int t = 1; t < (int)(blockDim.x >> 5); ++t) {
       rm = fmax(rm, red[0][t]); xm = fmax(xm, red[1][t]); bm = fmax(bm, red[2][t]); am = fmax(am, red[3][t]);
     }
-    const double be = rm / (am * xm + bm);
+    // b = 0 (a sound-hard body at k = 0) is solved exactly by x = 0: backward error 0, not 0/0
+    const double den = am * xm + bm;
+    const double be = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
     st[kk].anorm = am;
     st[kk].bnorm = bm;
     st[kk].berr = be;

@@ -52,3 +52,29 @@ def test_binding_names_match_header(lib):
 def test_version_string_without_gpu(lib):
     from paper_1706_07919_gb300 import binding
     assert "sm_103a" in binding.bie_version()
+
+
+def test_binding_rejects_mismatched_synthesis_buffers_before_launch():
+    """The synthesis writes P*M*Nt values of out_dtype: a short or mistyped output buffer is
+    rejected by the binding before any call into the library (CPU tensors, no GPU needed)."""
+    import numpy as np
+    import torch
+    from paper_1706_07919_gb300 import binding as B
+    Nk, M, P, Nt = 3, 5, 2, 16
+    T = torch.zeros((Nk, M), dtype=torch.complex128)
+    S = torch.zeros((P, Nt // 2 + 1), dtype=torch.complex128)
+    midx = np.arange(1, Nk + 1)
+    for fn in (lambda o, d: B.bie_synthesize(0, T, midx, S, Nt, o, d),
+               lambda o, d: B.bie_synthesize_noalloc(T, midx, S, Nt, o, d)):
+        with pytest.raises(ValueError, match="dtype"):
+            fn(torch.zeros((P, M, Nt), dtype=torch.float32), 0)
+        with pytest.raises(ValueError, match="elements"):
+            fn(torch.zeros((P, M, Nt - 1), dtype=torch.float64), 0)
+        with pytest.raises(ValueError, match="out_dtype"):
+            fn(torch.zeros((P, M, Nt), dtype=torch.float64), 2)
+    with pytest.raises(ValueError, match="Nt/2"):
+        B.bie_synthesize(0, T, midx, torch.zeros((P, Nt // 2), dtype=torch.complex128), Nt,
+                         torch.zeros((P, M, Nt), dtype=torch.float64), 0)
+    with pytest.raises(ValueError, match="T_out"):
+        B.bie_eval_field(0, torch.zeros((M, 3), dtype=torch.float64), np.ones(Nk), None, 0,
+                         torch.zeros((Nk, M - 1), dtype=torch.complex128))

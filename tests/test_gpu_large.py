@@ -1,7 +1,17 @@
-"""The mixed path at the lattice workload's full size (32 sound-soft spheres, N = 20 544): the
-CPU oracle cannot solve a system of this size in a test, so it checks what it can compute one by
-one -- sampled rows of the system, against which the GPU solution's per-row backward error must
-stay within the mixed path's bar, and the field at sampled points from the GPU's surface solution."""
+"""The mixed path at full size against the CPU FP64 oracle.
+
+* Two-sphere benchmark mesh (N = 2884): mixed solves of three wavenumbers -- two seeded, one next
+  to the interior Dirichlet eigenvalue ka = 4.493 of the spheres -- against the oracle's direct
+  solves, relative L2 <= 1e-6 (the mixed path's bar).
+* Lattice (32 sound-soft spheres, N = 20 544): the oracle cannot solve a system of this size in a
+  test, so it checks what it can compute one by one.  (1) Sampled rows of the FP64 assembly --
+  which at this N accumulates rows straight in the output matrix -- against the oracle's rows at
+  1e-12 of max|A|, in FP64 and float-float.  (2) A reference solution of that FP64 system (every
+  wavenumber re-assembled and refined against it with FP64 residuals), whose residual on the
+  oracle's rows is at FP64 level.  (3) The default mixed solution's forward error against that
+  reference, relative L2 <= 1e-6.  (4) The field at sampled points against the oracle's field
+  from the same surface data.
+"""
 import numpy as np
 import pytest
 
@@ -11,18 +21,64 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
+D = [0.0, 0.0, 1.0]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
 
 @pytest.fixture(scope="module")
 def lattice():
     return W.config_lattice_large(Nk=2048, grid=16)
 
 
-def test_large_lattice_rows_and_field(lattice):
+def test_two_sphere_benchmark_mesh_against_oracle():
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+    w = W.config_two_spheres_mixed()
+    m = w.mesh
+    assert m.N == 2884
+    idx = np.sort(np.concatenate([np.random.default_rng(2001).choice(len(w.k), 2, replace=False), [143]]))
+    ks = w.k[idx]  # includes k = 4.5, 0.007 from the zero 4.4934 of j_1
+    s = Solver(0)
+    s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
+    s.set_incident_plane_wave(w.direction)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    s.close()
+    errs = []
+    for i, k in enumerate(ks):
+        P, _ = oracle.solve_frequency(m, k, w.direction)
+        errs.append(rel(surf[i, 0], P))
+    assert max(errs) <= 1e-6, list(zip(ks, errs, [r.flags for r in rep]))
+
+
+def test_large_lattice_assembly_rows_match_oracle(lattice):
+    from paper_1706_07919_gb300 import Solver
+    m = lattice.mesh
+    assert m.N == 20544
+    rows = np.sort(np.random.default_rng(5003).choice(m.N, 6, replace=False))
+    s = Solver(0)
+    s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
+    for k, ff in ((lattice.k[639], 0), (lattice.k[1535], 1)):  # ka = 3.75, 9
+        s.set_option("assemble.bulk_ff", ff)
+        A, b = s.assemble(k)
+        Ag = A[torch.tensor(rows, device=A.device)].cpu().numpy()
+        bg = b.cpu().numpy()[rows]
+        del A, b
+        torch.cuda.empty_cache()
+        Ar, br = oracle.assemble_rows(m, k, D, rows)
+        assert np.abs(Ag - Ar).max() <= 1e-12 * np.abs(Ar).max(), (k, ff)
+        assert np.abs(bg - br).max() <= 1e-12 * np.abs(br).max(), (k, ff)
+    s.close()
+
+
+def test_large_lattice_forward_error_and_field(lattice):
     from paper_1706_07919_gb300 import Solver
     from paper_1706_07919_gb300 import binding as B
     w = lattice
     m = w.mesh
-    assert m.N == 20544
     ks = w.k[[255, 640, 1023]]  # ka = 1.5, 3.75, 6; three: the two-wavenumber assembly's last group is ragged
     s = Solver(0)
     s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
@@ -30,16 +86,23 @@ def test_large_lattice_rows_and_field(lattice):
     pts = w.xobs[np.random.default_rng(5002).choice(w.xobs.shape[0], 4, replace=False)]
     T = s.eval_field(torch.tensor(pts, device="cuda"), ks, surf, B.BIE_MODE_MIXED).cpu().numpy()
     surf = surf.cpu().numpy()
+    # reference: every wavenumber re-assembled (float-float bulk, FP64 near pairs) and refined
+    # against that FP64 system with FP64 residuals
+    s.set_option("mixed.fallback_err_est", 1e-30)
+    ref, rep_ref = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    ref = ref.cpu().numpy()
     s.close()
     rows = np.sort(np.random.default_rng(5001).choice(m.N, 6, replace=False))
     for i, k in enumerate(ks):
         assert rep[i].backward_err <= 1e-10
-        A, b = oracle.assemble_rows(m, k, [0.0, 0.0, 1.0], rows)
-        x = surf[i, 1]  # all nodes soft: the unknown is dP/dnu
-        r = A @ x - b
-        berr = np.abs(r) / (np.abs(A) @ np.abs(x) + np.abs(b))
-        assert berr.max() <= 1e-6, (k, berr)
+        assert rep_ref[i].flags & B.BIE_FLAG_FP64_ASSEMBLY and rep_ref[i].backward_err <= 1e-12
+        A, b = oracle.assemble_rows(m, k, D, rows)
+        for x, bar in ((ref[i, 1], 1e-11), (surf[i, 1], 1e-6)):  # all nodes soft: the unknown is dP/dnu
+            r = A @ x - b
+            berr = np.abs(r) / (np.abs(A) @ np.abs(x) + np.abs(b))
+            assert berr.max() <= bar, (k, berr)
+        assert rel(surf[i, 1], ref[i, 1]) <= 1e-6, (k, rel(surf[i, 1], ref[i, 1]), rep[i].flags)
         # the known boundary values: P = -exp(i k d.x) on every node
         assert np.allclose(surf[i, 0], -np.exp(1j * k * m.nodes[:, 2]), rtol=0, atol=1e-12)
         Tr = oracle.field(m, k, surf[i, 0], surf[i, 1], pts)
-        assert np.linalg.norm(T[i] - Tr) / np.linalg.norm(Tr) <= 1e-6
+        assert rel(T[i], Tr) <= 1e-6
