@@ -113,6 +113,29 @@ typedef struct {
   int32_t lu_block;    /* columns over which the deferred update runs ("mixed.lu_block") */
 } bie_tune_result;
 
+/* Device time of the phases of the last BIE_MODE_MIXED call (bie_get_phase_times), recorded
+ * with CUDA events on the context's stream when the option "mixed.phase_timing" is 1. */
+typedef struct {
+  double assembly_ms;    /* FP32 assembly of every batch (with the copy of A into the factor) */
+  double factor_ms;      /* blocked LU of every batch: panels and tensor-core trailing updates */
+  double refine_ms;      /* diagonal-block inverses, refinement and sensitivity estimates */
+  double reassembly_ms;  /* re-assembly and refinement of flagged wavenumbers */
+  int32_t batches;       /* batches timed */
+  int32_t systems;       /* wavenumbers factored */
+  int32_t reassembled;   /* wavenumbers re-assembled */
+  int32_t reserved;
+} bie_phase_times;
+
+/* Rates of the pipes that bound the library's kernels, measured by bie_measure_peaks. */
+typedef struct {
+  double ffma_tflops;  /* FP32 fused multiply-add (2 flops each), all SMs */
+  double dfma_tflops;  /* FP64 fused multiply-add */
+  double tf32_tflops;  /* tcgen05.mma kind::tf32, M = 128, N = 256, dense, 0 if not sm_100-family */
+  double bf16_tflops;  /* tcgen05.mma kind::f16 with BF16 operands, same shape */
+  int32_t sm_count;
+  int32_t reserved;
+} bie_peaks;
+
 /* Statistics of bie_sched_run. */
 typedef struct {
   int32_t jobs, workers;
@@ -187,6 +210,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "assemble.bulk_ff"     bie_assemble's bulk pairs in float-float (1) or FP64 (0, default)
  *   "mixed.graph"          1: replay the device work of full batches from a captured CUDA graph
  *                          (default), 0: launch every kernel directly
+ *   "mixed.phase_timing"   1: time the phases of each call with CUDA events (see
+ *                          bie_get_phase_times; graphs are then not used), 0: off (default)
  * Learned warm start and Krylov solve (BIE_MODE_LEARNED):
  *   "learned.stride"       every stride-th wavenumber of the call is an anchor (>= 2, default 8;
  *                          indices stride-1, 2 stride-1, ...; the last index if none)
@@ -270,6 +295,20 @@ int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk,
  * calls whose work overlaps on the GPU (different streams or threads) race. */
 int bie_synthesize_noalloc(const void* T, const int64_t* midx, int64_t Nk, int64_t M, const void* S,
                            int64_t P, int64_t Nt, void* out, int out_dtype, void* stream);
+
+/* Device time of each phase of the last BIE_MODE_MIXED call, recorded when the option
+ * "mixed.phase_timing" was 1 (the call then launches every kernel directly instead of replaying
+ * captured graphs).  out host.  Not part of the paper's method: a measurement aid for the
+ * rooflines of the factorisation and assembly. */
+int bie_get_phase_times(bie_ctx* ctx, bie_phase_times* out);
+
+/* Micro-benchmarks of the pipes that bound the library's kernels on device `cuda_device`: FP32
+ * and FP64 FMA throughput (CUDA cores) and dense tcgen05 tensor-core throughput for TF32 and BF16
+ * operands (M = 128, N = 256 MMAs issued back to back from shared memory, one CTA per SM).  Each
+ * rate is the best of five timed launches (CUDA events), a few milliseconds each; the call
+ * allocates 256 bytes and synchronises.  Not part of the paper's method: the denominators of the
+ * roofline fractions.  Errors: INVALID_ARG (device), CUDA, TIMEOUT (a bounded wait gave up). */
+int bie_measure_peaks(int cuda_device, bie_peaks* out);
 
 /* Autotuner of the mixed path (not part of the paper's method, which fixes no launch parameters):
  * for the context's geometry, times one batch of BIE_MODE_MIXED solves (sample wavenumbers

@@ -38,7 +38,7 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc", "bie_mlp_set_params",
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
             "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
-            "bie_sched_destroy", "bie_sched_add", "bie_sched_run"]
+            "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks"]
 
 
 class BieReport(ctypes.Structure):
@@ -58,6 +58,17 @@ class BieLearnedInfo(ctypes.Structure):
 class BieTuneResult(ctypes.Structure):
     _fields_ = [("n_bucket", ctypes.c_int32), ("batch", ctypes.c_int32), ("tcgen05", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("us_per_k", ctypes.c_double), ("lu_block", ctypes.c_int32)]
+
+
+class BiePhaseTimes(ctypes.Structure):
+    _fields_ = [("assembly_ms", ctypes.c_double), ("factor_ms", ctypes.c_double), ("refine_ms", ctypes.c_double),
+                ("reassembly_ms", ctypes.c_double), ("batches", ctypes.c_int32), ("systems", ctypes.c_int32),
+                ("reassembled", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class BiePeaks(ctypes.Structure):
+    _fields_ = [("ffma_tflops", ctypes.c_double), ("dfma_tflops", ctypes.c_double), ("tf32_tflops", ctypes.c_double),
+                ("bf16_tflops", ctypes.c_double), ("sm_count", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BieSchedStats(ctypes.Structure):
@@ -114,6 +125,8 @@ def load(path: str | None = None):
         "bie_sched_destroy": ([vp], i32),
         "bie_sched_add": ([vp, vp, i64, vp, i64, vp, vp, vp, vp, i64, i32, vp, vp, vp], i32),
         "bie_sched_run": ([vp, vp], i32),
+        "bie_get_phase_times": ([vp, vp], i32),
+        "bie_measure_peaks": ([i32, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -302,6 +315,18 @@ def bie_get_learned_info(ctx: int) -> dict:
     info = BieLearnedInfo()
     _check(load().bie_get_learned_info(ctx, ctypes.byref(info)))
     return {name: getattr(info, name) for name, _ in BieLearnedInfo._fields_}
+
+
+def bie_get_phase_times(ctx: int) -> dict:
+    pt = BiePhaseTimes()
+    _check(load().bie_get_phase_times(ctx, ctypes.byref(pt)))
+    return {name: getattr(pt, name) for name, _ in BiePhaseTimes._fields_ if name != "reserved"}
+
+
+def bie_measure_peaks(device: int = 0) -> dict:
+    pk = BiePeaks()
+    _check(load().bie_measure_peaks(device, ctypes.byref(pk)))
+    return {name: getattr(pk, name) for name, _ in BiePeaks._fields_ if name != "reserved"}
 
 
 # ---- autotuner and scheduler ------------------------------------------------------------------

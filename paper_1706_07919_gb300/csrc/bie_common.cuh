@@ -138,6 +138,8 @@ struct bie_ctx {
                                      // general kernel (also taken when an element mixes conditions)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
+  int phase_timing = 0;              // time the mixed path's phases with CUDA events (no graphs)
+  bie_phase_times phase{};           // phases of the last BIE_MODE_MIXED call (phase_timing 1)
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
   cudaStream_t cap_stream = nullptr; // private stream on which CUDA graphs are captured
   size_t pinned_bytes = 0;

@@ -299,6 +299,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     c->reassembly_ff = (int)value;
   } else if (n == "mixed.graph") {
     c->mixed_graph = value != 0.0 ? 1 : 0;
+  } else if (n == "mixed.phase_timing") {
+    c->phase_timing = value != 0.0 ? 1 : 0;
   } else if (n == "learned.stride") {
     if (value < 2 || value > 1e6) return fail(BIE_ERR_INVALID_ARG, "learned.stride must be in [2, 1e6]");
     c->learned_stride = (int)value;
@@ -472,6 +474,13 @@ int bie_autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path
   BIE_TRY(check_ctx(c, true));
   BIE_TRY(check_k(k, nk));
   return autotune(c, k, nk, cache_path, out);
+}
+
+int bie_get_phase_times(bie_ctx* c, bie_phase_times* out) {
+  BIE_TRY(check_ctx(c, false));
+  if (!out) return fail(BIE_ERR_INVALID_ARG, "NULL out");
+  *out = c->phase;
+  return BIE_OK;
 }
 
 int bie_get_learned_info(bie_ctx* c, bie_learned_info* out) {

@@ -98,20 +98,45 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   // The device part of a batch (assembly, factorisation, refinement) is stream-ordered and needs
   // no host decision, so full batches after the first are captured once in a CUDA graph and
   // replayed; the wavenumbers reach the graph through a pinned host buffer.
+  // Phase timing (option "mixed.phase_timing"): events around assembly, factorisation, refinement
+  // and the re-assembly of flagged wavenumbers, read after each batch; graphs are then not used.
+  const bool timing = c->phase_timing != 0;
+  cudaEvent_t ev[6] = {};
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() { for (int i = 0; i < 6; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+  } evguard{ev};
+  if (timing) {
+    c->phase = bie_phase_times{};
+    for (int i = 0; i < 6; ++i) BIE_CUDA_TRY(cudaEventCreate(&ev[i]));
+  }
+  auto mark = [&](int i) -> int {
+    if (timing) BIE_CUDA_TRY(cudaEventRecord(ev[i], c->stream));
+    return BIE_OK;
+  };
   auto batch_core = [&](const double* ksrc, int nk) -> int {
+    BIE_TRY(mark(0));
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, ksrc, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
     BIE_TRY(assemble32(c, kdev, nk, A, ld, b, known, rowsum, LU));  // LU is free until the copy below
     BIE_CUDA_TRY(cudaMemcpyAsync(LU, A, (size_t)nk * mat, cudaMemcpyDeviceToDevice, c->stream));
+    BIE_TRY(mark(1));
     if (c->tc_version > 0)
       BIE_TRY(lu_factor_tc(c, LU, nk, (int)N, (int)ld, bstride, piv, info, tcs, tc_scratch));
     else
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
+    BIE_TRY(mark(2));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
                          c->refine_tol, Dinv));
+    BIE_TRY(mark(3));
     return BIE_OK;
   };
-  bool use_graph = c->mixed_graph && Nk >= 2 * kb;
+  auto elapsed = [&](int a, int b2) -> double {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[a], ev[b2]) != cudaSuccess) return 0.0;
+    return (double)ms;
+  };
+  bool use_graph = c->mixed_graph && !timing && Nk >= 2 * kb;
   double* kpin = nullptr;
   if (use_graph) {
     BIE_TRY(ensure_pinned(c, (size_t)kb * sizeof(double)));
@@ -169,6 +194,13 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     }
     BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
     BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (timing) {  // the batch has completed (its state was read)
+      c->phase.assembly_ms += elapsed(0, 1);
+      c->phase.factor_ms += elapsed(1, 2);
+      c->phase.refine_ms += elapsed(2, 3);
+      c->phase.batches += 1;
+      c->phase.systems += nk;
+    }
     std::vector<int32_t> flagged;
     for (int i = 0; i < nk; ++i) {
       const bool conv = done[i] && std::isfinite(berr[i]);
@@ -192,10 +224,16 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
       BIE_CUDA_TRY(cudaMemcpyAsync(kg, kv.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+      BIE_TRY(mark(4));
       BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
       BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
                                  c->refine64_it_max, c->refine64_tol, Dinv));
+      BIE_TRY(mark(5));
       BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
+      if (timing) {
+        c->phase.reassembly_ms += elapsed(4, 5);
+        c->phase.reassembled += ng;
+      }
       for (int g = 0; g < ng; ++g) {
         const int64_t idx = k0 + flagged[f0 + g];
         if (rep) {
