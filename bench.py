@@ -8,9 +8,13 @@ tcgen05 TF32 LU, float-float iterative refinement, FP64 re-solve of flagged wave
 a 128 x 128 grid of the plane z = 0 over [-5, 5]^2, synthesis of 1024 time samples.
 
 Metric: frequency solves per second of the whole path (each solve carries its share of the field
-evaluation and synthesis), with space-time points per second and the per-phase times alongside;
-accuracy of the solves against the FP64 GPU path on sampled wavenumbers (the FP64 path itself is
-parity-tested against the CPU oracle).
+evaluation and synthesis), with space-time points per second and the per-phase times alongside.
+Accuracy gate (after the timed steps): every one of the 512 surface solutions is compared with a
+solution of the FP64-accurate system (each wavenumber re-assembled with float-float bulk pairs and
+FP64 near pairs, refined with FP64 residuals to a backward error of 1e-13), one wavenumber with the
+CPU oracle's direct solve, and a few with the plain FP64 GPU path; a solve whose relative L2 error
+exceeds 1e-6 is not counted in `value`.  Rooflines divide by rates measured in the same run
+(bie_measure_peaks: FP32 FMA for the field kernel, tcgen05 TF32 for the LU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -30,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BEM freq solves/s & space-time pts/s at rel err <=1e-6 vs FP64; roofline frac"
 UNIT = "freq_solves/s"
+TOL = 1e-6  # relative L2 error of a counted solve against the FP64-accurate system
 
 
 def _peaks():
@@ -90,6 +95,15 @@ class ClockSampler:
 def build_workload():
     from workloads import config_two_spheres_mixed
     return config_two_spheres_mixed()
+
+
+def bench_config(w, args, world: int) -> dict:
+    """The workload description, identical in both arms."""
+    return {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "E": int(w.mesh.E),
+            "Nk": len(w.k), "ka_max": float(w.k[-1]), "M": int(w.xobs.shape[0]), "Nt": w.Nt,
+            "pulses": int(w.pulses.shape[0]), "parallelism": f"{world} independent replica(s), one per GPU",
+            "l2": "working set (128 x 133 MB systems per batch) larger than L2; no flush needed",
+            "mixed_batch": args.batch}
 
 
 class RankGroup:
@@ -155,6 +169,7 @@ def run_ours(args):
 
     w = build_workload()
     Nk, M, Nt, P = len(w.k), w.xobs.shape[0], w.Nt, w.pulses.shape[0]
+    peaks = B.bie_measure_peaks(local)  # pipe rates of this GPU (roofline denominators)
     stream = torch.cuda.Stream(dev)
     sol = Solver(local, stream)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
@@ -213,7 +228,22 @@ def run_ours(args):
     launches = B.bie_kernel_launches() - launches0
     rep = reports["rep"]
 
-    # ---- accuracy on sampled wavenumbers against the FP64 GPU path (outside the timed region) ----
+    # ---- accuracy gate (outside the timed region) ----
+    # (1) every wavenumber against the solution of the FP64-accurate system: re-assembly with
+    #     float-float bulk pairs and FP64 near pairs, refinement with FP64 residuals to 1e-13
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sol.set_option("mixed.fallback_err_est", 1e-30)
+    g0.record(stream)
+    ref, rep_ref = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    sol.set_option("mixed.fallback_err_est", 2.5e-7)
+    err_all = (torch.linalg.norm((surf - ref).reshape(Nk, -1), dim=1) /
+               torch.linalg.norm(ref.reshape(Nk, -1), dim=1)).cpu().numpy()
+    ref_berr = max(r.backward_err for r in rep_ref)
+    del ref
+    n_over = int((err_all > TOL).sum())
+    # (2) the plain FP64 GPU path (FP64 assembly and LU) on sampled wavenumbers
     rng = np.random.Generator(np.random.PCG64(2001))
     sample = np.sort(rng.choice(Nk, size=args.check, replace=False))
     ks = w.k[sample]
@@ -226,15 +256,34 @@ def run_ours(args):
     errs = [(torch.linalg.norm(surf[i] - s64[j]) / torch.linalg.norm(s64[j])).item() for j, i in enumerate(sample)]
     T64 = sol.eval_field(xo, ks, s64, B.BIE_MODE_FP64)
     ferrs = [(torch.linalg.norm(T[i] - T64[j]) / torch.linalg.norm(T64[j])).item() for j, i in enumerate(sample)]
+    del s64, T64
+
+    # ---- phases of one more (untimed) sweep, for the LU's own roofline ----
+    sol.set_option("mixed.phase_timing", 1)
+    sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    phases = B.bie_get_phase_times(sol.ctx)
+    sol.set_option("mixed.phase_timing", 0)
+    roof_lu = roofline_lu(w, phases, peaks)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
     e2e = run_e2e(args, w, sol, B, dev, stream)
     solve_rate = Nk * args.steps / (phase[0] / 1e3)
 
     # ---- roofline of the dominant kernel: the field phase of the timed steps ----
-    roof = roofline_field(w, phase[1] / args.steps, M, Nk, args.field_variant)
+    roof = roofline_field(w, phase[1] / args.steps, M, Nk, args.field_variant, peaks)
 
-    value = job_throughput(Nk, world, args.steps, t_ms)
+    # ---- the CPU oracle on a bounded sample; its surface solution also checks the GPU's ----
+    cpu = None
+    if grp.is_root and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, w)
+        kk = cpu.pop("k_index")
+        Por = cpu.pop("P")
+        cpu_err = float(np.linalg.norm(surf[kk, 0].cpu().numpy() - Por) / np.linalg.norm(Por))
+    else:
+        cpu_err = None
+
+    n_pass = Nk - n_over
+    value = job_throughput(n_pass, world, args.steps, t_ms)
     pts = job_throughput(M * Nt * P, world, args.steps, t_ms)
     nfall = sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64)
     nre64 = sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY)
@@ -243,22 +292,29 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded meshes/points/pulse)",
-        "config": {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "E": int(w.mesh.E),
-                   "Nk": Nk, "ka_max": float(w.k[-1]), "M": M, "Nt": Nt, "pulses": P,
-                   "parallelism": f"{world} independent replica(s), one per GPU",
-                   "l2": "working set (64 x 133 MB systems per batch) larger than L2; no flush needed",
-                   "mixed_batch": args.batch},
+        "config": bench_config(w, args, world),
         "space_time_pts_per_s": pts,
         "phase_ms_per_step": {"solve": phase[0] / args.steps, "field": phase[1] / args.steps,
                               "spectrum_synthesis": phase[2] / args.steps},
-        "accuracy": {"sampled_k": [float(x) for x in ks], "max_rel_err_surface_vs_fp64": max(errs),
-                     "max_rel_err_field_vs_fp64": max(ferrs), "fp64_reassembled": nre64, "fp64_full_solves": nfall,
-                     "max_refine_iters": max(r.iters for r in rep)},
+        "accuracy": {"tolerance": TOL, "solves_counted": n_pass, "solves_over_tolerance": n_over,
+                     "max_rel_err_vs_fp64_system_all_k": float(err_all.max()),
+                     "median_rel_err_vs_fp64_system": float(np.median(err_all)),
+                     "fp64_system_reference": "all 512 wavenumbers re-assembled (float-float bulk, FP64 near "
+                                              "pairs) and refined with FP64 residuals",
+                     "fp64_system_max_backward_err": ref_berr,
+                     "fp64_system_ms": g0.elapsed_time(g1),
+                     "max_rel_err_vs_oracle": cpu_err,
+                     "oracle_k": float(w.k[kk]) if cpu is not None else None,
+                     "sampled_k": [float(x) for x in ks], "max_rel_err_surface_vs_fp64_path": max(errs),
+                     "max_rel_err_field_vs_fp64_path": max(ferrs), "fp64_reassembled": nre64,
+                     "fp64_full_solves": nfall, "max_refine_iters": max(r.iters for r in rep)},
         "fp64_path": {"solves_per_s": fp64_solves_per_s, "sample": f"{len(ks)} wavenumbers, same N",
                       "mixed_solve_phase_speedup": solve_rate / fp64_solves_per_s},
         "clocks": clk.summary(),
         "e2e": e2e,
         "roofline": roof,
+        "roofline_lu": roof_lu,
+        "peaks_measured": peaks,
         "gpu_launches": int(launches),
     }
     sol.close()
@@ -269,7 +325,7 @@ def run_ours(args):
     if not args.no_large:
         line["large"] = run_large(args, dev, stream)
     if grp.is_root:
-        line["cpu_baseline"] = cpu_baseline(args, w) if world == 1 and not args.no_cpu else None
+        line["cpu_baseline"] = cpu
         print(json.dumps(line))
     grp.close()
 
@@ -338,9 +394,11 @@ def run_learned(args, dev, stream):
 
 def run_large(args, dev, stream):
     """The lattice workload (4 x 4 x 2 sound-soft spheres, N = 20 544) on a bounded sample: one
-    batch of `--large-nk` wavenumbers spread over (0, 24] solved in mixed precision, their field on
-    the full 256 x 256 plane and the synthesis of the eight pulses at 4096 samples (the full
-    workload has 2048 wavenumbers).  CUDA events on the library's stream around each phase."""
+    batch of the zero-frequency term k = 0 (soft bodies scatter at k = 0, and the Gaussian pulse
+    has a non-zero mean) plus `--large-nk` wavenumbers spread over (0, 24], solved in mixed
+    precision, their field on the full 256 x 256 plane and the synthesis of the eight pulses at
+    4096 samples (the full workload has 2048 wavenumbers).  CUDA events on the library's stream
+    around each phase."""
     import torch
 
     from workloads import config_lattice_large
@@ -350,8 +408,8 @@ def run_large(args, dev, stream):
     w = config_lattice_large()
     nk = args.large_nk
     idx = np.linspace(0, len(w.k) - 1, nk).round().astype(np.int64)
-    ks = w.k[idx]
-    midx = idx + 1  # frequency index m of each wavenumber (k_m = m dk)
+    ks = np.concatenate([[0.0], w.k[idx]])
+    midx = np.concatenate([[0], idx + 1])  # frequency index m of each wavenumber (k_m = m dk), m = 0 first
     M, Nt, P = w.xobs.shape[0], w.Nt, w.pulses.shape[0]
     sol = Solver(dev.index if dev.index is not None else 0, stream)
     sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
@@ -372,9 +430,9 @@ def run_large(args, dev, stream):
     torch.cuda.synchronize(dev)
     t_solve, t_field, t_syn = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
     sol.close()
-    return {"workload": "lattice_4x4x2_soft_N20544", "N": int(w.mesh.N), "wavenumbers": nk,
-            "k": [float(x) for x in ks], "solves_per_s": nk / (t_solve / 1e3),
-            "field_evals_per_s": M * w.mesh.E * 16 * nk / (t_field / 1e3), "points": M, "pulses": P, "Nt": Nt,
+    return {"workload": "lattice_4x4x2_soft_N20544", "N": int(w.mesh.N), "wavenumbers": len(ks),
+            "k": [float(x) for x in ks], "solves_per_s": len(ks) / (t_solve / 1e3),
+            "field_evals_per_s": M * w.mesh.E * 16 * len(ks) / (t_field / 1e3), "points": M, "pulses": P, "Nt": Nt,
             "phase_ms": {"solve": t_solve, "field": t_field, "spectrum_synthesis": t_syn},
             "fp64_reassembled": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
             "max_backward_err": max(r.backward_err for r in rep)}
@@ -455,16 +513,17 @@ def run_e2e(args, w, sol, B, dev, stream):
             "d2h_bytes_per_step": int(hsurf.numel() * 16 + hout.numel() * 4)}
 
 
-def roofline_field(w, field_ms, M, Nk, variant):
+def roofline_field(w, field_ms, M, Nk, variant, peaks):
     """The dominant kernel of the step is the field evaluation (Eq. BRIEFdmn), FP32-ALU-bound:
     algorithmic flops per (point, quadrature point, k) x evaluations / the field phase's device time
     in the timed steps (CUDA events on the library's stream; the phase also holds the foot-point
-    projection and the interpolation to quadrature points, about 1 % of it)."""
+    projection and the interpolation to quadrature points, about 1 % of it), against the FP32 FMA
+    rate measured in the same run (bie_measure_peaks)."""
     EQ = w.mesh.E * 16
     evals = M * EQ * Nk
     flops_per_eval = FIELD_FLOPS_PER_EVAL
     achieved = flops_per_eval * evals / (field_ms * 1e-3) / 1e12
-    peak = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 FFMA, 152 SMs x 128 lanes x 2 flops at 2.07 GHz
+    peak = peaks["ffma_tflops"]
     launches = (Nk + FIELD_BATCH - 1) // FIELD_BATCH
     name = {1: "k_field32c<16,64,4,64>", 2: "k_field32c<16,128,3,32>"}.get(variant, "k_field32b")
     return {"kernel": name + " (Eq. BRIEFdmn, float-float phases)", "bound": "alu",
@@ -472,7 +531,28 @@ def roofline_field(w, field_ms, M, Nk, variant):
             "traffic": FIELD_LAUNCH_DRAM_BYTES.get(variant), "traffic_unit": "bytes per launch",
             "evals_per_s": evals / (field_ms * 1e-3), "flops_per_eval": flops_per_eval,
             "launches_per_step": launches, "ms_per_launch": field_ms / launches,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)"}
+            "peak_source": f"measured in this run: FP32 FMA micro-benchmark on {peaks['sm_count']} SMs "
+                           "(bie_measure_peaks)"}
+
+
+def roofline_lu(w, phases, peaks):
+    """The blocked LU of the mixed path (panels, row swaps, U-block solves and tcgen05 trailing
+    updates): useful flops (8/3) N^3 per wavenumber (complex LU) over the factorisation phase's
+    device time in one untimed sweep of the 512 wavenumbers with phase timing on (CUDA events
+    around the factorisation of each batch), against the tcgen05 TF32 rate measured in the same
+    run (bie_measure_peaks)."""
+    N = w.mesh.N
+    flops = phases["systems"] * (8.0 / 3.0) * float(N) ** 3
+    t = phases["factor_ms"] * 1e-3
+    achieved = flops / t / 1e12 if t > 0 else None
+    peak = peaks["tf32_tflops"]
+    return {"kernel": "blocked complex LU (k_leaf, k_swap_trsm, k_trsm64, tc2::k_update_tc2)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved and peak else None, "flops_per_system": (8.0 / 3.0) * float(N) ** 3,
+            "systems": phases["systems"], "factor_ms": phases["factor_ms"],
+            "phase_ms": {k: phases[k] for k in ("assembly_ms", "factor_ms", "refine_ms", "reassembly_ms")},
+            "peak_source": "measured in this run: tcgen05.mma kind::tf32 M128 N256 micro-benchmark "
+                           "(bie_measure_peaks)"}
 
 
 # wavenumbers per field launch of the library (bie_eval_field)
@@ -508,22 +588,28 @@ def cpu_baseline(args, w):
     t_solve = (time.perf_counter() - t) / len(kidx)
     t = time.perf_counter()
     oracle.field(w.mesh, w.k[kidx[0]], P, Pn, pts)
-    t_field = (time.perf_counter() - t) * (w.xobs.shape[0] / len(pts))
+    t_pts = time.perf_counter() - t
+    t_field = t_pts * (w.xobs.shape[0] / len(pts))
     per_k = t_solve + t_field
     return {"value": 1.0 / per_k, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(kidx)} wavenumber solve(s) (assembly+LU+solve, N={w.mesh.N}) and the field at "
-                      f"{len(pts)} of {w.xobs.shape[0]} points scaled to all points; synthesis not counted",
-            "seconds_per_frequency": per_k}
+                      f"{len(pts)} of {w.xobs.shape[0]} points; value = 1 / (solve time + field time scaled "
+                      "to all points); synthesis not counted",
+            "seconds_per_frequency": per_k, "sample_wall_s": t_solve * len(kidx) + t_pts,
+            "k_index": int(kidx[0]), "P": P}
 
 
 # ------------------------------------------------------------------------- reference arm ----
 def run_reference(args):
-    """The oracle as the reference arm, timed on the host cores on bounded samples."""
+    """The oracle as the reference arm, timed on the host cores: each step is one bounded sample
+    (one frequency solve at N = 2884 plus the field at --cpu-points of the 16 384 points, the same
+    sample as the GPU arm's cpu_baseline leg); `ms_per_step` is the measured wall time per sample,
+    `value` extrapolates each sample to whole frequency solves (field at every point)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = build_workload()
-    args.cpu_points = max(8, args.cpu_points // 2)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     vals = []
     for _ in range(args.warmup):      # warm-up samples (page-in, thread pool start), untimed
         cpu_baseline(args, w)
@@ -534,15 +620,16 @@ def run_reference(args):
         vals.append(cb["value"])
     dt = time.perf_counter() - t
     value = float(np.mean(vals))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded meshes/points/pulse)", "impl": "reference",
-            "config": {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "Nk": len(w.k),
-                       "M": int(w.xobs.shape[0]), "Nt": w.Nt},
+            "config": bench_config(w, args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "extrapolation": "ms_per_step is the measured wall time of one sample; value = 1 / (seconds per "
+                             "frequency solve with the field at all points), from each sample's timings",
             "wall_s": dt}
     print(json.dumps(line))
 
@@ -644,9 +731,18 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step", "peaks"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.case == "peaks":  # the pipe micro-benchmarks alone, as one JSON line
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_1706_07919_gb300 import binding as B
+        pk = B.bie_measure_peaks(0)
+        pk["gpu"] = torch.cuda.get_device_name(0)
+        print(json.dumps(pk))
+        return
     if args.case:
         run_case(args)
         return
