@@ -278,6 +278,16 @@ int bie_pulse_spectrum(bie_ctx* ctx, const double* s, int64_t P, int64_t Nt, voi
 int bie_synthesize(bie_ctx* ctx, const void* T, const int64_t* midx, int64_t Nk, int64_t M,
                    const void* S, int64_t P, int64_t Nt, void* out, int out_dtype);
 
+/* Dominant frequencies of the incident pulses (Sec. 4, Table I, and Sec. 5: accurate space-time
+ * fields follow from the few wavenumbers at which the incident spectrum is largest, so only those
+ * need a frequency solve).  Ranks m = 0 .. Nt/2 by max over the pulses of |S[p][m]| (ties: the
+ * lower m first) and returns the K largest in ascending order, ready as bie_synthesize's midx
+ * (the wavenumbers to solve are k_m = 2 pi m / (c T) for the window length T).
+ *   S device c128 [P][Nt/2+1] as written by bie_pulse_spectrum; midx_out host i64 [K].
+ * Synchronises.  Errors: INVALID_ARG (P < 1, Nt not a power of two in [2, 4096], K outside
+ * [0, Nt/2 + 1], NULL pointer). */
+int bie_top_frequencies(bie_ctx* ctx, const void* S, int64_t P, int64_t Nt, int64_t K, int64_t* midx_out);
+
 /* Allocation-free variant of bie_synthesize.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run -- a host framework that
  * hands out a fixed device-memory budget through its own pool, or a latency-bound pipeline in

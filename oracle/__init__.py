@@ -14,6 +14,7 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   foot_points                             pinned: sphere closest point is radial projection
   field                                   pinned: interior point source, conventional representation
   dft / synthesize                        pinned: numpy FFT, Gaussian closed form, Parseval
+  top_frequencies                         pinned: numpy lexsort with ties; Table I of the paper
   full solve                              pinned: analytic rigid/soft sphere partial-wave series;
                                           k = 0: soft sphere -a/r, harmonic linear identity, limit k -> 0
   mlp_features                            pinned: closed-form values at chosen nodes
@@ -69,6 +70,7 @@ def _load():
             "or_field": [c_dp, i64, c_ip, i64, dbl, i32, c_dp, c_dp, c_dp, i64, c_ip, c_dp, c_dp, c_dp],
             "or_dft": [i64, c_dp, c_dp],
             "or_synthesize": [i64, i64, c_dp, c_ip, i64, i64, c_dp, c_dp],
+            "or_top_frequencies": [i64, i64, c_dp, i64, c_ip],
             "or_assemble_rows": [c_dp, i64, c_ip, i64, c_dp, c_ip, dbl, c_dp, i32, i32, c_dp, i64, c_dp, c_dp],
             "or_mlp_features": [c_dp, c_dp, i64, c_dp, i64, c_dp, c_dp, dbl, dbl, c_dp],
             "or_mlp_forward": [c_dp, c_dp, i64, c_dp],
@@ -252,6 +254,15 @@ def synthesize(T: np.ndarray, midx: np.ndarray, S: np.ndarray, Nt: int) -> np.nd
     P = S.shape[0]
     out = np.zeros((P, M, Nt))
     _check(_load().or_synthesize(Nk, M, _p(T), _p(midx), P, Nt, _p(S), _p(out)), "synthesize")
+    return out
+
+
+def top_frequencies(S: np.ndarray, K: int) -> np.ndarray:
+    """The K frequency indices m (0 <= m <= Nt/2) of largest max over pulses |S[p][m]| (Sec. 4,
+    Table I), ties to the lower m, ascending.  S [P][Nt] full spectra (as dft returns them)."""
+    S = np.ascontiguousarray(np.atleast_2d(S), np.complex128)
+    out = np.zeros(int(K), np.int64)
+    _check(_load().or_top_frequencies(S.shape[0], S.shape[1], _p(S), int(K), _p(out)), "top_frequencies")
     return out
 
 

@@ -592,3 +592,35 @@ int or_synthesize(int64_t Nk, int64_t M, const cplx* T, const int64_t* midx, int
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Dominant frequencies (Sec. 4, Table I): the K indices m (0 <= m <= Nt/2) with the largest
+ * amplitude max_p |S[p][m]| of the incident spectra, ties to the lower m, returned ascending.
+ * Plain repeated selection of the largest remaining amplitude.
+ * ------------------------------------------------------------------------------------------ */
+int or_top_frequencies(int64_t P, int64_t Nt, const cplx* S, int64_t K, int64_t* midx) {
+  const int64_t nm = Nt / 2 + 1;
+  if (P < 1 || Nt < 2 || K < 0 || K > nm) return -1;
+  double* amp = (double*)malloc(sizeof(double) * nm);
+  char* taken = (char*)calloc(nm, 1);
+  if (!amp || !taken) { free(amp); free(taken); return -3; }
+  for (int64_t m = 0; m < nm; ++m) {
+    amp[m] = 0.0;
+    for (int64_t p = 0; p < P; ++p) {
+      double a = cabs(S[p * Nt + m]);
+      if (a > amp[m]) amp[m] = a;
+    }
+  }
+  for (int64_t r = 0; r < K; ++r) {
+    int64_t best = -1;
+    for (int64_t m = 0; m < nm; ++m)
+      if (!taken[m] && (best < 0 || amp[m] > amp[best])) best = m;
+    taken[best] = 1;
+  }
+  int64_t c = 0;
+  for (int64_t m = 0; m < nm; ++m)
+    if (taken[m]) midx[c++] = m;
+  free(amp);
+  free(taken);
+  return 0;
+}

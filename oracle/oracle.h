@@ -104,6 +104,11 @@ int or_dft(int64_t Nt, const double* s, double _Complex* S);
 int or_synthesize(int64_t Nk, int64_t M, const double _Complex* T, const int64_t* midx,
                   int64_t P, int64_t Nt, const double _Complex* S, double* p);
 
+/* Dominant frequencies (Sec. 4, Table I): the K indices m in [0, Nt/2] of largest
+ * max_p |S[p][m]| (S [P][Nt], full spectra as or_dft writes them), ties to the lower m,
+ * written ascending to midx [K]. */
+int or_top_frequencies(int64_t P, int64_t Nt, const double _Complex* S, int64_t K, int64_t* midx);
+
 /* ---- learned warm start of the frequency sweep (not part of the paper's method) -------------
  * Feature map, network, loss and optimiser step are defined in full at the top of mlp.c; the
  * parameter vector is W1 (256x64) | b1 | W2 (256x256) | b2 | W3 (256x256) | b3 | W4 (2x256) | b4. */

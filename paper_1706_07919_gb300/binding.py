@@ -38,7 +38,8 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_eval_field", "bie_pulse_spectrum", "bie_synthesize", "bie_synthesize_noalloc", "bie_mlp_set_params",
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
             "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
-            "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks"]
+            "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks",
+            "bie_top_frequencies"]
 
 
 class BieReport(ctypes.Structure):
@@ -127,6 +128,7 @@ def load(path: str | None = None):
         "bie_sched_run": ([vp, vp], i32),
         "bie_get_phase_times": ([vp, vp], i32),
         "bie_measure_peaks": ([i32, vp], i32),
+        "bie_top_frequencies": ([vp, vp, i64, i64, i64, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -256,6 +258,14 @@ def bie_synthesize(ctx: int, T, midx, S, Nt: int, out, out_dtype: int) -> None:
     _synth_shapes(T, midx, S, Nt, out, out_dtype)
     _check(load().bie_synthesize(ctx, _dp(T), _hp(midx), midx.shape[0], T.shape[1], _dp(S), S.shape[0], Nt,
                                  _dp(out), out_dtype))
+
+
+def bie_top_frequencies(ctx: int, S, Nt: int, K: int) -> np.ndarray:
+    if len(S.shape) != 2 or S.shape[1] != Nt // 2 + 1 or _dtype_name(S) != "complex128":
+        raise ValueError(f"S must be complex128 [P][Nt/2+1={Nt // 2 + 1}]")
+    out = np.zeros(max(0, int(K)), np.int64)
+    _check(load().bie_top_frequencies(ctx, _dp(S), S.shape[0], int(Nt), int(K), _hp(out)))
+    return out
 
 
 def bie_synthesize_noalloc(T, midx, S, Nt: int, out, out_dtype: int, stream: int | None = None) -> None:

@@ -102,6 +102,7 @@ int field64(bie_ctx* c, const double* kv, int nk, const cd* surf, const double* 
 int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout);
 int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t M, const cd* Sp, int64_t P, int n,
                void* out, int out_dtype);
+int top_frequencies(bie_ctx* c, const cd* S, int64_t P, int nm, int K, int64_t* midx_dev);
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
                 int32_t* perm_keep, cf* d_keep);
 int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
@@ -564,6 +565,22 @@ int bie_synthesize(bie_ctx* c, const void* T, const int64_t* midx, int64_t Nk, i
   int64_t* md = (int64_t*)c->work3.p;
   if (Nk > 0) BIE_CUDA_TRY(cudaMemcpyAsync(md, midx, Nk * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   BIE_TRY(synthesize(c, (const cd*)T, md, (int)Nk, M, (const cd*)S, P, (int)Nt, out, out_dtype));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+int bie_top_frequencies(bie_ctx* c, const void* S, int64_t P, int64_t Nt, int64_t K, int64_t* midx_out) {
+  BIE_TRY(check_ctx(c, false));
+  if (P < 1 || Nt < 2 || Nt > 4096 || (Nt & (Nt - 1)))
+    return fail(BIE_ERR_INVALID_ARG, "need P >= 1 and Nt a power of two in [2, 4096]");
+  const int64_t nm = Nt / 2 + 1;
+  if (K < 0 || K > nm) return fail(BIE_ERR_INVALID_ARG, "K must be in [0, Nt/2 + 1]");
+  if (K == 0) return BIE_OK;
+  if (!S || !midx_out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
+  BIE_TRY(ensure_buf(c->work3, (size_t)K * sizeof(int64_t)));
+  int64_t* md = (int64_t*)c->work3.p;
+  BIE_TRY(top_frequencies(c, (const cd*)S, P, (int)nm, (int)K, md));
+  BIE_CUDA_TRY(cudaMemcpyAsync(midx_out, md, (size_t)K * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }

@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
 // points and each run is added to a compensated sum kept in shared memory, so only 2 KB partial
 // sums stay in registers; the phase step e^{i dk R} takes its phase from an FMA-split product
 // (no 2 pi reduction in float-float: dk R is small).
-template <int KB, int TP, int MINB, int UT>
+// ZF: the group may hold k = 0 (f takes its limit nu0.r there); false for groups of k > 0 only,
+// which keeps the zero-frequency select out of the inner loop.
+template <int KB, int TP, int MINB, int UT, bool ZF>
 __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
                                                        const float* __restrict__ qtab, const cf* __restrict__ Pq,
                                                        const cf* __restrict__ Pnq, const cd* __restrict__ surf,
@@ -460,7 +462,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   __shared__ float4 sq[KB][UT];  // surface values at the tile's points: P re, im, dP re, im
   __shared__ float4 s0[KB][TP];  // surface values at the foot points, same order
   __shared__ float sacc[KB][4][TP];  // compensated sums: re (s, c), im (s, c)
-  __shared__ float4 sk[KB];  // k (FP32 head), 1 / k (0 at k = 0), 1 at k = 0 else 0, k - head
+  __shared__ float2 sk[KB];  // k (FP32 head), 1 / k (0 at k = 0)
+  __shared__ float sklo[KB];  // k - head
   const int kbase = blockIdx.y * KB;
   const int nkb = min(KB, nk - kbase);
   const int tid = threadIdx.x;
@@ -468,7 +471,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   const bool active = m < M;
   if (tid < nkb) {
     const ff k = ff_from_double(kv[kbase + tid]);
-    sk[tid] = make_float4(k.hi, kinv32(kv[kbase + tid]), kv[kbase + tid] > 0.0 ? 0.f : 1.f, k.lo);
+    sk[tid] = make_float2(k.hi, kinv32(kv[kbase + tid]));
+    sklo[tid] = k.lo;
   }
 #pragma unroll
   for (int j = 0; j < KB; ++j)
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
       float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
       if (uniform) {
-        const ff k0 = {sk[0].x, sk[0].w};
+        const ff k0 = {sk[0].x, sklo[0]};
         cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
         cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
         cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
@@ -554,10 +558,10 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
 #pragma unroll
       for (int j = 0; j < KB; ++j) {
         if (j < nkb) {
-          const float4 kj = sk[j];
-          const float khi = kj.x, kinv = kj.y, kzero = kj.z;
+          const float2 kj = sk[j];
+          const float khi = kj.x, kinv = kj.y;
           if (!uniform) {
-            const ff k = {khi, kj.w};
+            const ff k = {khi, sklo[j]};
             cis_ffk(ff_mul(k, Rp), tp, cp, spp);
             cis_ffk(ff_mul(k, R0), tp, c0, s0v);
             cis_ffk(ff_mul(k, nr), tp, cg, sgv);
@@ -580,8 +584,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
           const float gdr = cp - c0, gdi = spp - s0v;
           const float ddr = __fmaf_rn(__fmaf_rn(s0v, kR0, c0), rn0, -(__fmaf_rn(spp, kRp, cp) * rnp));
           const float ddi = __fmaf_rn(__fmaf_rn(cp, kRp, -spp), rnp, -(__fmaf_rn(c0, kR0, -s0v) * rn0));
-          // f = sin(k nu0.r)/k, or its limit nu0.r at k = 0 (kinv 0, kzero 1)
-          const float g = cg, f = __fmaf_rn(kzero, nr.hi, sgv * kinv), dg = -khi * sgv * nn, df = cg * nn;
+          // f = sin(k nu0.r)/k, or its limit nu0.r at k = 0 (kinv 0)
+          const float g = cg, f = (ZF && kinv == 0.f) ? nr.hi : sgv * kinv, dg = -khi * sgv * nn, df = cg * nn;
           const float4 p0 = s0[j][tid], pq = sq[j][u];
           const float P0r = p0.x, P0i = p0.y, Q0r = p0.z, Q0i = p0.w;
           const float Ptr = pq.x - P0r * g - Q0r * f, Pti = pq.y - P0i * g - Q0i * f;
@@ -626,10 +630,14 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
 template <int KB, int TP, int MINB, int UT>
 static void launch_field32c(bie_ctx* c, int64_t EQ, const cf* Pq, const cf* Pnq, const cd* surf, const double* xp,
                             int64_t M, const int32_t* foot_elem, const double* foot, const double* kv, int nk, cd* T,
-                            TwoPi3f tp, int uniform, ff dk) {
+                            TwoPi3f tp, int uniform, ff dk, bool zero) {
   dim3 gb((unsigned)((M + TP - 1) / TP), (unsigned)((nk + KB - 1) / KB));
-  BIE_LAUNCH(k_field32c<KB, TP, MINB, UT><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M,
-                                                              foot_elem, foot, kv, nk, T, tp, uniform, dk));
+  if (zero)
+    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, true><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf,
+                                                                          xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dk));
+  else
+    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, false><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf,
+                                                                           xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dk));
 }
 
 int ensure_mixed_tables(bie_ctx* c);
@@ -654,25 +662,38 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
     if (c->field_accurate_phase) {
       const int v = c->field_variant;
       const int KBv = (v >= 1) ? 16 : FKB;
-      // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-      int uniform = nk > 1 ? 1 : 0;
-      const double dkv = nk > 1 ? hk[1] - hk[0] : 0.0;
-      for (int j = 0; j < nk && uniform; ++j) {
-        const double expect = hk[(j / KBv) * KBv] + (j % KBv) * dkv;
-        if (std::fabs(hk[j] - expect) > 1e-12 * std::fabs(hk[j]) || !(dkv > 0.0)) uniform = 0;
-      }
-      const ff dkf = ff_from_double(dkv);
-      if (v == 1) {
-        launch_field32c<16, 64, 4, 64>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else if (v == 2) {
-        launch_field32c<16, 128, 3, 32>(c, EQ, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dkf);
-      } else {
-        dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((nk + FKB - 1) / FKB));
-        BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem,
-                                                        foot, kv, nk, T, tp, uniform, dkf));
+      // runs of wavenumbers that are all zero or all positive, one launch each (k = 0, the
+      // zero-frequency term, takes f's limit inside the kernel; positive runs skip that select)
+      for (int r0 = 0; r0 < nk;) {
+        const bool zero = hk[r0] == 0.0;
+        int r1 = r0 + 1;
+        while (r1 < nk && (hk[r1] == 0.0) == zero) ++r1;
+        const int n = r1 - r0;
+        // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
+        int uniform = n > 1 ? 1 : 0;
+        const double dkv = n > 1 ? hk[r0 + 1] - hk[r0] : 0.0;
+        for (int j = 0; j < n && uniform; ++j) {
+          const double expect = hk[r0 + (j / KBv) * KBv] + (j % KBv) * dkv;
+          if (std::fabs(hk[r0 + j] - expect) > 1e-12 * std::fabs(hk[r0 + j]) || !(dkv > 0.0)) uniform = 0;
+        }
+        const ff dkf = ff_from_double(dkv);
+        const double* kr = kv + r0;
+        const cf *Pqr = Pq + (int64_t)r0 * EQ, *Pnqr = Pnq + (int64_t)r0 * EQ;
+        const cd* sr = surf + (int64_t)r0 * 2 * c->N;
+        cd* Tr = T + (int64_t)r0 * M;
+        if (v == 1) {
+          launch_field32c<16, 64, 4, 64>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero);
+        } else if (v == 2) {
+          launch_field32c<16, 128, 3, 32>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero);
+        } else {
+          dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((n + FKB - 1) / FKB));
+          BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pqr, Pnqr, sr, xp, M, foot_elem,
+                                                          foot, kr, n, Tr, tp, uniform, dkf));
+        }
+        r0 = r1;
       }
     }
     else

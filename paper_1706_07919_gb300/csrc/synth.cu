@@ -124,6 +124,76 @@ int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t
 }
 
 // ------------------------------------------------------------------------------------------
+// Dominant frequencies (Sec. 4, Table I; Sec. 5): the space-time field is accurate already from
+// the wavenumbers at which the incident spectrum is largest, so only those need a frequency
+// solve.  One CTA ranks m = 0 .. nm-1 by max over the pulses of |S[p][m]|^2 (ties: the lower m
+// first) with a bitonic sort in shared memory, keeps the first K and sorts them ascending.
+// ------------------------------------------------------------------------------------------
+constexpr int kTopMax = 4096;  // padded sort length (nm = Nt/2 + 1 <= 2049)
+
+__global__ void __launch_bounds__(1024) k_top_frequencies(const cd* __restrict__ S, int64_t P, int nm, int K,
+                                                          int64_t* __restrict__ midx_out) {
+  extern __shared__ unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);     // [kTopMax]
+  int32_t* idx = reinterpret_cast<int32_t*>(key + kTopMax);  // [kTopMax]
+  int L = 1;
+  while (L < nm) L <<= 1;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    double a = -1.0;  // padding sorts last
+    if (m < nm) {
+      a = 0.0;
+      for (int64_t p = 0; p < P; ++p) {
+        const cd v = S[p * nm + m];
+        a = fmax(a, v.re * v.re + v.im * v.im);
+      }
+    }
+    key[m] = a;
+    idx[m] = m;
+  }
+  __syncthreads();
+  // descending by key, ascending by index on ties
+  for (int size = 2; size <= L; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < L / 2; t += blockDim.x) {
+        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+        const bool up = (i & size) == 0;  // this run ends in the wanted order
+        const bool j_first = key[j] > key[i] || (key[j] == key[i] && idx[j] < idx[i]);
+        if (j_first == up) {
+          const double tk = key[i]; key[i] = key[j]; key[j] = tk;
+          const int32_t ti = idx[i]; idx[i] = idx[j]; idx[j] = ti;
+        }
+      }
+      __syncthreads();
+    }
+  // the K selected indices in ascending order
+  int LK = 1;
+  while (LK < K) LK <<= 1;
+  for (int t = threadIdx.x; t < LK; t += blockDim.x) key[t] = t < K ? (double)idx[t] : 1e300;
+  __syncthreads();
+  for (int size = 2; size <= LK; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < LK / 2; t += blockDim.x) {
+        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+        const bool up = (i & size) == 0;
+        if ((key[j] < key[i]) == up) {
+          const double tk = key[i]; key[i] = key[j]; key[j] = tk;
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < K; t += blockDim.x) midx_out[t] = (int64_t)key[t];
+}
+
+int top_frequencies(bie_ctx* c, const cd* S, int64_t P, int nm, int K, int64_t* midx_dev) {
+  if (nm > kTopMax) return fail(BIE_ERR_INVALID_ARG, "too many frequencies to rank");
+  const size_t smem = kTopMax * (sizeof(double) + sizeof(int32_t));
+  BIE_TRY((set_smem_max(k_top_frequencies)));
+  BIE_LAUNCH(k_top_frequencies<<<1, 1024, smem, c->stream>>>(S, P, nm, K, midx_dev));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
 // Allocation-free synthesis.  Some callers cannot allocate device memory while they run: a host
 // framework that hands out a fixed device-memory budget through its own pool, or a latency-bound
 // pipeline in which cudaMalloc/cudaFree would synchronise the device.  For them the synthesis's

@@ -77,6 +77,9 @@ class Solver:
         B.bie_synthesize(self.ctx, T, midx, S, Nt, o, code)
         return o
 
+    def top_frequencies(self, S: torch.Tensor, Nt: int, K: int):
+        return B.bie_top_frequencies(self.ctx, S, Nt, K)
+
     # ---- learned warm start (BIE_MODE_LEARNED's network) ----
     def mlp_set_params(self, theta):
         B.bie_mlp_set_params(self.ctx, theta)

@@ -3,6 +3,7 @@ library routines (numpy, scipy), closed forms, exact quadrature of monomials, th
 sphere series, Green's-identity special solutions and convergence under mesh refinement.
 Each test names the passage of the paper whose reading it checks."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -419,3 +420,55 @@ def test_scattering_amplitude_reciprocity():
     f11 = _far_field(m, k, P1, Pn1, d2)
     assert abs(f12 - f21) <= 1e-3 * abs(f12), (f12, f21)  # measured 6.5e-5
     assert abs(f11 - f12) > 0.1 * abs(f12)  # a generic pair of amplitudes differs: the pin has teeth
+
+
+# ---------------- dominant frequencies and Table I (Sec. 4) ------------------------------------
+def test_top_frequencies_match_lexsort_with_ties():
+    rng = np.random.default_rng(21)
+    Nt = 64
+    S = rng.standard_normal((3, Nt)) + 1j * rng.standard_normal((3, Nt))
+    S[:, 5] = S[:, 9] = 2.5  # a tie: the lower index ranks first
+    S[:, 12] = 2.5
+    amp = np.abs(S[:, : Nt // 2 + 1]).max(axis=0)
+    for K in (0, 1, 2, 3, 7, Nt // 2 + 1):
+        order = np.lexsort((np.arange(amp.size), -amp))
+        np.testing.assert_array_equal(oracle.top_frequencies(S, K), np.sort(order[:K]))
+
+
+def _table_one():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_rms.txt")
+    rows = [list(map(float, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return np.array(rows)
+
+
+def rms_percent(pK, pall):
+    """Reading of Table I's measure: the RMS over the period's time steps of the difference,
+    relative to the largest |p| of the all-frequency signal at that point, in percent."""
+    return 100.0 * np.sqrt(((pK - pall) ** 2).mean(axis=-1)) / np.abs(pall).max(axis=-1)
+
+
+def test_oracle_reproduces_table_one():
+    """The paper's own experiment: soft sphere, 1002 nodes, Eq. (pulse) with 2N_c = 4, alpha = 0.1,
+    w = 20.1a, 64 frequencies; the field at (0,0,-1.1a) and (0,0,-4a) synthesised from the 5, 10,
+    20 dominant frequencies against all 64.  Printed values (tests/golden/table1_rms.txt) within
+    30 % (measured 4.35, 4.84 / 1.68, 1.70 / 0.57, 0.55); the kept amplitudes above the printed
+    epsilon bounds, which are rounded (the 10th amplitude is 3.497 % of the largest, printed
+    "> 3.5 %")."""
+    from workloads import config_paper_sphere
+    w = config_paper_sphere(bc=1)
+    pts = w.xobs[:2]
+    S = oracle.dft(w.pulses[0])
+    T = np.zeros((len(w.k), 2), complex)
+    for i, k in enumerate(w.k):
+        P, Pn = oracle.solve_frequency(w.mesh, k, D)
+        T[i] = oracle.field(w.mesh, k, P, Pn, pts)
+    m_all = np.arange(len(w.k))
+    pall = oracle.synthesize(T, m_all, S[None, :], w.Nt)[0]
+    amp = np.abs(S[: w.Nt // 2 + 1])
+    for K, eps, r11, r40 in _table_one():
+        sel = oracle.top_frequencies(S[None, :], int(K))
+        assert sel.max() < len(w.k)
+        assert amp[sel].min() / amp.max() > 0.98 * eps
+        pK = oracle.synthesize(T[sel], sel, S[None, :], w.Nt)[0]
+        got = rms_percent(pK, pall)
+        np.testing.assert_allclose(got, [r11, r40], rtol=0.3)

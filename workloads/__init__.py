@@ -10,6 +10,7 @@ from .meshes import (Mesh, octa_sphere, ico_sphere, scale_translate, merge_meshe
                      ellipsoid_from_sphere)
 from .pulses import gaussian_pulse, ricker_pulse, modulated_gaussian, paper_sine_pulse
 from .configs import (config_sphere_fp64, config_two_spheres_mixed, config_spheroid_learned, config_uneven_batch, config_lattice_large,
+                      config_paper_sphere,
                       uneven_configuration, shell_points,
                       spheroid_shell_points, plane_grid_points, Workload)
 
@@ -17,7 +18,7 @@ __all__ = [
     "Mesh", "octa_sphere", "ico_sphere", "scale_translate", "merge_meshes",
     "ellipsoid_from_sphere", "gaussian_pulse", "ricker_pulse", "modulated_gaussian",
     "paper_sine_pulse", "config_sphere_fp64", "config_two_spheres_mixed", "config_spheroid_learned",
-    "config_uneven_batch", "uneven_configuration", "config_lattice_large",
+    "config_uneven_batch", "uneven_configuration", "config_lattice_large", "config_paper_sphere",
     "shell_points", "spheroid_shell_points",
     "plane_grid_points", "Workload",
 ]

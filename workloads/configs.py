@@ -196,3 +196,30 @@ def config_lattice_large(Nk: int = 2048, grid: int = 256, Nt: int = 4096, freq: 
         rows.append(np.cos(np.outer(t, w) + ph) @ amp / np.sqrt(m.size))
     pulses = np.stack(rows)
     return Workload("lattice_large", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs, pulses, Nt, T)
+
+
+def config_paper_sphere(bc: int = 1, Nc2: int = 4, alpha: float = 0.1, width: float = 20.1, Nf: int = 128,
+                        freq: int = 5, grid: int = 80, half: float = 10.0) -> Workload:
+    """The paper's own sphere experiment (Sec. 4): a unit sphere (soft, bc = 1, or hard, bc = 0)
+    meshed with 500 quadratic elements / 1002 nodes (icosahedral grid, 5 divisions per face); the
+    incident pulse of Eq. (pulse) with 2 N_c = Nc2 cycles modulated by exp(-alpha |tau|) in a window
+    of width w = 20.1 a, so k_0 a = 8 pi N_c a / w, sampled at N_f = 128 points of the period
+    T = w / c; the 64 frequencies k_m = 2 pi m / w, m = 0 .. 63 (m = 0 included: S_0 vanishes for
+    this odd pulse, the zero-frequency solve costs one wavenumber).  Observation points: the two
+    points of Table I, (0, 0, -1.1 a) and (0, 0, -4 a), then the 80 x 80 grid of the snapshots in the
+    y-z plane over [-10 a, 10 a]^2 without the points inside the sphere (r < 1.02 a)."""
+    mesh = ico_sphere(freq, 1.0, bc=bc)
+    from .pulses import paper_sine_pulse
+    T = width
+    k0 = 8.0 * np.pi * (Nc2 / 2.0) / width
+    pulses = paper_sine_pulse(Nf, T, k0, Nc2, alpha, 0.0)[None, :]
+    dk = 2.0 * np.pi / width
+    k = dk * np.arange(0, Nf // 2, dtype=np.float64)
+    g = np.linspace(-half, half, grid)
+    Y, Z = np.meshgrid(g, g, indexing="ij")
+    yz = np.stack([np.zeros(grid * grid), Y.ravel(), Z.ravel()], axis=1)
+    yz = yz[np.linalg.norm(yz, axis=1) >= 1.02]
+    xobs = np.concatenate([np.array([[0.0, 0.0, -1.1], [0.0, 0.0, -4.0]]), yz])
+    return Workload(f"paper_sphere_{'soft' if bc else 'hard'}", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs,
+                    pulses, Nf, T)
+
