@@ -251,6 +251,24 @@ int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
 int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, void* surf_out,
                           bie_report* rep);
 
+/* Frequency solves for several incident plane waves at once (Sec. 5: for a fixed configuration the
+ * solution matrix is kept and only the incident wave changes).  Per wavenumber the system matrix
+ * is assembled and factored once; the right-hand side of direction d is -B known_d, B the
+ * known-column matrix (the coefficients of the known boundary values in Eq. BRIEF, i.e. the system
+ * matrix with every node's condition exchanged, assembled once by the same kernels), known_d the
+ * scattered-field boundary values of exp(i k d.x) (Sec. 4).
+ *   k        host f64 [Nk] as bie_solve_frequencies
+ *   dirs     host f64 [ndir][3], non-zero (normalised here); the context's own direction is unused
+ *   mode     BIE_MODE_FP64 or BIE_MODE_MIXED (iterative refinement per direction against the shared
+ *            factor; flagged wavenumbers re-assembled per direction as in bie_solve_frequencies)
+ *   surf_out device c128 [Nk][ndir][2][N]: P and dP/dn per wavenumber and direction
+ *   rep      host bie_report [Nk][ndir] or NULL
+ * Memory: one more N x N matrix per wavenumber in flight than bie_solve_frequencies.
+ * Synchronises.  Errors: as bie_solve_frequencies; INVALID_ARG for ndir outside [1, 4096], a zero
+ * direction or BIE_MODE_LEARNED. */
+int bie_solve_frequencies_multi(bie_ctx* ctx, const double* k, int64_t Nk, const double* dirs, int64_t ndir,
+                                int mode, void* surf_out, bie_report* rep);
+
 /* Scattered field at M observation points (Eq. BRIEFdmn with the closest surface point x0 of
  * each point, Sec. 3), for every k:
  *   xobs  device f64 [M][3] points in the fluid (a point behind its closest surface point, i.e.

@@ -39,7 +39,7 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
             "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
             "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks",
-            "bie_top_frequencies"]
+            "bie_top_frequencies", "bie_solve_frequencies_multi"]
 
 
 class BieReport(ctypes.Structure):
@@ -129,6 +129,7 @@ def load(path: str | None = None):
         "bie_get_phase_times": ([vp, vp], i32),
         "bie_measure_peaks": ([i32, vp], i32),
         "bie_top_frequencies": ([vp, vp, i64, i64, i64, vp], i32),
+        "bie_solve_frequencies_multi": ([vp, vp, i64, vp, i64, i32, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -208,6 +209,20 @@ def bie_solve_frequencies(ctx: int, k, mode: int, surf_out, reports: bool = True
     _check(load().bie_solve_frequencies(ctx, _hp(k), k.shape[0], mode, _dp(surf_out),
                                         ctypes.cast(rep, ctypes.c_void_p) if rep is not None else None))
     return list(rep)[: k.shape[0]] if rep is not None else None
+
+
+def bie_solve_frequencies_multi(ctx: int, k, dirs, mode: int, surf_out, reports: bool = True):
+    k = np.ascontiguousarray(k, np.float64)
+    d = np.ascontiguousarray(np.atleast_2d(dirs), np.float64)
+    if d.shape[1] != 3:
+        raise ValueError("dirs must be [ndir][3]")
+    n = k.shape[0] * d.shape[0]
+    if _dtype_name(surf_out) != "complex128" or (k.shape[0] and _numel(surf_out) % (2 * n)):
+        raise ValueError("surf_out must be complex128 [Nk][ndir][2][N]")
+    rep = (BieReport * max(1, n))() if reports else None
+    _check(load().bie_solve_frequencies_multi(ctx, _hp(k), k.shape[0], _hp(d), d.shape[0], mode, _dp(surf_out),
+                                              ctypes.cast(rep, ctypes.c_void_p) if rep is not None else None))
+    return list(rep)[:n] if rep is not None else None
 
 
 def bie_eval_field(ctx: int, xobs, k, surf, mode: int, T_out) -> None:

@@ -95,6 +95,7 @@ struct bie_ctx {
   int32_t* elems = nullptr;    // [E][6]
   double* normals = nullptr;   // [N][3]
   uint8_t* bc = nullptr;       // [N]
+  uint8_t* bc_flip = nullptr;  // [N] 1 - bc: assembles the known-column matrix (several directions)
   std::vector<double> h_nodes, h_normals;
   std::vector<int32_t> h_elems;
   std::vector<uint8_t> h_bc;

@@ -104,7 +104,7 @@ int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t
                void* out, int out_dtype);
 int top_frequencies(bie_ctx* c, const cd* S, int64_t P, int nm, int K, int64_t* midx_dev);
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep, cf* d_keep);
+                int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir);
 int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
 void mlp_free(bie_ctx* c);
 int mlp_set_params(bie_ctx* c, const float* theta_host);
@@ -121,26 +121,27 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
 
 static void free_geometry(bie_ctx* c) {
   void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
-                  c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear};
+                  c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear, c->bc_flip};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->nshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
-  c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr;
+  c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr; c->bc_flip = nullptr;
   c->far_r2 = 0.0;
   c->uniform_bc = -1;
   c->has_geom = false;
 }
 
 // P, P' at every node from the solution vector and the known boundary values.
+// surf: [nk] blocks of [2][N], kstride elements apart (2N, or 2N x directions).
 __global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, const cd* __restrict__ x,
-                                 const cd* __restrict__ known, cd* __restrict__ surf) {
+                                 const cd* __restrict__ known, cd* __restrict__ surf, int64_t kstride) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int kk = blockIdx.y;
   if (j >= N) return;
   cd xv = x[(int64_t)kk * N + j], kv = known[(int64_t)kk * N + j];
-  cd* s = surf + (int64_t)kk * 2 * N;
+  cd* s = surf + (int64_t)kk * kstride;
   if (bc[j] == 0) { s[j] = xv; s[N + j] = kv; }
   else { s[j] = kv; s[N + j] = xv; }
 }
@@ -163,6 +164,99 @@ static int check_k(const double* k, int64_t Nk, bool allow_zero = true) {
       return fail(BIE_ERR_INVALID_ARG, "k[" + std::to_string(i) + "] must be finite and " +
                                            (allow_zero ? "either 0 or >= 1e-30" : ">= 1e-30"));
   }
+  return BIE_OK;
+}
+
+// The boundary conditions exchanged at every node (device, made once per geometry): assembling
+// with them gives the known-column matrix of the real conditions.
+int flipped_bc(bie_ctx* c, uint8_t** out) {
+  if (!c->bc_flip) {
+    std::vector<uint8_t> f(c->N);
+    for (int64_t j = 0; j < c->N; ++j) f[j] = (uint8_t)(1 - c->h_bc[j]);
+    BIE_CUDA_TRY(cudaMalloc(&c->bc_flip, c->N));
+    BIE_CUDA_TRY(cudaMemcpy(c->bc_flip, f.data(), c->N, cudaMemcpyHostToDevice));
+  }
+  *out = c->bc_flip;
+  return BIE_OK;
+}
+
+int rhs_from_known64(bie_ctx* c, const cd* B, int nk, int n, const cd* known, cd* zero, cd* b, double* rowabs,
+                     void* state_dev);
+size_t refine_state_bytes(int nk);
+__global__ void k_known64(const double* __restrict__ nodes, const double* __restrict__ normals,
+                          const uint8_t* __restrict__ bc, int64_t N, const double* __restrict__ kv, double dx,
+                          double dy, double dz, cd* __restrict__ known);
+
+// Several incident directions in FP64 (see solve_mixed): A and the known-column matrix B assembled
+// once per wavenumber, A factored once, b_d = -B known_d per direction.  surf_out [Nk][ndir][2][N].
+int solve_fp64_multi(bie_ctx* c, const double* k, int64_t Nk, const double* dirs, int ndir, cd* surf_out,
+                     bie_report* rep) {
+  const int64_t N = c->N;
+  uint8_t* bc_flip = nullptr;
+  BIE_TRY(flipped_bc(c, &bc_flip));
+  const double dir0[3] = {c->dir[0], c->dir[1], c->dir[2]};
+  struct DirGuard {
+    bie_ctx* c;
+    double d[3];
+    ~DirGuard() { for (int t = 0; t < 3; ++t) c->dir[t] = d[t]; }
+  } dirguard{c, {dir0[0], dir0[1], dir0[2]}};
+  auto set_dir = [&](int d) { for (int t = 0; t < 3; ++t) c->dir[t] = dirs[3 * d + t]; };
+  const size_t st_bytes = (refine_state_bytes(1) + 15) / 16 * 16;
+  const size_t perk = 2 * (size_t)N * N * sizeof(cd) + (size_t)N * sizeof(cd) * 8 + (size_t)N * sizeof(double) +
+                      (size_t)N * 4 + st_bytes + 64;
+  size_t free_b = 0, total_b = 0;
+  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
+  if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "two FP64 matrices of N = " + std::to_string(N) + " do not fit");
+  BIE_TRY(ensure_buf(c->work, kb * perk + 4096));
+  char* base = (char*)c->work.p;
+  cd* A = (cd*)base;
+  cd* Bm = A + kb * N * N;
+  cd* b = Bm + kb * N * N;
+  cd* scratch = b + kb * N;  // known [kb][N], rowsum [kb][N][3]
+  cd* bd = scratch + kb * N * 4;
+  cd* zero = bd + kb * N;
+  cd* known = zero + kb * N;
+  double* rowabs = (double*)(known + kb * N);
+  int32_t* piv = (int32_t*)(rowabs + kb * N);
+  int32_t* info = piv + kb * N;
+  char* stp = (char*)(((uintptr_t)(info + kb) + 15) & ~(uintptr_t)15);
+  void* state = stp;
+  double* kdev = (double*)(stp + kb * st_bytes);
+  std::vector<int32_t> hinfo(kb);
+  for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
+    const int nk = (int)std::min<int64_t>(kb, Nk - k0);
+    BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    BIE_CUDA_TRY(cudaMemsetAsync(info, 0, nk * sizeof(int32_t), c->stream));
+    set_dir(0);
+    uint8_t* bc_real = c->bc;
+    c->bc = bc_flip;
+    int rc = assemble64(c, kdev, nk, Bm, bd, scratch, false);  // b and known of this call: discarded
+    c->bc = bc_real;
+    BIE_TRY(rc);
+    BIE_TRY(assemble64(c, kdev, nk, A, b, scratch, false));
+    BIE_TRY(lu_factor64(c, A, nk, (int)N, (int)N, N * N, piv, info));
+    for (int d = 0; d < ndir; ++d) {
+      set_dir(d);
+      dim3 gk((unsigned)((N + 255) / 256), nk);
+      BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kdev, c->dir[0], c->dir[1],
+                                                     c->dir[2], known));
+      BIE_TRY(rhs_from_known64(c, Bm, nk, (int)N, known, zero, bd, rowabs, state));
+      BIE_TRY(lu_solve64(c, A, nk, (int)N, (int)N, N * N, piv, bd, N));
+      dim3 g((unsigned)((N + 255) / 256), nk);
+      BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, bd, known, surf_out + (k0 * ndir + d) * 2 * N,
+                                                           (int64_t)ndir * 2 * N));
+      BIE_CUDA_TRY(cudaGetLastError());
+    }
+    if (rep) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+      BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      for (int i = 0; i < nk; ++i)
+        for (int d = 0; d < ndir; ++d)
+          rep[(k0 + i) * ndir + d] = bie_report{0, BIE_MODE_FP64, hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u, 0, 0.0, 0.0};
+    }
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }
 
@@ -190,7 +284,7 @@ int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report
     BIE_TRY(lu_factor64(c, A, nk, (int)N, (int)N, N * N, piv, info));
     BIE_TRY(lu_solve64(c, A, nk, (int)N, (int)N, N * N, piv, b, N));
     dim3 g((unsigned)((N + 255) / 256), nk);
-    BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, b, scratch, surf_out + k0 * 2 * N));
+    BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, b, scratch, surf_out + k0 * 2 * N, 2 * N));
     BIE_CUDA_TRY(cudaGetLastError());
     if (rep) {
       BIE_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -406,7 +500,7 @@ int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, voi
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
   if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
-  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr);
+  if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr, nullptr, 1);
   if (mode == BIE_MODE_LEARNED) return solve_learned(c, k, Nk, (cd*)surf_out, rep);
   return fail(BIE_ERR_INVALID_ARG, "unknown mode " + std::to_string(mode));
 }
@@ -583,6 +677,28 @@ int bie_top_frequencies(bie_ctx* c, const void* S, int64_t P, int64_t Nt, int64_
   BIE_CUDA_TRY(cudaMemcpyAsync(midx_out, md, (size_t)K * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
+}
+
+int bie_solve_frequencies_multi(bie_ctx* c, const double* k, int64_t Nk, const double* dirs, int64_t ndir, int mode,
+                                void* surf_out, bie_report* rep) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, Nk));
+  if (ndir < 1 || ndir > 4096) return fail(BIE_ERR_INVALID_ARG, "ndir must be in [1, 4096]");
+  if (!dirs) return fail(BIE_ERR_INVALID_ARG, "NULL dirs");
+  std::vector<double> d(3 * ndir);
+  for (int64_t i = 0; i < ndir; ++i) {
+    const double* v = dirs + 3 * i;
+    const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(n > 0.0) || !std::isfinite(n))
+      return fail(BIE_ERR_INVALID_ARG, "direction " + std::to_string(i) + " must be finite and non-zero");
+    for (int t = 0; t < 3; ++t) d[3 * i + t] = v[t] / n;
+  }
+  if (Nk == 0) return BIE_OK;
+  if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
+  if (mode == BIE_MODE_FP64) return solve_fp64_multi(c, k, Nk, d.data(), (int)ndir, (cd*)surf_out, rep);
+  if (mode == BIE_MODE_MIXED)
+    return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr, d.data(), (int)ndir);
+  return fail(BIE_ERR_INVALID_ARG, "bie_solve_frequencies_multi supports BIE_MODE_FP64 and BIE_MODE_MIXED");
 }
 
 }  // extern "C"

@@ -19,7 +19,7 @@
 namespace bie {
 
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep, cf* d_keep);
+                int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir);
 int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq);
 int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstride, const cd* b, cd* x, const cf* LU,
                 int64_t lu_bstride, const int32_t* perm, const cf* Dinv, const int32_t* sel, int m, int cycles,
@@ -173,7 +173,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     return (double)ms;
   };
   BIE_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
-  BIE_TRY(solve_mixed(c, ka.data(), na, surf_a, rep_a.data(), LUk, permk, Dk));
+  BIE_TRY(solve_mixed(c, ka.data(), na, surf_a, rep_a.data(), LUk, permk, Dk, nullptr, 1));
   BIE_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
   BIE_CUDA_TRY(cudaEventSynchronize(ev[1]));
   info.anchors_ms = elapsed(0, 1);
@@ -325,7 +325,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     cd* surf_r = (cd*)tmp;
     int32_t* ridx = (int32_t*)((char*)tmp + (size_t)nr * 2 * N * sizeof(cd));
     std::vector<bie_report> rr((size_t)nr);
-    int rc = solve_mixed(c, redo.data(), nr, surf_r, rr.data(), nullptr, nullptr, nullptr);
+    int rc = solve_mixed(c, redo.data(), nr, surf_r, rr.data(), nullptr, nullptr, nullptr, nullptr, 1);
     if (rc == BIE_OK) {
       std::vector<int32_t> hi(redo_idx.begin(), redo_idx.end());
       rc = cudaMemcpyAsync(ridx, hi.data(), nr * 4, cudaMemcpyHostToDevice, c->stream) == cudaSuccess ? BIE_OK

@@ -28,8 +28,14 @@ size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est);
 int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
+int rhs_from_known(bie_ctx* c, const cf* B, int nk, int n, int64_t ld, int64_t bstride, const cd* known, cd* zero,
+                   cd* b, double* rowabs, void* state_dev);
+int flipped_bc(bie_ctx* c, uint8_t** out);
+__global__ void k_known64(const double* __restrict__ nodes, const double* __restrict__ normals,
+                          const uint8_t* __restrict__ bc, int64_t N, const double* __restrict__ kv, double dx,
+                          double dy, double dz, cd* __restrict__ known);
 __global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, const cd* __restrict__ x,
-                                 const cd* __restrict__ known, cd* __restrict__ surf);
+                                 const cd* __restrict__ known, cd* __restrict__ surf, int64_t kstride);
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -38,16 +44,38 @@ constexpr int kFallbackGroupMax = 32;  // FP64 systems re-assembled and refined 
 // lu_keep / perm_keep / d_keep (optional, device): receive the low-precision factor ([Nk][N][ld],
 // ld = N rounded up to 64), row permutation ([Nk][N]) and diagonal-block inverses
 // ([Nk][diag_inv_stride(N)]) of every wavenumber.
+// dirs (host [ndir][3], unit vectors; NULL: the context's direction, ndir = 1): several incident
+// plane waves share each wavenumber's matrix and factor (Sec. 5: the solution matrix is kept and
+// only the incident wave changes).  Their right-hand sides come from the known-column matrix B --
+// the coefficients of the known boundary values in Eq. (BRIEF), which is the system matrix with
+// every node's condition exchanged, assembled once per wavenumber by the same kernels -- as
+// b_d = -B known_d (float-float products).  surf_out [Nk][ndir][2][N], rep [Nk][ndir].
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep, cf* d_keep) {
+                int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir) {
   const int64_t N = c->N;
+  if (!dirs || ndir < 1) ndir = 1;
+  const bool multi = ndir > 1;
+  double dir0[3] = {c->dir[0], c->dir[1], c->dir[2]};
+  std::vector<double> hdirs(3 * ndir);
+  for (int d = 0; d < ndir; ++d)
+    for (int t = 0; t < 3; ++t) hdirs[3 * d + t] = dirs ? dirs[3 * d + t] : dir0[t];
+  struct DirGuard {  // the context's direction is switched per direction and restored on return
+    bie_ctx* c;
+    double d[3];
+    ~DirGuard() { for (int t = 0; t < 3; ++t) c->dir[t] = d[t]; }
+  } dirguard{c, {dir0[0], dir0[1], dir0[2]}};
+  auto set_dir = [&](int d) { for (int t = 0; t < 3; ++t) c->dir[t] = hdirs[3 * d + t]; };
+  set_dir(0);
+  uint8_t* bc_flip = nullptr;
+  if (multi) BIE_TRY(flipped_bc(c, &bc_flip));
+  const int64_t kstride = (int64_t)ndir * 2 * N;  // surf_out elements between wavenumbers
   const int64_t ld = (N + 63) / 64 * 64;
   const size_t mat = align256((size_t)N * ld * sizeof(cf));  // == N * ld * 8: ld is a multiple of 64
   const size_t vec = align256((size_t)N * sizeof(cd));
   const int64_t dstride = diag_inv_stride((int)N);
   const size_t dsz = align256((size_t)dstride * sizeof(cf));
-  const size_t perk = 2 * mat + dsz + 4 * vec + align256((size_t)N * 6 * sizeof(double)) + align256((size_t)N * 8) +
-                      2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
+  const size_t perk = (multi ? 3 : 2) * mat + dsz + 4 * vec + align256((size_t)N * 6 * sizeof(double)) +
+                      align256((size_t)N * 8) + 2 * align256((size_t)N * 4) + align256(refine_state_bytes(1)) + 64;
   // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel.  One
   // group refines its systems in the same launches (one CTA per system in the triangular
   // solves), so a larger group fills more of the GPU; it is capped at an eighth of free memory.
@@ -66,6 +94,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);
   cf* LU = (cf*)take(kb * mat);
+  cf* Bk = multi ? (cf*)take(kb * mat) : nullptr;  // known-column matrices
   cf* Dinv = (cf*)take(kb * dsz);
   cd* b = (cd*)take(kb * vec);
   cd* x = (cd*)take(kb * vec);
@@ -95,6 +124,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   std::vector<double> gb(G), ge(G);
   std::vector<double> full64;
   std::vector<int64_t> full64_idx;
+  std::vector<int> full64_dir;
   // The device part of a batch (assembly, factorisation, refinement) is stream-ordered and needs
   // no host decision, so full batches after the first are captured once in a CUDA graph and
   // replayed; the wavenumbers reach the graph through a pinned host buffer.
@@ -136,7 +166,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     if (cudaEventElapsedTime(&ms, ev[a], ev[b2]) != cudaSuccess) return 0.0;
     return (double)ms;
   };
-  bool use_graph = c->mixed_graph && !timing && Nk >= 2 * kb;
+  bool use_graph = c->mixed_graph && !timing && !multi && Nk >= 2 * kb;
   double* kpin = nullptr;
   if (use_graph) {
     BIE_TRY(ensure_pinned(c, (size_t)kb * sizeof(double)));
@@ -181,6 +211,14 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
         BIE_TRY(batch_core(k + k0, nk));
       }
     } else {
+      if (multi) {  // the known-column matrices B first (the factor's buffer is free scratch until then)
+        BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        uint8_t* bc_real = c->bc;
+        c->bc = bc_flip;
+        const int rc = assemble32(c, kdev, nk, Bk, ld, x, r, rowsum, LU);  // b and known: discarded
+        c->bc = bc_real;
+        BIE_TRY(rc);
+      }
       BIE_TRY(batch_core(k + k0, nk));
     }
     if (lu_keep) {
@@ -192,69 +230,86 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
         BIE_CUDA_TRY(cudaMemcpyAsync(d_keep + k0 * dstride, Dinv, (size_t)nk * dstride * sizeof(cf),
                                      cudaMemcpyDeviceToDevice, c->stream));
     }
-    BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
-    BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (timing) {  // the batch has completed (its state was read)
-      c->phase.assembly_ms += elapsed(0, 1);
-      c->phase.factor_ms += elapsed(1, 2);
-      c->phase.refine_ms += elapsed(2, 3);
-      c->phase.batches += 1;
-      c->phase.systems += nk;
-    }
-    std::vector<int32_t> flagged;
-    for (int i = 0; i < nk; ++i) {
-      const bool conv = done[i] && std::isfinite(berr[i]);
-      const bool sensitive = !(est[i] <= c->fallback_err_est);
-      if (rep)
-        rep[k0 + i] = bie_report{iters[i], BIE_MODE_MIXED,
-                                 (conv ? 0u : BIE_FLAG_NOT_CONVERGED) | (hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u) |
-                                     (sensitive ? BIE_FLAG_ILL_CONDITIONED : 0u),
-                                 0, berr[i], est[i]};
-      if (hinfo[i]) {  // singular low-precision factor: nothing to refine with
-        full64.push_back(k[k0 + i]);
-        full64_idx.push_back(k0 + i);
-      } else if (!conv || sensitive) {
-        flagged.push_back(i);
+    for (int d = 0; d < ndir; ++d) {
+      const int64_t r0 = (k0 * ndir + d);  // report and output slot of (k0, d); wavenumbers ndir apart
+      if (d > 0) {  // next incident direction: same matrices and factors, new right-hand side
+        set_dir(d);
+        dim3 gk((unsigned)((N + 255) / 256), nk);
+        BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kdev, c->dir[0], c->dir[1],
+                                                       c->dir[2], known));
+        BIE_TRY(rhs_from_known(c, Bk, nk, (int)N, ld, bstride, known, r, b, rowabs, state));
+        BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
+                             c->refine_tol, Dinv));
       }
-    }
-    // FP64 re-assembly and refinement with the existing factor, in groups
-    for (size_t f0 = 0; f0 < flagged.size(); f0 += G) {
-      const int ng = (int)std::min<size_t>(G, flagged.size() - f0);
-      std::vector<double> kv(ng);
-      for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
-      BIE_CUDA_TRY(cudaMemcpyAsync(kg, kv.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-      BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-      BIE_TRY(mark(4));
-      BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
-      BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
-                                 c->refine64_it_max, c->refine64_tol, Dinv));
-      BIE_TRY(mark(5));
-      BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
-      if (timing) {
-        c->phase.reassembly_ms += elapsed(4, 5);
-        c->phase.reassembled += ng;
+      BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
+      if (d == 0) BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (timing && d == 0) {  // the batch has completed (its state was read)
+        c->phase.assembly_ms += elapsed(0, 1);
+        c->phase.factor_ms += elapsed(1, 2);
+        c->phase.refine_ms += elapsed(2, 3);
+        c->phase.batches += 1;
+        c->phase.systems += nk;
       }
-      for (int g = 0; g < ng; ++g) {
-        const int64_t idx = k0 + flagged[f0 + g];
-        if (rep) {
-          rep[idx].flags |= BIE_FLAG_FP64_ASSEMBLY;
-          rep[idx].iters += gi[g];
-          rep[idx].backward_err = gb[g];
-          if (gd[g]) rep[idx].flags &= ~BIE_FLAG_NOT_CONVERGED;
-        }
-        if (!gd[g] || !std::isfinite(gb[g])) {
-          full64.push_back(k[idx]);
-          full64_idx.push_back(idx);
+      std::vector<int32_t> flagged;
+      for (int i = 0; i < nk; ++i) {
+        const bool conv = done[i] && std::isfinite(berr[i]);
+        const bool sensitive = !(est[i] <= c->fallback_err_est);
+        if (rep)
+          rep[r0 + (int64_t)i * ndir] = bie_report{iters[i], BIE_MODE_MIXED,
+                                                   (conv ? 0u : BIE_FLAG_NOT_CONVERGED) |
+                                                       (hinfo[i] ? BIE_FLAG_ZERO_PIVOT : 0u) |
+                                                       (sensitive ? BIE_FLAG_ILL_CONDITIONED : 0u),
+                                                   0, berr[i], est[i]};
+        if (hinfo[i]) {  // singular low-precision factor: nothing to refine with
+          full64.push_back(k[k0 + i]);
+          full64_idx.push_back(r0 + (int64_t)i * ndir);
+          full64_dir.push_back(d);
+        } else if (!conv || sensitive) {
+          flagged.push_back(i);
         }
       }
+      // FP64 re-assembly (for this direction) and refinement with the existing factor, in groups
+      for (size_t f0 = 0; f0 < flagged.size(); f0 += G) {
+        const int ng = (int)std::min<size_t>(G, flagged.size() - f0);
+        std::vector<double> kv(ng);
+        for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
+        BIE_CUDA_TRY(cudaMemcpyAsync(kg, kv.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, flagged.data() + f0, ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        BIE_TRY(mark(4));
+        BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
+        BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
+                                   c->refine64_it_max, c->refine64_tol, Dinv));
+        BIE_TRY(mark(5));
+        BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
+        if (timing) {
+          c->phase.reassembly_ms += elapsed(4, 5);
+          c->phase.reassembled += ng;
+        }
+        for (int g = 0; g < ng; ++g) {
+          const int64_t idx = r0 + (int64_t)flagged[f0 + g] * ndir;
+          if (rep) {
+            rep[idx].flags |= BIE_FLAG_FP64_ASSEMBLY;
+            rep[idx].iters += gi[g];
+            rep[idx].backward_err = gb[g];
+            if (gd[g]) rep[idx].flags &= ~BIE_FLAG_NOT_CONVERGED;
+          }
+          if (!gd[g] || !std::isfinite(gb[g])) {
+            full64.push_back(k[k0 + flagged[f0 + g]]);
+            full64_idx.push_back(idx);
+            full64_dir.push_back(d);
+          }
+        }
+      }
+      dim3 g((unsigned)((N + 255) / 256), nk);
+      BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, surf_out + r0 * 2 * N, kstride));
+      BIE_CUDA_TRY(cudaGetLastError());
     }
-    dim3 g((unsigned)((N + 255) / 256), nk);
-    BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, surf_out + k0 * 2 * N));
-    BIE_CUDA_TRY(cudaGetLastError());
+    set_dir(0);
   }
   // last resort: the full FP64 path
   for (size_t f = 0; f < full64.size(); ++f) {
     bie_report r64;
+    set_dir(full64_dir[f]);
     BIE_TRY(solve_fp64(c, &full64[f], 1, surf_out + full64_idx[f] * 2 * N, &r64));
     if (rep) {
       rep[full64_idx[f]].flags |= BIE_FLAG_FALLBACK_FP64;

@@ -431,6 +431,23 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
 
 size_t refine_state_bytes(int nk) { return (size_t)nk * sizeof(RefineState); }
 
+// Right-hand sides b = -B known of nk systems from their known-column matrices B (the FP32
+// entries multiplied exactly and summed in float-float, as the residual).  zero: scratch
+// [nk][n], overwritten with zeros; rowabs, state: scratch.
+int rhs_from_known(bie_ctx* c, const cf* B, int nk, int n, int64_t ld, int64_t bstride, const cd* known, cd* zero,
+                   cd* b, double* rowabs, void* state_dev) {
+  RefineState* st = (RefineState*)state_dev;
+  BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
+  BIE_CUDA_TRY(cudaMemsetAsync(zero, 0, (size_t)nk * n * sizeof(cd), c->stream));
+  const int stage = (size_t)n * sizeof(float4) <= 200 * 1024 ? 1 : 0;
+  const size_t sm_res = stage ? (size_t)n * sizeof(float4) : 0;
+  BIE_TRY((set_smem_max(k_residual_ff)));
+  dim3 gr((unsigned)((n + 15) / 16), nk);
+  BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(B, n, ld, bstride, zero, known, b, rowabs, st, stage));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 // ---- refinement against the FP64-assembled system (wavenumbers flagged by the estimate) ------
 // r = b64 - A64 x in FP64; corrections still come from the low-precision factor of the FP32
 // system, which remains a good preconditioner while cond(A) * (its error) < 1.
@@ -461,6 +478,18 @@ __global__ void __launch_bounds__(512) k_residual64(const cd* __restrict__ A, in
     r[(int64_t)g * n + i] = {bi.re - sr, bi.im - si};
     rowabs[(int64_t)g * n + i] = sa;
   }
+}
+
+// FP64 variant: B [nk][n][n] (cd), b = -B known with FP64 products and sums.
+int rhs_from_known64(bie_ctx* c, const cd* B, int nk, int n, const cd* known, cd* zero, cd* b, double* rowabs,
+                     void* state_dev) {
+  RefineState* st = (RefineState*)state_dev;
+  BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
+  BIE_CUDA_TRY(cudaMemsetAsync(zero, 0, (size_t)nk * n * sizeof(cd), c->stream));
+  dim3 gr((unsigned)((n + 15) / 16), nk);
+  BIE_LAUNCH(k_residual64<<<gr, 512, 0, c->stream>>>(B, n, zero, known, b, rowabs, st));
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
 }
 
 __global__ void k_gather_scatter(cd* __restrict__ xb, cd* __restrict__ xg, const int32_t* __restrict__ sel, int n,

@@ -21,7 +21,7 @@
 namespace bie {
 
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
-                int32_t* perm_keep, cf* d_keep);
+                int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir);
 
 struct TuneEntry {
   int batch = 0, tc = 0, block = 256;
@@ -110,9 +110,9 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
     c->tc_version = tc;
     c->lu_block = block;
     c->mixed_graph = 0;
-    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr));
+    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr, nullptr, 1));
     cudaEventRecord(e0, c->stream);
-    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr));
+    BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr, nullptr, 1));
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;

@@ -57,6 +57,15 @@ class Solver:
         rep = B.bie_solve_frequencies(self.ctx, k, mode, surf)
         return surf, rep
 
+    def solve_frequencies_multi(self, k, dirs, mode: int = B.BIE_MODE_MIXED, out=None):
+        """Surface solutions [Nk][ndir][2][N] for several incident directions sharing each factor."""
+        k = np.ascontiguousarray(k, np.float64)
+        nd = np.atleast_2d(dirs).shape[0]
+        surf = out if out is not None else torch.empty((k.shape[0], nd, 2, self.N), dtype=torch.complex128,
+                                                       device=self._dev())
+        rep = B.bie_solve_frequencies_multi(self.ctx, k, dirs, mode, surf)
+        return surf, rep
+
     def eval_field(self, xobs: torch.Tensor, k, surf: torch.Tensor, mode: int = B.BIE_MODE_FP64, out=None):
         k = np.ascontiguousarray(k, np.float64)
         T = out if out is not None else torch.empty((k.shape[0], xobs.shape[0]), dtype=torch.complex128,
