@@ -82,3 +82,78 @@ def test_paper_soft_sphere_table_one(B):
         assert rel(sc[i, 1], Pn) <= 1e-6, (i, rep[i].flags)
         assert rel(Tc[i], oracle.field(w.mesh, w.k[i], P, Pn, pts)) <= 1e-6
     s.close()
+
+
+def _total_field_peak_ratio(s, B, w, surf):
+    """max over the observation points and the period of |p_inc + p_scat|, over max |p_inc|: the
+    scattered spectra plus the incident exp(i k d.x), synthesised with the pulse spectrum."""
+    xo = torch.tensor(w.xobs, dtype=torch.float64, device="cuda:0")
+    T = s.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
+    phase = torch.tensor(np.exp(1j * np.outer(w.k, w.xobs @ w.direction)), device="cuda:0")
+    S = s.pulse_spectrum(torch.tensor(w.pulses, device="cuda:0"))
+    m_all = np.arange(len(w.k))
+    p_tot = s.synthesize((T + phase).contiguous(), m_all, S, w.Nt)
+    p_inc = s.synthesize(phase.contiguous(), m_all, S, w.Nt)
+    return (p_tot.abs().max() / p_inc.abs().max()).item()
+
+
+def test_paper_two_spheres_amplification(B):
+    """Sec. 4.1, Fig. 6: two hard spheres 3a apart, 2N_c = 10: the total field exceeds the incident
+    maximum by up to 80 % (ratio 1.8, within 30 %)."""
+    from paper_1706_07919_gb300 import Solver
+    from workloads import config_paper_two_spheres
+    w = config_paper_two_spheres()
+    s = Solver(0)
+    s.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    s.set_incident_plane_wave(w.direction)
+    surf, rep = s.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    ratio = _total_field_peak_ratio(s, B, w, surf)
+    sc = surf.cpu().numpy()
+    for i in (7, 20):
+        P, _ = oracle.solve_frequency(w.mesh, w.k[i], D)
+        assert rel(sc[i, 0], P) <= 1e-6
+    s.close()
+    assert 1.8 * 0.7 <= ratio <= 1.8 * 1.3, ratio
+
+
+def test_bowl_against_oracle(B):
+    """The bowl geometry (Eq. dish, coarse revolution mesh, N = 338) through the mixed and FP64
+    paths against the oracle's solves and fields."""
+    from paper_1706_07919_gb300 import Solver
+    from workloads import bowl_mesh, bowl_inside
+    m = bowl_mesh(8, 12)
+    pts = np.array([[0.0, 0.3, -1.2], [0.5, -0.4, 0.9], [0.0, 0.0, -0.75], [1.3, 0.2, 0.1]])
+    assert not bowl_inside(pts, margin=0.05).any()
+    ks = np.array([0.0, 1.7, 3.75, 6.2])
+    s = Solver(0)
+    s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
+    s.set_incident_plane_wave(D)
+    xo = torch.tensor(pts, dtype=torch.float64, device="cuda:0")
+    for mode, tol in ((B.BIE_MODE_FP64, 1e-10), (B.BIE_MODE_MIXED, 1e-6)):
+        surf, _ = s.solve_frequencies(ks, mode)
+        T = s.eval_field(xo, ks, surf, mode).cpu().numpy()
+        sc = surf.cpu().numpy()
+        for i, k in enumerate(ks):
+            if k == 0.0:
+                assert np.abs(sc[i]).max() == 0.0  # hard body at k = 0
+                continue
+            P, Pn = oracle.solve_frequency(m, k, D)
+            assert rel(sc[i, 0], P) <= tol, (mode, k)
+            assert rel(T[i], oracle.field(m, k, P, Pn, pts)) <= tol, (mode, k)
+    s.close()
+
+
+def test_paper_bowl_focusing(B):
+    """Sec. 4.2, Figs. 7-8: the hard bowl tilted by 0.15 pi, 2N_c = 6, alpha = 0.001: hot spots
+    near the bowl raise the pressure to about 4.5 times the incident maximum (within 30 %)."""
+    from paper_1706_07919_gb300 import Solver
+    from workloads import config_paper_bowl
+    w = config_paper_bowl()
+    s = Solver(0)
+    s.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    s.set_incident_plane_wave(w.direction)
+    surf, rep = s.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    ratio = _total_field_peak_ratio(s, B, w, surf)
+    s.close()
+    assert all(r.backward_err <= 1e-10 for r in rep)
+    assert 4.5 * 0.7 <= ratio <= 4.5 * 1.3, ratio

@@ -223,3 +223,70 @@ def config_paper_sphere(bc: int = 1, Nc2: int = 4, alpha: float = 0.1, width: fl
     return Workload(f"paper_sphere_{'soft' if bc else 'hard'}", mesh, k, dk, np.array([0.0, 0.0, 1.0]), xobs,
                     pulses, Nf, T)
 
+
+
+def _yz_grid(n: int, half: float, centre=(0.0, 0.0)) -> np.ndarray:
+    g = np.linspace(-half, half, n)
+    Y, Z = np.meshgrid(g + centre[0], g + centre[1], indexing="ij")
+    return np.stack([np.zeros(n * n), Y.ravel(), Z.ravel()], axis=1)
+
+
+def config_paper_two_spheres(Nc2: int = 10, alpha: float = 0.1, width: float = 20.1, Nf: int = 128,
+                             freq: int = 5, grid: int = 80, half: float = 10.0) -> Workload:
+    """Sec. 4.1, Fig. 6: two sound-hard unit spheres 3a apart between centres along the propagation
+    direction (centres (0, 0, -1.5) and (0, 0, 1.5)), 1002 nodes each (N = 2004); the pulse of
+    Eq. (pulse) with 2N_c = 10 cycles, alpha = 0.1, w = 20.1a (k_0 a = 40 pi / 20.1), N_f = 128, the
+    64 frequencies k_m = 2 pi m / w; observation points on the 80 x 80 y-z grid over [-10a, 10a]^2
+    and on a finer 61 x 61 grid over [-1.5a, 1.5a] x [-3a, 3a] around the pair, outside both spheres
+    by at least 0.02a."""
+    s = ico_sphere(freq, 1.0, bc=0)
+    mesh = merge_meshes([scale_translate(s, 1.0, (0.0, 0.0, -1.5)), scale_translate(s, 1.0, (0.0, 0.0, 1.5))])
+    from .pulses import paper_sine_pulse
+    T = width
+    k0 = 8.0 * np.pi * (Nc2 / 2.0) / width
+    pulses = paper_sine_pulse(Nf, T, k0, Nc2, alpha, 0.0)[None, :]
+    dk = 2.0 * np.pi / width
+    k = dk * np.arange(0, Nf // 2, dtype=np.float64)
+    g = np.linspace(-1.5, 1.5, 61)
+    Y, Z = np.meshgrid(g, 2.0 * g, indexing="ij")
+    fine = np.stack([np.zeros(Y.size), Y.ravel(), Z.ravel()], axis=1)
+    pts = np.concatenate([_yz_grid(grid, half), fine])
+    keep = np.ones(len(pts), bool)
+    for cz in (-1.5, 1.5):
+        keep &= np.linalg.norm(pts - np.array([0.0, 0.0, cz]), axis=1) >= 1.02
+    return Workload("paper_two_spheres", mesh, k, dk, np.array([0.0, 0.0, 1.0]), pts[keep], pulses, Nf, T)
+
+
+def bowl_inside(points: np.ndarray, tilt: float = 0.15 * np.pi, margin: float = 0.0) -> np.ndarray:
+    """True where a point lies inside the bowl body of Eq. (dish) (axis tilted by `tilt` about x),
+    or within `margin` of it along the axis direction."""
+    c, s = np.cos(tilt), np.sin(tilt)
+    axis = np.array([0.0, s, c])
+    eta = points @ axis
+    rho = np.linalg.norm(points - eta[:, None] * axis[None, :], axis=1)
+    r = np.clip(rho, 0.0, 1.0)
+    half = 0.2 * np.sqrt(1.0 - r * r)
+    mid = -0.6 * r * r
+    return (rho < 1.0 + margin) & (eta > mid - half - margin) & (eta < mid + half + margin)
+
+
+def config_paper_bowl(Nc2: int = 6, alpha: float = 0.001, width: float = 20.1, Nf: int = 128,
+                      n_theta: int = 48, n_phi: int = 48, grid: int = 81, half: float = 2.0) -> Workload:
+    """Sec. 4.2, Figs. 7-8: the sound-hard bowl of Eq. (dish) (the closed curve xi = sin t,
+    eta = 0.2 cos t - 0.6 sin^2 t rotated about the eta axis), its axis turned 0.15 pi away from the
+    propagation direction +z, meshed by revolution (48 rings x 48 azimuths: E = 4512, N = 9026); the
+    pulse of Eq. (pulse) with 2N_c = 6, alpha = 0.001, w = 20.1a (k_0 a = 24 pi / 20.1), N_f = 128,
+    64 frequencies; observation points on an 81 x 81 y-z grid over [-2a, 2a]^2 (the plane that
+    holds the tilted axis) outside the body by at least 0.02a, and on the 80 x 80 grid of the
+    snapshots over [-10a, 10a]^2."""
+    from .meshes import bowl_mesh
+    from .pulses import paper_sine_pulse
+    mesh = bowl_mesh(n_theta, n_phi)
+    T = width
+    k0 = 8.0 * np.pi * (Nc2 / 2.0) / width
+    pulses = paper_sine_pulse(Nf, T, k0, Nc2, alpha, 0.0)[None, :]
+    dk = 2.0 * np.pi / width
+    k = dk * np.arange(0, Nf // 2, dtype=np.float64)
+    pts = np.concatenate([_yz_grid(grid, half), _yz_grid(80, 10.0)])
+    pts = pts[~bowl_inside(pts, margin=0.02)]
+    return Workload("paper_bowl", mesh, k, dk, np.array([0.0, 0.0, 1.0]), pts, pulses, Nf, T)

@@ -183,3 +183,99 @@ def merge_meshes(meshes: list[Mesh]) -> Mesh:
         off += m.N
     return Mesh(np.concatenate(nodes), np.concatenate(elems).astype(np.int32), np.concatenate(normals),
                 np.concatenate(bcs), np.concatenate(body))
+
+
+def revolution_mesh(profile, n_theta: int, n_phi: int, bc: int = 0) -> Mesh:
+    """Closed surface of revolution about the z axis from a profile curve.
+
+    profile(theta) -> (rho, z, drho, dz) for theta in [0, pi]: distance from the axis, height, and
+    their derivatives; rho(0) = rho(pi) = 0 (the poles) and rho > 0 in between.  The surface point
+    is (rho cos phi, rho sin phi, z).  Rings at theta_i = i pi / n_theta (i = 1 .. n_theta - 1) with
+    n_phi vertices each, fans of triangles at the two poles, quads between rings split in two.  Every
+    mid-edge node is the surface point at the middle of its edge in the (theta, phi) parameters, so
+    all nodes lie on the exact surface; node normals are the exact unit normals t_theta x t_phi
+    (pointing away from the enclosed body when the profile runs from the top pole down).
+    N = 2 E + 2 with E = 2 (n_theta - 1) n_phi."""
+    if n_theta < 2 or n_phi < 3:
+        raise ValueError("need n_theta >= 2 and n_phi >= 3")
+    index: dict[tuple[int, int], int] = {}
+    pts: list[np.ndarray] = []
+    nrm: list[np.ndarray] = []
+
+    def node(it2: int, ip2: int) -> int:
+        """Node at theta = it2 * pi / (2 n_theta), phi = ip2 * pi / n_phi (half-steps)."""
+        if it2 == 0 or it2 == 2 * n_theta:
+            key = (it2, 0)
+        else:
+            key = (it2, ip2 % (2 * n_phi))
+        if key not in index:
+            th = key[0] * np.pi / (2 * n_theta)
+            ph = key[1] * np.pi / n_phi
+            rho, z, drho, dz = profile(th)
+            if key[0] in (0, 2 * n_theta):
+                rho = 0.0
+            c, s = np.cos(ph), np.sin(ph)
+            p = np.array([rho * c, rho * s, z])
+            t_th = np.array([drho * c, drho * s, dz])
+            if key[0] in (0, 2 * n_theta):  # the normal on the axis: along +-z
+                n = np.array([0.0, 0.0, 1.0 if key[0] == 0 else -1.0])
+            else:
+                t_ph = np.array([-rho * s, rho * c, 0.0])
+                n = np.cross(t_th, t_ph)
+            index[key] = len(pts)
+            pts.append(p)
+            nrm.append(n / np.linalg.norm(n))
+        return index[key]
+
+    elems = []
+
+    poles = (0, 2 * n_theta)
+
+    def tri(a, b, c):  # vertices at even half-step coordinates; mid nodes at parametric midpoints
+        mids = []
+        for p, q in ((a, b), (b, c), (c, a)):
+            if p[0] in poles:    # an edge from a pole runs along the ring vertex's meridian
+                ip2 = q[1]
+            elif q[0] in poles:
+                ip2 = p[1]
+            else:
+                ip2 = (p[1] + q[1]) // 2
+            mids.append(node((p[0] + q[0]) // 2, ip2))
+        return [node(*a), node(*b), node(*c)] + mids
+
+    for j in range(n_phi):
+        j2, j3 = 2 * j, 2 * (j + 1)
+        elems.append(tri((0, j2), (2, j2), (2, j3)))                                  # top fan
+        elems.append(tri((2 * n_theta, j2), (2 * n_theta - 2, j3), (2 * n_theta - 2, j2)))  # bottom fan
+        for i in range(1, n_theta - 1):
+            a, b = (2 * i, j2), (2 * i, j3)
+            c, d = (2 * i + 2, j2), (2 * i + 2, j3)
+            elems.append(tri(a, c, d))
+            elems.append(tri(a, d, b))
+    nodes = np.array(pts)
+    normals = np.array(nrm)
+    el = np.array(elems, dtype=np.int64)
+    # orient every element so that its geometric normal agrees with the exact normal
+    v0, v1, v2 = nodes[el[:, 0]], nodes[el[:, 1]], nodes[el[:, 2]]
+    gn = np.cross(v1 - v0, v2 - v0)
+    ref = normals[el[:, 0]] + normals[el[:, 1]] + normals[el[:, 2]]
+    flip = np.einsum("ij,ij->i", gn, ref) < 0
+    el[flip] = el[flip][:, [0, 2, 1, 5, 4, 3]]
+    return Mesh(nodes, el.astype(np.int32), normals, np.full(nodes.shape[0], bc, dtype=np.uint8),
+                np.zeros(nodes.shape[0], np.int32))
+
+
+def bowl_profile(theta):
+    """The closed generating curve of the paper's acoustic bowl, Eq. (dish), for a = 1:
+    xi = sin(theta), eta = 0.2 cos(theta) - 0.6 sin(theta)^2, as (rho, z, drho, dz)."""
+    s, c = np.sin(theta), np.cos(theta)
+    return s, 0.2 * c - 0.6 * s * s, c, -0.2 * s - 1.2 * s * c
+
+
+def bowl_mesh(n_theta: int = 48, n_phi: int = 48, tilt: float = 0.15 * np.pi, bc: int = 0) -> Mesh:
+    """The hard bowl of Sec. 4.2: the curve of Eq. (dish) rotated about its eta axis, with that axis
+    turned by `tilt` (radians, about the x axis) away from the propagation direction +z."""
+    m = revolution_mesh(bowl_profile, n_theta, n_phi, bc)
+    c, s = np.cos(tilt), np.sin(tilt)
+    rot = np.array([[1.0, 0.0, 0.0], [0.0, c, s], [0.0, -s, c]])  # e_z -> (0, sin tilt, cos tilt)
+    return scale_translate(m, 1.0, (0.0, 0.0, 0.0), rot=rot)
