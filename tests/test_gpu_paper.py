@@ -50,7 +50,7 @@ def test_top_frequencies_match_oracle(B):
         sig[:, : Nt // 4] = 0.0
         S = s.pulse_spectrum(torch.tensor(sig, device="cuda:0"))
         Sfull = np.stack([oracle.dft(x) for x in sig])
-        for K in sorted({0, 1, 5, Nt // 4, Nt // 2 + 1}):
+        for K in sorted(K for K in {0, 1, 5, Nt // 4, Nt // 2 + 1} if K <= Nt // 2 + 1):
             got = s.top_frequencies(S, Nt, K)
             np.testing.assert_array_equal(got, oracle.top_frequencies(Sfull, K))
     s.close()
@@ -74,7 +74,10 @@ def test_paper_soft_sphere_table_one(B):
         sel = s.top_frequencies(S, w.Nt, int(K))
         np.testing.assert_array_equal(sel, oracle.top_frequencies(Sfull[None, :], int(K)))
         pK = s.synthesize(T[torch.tensor(sel, device="cuda:0")].contiguous(), sel, S, w.Nt).cpu().numpy()[0]
-        np.testing.assert_allclose(rms_percent(pK, pall), [r11, r40], rtol=0.3)
+        got = rms_percent(pK, pall)
+        print(f"Table I, K = {int(K)}: {got[0]:.2f} % at (0,0,-1.1a), {got[1]:.2f} % at (0,0,-4a) "
+              f"(printed {r11}, {r40})")
+        np.testing.assert_allclose(got, [r11, r40], rtol=0.3)
     # sampled wavenumbers against the oracle (the zero-frequency solve among them)
     Tc, sc = T.cpu().numpy(), surf.cpu().numpy()
     for i in (0, 13, 20, 47):
@@ -113,6 +116,7 @@ def test_paper_two_spheres_amplification(B):
         P, _ = oracle.solve_frequency(w.mesh, w.k[i], D)
         assert rel(sc[i, 0], P) <= 1e-6
     s.close()
+    print(f"two spheres 3a apart: peak total / peak incident = {ratio:.3f} (paper: up to 1.8)")
     assert 1.8 * 0.7 <= ratio <= 1.8 * 1.3, ratio
 
 
@@ -156,4 +160,5 @@ def test_paper_bowl_focusing(B):
     ratio = _total_field_peak_ratio(s, B, w, surf)
     s.close()
     assert all(r.backward_err <= 1e-10 for r in rep)
+    print(f"bowl: peak total / peak incident = {ratio:.3f} (paper: about 4.5)")
     assert 4.5 * 0.7 <= ratio <= 4.5 * 1.3, ratio
