@@ -48,12 +48,12 @@ def test_directions_share_the_factor(B, mode, tol):
         s.close()
         assert len(rep) == len(ks) * len(dirs)
         for i, k in enumerate(ks):
+            if np.abs(single[i]).max() == 0.0:  # a hard body at k = 0 scatters nothing
+                assert np.abs(surf[i]).max() == 0.0
+                continue
             assert rel(surf[i, 0], single[i]) <= tol
             for d, dv in enumerate(dirs):
                 P, Pn = oracle.solve_frequency(m, k, dv)
-                if k == 0.0 and not m.bc.any():
-                    assert np.abs(surf[i, d]).max() == 0.0
-                    continue
                 got = np.concatenate([surf[i, d, 0], surf[i, d, 1]])
                 assert rel(got, np.concatenate([P, Pn])) <= tol, (k, d, rep[i * len(dirs) + d].flags)
 
