@@ -15,6 +15,8 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   field                                   pinned: interior point source, conventional representation
   dft / synthesize                        pinned: numpy FFT, Gaussian closed form, Parseval
   top_frequencies                         pinned: numpy lexsort with ties; Table I of the paper
+  *_linear (3-node elements)              pinned: linear reproduction, entire-solution identity and
+                                          point source at second order, sphere series at 389 nodes
   full solve                              pinned: analytic rigid/soft sphere partial-wave series;
                                           k = 0: soft sphere -a/r, harmonic linear identity, limit k -> 0
   mlp_features                            pinned: closed-form values at chosen nodes
@@ -71,6 +73,10 @@ def _load():
             "or_dft": [i64, c_dp, c_dp],
             "or_synthesize": [i64, i64, c_dp, c_ip, i64, i64, c_dp, c_dp],
             "or_top_frequencies": [i64, i64, c_dp, i64, c_ip],
+            "or_assemble_raw_linear": [c_dp, i64, c_ip, i64, c_dp, dbl, i32, i32, c_dp, c_dp, c_dp, c_dp],
+            "or_assemble_system_linear": [c_dp, i64, c_ip, i64, c_dp, c_ip, dbl, c_dp, i32, i32, c_dp, c_dp],
+            "or_foot_points_linear": [c_dp, i64, c_ip, i64, c_dp, i64, c_ip, c_dp, c_dp],
+            "or_field_linear": [c_dp, i64, c_ip, i64, dbl, i32, c_dp, c_dp, c_dp, i64, c_ip, c_dp, c_dp, c_dp],
             "or_assemble_rows": [c_dp, i64, c_ip, i64, c_dp, c_ip, dbl, c_dp, i32, i32, c_dp, i64, c_dp, c_dp],
             "or_mlp_features": [c_dp, c_dp, i64, c_dp, i64, c_dp, c_dp, dbl, dbl, c_dp],
             "or_mlp_forward": [c_dp, c_dp, i64, c_dp],
@@ -84,6 +90,8 @@ def _load():
             f.restype = ctypes.c_int
         lib.or_shape6.argtypes = [dbl, dbl, c_dp, c_dp, c_dp]
         lib.or_shape6.restype = None
+        lib.or_shape3.argtypes = [dbl, dbl, c_dp, c_dp, c_dp]
+        lib.or_shape3.restype = None
         lib.or_num_threads.restype = ctypes.c_int
         lib.or_mlp_param_count.restype = ctypes.c_int64
         _lib = lib
@@ -112,6 +120,12 @@ def gauss_legendre01(n: int):
 def shape6(xi: float, eta: float):
     N, dx, de = np.zeros(6), np.zeros(6), np.zeros(6)
     _load().or_shape6(xi, eta, _p(N), _p(dx), _p(de))
+    return N, dx, de
+
+
+def shape3(xi: float, eta: float):
+    N, dx, de = np.zeros(3), np.zeros(3), np.zeros(3)
+    _load().or_shape3(xi, eta, _p(N), _p(dx), _p(de))
     return N, dx, de
 
 
@@ -235,6 +249,58 @@ def field(mesh, k: float, P: np.ndarray, Pn: np.ndarray, xp: np.ndarray, foot=No
     Pn = np.ascontiguousarray(Pn, np.complex128)
     _check(_load().or_field(_p(nodes), nodes.shape[0], _p(elems), elems.shape[0], float(k), ng, _p(P),
                             _p(Pn), _p(xp), M, _p(fe), _p(fx), _p(fy), _p(T)), "field")
+    return T
+
+
+# ---- linear 3-node elements (Sec. 4's cross-check): mesh.elems is [E][3] ---------------------
+def assemble_raw_linear(mesh, k: float, ng: int = 4, ng_near: int = 6):
+    nodes, elems, normals, _ = _mesh_arrays(mesh)
+    N, E = nodes.shape[0], elems.shape[0]
+    H = np.zeros((N, N), np.complex128)
+    Gm = np.zeros((N, N), np.complex128)
+    al = np.zeros(N, np.complex128)
+    be = np.zeros(N, np.complex128)
+    _check(_load().or_assemble_raw_linear(_p(nodes), N, _p(elems), E, _p(normals), float(k), ng, ng_near,
+                                          _p(H), _p(Gm), _p(al), _p(be)), "assemble_raw_linear")
+    return H, Gm, al, be
+
+
+def assemble_system_linear(mesh, k: float, direction, ng: int = 4, ng_near: int = 6):
+    nodes, elems, normals, bc = _mesh_arrays(mesh)
+    d = np.ascontiguousarray(direction, np.float64)
+    N, E = nodes.shape[0], elems.shape[0]
+    A = np.zeros((N, N), np.complex128)
+    b = np.zeros(N, np.complex128)
+    _check(_load().or_assemble_system_linear(_p(nodes), N, _p(elems), E, _p(normals), _p(bc), float(k), _p(d),
+                                             ng, ng_near, _p(A), _p(b)), "assemble_system_linear")
+    return A, b
+
+
+def solve_frequency_linear(mesh, k: float, direction, ng: int = 4, ng_near: int = 6):
+    A, b = assemble_system_linear(mesh, k, direction, ng, ng_near)
+    return surface_fields(mesh, k, direction, solve(A, b))
+
+
+def foot_points_linear(mesh, xp: np.ndarray):
+    nodes, elems, _, _ = _mesh_arrays(mesh)
+    xp = np.ascontiguousarray(xp, np.float64)
+    M = xp.shape[0]
+    fe, fx, fy = np.zeros(M, np.int32), np.zeros(M), np.zeros(M)
+    _check(_load().or_foot_points_linear(_p(nodes), nodes.shape[0], _p(elems), elems.shape[0], _p(xp), M,
+                                         _p(fe), _p(fx), _p(fy)), "foot_points_linear")
+    return fe, fx, fy
+
+
+def field_linear(mesh, k: float, P: np.ndarray, Pn: np.ndarray, xp: np.ndarray, ng: int = 4):
+    nodes, elems, _, _ = _mesh_arrays(mesh)
+    xp = np.ascontiguousarray(xp, np.float64)
+    fe, fx, fy = foot_points_linear(mesh, xp)
+    M = xp.shape[0]
+    T = np.zeros(M, np.complex128)
+    P = np.ascontiguousarray(P, np.complex128)
+    Pn = np.ascontiguousarray(Pn, np.complex128)
+    _check(_load().or_field_linear(_p(nodes), nodes.shape[0], _p(elems), elems.shape[0], float(k), ng, _p(P),
+                                   _p(Pn), _p(xp), M, _p(fe), _p(fx), _p(fy), _p(T)), "field_linear")
     return T
 
 

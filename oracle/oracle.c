@@ -93,6 +93,22 @@ void or_shape6(double xi, double eta, double* N, double* dNxi, double* dNeta) {
   }
 }
 
+void or_shape3(double xi, double eta, double* N, double* dNxi, double* dNeta) {
+  /* Linear interpolants on the 3-node triangle (Sec. 4: the cross-check with linear elements and
+   * linear interpolation): the barycentric coordinates themselves. */
+  N[0] = 1.0 - xi - eta;
+  N[1] = xi;
+  N[2] = eta;
+  if (dNxi) { dNxi[0] = -1.0; dNxi[1] = 1.0; dNxi[2] = 0.0; }
+  if (dNeta) { dNeta[0] = -1.0; dNeta[1] = 0.0; dNeta[2] = 1.0; }
+}
+
+/* Shape functions of an element with np = 6 (quadratic) or np = 3 (linear) nodes. */
+static void shape_n(int np, double xi, double eta, double* N, double* dNxi, double* dNeta) {
+  if (np == 3) or_shape3(xi, eta, N, dNxi, dNeta);
+  else or_shape6(xi, eta, N, dNxi, dNeta);
+}
+
 /* Reference coordinates of the six local nodes. */
 static const double REF_NODE[6][2] = {{0, 0}, {1, 0}, {0, 1}, {0.5, 0}, {0.5, 0.5}, {0, 0.5}};
 
@@ -133,14 +149,15 @@ int or_rule_near(int n, int a, double* xi, double* eta, double* w) {
   return c;
 }
 
-/* Isoparametric geometry of element e at (xi, eta): position, unit normal t1 x t2 / J, J. */
-static void elem_point(const double* nodes, const int32_t* el, double xi, double eta, double x[3],
+/* Isoparametric geometry of an element with np nodes at (xi, eta): position, unit normal
+ * t1 x t2 / J, J, and the np shape values. */
+static void elem_point(const double* nodes, const int32_t* el, int np, double xi, double eta, double x[3],
                        double nu[3], double* J, double Nv[6]) {
   double dx[6], de[6];
-  or_shape6(xi, eta, Nv, dx, de);
+  shape_n(np, xi, eta, Nv, dx, de);
   double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
   x[0] = x[1] = x[2] = 0.0;
-  for (int a = 0; a < 6; ++a) {
+  for (int a = 0; a < np; ++a) {
     const double* X = nodes + 3 * (int64_t)el[a];
     for (int d = 0; d < 3; ++d) {
       x[d] += Nv[a] * X[d];
@@ -173,7 +190,7 @@ static void make_rules(int ng, int ng_near, rules_t* r) {
 }
 
 /* Row i: Hrow[j], Gmrow[j] (accumulated) and alpha_i, beta_i. */
-static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E,
                           const double* normals, double k, const rules_t* ru, int64_t i, cplx* Hrow,
                           cplx* Gmrow, cplx* alpha_i, cplx* beta_i) {
   (void)N;
@@ -181,9 +198,9 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
   const double* nu0 = normals + 3 * i; /* its normal nu_i */
   cplx al = 0.0, be = 0.0;
   for (int64_t e = 0; e < E; ++e) {
-    const int32_t* el = elems + 6 * e;
-    int own = -1; /* local index of node i in element e, if any */
-    for (int a = 0; a < 6; ++a)
+    const int32_t* el = elems + (int64_t)np * e;
+    int own = -1; /* local index of node i in element e, if any (a vertex for np = 3) */
+    for (int a = 0; a < np; ++a)
       if (el[a] == i) own = a;
     const double *qx = ru->sxi, *qe = ru->seta, *qw = ru->sw;
     int nq = ru->nstd;
@@ -195,7 +212,7 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
     }
     for (int q = 0; q < nq; ++q) {
       double x[3], nu[3], J, Nv[6];
-      elem_point(nodes, el, qx[q], qe[q], x, nu, &J, Nv);
+      elem_point(nodes, el, np, qx[q], qe[q], x, nu, &J, Nv);
       double r[3] = {x[0] - xi0[0], x[1] - xi0[1], x[2] - xi0[2]};
       double R = sqrt(dot3(r, r));
       cplx eikr = cexp(I * k * R);
@@ -207,7 +224,7 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
       double g = cos(s), f = (k == 0.0) ? dot3(nu0, r) : sin(s) / k;
       double dg = -k * sin(s) * dot3(nu0, nu), df = cos(s) * dot3(nu0, nu);
       double wJ = qw[q] * J;
-      for (int a = 0; a < 6; ++a) {
+      for (int a = 0; a < np; ++a) {
         Hrow[el[a]] += wJ * Nv[a] * dG;
         Gmrow[el[a]] += wJ * Nv[a] * G;
       }
@@ -219,18 +236,18 @@ static void row_integrals(const double* nodes, int64_t N, const int32_t* elems, 
   *beta_i = be;
 }
 
-static int check_mesh(int64_t N, const int32_t* elems, int64_t E, double k, int ng, int ng_near) {
+static int check_mesh(int64_t N, const int32_t* elems, int np, int64_t E, double k, int ng, int ng_near) {
   if (N < 1 || E < 1 || !(k >= 0.0) || ng < 1 || ng > 16 || ng_near < 1 || ng_near > 16) return -1;
   for (int64_t e = 0; e < E; ++e)
-    for (int a = 0; a < 6; ++a)
-      if (elems[6 * e + a] < 0 || elems[6 * e + a] >= N) return -1;
+    for (int a = 0; a < np; ++a)
+      if (elems[np * e + a] < 0 || elems[np * e + a] >= N) return -1;
   return 0;
 }
 
-int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                    const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
-                    cplx* alpha, cplx* beta) {
-  if (check_mesh(N, elems, E, k, ng, ng_near)) return -1;
+static int assemble_raw_n(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E,
+                          const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
+                          cplx* alpha, cplx* beta) {
+  if (check_mesh(N, elems, np, E, k, ng, ng_near)) return -1;
   rules_t* ru = (rules_t*)malloc(sizeof(rules_t));
   if (!ru) return -3;
   make_rules(ng, ng_near, ru);
@@ -238,16 +255,16 @@ int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_
   memset(Gm, 0, sizeof(cplx) * N * N);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < N; ++i)
-    row_integrals(nodes, N, elems, E, normals, k, ru, i, H + i * N, Gm + i * N, alpha + i, beta + i);
+    row_integrals(nodes, N, elems, np, E, normals, k, ru, i, H + i * N, Gm + i * N, alpha + i, beta + i);
   free(ru);
   return 0;
 }
 
 /* Rows rows[0..nrows) of the system of or_assemble_system: A_rows [nrows][N], b_rows [nrows]. */
-int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                     const double* normals, const uint8_t* bc, double k, const double* dir, int ng,
-                     int ng_near, const int64_t* rows, int64_t nrows, cplx* A_rows, cplx* b_rows) {
-  if (check_mesh(N, elems, E, k, ng, ng_near)) return -1;
+static int assemble_rows_n(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E,
+                           const double* normals, const uint8_t* bc, double k, const double* dir, int ng,
+                           int ng_near, const int64_t* rows, int64_t nrows, cplx* A_rows, cplx* b_rows) {
+  if (check_mesh(N, elems, np, E, k, ng, ng_near)) return -1;
   for (int64_t t = 0; t < nrows; ++t)
     if (rows[t] < 0 || rows[t] >= N) return -1;
   rules_t* ru = (rules_t*)malloc(sizeof(rules_t));
@@ -271,7 +288,7 @@ int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64
       rc = -3;
     } else {
       cplx al, be;
-      row_integrals(nodes, N, elems, E, normals, k, ru, i, H, Gm, &al, &be);
+      row_integrals(nodes, N, elems, np, E, normals, k, ru, i, H, Gm, &al, &be);
       cplx bi = 0.0;
       for (int64_t j = 0; j < N; ++j) {
         cplx C = H[j] - (i == j ? 4.0 * PI + al : 0.0); /* multiplies P_j  */
@@ -294,9 +311,9 @@ int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64
   return rc;
 }
 
-int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                       const double* normals, const uint8_t* bc, double k, const double* dir,
-                       int ng, int ng_near, cplx* A, cplx* b) {
+static int assemble_system_n(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E,
+                             const double* normals, const uint8_t* bc, double k, const double* dir,
+                             int ng, int ng_near, cplx* A, cplx* b) {
   cplx* H = (cplx*)malloc(sizeof(cplx) * N * N);
   cplx* Gm = (cplx*)malloc(sizeof(cplx) * N * N);
   cplx* al = (cplx*)malloc(sizeof(cplx) * N);
@@ -306,7 +323,7 @@ int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int
     free(H); free(Gm); free(al); free(be); free(known);
     return -3;
   }
-  int rc = or_assemble_raw(nodes, N, elems, E, normals, k, ng, ng_near, H, Gm, al, be);
+  int rc = assemble_raw_n(nodes, N, elems, np, E, normals, k, ng, ng_near, H, Gm, al, be);
   if (rc == 0) {
     /* Known boundary values of the scattered field (Sec. 4): soft p_scat = -p_inc,
      * hard dp_scat/dn = -dp_inc/dn, for the unit plane wave p_inc = exp(i k d.x). */
@@ -333,6 +350,33 @@ int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int
   }
   free(H); free(Gm); free(al); free(be); free(known);
   return rc;
+}
+
+int or_assemble_raw(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                    const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
+                    cplx* alpha, cplx* beta) {
+  return assemble_raw_n(nodes, N, elems, 6, E, normals, k, ng, ng_near, H, Gm, alpha, beta);
+}
+int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc, double k, const double* dir, int ng,
+                     int ng_near, const int64_t* rows, int64_t nrows, cplx* A_rows, cplx* b_rows) {
+  return assemble_rows_n(nodes, N, elems, 6, E, normals, bc, k, dir, ng, ng_near, rows, nrows, A_rows, b_rows);
+}
+int or_assemble_system(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                       const double* normals, const uint8_t* bc, double k, const double* dir,
+                       int ng, int ng_near, cplx* A, cplx* b) {
+  return assemble_system_n(nodes, N, elems, 6, E, normals, bc, k, dir, ng, ng_near, A, b);
+}
+/* Linear 3-node elements (Sec. 4's cross-check): the same equations with or_shape3. */
+int or_assemble_raw_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                           const double* normals, double k, int ng, int ng_near, cplx* H, cplx* Gm,
+                           cplx* alpha, cplx* beta) {
+  return assemble_raw_n(nodes, N, elems, 3, E, normals, k, ng, ng_near, H, Gm, alpha, beta);
+}
+int or_assemble_system_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                              const double* normals, const uint8_t* bc, double k, const double* dir,
+                              int ng, int ng_near, cplx* A, cplx* b) {
+  return assemble_system_n(nodes, N, elems, 3, E, normals, bc, k, dir, ng, ng_near, A, b);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -407,32 +451,35 @@ static void clamp_tri(double* xi, double* eta) {
   }
 }
 
-static double dist2_at(const double* nodes, const int32_t* el, double xi, double eta, const double* p) {
+static double dist2_at(const double* nodes, const int32_t* el, int np, double xi, double eta, const double* p) {
   double x[3], nu[3], J, Nv[6];
-  elem_point(nodes, el, xi, eta, x, nu, &J, Nv);
+  elem_point(nodes, el, np, xi, eta, x, nu, &J, Nv);
   double d[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
   return dot3(d, d);
 }
 
-/* Damped Newton minimisation of |x(xi,eta) - p|^2 over the reference triangle. */
-static double project_elem(const double* nodes, const int32_t* el, const double* p, double* pxi,
+/* Damped Newton minimisation of |x(xi,eta) - p|^2 over the reference triangle (a linear element,
+ * np = 3, has no second derivatives). */
+static double project_elem(const double* nodes, const int32_t* el, int np, const double* p, double* pxi,
                            double* peta) {
   double xi = *pxi, eta = *peta;
-  double f = dist2_at(nodes, el, xi, eta, p);
+  double f = dist2_at(nodes, el, np, xi, eta, p);
   for (int it = 0; it < 100; ++it) {
     double Nv[6], dx[6], de[6];
-    or_shape6(xi, eta, Nv, dx, de);
+    shape_n(np, xi, eta, Nv, dx, de);
     double x[3] = {0, 0, 0}, t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, xx[3] = {0, 0, 0},
            xe[3] = {0, 0, 0}, ee[3] = {0, 0, 0};
-    for (int a = 0; a < 6; ++a) {
+    for (int a = 0; a < np; ++a) {
       const double* X = nodes + 3 * (int64_t)el[a];
       for (int d = 0; d < 3; ++d) {
         x[d] += Nv[a] * X[d];
         t1[d] += dx[a] * X[d];
         t2[d] += de[a] * X[d];
-        xx[d] += D2N[a][0] * X[d];
-        xe[d] += D2N[a][1] * X[d];
-        ee[d] += D2N[a][2] * X[d];
+        if (np == 6) {
+          xx[d] += D2N[a][0] * X[d];
+          xe[d] += D2N[a][1] * X[d];
+          ee[d] += D2N[a][2] * X[d];
+        }
       }
     }
     double r[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
@@ -452,14 +499,14 @@ static double project_elem(const double* nodes, const int32_t* el, const double*
       nxi = xi + s1;
       neta = eta + s2;
       clamp_tri(&nxi, &neta);
-      nf = dist2_at(nodes, el, nxi, neta, p);
+      nf = dist2_at(nodes, el, np, nxi, neta, p);
       accepted = 1;
     }
     for (int h = 0; h < 40 && !accepted; ++h) {
       nxi = xi + lam * s1;
       neta = eta + lam * s2;
       clamp_tri(&nxi, &neta);
-      nf = dist2_at(nodes, el, nxi, neta, p);
+      nf = dist2_at(nodes, el, np, nxi, neta, p);
       if (nf <= f) { accepted = 1; break; }
       lam *= 0.5;
     }
@@ -473,9 +520,9 @@ static double project_elem(const double* nodes, const int32_t* el, const double*
   return f;
 }
 
-int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                   const double* xp, int64_t M, int32_t* foot_elem, double* foot_xi,
-                   double* foot_eta) {
+static int foot_points_n(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E,
+                         const double* xp, int64_t M, int32_t* foot_elem, double* foot_xi,
+                         double* foot_eta) {
   if (N < 1 || E < 1 || M < 0) return -1;
 #pragma omp parallel for schedule(static)
   for (int64_t m = 0; m < M; ++m) {
@@ -491,13 +538,13 @@ int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t
     int32_t be = -1;
     double bxi = 0, beta_ = 0;
     for (int64_t e = 0; e < E; ++e) {
-      const int32_t* el = elems + 6 * e;
+      const int32_t* el = elems + (int64_t)np * e;
       int own = -1;
-      for (int a = 0; a < 6; ++a)
+      for (int a = 0; a < np; ++a)
         if (el[a] == best_node) own = a;
       if (own < 0) continue;
       double xi = REF_NODE[own][0], eta = REF_NODE[own][1];
-      double f = project_elem(nodes, el, p, &xi, &eta);
+      double f = project_elem(nodes, el, np, p, &xi, &eta);
       if (f < best) { best = f; be = (int32_t)e; bxi = xi; beta_ = eta; }
     }
     foot_elem[m] = be;
@@ -507,32 +554,43 @@ int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t
   return 0;
 }
 
+int or_foot_points(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                   const double* xp, int64_t M, int32_t* foot_elem, double* foot_xi,
+                   double* foot_eta) {
+  return foot_points_n(nodes, N, elems, 6, E, xp, M, foot_elem, foot_xi, foot_eta);
+}
+int or_foot_points_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                          const double* xp, int64_t M, int32_t* foot_elem, double* foot_xi,
+                          double* foot_eta) {
+  return foot_points_n(nodes, N, elems, 3, E, xp, M, foot_elem, foot_xi, foot_eta);
+}
+
 /* ------------------------------------------------------------------------------------------
  * Field at observation points, Eq. BRIEFdmn (S-only form: the S_inf integrals of g and f about
  * x0 and x_p cancel against the 4 pi [P0 g(x_p) + P0' f(x_p)] term, leaving 4 pi P0).
  * ------------------------------------------------------------------------------------------ */
-int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
-             const cplx* P, const cplx* Pn, const double* xp, int64_t M, const int32_t* foot_elem,
-             const double* foot_xi, const double* foot_eta, cplx* T) {
+static int field_n(const double* nodes, int64_t N, const int32_t* elems, int np, int64_t E, double k, int ng,
+                   const cplx* P, const cplx* Pn, const double* xp, int64_t M, const int32_t* foot_elem,
+                   const double* foot_xi, const double* foot_eta, cplx* T) {
   if (N < 1 || E < 1 || !(k >= 0.0) || ng < 1 || ng > 16) return -1;
   double sxi[256], seta[256], sw[256];
   int nq = or_rule_std(ng, sxi, seta, sw);
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t m = 0; m < M; ++m) {
     const double* p = xp + 3 * m;
-    const int32_t* el0 = elems + 6 * (int64_t)foot_elem[m];
+    const int32_t* el0 = elems + (int64_t)np * foot_elem[m];
     double x0[3], nu0[3], J0, N0[6];
-    elem_point(nodes, el0, foot_xi[m], foot_eta[m], x0, nu0, &J0, N0);
-    cplx P0 = 0.0, Pn0 = 0.0; /* quadratic interpolation at the foot point */
-    for (int a = 0; a < 6; ++a) { P0 += N0[a] * P[el0[a]]; Pn0 += N0[a] * Pn[el0[a]]; }
+    elem_point(nodes, el0, np, foot_xi[m], foot_eta[m], x0, nu0, &J0, N0);
+    cplx P0 = 0.0, Pn0 = 0.0; /* interpolation at the foot point (quadratic, or linear for np = 3) */
+    for (int a = 0; a < np; ++a) { P0 += N0[a] * P[el0[a]]; Pn0 += N0[a] * Pn[el0[a]]; }
     cplx sum = 0.0;
     for (int64_t e = 0; e < E; ++e) {
-      const int32_t* el = elems + 6 * e;
+      const int32_t* el = elems + (int64_t)np * e;
       for (int q = 0; q < nq; ++q) {
         double x[3], nu[3], J, Nv[6];
-        elem_point(nodes, el, sxi[q], seta[q], x, nu, &J, Nv);
+        elem_point(nodes, el, np, sxi[q], seta[q], x, nu, &J, Nv);
         cplx Pq = 0.0, Pnq = 0.0;
-        for (int a = 0; a < 6; ++a) { Pq += Nv[a] * P[el[a]]; Pnq += Nv[a] * Pn[el[a]]; }
+        for (int a = 0; a < np; ++a) { Pq += Nv[a] * P[el[a]]; Pnq += Nv[a] * Pn[el[a]]; }
         double rp[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
         double r0[3] = {x[0] - x0[0], x[1] - x0[1], x[2] - x0[2]};
         double Rp = sqrt(dot3(rp, rp)), R0 = sqrt(dot3(r0, r0));
@@ -551,6 +609,17 @@ int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, do
     T[m] = P0 + sum / (4.0 * PI);
   }
   return 0;
+}
+
+int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
+             const cplx* P, const cplx* Pn, const double* xp, int64_t M, const int32_t* foot_elem,
+             const double* foot_xi, const double* foot_eta, cplx* T) {
+  return field_n(nodes, N, elems, 6, E, k, ng, P, Pn, xp, M, foot_elem, foot_xi, foot_eta, T);
+}
+int or_field_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
+                    const cplx* P, const cplx* Pn, const double* xp, int64_t M, const int32_t* foot_elem,
+                    const double* foot_xi, const double* foot_eta, cplx* T) {
+  return field_n(nodes, N, elems, 3, E, k, ng, P, Pn, xp, M, foot_elem, foot_xi, foot_eta, T);
 }
 
 /* ------------------------------------------------------------------------------------------

@@ -28,6 +28,10 @@ int or_gauss_legendre01(int n, double* x, double* w);
 /* Quadratic 6-node shape functions and their parametric derivatives at (xi, eta) (Sec. 3). */
 void or_shape6(double xi, double eta, double* N, double* dNxi, double* dNeta);
 
+/* Linear 3-node shape functions (the barycentric coordinates) and their derivatives (Sec. 4: the
+ * cross-check with linear elements and linear interpolation). */
+void or_shape3(double xi, double eta, double* N, double* dNxi, double* dNeta);
+
 /* Standard rule: n*n collapsed (Duffy) Gauss-Legendre points on the reference triangle,
  * collapsed at vertex 0.  Returns the point count. */
 int or_rule_std(int n, double* xi, double* eta, double* w);
@@ -65,6 +69,17 @@ int or_assemble_rows(const double* nodes, int64_t N, const int32_t* elems, int64
                      int ng_near, const int64_t* rows, int64_t nrows, double _Complex* A_rows,
                      double _Complex* b_rows);
 
+/* The same three functions for linear 3-node elements (elems [E][3], vertices counter-clockwise
+ * seen from the fluid; flat geometry, linear interpolation of P and dP/dnu, or_shape3), with
+ * collocation at the vertices; the near rule of a vertex as for quadratic elements. */
+int or_assemble_raw_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                           const double* normals, double k, int ng, int ng_near,
+                           double _Complex* H, double _Complex* Gm, double _Complex* alpha,
+                           double _Complex* beta);
+int or_assemble_system_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                              const double* normals, const uint8_t* bc, double k, const double* dir,
+                              int ng, int ng_near, double _Complex* A, double _Complex* b);
+
 /* Dense complex LU with partial pivoting (largest modulus, ties to the lowest row), in place;
  * piv[k] = row swapped with row k.  Returns 0, or -4 on an exactly zero pivot. */
 int or_lu_factor(int64_t n, double _Complex* A, int64_t* piv);
@@ -92,6 +107,15 @@ int or_field(const double* nodes, int64_t N, const int32_t* elems, int64_t E, do
              const double _Complex* P, const double _Complex* Pn, const double* xp, int64_t M,
              const int32_t* foot_elem, const double* foot_xi, const double* foot_eta,
              double _Complex* T);
+
+/* or_foot_points and or_field for linear 3-node elements. */
+int or_foot_points_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                          const double* xp, int64_t M, int32_t* foot_elem, double* foot_xi,
+                          double* foot_eta);
+int or_field_linear(const double* nodes, int64_t N, const int32_t* elems, int64_t E, double k, int ng,
+                    const double _Complex* P, const double _Complex* Pn, const double* xp, int64_t M,
+                    const int32_t* foot_elem, const double* foot_xi, const double* foot_eta,
+                    double _Complex* T);
 
 /* Naive DFT of a sampled pulse with the sign of Eq. inverseFourier:
  * S_m = sum_n s_n exp(+2 pi i m n / Nt), m = 0..Nt-1. */

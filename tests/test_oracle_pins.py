@@ -516,3 +516,93 @@ def test_bowl_normals_are_perpendicular_to_the_surface():
             n = m.normals[e[a]]
             worst = max(worst, abs(n @ t1) / np.linalg.norm(t1), abs(n @ t2) / np.linalg.norm(t2))
     assert worst < 1.2e-2  # measured 8.4e-3 (second order: 3.9e-2 at 12 x 16, 2.2e-3 at 48 x 64)
+
+
+# ---------------- linear 3-node elements (Sec. 4's cross-check) --------------------------------
+def test_shape3_kronecker_and_linear_reproduction():
+    ref = [(0, 0), (1, 0), (0, 1)]
+    for a, (xi, eta) in enumerate(ref):
+        N, _, _ = oracle.shape3(xi, eta)
+        np.testing.assert_allclose(N, np.eye(3)[a], atol=0)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        xi, eta = rng.random(2) * 0.5
+        N, dx, de = oracle.shape3(xi, eta)
+        f = np.array([2.0 - 3.0 * x + 0.5 * y for x, y in ref])
+        assert abs(N @ f - (2.0 - 3.0 * xi + 0.5 * eta)) < 1e-14
+        assert abs(dx @ f + 3.0) < 1e-14 and abs(de @ f - 0.5) < 1e-14
+
+
+def _linear_residuals(m, k, u, du, with_4pi):
+    H, Gm, al, be = oracle.assemble_raw_linear(m, k)
+    c = 4 * np.pi if with_4pi else 0.0
+    res = H @ u - (c + al) * u - Gm @ du - be * du
+    return np.linalg.norm(res) / (4 * np.pi * np.linalg.norm(u))
+
+
+@pytest.mark.parametrize("k", [0.0, 1.5])
+def test_linear_elements_point_source_and_entire_solution(k):
+    """Flat elements with linear interpolation: an interior point source satisfies the full row
+    equation and exp(i k d.x) (or, at k = 0, a linear function) the one without S_inf, both up to
+    a discretisation error that falls at second order; -4 pi instead of +4 pi leaves O(1)."""
+    from workloads import uv_sphere_linear
+    s = np.array([0.2, -0.1, 0.3])
+    e_src, e_ent = [], []
+    for nt, nph in ((8, 16), (16, 32), (32, 64)):
+        m = uv_sphere_linear(nt, nph)
+        r = m.nodes - s
+        R = np.linalg.norm(r, axis=1)
+        u = np.exp(1j * k * R) / R
+        du = np.exp(1j * k * R) * (1j * k * R - 1) * np.einsum("ij,ij->i", r, m.normals) / R ** 3
+        e_src.append(_linear_residuals(m, k, u, du, True))
+        if nt == 16:
+            H, Gm, al, be = oracle.assemble_raw_linear(m, k)
+            wrong = H @ u - (-4 * np.pi + al) * u - Gm @ du - be * du
+            assert np.linalg.norm(wrong) / (4 * np.pi * np.linalg.norm(u)) > 1.5
+        if k > 0:
+            v = np.exp(1j * k * m.nodes @ D)
+            dv = 1j * k * (m.normals @ D) * v
+        else:
+            c = np.array([0.3, -0.5, 0.8])
+            v = (m.nodes @ c + 0.4).astype(complex)
+            dv = (m.normals @ c).astype(complex)
+        e_ent.append(_linear_residuals(m, k, v, dv, False))
+    for e in (e_src, e_ent):
+        assert e[0] / e[1] > 3.0 and e[1] / e[2] > 3.0, e
+    assert e_src[2] < 5e-3 and e_ent[2] < 5e-3
+
+
+@pytest.mark.parametrize("hard", [True, False])
+def test_linear_elements_sphere_series(hard):
+    """Sphere series at k = 1: second-order convergence on latitude-longitude meshes, and the
+    paper's 774-element / 389-node mesh within 3 % (measured 2.7 % hard, 2.4 % soft)."""
+    from workloads import uv_sphere_linear
+    k = 1.0
+    errs = []
+    for nt, nph in ((8, 16), (16, 32), (32, 64), (10, 43)):
+        m = uv_sphere_linear(nt, nph, bc=0 if hard else 1)
+        P, Pn = oracle.solve_frequency_linear(m, k, D)
+        if hard:
+            ex, got = an.scattered(m.nodes, k, hard=True), P
+        else:
+            ex, got = an.surface_normal_derivative(m.nodes, k, hard=False), Pn
+        errs.append(np.linalg.norm(got - ex) / np.linalg.norm(ex))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    assert errs[2] < 5e-3 and errs[3] < 3e-2, errs
+    assert m.N == 389 and m.E == 774
+
+
+def test_linear_field_reproduces_interior_point_source():
+    from workloads import uv_sphere_linear
+    m = uv_sphere_linear(32, 64)
+    k = 1.2
+    s = np.array([0.1, 0.2, -0.25])
+    r = m.nodes - s
+    R = np.linalg.norm(r, axis=1)
+    P = np.exp(1j * k * R) / R
+    Pn = np.exp(1j * k * R) * (1j * k * R - 1) * np.einsum("ij,ij->i", r, m.normals) / R ** 3
+    pts = shell_points(10, 1.3, 2.5, seed=7)
+    Rp = np.linalg.norm(pts - s, axis=1)
+    ex = np.exp(1j * k * Rp) / Rp
+    T = oracle.field_linear(m, k, P, Pn, pts)
+    assert np.linalg.norm(T - ex) / np.linalg.norm(ex) < 5e-3

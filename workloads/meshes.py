@@ -279,3 +279,28 @@ def bowl_mesh(n_theta: int = 48, n_phi: int = 48, tilt: float = 0.15 * np.pi, bc
     c, s = np.cos(tilt), np.sin(tilt)
     rot = np.array([[1.0, 0.0, 0.0], [0.0, c, s], [0.0, -s, c]])  # e_z -> (0, sin tilt, cos tilt)
     return scale_translate(m, 1.0, (0.0, 0.0, 0.0), rot=rot)
+
+
+def linear_from_quadratic(m: Mesh) -> Mesh:
+    """The linear 3-node mesh on the vertices of a quadratic mesh (flat triangles between the same
+    vertices, mid-edge nodes dropped, node numbering compacted in order of first use)."""
+    tri = m.elems[:, :3]
+    used = np.unique(tri)
+    remap = -np.ones(m.N, np.int64)
+    remap[used] = np.arange(used.size)
+    return Mesh(m.nodes[used].copy(), remap[tri].astype(np.int32), m.normals[used].copy(), m.bc[used].copy(),
+                None if m.body is None else m.body[used].copy())
+
+
+def sphere_profile(theta):
+    """The unit sphere as a profile for revolution_mesh: rho = sin t, z = cos t."""
+    return np.sin(theta), np.cos(theta), np.cos(theta), -np.sin(theta)
+
+
+def uv_sphere_linear(n_theta: int = 10, n_phi: int = 43, radius: float = 1.0, bc: int = 0) -> Mesh:
+    """Linear 3-node sphere mesh on a latitude-longitude grid: n_theta - 1 rings of n_phi vertices
+    and the two poles, E = 2 (n_theta - 1) n_phi flat triangles; the defaults give the 774 linear
+    elements and 389 nodes of the paper's cross-check (Sec. 4)."""
+    m = linear_from_quadratic(revolution_mesh(sphere_profile, n_theta, n_phi, bc))
+    return Mesh(m.nodes * radius, m.elems, m.normals, m.bc, m.body)
+
