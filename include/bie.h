@@ -184,6 +184,22 @@ int bie_set_quadrature(bie_ctx* ctx, int ng, int ng_near);
 int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
                      const double* normals, const uint8_t* bc);
 
+/* Surface mesh of linear 3-node elements (Sec. 4: the paper's cross-check of its quadratic-element
+ * results with 774 flat linear elements and 389 nodes, linear interpolation on each element):
+ *   nodes host f64 [N][3], elems host i32 [E][3] (vertices counter-clockwise seen from the fluid),
+ *   normals host f64 [N][3] or NULL (as bie_set_geometry), bc host u8 [N]; every element must
+ *   carry one boundary condition on its three vertices.
+ * The library forms the flat quadratic image of the mesh (one mid-edge node per edge at its
+ * midpoint; on it, quadratic interpolation of the vertex values' linear interpolant is exact),
+ * assembles that system with its own kernels and reduces it to the vertex unknowns (rows of the
+ * vertices, each mid-edge column shared half and half by its two vertices) -- exactly the
+ * linear-element system.  Afterwards bie_assemble returns the [N][N] linear system,
+ * bie_solve_frequencies (BIE_MODE_FP64 only) writes surf [Nk][2][N] at the vertices, and
+ * bie_eval_field takes that surf (interpolated linearly onto the image for Eq. BRIEFdmn).
+ * Errors: as bie_set_geometry; INVALID_ARG for an element with two conditions. */
+int bie_set_geometry_linear(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                            const double* normals, const uint8_t* bc);
+
 /* Direction d (host f64[3], normalised here) of the incident plane wave exp(i k d.x) (Sec. 4).
  * Default (0, 0, 1).  Errors: INVALID_ARG for a zero or non-finite vector. */
 int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);

@@ -39,7 +39,7 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
             "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
             "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks",
-            "bie_top_frequencies", "bie_solve_frequencies_multi"]
+            "bie_top_frequencies", "bie_solve_frequencies_multi", "bie_set_geometry_linear"]
 
 
 class BieReport(ctypes.Structure):
@@ -130,6 +130,7 @@ def load(path: str | None = None):
         "bie_measure_peaks": ([i32, vp], i32),
         "bie_top_frequencies": ([vp, vp, i64, i64, i64, vp], i32),
         "bie_solve_frequencies_multi": ([vp, vp, i64, vp, i64, i32, vp, vp], i32),
+        "bie_set_geometry_linear": ([vp, vp, i64, vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -188,6 +189,17 @@ def bie_set_geometry(ctx: int, nodes, elems, normals, bc) -> None:
     nrm = None if normals is None else np.ascontiguousarray(normals, np.float64)
     _check(load().bie_set_geometry(ctx, _hp(nodes), nodes.shape[0], _hp(elems), elems.shape[0],
                                    None if nrm is None else _hp(nrm), _hp(bc)))
+
+
+def bie_set_geometry_linear(ctx: int, nodes, elems, normals, bc) -> None:
+    nodes = np.ascontiguousarray(nodes, np.float64)
+    elems = np.ascontiguousarray(elems, np.int32)
+    if elems.ndim != 2 or elems.shape[1] != 3:
+        raise ValueError("linear elements are [E][3]")
+    bc = np.ascontiguousarray(bc, np.uint8)
+    nrm = None if normals is None else np.ascontiguousarray(normals, np.float64)
+    _check(load().bie_set_geometry_linear(ctx, _hp(nodes), nodes.shape[0], _hp(elems), elems.shape[0],
+                                          None if nrm is None else _hp(nrm), _hp(bc)))
 
 
 def bie_set_incident_plane_wave(ctx: int, direction) -> None:

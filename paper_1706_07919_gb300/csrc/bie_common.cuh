@@ -96,6 +96,12 @@ struct bie_ctx {
   double* normals = nullptr;   // [N][3]
   uint8_t* bc = nullptr;       // [N]
   uint8_t* bc_flip = nullptr;  // [N] 1 - bc: assembles the known-column matrix (several directions)
+  // linear 3-node elements (bie_set_geometry_linear): the geometry above is their flat quadratic
+  // image (N = lin_N vertices, then one mid-edge node per edge); 0 for quadratic meshes
+  int64_t lin_N = 0;
+  int32_t* lin_adj_off = nullptr;  // [lin_N + 1] CSR: mid-edge nodes next to each vertex
+  int32_t* lin_adj = nullptr;
+  int32_t* lin_mid = nullptr;      // [2][N - lin_N] the two vertices of each mid-edge node
   std::vector<double> h_nodes, h_normals;
   std::vector<int32_t> h_elems;
   std::vector<uint8_t> h_bc;
@@ -165,6 +171,7 @@ struct bie_ctx {
   bie::DeviceBuf work2;  // FFT twiddles
   bie::DeviceBuf work3;  // foot points, field scratch, synthesis indices
   bie::DeviceBuf work4;  // learned mode: the anchors' factors, permutations and solutions
+  bie::DeviceBuf work5;  // linear elements: surface values interpolated onto the flat quadratic image
 };
 
 namespace bie {

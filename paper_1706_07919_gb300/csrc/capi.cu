@@ -103,6 +103,9 @@ int pulse_spectrum(bie_ctx* c, const double* s, int64_t P, int n, cd* Sout);
 int synthesize(bie_ctx* c, const cd* T, const int64_t* midx_dev, int nk, int64_t M, const cd* Sp, int64_t P, int n,
                void* out, int out_dtype);
 int top_frequencies(bie_ctx* c, const cd* S, int64_t P, int nm, int K, int64_t* midx_dev);
+int solve_fp64_linear(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
+int assemble_linear_one(bie_ctx* c, double k, cd* A_out, cd* b_out);
+int expand_linear(bie_ctx* c, const cd* surf_lin, int nk, cd* surf_q);
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
                 int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir);
 int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
@@ -121,13 +124,15 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
 
 static void free_geometry(bie_ctx* c) {
   void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
-                  c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear, c->bc_flip};
+                  c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear, c->bc_flip,
+                  c->lin_adj_off, c->lin_adj, c->lin_mid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->nshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
   c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr; c->bc_flip = nullptr;
+  c->lin_adj_off = nullptr; c->lin_adj = nullptr; c->lin_mid = nullptr; c->lin_N = 0;
   c->far_r2 = 0.0;
   c->uniform_bc = -1;
   c->has_geom = false;
@@ -337,6 +342,7 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c->work2);
   free_buf(c->work3);
   free_buf(c->work4);
+  free_buf(c->work5);
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -447,9 +453,8 @@ int bie_set_incident_plane_wave(bie_ctx* c, const double* dir) {
   return BIE_OK;
 }
 
-int bie_set_geometry(bie_ctx* c, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
-                     const double* normals, const uint8_t* bc) {
-  BIE_TRY(check_ctx(c, false));
+int set_geometry_impl(bie_ctx* c, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                      const double* normals, const uint8_t* bc) {
   if (!nodes || !elems || !bc) return fail(BIE_ERR_INVALID_ARG, "NULL nodes, elems or bc");
   if (N < 3 || E < 1) return fail(BIE_ERR_INVALID_ARG, "need N >= 3 and E >= 1");
   if (N > (int64_t)1 << 30 || E > (int64_t)1 << 28) return fail(BIE_ERR_INVALID_ARG, "mesh too large");
@@ -481,10 +486,17 @@ int bie_set_geometry(bie_ctx* c, const double* nodes, int64_t N, const int32_t* 
   return BIE_OK;
 }
 
+int bie_set_geometry(bie_ctx* c, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
+                     const double* normals, const uint8_t* bc) {
+  BIE_TRY(check_ctx(c, false));
+  return set_geometry_impl(c, nodes, N, elems, E, normals, bc);
+}
+
 int bie_assemble(bie_ctx* c, double k, void* A_out, void* b_out) {
   BIE_TRY(check_ctx(c, true));
   if (!A_out || !b_out) return fail(BIE_ERR_INVALID_ARG, "NULL output");
   BIE_TRY(check_k(&k, 1));
+  if (c->lin_N > 0) return assemble_linear_one(c, k, (cd*)A_out, (cd*)b_out);
   const int64_t N = c->N;
   BIE_TRY(ensure_buf(c->work, (size_t)N * 4 * sizeof(cd) + 64));
   double* kdev = (double*)((char*)c->work.p + (size_t)N * 4 * sizeof(cd));
@@ -499,6 +511,10 @@ int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, voi
   BIE_TRY(check_k(k, Nk, mode != BIE_MODE_LEARNED));
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
+  if (c->lin_N > 0) {
+    if (mode != BIE_MODE_FP64) return fail(BIE_ERR_INVALID_ARG, "linear elements: BIE_MODE_FP64 only");
+    return solve_fp64_linear(c, k, Nk, (cd*)surf_out, rep);
+  }
   if (mode == BIE_MODE_FP64) return solve_fp64(c, k, Nk, (cd*)surf_out, rep);
   if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr, nullptr, 1);
   if (mode == BIE_MODE_LEARNED) return solve_learned(c, k, Nk, (cd*)surf_out, rep);
@@ -617,10 +633,16 @@ int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, i
   if (bad != ~0ull)
     return fail(BIE_ERR_INVALID_ARG, "observation point " + std::to_string(bad) +
                                          " lies inside a scatterer (Eq. BRIEFdmn needs points in the fluid)");
+  const int64_t Ns = c->lin_N > 0 ? c->lin_N : c->N;  // nodes of the caller's surface values
+  if (c->lin_N > 0) BIE_TRY(ensure_buf(c->work5, (size_t)kb * 2 * c->N * sizeof(cd)));
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    const cd* s = (const cd*)surf + k0 * 2 * c->N;
+    const cd* s = (const cd*)surf + k0 * 2 * Ns;
+    if (c->lin_N > 0) {  // linear elements: interpolate onto the flat quadratic image
+      BIE_TRY(expand_linear(c, s, nk, (cd*)c->work5.p));
+      s = (const cd*)c->work5.p;
+    }
     cd* T = (cd*)T_out + k0 * M;
     if (mode == BIE_MODE_FP64)
       BIE_TRY(field64(c, kdev, nk, s, xobs, M, foot_elem, foot, T, scratch));
@@ -695,6 +717,7 @@ int bie_solve_frequencies_multi(bie_ctx* c, const double* k, int64_t Nk, const d
   }
   if (Nk == 0) return BIE_OK;
   if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
+  if (c->lin_N > 0) return fail(BIE_ERR_INVALID_ARG, "linear elements: one direction per call (bie_solve_frequencies)");
   if (mode == BIE_MODE_FP64) return solve_fp64_multi(c, k, Nk, d.data(), (int)ndir, (cd*)surf_out, rep);
   if (mode == BIE_MODE_MIXED)
     return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr, d.data(), (int)ndir);

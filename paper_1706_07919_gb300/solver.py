@@ -38,6 +38,11 @@ class Solver:
         B.bie_set_geometry(self.ctx, nodes, elems, normals, bc)
         self.N = int(np.asarray(nodes).shape[0])
 
+    def set_geometry_linear(self, nodes, elems, normals, bc):
+        """Linear 3-node elements (elems [E][3]); outputs are per vertex."""
+        B.bie_set_geometry_linear(self.ctx, nodes, elems, normals, bc)
+        self.N = int(np.asarray(nodes).shape[0])
+
     def set_option(self, name: str, value: float):
         B.bie_set_option(self.ctx, name, value)
 
