@@ -411,7 +411,7 @@ __global__ void k_foot_points(const double* __restrict__ nodes, int64_t N, const
   double p[3] = {xp[3 * m], xp[3 * m + 1], xp[3 * m + 2]};
   int64_t best_node = 0;
   double bd = INFINITY;
-  for (int64_t j = 0; j < N; ++j) {
+  for (int64_t j = 0; j < N; ++j) {  // N: the nodes searched (the vertices only for linear elements)
     double d0 = nodes[3 * j] - p[0], d1 = nodes[3 * j + 1] - p[1], d2 = nodes[3 * j + 2] - p[2];
     double d = d0 * d0 + d1 * d1 + d2 * d2;
     if (d < bd) { bd = d; best_node = j; }
@@ -449,8 +449,11 @@ __global__ void k_foot_points(const double* __restrict__ nodes, int64_t N, const
 int launch_foot_points(bie_ctx* c, const double* xp, int64_t M, int32_t* foot_elem, double* foot,
                        unsigned long long* first_inside) {
   if (M == 0) return BIE_OK;
-  BIE_LAUNCH(k_foot_points<<<(unsigned)((M + 127) / 128), 128, 0, c->stream>>>(c->nodes, c->N, c->elems, c->n2e_off, c->n2e, xp,
-                                                                     M, foot_elem, foot, first_inside));
+  // linear elements: the nearest vertex starts the search (their flat image's mid-edge nodes are
+  // not nodes of the linear mesh), as the closest-point reading prescribes for that mesh
+  const int64_t nsearch = c->lin_N > 0 ? c->lin_N : c->N;
+  BIE_LAUNCH(k_foot_points<<<(unsigned)((M + 127) / 128), 128, 0, c->stream>>>(c->nodes, nsearch, c->elems, c->n2e_off, c->n2e,
+                                                                     xp, M, foot_elem, foot, first_inside));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
