@@ -324,6 +324,8 @@ def run_ours(args):
         line["uneven"] = run_uneven(args, dev)
     if not args.no_large:
         line["large"] = run_large(args, dev, stream)
+    if not args.no_paper:
+        line["paper"] = run_paper(args, dev, stream)
     if grp.is_root:
         line["cpu_baseline"] = cpu
         print(json.dumps(line))
@@ -390,6 +392,92 @@ def run_learned(args, dev, stream):
             "zero_start_krylov_fallback": info_z["krylov_fallback"],
             "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,
             "timing": "wall clock around each synchronising call (host-side setup included)"}
+
+
+def run_paper(args, dev, stream):
+    """The paper's own experiments (Sec. 4) on the device: (1) the 1002-node soft sphere with the
+    pulse of Eq. (pulse) (2N_c = 4, alpha = 0.1, w = 20.1a), 64 frequencies, the field at the two
+    points of Table I and the 80 x 80 snapshot grid, synthesised from all frequencies and from the
+    5, 10, 20 dominant ones (chosen on the device): Table I's RMS errors; (2) eight incident
+    directions on the same sphere sharing each wavenumber's factor, against eight separate sweeps;
+    (3) the peak total-field amplification of the two hard spheres 3a apart and of the tilted hard
+    bowl.  Wall clock around synchronising calls."""
+    import torch
+
+    from workloads import config_paper_sphere, config_paper_two_spheres, config_paper_bowl
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+
+    out = {}
+    w = config_paper_sphere(bc=1)
+    sol = Solver(dev.index if dev.index is not None else 0, stream)
+    sol.set_geometry(w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc)
+    sol.set_incident_plane_wave(w.direction)
+    xo = torch.tensor(w.xobs, dtype=torch.float64, device=dev)
+    pulses = torch.tensor(w.pulses, dtype=torch.float64, device=dev)
+    sol.solve_frequencies(w.k[:8], B.BIE_MODE_MIXED)  # warm-up
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    surf, _ = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+    T = sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
+    S = sol.pulse_spectrum(pulses)
+    m_all = np.arange(len(w.k))
+    p_all = sol.synthesize(T, m_all, S, w.Nt)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t
+    pall = p_all[0, :2].cpu().numpy()
+    rms = {}
+    for K in (5, 10, 20):
+        sel = sol.top_frequencies(S, w.Nt, K)
+        pK = sol.synthesize(T[torch.tensor(sel, device=dev)].contiguous(), sel, S, w.Nt)[0, :2].cpu().numpy()
+        r = 100.0 * np.sqrt(((pK - pall) ** 2).mean(axis=-1)) / np.abs(pall).max(axis=-1)
+        rms[str(K)] = [float(r[0]), float(r[1])]
+    out["sphere_table1"] = {"workload": "soft sphere N1002, Eq. pulse 2Nc=4 alpha=0.1 w=20.1, 64 k, 6350 points x 128 steps",
+                            "rms_percent_at_-1.1a_-4a": rms, "printed": {"5": [4.4, 4.9], "10": [1.6, 1.7], "20": [0.5, 0.6]},
+                            "solves_per_s": len(w.k) / dt,
+                            "space_time_pts_per_s": w.xobs.shape[0] * w.Nt / dt}
+    # several incident directions sharing each factor
+    rng = np.random.Generator(np.random.PCG64(6001))
+    dirs = rng.standard_normal((8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    sm, _ = sol.solve_frequencies_multi(w.k, dirs, B.BIE_MODE_MIXED)
+    torch.cuda.synchronize(dev)
+    t_multi = time.perf_counter() - t
+    t = time.perf_counter()
+    errs = []
+    for d in range(len(dirs)):
+        sol.set_incident_plane_wave(dirs[d])
+        s1, _ = sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+        errs.append((torch.linalg.norm(s1 - sm[:, d]) / torch.linalg.norm(s1)).item())
+    torch.cuda.synchronize(dev)
+    t_sep = time.perf_counter() - t
+    sol.close()
+    out["directions"] = {"workload": "soft sphere N1002, 64 k x 8 seeded directions", "solves_per_s": 64 * 8 / t_multi,
+                         "separate_sweeps_solves_per_s": 64 * 8 / t_sep, "speedup": t_sep / t_multi,
+                         "max_rel_diff_vs_separate": max(errs)}
+    # amplification of the total field
+    for name, w2, paper in (("two_spheres_3a", config_paper_two_spheres(), 1.8), ("bowl", config_paper_bowl(), 4.5)):
+        s2 = Solver(dev.index if dev.index is not None else 0, stream)
+        s2.set_geometry(w2.mesh.nodes, w2.mesh.elems, w2.mesh.normals, w2.mesh.bc)
+        s2.set_incident_plane_wave(w2.direction)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        surf2, _ = s2.solve_frequencies(w2.k, B.BIE_MODE_MIXED)
+        xo2 = torch.tensor(w2.xobs, dtype=torch.float64, device=dev)
+        T2 = s2.eval_field(xo2, w2.k, surf2, B.BIE_MODE_MIXED)
+        inc = torch.tensor(np.exp(1j * np.outer(w2.k, w2.xobs @ w2.direction)), device=dev)
+        S2 = s2.pulse_spectrum(torch.tensor(w2.pulses, device=dev))
+        m2 = np.arange(len(w2.k))
+        ptot = s2.synthesize((T2 + inc).contiguous(), m2, S2, w2.Nt)
+        pinc = s2.synthesize(inc.contiguous(), m2, S2, w2.Nt)
+        ratio = (ptot.abs().max() / pinc.abs().max()).item()
+        torch.cuda.synchronize(dev)
+        out[name] = {"N": int(w2.mesh.N), "points": int(w2.xobs.shape[0]), "peak_total_over_incident": ratio,
+                     "paper": paper, "seconds": time.perf_counter() - t}
+        s2.close()
+    return out
 
 
 def run_large(args, dev, stream):
@@ -727,6 +815,8 @@ def main():
                     help="skip the lattice (N = 20544) sample")
     ap.add_argument("--large-nk", dest="large_nk", type=int, default=8,
                     help="wavenumbers of the lattice sample")
+    ap.add_argument("--no-paper", dest="no_paper", action="store_true",
+                    help="skip the paper's own experiments (Table I, directions, amplification)")
     ap.add_argument("--no-uneven", dest="no_uneven", action="store_true",
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
