@@ -366,9 +366,17 @@ def run_learned(args, dev, stream):
     t_l, rep_l = timed(B.BIE_MODE_LEARNED, surf)
     info = sol.learned_info()
     t_d, _ = timed(B.BIE_MODE_MIXED, surf_d)
-    sol.set_option("learned.x0", 0)
-    t_z, _ = timed(B.BIE_MODE_LEARNED, surf_d)
-    info_z = sol.learned_info()
+    starts = {}
+    for code, name in ((0, "zero"), (2, "nearest_anchor"), (3, "anchor_interpolant")):
+        sol.set_option("learned.x0", code)
+        t_s, _ = timed(B.BIE_MODE_LEARNED, surf_d)
+        inf = sol.learned_info()
+        starts[name] = {"solves_per_s": Nk / t_s, "mean_arnoldi_steps": inf["mean_iters"],
+                        "x0_rel_err": inf["x0_rel_err"], "krylov_fallback": inf["krylov_fallback"]}
+    starts["network"] = {"solves_per_s": Nk / t_l, "mean_arnoldi_steps": info["mean_iters"],
+                         "x0_rel_err": info["x0_rel_err"], "krylov_fallback": info["krylov_fallback"]}
+    t_z = Nk / starts["zero"]["solves_per_s"]
+    info_z = {"mean_iters": starts["zero"]["mean_arnoldi_steps"], "krylov_fallback": starts["zero"]["krylov_fallback"]}
     sol.set_option("learned.x0", 1)
     # accuracy: sampled wavenumbers that GMRES solved, against the FP64 path
     rng = np.random.Generator(np.random.PCG64(3002))
@@ -390,6 +398,7 @@ def run_learned(args, dev, stream):
                                                        "gmres_ms", "estimate_ms", "redo_ms")},
             "zero_start_mean_arnoldi_steps": info_z["mean_iters"],
             "zero_start_krylov_fallback": info_z["krylov_fallback"],
+            "starts": starts,
             "sampled_k": [float(w.k[i]) for i in sample], "max_rel_err_surface_vs_fp64": max(errs) if errs else None,
             "timing": "wall clock around each synchronising call (host-side setup included)"}
 

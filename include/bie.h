@@ -232,7 +232,9 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "learned.stride"       every stride-th wavenumber of the call is an anchor (>= 2, default 8;
  *                          indices stride-1, 2 stride-1, ...; the last index if none)
  *   "learned.x0"           initial guess of the GMRES solves: 1 the network (default), 0 zero,
- *                          2 the nearest anchor's solution
+ *                          2 the nearest anchor's solution, 3 the bracketing anchors' solutions
+ *                          demodulated by exp(-i k_a d.x), interpolated linearly in k and
+ *                          modulated with exp(i k d.x)
  *   "learned.epochs"       training epochs (0..100000, default 60)
  *   "learned.batch"        rows per minibatch (128..1048576, rounded up to 128; default 8192)
  *   "learned.lr", "learned.lr_min"  Adam step size, cosine-decayed to lr_min (default 2e-3, 1e-4)

@@ -406,8 +406,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value < 2 || value > 1e6) return fail(BIE_ERR_INVALID_ARG, "learned.stride must be in [2, 1e6]");
     c->learned_stride = (int)value;
   } else if (n == "learned.x0") {
-    if (value != 0.0 && value != 1.0 && value != 2.0)
-      return fail(BIE_ERR_INVALID_ARG, "learned.x0 must be 0 (zero), 1 (network) or 2 (nearest anchor)");
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+      return fail(BIE_ERR_INVALID_ARG,
+                  "learned.x0 must be 0 (zero), 1 (network), 2 (nearest anchor) or 3 (anchor interpolant)");
     c->learned_x0 = (int)value;
   } else if (n == "learned.epochs") {
     if (value < 0 || value > 100000) return fail(BIE_ERR_INVALID_ARG, "learned.epochs must be in [0, 100000]");

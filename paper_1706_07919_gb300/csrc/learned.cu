@@ -46,6 +46,28 @@ __global__ void k_unknowns_from_surf(const cd* __restrict__ surf, const int32_t*
   x[(int64_t)kk * N + i] = surf[((int64_t)sel[kk] * 2 + (bc[i] ? 1 : 0)) * N + i];
 }
 
+// Initial guess from the two anchors that bracket k (the nearest one twice at the ends): their
+// unknowns demodulated by the incident phase, u exp(-i k_a d.x), interpolated linearly in k, and
+// modulated again with exp(i k d.x).  par[kk] = {k, k_lo, k_hi, t}, t the weight of the upper anchor.
+__global__ void k_interp_start(const cd* __restrict__ surf, const int32_t* __restrict__ lo,
+                               const int32_t* __restrict__ hi, const double4* __restrict__ par,
+                               const uint8_t* __restrict__ bc, const double* __restrict__ nodes, double dx, double dy,
+                               double dz, int64_t N, cd* __restrict__ x) {
+  const int kk = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double4 q = par[kk];
+  const double dxi = dx * nodes[3 * i] + dy * nodes[3 * i + 1] + dz * nodes[3 * i + 2];
+  const int f = bc[i] ? 1 : 0;
+  const cd a = surf[((int64_t)lo[kk] * 2 + f) * N + i], b = surf[((int64_t)hi[kk] * 2 + f) * N + i];
+  double s, c;
+  sincos((q.x - q.y) * dxi, &s, &c);  // exp(i (k - k_lo) d.x)
+  const cd ua = {a.re * c - a.im * s, a.re * s + a.im * c};
+  sincos((q.x - q.z) * dxi, &s, &c);
+  const cd ub = {b.re * c - b.im * s, b.re * s + b.im * c};
+  x[(int64_t)kk * N + i] = {(1.0 - q.w) * ua.re + q.w * ub.re, (1.0 - q.w) * ua.im + q.w * ub.im};
+}
+
 // out[kk] = ||a - b|| / ||b|| over the n entries of system kk (one CTA each)
 __global__ void k_rel_diff(const cd* __restrict__ a, const cd* __restrict__ b, int64_t n, double* __restrict__ out) {
   __shared__ double red[2][32];
@@ -235,6 +257,8 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   int32_t* sel = (int32_t*)take((size_t)kb * 4);
   int32_t* dst = (int32_t*)take((size_t)kb * 4);
   double* rel = (double*)take((size_t)kb * 2 * 8);
+  int32_t* sel_hi = (int32_t*)take((size_t)kb * 4);
+  double4* ipar = (double4*)take((size_t)kb * sizeof(double4));
   void* gscr = take(gmres_scratch_bytes((int)kb, (int)N, m));
   cf* kqs = (cf*)take(kb * kqb);
   const int64_t bstride = (int64_t)(mat / sizeof(cf));
@@ -247,12 +271,25 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   for (int64_t o0 = 0; o0 < nothers; o0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, nothers - o0);
     std::vector<double> kv(nk);
-    std::vector<int32_t> hs(nk), hd(nk);
+    std::vector<int32_t> hs(nk), hd(nk), hlo(nk), hhi(nk);
+    std::vector<double4> hp(nk);
     for (int i = 0; i < nk; ++i) {
       const int64_t gi = others[o0 + i];
       kv[i] = k[gi];
       hs[i] = nearest[gi];
       hd[i] = (int32_t)gi;
+      // anchors bracketing k (by value): the closest below and above, else the nearest twice
+      int32_t lo = -1, hi = -1;
+      for (int64_t a = 0; a < na; ++a) {
+        if (ka[a] <= k[gi] && (lo < 0 || ka[a] > ka[lo])) lo = (int32_t)a;
+        if (ka[a] >= k[gi] && (hi < 0 || ka[a] < ka[hi])) hi = (int32_t)a;
+      }
+      if (lo < 0) lo = hs[i];
+      if (hi < 0) hi = hs[i];
+      const double span = ka[hi] - ka[lo];
+      hlo[i] = lo;
+      hhi[i] = hi;
+      hp[i] = make_double4(k[gi], ka[lo], ka[hi], span > 0.0 ? (k[gi] - ka[lo]) / span : 0.0);
     }
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, kv.data(), nk * 8, cudaMemcpyHostToDevice, c->stream));
     BIE_CUDA_TRY(cudaMemcpyAsync(sel, hs.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
@@ -265,6 +302,15 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     } else if (c->learned_x0 == 2) {
       dim3 g((unsigned)((N + 255) / 256), (unsigned)nk);
       BIE_LAUNCH(k_unknowns_from_surf<<<g, 256, 0, c->stream>>>(surf_a, sel, c->bc, N, x));
+    } else if (c->learned_x0 == 3) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(sel, hlo.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
+      BIE_CUDA_TRY(cudaMemcpyAsync(sel_hi, hhi.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
+      BIE_CUDA_TRY(cudaMemcpyAsync(ipar, hp.data(), nk * sizeof(double4), cudaMemcpyHostToDevice, c->stream));
+      dim3 g((unsigned)((N + 255) / 256), (unsigned)nk);
+      BIE_LAUNCH(k_interp_start<<<g, 256, 0, c->stream>>>(surf_a, sel, sel_hi, ipar, c->bc, c->nodes, c->dir[0],
+                                                          c->dir[1], c->dir[2], N, x));
+      // the preconditioner stays the nearest anchor's factor
+      BIE_CUDA_TRY(cudaMemcpyAsync(sel, hs.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
     } else {
       BIE_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nk * N * sizeof(cd), c->stream));
     }

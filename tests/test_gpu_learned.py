@@ -216,5 +216,29 @@ def test_network_entry_points_report_errors(small_spheroid):
     with pytest.raises(Bd.BieError):
         s.set_option("gmres.m", 100)
     with pytest.raises(Bd.BieError):
-        s.set_option("learned.x0", 3)
+        s.set_option("learned.x0", 4)
     s.close()
+
+
+def test_anchor_interpolant_start():
+    """learned.x0 = 3: the bracketing anchors' demodulated solutions interpolated in k start GMRES;
+    the solves match the oracle at the mixed bar, and the start is closer to the solution than the
+    nearest anchor's (phase-uncorrected) solution."""
+    from paper_1706_07919_gb300 import binding as Bd
+    mesh = W.ellipsoid_from_sphere(W.ico_sphere(3, 1.0, bc=0), (1.0, 1.0, 2.0))
+    k = 0.05 * np.arange(1, 33)
+    info = {}
+    for x0 in (3, 2):
+        s = _solver(mesh)
+        s.set_option("learned.x0", x0)
+        s.set_option("learned.stride", 4)
+        surf, rep = s.solve_frequencies(k, Bd.BIE_MODE_LEARNED)
+        info[x0] = s.learned_info()
+        sc = surf.cpu().numpy()
+        s.close()
+        if x0 == 3:
+            for i in (0, 5, 14, 30):
+                P, _ = oracle.solve_frequency(mesh, k[i], [0.0, 0.0, 1.0])
+                assert np.linalg.norm(sc[i, 0] - P) / np.linalg.norm(P) <= 1e-6
+    assert info[3]["x0_rel_err"] < info[2]["x0_rel_err"], (info[3]["x0_rel_err"], info[2]["x0_rel_err"])
+
