@@ -665,13 +665,12 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-      // runs of wavenumbers that are all zero or all positive, one launch each (k = 0, the
-      // zero-frequency term, takes f's limit inside the kernel; positive runs skip that select)
-      for (int r0 = 0; r0 < nk;) {
-        const bool zero = hk[r0] == 0.0;
-        int r1 = r0 + 1;
-        while (r1 < nk && (hk[r1] == 0.0) == zero) ++r1;
-        const int n = r1 - r0;
+      // k = 0 (the zero-frequency term) takes f's limit inside the kernel; launches without it
+      // keep that select out of the inner loop
+      bool zero = false;
+      for (int j = 0; j < nk; ++j) zero |= hk[j] == 0.0;
+      {
+        const int r0 = 0, n = nk;
         // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
         int uniform = n > 1 ? 1 : 0;
         const double dkv = n > 1 ? hk[r0 + 1] - hk[r0] : 0.0;
@@ -693,7 +692,6 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
           BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pqr, Pnqr, sr, xp, M, foot_elem,
                                                           foot, kr, n, Tr, tp, uniform, dkf));
         }
-        r0 = r1;
       }
     }
     else
