@@ -754,7 +754,17 @@ def run_case(args):
     sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.asm_kb", args.asm_kb)
     sol.set_option("field.variant", args.field_variant)
-    if args.case == "step":
+    if args.case == "phases":  # one untimed sweep, then one with phase timing (device times per phase)
+        sol.set_incident_plane_wave(w.direction)
+        sol.set_option("mixed.batch", args.batch)
+        sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+        sol.set_option("mixed.phase_timing", 1)
+        sol.solve_frequencies(w.k, B.BIE_MODE_MIXED)
+        ph = B.bie_get_phase_times(sol.ctx)
+        flops = ph["systems"] * (8.0 / 3.0) * float(w.mesh.N) ** 3
+        ph["lu_tflops"] = flops / (ph["factor_ms"] * 1e-3) / 1e12
+        print("case phases:", json.dumps(ph))
+    elif args.case == "step":
         sol.set_incident_plane_wave(w.direction)
         sol.set_option("mixed.batch", args.batch)
         xo = torch.tensor(w.xobs, dtype=torch.float64, device="cuda")
@@ -830,7 +840,8 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step", "peaks"], default=None,
+    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step", "peaks", "phases"],
+                    default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.case == "peaks":  # the pipe micro-benchmarks alone, as one JSON line

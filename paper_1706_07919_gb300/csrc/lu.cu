@@ -186,44 +186,57 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
     const int r = t / lw, c = t - r * lw;
     M[(int64_t)(c0 + r) * ld + c0 + c] = L[c * rows + r];
   }
-  // other panel columns: the leaf's swaps (in order), then the U-block solve right of the leaf
+  // other panel columns: their rows c0 .. c0+lw-1 are staged in shared memory (X, [lw][wall]),
+  // where each column's thread applies the leaf's swaps in order (rows below the leaf are swapped
+  // in global memory) and solves the U block right of the leaf; then X is written back.  The
+  // dependent chains of a column run on shared memory, not on global-memory round trips.
   const int pend = min(p0 + w, n);
-  for (int j = p0 + tid; j < pend; j += nt) {
+  const int wall = pend - p0;
+  Cx<S>* X = L + (size_t)rows * lw;  // [lw][wall]
+  for (int t = tid; t < lw * wall; t += nt) {
+    const int s = t / wall, jj = t - s * wall, j = p0 + jj;
+    if (j >= c0 && j < c0 + lw) continue;
+    X[t] = M[(int64_t)(c0 + s) * ld + j];
+  }
+  __syncthreads();
+  for (int jj = tid; jj < wall; jj += nt) {
+    const int j = p0 + jj;
     if (j >= c0 && j < c0 + lw) continue;
     for (int s = 0; s < lw; ++s) {
-      const int p = c0 + s_piv[s];
-      if (p != c0 + s) {
-        const Cx<S> t = M[(int64_t)(c0 + s) * ld + j];
-        M[(int64_t)(c0 + s) * ld + j] = M[(int64_t)p * ld + j];
-        M[(int64_t)p * ld + j] = t;
+      const int p = s_piv[s];  // leaf-relative row, p >= s
+      if (p != s) {
+        const Cx<S> t = X[s * wall + jj];
+        if (p < lw) {
+          X[s * wall + jj] = X[p * wall + jj];
+          X[p * wall + jj] = t;
+        } else {
+          Cx<S>& g = M[(int64_t)(c0 + p) * ld + j];
+          X[s * wall + jj] = g;
+          g = t;
+        }
       }
     }
     if (j >= c0 + lw)
       for (int s = 1; s < lw; ++s) {
-        Cx<S> v = M[(int64_t)(c0 + s) * ld + j];
+        Cx<S> v = X[s * wall + jj];
         for (int t = 0; t < s; ++t) {
           const Cx<S> l = L[t * rows + s];
-          const Cx<S> xt = M[(int64_t)(c0 + t) * ld + j];
+          const Cx<S> xt = X[t * wall + jj];
           v.re -= l.re * xt.re - l.im * xt.im;
           v.im -= l.re * xt.im + l.im * xt.re;
         }
-        M[(int64_t)(c0 + s) * ld + j] = v;
+        X[s * wall + jj] = v;
       }
+    for (int s = 0; s < lw; ++s) M[(int64_t)(c0 + s) * ld + j] = X[s * wall + jj];
   }
-  // rows below the leaf, panel columns right of it: A -= L_leaf U_leaf, with the leaf's L from
-  // shared memory and its just-solved U block read once into shared memory after it; consecutive
-  // threads take consecutive columns of a row (coalesced read-modify-write)
+  // rows below the leaf, panel columns right of it: A -= L_leaf U_leaf, with the leaf's L and its
+  // just-solved U block (in X) from shared memory; consecutive threads take consecutive columns
+  // of a row (coalesced read-modify-write)
   const int cs = c0 + lw, wr = pend - cs;
   if (fuse && wr > 0 && rows > lw) {
-    __syncthreads();  // this CTA's U-block writes above are complete
-    Cx<S>* U = L + (size_t)rows * lw;  // [lw][wr]
-#pragma unroll 4
-    for (int t = tid; t < lw * wr; t += nt) {
-      const int s = t / wr, j = t - s * wr;
-      U[t] = M[(int64_t)(c0 + s) * ld + cs + j];
-    }
-    __syncthreads();
-    if (pairs && (wr & 1) == 0) {  // cs = c0 + lw is even too
+    __syncthreads();  // every column's U block is complete in X
+    const Cx<S>* U = X + (cs - p0);  // U[s * wall + j]: row c0 + s, column cs + j
+    if (pairs && (wr & 1) == 0 && (wall & 1) == 0) {  // cs = c0 + lw and cs - p0 are even too
       // FP32: a thread takes two adjacent columns (one 16-byte load and store), several in flight
       const int hw = wr >> 1;
 #pragma unroll 4
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
         float4 a = *mp;
         for (int s2 = 0; s2 < lw; ++s2) {
           const Cx<S> l = L[s2 * rows + r];
-          const float4 u = *reinterpret_cast<const float4*>(&U[s2 * wr + j]);
+          const float4 u = *reinterpret_cast<const float4*>(&U[s2 * wall + j]);
           a.x -= l.re * u.x - l.im * u.y;
           a.y -= l.re * u.y + l.im * u.x;
           a.z -= l.re * u.z - l.im * u.w;
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(1024) k_leaf(Cx<S>* __restrict__ A, int64_t bs
         Cx<S>& m = M[(int64_t)(c0 + r) * ld + cs + j];
         Cx<S> a = m;
         for (int s2 = 0; s2 < lw; ++s2) {
-          const Cx<S> l = L[s2 * rows + r], u = U[s2 * wr + j];
+          const Cx<S> l = L[s2 * rows + r], u = U[s2 * wall + j];
           a.re -= l.re * u.re - l.im * u.im;
           a.im -= l.re * u.im + l.im * u.re;
         }
@@ -328,7 +341,7 @@ static int panel_factor(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t 
   for (int c0 = p0; c0 < p0 + w; c0 += lw) {
     const int l = std::min(lw, p0 + w - c0);
     const int wr = std::max(0, std::min(p0 + w, n) - c0 - l);  // panel columns right of the leaf
-    const size_t smem = ((size_t)(n - c0) * l + (fuse ? (size_t)l * wr : 0)) * sizeof(Cx<S>);
+    const size_t smem = ((size_t)(n - c0) * l + (size_t)l * std::min(w, n - p0)) * sizeof(Cx<S>);
     BIE_LAUNCH(k_leaf<S><<<batch, 1024, smem, c->stream>>>(A, bstride, n, ld, p0, w, c0, l, piv, info, fuse));
     const int rows = n - c0 - l;
     if (!fuse && rows > 0 && wr > 0) {
