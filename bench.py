@@ -793,6 +793,11 @@ def run_case(args):
         sol.set_option("mixed.fallback_err_est", 1.0)
         surf, rep = sol.solve_frequencies(w.k[100:104], B.BIE_MODE_MIXED)
         print("case lu: refinement corrections", [r.iters for r in rep])
+    elif args.case == "lu16":  # one batch of 16 systems (a few GB on the device)
+        sol.set_option("mixed.fallback_err_est", 1.0)
+        sol.set_option("mixed.batch", 16)
+        surf, rep = sol.solve_frequencies(w.k[100:116], B.BIE_MODE_MIXED)
+        print("case lu16: refinement corrections", [r.iters for r in rep])
     elif args.case == "field512":
         ks = w.k
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -840,7 +845,7 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "field", "field512", "batch", "learned", "step", "peaks", "phases"],
+    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "batch", "learned", "step", "peaks", "phases"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
