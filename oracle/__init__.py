@@ -12,7 +12,7 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                                           Appendix-B I1 = +4 pi, convergence order
   lu_factor / lu_solve                    pinned: numpy.linalg.solve, backward error
   foot_points                             pinned: sphere closest point is radial projection
-  field                                   pinned: interior point source, conventional representation
+  field                                   pinned: interior point source reproduced, sphere series after a solve
   dft / synthesize                        pinned: numpy FFT, Gaussian closed form, Parseval
   top_frequencies                         pinned: numpy lexsort with ties; Table I of the paper
   *_linear (3-node elements)              pinned: linear reproduction, entire-solution identity and
