@@ -550,7 +550,7 @@ def run_uneven(args, dev):
     meshes = [uneven_configuration(i)[0] for i in range(64)]
     outs = [torch.empty((nk, 2, m.N), dtype=torch.complex128, device=dev) for m in meshes]
     res = {}
-    for workers in (4, 1):
+    for workers in (args.uneven_workers, 1):
         sched = B.bie_sched_create(dev.index if dev.index is not None else 0, workers, None)
         jobs = [B.bie_sched_add(sched, m.nodes, m.elems, m.normals, m.bc, [0.0, 0.0, 1.0], k, B.BIE_MODE_MIXED, o)
                 for m, o in zip(meshes, outs)]
@@ -561,13 +561,13 @@ def run_uneven(args, dev):
         dt = time.perf_counter() - t
         B.bie_sched_destroy(sched)
         res[workers] = (dt, st, jobs)
-    dt4, st4, jobs4 = res[4]
+    dt4, st4, jobs4 = res[args.uneven_workers]
     flagged = sum(1 for j in jobs4 for r in j.reports() if r.flags & B.BIE_FLAG_FP64_ASSEMBLY)
     worst = max(r.backward_err for j in jobs4 for r in j.reports())
     Ns = [m.N for m in meshes]
     return {"workload": "uneven_64_configs_N162_to_7976", "wavenumbers_per_config": nk,
             "solves": 64 * nk, "solves_per_s": 64 * nk / dt4, "solves_per_s_one_worker": 64 * nk / res[1][0],
-            "workers": 4, "wall_s": dt4, "busy_s": st4["busy_ms"] / 1e3, "sum_N": int(sum(Ns)),
+            "workers": args.uneven_workers, "wall_s": dt4, "busy_s": st4["busy_ms"] / 1e3, "sum_N": int(sum(Ns)),
             "max_N": int(max(Ns)), "fp64_reassembled": flagged, "max_backward_err": worst,
             "timing": "wall clock around bie_sched_run (mesh set-up of every job included)"}
 
@@ -845,10 +845,46 @@ def main():
                     help="skip the uneven multi-configuration batch through the scheduler")
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
-    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "batch", "learned", "step", "peaks", "phases"],
+    ap.add_argument("--uneven-workers", dest="uneven_workers", type=int, default=4)
+    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "batch", "learned", "step", "peaks", "phases",
+                                       "uneven_full"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.case == "uneven_full":  # the whole uneven workload: 64 configurations x 256 wavenumbers
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_1706_07919_gb300 import binding as B
+        from workloads import config_uneven_batch
+        ws = config_uneven_batch()
+        dev = torch.device("cuda", 0)
+        outs = [torch.empty((len(w.k), 2, w.mesh.N), dtype=torch.complex128, device=dev) for w in ws]
+        res = {}
+        for workers in (args.uneven_workers, 1):
+            sched = B.bie_sched_create(0, workers, None)
+            jobs = [B.bie_sched_add(sched, w.mesh.nodes, w.mesh.elems, w.mesh.normals, w.mesh.bc, w.direction, w.k,
+                                    B.BIE_MODE_MIXED, o) for w, o in zip(ws, outs)]
+            torch.cuda.synchronize(dev)
+            util = subprocess.Popen(["nvidia-smi", "-i", "0", "--query-gpu=utilization.gpu", "--format=csv,noheader,nounits",
+                                     "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            t = time.perf_counter()
+            st = B.bie_sched_run(sched)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t
+            util.terminate()
+            u = [float(x) for x in util.communicate(timeout=5)[0].split() if x.strip().replace('.', '', 1).isdigit()]
+            B.bie_sched_destroy(sched)
+            ns = sum(len(w.k) for w in ws)
+            worst = max(r.backward_err for j in jobs for r in j.reports())
+            res[workers] = {"solves": ns, "wall_s": dt, "solves_per_s": ns / dt, "busy_s": st["busy_ms"] / 1e3,
+                            "gpu_util_median_pct": float(np.median(u)) if u else None,
+                            "fp64_reassembled": sum(1 for j in jobs for r in j.reports() if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
+                            "max_backward_err": worst}
+        print(json.dumps({"case": "uneven_full", "workload": "uneven_64_configs_N162_to_7976_Nk256",
+                          "workers": res[args.uneven_workers], "one_worker": res[1],
+                          "speedup": res[1]["wall_s"] / res[args.uneven_workers]["wall_s"]}))
+        return
     if args.case == "peaks":  # the pipe micro-benchmarks alone, as one JSON line
         import torch
         import __graft_entry__

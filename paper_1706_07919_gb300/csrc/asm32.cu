@@ -651,7 +651,7 @@ const int32_t* sorted_elems_ptr(bie_ctx* c) { return sorted_elems(c); }
 int ensure_mixed_tables(bie_ctx* c) {
   if (c->qgeo32) return BIE_OK;
   const int64_t nq = c->E * c->rule.Q, nn = c->E * 6 * (int64_t)c->rule.QN;
-  BIE_CUDA_TRY(cudaMalloc(&c->qgeo32, (sorted_aos_offset(c) + 16 * (size_t)(nq + nn)) * sizeof(float)));
+  BIE_TRY(dev_alloc(c, (void**)&c->qgeo32, (sorted_aos_offset(c) + 16 * (size_t)(nq + nn)) * sizeof(float)));
   BIE_LAUNCH(k_points_to32<<<(unsigned)((nq + 255) / 256), 256, 0, c->stream>>>(c->qgeo, nq, c->qgeo32, nullptr));
   BIE_LAUNCH(k_points_to32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->ngeo, nn, c->qgeo32 + P32COUNT * nq,
                                                                                 near_aos(c)));

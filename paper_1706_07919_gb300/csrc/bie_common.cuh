@@ -176,7 +176,12 @@ struct bie_ctx {
 
 namespace bie {
 
-int ensure_buf(DeviceBuf& b, size_t bytes);
+// Device memory of a context comes from the stream-ordered allocator on the context's stream
+// (cudaMallocAsync / cudaFreeAsync): freeing and growing buffers never synchronises the device,
+// so contexts on other streams (the scheduler's workers) keep running.
+int dev_alloc(bie_ctx* c, void** p, size_t bytes);
+void dev_free(bie_ctx* c, void* p);
+int ensure_buf(bie_ctx* c, DeviceBuf& b, size_t bytes);
 // The device's per-block shared-memory opt-in limit.  Kernels with dynamic shared memory get
 // this limit once (never a launch-specific size), so that contexts on other threads launching
 // the same kernel with other sizes cannot lower it between another thread's set and launch.

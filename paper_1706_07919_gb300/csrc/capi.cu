@@ -26,16 +26,27 @@ int cuda_fail(cudaError_t e, const char* what) {
   return (e == cudaErrorMemoryAllocation) ? BIE_ERR_OOM : BIE_ERR_CUDA;
 }
 
-int ensure_buf(DeviceBuf& b, size_t bytes) {
-  if (b.bytes >= bytes) return BIE_OK;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+int dev_alloc(bie_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 1), c->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     return fail(BIE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
   }
+  return BIE_OK;
+}
+
+void dev_free(bie_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+int ensure_buf(bie_ctx* c, DeviceBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return BIE_OK;
+  dev_free(c, b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  BIE_TRY(dev_alloc(c, &b.p, bytes));
   b.bytes = bytes;
   return BIE_OK;
 }
@@ -80,8 +91,8 @@ int ensure_pinned(bie_ctx* c, size_t bytes) {
   return BIE_OK;
 }
 
-void free_buf(DeviceBuf& b) {
-  if (b.p) cudaFree(b.p);
+void free_buf(bie_ctx* c, DeviceBuf& b) {
+  dev_free(c, b.p);
   b.p = nullptr;
   b.bytes = 0;
 }
@@ -126,8 +137,7 @@ static void free_geometry(bie_ctx* c) {
   void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
                   c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear, c->bc_flip,
                   c->lin_adj_off, c->lin_adj, c->lin_mid};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(c, p);
   c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->nshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
@@ -178,8 +188,8 @@ int flipped_bc(bie_ctx* c, uint8_t** out) {
   if (!c->bc_flip) {
     std::vector<uint8_t> f(c->N);
     for (int64_t j = 0; j < c->N; ++j) f[j] = (uint8_t)(1 - c->h_bc[j]);
-    BIE_CUDA_TRY(cudaMalloc(&c->bc_flip, c->N));
-    BIE_CUDA_TRY(cudaMemcpy(c->bc_flip, f.data(), c->N, cudaMemcpyHostToDevice));
+    BIE_TRY(dev_alloc(c, (void**)&c->bc_flip, c->N));
+    BIE_CUDA_TRY(cudaMemcpyAsync(c->bc_flip, f.data(), c->N, cudaMemcpyHostToDevice, c->stream));
   }
   *out = c->bc_flip;
   return BIE_OK;
@@ -213,7 +223,7 @@ int solve_fp64_multi(bie_ctx* c, const double* k, int64_t Nk, const double* dirs
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "two FP64 matrices of N = " + std::to_string(N) + " do not fit");
-  BIE_TRY(ensure_buf(c->work, kb * perk + 4096));
+  BIE_TRY(ensure_buf(c, c->work, kb * perk + 4096));
   char* base = (char*)c->work.p;
   cd* A = (cd*)base;
   cd* Bm = A + kb * N * N;
@@ -272,7 +282,7 @@ int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "one FP64 system of N = " + std::to_string(N) + " does not fit in device memory");
-  BIE_TRY(ensure_buf(c->work, kb * perk + 4096));
+  BIE_TRY(ensure_buf(c, c->work, kb * perk + 4096));
   char* base = (char*)c->work.p;
   cd* A = (cd*)base;
   cd* b = A + kb * N * N;
@@ -338,11 +348,11 @@ int bie_destroy(bie_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   free_geometry(c);
-  free_buf(c->work);
-  free_buf(c->work2);
-  free_buf(c->work3);
-  free_buf(c->work4);
-  free_buf(c->work5);
+  free_buf(c, c->work);
+  free_buf(c, c->work2);
+  free_buf(c, c->work3);
+  free_buf(c, c->work4);
+  free_buf(c, c->work5);
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -471,16 +481,17 @@ int set_geometry_impl(bie_ctx* c, const double* nodes, int64_t N, const int32_t*
   if (normals) c->h_normals.assign(normals, normals + 3 * N);
   BIE_TRY(host_geometry_checks(c, normals == nullptr));
   build_quad_rule(c->rule, c->ng, c->ng_near);
-  BIE_CUDA_TRY(cudaMalloc(&c->nodes, 3 * N * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&c->normals, 3 * N * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&c->elems, 6 * E * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->bc, N));
-  BIE_CUDA_TRY(cudaMalloc(&c->d_nnear, 6 * sizeof(int)));
-  BIE_CUDA_TRY(cudaMemcpy(c->nodes, c->h_nodes.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->normals, c->h_normals.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->elems, c->h_elems.data(), 6 * E * sizeof(int32_t), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->bc, c->h_bc.data(), N, cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->d_nnear, c->rule.nnear, 6 * sizeof(int), cudaMemcpyHostToDevice));
+  BIE_TRY(dev_alloc(c, (void**)&c->nodes, 3 * N * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->normals, 3 * N * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->elems, 6 * E * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->bc, N));
+  BIE_TRY(dev_alloc(c, (void**)&c->d_nnear, 6 * sizeof(int)));
+  // the host copies live in the context, so the asynchronous uploads may outlive this call
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->nodes, c->h_nodes.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->normals, c->h_normals.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->elems, c->h_elems.data(), 6 * E * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->bc, c->h_bc.data(), N, cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->d_nnear, c->rule.nnear, 6 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   BIE_TRY(build_colouring(c));
   BIE_TRY(upload_geometry_tables(c));
   c->has_geom = true;
@@ -499,7 +510,7 @@ int bie_assemble(bie_ctx* c, double k, void* A_out, void* b_out) {
   BIE_TRY(check_k(&k, 1));
   if (c->lin_N > 0) return assemble_linear_one(c, k, (cd*)A_out, (cd*)b_out);
   const int64_t N = c->N;
-  BIE_TRY(ensure_buf(c->work, (size_t)N * 4 * sizeof(cd) + 64));
+  BIE_TRY(ensure_buf(c, c->work, (size_t)N * 4 * sizeof(cd) + 64));
   double* kdev = (double*)((char*)c->work.p + (size_t)N * 4 * sizeof(cd));
   BIE_CUDA_TRY(cudaMemcpyAsync(kdev, &k, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_TRY(assemble64(c, kdev, 1, (cd*)A_out, (cd*)b_out, c->work.p, c->assemble_ff != 0));
@@ -618,7 +629,7 @@ int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, i
   // then spans many waves of resident CTAs, so the last, partial wave costs little
   constexpr int64_t kMaxFieldBatch = 512;
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, kMaxFieldBatch));
-  BIE_TRY(ensure_buf(c->work3, foot_bytes + kb * perk + kMaxFieldBatch * sizeof(double) + 4096 + 256));
+  BIE_TRY(ensure_buf(c, c->work3, foot_bytes + kb * perk + kMaxFieldBatch * sizeof(double) + 4096 + 256));
   double* foot = (double*)c->work3.p;
   int32_t* foot_elem = (int32_t*)(foot + 8 * M);
   char* after = (char*)(((uintptr_t)(foot_elem + M) + 255) & ~(uintptr_t)255);
@@ -635,7 +646,7 @@ int bie_eval_field(bie_ctx* c, const double* xobs, int64_t M, const double* k, i
     return fail(BIE_ERR_INVALID_ARG, "observation point " + std::to_string(bad) +
                                          " lies inside a scatterer (Eq. BRIEFdmn needs points in the fluid)");
   const int64_t Ns = c->lin_N > 0 ? c->lin_N : c->N;  // nodes of the caller's surface values
-  if (c->lin_N > 0) BIE_TRY(ensure_buf(c->work5, (size_t)kb * 2 * c->N * sizeof(cd)));
+  if (c->lin_N > 0) BIE_TRY(ensure_buf(c, c->work5, (size_t)kb * 2 * c->N * sizeof(cd)));
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     BIE_CUDA_TRY(cudaMemcpyAsync(kdev, k + k0, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -678,7 +689,7 @@ int bie_synthesize(bie_ctx* c, const void* T, const int64_t* midx, int64_t Nk, i
     if (midx[r] < 0 || midx[r] > Nt / 2) return fail(BIE_ERR_INVALID_ARG, "midx out of [0, Nt/2]");
     if (r > 0 && midx[r] <= midx[r - 1]) return fail(BIE_ERR_INVALID_ARG, "midx must be strictly increasing");
   }
-  BIE_TRY(ensure_buf(c->work3, (size_t)std::max<int64_t>(Nk, 1) * sizeof(int64_t)));
+  BIE_TRY(ensure_buf(c, c->work3, (size_t)std::max<int64_t>(Nk, 1) * sizeof(int64_t)));
   int64_t* md = (int64_t*)c->work3.p;
   if (Nk > 0) BIE_CUDA_TRY(cudaMemcpyAsync(md, midx, Nk * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   BIE_TRY(synthesize(c, (const cd*)T, md, (int)Nk, M, (const cd*)S, P, (int)Nt, out, out_dtype));
@@ -694,7 +705,7 @@ int bie_top_frequencies(bie_ctx* c, const void* S, int64_t P, int64_t Nt, int64_
   if (K < 0 || K > nm) return fail(BIE_ERR_INVALID_ARG, "K must be in [0, Nt/2 + 1]");
   if (K == 0) return BIE_OK;
   if (!S || !midx_out) return fail(BIE_ERR_INVALID_ARG, "NULL pointer");
-  BIE_TRY(ensure_buf(c->work3, (size_t)K * sizeof(int64_t)));
+  BIE_TRY(ensure_buf(c, c->work3, (size_t)K * sizeof(int64_t)));
   int64_t* md = (int64_t*)c->work3.p;
   BIE_TRY(top_frequencies(c, (const cd*)S, P, (int)nm, (int)K, md));
   BIE_CUDA_TRY(cudaMemcpyAsync(midx_out, md, (size_t)K * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));

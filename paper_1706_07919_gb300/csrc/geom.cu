@@ -173,8 +173,8 @@ int upload_geometry_tables(bie_ctx* c) {
   put(r.xi); put(r.eta); put(r.w); put(r.nxi); put(r.neta); put(r.nw);
   double* d_tab = nullptr;
   int* d_cnt = nullptr;
-  BIE_CUDA_TRY(cudaMalloc(&d_tab, tab.size() * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&d_cnt, 6 * sizeof(int)));
+  BIE_TRY(dev_alloc(c, (void**)&d_tab, tab.size() * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&d_cnt, 6 * sizeof(int)));
   BIE_CUDA_TRY(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(d_cnt, r.nnear, 6 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   const double* sxi = d_tab;
@@ -185,8 +185,8 @@ int upload_geometry_tables(bie_ctx* c) {
   const double* nw = neta + 6 * r.QN;
 
   int64_t totq = E * r.Q, totn = E * 6 * r.QN;
-  BIE_CUDA_TRY(cudaMalloc(&c->qgeo, GCOUNT * totq * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&c->ngeo, GCOUNT * totn * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->qgeo, GCOUNT * totq * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->ngeo, GCOUNT * totn * sizeof(double)));
   BIE_LAUNCH(k_geom_points<<<(unsigned)((totq + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, r.Q, r.Q, sxi, seta,
                                                                         sw, 0, d_cnt, c->qgeo, totq));
   BIE_LAUNCH(k_geom_points<<<(unsigned)((totn + 255) / 256), 256, 0, c->stream>>>(c->nodes, c->elems, E, 0, r.QN, nxi, neta,
@@ -200,17 +200,17 @@ int upload_geometry_tables(bie_ctx* c) {
     for (int t = 0; t < r.nnear[a]; ++t)
       shape6(r.nxi[a * r.QN + t], r.neta[a * r.QN + t], &ns[(a * r.QN + t) * 6], nullptr, nullptr);
   std::vector<float> qs32(qs.begin(), qs.end()), ns32(ns.begin(), ns.end());
-  BIE_CUDA_TRY(cudaMalloc(&c->qshape, qs.size() * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&c->nshape, ns.size() * sizeof(double)));
-  BIE_CUDA_TRY(cudaMalloc(&c->qshape32, qs32.size() * sizeof(float)));
-  BIE_CUDA_TRY(cudaMalloc(&c->nshape32, ns32.size() * sizeof(float)));
+  BIE_TRY(dev_alloc(c, (void**)&c->qshape, qs.size() * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->nshape, ns.size() * sizeof(double)));
+  BIE_TRY(dev_alloc(c, (void**)&c->qshape32, qs32.size() * sizeof(float)));
+  BIE_TRY(dev_alloc(c, (void**)&c->nshape32, ns32.size() * sizeof(float)));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->qshape, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->nshape, ns.data(), ns.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->qshape32, qs32.data(), qs32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaMemcpyAsync(c->nshape32, ns32.data(), ns32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  cudaFree(d_tab);
-  cudaFree(d_cnt);
+  dev_free(c, d_tab);
+  dev_free(c, d_cnt);
   return BIE_OK;
 }
 
@@ -272,14 +272,18 @@ int build_colouring(bie_ctx* c) {
     csr.insert(csr.end(), n2e[i].begin(), n2e[i].end());
   }
   c->max_n2e = mx;
-  BIE_CUDA_TRY(cudaMalloc(&c->color_off, off.size() * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->elem_perm, perm.size() * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->n2e_off, csr_off.size() * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->n2e, std::max<size_t>(1, csr.size()) * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMemcpy(c->color_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->elem_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->n2e_off, csr_off.data(), csr_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->n2e, csr.data(), csr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BIE_TRY(dev_alloc(c, (void**)&c->color_off, off.size() * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->elem_perm, perm.size() * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->n2e_off, csr_off.size() * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->n2e, std::max<size_t>(1, csr.size()) * sizeof(int32_t)));
+  // pageable sources: each copy returns once its data is staged, so the locals may go
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->color_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->elem_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->n2e_off, csr_off.data(), csr_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               c->stream));
+  if (!csr.empty())
+    BIE_CUDA_TRY(cudaMemcpyAsync(c->n2e, csr.data(), csr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }
 

@@ -173,7 +173,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   const size_t d_bytes = align256((size_t)na * dstride * sizeof(cf));
   const size_t keep_bytes = lu_bytes + d_bytes + align256((size_t)na * N * 4) +
                             align256((size_t)na * 2 * N * sizeof(cd)) + align256((size_t)Nk * 4) + 4096;
-  BIE_TRY(ensure_buf(c->work4, keep_bytes));
+  BIE_TRY(ensure_buf(c, c->work4, keep_bytes));
   char* kp = (char*)c->work4.p;
   cf* LUk = (cf*)kp;
   cf* Dk = (cf*)(kp + lu_bytes);
@@ -241,7 +241,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   const int64_t nothers = (int64_t)others.size();
   const int64_t kb =
       std::max<int64_t>(1, std::min<int64_t>(nothers, std::min<int64_t>(c->mixed_batch, (int64_t)(avail / perk))));
-  BIE_TRY(ensure_buf(c->work, kb * perk + gmres_scratch_bytes((int)kb, (int)N, m) + 65536));
+  BIE_TRY(ensure_buf(c, c->work, kb * perk + gmres_scratch_bytes((int)kb, (int)N, m) + 65536));
   char* p = (char*)c->work.p;
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);
@@ -367,7 +367,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   if (!redo.empty()) {
     const int64_t nr = (int64_t)redo.size();
     void* tmp = nullptr;
-    BIE_CUDA_TRY(cudaMalloc(&tmp, (size_t)nr * 2 * N * sizeof(cd) + (size_t)nr * 4 + 256));
+    BIE_TRY(dev_alloc(c, &tmp, (size_t)nr * 2 * N * sizeof(cd) + (size_t)nr * 4 + 256));
     cd* surf_r = (cd*)tmp;
     int32_t* ridx = (int32_t*)((char*)tmp + (size_t)nr * 2 * N * sizeof(cd));
     std::vector<bie_report> rr((size_t)nr);
@@ -386,7 +386,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
           rep[redo_idx[i]].flags |= keep & BIE_FLAG_ILL_CONDITIONED;
         }
     }
-    cudaFree(tmp);
+    dev_free(c, tmp);
     BIE_TRY(rc);
   }
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -132,7 +132,7 @@ int solve_fp64_linear(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
   BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(64, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "linear-element systems do not fit in device memory");
-  BIE_TRY(ensure_buf(c->work, (size_t)kb * perk + 8192));
+  BIE_TRY(ensure_buf(c, c->work, (size_t)kb * perk + 8192));
   char* base = (char*)c->work.p;
   cd* Al = (cd*)base;
   cd* bl = Al + kb * Nl * Nl;
@@ -166,7 +166,7 @@ int solve_fp64_linear(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
 // bie_assemble on linear elements: A_out [Nl][Nl], b_out [Nl].
 int assemble_linear_one(bie_ctx* c, double k, cd* A_out, cd* b_out) {
   const int64_t Nl = c->lin_N;
-  BIE_TRY(ensure_buf(c->work, linear_scratch_bytes(c, 1) + (size_t)Nl * sizeof(cd) + 256));
+  BIE_TRY(ensure_buf(c, c->work, linear_scratch_bytes(c, 1) + (size_t)Nl * sizeof(cd) + 256));
   double* kdev = (double*)c->work.p;
   cd* known = (cd*)((char*)c->work.p + 256);
   char* scratch = (char*)(known + Nl);
@@ -249,12 +249,14 @@ extern "C" int bie_set_geometry_linear(bie_ctx* c, const double* nodes, int64_t 
   }
   std::vector<int32_t> mids(2 * std::max<int64_t>(nm, 1));
   for (int64_t m = 0; m < nm; ++m) { mids[m] = mid_a[m]; mids[nm + m] = mid_b[m]; }
-  BIE_CUDA_TRY(cudaMalloc(&c->lin_adj_off, (N + 1) * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->lin_adj, std::max<int64_t>(2 * nm, 1) * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMalloc(&c->lin_mid, mids.size() * sizeof(int32_t)));
-  BIE_CUDA_TRY(cudaMemcpy(c->lin_adj_off, off.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-  if (nm > 0) BIE_CUDA_TRY(cudaMemcpy(c->lin_adj, adj.data(), 2 * nm * sizeof(int32_t), cudaMemcpyHostToDevice));
-  BIE_CUDA_TRY(cudaMemcpy(c->lin_mid, mids.data(), mids.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  BIE_TRY(dev_alloc(c, (void**)&c->lin_adj_off, (N + 1) * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->lin_adj, std::max<int64_t>(2 * nm, 1) * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->lin_mid, mids.size() * sizeof(int32_t)));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->lin_adj_off, off.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if (nm > 0)
+    BIE_CUDA_TRY(cudaMemcpyAsync(c->lin_adj, adj.data(), 2 * nm * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->lin_mid, mids.data(), mids.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->lin_N = N;
   return BIE_OK;
 }

@@ -89,7 +89,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, c->lu_block);
   if ((size_t)kb * perk + tc_scratch + fb > free_b)
     return fail(BIE_ERR_OOM, "mixed-precision workspace for N = " + std::to_string(N) + " does not fit");
-  BIE_TRY(ensure_buf(c->work, kb * perk + tc_scratch + fb + 16384));
+  BIE_TRY(ensure_buf(c, c->work, kb * perk + tc_scratch + fb + 16384));
   char* p = (char*)c->work.p;
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);

@@ -550,18 +550,18 @@ static int mlp_state(bie_ctx* c, MlpState** out) {
     MlpState* s = new MlpState();
     c->mlp = s;  // freed by mlp_free even if an allocation below fails
     const size_t P = (size_t)NPARAM;
-    BIE_CUDA_TRY(cudaMalloc(&s->theta, P * 4));
-    BIE_CUDA_TRY(cudaMalloc(&s->grad, P * 4));
-    BIE_CUDA_TRY(cudaMalloc(&s->m, P * 4));
-    BIE_CUDA_TRY(cudaMalloc(&s->v, P * 4));
-    BIE_CUDA_TRY(cudaMalloc(&s->w1, W_H * D_IN * 2));
-    BIE_CUDA_TRY(cudaMalloc(&s->w2, W_H * W_H * 2));
-    BIE_CUDA_TRY(cudaMalloc(&s->w3, W_H * W_H * 2));
-    BIE_CUDA_TRY(cudaMalloc(&s->w2t, W_H * W_H * 2));
-    BIE_CUDA_TRY(cudaMalloc(&s->w3t, W_H * W_H * 2));
-    BIE_CUDA_TRY(cudaMalloc(&s->step, 64));
-    BIE_CUDA_TRY(cudaMalloc(&s->loss, 64));
-    BIE_CUDA_TRY(cudaMalloc(&s->err, 64));
+    BIE_TRY(dev_alloc(c, (void**)&s->theta, P * 4));
+    BIE_TRY(dev_alloc(c, (void**)&s->grad, P * 4));
+    BIE_TRY(dev_alloc(c, (void**)&s->m, P * 4));
+    BIE_TRY(dev_alloc(c, (void**)&s->v, P * 4));
+    BIE_TRY(dev_alloc(c, (void**)&s->w1, W_H * D_IN * 2));
+    BIE_TRY(dev_alloc(c, (void**)&s->w2, W_H * W_H * 2));
+    BIE_TRY(dev_alloc(c, (void**)&s->w3, W_H * W_H * 2));
+    BIE_TRY(dev_alloc(c, (void**)&s->w2t, W_H * W_H * 2));
+    BIE_TRY(dev_alloc(c, (void**)&s->w3t, W_H * W_H * 2));
+    BIE_TRY(dev_alloc(c, (void**)&s->step, 64));
+    BIE_TRY(dev_alloc(c, (void**)&s->loss, 64));
+    BIE_TRY(dev_alloc(c, (void**)&s->err, 64));
     BIE_CUDA_TRY(cudaMemsetAsync(s->grad, 0, P * 4, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(s->m, 0, P * 4, c->stream));
     BIE_CUDA_TRY(cudaMemsetAsync(s->v, 0, P * 4, c->stream));
@@ -577,7 +577,7 @@ void mlp_free(bie_ctx* c) {
   if (!s) return;
   for (void* p : {(void*)s->theta, (void*)s->grad, (void*)s->m, (void*)s->v, (void*)s->w1, (void*)s->w2, (void*)s->w3,
                   (void*)s->w2t, (void*)s->w3t, (void*)s->step, (void*)s->loss, (void*)s->err, s->block, s->dset})
-    if (p) cudaFree(p);
+    dev_free(c, p);
   delete s;
   c->mlp = nullptr;
 }
@@ -586,14 +586,13 @@ static int ensure_act(bie_ctx* c, MlpState* s, int64_t rows) {
   rows = round_up(std::max<int64_t>(rows, 128), 128);
   if (rows <= s->cap) return BIE_OK;
   if (s->block) {
-    BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    cudaFree(s->block);
+    dev_free(c, s->block);
     s->block = nullptr;
     s->cap = 0;
   }
   const size_t r = (size_t)rows;
   const size_t bytes = r * (2 * D_IN * 2 + 10 * W_H * 2 + 2 * 4) + 16 * 256;
-  BIE_CUDA_TRY(cudaMalloc(&s->block, bytes));
+  BIE_TRY(dev_alloc(c, (void**)&s->block, bytes));
   char* q = (char*)s->block;
   auto take = [&](size_t b) { char* p = q; q += (b + 255) & ~(size_t)255; return (void*)p; };
   s->X0 = (bf16*)take(r * D_IN * 2);
@@ -743,7 +742,7 @@ static int features(bie_ctx* c, const double* kdev, int nk, bf16* X, float* Xf) 
 }
 
 static int upload_k(bie_ctx* c, const double* k, int64_t nk, double** kdev) {
-  BIE_TRY(ensure_buf(c->work3, (size_t)nk * sizeof(double) + 256));
+  BIE_TRY(ensure_buf(c, c->work3, (size_t)nk * sizeof(double) + 256));
   *kdev = (double*)c->work3.p;
   BIE_CUDA_TRY(cudaMemcpyAsync(*kdev, k, nk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   return BIE_OK;
@@ -892,13 +891,12 @@ int mlp_train(bie_ctx* c, const double* k, int64_t nk, const cd* surf, int epoch
   const int64_t Bvalid = std::min<int64_t>(Bv, rows);
   // training set: features + scaled targets
   if (s->dset) {
-    BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    cudaFree(s->dset);
+    dev_free(c, s->dset);
     s->dset = nullptr;
   }
   const size_t xb = ((size_t)rows * D_IN * 2 + 255) & ~(size_t)255, tb = ((size_t)rows * 8 + 255) & ~(size_t)255;
   const size_t ib = ((size_t)nmb * Bp * 4 + 255) & ~(size_t)255;
-  BIE_CUDA_TRY(cudaMalloc(&s->dset, xb + tb + ib + 256 + (size_t)nk * 8 + 256));
+  BIE_TRY(dev_alloc(c, (void**)&s->dset, xb + tb + ib + 256 + (size_t)nk * 8 + 256));
   s->Xall = (bf16*)s->dset;
   s->Tall = (float*)((char*)s->dset + xb);
   s->idx = (int32_t*)((char*)s->dset + xb + tb);

@@ -87,7 +87,7 @@ __global__ void k_synth(const cd* __restrict__ T, const int64_t* __restrict__ mi
 }
 
 static int twiddle_table(bie_ctx* c, int n, double2** tw) {
-  BIE_TRY(ensure_buf(c->work2, (size_t)(n / 2 + 1) * sizeof(double2)));
+  BIE_TRY(ensure_buf(c, c->work2, (size_t)(n / 2 + 1) * sizeof(double2)));
   *tw = (double2*)c->work2.p;
   BIE_LAUNCH(k_twiddles<<<(n / 2 + 255) / 256, 256, 0, c->stream>>>(n, *tw));
   BIE_CUDA_TRY(cudaGetLastError());

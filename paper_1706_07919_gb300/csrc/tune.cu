@@ -99,7 +99,7 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   const int batches[] = {8, 16, 32, 64, 128, 256};
   const int tcs[] = {3, 2};
   size_t surf_bytes = (size_t)256 * 2 * N * sizeof(cd);
-  if (cudaMalloc(&surf, surf_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+  if (dev_alloc(c, (void**)&surf, surf_bytes) != BIE_OK || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(BIE_ERR_OOM, "autotune scratch");
   // one timed batch (after an untimed one that sizes the workspace and builds the tables)
@@ -136,7 +136,7 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
       if (rc != BIE_OK) break;
       if (us < best.us_per_k) best = TuneEntry{best.batch, 3, block, us};
     }
-  if (surf) cudaFree(surf);
+  dev_free(c, surf);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   c->mixed_graph = saved_graph;
