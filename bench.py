@@ -516,9 +516,13 @@ def run_large(args, dev, stream):
         pulses = torch.tensor(w.pulses, dtype=torch.float64, device=dev)
         out = torch.empty((P, M, Nt), dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sol.set_option("mixed.phase_timing", 1)  # one batch: no graph replay to lose
+    l0 = B.bie_kernel_launches()
     ev[0].record(stream)
     surf, rep = sol.solve_frequencies(ks, B.BIE_MODE_MIXED)
     ev[1].record(stream)
+    solve_launches = B.bie_kernel_launches() - l0
+    ph = B.bie_get_phase_times(sol.ctx)
     T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
     ev[2].record(stream)
     S = sol.pulse_spectrum(pulses)
@@ -532,7 +536,10 @@ def run_large(args, dev, stream):
             "field_evals_per_s": M * w.mesh.E * 16 * len(ks) / (t_field / 1e3), "points": M, "pulses": P, "Nt": Nt,
             "phase_ms": {"solve": t_solve, "field": t_field, "spectrum_synthesis": t_syn},
             "fp64_reassembled": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
-            "max_backward_err": max(r.backward_err for r in rep)}
+            "max_backward_err": max(r.backward_err for r in rep),
+            "solve_phase_ms": {k_: ph[k_] for k_ in ("assembly_ms", "factor_ms", "refine_ms", "reassembly_ms")},
+            "lu_tflops": ph["systems"] * (8.0 / 3.0) * float(w.mesh.N) ** 3 / (ph["factor_ms"] * 1e-3) / 1e12,
+            "solve_kernel_launches": int(solve_launches)}
 
 
 def run_uneven(args, dev):
