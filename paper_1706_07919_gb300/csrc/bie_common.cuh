@@ -146,6 +146,8 @@ struct bie_ctx {
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
   int phase_timing = 0;              // time the mixed path's phases with CUDA events (no graphs)
+  size_t mem_budget = 0;             // device bytes this context may size its workspaces to
+                                     // (0: all free memory; the scheduler gives each worker a share)
   bie_phase_times phase{};           // phases of the last BIE_MODE_MIXED call (phase_timing 1)
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
   cudaStream_t cap_stream = nullptr; // private stream on which CUDA graphs are captured
@@ -182,6 +184,8 @@ namespace bie {
 int dev_alloc(bie_ctx* c, void** p, size_t bytes);
 void dev_free(bie_ctx* c, void* p);
 int ensure_buf(bie_ctx* c, DeviceBuf& b, size_t bytes);
+// Free device memory for this context's workspace sizing: cudaMemGetInfo, capped by mem_budget.
+int device_free(bie_ctx* c, size_t* free_b);
 // The device's per-block shared-memory opt-in limit.  Kernels with dynamic shared memory get
 // this limit once (never a launch-specific size), so that contexts on other threads launching
 // the same kernel with other sizes cannot lower it between another thread's set and launch.

@@ -37,6 +37,13 @@ int dev_alloc(bie_ctx* c, void** p, size_t bytes) {
   return BIE_OK;
 }
 
+int device_free(bie_ctx* c, size_t* free_b) {
+  size_t total = 0;
+  BIE_CUDA_TRY(cudaMemGetInfo(free_b, &total));
+  if (c->mem_budget > 0) *free_b = std::min(*free_b, c->mem_budget);
+  return BIE_OK;
+}
+
 void dev_free(bie_ctx* c, void* p) {
   if (p) cudaFreeAsync(p, c->stream);
 }
@@ -219,8 +226,8 @@ int solve_fp64_multi(bie_ctx* c, const double* k, int64_t Nk, const double* dirs
   const size_t st_bytes = (refine_state_bytes(1) + 15) / 16 * 16;
   const size_t perk = 2 * (size_t)N * N * sizeof(cd) + (size_t)N * sizeof(cd) * 8 + (size_t)N * sizeof(double) +
                       (size_t)N * 4 + st_bytes + 64;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "two FP64 matrices of N = " + std::to_string(N) + " do not fit");
   BIE_TRY(ensure_buf(c, c->work, kb * perk + 4096));
@@ -278,8 +285,8 @@ int solve_fp64_multi(bie_ctx* c, const double* k, int64_t Nk, const double* dirs
 int solve_fp64(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep) {
   const int64_t N = c->N;
   const size_t perk = (size_t)N * N * sizeof(cd) + (size_t)N * sizeof(cd) * 6 + (size_t)N * 4 + 64;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(256, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "one FP64 system of N = " + std::to_string(N) + " does not fit in device memory");
   BIE_TRY(ensure_buf(c, c->work, kb * perk + 4096));

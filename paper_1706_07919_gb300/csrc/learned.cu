@@ -235,8 +235,8 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
   const size_t kqb = align256((size_t)c->E * c->rule.Q * sizeof(cf));  // known values at quadrature points
   const size_t perk = mat + 5 * vec + align256((size_t)N * 6 * sizeof(double)) + gmres_scratch_bytes(1, (int)N, m) +
                       2 * align256(refine_state_bytes(1)) + kqb + 64;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   const size_t avail = free_b / 2 + c->work.bytes;  // the mixed path's workspace is reused
   const int64_t nothers = (int64_t)others.size();
   const int64_t kb =

@@ -128,8 +128,8 @@ int solve_fp64_linear(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
   const int64_t Nl = c->lin_N;
   const size_t perk = linear_scratch_bytes(c, 1) + (size_t)Nl * Nl * sizeof(cd) + 3 * (size_t)Nl * sizeof(cd) +
                       (size_t)Nl * 4 + 64;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   const int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(64, (int64_t)((free_b / 2) / perk))));
   if ((size_t)kb * perk > free_b) return fail(BIE_ERR_OOM, "linear-element systems do not fit in device memory");
   BIE_TRY(ensure_buf(c, c->work, (size_t)kb * perk + 8192));

@@ -80,8 +80,8 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   // group refines its systems in the same launches (one CTA per system in the triangular
   // solves), so a larger group fills more of the GPU; it is capped at an eighth of free memory.
   const size_t fb1 = align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   const int G = (int)std::max<size_t>(1, std::min<size_t>(kFallbackGroupMax, (free_b / 8) / fb1));
   const size_t fb = (size_t)G * fb1 + 4096;
   const size_t avail = free_b > fb ? free_b - fb : 0;
@@ -89,7 +89,15 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, c->lu_block);
   if ((size_t)kb * perk + tc_scratch + fb > free_b)
     return fail(BIE_ERR_OOM, "mixed-precision workspace for N = " + std::to_string(N) + " does not fit");
-  BIE_TRY(ensure_buf(c, c->work, kb * perk + tc_scratch + fb + 16384));
+  // memory shared with other contexts (scheduler workers on other streams) can run short between
+  // the query above and the allocation: halve the batch and try again
+  for (;;) {
+    const int rc = ensure_buf(c, c->work, kb * perk + tc_scratch + fb + 16384);
+    if (rc == BIE_OK) break;
+    if (rc != BIE_ERR_OOM || kb == 1) return rc;
+    kb = std::max<int64_t>(1, kb / 2);
+    tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, c->lu_block);
+  }
   char* p = (char*)c->work.p;
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };
   cf* A = (cf*)take(kb * mat);

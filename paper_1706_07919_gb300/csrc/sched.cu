@@ -137,11 +137,8 @@ int bie_sched_run(bie_sched* s, bie_sched_stats* stats) {
         bie_tune_result tr;
         rc = bie::autotune(c, j.k.data(), (int64_t)std::min<size_t>(j.k.size(), 8), s->cache.c_str(), &tr);
       }
-      if (rc == BIE_OK) {  // this worker's share of device memory bounds its batch
-        const int64_t ld = (N + 63) / 64 * 64;
-        const size_t perk = 2 * (size_t)N * ld * sizeof(bie::cf) + 64 * (size_t)N + 8 * (size_t)N * N * 16 / 64;
-        const int cap = (int)std::max<size_t>(1, share / perk);
-        c->mixed_batch = std::max(1, std::min(c->mixed_batch, cap));
+      if (rc == BIE_OK) {  // this worker's share of device memory bounds its workspaces
+        c->mem_budget = share;
         rc = bie_solve_frequencies(c, j.k.data(), (int64_t)j.k.size(), j.mode, j.surf, j.rep);
       }
       if (rc != BIE_OK) {

@@ -86,8 +86,8 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   if (nk < 1) return fail(BIE_ERR_INVALID_ARG, "autotune needs at least one sample wavenumber");
   const int64_t ld = (N + 63) / 64 * 64;
   const size_t perk = 2 * (size_t)N * ld * sizeof(cf) + 64 * (size_t)N;
-  size_t free_b = 0, total_b = 0;
-  BIE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t free_b = 0;
+  BIE_TRY(device_free(c, &free_b));
   const int saved_batch = c->mixed_batch, saved_tc = c->tc_version, saved_graph = c->mixed_graph,
             saved_block = c->lu_block;
   TuneEntry best;
