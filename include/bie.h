@@ -214,7 +214,7 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
- *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 2.5e-7)
+ *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 3e-7)
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
  *   "field.variant"        mixed field kernel: 2 (default) groups of 16 wavenumbers, 128 points per
