@@ -196,7 +196,8 @@ int bie_set_geometry(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t
  * linear-element system.  Afterwards bie_assemble returns the [N][N] linear system,
  * bie_solve_frequencies (BIE_MODE_FP64 only) writes surf [Nk][2][N] at the vertices, and
  * bie_eval_field takes that surf (interpolated linearly onto the image for Eq. BRIEFdmn).
- * Errors: as bie_set_geometry; INVALID_ARG for an element with two conditions. */
+ * Errors: as bie_set_geometry; INVALID_ARG for an element with two conditions or an image of more
+ * than 25 600 nodes (N + number of edges). */
 int bie_set_geometry_linear(bie_ctx* ctx, const double* nodes, int64_t N, const int32_t* elems, int64_t E,
                             const double* normals, const uint8_t* bc);
 

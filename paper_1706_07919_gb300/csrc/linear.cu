@@ -216,6 +216,9 @@ extern "C" int bie_set_geometry_linear(bie_ctx* c, const double* nodes, int64_t 
     q[6 * e + 3] = (int32_t)m[0]; q[6 * e + 4] = (int32_t)m[1]; q[6 * e + 5] = (int32_t)m[2];
   }
   const int64_t nm = (int64_t)mid_a.size(), Nq = N + nm;
+  if (Nq > 25600)  // the flat image's FP64 systems (and the reduction's grid rows) stay bounded
+    return fail(BIE_ERR_INVALID_ARG, "linear mesh too large: its flat quadratic image has " + std::to_string(Nq) +
+                                         " nodes (at most 25600)");
   std::vector<double> xq(3 * Nq), nq(3 * Nq);
   std::vector<uint8_t> bq(Nq);
   std::copy(nodes, nodes + 3 * N, xq.begin());
