@@ -111,6 +111,7 @@ typedef struct {
   int32_t from_cache;  /* 1: read from the cache file, 0: measured now */
   double us_per_k;     /* measured time per wavenumber of the chosen setting */
   int32_t lu_block;    /* columns over which the deferred update runs ("mixed.lu_block") */
+  int32_t lu_panel;    /* panel width of the deferred version ("mixed.lu_panel") */
 } bie_tune_result;
 
 /* Device time of the phases of the last BIE_MODE_MIXED call (bie_get_phase_times), recorded
@@ -212,6 +213,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          2 the same kernel after every 64-column panel, 1 the
  *                          register-staged tcgen05 kernel, 0 FP32 on the CUDA cores.
  *   "mixed.lu_block"       columns of the deferred update of version 3: 128, 256 (default), 512
+ *   "mixed.lu_panel"       panel width of version 3: 64 (default) or 32 (more, narrower panels:
+ *                          shorter pivot chains per leaf, narrower K = 32 updates inside a block)
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
@@ -362,7 +365,8 @@ int bie_measure_peaks(int cuda_device, bie_peaks* out);
  * k host f64 [nk], repeated to fill the batch) for every candidate of "mixed.batch" in
  * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {3, 2}
  * (with "mixed.lu_block" 256), then, if version 3 won, "mixed.lu_block" 128 and 512 at the chosen
- * batch, and sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
+ * batch and then "mixed.lu_panel" 32 at the chosen batch and block, and sets the fastest per
+ * wavenumber on the context.  cache_path (host string or NULL): a JSON
  * file keyed by N rounded up to 64; an entry for this N is applied without measuring, a new
  * measurement is added to it.  out (host, optional) receives the choice.  Synchronises.
  * Errors: STATE without geometry, OOM if no candidate fits, INVALID_ARG if the cache cannot be

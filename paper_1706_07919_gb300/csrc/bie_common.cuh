@@ -129,6 +129,7 @@ struct bie_ctx {
                                      // with the update deferred over 256-column blocks
   int lu_block = 256;                // mixed.tcgen05 3: columns over which the trailing update is
                                      // deferred (128, 256 or 512)
+  int lu_panel = 64;                 // mixed.tcgen05 3: panel width (32 or 64)
   int mixed_batch = 64;              // wavenumbers per batch
   int refine_it_max = 10;            // refinement corrections per system
   int refine64_it_max = 30;          // corrections against the FP64 re-assembly of flagged systems

@@ -389,6 +389,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value != 128.0 && value != 256.0 && value != 512.0)
       return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 128, 256 or 512");
     c->lu_block = (int)value;
+  } else if (n == "mixed.lu_panel") {
+    if (value != 32.0 && value != 64.0) return fail(BIE_ERR_INVALID_ARG, "mixed.lu_panel must be 32 or 64");
+    c->lu_panel = (int)value;
   } else if (n == "mixed.batch") {
     if (value < 1 || value > 4096) return fail(BIE_ERR_INVALID_ARG, "mixed.batch must be in [1, 4096]");
     c->mixed_batch = (int)value;

@@ -240,7 +240,6 @@ namespace tc2 {
 
 constexpr int BM = 128;                  // rows per tile
 constexpr int BNR = 256;                 // real columns per tile (128 complex)
-constexpr int KR = 2 * tc::NB;           // reals along K (128)
 constexpr int KCH = 32;                  // floats per 128-byte swizzle row
 constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
@@ -305,18 +304,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// B^T of the real embedding for 64 rows of U (rows u0 .. u0+63 of A, row k = u0 + kk): for
-// column c in [cb, cend), B^T rows 2 (c - cb) and 2 (c - cb) + 1 get, at floats koff + 2 kk,
-// [ur, -ui] and [ui, ur] (rows `krow` floats long).  Columns at or past n are zero.
+// B^T of the real embedding for nrows (<= 64) rows of U (rows u0 .. u0+nrows-1 of A, row
+// k = u0 + kk): for column c in [cb, cend), B^T rows 2 (c - cb) and 2 (c - cb) + 1 get, at floats
+// koff + 2 kk, [ur, -ui] and [ui, ur] (rows `krow` floats long).  Columns at or past n are zero.
 // grid (ceil((cend - cb) / 32), batch)
 __global__ void __launch_bounds__(256) k_build_ub(const float* __restrict__ A, int64_t bstride, int n, int ld, int u0,
                                                   int cb, int cend, float* __restrict__ ub, int64_t ub_stride,
-                                                  int krow, int koff) {
+                                                  int krow, int koff, int nrows) {
   __shared__ float2 t[tc::NB][33];
   const int z = blockIdx.y;
   const int c0 = blockIdx.x * 32;
   const float* M = A + (int64_t)z * bstride * 2;
-  for (int e = threadIdx.x; e < tc::NB * 32; e += blockDim.x) {  // U rows k, columns cb + c0 .. +31
+  for (int e = threadIdx.x; e < nrows * 32; e += blockDim.x) {  // U rows k, columns cb + c0 .. +31
     const int k = e / 32, cc = e % 32;
     const int gc = cb + c0 + cc;
     float2 u = make_float2(0.f, 0.f);
@@ -325,8 +324,8 @@ __global__ void __launch_bounds__(256) k_build_ub(const float* __restrict__ A, i
   }
   __syncthreads();
   float* out = ub + (int64_t)z * ub_stride;
-  for (int e = threadIdx.x; e < 32 * tc::NB; e += blockDim.x) {
-    const int cc = e / tc::NB, k = e % tc::NB;
+  for (int e = threadIdx.x; e < 32 * nrows; e += blockDim.x) {
+    const int cc = e / nrows, k = e % nrows;
     if (cb + c0 + cc >= cend) continue;
     const float2 u = t[k][cc];
     const int64_t r = 2 * (int64_t)(c0 + cc);
@@ -550,9 +549,12 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
   const int ver = c->tc_version;
   const int NBO = c->lu_block;
+  // panel width of the deferred version (32 or 64; versions 1 and 2 use 64)
+  const int nb = (ver >= 3 && c->lu_panel == 32) ? 32 : NB;
   if (NBO % NB != 0 || NBO < NB || NBO > kMaxLuBlock) return fail(BIE_ERR_INVALID_ARG, "LU block must be 128, 256 or 512");
   float* ub = reinterpret_cast<float*>((char*)scratch + 256);
-  const int64_t ub_stride = (int64_t)2 * n * tc2::KR;  // floats per matrix, 64-row panel
+  const int kr = 2 * nb;                                // reals along K of one panel's B^T
+  const int64_t ub_stride = (int64_t)2 * n * kr;        // floats per matrix, one panel
   float* ubo = ub + (int64_t)batch * ub_stride;
   const int64_t ubo_stride = (int64_t)2 * n * (2 * NBO);  // floats per matrix, outer block
   const float* Af = reinterpret_cast<const float*>(A);
@@ -563,7 +565,7 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
       return fail(BIE_ERR_STATE, "tcgen05 scratch too small");
     BIE_TRY(tc2::make_map_3d(&mA, A, (uint64_t)2 * n, (uint64_t)n, (uint64_t)batch, (uint64_t)2 * ld * 4,
                              (uint64_t)bstride * 8));
-    BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)tc2::KR, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)tc2::KR * 4,
+    BIE_TRY(tc2::make_map_3d(&mB, ub, (uint64_t)kr, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)kr * 4,
                              (uint64_t)ub_stride * 4));
     BIE_TRY(tc2::make_map_3d(&mBo, ubo, (uint64_t)2 * NBO, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)2 * NBO * 4,
                              (uint64_t)ubo_stride * 4));
@@ -572,13 +574,13 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   } else {
     BIE_TRY((set_smem_max(k_update_tc)));
   }
-  // B^T of U rows u0 .. u0+63, columns [cb, cend), into the panel (o = 0) or outer-block buffer
-  auto build = [&](int u0, int cb, int cend, bool outer, int koff) -> int {
+  // B^T of U rows u0 .. u0+rows-1, columns [cb, cend), into the panel or the outer-block buffer
+  auto build = [&](int u0, int cb, int cend, bool outer, int koff, int rows) -> int {
     if (cend <= cb) return BIE_OK;
     dim3 gb((unsigned)((cend - cb + 31) / 32), (unsigned)batch);
     BIE_LAUNCH(tc2::k_build_ub<<<gb, 256, 0, c->stream>>>(Af, bstride, n, ld, u0, cb, cend, outer ? ubo : ub,
-                                                          outer ? ubo_stride : ub_stride, outer ? 2 * NBO : tc2::KR,
-                                                          koff));
+                                                          outer ? ubo_stride : ub_stride, outer ? 2 * NBO : kr,
+                                                          koff, rows));
     return BIE_OK;
   };
   auto update = [&](int r0, int r1, int c0, int c1, int kc0, int kcols, bool outer, int ub_c0) -> int {
@@ -594,20 +596,20 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   if (ver >= 3) {
     for (int P0 = 0; P0 < n; P0 += NBO) {
       const int E = std::min(n, P0 + NBO);
-      for (int p0 = P0; p0 < E; p0 += NB) {
-        const int w = std::min(NB, E - p0), q = p0 + w;
+      for (int p0 = P0; p0 < E; p0 += nb) {
+        const int w = std::min(nb, E - p0), q = p0 + w;
         BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E));
-        if (q < E) {  // then w == 64 (E - P0 is a multiple of 64 unless E == n)
-          BIE_TRY(build(p0, q, E, false, 0));
+        if (q < E) {  // then w == nb (E - P0 is a multiple of nb unless E == n)
+          BIE_TRY(build(p0, q, E, false, 0, w));
           BIE_TRY(update(q, n, q, E, p0, w, false, q));
         }
       }
       if (E >= n) continue;  // E - P0 == NBO from here on
-      for (int b = 0; b < NBO / NB; ++b) {
-        const int Rb = P0 + b * NB;
-        BIE_TRY(update(Rb, Rb + NB, E, n, P0, b * NB, true, E));
-        BIE_TRY(lu_trsm_rows32(c, A, batch, n, ld, bstride, Rb, NB, E));
-        BIE_TRY(build(Rb, E, n, true, 2 * NB * b));
+      for (int b = 0; b < NBO / nb; ++b) {
+        const int Rb = P0 + b * nb;
+        BIE_TRY(update(Rb, Rb + nb, E, n, P0, b * nb, true, E));
+        BIE_TRY(lu_trsm_rows32(c, A, batch, n, ld, bstride, Rb, nb, E));
+        BIE_TRY(build(Rb, E, n, true, 2 * nb * b, nb));
       }
       BIE_TRY(update(E, n, E, n, P0, NBO, true, E));
     }
@@ -620,7 +622,7 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
     const int rem = n - p0 - w;
     if (rem <= 0) continue;
     if (ver == 2) {
-      BIE_TRY(build(p0, p0 + NB, n, false, 0));
+      BIE_TRY(build(p0, p0 + NB, n, false, 0, NB));
       BIE_TRY(update(p0 + NB, n, p0 + NB, n, p0, NB, false, p0 + NB));
     } else {
       dim3 g((unsigned)((rem + BN - 1) / BN), (unsigned)((rem + BM - 1) / BM), (unsigned)batch);
