@@ -812,8 +812,12 @@ def run_case(args):
         ks = w.k
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
         xo = torch.tensor(w.xobs, device="cuda")
-        T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
-        print("case field512:", tuple(T.shape))
+        ms = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)  # synchronises
+            ms.append(1e3 * (time.perf_counter() - t0))
+        print("case field512:", tuple(T.shape), "variant", args.field_variant, "ms", [round(x, 1) for x in ms])
     else:
         ks = w.k[496:504]
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")

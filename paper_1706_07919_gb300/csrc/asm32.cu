@@ -83,18 +83,6 @@ struct TwoPi3 {
   float c1, c2, c3, inv;
 };
 
-// e^{i t} for t = a.hi + a.lo (float-float, |t| < 2^20): t = n 2pi + u, n = rint(t / 2pi), u
-// reduced in float-float (the product n c1 cancels exactly against a.hi: both are multiples of
-// ulp(c1) and the difference is below pi), then cos/sin of u_hi + u_lo by cis_reduced.
-__device__ __forceinline__ void ff_cis(ff a, const TwoPi3& tp, float& c, float& s) {
-  const float n = round_small(__fmul_rn(a.hi, tp.inv));
-  const float h = __fmaf_rn(-n, tp.c1, a.hi);  // exact: both terms are multiples of ulp(c1)
-  float t = __fmaf_rn(-n, tp.c2, a.lo);
-  t = __fmaf_rn(-n, tp.c3, t);
-  const ff u = ff_two_sum(h, t);
-  cis_reduced(u.hi, u.lo, c, s);
-}
-
 struct Kern32 {
   float Gr, Gi, dGr, dGi;
   float alr, ali, ber, bei;  // g dG - dg G, f dG - df G (without w J)
@@ -105,28 +93,31 @@ struct Kern32 {
 __device__ __forceinline__ void kernel32(const ff k, const float kinv, const ff* xi, const ff* nui, const TwoPi3& tp,
                                          const float* q, Kern32& o, float far_r2 = 3.0e38f) {
   // r = x_q - x_i in float-float
-  const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
-  const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
-  const ff rz = ff_sub(ff{q[2], q[5]}, xi[2]);
-  const ff R2 = ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz));
-  const ff R = ff_sqrt(R2);
-  const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
+  const ff rx = ff_diff_lazy(ff{q[0], q[3]}, xi[0]);
+  const ff ry = ff_diff_lazy(ff{q[1], q[4]}, xi[1]);
+  const ff rz = ff_diff_lazy(ff{q[2], q[5]}, xi[2]);
+  const ff R2 = ff_norm2_lazy(rx, ry, rz);
+  float invR;
+  const ff R = ff_sqrt_lazy(R2, invR);
+  const ff nr = ff_dot3_lazy(nui, rx, ry, rz);
   float c, s;
-  ff_cis(ff_mul(k, R), tp, c, s);
-  const float invR = 1.0f / R.hi;
+  cis_ffprod(k, R, c, s);
   const float kR = k.hi * R.hi;
   o.Gr = c * invR;
   o.Gi = s * invR;
   float rnu;
-  if (R2.hi > far_r2)
-    rnu = rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8];
-  else
-    rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]})).hi;
+  if (R2.hi > far_r2) {
+    rnu = (rx.hi + rx.lo) * q[6] + (ry.hi + ry.lo) * q[7] + (rz.hi + rz.lo) * q[8];
+  } else {
+    const ff nq[3] = {ff{q[6], q[10]}, ff{q[7], q[11]}, ff{q[8], q[12]}};
+    const ff d = ff_dot3_lazy(nq, rx, ry, rz);
+    rnu = d.hi + d.lo;
+  }
   const float rn = rnu * invR * invR * invR;
   o.dGr = (-c - s * kR) * rn;
   o.dGi = (c * kR - s) * rn;
   float cg, sg;
-  ff_cis(ff_mul(k, nr), tp, cg, sg);
+  cis_ffprod(k, nr, cg, sg);
   const float nn = nui[0].hi * q[6] + nui[1].hi * q[7] + nui[2].hi * q[8];
   const float g = cg, f = kinv != 0.f ? sg * kinv : nr.hi, dg = -k.hi * sg * nn, df = cg * nn;
   o.alr = g * o.dGr - dg * o.Gr;
@@ -366,42 +357,46 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
           const float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
           const float q[P32COUNT] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x};
           // geometry, shared by the KB wavenumbers
-          const ff rx = ff_sub(ff{q[0], q[3]}, xi[0]);
-          const ff ry = ff_sub(ff{q[1], q[4]}, xi[1]);
-          const ff rz = ff_sub(ff{q[2], q[5]}, xi[2]);
-          const ff R2 = ff_add(ff_add(ff_sqr(rx), ff_sqr(ry)), ff_sqr(rz));
-          const ff R = ff_sqrt(R2);
-          const ff nr = ff_add(ff_add(ff_mul(nui[0], rx), ff_mul(nui[1], ry)), ff_mul(nui[2], rz));
-          const float invR = __frcp_rn(R.hi);  // correctly rounded, as 1.0f / R.hi
+          // float-float geometry with lazy tails (distance, 1/R, nu_i.r)
+          const ff rx = ff_diff_lazy(ff{q[0], q[3]}, xi[0]);
+          const ff ry = ff_diff_lazy(ff{q[1], q[4]}, xi[1]);
+          const ff rz = ff_diff_lazy(ff{q[2], q[5]}, xi[2]);
+          const ff R2 = ff_norm2_lazy(rx, ry, rz);
+          float invR;
+          const ff R = ff_sqrt_lazy(R2, invR);
+          const ff nr = ff_dot3_lazy(nui, rx, ry, rz);
           float rnu;
-          if (R2.hi > far_r2)
-            rnu = rx.hi * q[6] + ry.hi * q[7] + rz.hi * q[8];
-          else
-            rnu = ff_add(ff_add(ff_mul(rx, ff{q[6], q[10]}), ff_mul(ry, ff{q[7], q[11]})), ff_mul(rz, ff{q[8], q[12]}))
-                      .hi;
-          const float rn = rnu * invR * invR * invR;
+          if (R2.hi > far_r2) {
+            rnu = (rx.hi + rx.lo) * q[6] + (ry.hi + ry.lo) * q[7] + (rz.hi + rz.lo) * q[8];
+          } else {
+            const ff nq[3] = {ff{q[6], q[10]}, ff{q[7], q[11]}, ff{q[8], q[12]}};
+            const ff d = ff_dot3_lazy(nq, rx, ry, rz);
+            rnu = d.hi + d.lo;
+          }
           const float nn = nui[0].hi * q[6] + nui[1].hi * q[7] + nui[2].hi * q[8];
           const float wj = q[P32W];
+          // the weight rides on 1/R and on r.nu/R^3: G and dG/dnu below are w G and w dG/dnu
+          const float wiR = wj * invR, wrn = wj * (rnu * invR * invR * invR);
           float sh[6];
 #pragma unroll
           for (int a = 0; a < 6; ++a) sh[a] = shp[qq * 6 + a];
 #pragma unroll
           for (int j = 0; j < KB; ++j) {
             float c, s;
-            ff_cis(ff_mul(k[j], R), tp, c, s);
+            cis_ffprod(k[j], R, c, s);
             const float kR = k[j].hi * R.hi;
-            const float Gr = c * invR, Gi = s * invR;
-            const float dGr = (-c - s * kR) * rn, dGi = (c * kR - s) * rn;
+            const float Gr = c * wiR, Gi = s * wiR;
+            const float dGr = (-c - s * kR) * wrn, dGi = (c * kR - s) * wrn;
             float cg, sg;
-            ff_cis(ff_mul(k[j], nr), tp, cg, sg);
+            cis_ffprod(k[j], nr, cg, sg);
             const float g = cg, f = kinv[j] != 0.f ? sg * kinv[j] : nr.hi, dg = -k[j].hi * sg * nn, df = cg * nn;
-            ear[j] = __fmaf_rn(wj, g * dGr - dg * Gr, ear[j]);
-            eai[j] = __fmaf_rn(wj, g * dGi - dg * Gi, eai[j]);
-            ebr[j] = __fmaf_rn(wj, f * dGr - df * Gr, ebr[j]);
-            ebi[j] = __fmaf_rn(wj, f * dGi - df * Gi, ebi[j]);
+            ear[j] = __fmaf_rn(g, dGr, __fmaf_rn(-dg, Gr, ear[j]));
+            eai[j] = __fmaf_rn(g, dGi, __fmaf_rn(-dg, Gi, eai[j]));
+            ebr[j] = __fmaf_rn(f, dGr, __fmaf_rn(-df, Gr, ebr[j]));
+            ebi[j] = __fmaf_rn(f, dGi, __fmaf_rn(-df, Gi, ebi[j]));
             // into A: dG (hard) or -G (soft); into b: G kq (hard) or -dG kq (soft)
-            const float war = wj * (soft ? -Gr : dGr), wai = wj * (soft ? -Gi : dGi);
-            const float wbr = wj * (soft ? -dGr : Gr), wbi = wj * (soft ? -dGi : Gi);
+            const float war = soft ? -Gr : dGr, wai = soft ? -Gi : dGi;
+            const float wbr = soft ? -dGr : Gr, wbi = soft ? -dGi : Gi;
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
               ar[j][a] = __fmaf_rn(sh[a], war, ar[j][a]);
@@ -664,19 +659,9 @@ int ensure_mixed_tables(bie_ctx* c) {
 // Assembles nk FP32 systems: A [nk][N][lda] (cf), b [nk][N] (cd).  known [nk][N] (cd) receives the
 // known boundary values; rowsum scratch: nk * N * 6 doubles; kq scratch: nk * E * Q cf (the known
 // values at the quadrature points, used by the uniform-condition bulk kernel; may be NULL).
-int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq) {
-  const int64_t N = c->N;
-  BIE_TRY(ensure_mixed_tables(c));
-  dim3 gk((unsigned)((N + 255) / 256), nk);
-  BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known));
-  int rows = 16 / ASM_W;
-  while (rows > 1 && (size_t)rows * N * sizeof(cf) > 200 * 1024) rows /= 2;
-  const size_t smem = (size_t)rows * N * sizeof(cf);
-  if (smem > 200 * 1024)
-    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP32 shared-memory row accumulator");
-  if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
-  const TwoPi3 tp = two_pi3();
-  if (!(c->far_r2 > 0.0)) {  // (3 x longest element edge)^2, once per geometry
+// (3 x longest element edge)^2: beyond it a pair's r.nu is formed in FP32 (once per geometry)
+double far_radius2(bie_ctx* c) {
+  if (!(c->far_r2 > 0.0)) {
     double h2 = 0.0;
     for (int64_t e = 0; e < c->E; ++e)
       for (int a = 0; a < 3; ++a) {
@@ -690,6 +675,22 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
       }
     c->far_r2 = 9.0 * h2;
   }
+  return c->far_r2;
+}
+
+int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, cd* known, double* rowsum, cf* kq) {
+  const int64_t N = c->N;
+  BIE_TRY(ensure_mixed_tables(c));
+  dim3 gk((unsigned)((N + 255) / 256), nk);
+  BIE_LAUNCH(k_known64<<<gk, 256, 0, c->stream>>>(c->nodes, c->normals, c->bc, N, kv, c->dir[0], c->dir[1], c->dir[2], known));
+  int rows = 16 / ASM_W;
+  while (rows > 1 && (size_t)rows * N * sizeof(cf) > 200 * 1024) rows /= 2;
+  const size_t smem = (size_t)rows * N * sizeof(cf);
+  if (smem > 200 * 1024)
+    return fail(BIE_ERR_INVALID_ARG, "N = " + std::to_string(N) + " too large for the FP32 shared-memory row accumulator");
+  if (c->rule.Q > 64) return fail(BIE_ERR_INVALID_ARG, "standard rule too large");
+  const TwoPi3 tp = two_pi3();
+  far_radius2(c);
   if (c->uniform_bc < 0) {  // does every element carry one condition on its six nodes?
     c->uniform_bc = 1;
     for (int64_t e = 0; e < c->E && c->uniform_bc; ++e)

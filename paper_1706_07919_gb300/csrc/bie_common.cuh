@@ -269,6 +269,49 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {  // a > 0
   r = __fadd_rn(r, a.lo);
   return ff_fast_two_sum(y, __fdividef(r, 2.0f * y));
 }
+// ---- float-float geometry with lazy tails -------------------------------------------------
+// Distances and projections for the FP32 kernels' phases keep head + tail as an unevaluated sum
+// without renormalising it: a tail may reach a few ulp of the coordinates (a difference of
+// nearby points), and every consumer (error-free products, cis_ffprod, the square root below)
+// takes head and tail as they are.  Relative errors: about 2e-11 on R, 1 ulp on 1/R.
+__device__ __forceinline__ ff ff_diff_lazy(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, -b.hi);
+  return {s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo))};
+}
+// x^2 + y^2 + z^2: the heads' squares error-free (FMA), their sum by two error-free additions,
+// and the errors with the tails' terms 2 hi lo + lo^2 gathered into the tail.
+__device__ __forceinline__ ff ff_norm2_lazy(ff x, ff y, ff z) {
+  const float px = __fmul_rn(x.hi, x.hi), py = __fmul_rn(y.hi, y.hi), pz = __fmul_rn(z.hi, z.hi);
+  float ex = __fmaf_rn(x.hi, x.hi, -px), ey = __fmaf_rn(y.hi, y.hi, -py), ez = __fmaf_rn(z.hi, z.hi, -pz);
+  ex = __fmaf_rn(x.lo, x.lo, __fmaf_rn(x.hi + x.hi, x.lo, ex));
+  ey = __fmaf_rn(y.lo, y.lo, __fmaf_rn(y.hi + y.hi, y.lo, ey));
+  ez = __fmaf_rn(z.lo, z.lo, __fmaf_rn(z.hi + z.hi, z.lo, ez));
+  const ff s1 = ff_two_sum(px, py), s2 = ff_two_sum(s1.hi, pz);
+  return {s2.hi, __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(s1.lo, s2.lo))};
+}
+// a . (x, y, z) for a float-float vector a: error-free head products (FMA, with the cross
+// terms), two error-free additions, errors gathered into the tail.
+__device__ __forceinline__ ff ff_dot3_lazy(const ff* a, ff x, ff y, ff z) {
+  const float p0 = __fmul_rn(a[0].hi, x.hi), p1 = __fmul_rn(a[1].hi, y.hi), p2 = __fmul_rn(a[2].hi, z.hi);
+  float e0 = __fmaf_rn(a[0].hi, x.hi, -p0), e1 = __fmaf_rn(a[1].hi, y.hi, -p1), e2 = __fmaf_rn(a[2].hi, z.hi, -p2);
+  e0 = __fmaf_rn(a[0].hi, x.lo, __fmaf_rn(a[0].lo, x.hi, e0));
+  e1 = __fmaf_rn(a[1].hi, y.lo, __fmaf_rn(a[1].lo, y.hi, e1));
+  e2 = __fmaf_rn(a[2].hi, z.lo, __fmaf_rn(a[2].lo, z.hi, e2));
+  const ff s1 = ff_two_sum(p0, p1), s2 = ff_two_sum(s1.hi, p2);
+  return {s2.hi, __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), e2), __fadd_rn(s1.lo, s2.lo))};
+}
+// R = sqrt(a) and inv = 1/R for a float-float a > 0 (a lazy tail): y0 = rsqrt(fl(a.hi + a.lo))
+// (2 ulp), R.hi = fl(a) y0, R.lo = ((a.hi - R.hi^2) + a.lo) y0 / 2 (the residual by FMA: one
+// Newton step, error about y0's squared), inv = y0 + y0 (1 - R.hi y0) / 2 (one Newton step).
+__device__ __forceinline__ ff ff_sqrt_lazy(ff a, float& inv) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float y0 = rsqrtf(s);
+  const float y = __fmul_rn(s, y0);
+  const float h = 0.5f * y0;
+  inv = __fmaf_rn(h, __fmaf_rn(-y, y0, 1.0f), y0);
+  return {y, __fmul_rn(__fadd_rn(__fmaf_rn(-y, y, a.hi), a.lo), h)};
+}
+
 __host__ __device__ __forceinline__ ff ff_from_double(double x) {
   float hi = (float)x;
   return {hi, (float)(x - (double)hi)};
@@ -314,6 +357,53 @@ __device__ __forceinline__ void cis_reduced(float vh, float vl, float& c, float&
   const float a = (qi & 1) ? sv : cv, b = (qi & 1) ? cv : sv;
   c = (qi == 1 || qi == 2) ? -a : a;
   s = (qi >= 2) ? -b : b;
+}
+
+// pi/2 as an unevaluated sum of three floats: h1 = fl32(pi/2), h2 = fl32(pi/2 - h1),
+// h3 = fl32(pi/2 - h1 - h2), from pi to 200 bits; the remainder is below 1.1e-23.
+constexpr float kHalfPi1 = 1.57079637050628662f;
+constexpr float kHalfPi2 = -4.37113882867379e-8f;
+constexpr float kHalfPi3 = -1.71512451000588e-15f;
+
+// e^{i t} for t = p + e, p a float with |p| < 2^20 and e a correction of a few ulp(p) (the tail
+// of an error-free product), in one reduction: n = rint(p 2/pi), u = (p - n h1) + (e - n h2 -
+// n h3).  The first difference is exact under FMA: for |p| >= 1 both p and n h1 are multiples of
+// ulp(h1) = 2^-23 and the difference is below 1; below 1, n is 0 or +-1 and the difference is a
+// multiple of ulp(p) below 1.  u then rounds once to FP32 (|u| <= pi/4 plus the quotient's
+// rounding), and cos/sin of u come from the Taylor series of cis_reduced, placed in the quadrant
+// n mod 4 (read from the low bits of the rounding sum).
+__device__ __forceinline__ void cis_split(float p, float e, float& c, float& s) {
+  const float kTwoOverPi = 0.636619772367581343f;
+  const float qm = __fmaf_rn(p, kTwoOverPi, kRoundMagic);
+  const float n = __fsub_rn(qm, kRoundMagic);
+  const float h = __fmaf_rn(-n, kHalfPi1, p);
+  float t = __fmaf_rn(-n, kHalfPi2, e);
+  t = __fmaf_rn(-n, kHalfPi3, t);
+  const float v = __fadd_rn(h, t);
+  const float v2 = v * v;
+  float ps = __fmaf_rn(v2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);  // 1/9!, -1/7!
+  ps = __fmaf_rn(v2, ps, 8.33333333333333333e-3f);                              // 1/5!
+  ps = __fmaf_rn(v2, ps, -1.66666666666666667e-1f);                             // -1/3!
+  const float sv = __fmaf_rn(v * v2, ps, v);
+  float pc = __fmaf_rn(v2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+  pc = __fmaf_rn(v2, pc, -1.38888888888888889e-3f);                             // -1/6!
+  pc = __fmaf_rn(v2, pc, 4.16666666666666667e-2f);                              // 1/4!
+  pc = __fmaf_rn(v2, pc, -0.5f);
+  const float cv = __fmaf_rn(v2, pc, 1.0f);
+  const int qi = __float_as_int(qm) & 3;
+  const float a = (qi & 1) ? sv : cv, b = (qi & 1) ? cv : sv;
+  c = (qi == 1 || qi == 2) ? -a : a;
+  s = (qi >= 2) ? -b : b;
+}
+
+// e^{i k R} for float-float k and R (|k R| < 2^20): the product's head and its error-free tail
+// (with the cross terms) go to cis_split without renormalisation.
+__device__ __forceinline__ void cis_ffprod(ff k, ff R, float& c, float& s) {
+  const float p = __fmul_rn(k.hi, R.hi);
+  float e = __fmaf_rn(k.hi, R.hi, -p);
+  e = __fmaf_rn(k.hi, R.lo, e);
+  e = __fmaf_rn(k.lo, R.hi, e);
+  cis_split(p, e, c, s);
 }
 
 // Barrier of the nthreads threads (whole warps) that use barrier `id` (1..15; 0 is

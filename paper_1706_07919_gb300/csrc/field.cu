@@ -294,18 +294,9 @@ __global__ void __launch_bounds__(FT) k_field32(const int32_t* __restrict__ elem
 
 // k-batched variant of the float-float kernel: each (point, quadrature point) pair's geometry --
 // the float-float distances to x_p and x0, nu0.(x - x0), r.nu -- is formed once and reused for FKB
-// wavenumbers; per wavenumber only the three phases (float-float product and 2 pi reduction,
-// then cis_reduced) and the FP32 integrand remain.
+// wavenumbers; per wavenumber only the three phases (float-float product reduced by pi/2 in one
+// step, cis_ffprod) and the FP32 integrand remain.
 constexpr int FKB = 8;
-
-__device__ __forceinline__ void cis_ffk(ff a, const TwoPi3f& tp, float& c, float& s) {
-  const float n = round_small(__fmul_rn(a.hi, tp.inv));
-  const float h = __fmaf_rn(-n, tp.c1, a.hi);
-  float t = __fmaf_rn(-n, tp.c2, a.lo);
-  t = __fmaf_rn(-n, tp.c3, t);
-  const ff u = ff_two_sum(h, t);
-  cis_reduced(u.hi, u.lo, c, s);
-}
 
 __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ elems, int64_t N, int64_t EQ,
                                                  const float* __restrict__ qtab, const cf* __restrict__ Pq,
@@ -391,12 +382,12 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
       if (uniform) {
         const ff k0 = {sk[0][0], sk[0][1]};
-        cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
-        cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
-        cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
-        cis_ffk(ff_mul(dk, Rp), tp, dcp, dsp);
-        cis_ffk(ff_mul(dk, R0), tp, dc0, ds0);
-        cis_ffk(ff_mul(dk, nr), tp, dcg, dsg);
+        cis_ffprod(k0, Rp, cp, spp);
+        cis_ffprod(k0, R0, c0, s0v);
+        cis_ffprod(k0, nr, cg, sgv);
+        cis_ffprod(dk, Rp, dcp, dsp);
+        cis_ffprod(dk, R0, dc0, ds0);
+        cis_ffprod(dk, nr, dcg, dsg);
       }
 #pragma unroll
       for (int j = 0; j < FKB; ++j) {
@@ -404,9 +395,9 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
           const ff k = {sk[j][0], sk[j][1]};
           const float kinv = sk[j][2];
           if (!uniform) {
-            cis_ffk(ff_mul(k, Rp), tp, cp, spp);
-            cis_ffk(ff_mul(k, R0), tp, c0, s0v);
-            cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+            cis_ffprod(k, Rp, cp, spp);
+            cis_ffprod(k, R0, c0, s0v);
+            cis_ffprod(k, nr, cg, sgv);
           } else if (j > 0) {
             float t = cp * dcp - spp * dsp;
             spp = spp * dcp + cp * dsp;
@@ -446,8 +437,9 @@ __global__ void __launch_bounds__(FT) k_field32b(const int32_t* __restrict__ ele
 // Variant of k_field32b with the wavenumber-group size KB, the points per CTA TP and the minimum
 // resident CTAs MINB as template parameters: terms are summed in FP32 over runs of 32 quadrature
 // points and each run is added to a compensated sum kept in shared memory, so only 2 KB partial
-// sums stay in registers; the phase step e^{i dk R} takes its phase from an FMA-split product
-// (no 2 pi reduction in float-float: dk R is small).
+// sums stay in registers; every phase (group start k_0 R and step dk R) comes from the
+// float-float product reduced by pi/2 in one step (cis_ffprod).  far_r2: beyond it r0.nu_q is
+// formed in FP32.
 // ZF: the group may hold k = 0 (f takes its limit nu0.r there); false for groups of k > 0 only,
 // which keeps the zero-frequency select out of the inner loop.
 template <int KB, int TP, int MINB, int UT, bool ZF>
@@ -457,7 +449,8 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
                                                        const double* __restrict__ xp, int64_t M,
                                                        const int32_t* __restrict__ foot_elem,
                                                        const double* __restrict__ foot, const double* __restrict__ kv,
-                                                       int nk, cd* __restrict__ T, TwoPi3f tp, int uniform, ff dk) {
+                                                       int nk, cd* __restrict__ T, int uniform, ff dk,
+                                                       float far_r2) {
   __shared__ float4 sg[UT][4];  // a tile of UT quadrature points: 13 table values (P32 order), padded
   __shared__ float4 sq[KB][UT];  // surface values at the tile's points: P re, im, dP re, im
   __shared__ float4 s0[KB][TP];  // surface values at the foot points, same order
@@ -526,32 +519,41 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
       const ff qx = {g0.x, g0.w}, qy = {g0.y, g1.x}, qz = {g0.z, g1.y};
       const float nx = g1.z, ny = g1.w, nz = g2.x, wj = g2.y;
       const ff nux = {nx, g2.z}, nuy = {ny, g2.w}, nuz = {nz, g3.x};
-      const ff rpx = ff_sub(qx, p[0]), rpy = ff_sub(qy, p[1]), rpz = ff_sub(qz, p[2]);
-      const ff r0x = ff_sub(qx, x0[0]), r0y = ff_sub(qy, x0[1]), r0z = ff_sub(qz, x0[2]);
-      const ff Rp = ff_sqrt(ff_add(ff_add(ff_sqr(rpx), ff_sqr(rpy)), ff_sqr(rpz)));
-      const ff R0 = ff_sqrt(ff_add(ff_add(ff_sqr(r0x), ff_sqr(r0y)), ff_sqr(r0z)));
-      const ff nr = ff_add(ff_add(ff_mul(nu0[0], r0x), ff_mul(nu0[1], r0y)), ff_mul(nu0[2], r0z));
-      const float iRp = 1.0f / Rp.hi, iR0 = 1.0f / R0.hi;
+      // float-float geometry with lazy tails (distances, 1/R, nu0.r)
+      const ff rpx = ff_diff_lazy(qx, p[0]), rpy = ff_diff_lazy(qy, p[1]), rpz = ff_diff_lazy(qz, p[2]);
+      const ff r0x = ff_diff_lazy(qx, x0[0]), r0y = ff_diff_lazy(qy, x0[1]), r0z = ff_diff_lazy(qz, x0[2]);
+      const ff R0sq = ff_norm2_lazy(r0x, r0y, r0z);
+      float iRp, iR0;
+      const ff Rp = ff_sqrt_lazy(ff_norm2_lazy(rpx, rpy, rpz), iRp);
+      const ff R0 = ff_sqrt_lazy(R0sq, iR0);
+      const ff nr = ff_dot3_lazy(nu0, r0x, r0y, r0z);
       // the recurrences below carry the weighted kernels Gp = w e^{ik Rp} / Rp and G0 (same for
       // the foot point); then dG/dnu = G (ik R - 1) r.nu / R^2
       const float ap = wj * iRp, a0 = wj * iR0;
-      const float rnp = (rpx.hi * nx + rpy.hi * ny + rpz.hi * nz) * iRp * iRp;
-      const float rn0 = ff_add(ff_add(ff_mul(r0x, nux), ff_mul(r0y, nuy)), ff_mul(r0z, nuz)).hi * iR0 * iR0;
+      const float rnp = ((rpx.hi + rpx.lo) * nx + (rpy.hi + rpy.lo) * ny + (rpz.hi + rpz.lo) * nz) * iRp * iRp;
+      // r0.nu is second-order small near the foot point (error-free products there); beyond
+      // far_r2 its FP32 rounding eps R0 perturbs dG0 by eps / R0^2, the term's own rounding
+      float rn0;
+      if (R0sq.hi > far_r2) {
+        rn0 = (r0x.hi + r0x.lo) * nx + (r0y.hi + r0y.lo) * ny + (r0z.hi + r0z.lo) * nz;
+      } else {
+        const ff nuq[3] = {nux, nuy, nuz};
+        const ff d = ff_dot3_lazy(nuq, r0x, r0y, r0z);
+        rn0 = d.hi + d.lo;
+      }
+      rn0 *= iR0 * iR0;
       const float nn = nu0[0].hi * nx + nu0[1].hi * ny + nu0[2].hi * nz;
       float cp = 0.f, spp = 0.f, c0 = 0.f, s0v = 0.f, cg = 0.f, sgv = 0.f;
       float dcp = 1.f, dsp = 0.f, dc0 = 1.f, ds0 = 0.f, dcg = 1.f, dsg = 0.f;
       if (uniform) {
         const ff k0 = {sk[0].x, sklo[0]};
-        cis_ffk(ff_mul(k0, Rp), tp, cp, spp);
-        cis_ffk(ff_mul(k0, R0), tp, c0, s0v);
-        cis_ffk(ff_mul(k0, nr), tp, cg, sgv);
-        // step phases dk R: FP32 head plus its exact FMA error and the cross terms as the tail
-        float h = dk.hi * Rp.hi;
-        cis_reduced(h, __fmaf_rn(dk.hi, Rp.hi, -h) + (dk.hi * Rp.lo + dk.lo * Rp.hi), dcp, dsp);
-        h = dk.hi * R0.hi;
-        cis_reduced(h, __fmaf_rn(dk.hi, R0.hi, -h) + (dk.hi * R0.lo + dk.lo * R0.hi), dc0, ds0);
-        h = dk.hi * nr.hi;
-        cis_reduced(h, __fmaf_rn(dk.hi, nr.hi, -h) + (dk.hi * nr.lo + dk.lo * nr.hi), dcg, dsg);
+        cis_ffprod(k0, Rp, cp, spp);
+        cis_ffprod(k0, R0, c0, s0v);
+        cis_ffprod(k0, nr, cg, sgv);
+        // step phases dk R
+        cis_ffprod(dk, Rp, dcp, dsp);
+        cis_ffprod(dk, R0, dc0, ds0);
+        cis_ffprod(dk, nr, dcg, dsg);
         cp *= ap; spp *= ap;
         c0 *= a0; s0v *= a0;
       }
@@ -562,9 +564,9 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
           const float khi = kj.x, kinv = kj.y;
           if (!uniform) {
             const ff k = {khi, sklo[j]};
-            cis_ffk(ff_mul(k, Rp), tp, cp, spp);
-            cis_ffk(ff_mul(k, R0), tp, c0, s0v);
-            cis_ffk(ff_mul(k, nr), tp, cg, sgv);
+            cis_ffprod(k, Rp, cp, spp);
+            cis_ffprod(k, R0, c0, s0v);
+            cis_ffprod(k, nr, cg, sgv);
             cp *= ap; spp *= ap;
             c0 *= a0; s0v *= a0;
           } else if (j > 0) {
@@ -627,17 +629,21 @@ __global__ void __launch_bounds__(TP, MINB) k_field32c(const int32_t* __restrict
   }
 }
 
+double far_radius2(bie_ctx* c);
+
 template <int KB, int TP, int MINB, int UT>
 static void launch_field32c(bie_ctx* c, int64_t EQ, const cf* Pq, const cf* Pnq, const cd* surf, const double* xp,
                             int64_t M, const int32_t* foot_elem, const double* foot, const double* kv, int nk, cd* T,
                             TwoPi3f tp, int uniform, ff dk, bool zero) {
+  (void)tp;
   dim3 gb((unsigned)((M + TP - 1) / TP), (unsigned)((nk + KB - 1) / KB));
+  const float far_r2 = (float)far_radius2(c);
   if (zero)
-    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, true><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf,
-                                                                          xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dk));
+    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, true><<<gb, TP, 0, c->stream>>>(
+        c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, uniform, dk, far_r2));
   else
-    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, false><<<gb, TP, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf,
-                                                                           xp, M, foot_elem, foot, kv, nk, T, tp, uniform, dk));
+    BIE_LAUNCH(k_field32c<KB, TP, MINB, UT, false><<<gb, TP, 0, c->stream>>>(
+        c->elems, c->N, EQ, c->qgeo32, Pq, Pnq, surf, xp, M, foot_elem, foot, kv, nk, T, uniform, dk, far_r2));
 }
 
 int ensure_mixed_tables(bie_ctx* c);
