@@ -818,6 +818,11 @@ def run_case(args):
             T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)  # synchronises
             ms.append(1e3 * (time.perf_counter() - t0))
         print("case field512:", tuple(T.shape), "variant", args.field_variant, "ms", [round(x, 1) for x in ms])
+    elif args.case == "field_sample":  # all 512 wavenumbers at every 8th point (profiler captures)
+        surf = torch.full((len(w.k), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
+        xo = torch.tensor(w.xobs[::8], device="cuda")
+        T = sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
+        print("case field_sample:", tuple(T.shape))
     else:
         ks = w.k[496:504]
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -861,7 +866,7 @@ def main():
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
     ap.add_argument("--uneven-workers", dest="uneven_workers", type=int, default=4)
-    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "batch", "learned", "step", "peaks", "phases",
+    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "field_sample", "batch", "learned", "step", "peaks", "phases",
                                        "uneven_full"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
