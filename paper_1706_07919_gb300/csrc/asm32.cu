@@ -351,11 +351,24 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
         float sr[KB], si[KB], ear[KB], eai[KB], ebr[KB], ebi[KB];
 #pragma unroll
         for (int j = 0; j < KB; ++j) sr[j] = si[j] = ear[j] = eai[j] = ebr[j] = ebi[j] = 0.f;
+        // the point's 64-byte record (colour-sorted, point-major: four 16-byte loads); the next
+        // point's is loaded while this one is computed
+        const float4* qp = qaos + ((int64_t)qlo * E + t) * 4;
+        float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
+        cf kqn[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) kqn[j] = kq[((int64_t)min(k0 + j, nk - 1) * Q + qlo) * E + t];
         for (int qq = qlo; qq < qhi; ++qq) {
-          // the point's 64-byte record (colour-sorted, point-major): four 16-byte loads
-          const float4* qp = qaos + ((int64_t)qq * E + t) * 4;
-          const float4 v0 = qp[0], v1 = qp[1], v2 = qp[2], v3 = qp[3];
           const float q[P32COUNT] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x};
+          cf kqc[KB];
+#pragma unroll
+          for (int j = 0; j < KB; ++j) kqc[j] = kqn[j];
+          if (qq + 1 < qhi) {
+            const float4* qn = qaos + ((int64_t)(qq + 1) * E + t) * 4;
+            v0 = qn[0]; v1 = qn[1]; v2 = qn[2]; v3 = qn[3];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) kqn[j] = kq[((int64_t)min(k0 + j, nk - 1) * Q + qq + 1) * E + t];
+          }
           // geometry, shared by the KB wavenumbers
           // float-float geometry with lazy tails (distance, 1/R, nu_i.r)
           const ff rx = ff_diff_lazy(ff{q[0], q[3]}, xi[0]);
@@ -402,7 +415,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
               ar[j][a] = __fmaf_rn(sh[a], war, ar[j][a]);
               ai[j][a] = __fmaf_rn(sh[a], wai, ai[j][a]);
             }
-            const cf kqv = kq[((int64_t)min(k0 + j, nk - 1) * Q + qq) * E + t];
+            const cf kqv = kqc[j];
             sr[j] = __fmaf_rn(wbr, kqv.re, __fmaf_rn(-wbi, kqv.im, sr[j]));
             si[j] = __fmaf_rn(wbr, kqv.im, __fmaf_rn(wbi, kqv.re, si[j]));
           }
