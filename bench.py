@@ -177,6 +177,7 @@ def run_ours(args):
     sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.lu_block", args.lu_block)
     sol.set_option("mixed.lu_panel", args.lu_panel)
+    sol.set_option("mixed.lu_tile", args.lu_tile)
     sol.set_option("mixed.asm_kb", args.asm_kb)
     sol.set_option("field.variant", args.field_variant)
     sol.set_option("mixed.batch", args.batch)
@@ -762,6 +763,7 @@ def run_case(args):
     sol.set_option("mixed.tcgen05", args.tc)
     sol.set_option("mixed.lu_block", args.lu_block)
     sol.set_option("mixed.lu_panel", args.lu_panel)
+    sol.set_option("mixed.lu_tile", args.lu_tile)
     sol.set_option("mixed.asm_kb", args.asm_kb)
     sol.set_option("field.variant", args.field_variant)
     if args.case == "phases":  # one untimed sweep, then one with phase timing (device times per phase)
@@ -842,6 +844,7 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--lu-block", type=int, default=256, help="columns of the deferred LU update (128, 256, 512)")
     ap.add_argument("--lu-panel", type=int, default=64, help="panel width of the deferred LU update (64, 32)")
+    ap.add_argument("--lu-tile", type=int, default=256, help="real columns of the LU update tile (256, 128)")
     ap.add_argument("--field-variant", type=int, default=2,
                     help="mixed field kernel: 2 (128 points per CTA, 32-point tiles), 1 (64 points), 0 (k_field32b)")
     ap.add_argument("--asm-kb", type=int, default=2,

@@ -112,6 +112,7 @@ typedef struct {
   double us_per_k;     /* measured time per wavenumber of the chosen setting */
   int32_t lu_block;    /* columns over which the deferred update runs ("mixed.lu_block") */
   int32_t lu_panel;    /* panel width of the deferred version ("mixed.lu_panel") */
+  int32_t lu_tile;     /* real columns of the update tile ("mixed.lu_tile") */
 } bie_tune_result;
 
 /* Device time of the phases of the last BIE_MODE_MIXED call (bie_get_phase_times), recorded
@@ -215,6 +216,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "mixed.lu_block"       columns of the deferred update of version 3: 128, 256 (default), 512
  *   "mixed.lu_panel"       panel width of version 3: 64 (default) or 32 (more, narrower panels:
  *                          shorter pivot chains per leaf, narrower K = 32 updates inside a block)
+ *   "mixed.lu_tile"        tile of the tensor-core update (versions 2, 3): 128 rows x 256 real
+ *                          columns (default; MMA N = 256) or 128 x 128 (MMA N = 128)
  *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
@@ -365,8 +368,8 @@ int bie_measure_peaks(int cuda_device, bie_peaks* out);
  * k host f64 [nk], repeated to fill the batch) for every candidate of "mixed.batch" in
  * {8, 16, 32, 64, 128, 256} that fits a third of free device memory and "mixed.tcgen05" in {3, 2}
  * (with "mixed.lu_block" 256), then, if version 3 won, "mixed.lu_block" 128 and 512 at the chosen
- * batch and then "mixed.lu_panel" 32 at the chosen batch and block, and sets the fastest per
- * wavenumber on the context.  cache_path (host string or NULL): a JSON
+ * batch, then "mixed.lu_panel" 32 at the chosen batch and block, then "mixed.lu_tile" 128, and
+ * sets the fastest per wavenumber on the context.  cache_path (host string or NULL): a JSON
  * file keyed by N rounded up to 64; an entry for this N is applied without measuring, a new
  * measurement is added to it.  out (host, optional) receives the choice.  Synchronises.
  * Errors: STATE without geometry, OOM if no candidate fits, INVALID_ARG if the cache cannot be

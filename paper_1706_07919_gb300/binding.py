@@ -59,7 +59,7 @@ class BieLearnedInfo(ctypes.Structure):
 class BieTuneResult(ctypes.Structure):
     _fields_ = [("n_bucket", ctypes.c_int32), ("batch", ctypes.c_int32), ("tcgen05", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("us_per_k", ctypes.c_double), ("lu_block", ctypes.c_int32),
-                ("lu_panel", ctypes.c_int32)]
+                ("lu_panel", ctypes.c_int32), ("lu_tile", ctypes.c_int32)]
 
 
 class BiePhaseTimes(ctypes.Structure):

@@ -130,6 +130,7 @@ struct bie_ctx {
   int lu_block = 256;                // mixed.tcgen05 3: columns over which the trailing update is
                                      // deferred (128, 256 or 512)
   int lu_panel = 64;                 // mixed.tcgen05 3: panel width (32 or 64)
+  int lu_tile = 256;                 // mixed.tcgen05 2, 3: update tile width in real columns (256 or 128)
   int mixed_batch = 64;              // wavenumbers per batch
   int refine_it_max = 10;            // refinement corrections per system
   int refine64_it_max = 30;          // corrections against the FP64 re-assembly of flagged systems

@@ -389,6 +389,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value != 128.0 && value != 256.0 && value != 512.0)
       return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 128, 256 or 512");
     c->lu_block = (int)value;
+  } else if (n == "mixed.lu_tile") {
+    if (value != 128.0 && value != 256.0) return fail(BIE_ERR_INVALID_ARG, "mixed.lu_tile must be 128 or 256");
+    c->lu_tile = (int)value;
   } else if (n == "mixed.lu_panel") {
     if (value != 32.0 && value != 64.0) return fail(BIE_ERR_INVALID_ARG, "mixed.lu_panel must be 32 or 64");
     c->lu_panel = (int)value;

@@ -239,13 +239,16 @@ __global__ void __launch_bounds__(128, 2) k_update_tc(float* __restrict__ A, int
 namespace tc2 {
 
 constexpr int BM = 128;                  // rows per tile
-constexpr int BNR = 256;                 // real columns per tile (128 complex)
 constexpr int KCH = 32;                  // floats per 128-byte swizzle row
 constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KCH * 4;    // 16 KB
-constexpr int B_STAGE = BNR * KCH * 4;   // 32 KB (two 128-row TMA boxes)
-constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 2 * A_STAGE + 1024;  // ring + 2 epilogue boxes
-constexpr int TMEM_COLS = 512;           // two 256-column accumulators
+// BNR: real columns per tile, 256 (128 complex; the default) or 128, a template parameter of
+// the kernel ("mixed.lu_tile"): B stage BNR x 32 floats (one 128-row TMA box per 128 rows),
+// two BNR-column accumulators in TMEM
+template <int BNR>
+constexpr int b_stage() { return BNR * KCH * 4; }
+template <int BNR>
+constexpr int smem_bytes() { return STAGES * (A_STAGE + b_stage<BNR>()) + 2 * A_STAGE + 1024; }  // ring + 2 boxes
 constexpr int NTHREADS = 192;
 constexpr uint32_t SPIN = 1u << 22;
 
@@ -287,7 +290,8 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-__host__ __device__ constexpr uint32_t idesc_m128n128() {
+template <int BNR>
+__host__ __device__ constexpr uint32_t idesc_m128() {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BNR >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -343,9 +347,13 @@ struct Region {
   int r0, r1, c0, c1, kc0, nchk, ub_c0, ntm, ntn;
 };
 
+template <int BNR>
 __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, int batch,
                                                            const Region rg, int32_t* __restrict__ err) {
+  static_assert(BNR == 128 || BNR == 256, "tile of 128 or 256 real columns");
+  constexpr int B_STAGE = b_stage<BNR>();
+  constexpr int TMEM_COLS = 2 * BNR;  // two BNR-column accumulators (a power of two >= 32)
   extern __shared__ unsigned char smraw[];
   __shared__ Bars bar;
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -388,15 +396,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
           if (!ok) break;
           mbar_expect_tx(baddr(bar.full[s]), A_STAGE + B_STAGE);
           tma_load_3d(smA + s * A_STAGE, &tmA, 2 * rg.kc0 + ch * KCH, rg.r0 + tm * BM, z, baddr(bar.full[s]));
-          const int yb = 2 * (rg.c0 - rg.ub_c0) + tn * BNR;  // B^T rows of the tile, two boxes of BM rows
-          tma_load_3d(smB + s * B_STAGE, &tmB, ch * KCH, yb, z, baddr(bar.full[s]));
-          tma_load_3d(smB + s * B_STAGE + BM * KCH * 4, &tmB, ch * KCH, yb + BM, z, baddr(bar.full[s]));
+          const int yb = 2 * (rg.c0 - rg.ub_c0) + tn * BNR;  // B^T rows of the tile, boxes of BM rows
+#pragma unroll
+          for (int bx = 0; bx < BNR / BM; ++bx)
+            tma_load_3d(smB + s * B_STAGE + bx * BM * KCH * 4, &tmB, ch * KCH, yb + bx * BM, z, baddr(bar.full[s]));
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer ----
-      const uint32_t idesc = idesc_m128n128();
+      const uint32_t idesc = idesc_m128<BNR>();
       uint32_t it = 0, ti = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++ti) {
@@ -569,7 +578,8 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
                              (uint64_t)ub_stride * 4));
     BIE_TRY(tc2::make_map_3d(&mBo, ubo, (uint64_t)2 * NBO, (uint64_t)2 * n, (uint64_t)batch, (uint64_t)2 * NBO * 4,
                              (uint64_t)ubo_stride * 4));
-    BIE_TRY((set_smem_max(tc2::k_update_tc2)));
+    BIE_TRY((set_smem_max(tc2::k_update_tc2<256>)));
+    BIE_TRY((set_smem_max(tc2::k_update_tc2<128>)));
     BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   } else {
     BIE_TRY((set_smem_max(k_update_tc)));
@@ -583,14 +593,20 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
                                                           koff, rows));
     return BIE_OK;
   };
+  // tile width in real columns ("mixed.lu_tile": 256 = 128 complex columns, or 128)
+  const int bnr = c->lu_tile == 128 ? 128 : 256;
   auto update = [&](int r0, int r1, int c0, int c1, int kc0, int kcols, bool outer, int ub_c0) -> int {
     if (r1 <= r0 || c1 <= c0 || kcols <= 0) return BIE_OK;
     tc2::Region rg{r0, r1, c0, c1, kc0, 2 * kcols / tc2::KCH, ub_c0, (r1 - r0 + tc2::BM - 1) / tc2::BM,
-                   (c1 - c0 + tc2::BNR / 2 - 1) / (tc2::BNR / 2)};
+                   (c1 - c0 + bnr / 2 - 1) / (bnr / 2)};
     const int ntiles = rg.ntm * rg.ntn * batch;
     const int grid = std::min(ntiles, nsm);
-    BIE_LAUNCH(tc2::k_update_tc2<<<grid, tc2::NTHREADS, tc2::SMEM_BYTES, c->stream>>>(mA, outer ? mBo : mB, batch, rg,
-                                                                                     err));
+    if (bnr == 256)
+      BIE_LAUNCH(tc2::k_update_tc2<256><<<grid, tc2::NTHREADS, tc2::smem_bytes<256>(), c->stream>>>(
+          mA, outer ? mBo : mB, batch, rg, err));
+    else
+      BIE_LAUNCH(tc2::k_update_tc2<128><<<grid, tc2::NTHREADS, tc2::smem_bytes<128>(), c->stream>>>(
+          mA, outer ? mBo : mB, batch, rg, err));
     return BIE_OK;
   };
   if (ver >= 3) {

@@ -2,11 +2,12 @@
 // For a geometry of N nodes the tuner times one batch of mixed-precision frequency solves for
 // every candidate (wavenumbers per batch x LU trailing-update kernel) and keeps the fastest per
 // wavenumber, then for the deferred update (tcgen05 = 3) the block over which it is deferred
-// (128, 256, 512 columns) and the panel width (64, 32) at the chosen batch.  Results are cached per
-// N bucket (N rounded up to a multiple of 64) in a small JSON file:
+// (128, 256, 512 columns), the panel width (64, 32) and the update's tile width (256, 128 real
+// columns) at the chosen batch.  Results are cached per N bucket (N rounded up to a multiple of
+// 64) in a small JSON file:
 //   {"bie_autotune": 1, "entries": {"2944": {"batch": 128, "tcgen05": 3, "lu_block": 256,
-//                                            "us_per_k": ..., "lu_panel": 64}}}
-// (entries written without "lu_panel" read as 64).
+//                                            "us_per_k": ..., "lu_panel": 64, "lu_tile": 256}}}
+// (entries written without "lu_panel" / "lu_tile" read as 64 / 256).
 #include <algorithm>
 #include <cstdio>
 #include <fstream>
@@ -28,7 +29,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
 struct TuneEntry {
   int batch = 0, tc = 0, block = 256;
   double us_per_k = 0.0;
-  int panel = 64;
+  int panel = 64, tile = 256;
 };
 
 static std::map<int, TuneEntry> load_cache(const char* path) {
@@ -41,14 +42,17 @@ static std::map<int, TuneEntry> load_cache(const char* path) {
   const std::string s = ss.str();
   for (size_t i = 0; i + 1 < s.size(); ++i) {
     if (s[i] != '"' || !(s[i + 1] >= '0' && s[i + 1] <= '9')) continue;
-    int key = 0, b = 0, t = 0, blk = 0, pan = 64;
+    int key = 0, b = 0, t = 0, blk = 0, pan = 64, til = 256;
     double us = 0.0;
-    const int got = std::sscanf(s.c_str() + i,
-                                "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %lf, \"lu_panel\": %d}",
-                                &key, &b, &t, &blk, &us, &pan);
-    if ((got == 5 || got == 6) && b >= 1 && t >= 0 && t <= 3 && (blk == 128 || blk == 256 || blk == 512) &&
-        (pan == 32 || pan == 64))
-      m[key] = TuneEntry{b, t, blk, us, got == 6 ? pan : 64};
+    const int got = std::sscanf(
+        s.c_str() + i,
+        "\"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %lf, \"lu_panel\": %d, \"lu_tile\": %d}",
+        &key, &b, &t, &blk, &us, &pan, &til);
+    if (got < 6) pan = 64;
+    if (got < 7) til = 256;
+    if (got >= 5 && b >= 1 && t >= 0 && t <= 3 && (blk == 128 || blk == 256 || blk == 512) &&
+        (pan == 32 || pan == 64) && (til == 128 || til == 256))
+      m[key] = TuneEntry{b, t, blk, us, pan, til};
   }
   return m;
 }
@@ -65,11 +69,12 @@ static bool save_cache(const char* path, const std::map<int, TuneEntry>& m) {
   f << "{\"bie_autotune\": 1, \"entries\": {\n";
   size_t i = 0;
   for (const auto& kv : m) {
-    char line[224];
+    char line[256];
     std::snprintf(line, sizeof(line),
-                  "  \"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %.3f, \"lu_panel\": %d}%s\n",
+                  "  \"%d\": {\"batch\": %d, \"tcgen05\": %d, \"lu_block\": %d, \"us_per_k\": %.3f, \"lu_panel\": %d, "
+                  "\"lu_tile\": %d}%s\n",
                   kv.first, kv.second.batch, kv.second.tc, kv.second.block, kv.second.us_per_k, kv.second.panel,
-                  (++i < m.size()) ? "," : "");
+                  kv.second.tile, (++i < m.size()) ? "," : "");
     f << line;
   }
   f << "}}\n";
@@ -87,9 +92,10 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
     c->tc_version = it->second.tc;
     c->lu_block = it->second.block;
     c->lu_panel = it->second.panel;
+    c->lu_tile = it->second.tile;
     if (out)
       *out = bie_tune_result{key, it->second.batch, it->second.tc, 1, it->second.us_per_k, it->second.block,
-                             it->second.panel};
+                             it->second.panel, it->second.tile};
     return BIE_OK;
   }
   if (nk < 1) return fail(BIE_ERR_INVALID_ARG, "autotune needs at least one sample wavenumber");
@@ -98,7 +104,7 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
   size_t free_b = 0;
   BIE_TRY(device_free(c, &free_b));
   const int saved_batch = c->mixed_batch, saved_tc = c->tc_version, saved_graph = c->mixed_graph,
-            saved_block = c->lu_block, saved_panel = c->lu_panel;
+            saved_block = c->lu_block, saved_panel = c->lu_panel, saved_tile = c->lu_tile;
   TuneEntry best;
   best.us_per_k = 1e300;
   std::vector<double> kk;
@@ -112,13 +118,14 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
       cudaEventCreate(&e1) != cudaSuccess)
     rc = fail(BIE_ERR_OOM, "autotune scratch");
   // one timed batch (after an untimed one that sizes the workspace and builds the tables)
-  auto measure = [&](int b, int tc, int block, double* us, int panel = 64) -> int {
+  auto measure = [&](int b, int tc, int block, double* us, int panel = 64, int tile = 256) -> int {
     kk.resize((size_t)b);
     for (int i = 0; i < b; ++i) kk[i] = k[i % nk];
     c->mixed_batch = b;
     c->tc_version = tc;
     c->lu_block = block;
     c->lu_panel = panel;
+    c->lu_tile = tile;
     c->mixed_graph = 0;
     BIE_TRY(solve_mixed(c, kk.data(), b, surf, nullptr, nullptr, nullptr, nullptr, nullptr, 1));
     cudaEventRecord(e0, c->stream);
@@ -136,7 +143,7 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
       if ((size_t)b * perk > free_b / 3) continue;
       double us = 0.0;
       rc = measure(b, tc, 256, &us);
-      if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{b, tc, 256, us, 64};
+      if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{b, tc, 256, us, 64, 256};
     }
   }
   if (rc == BIE_OK && best.tc == 3)  // then the block of the deferred update at the chosen batch
@@ -144,12 +151,17 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
       double us = 0.0;
       rc = measure(best.batch, 3, block, &us);
       if (rc != BIE_OK) break;
-      if (us < best.us_per_k) best = TuneEntry{best.batch, 3, block, us, 64};
+      if (us < best.us_per_k) best = TuneEntry{best.batch, 3, block, us, 64, 256};
     }
   if (rc == BIE_OK && best.tc == 3) {  // then the panel width at the chosen batch and block
     double us = 0.0;
     rc = measure(best.batch, 3, best.block, &us, 32);
-    if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{best.batch, 3, best.block, us, 32};
+    if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{best.batch, 3, best.block, us, 32, 256};
+  }
+  if (rc == BIE_OK && best.tc >= 2) {  // then the update's tile width
+    double us = 0.0;
+    rc = measure(best.batch, best.tc, best.block, &us, best.panel, 128);
+    if (rc == BIE_OK && us < best.us_per_k) best = TuneEntry{best.batch, best.tc, best.block, us, best.panel, 128};
   }
   dev_free(c, surf);
   if (e0) cudaEventDestroy(e0);
@@ -160,19 +172,21 @@ int autotune(bie_ctx* c, const double* k, int64_t nk, const char* cache_path, bi
     c->tc_version = saved_tc;
     c->lu_block = saved_block;
     c->lu_panel = saved_panel;
+    c->lu_tile = saved_tile;
     return rc != BIE_OK ? rc : fail(BIE_ERR_OOM, "autotune: no candidate fits in device memory");
   }
   c->mixed_batch = best.batch;
   c->tc_version = best.tc;
   c->lu_block = best.block;
   c->lu_panel = best.panel;
+  c->lu_tile = best.tile;
   if (cache_path) {
     std::lock_guard<std::mutex> g(g_cache_mu);
     cache = load_cache(cache_path);  // another thread or process may have added entries meanwhile
     cache[key] = best;
     if (!save_cache(cache_path, cache)) return fail(BIE_ERR_INVALID_ARG, std::string("cannot write ") + cache_path);
   }
-  if (out) *out = bie_tune_result{key, best.batch, best.tc, 0, best.us_per_k, best.block, best.panel};
+  if (out) *out = bie_tune_result{key, best.batch, best.tc, 0, best.us_per_k, best.block, best.panel, best.tile};
   return BIE_OK;
 }
 

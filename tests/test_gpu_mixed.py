@@ -228,6 +228,23 @@ def test_mixed_lu_block_variants(Solver, B, two_spheres, block):
         s.set_option("mixed.lu_block", 192)
 
 
+@pytest.mark.parametrize("tc", [3, 2])
+def test_mixed_lu_tile128(Solver, B, two_spheres, tc):
+    """Update tiles of 128 x 128 real columns (MMA N = 128) in the deferred (3) and per-panel (2)
+    tensor-core updates give the oracle's solutions with few refinement corrections."""
+    ks = np.array([1.5, 8.0])
+    s = _solver(Solver, two_spheres, tc=tc)
+    s.set_option("mixed.lu_tile", 128)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    surf = surf.cpu().numpy()
+    for i, k in enumerate(ks):
+        P, Pn = oracle.solve_frequency(two_spheres, k, D)
+        assert rel(surf[i, 0], P) <= TOL, (k, rel(surf[i, 0], P))
+        assert rep[i].iters <= 8 and not (rep[i].flags & B.BIE_FLAG_NOT_CONVERGED), (k, rep[i].iters)
+    with pytest.raises(B.BieError):
+        s.set_option("mixed.lu_tile", 64)
+
+
 @pytest.mark.parametrize("block", [128, 256])
 def test_mixed_lu_panel32(Solver, B, two_spheres, block):
     """32-column panels in the deferred update (N = 1284: a ragged last panel and block) give the

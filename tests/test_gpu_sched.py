@@ -51,14 +51,14 @@ def test_autotune_cache(tmp_path):
     r1 = B.bie_autotune(s.ctx, [1.0, 2.5, 4.0], cache)
     assert r1["from_cache"] == 0 and r1["n_bucket"] == 320
     assert r1["batch"] in (8, 16, 32, 64, 128, 256) and r1["tcgen05"] in (2, 3) and r1["us_per_k"] > 0
-    assert r1["lu_block"] in (128, 256, 512) and r1["lu_panel"] in (32, 64)
+    assert r1["lu_block"] in (128, 256, 512) and r1["lu_panel"] in (32, 64) and r1["lu_tile"] in (128, 256)
     data = json.load(open(cache))
     assert data["entries"]["320"]["batch"] == r1["batch"]
     s.close()
     s = _solver(mesh)
     r2 = B.bie_autotune(s.ctx, [1.0], cache)
     assert r2["from_cache"] == 1 and r2["batch"] == r1["batch"] and r2["tcgen05"] == r1["tcgen05"]
-    assert r2["lu_block"] == r1["lu_block"] and r2["lu_panel"] == r1["lu_panel"]
+    assert r2["lu_block"] == r1["lu_block"] and r2["lu_panel"] == r1["lu_panel"] and r2["lu_tile"] == r1["lu_tile"]
     surf, rep = s.solve_frequencies([2.25], B.BIE_MODE_MIXED)
     P, _ = oracle.solve_frequency(mesh, 2.25, [0.0, 0.0, 1.0])
     assert _rel(surf.cpu().numpy()[0, 0], P) <= 1e-6
