@@ -79,7 +79,11 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   // FP64 re-assembly group: A64, b64, known/rowsum scratch, xg, r, rowabs, state, k, sel.  One
   // group refines its systems in the same launches (one CTA per system in the triangular
   // solves), so a larger group fills more of the GPU; it is capped at an eighth of free memory.
-  const size_t fb1 = align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024;
+  // With one direction the flagged systems of all batches are pooled (their factor, permutation,
+  // diagonal-block inverses, solution and known values copied aside) and re-assembled and refined
+  // together when the pool is full and after the last batch, instead of batch by batch.
+  const size_t pool1 = multi ? 0 : mat + align256((size_t)N * 4) + dsz + 2 * vec;
+  const size_t fb1 = align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024 + pool1;
   size_t free_b = 0;
   BIE_TRY(device_free(c, &free_b));
   const int G = (int)std::max<size_t>(1, std::min<size_t>(kFallbackGroupMax, (free_b / 8) / fb1));
@@ -125,6 +129,13 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   void* state_g = take(refine_state_bytes(G));
   double* kg = (double*)take(G * sizeof(double));
   int32_t* sel_g = (int32_t*)take(G * sizeof(int32_t));
+  cf* pLU = multi ? nullptr : (cf*)take((size_t)G * mat);  // the pool (one direction)
+  int32_t* pperm = multi ? nullptr : (int32_t*)take((size_t)G * N * 4);
+  cf* pD = multi ? nullptr : (cf*)take((size_t)G * dsz);
+  cd* px = multi ? nullptr : (cd*)take((size_t)G * vec);
+  cd* pknown = multi ? nullptr : (cd*)take((size_t)G * vec);
+  std::vector<double> pool_k;
+  std::vector<int64_t> pool_idx;
   const int64_t bstride = (int64_t)(mat / sizeof(cf));
   std::vector<int32_t> done(kb), iters(kb), hinfo(kb);
   std::vector<double> berr(kb), est(kb);
@@ -186,6 +197,49 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     cudaGraphExec_t* e;
     ~ExecGuard() { if (*e) cudaGraphExecDestroy(*e); }
   } guard{&gexec};
+  // Re-assembles the pooled systems in FP64 (float-float bulk), refines them with their TF32
+  // factors and writes their surface values and reports.
+  auto flush_pool = [&]() -> int {
+    const int ng = (int)pool_k.size();
+    if (ng == 0) return BIE_OK;
+    std::vector<int32_t> ident(ng);
+    for (int g = 0; g < ng; ++g) ident[g] = g;
+    BIE_CUDA_TRY(cudaMemcpyAsync(kg, pool_k.data(), ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, ident.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    BIE_TRY(mark(4));
+    BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
+    BIE_TRY(refine_fp64_system(c, A64, b64, pLU, ld, bstride, pperm, sel_g, ng, (int)N, px, xg, rg, rowabs_g, state_g,
+                               c->refine64_it_max, c->refine64_tol, pD));
+    BIE_TRY(mark(5));
+    for (int g = 0; g < ng; ++g) {
+      dim3 gs((unsigned)((N + 255) / 256), 1);
+      BIE_LAUNCH(k_surface_fields<<<gs, 256, 0, c->stream>>>(c->bc, N, px + (int64_t)g * N, pknown + (int64_t)g * N,
+                                                            surf_out + pool_idx[g] * 2 * N, 2 * N));
+    }
+    BIE_CUDA_TRY(cudaGetLastError());
+    BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
+    if (timing) {
+      c->phase.reassembly_ms += elapsed(4, 5);
+      c->phase.reassembled += ng;
+    }
+    for (int g = 0; g < ng; ++g) {
+      const int64_t idx = pool_idx[g];
+      if (rep) {
+        rep[idx].flags |= BIE_FLAG_FP64_ASSEMBLY;
+        rep[idx].iters += gi[g];
+        rep[idx].backward_err = gb[g];
+        if (gd[g]) rep[idx].flags &= ~BIE_FLAG_NOT_CONVERGED;
+      }
+      if (!gd[g] || !std::isfinite(gb[g])) {
+        full64.push_back(pool_k[g]);
+        full64_idx.push_back(idx);
+        full64_dir.push_back(0);
+      }
+    }
+    pool_k.clear();
+    pool_idx.clear();
+    return BIE_OK;
+  };
   for (int64_t k0 = 0; k0 < Nk; k0 += kb) {
     const int nk = (int)std::min<int64_t>(kb, Nk - k0);
     if (use_graph && k0 > 0 && nk == kb) {
@@ -276,8 +330,9 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
           flagged.push_back(i);
         }
       }
-      // FP64 re-assembly (for this direction) and refinement with the existing factor, in groups
-      for (size_t f0 = 0; f0 < flagged.size(); f0 += G) {
+      // several directions: FP64 re-assembly (for this direction) and refinement with the existing
+      // factor, in groups, batch by batch
+      for (size_t f0 = 0; multi && f0 < flagged.size(); f0 += G) {
         const int ng = (int)std::min<size_t>(G, flagged.size() - f0);
         std::vector<double> kv(ng);
         for (int g = 0; g < ng; ++g) kv[g] = k[k0 + flagged[f0 + g]];
@@ -311,9 +366,29 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       dim3 g((unsigned)((N + 255) / 256), nk);
       BIE_LAUNCH(k_surface_fields<<<g, 256, 0, c->stream>>>(c->bc, N, x, known, surf_out + r0 * 2 * N, kstride));
       BIE_CUDA_TRY(cudaGetLastError());
+      // (after the batch's surface values, which a flush of the pool overwrites for its systems)
+      if (!multi) {  // into the pool (flushed when full and after the last batch)
+        for (const int i : flagged) {
+          if ((int)pool_k.size() == G) BIE_TRY(flush_pool());
+          const int64_t slot = (int64_t)pool_k.size();
+          BIE_CUDA_TRY(cudaMemcpyAsync(pLU + slot * bstride, LU + (int64_t)i * bstride, mat, cudaMemcpyDeviceToDevice,
+                                       c->stream));
+          BIE_CUDA_TRY(cudaMemcpyAsync(pperm + slot * N, perm + (int64_t)i * N, (size_t)N * 4, cudaMemcpyDeviceToDevice,
+                                       c->stream));
+          BIE_CUDA_TRY(cudaMemcpyAsync(pD + slot * dstride, Dinv + (int64_t)i * dstride, (size_t)dstride * sizeof(cf),
+                                       cudaMemcpyDeviceToDevice, c->stream));
+          BIE_CUDA_TRY(cudaMemcpyAsync(px + slot * N, x + (int64_t)i * N, (size_t)N * sizeof(cd),
+                                       cudaMemcpyDeviceToDevice, c->stream));
+          BIE_CUDA_TRY(cudaMemcpyAsync(pknown + slot * N, known + (int64_t)i * N, (size_t)N * sizeof(cd),
+                                       cudaMemcpyDeviceToDevice, c->stream));
+          pool_k.push_back(k[k0 + i]);
+          pool_idx.push_back(r0 + (int64_t)i * ndir);
+        }
+      }
     }
     set_dir(0);
   }
+  BIE_TRY(flush_pool());
   // last resort: the full FP64 path
   for (size_t f = 0; f < full64.size(); ++f) {
     bie_report r64;

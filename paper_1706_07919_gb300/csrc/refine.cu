@@ -335,25 +335,34 @@ __global__ void k_refine_check(int n, const cd* __restrict__ b, const cd* __rest
 // perturbation of the size of the assembly's rounding.  z = (LU)^{-1} v then estimates the
 // solution's error against the FP64-assembled system; near an interior resonance (Sec. 4's remark
 // on w = 20.1a) ||z|| / ||x|| grows with the condition number and the system is re-solved in FP64.
+// stage: x rounded to FP32 once per CTA into shared memory (n * 8 bytes); otherwise every lane
+// rounds the FP64 entries it reads.  The magnitude |A_ij| comes from the FP32 reciprocal square
+// root (a relative error of a few 1e-8 in a random perturbation's size).
 __global__ void __launch_bounds__(512) k_perturb(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
-                                                 const cd* __restrict__ x, cd* __restrict__ v, float eps) {
+                                                 const cd* __restrict__ x, cd* __restrict__ v, float eps, int stage) {
+  extern __shared__ float2 xs32[];  // [n]
   const int kk = blockIdx.y;
+  const cd* xk = x + (int64_t)kk * n;
+  if (stage) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) xs32[j] = make_float2((float)xk[j].re, (float)xk[j].im);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * 16 + warp;
   if (i >= n) return;
   const cf* row = A + (int64_t)kk * bstride + (int64_t)i * ld;
-  const cd* xk = x + (int64_t)kk * n;
   float sr = 0.f, si = 0.f;
   for (int j = lane; j < n; j += 32) {
     const cf a = row[j];
-    const float m = eps * sqrtf(a.re * a.re + a.im * a.im);
+    const float a2 = a.re * a.re + a.im * a.im;
+    const float m = a2 > 0.f ? eps * (a2 * rsqrtf(a2)) : 0.f;
     uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)j * 0x85EBCA77u + 0x27D4EB2Fu);
     h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12;
     const uint32_t q = (h >> 30) & 3u;
     const float er = (q == 0) ? m : (q == 2 ? -m : 0.f), ei = (q == 1) ? m : (q == 3 ? -m : 0.f);
-    const float xr = (float)xk[j].re, xi = (float)xk[j].im;
-    sr += er * xr - ei * xi;
-    si += er * xi + ei * xr;
+    const float2 xv = stage ? xs32[j] : make_float2((float)xk[j].re, (float)xk[j].im);
+    sr += er * xv.x - ei * xv.y;
+    si += er * xv.y + ei * xv.x;
   }
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -422,7 +431,10 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
     BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0, D, dstride));
   }
   // assembly-sensitivity estimate (r is free now)
-  BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f));
+  const int pstage = (size_t)n * sizeof(float2) <= 200 * 1024 ? 1 : 0;
+  BIE_TRY((set_smem_max(k_perturb)));
+  BIE_LAUNCH(k_perturb<<<gr, 512, pstage ? (size_t)n * sizeof(float2) : 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f,
+                                                                                      pstage));
   BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
   BIE_LAUNCH(k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st));
   BIE_CUDA_TRY(cudaGetLastError());
