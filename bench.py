@@ -102,7 +102,7 @@ def bench_config(w, args, world: int) -> dict:
     return {"workload": "two_spheres_N2884_Nk512_M16384_Nt1024", "N": int(w.mesh.N), "E": int(w.mesh.E),
             "Nk": len(w.k), "ka_max": float(w.k[-1]), "M": int(w.xobs.shape[0]), "Nt": w.Nt,
             "pulses": int(w.pulses.shape[0]), "parallelism": f"{world} independent replica(s), one per GPU",
-            "l2": "working set (128 x 133 MB systems per batch) larger than L2; no flush needed",
+            "l2": f"working set ({args.batch} x 133 MB systems per batch) larger than L2; no flush needed",
             "mixed_batch": args.batch}
 
 
@@ -841,7 +841,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lu-block", type=int, default=256, help="columns of the deferred LU update (128, 256, 512)")
     ap.add_argument("--lu-panel", type=int, default=64, help="panel width of the deferred LU update (64, 32)")
     ap.add_argument("--lu-tile", type=int, default=256, help="real columns of the LU update tile (256, 128)")
