@@ -161,6 +161,24 @@ def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B, ff):
         assert rel(surf[i, 0], P) <= 1e-8, (k, rel(surf[i, 0], P))
 
 
+def test_pooled_reassembly_across_batches(Solver, B):
+    """Every wavenumber flagged, 70 wavenumbers in batches of 8: the flagged systems of all batches
+    are pooled (factors, permutations, solutions copied aside) and re-assembled and refined in
+    groups when the pool fills and after the last batch; each surface solution must match the FP64
+    path's to the FP64 refinement's accuracy and carry the re-assembly flag."""
+    w = config_sphere_fp64()
+    ks = np.linspace(0.5, 9.5, 70)
+    s = _solver(Solver, w.mesh)
+    s.set_option("mixed.fallback_err_est", 1e-30)
+    s.set_option("mixed.batch", 8)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    ref, _ = s.solve_frequencies(ks, B.BIE_MODE_FP64)
+    surf, ref = surf.cpu().numpy(), ref.cpu().numpy()
+    for i in range(len(ks)):
+        assert rep[i].flags & B.BIE_FLAG_FP64_ASSEMBLY and not rep[i].flags & B.BIE_FLAG_NOT_CONVERGED, i
+        assert rel(surf[i, 0], ref[i, 0]) <= 1e-8 and rel(surf[i, 1], ref[i, 1]) <= 1e-8, (ks[i], rel(surf[i, 0], ref[i, 0]))
+
+
 @pytest.mark.parametrize("kb", [0, 1, 2])
 def test_bulk_assembly_variants_match_oracle(Solver, B, two_spheres, kb):
     """The FP32 bulk assembly with one (general kernel, kb 0) or several wavenumbers per thread
