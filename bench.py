@@ -666,10 +666,10 @@ FIELD_BATCH = 512
 
 # DRAM bytes (read + write) of one launch of the field kernel in this configuration (512
 # wavenumbers x 16 384 points) per kernel variant, from an ncu capture of a launch of exactly
-# that shape (`bench.py --case field512`): 222.7 MB read (tables and surface values) and 106.3 MB
+# that shape (`bench.py --case field512`): 221.8 MB read (tables and surface values) and 105.9 MB
 # written (the 134 MB field, part of it still in L2 when the launch ends).  Variants without an
 # entry have no capture of the current kernel.
-FIELD_LAUNCH_DRAM_BYTES = {2: 222_739_456 + 106_288_640}
+FIELD_LAUNCH_DRAM_BYTES = {2: 221_766_912 + 105_931_520}
 
 # algorithmic flops of one field evaluation (one observation point, one quadrature point, one k),
 # counted on the FP64 formula: 2 distances (3 sub, 3 mul, 2 add, sqrt, div = 10 each), the
