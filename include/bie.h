@@ -213,7 +213,11 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          trailing matrix deferred over blocks of "mixed.lu_block" columns,
  *                          2 the same kernel after every 64-column panel, 1 the
  *                          register-staged tcgen05 kernel, 0 FP32 on the CUDA cores.
- *   "mixed.lu_block"       columns of the deferred update of version 3: 128, 256 (default), 512
+ *   "mixed.lu_block"       columns of the deferred update of version 3: 128, 256, 512, or 0
+ *                          (default): 512 from N = 8192 on, else 256
+ *   "mixed.lu_coop"        1 (default): the panels of few tall matrices (at most half as many
+ *                          matrices as SMs, more than 1536 rows) are factored by several CTAs per
+ *                          matrix in one cooperative launch; 0: one CTA per matrix always
  *   "mixed.lu_panel"       panel width of version 3: 64 (default) or 32 (more, narrower panels:
  *                          shorter pivot chains per leaf, narrower K = 32 updates inside a block)
  *   "mixed.lu_tile"        tile of the tensor-core update (versions 2, 3): 128 rows x 256 real

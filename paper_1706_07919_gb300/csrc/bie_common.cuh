@@ -127,8 +127,9 @@ struct bie_ctx {
   int tc_version = 3;                // LU trailing update: 0 SIMT FP32, 1 tcgen05 (register-staged),
                                      // 2 tcgen05 (persistent, TMA-fed, warp-specialised), 3 as 2
                                      // with the update deferred over 256-column blocks
-  int lu_block = 256;                // mixed.tcgen05 3: columns over which the trailing update is
-                                     // deferred (128, 256 or 512)
+  int lu_block = 0;                  // mixed.tcgen05 3: columns over which the trailing update is
+                                     // deferred (128, 256 or 512; 0: 512 from N = 8192 on, else 256)
+  int lu_coop = 1;                   // several CTAs per matrix in the panels of few tall matrices
   int lu_panel = 64;                 // mixed.tcgen05 3: panel width (32 or 64)
   int lu_tile = 256;                 // mixed.tcgen05 2, 3: update tile width in real columns (256 or 128)
   int mixed_batch = 64;              // wavenumbers per batch

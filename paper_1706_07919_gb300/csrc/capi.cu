@@ -386,9 +386,11 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
       return fail(BIE_ERR_INVALID_ARG, "mixed.tcgen05 must be 0 (SIMT), 1, 2 or 3 (tensor-core kernels)");
     c->tc_version = (int)value;
   } else if (n == "mixed.lu_block") {
-    if (value != 128.0 && value != 256.0 && value != 512.0)
-      return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 128, 256 or 512");
+    if (value != 0.0 && value != 128.0 && value != 256.0 && value != 512.0)
+      return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 0 (by N), 128, 256 or 512");
     c->lu_block = (int)value;
+  } else if (n == "mixed.lu_coop") {
+    c->lu_coop = value != 0.0 ? 1 : 0;
   } else if (n == "mixed.lu_tile") {
     if (value != 128.0 && value != 256.0) return fail(BIE_ERR_INVALID_ARG, "mixed.lu_tile must be 128 or 256");
     c->lu_tile = (int)value;

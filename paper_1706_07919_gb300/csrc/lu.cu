@@ -315,6 +315,291 @@ __global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int6
   }
 }
 
+// ---- cooperative panel: several CTAs per matrix for a few tall matrices ----------------------
+// With few matrices in a batch (at most half as many as co-resident CTAs) and panels taller than
+// a 16-column leaf that fits one CTA's shared memory, one CTA per matrix leaves most SMs idle and
+// has to narrow its leaves to a column or two.  Here `cpm` CTAs share each matrix: CTA j of
+// matrix z holds rows [p0 + j ch, p0 + (j + 1) ch) of a leaf of up to 16 columns in shared memory
+// (column by column), and the CTAs of one matrix agree on every pivot through a per-matrix
+// barrier in global memory, one per column:
+//   each CTA posts its best candidate row (largest modulus, lowest row on ties) with the
+//   candidate's leaf entries, and the holder of row c posts row c's; after the barrier every CTA
+//   picks the same winner p, the holders of rows c and p exchange them in shared memory, and
+//   every CTA scales column c of its rows and applies the rank-1 update to the rest of its leaf.
+// After a leaf, CTA 0 (its chunk holds the panel's diagonal rows: ch is a multiple of 64) applies
+// the leaf's row interchanges, as one gather of the at most 2 lw rows they touch, to the panel's
+// other columns and solves the leaf's U block L11^{-1} A12 for the panel columns right of the
+// leaf; after a second barrier every CTA updates its rows of those columns, A -= L U (K = lw).
+// Launched cooperatively, so that all CTAs are resident together.  Every wait is bounded: a CTA
+// whose wait gives up raises the error word (bit 8) and an abort flag on which every other wait
+// ends, and all CTAs leave.  Data written by other CTAs is read with L2-coherent loads.
+namespace coop {
+constexpr int NT = 512;
+constexpr int LWMAX = 16;
+constexpr int WMAX = 64;                 // panel width
+constexpr uint32_t SPIN = 1u << 21;      // polls of one barrier (about a second) before giving up
+struct alignas(16) Cand {                // one CTA's pivot candidate for one column
+  float best;                            // |a|^2 (-1: no row)
+  int idx;                               // its row
+  int pad0, pad1;
+  Cx<float> v[LWMAX];                    // its leaf entries
+};
+// scratch: [nmat] barrier counters, abort flag, [2][grid] candidates, [2][nmat][LWMAX] row c
+inline size_t scratch_bytes(int nmat, int grid) {
+  return 256 + (size_t)(nmat + 1) * 4 + 256 + 2 * (size_t)grid * sizeof(Cand) + 2 * (size_t)nmat * LWMAX * 8 + 256;
+}
+}  // namespace coop
+constexpr int kCoopMaxGrid = 4096;  // CTAs of one cooperative panel launch (at most)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ Cx<float> ldcg_cx(const Cx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+__global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
+    Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w, int lw, int cpm, int ch,
+    int32_t* __restrict__ piv, int32_t* __restrict__ info, unsigned* __restrict__ bar, unsigned* abort_flag,
+    coop::Cand* __restrict__ cand, Cx<float>* __restrict__ diag, int32_t* __restrict__ err) {
+  using coop::LWMAX;
+  using coop::NT;
+  extern __shared__ float4 coop_smem[];
+  Cx<float>* S = reinterpret_cast<Cx<float>*>(coop_smem);  // [lw][ch]: leaf entry (r, t) at t * ch + r - r_lo
+  Cx<float>* Ub = S + (size_t)lw * ch;                     // [LWMAX][WMAX]: the leaf's U block
+  coop::Cand* sc = reinterpret_cast<coop::Cand*>(Ub + LWMAX * coop::WMAX);  // [cpm]: the matrix's candidates
+  __shared__ Cx<float> s_u[LWMAX], s_d[LWMAX];             // pivot row, former row c (leaf entries)
+  __shared__ float red_v[NT / 32];
+  __shared__ int red_i[NT / 32];
+  __shared__ int s_p, s_abort, s_m;
+  __shared__ int s_piv[LWMAX], s_rows[2 * LWMAX], s_src[2 * LWMAX];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nmat = gridDim.x / cpm;
+  const int z = blockIdx.x / cpm, j = blockIdx.x - z * cpm;
+  Cx<float>* M = A + (int64_t)z * bstride;
+  const int r_lo = p0 + j * ch, r_hi = min(n, r_lo + ch);  // empty when r_lo >= n
+  const int pend = min(p0 + w, n);
+  unsigned gen = 0;
+  if (tid == 0) s_abort = 0;
+  __syncthreads();
+  // barrier of the cpm CTAs of matrix z; false when a wait gave up here or elsewhere.  The
+  // arrival is a release (it orders the CTA's writes, gathered by bar.sync, before it), the
+  // poll an acquire.
+  auto barrier = [&]() -> bool {
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(bar + z) : "memory");
+      const unsigned target = (gen + 1) * (unsigned)cpm;
+      bool ok = false;
+      for (uint32_t it = 0; it < coop::SPIN; ++it) {
+        if (ld_acquire_gpu(bar + z) >= target) { ok = true; break; }
+        if (ld_acquire_gpu(abort_flag)) break;
+        if (it > 16) __nanosleep(32);
+      }
+      if (!ok) {
+        atomicOr(err, 8);
+        atomicExch(abort_flag, 1u);
+        s_abort = 1;
+      }
+      asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+    }
+    ++gen;
+    __syncthreads();
+    return s_abort == 0;
+  };
+  for (int c0 = p0; c0 < pend; c0 += lw) {
+    const int l = min(lw, pend - c0);
+    const int a = max(r_lo, c0);       // first leaf row held here
+    const int nr = max(0, r_hi - a);
+    for (int e = tid; e < nr * l; e += NT) {
+      const int rr = e / l, t = e - rr * l;
+      S[t * ch + a - r_lo + rr] = ldcg_cx(M + (int64_t)(a + rr) * ld + c0 + t);
+    }
+    __syncthreads();
+    // this thread's candidate for the leaf's first column (later columns: found during the
+    // rank-1 update of the column before)
+    float best = -1.f;
+    int bi = n;
+    for (int r = a + tid; r < r_hi; r += NT) {
+      const Cx<float> v = S[r - r_lo];
+      const float m = v.re * v.re + v.im * v.im;
+      if (m > best) { best = m; bi = r; }
+    }
+    for (int cc = 0; cc < l; ++cc) {
+      const int c = c0 + cc, buf = c & 1;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+      __syncthreads();
+      if (warp == 0) {
+        best = lane < NT / 32 ? red_v[lane] : -1.f;
+        bi = lane < NT / 32 ? red_i[lane] : n;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        coop::Cand* cd = cand + (int64_t)buf * gridDim.x + blockIdx.x;
+        if (lane == 0) { cd->best = best; cd->idx = bi; }
+        if (lane < l) cd->v[lane] = bi < r_hi ? S[lane * ch + bi - r_lo] : Cx<float>{0.f, 0.f};
+        if (c >= r_lo && c < r_hi && lane < l)
+          diag[((int64_t)buf * nmat + z) * LWMAX + lane] = S[lane * ch + c - r_lo];
+      }
+      if (!barrier()) return;
+      {  // the matrix's candidates and row c, in one round trip
+        const float4* src = reinterpret_cast<const float4*>(cand + (int64_t)buf * gridDim.x + (int64_t)z * cpm);
+        float4* dst = reinterpret_cast<float4*>(sc);
+        constexpr int W4 = (int)(sizeof(coop::Cand) / 16);
+        for (int e = tid; e < cpm * W4; e += NT) dst[e] = __ldcg(src + e);
+        if (tid >= NT - LWMAX && tid - (NT - LWMAX) < l)
+          s_d[tid - (NT - LWMAX)] = ldcg_cx(diag + ((int64_t)buf * nmat + z) * LWMAX + tid - (NT - LWMAX));
+      }
+      __syncthreads();
+      if (warp == 0) {  // the winner among the matrix's CTAs (the same in all of them)
+        float b2 = -1.f;
+        int i2 = n, w2 = 0;
+        for (int q = lane; q < cpm; q += 32) {
+          const float bq = sc[q].best;
+          const int iq = sc[q].idx;
+          if (bq > b2 || (bq == b2 && iq < i2)) { b2 = bq; i2 = iq; w2 = q; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, b2, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
+          const int ow = __shfl_xor_sync(0xffffffffu, w2, o);
+          if (ob > b2 || (ob == b2 && oi < i2)) { b2 = ob; i2 = oi; w2 = ow; }
+        }
+        if (i2 >= n) i2 = c;
+        if (lane == 0) {
+          s_p = i2;
+          s_piv[cc] = i2;
+          if (j == 0) {
+            piv[(int64_t)z * n + c] = i2;
+            if (!(b2 > 0) && info) atomicOr(info + z, 1);
+          }
+        }
+        if (lane < l) s_u[lane] = sc[w2].v[lane];
+      }
+      __syncthreads();
+      const int p = s_p;
+      // rows c and p exchange (row c takes the pivot row; the thread of row p, below, restores
+      // the former row c into it); rows below c are scaled and updated, and each thread keeps its
+      // best candidate for the next column
+      if (p != c && tid < l && c >= r_lo && c < r_hi) S[tid * ch + c - r_lo] = s_u[tid];
+      const Cx<float> d = s_u[cc];
+      const float dd = d.re * d.re + d.im * d.im;
+      const bool ok = dd > 0.f;
+      best = -1.f;
+      bi = n;
+      for (int r = max(a, c + 1) + tid; r < r_hi; r += NT) {
+        if (r == p)
+          for (int t = 0; t < l; ++t) S[t * ch + r - r_lo] = s_d[t];
+        Cx<float> lv = S[cc * ch + r - r_lo];
+        if (ok) lv = cx_div(lv, d);
+        S[cc * ch + r - r_lo] = lv;
+        for (int t = cc + 1; t < l; ++t) {
+          const Cx<float> u = s_u[t];
+          Cx<float>& x = S[t * ch + r - r_lo];
+          x.re -= lv.re * u.re - lv.im * u.im;
+          x.im -= lv.re * u.im + lv.im * u.re;
+          if (t == cc + 1) {
+            const float m = x.re * x.re + x.im * x.im;
+            if (m > best) { best = m; bi = r; }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < nr * l; e += NT) {
+      const int rr = e / l, t = e - rr * l;
+      M[(int64_t)(a + rr) * ld + c0 + t] = S[t * ch + a - r_lo + rr];
+    }
+    if (j == 0) {
+      // net effect of the leaf's interchanges on the rows they touch: row s_rows[i] receives the
+      // former row s_src[i]; the leaf's own rows c0 .. c0+l-1 come first
+      if (tid == 0) {
+        int m = 0;
+        for (int t = 0; t < l; ++t) { s_rows[m] = c0 + t; s_src[m] = c0 + t; ++m; }
+        for (int t = 0; t < l; ++t) {
+          const int pr = s_piv[t];
+          if (pr == c0 + t) continue;
+          int ip = -1;
+          for (int i = 0; i < m; ++i)
+            if (s_rows[i] == pr) { ip = i; break; }
+          if (ip < 0) { s_rows[m] = pr; s_src[m] = pr; ip = m++; }
+          const int tmp = s_src[t];
+          s_src[t] = s_src[ip];
+          s_src[ip] = tmp;
+        }
+        s_m = m;
+      }
+      __syncthreads();
+      const int m = s_m;
+      for (int jj = p0 + tid; jj < pend; jj += NT) {  // the panel's columns outside the leaf
+        if (jj >= c0 && jj < c0 + l) continue;
+        Cx<float> v[2 * LWMAX];
+        for (int i = 0; i < m; ++i) v[i] = ldcg_cx(M + (int64_t)s_src[i] * ld + jj);
+        if (jj >= c0 + l)  // U block: forward substitution with the leaf's unit lower L11
+          for (int s = 1; s < l; ++s)
+            for (int t = 0; t < s; ++t) {
+              const Cx<float> lv = S[t * ch + c0 + s - r_lo];
+              v[s].re -= lv.re * v[t].re - lv.im * v[t].im;
+              v[s].im -= lv.re * v[t].im + lv.im * v[t].re;
+            }
+        for (int i = 0; i < m; ++i) M[(int64_t)s_rows[i] * ld + jj] = v[i];
+      }
+    }
+    if (!barrier()) return;
+    const int cs = c0 + l, wr = pend - cs;
+    if (wr > 0) {  // rows below the leaf, panel columns right of it: A -= L_leaf U_leaf
+      for (int e = tid; e < l * wr; e += NT) {
+        const int t = e / wr, jj = e - t * wr;
+        Ub[t * coop::WMAX + jj] = ldcg_cx(M + (int64_t)(c0 + t) * ld + cs + jj);
+      }
+      __syncthreads();
+      const int rb = max(r_lo, cs);
+      const int nrow = max(0, r_hi - rb);
+      if ((wr & 1) == 0 && ((ld | cs) & 1) == 0 && (bstride & 1) == 0) {  // two columns per thread, 16-byte accesses
+        const int hw = wr >> 1;
+#pragma unroll 2
+        for (int e = tid; e < nrow * hw; e += NT) {
+          const int rr = e / hw, jj = 2 * (e - rr * hw), r = rb + rr;
+          float4* mp = reinterpret_cast<float4*>(M + (int64_t)r * ld + cs + jj);
+          float4 acc = __ldcg(mp);
+          for (int t = 0; t < l; ++t) {
+            const Cx<float> lv = S[t * ch + r - r_lo];
+            const float4 u = *reinterpret_cast<const float4*>(Ub + t * coop::WMAX + jj);
+            acc.x -= lv.re * u.x - lv.im * u.y;
+            acc.y -= lv.re * u.y + lv.im * u.x;
+            acc.z -= lv.re * u.z - lv.im * u.w;
+            acc.w -= lv.re * u.w + lv.im * u.z;
+          }
+          *mp = acc;
+        }
+      } else {
+        for (int e = tid; e < nrow * wr; e += NT) {
+          const int rr = e / wr, jj = e - rr * wr, r = rb + rr;
+          Cx<float>* mp = M + (int64_t)r * ld + cs + jj;
+          Cx<float> acc = ldcg_cx(mp);
+          for (int t = 0; t < l; ++t) {
+            const Cx<float> lv = S[t * ch + r - r_lo], u = Ub[t * coop::WMAX + jj];
+            acc.re -= lv.re * u.re - lv.im * u.im;
+            acc.im -= lv.re * u.im + lv.im * u.re;
+          }
+          *mp = acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Leaf width for a panel whose rows start at p0: the widest power of two <= 16 whose leaf and U
 // block (lw x 64) fit in 200 KB of shared memory (fewer, wider leaves re-read the panel fewer
 // times); 0 if even one column does not fit (then the global-memory panel runs).
@@ -577,13 +862,72 @@ int lu_factor_simt(bie_ctx* c, Cx<S>* A, int batch, int n, int ld, int64_t bstri
   return BIE_OK;
 }
 
+size_t lu_coop_scratch_bytes(int batch) { return coop::scratch_bytes(batch, kCoopMaxGrid); }
+
+// The cooperative panel (k_panel_coop) for the panel at p0 when it applies: a panel taller than
+// the 16-column one-CTA leaf holds (1536 rows), at most half as many matrices as SMs, and a
+// chunk of rows per CTA whose leaf of at least 4 columns fits shared memory.  *used tells whether
+// it ran.  `coop` is the scratch of lu_coop_scratch_bytes(batch), err the LU's error word.
+static int panel_coop32(bie_ctx* c, Cx<float>* A, int batch, int n, int ld, int64_t bstride, int p0, int w,
+                        int32_t* piv, int32_t* info, void* coop, int32_t* err, bool* used) {
+  *used = false;
+  const int rows = n - p0;
+  if (!coop || !c->lu_coop || w > coop::WMAX || rows <= 1536) return BIE_OK;
+  int nsm = 0;
+  BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  int cpm = std::min(nsm / batch, (rows + 255) / 256);  // one CTA per SM (the leaf takes most of its memory)
+  if (cpm < 2) return BIE_OK;
+  const int ch = ((rows + cpm - 1) / cpm + 63) / 64 * 64;
+  cpm = (rows + ch - 1) / ch;
+  if (cpm < 2 || batch * cpm > kCoopMaxGrid) return BIE_OK;
+  BIE_TRY((set_smem_max(k_panel_coop)));
+  cudaFuncAttributes fa;
+  BIE_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)k_panel_coop));
+  const size_t limit = (size_t)smem_optin() - fa.sharedSizeBytes;
+  int lw = coop::LWMAX;
+  auto smem_of = [&](int l) {
+    return ((size_t)l * ch + (size_t)coop::LWMAX * coop::WMAX) * sizeof(Cx<float>) + (size_t)cpm * sizeof(coop::Cand);
+  };
+  while (lw >= 4 && smem_of(lw) > limit) lw >>= 1;
+  if (lw < 4) return BIE_OK;
+  lw = std::min(lw, w);
+  const size_t smem = smem_of(lw);
+  int per_sm = 0;
+  BIE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop, coop::NT, smem));
+  if ((int64_t)per_sm * nsm < (int64_t)batch * cpm) return BIE_OK;
+  char* base = (char*)coop + 256;
+  unsigned* bar = (unsigned*)base;  // [batch] counters, then the abort flag
+  unsigned* abort_flag = bar + batch;
+  coop::Cand* cand = (coop::Cand*)(base + (((size_t)(batch + 1) * 4 + 255) & ~(size_t)255));
+  Cx<float>* diag = (Cx<float>*)(cand + 2 * (size_t)batch * cpm);
+  BIE_CUDA_TRY(cudaMemsetAsync(bar, 0, (size_t)(batch + 1) * 4, c->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(batch * cpm));
+  cfg.blockDim = dim3(coop::NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  BIE_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_coop, A, bstride, n, ld, p0, w, lw, cpm, ch, piv, info, bar,
+                                  abort_flag, cand, diag, err));
+  *used = true;
+  return BIE_OK;
+}
+
 // Panel factorisation plus row swaps (all columns) and the U12 solve of the columns in
 // [p0 + w, tend) for one block column (FP32); the trailing update is left to the caller (the
-// tensor-core kernels of lu_tc.cu).
+// tensor-core kernels of lu_tc.cu).  coop / err: scratch and error word of the cooperative panel
+// (NULL: one CTA per matrix always).
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info, int tend) {
+                     int32_t* info, int tend, void* coop, int32_t* err) {
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
-  BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
+  bool used = false;
+  BIE_TRY(panel_coop32(c, M, batch, n, ld, bstride, p0, w, piv, info, coop, err, &used));
+  if (!used) BIE_TRY(panel_factor<float>(c, M, batch, n, ld, bstride, p0, w, piv, info));
   dim3 gs((unsigned)((n + 127) / 128), batch);
   if (w == 64) {  // swaps here, the solve with the register-resident kernel
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, 0, c->stream>>>(M, bstride, n, ld, p0, w, piv, 0, p0 + w, 1));

@@ -22,7 +22,8 @@
 namespace bie {
 
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info, int tend);
+                     int32_t* info, int tend, void* coop, int32_t* err);
+size_t lu_coop_scratch_bytes(int batch);
 int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo);
 
 namespace tc {
@@ -544,10 +545,20 @@ static int make_map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d
 //     A22 (rows and columns >= E) -= L21 U12 with K = 256.
 constexpr int kMaxLuBlock = 512;
 
+// Columns of the deferred update: the "mixed.lu_block" option, or (0, the default) 512 from
+// N = 8192 on -- at 256 the A22 traffic (16 B per complex entry per block) would bound the update
+// of such matrices below the TF32 rate (128 flop per byte at 256, 256 at 512) -- and 256 below.
+int lu_block_for(const bie_ctx* c, int n) {
+  if (c->lu_block > 0) return c->lu_block;
+  return n >= 8192 ? 512 : 256;
+}
+
 size_t lu_tc_scratch_bytes(int batch, int n, int block) {
-  // error flag, B^T for one 64-row panel (128 floats per row) and for one outer block (2 NBO)
+  // error flag, the cooperative panel's scratch, B^T for one 64-row panel (128 floats per row)
+  // and for one outer block (2 NBO)
   if (block < tc::NB || block > kMaxLuBlock) block = kMaxLuBlock;
-  return 256 + (size_t)batch * 2 * n * (2 * tc::NB + 2 * block) * sizeof(float);
+  return 256 + ((lu_coop_scratch_bytes(batch) + 255) & ~(size_t)255) +
+         (size_t)batch * 2 * n * (2 * tc::NB + 2 * block) * sizeof(float);
 }
 
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
@@ -556,12 +567,13 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   if (ld % 64 != 0 || bstride % 2 != 0) return fail(BIE_ERR_INVALID_ARG, "tcgen05 LU needs ld % 64 == 0 and even batch stride");
   int32_t* err = (int32_t*)scratch;
   BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
+  void* coop = (char*)scratch + 256;
   const int ver = c->tc_version;
-  const int NBO = c->lu_block;
+  const int NBO = lu_block_for(c, n);
   // panel width of the deferred version (32 or 64; versions 1 and 2 use 64)
   const int nb = (ver >= 3 && c->lu_panel == 32) ? 32 : NB;
   if (NBO % NB != 0 || NBO < NB || NBO > kMaxLuBlock) return fail(BIE_ERR_INVALID_ARG, "LU block must be 128, 256 or 512");
-  float* ub = reinterpret_cast<float*>((char*)scratch + 256);
+  float* ub = reinterpret_cast<float*>((char*)coop + ((lu_coop_scratch_bytes(batch) + 255) & ~(size_t)255));
   const int kr = 2 * nb;                                // reals along K of one panel's B^T
   const int64_t ub_stride = (int64_t)2 * n * kr;        // floats per matrix, one panel
   float* ubo = ub + (int64_t)batch * ub_stride;
@@ -614,7 +626,7 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
       const int E = std::min(n, P0 + NBO);
       for (int p0 = P0; p0 < E; p0 += nb) {
         const int w = std::min(nb, E - p0), q = p0 + w;
-        BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E));
+        BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E, coop, err));
         if (q < E) {  // then w == nb (E - P0 is a multiple of nb unless E == n)
           BIE_TRY(build(p0, q, E, false, 0, w));
           BIE_TRY(update(q, n, q, E, p0, w, false, q));
@@ -634,7 +646,7 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   }
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int w = std::min(NB, n - p0);
-    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n));
+    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n, coop, err));
     const int rem = n - p0 - w;
     if (rem <= 0) continue;
     if (ver == 2) {

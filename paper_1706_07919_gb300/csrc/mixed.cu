@@ -17,6 +17,7 @@ int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, in
 int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
                  void* scratch, size_t scratch_bytes);
 size_t lu_tc_scratch_bytes(int batch, int n, int block);
+int lu_block_for(const bie_ctx* c, int n);
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
                  int it_max, double tol, cf* D);
@@ -90,7 +91,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   const size_t fb = (size_t)G * fb1 + 4096;
   const size_t avail = free_b > fb ? free_b - fb : 0;
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(c->mixed_batch, (int64_t)((avail / 2) / perk))));
-  size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, c->lu_block);
+  size_t tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, lu_block_for(c, (int)N));
   if ((size_t)kb * perk + tc_scratch + fb > free_b)
     return fail(BIE_ERR_OOM, "mixed-precision workspace for N = " + std::to_string(N) + " does not fit");
   // memory shared with other contexts (scheduler workers on other streams) can run short between
@@ -100,7 +101,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     if (rc == BIE_OK) break;
     if (rc != BIE_ERR_OOM || kb == 1) return rc;
     kb = std::max<int64_t>(1, kb / 2);
-    tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, c->lu_block);
+    tc_scratch = lu_tc_scratch_bytes((int)kb, (int)N, lu_block_for(c, (int)N));
   }
   char* p = (char*)c->work.p;
   auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return (void*)q; };

@@ -106,3 +106,40 @@ def test_large_lattice_forward_error_and_field(lattice):
         assert np.allclose(surf[i, 0], -np.exp(1j * k * m.nodes[:, 2]), rtol=0, atol=1e-12)
         Tr = oracle.field(m, k, surf[i, 0], surf[i, 1], pts)
         assert rel(T[i], Tr) <= 1e-6
+
+
+def test_cooperative_panel_matches_one_cta_panel():
+    """Three wavenumbers of the two-sphere benchmark mesh (N = 2884) factor their tall panels with
+    several CTAs per matrix (the default for so few matrices); the same solve with one CTA per
+    matrix (option mixed.lu_coop 0) launches more kernels and gives the same solutions: unrefined
+    (the TF32 factor alone, refine.it_max 0) within the 2e-2 that TF32 rounding times the
+    condition number allows (a broken panel is O(1) off), refined within 1e-9 of each other, and
+    the refined ones within the mixed path's 1e-6 of the oracle."""
+    from paper_1706_07919_gb300 import Solver
+    from paper_1706_07919_gb300 import binding as B
+    w = W.config_two_spheres_mixed()
+    m = w.mesh
+    ks = w.k[[40, 211, 470]]  # ka = 1.28, 6.6, 14.7
+    out = {}
+    for coop in (1, 0):
+        for it in (0, 10):
+            s = Solver(0)
+            s.set_geometry(m.nodes, m.elems, m.normals, m.bc)
+            s.set_incident_plane_wave(w.direction)
+            s.set_option("mixed.lu_coop", coop)
+            s.set_option("refine.it_max", it)
+            if it == 0:
+                s.set_option("refine.tol", 0.5)
+            s.set_option("mixed.fallback_err_est", 1.0)  # no re-assembly: compare the factors' solutions
+            l0 = B.bie_kernel_launches()
+            surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+            out[coop, it] = (surf.cpu().numpy(), B.bie_kernel_launches() - l0, rep)
+            s.close()
+    assert out[1, 10][1] < out[0, 10][1], (out[1, 10][1], out[0, 10][1])
+    for i, k in enumerate(ks):
+        assert rel(out[1, 0][0][i, 0], out[1, 10][0][i, 0]) <= 2e-2, k
+        assert rel(out[0, 0][0][i, 0], out[1, 10][0][i, 0]) <= 2e-2, k
+        assert rel(out[1, 10][0][i, 0], out[0, 10][0][i, 0]) <= 1e-9, k
+        assert out[1, 10][2][i].backward_err <= 1e-10
+    P, _ = oracle.solve_frequency(m, ks[1], w.direction)
+    assert rel(out[1, 10][0][1, 0], P) <= 1e-6
