@@ -15,9 +15,8 @@ __global__ void k_trsv_lu(const cf* __restrict__ LU, int n, int64_t ld, int64_t 
                           const RefineState* __restrict__ st, const int32_t* __restrict__ sel, int64_t rstride,
                           int64_t roff, int64_t ostride, int64_t ooff, const cf* __restrict__ Dinv, int64_t dstride);
 int64_t diag_inv_stride(int n);
-__global__ void k_residual_ff(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride, const cd* __restrict__ b,
-                              const cd* __restrict__ x, cd* __restrict__ r, double* __restrict__ rowabs,
-                              const RefineState* __restrict__ st, int stage);
+int residual_ff(bie_ctx* c, const cf* A, int n, int64_t ld, int64_t bstride, int nk, const cd* b, const cd* x, cd* r,
+                double* rowabs, const RefineState* st);
 __global__ void k_refine_check(int n, const cd* __restrict__ b, const cd* __restrict__ x, const cd* __restrict__ r,
                                const double* __restrict__ rowabs, RefineState* __restrict__ st, double tol,
                                int count_iter);
@@ -267,16 +266,13 @@ int gmres_solve(bie_ctx* c, const cf* A, int nk, int n, int64_t ld, int64_t bstr
   RefineState* rs = (RefineState*)state_dev;
   BIE_CUDA_TRY(cudaMemsetAsync(rs, 0, nk * sizeof(RefineState), c->stream));
   BIE_CUDA_TRY(cudaMemsetAsync(gs, 0, nk * sizeof(GmresState), c->stream));
-  const int stage = (size_t)n * sizeof(float4) <= 200 * 1024 ? 1 : 0;
-  const size_t sm_trsv = (size_t)n * sizeof(cf), sm_res = stage ? (size_t)n * sizeof(float4) : 0,
-               sm_mv = (size_t)n * sizeof(float2);
+  const size_t sm_trsv = (size_t)n * sizeof(cf), sm_mv = (size_t)n * sizeof(float2);
   if (sm_trsv > 200 * 1024) return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory Krylov kernels");
   BIE_TRY((set_smem_max(k_trsv_lu)));
-  BIE_TRY((set_smem_max(k_residual_ff)));
   BIE_TRY((set_smem_max(k_gm_matvec)));
   dim3 gr((unsigned)((n + 15) / 16), nk);
   for (int cy = 0; cy <= cycles; ++cy) {
-    BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, rs, stage));
+    BIE_TRY(residual_ff(c, A, n, ld, bstride, nk, b, x, r, rowabs, rs));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, rs, tol, 0));
     if (cy == cycles) break;
     BIE_LAUNCH(k_gm_start<<<nk, 1024, 0, c->stream>>>(n, m, r, V, g, gs, rs, gate, tol));

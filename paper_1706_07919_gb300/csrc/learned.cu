@@ -32,8 +32,7 @@ int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, 
 int mlp_init_params(bie_ctx* c, uint64_t seed);
 int mlp_train(bie_ctx* c, const double* k, int64_t nk, const cd* surf, int epochs, float* loss_hist);
 int mlp_predict_dev(bie_ctx* c, const double* kdev, int nk, cd* x0);
-__global__ void k_perturb(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride, const cd* __restrict__ x,
-                          cd* __restrict__ v, float eps, int stage);
+int perturb(bie_ctx* c, const cf* A, int n, int64_t ld, int64_t bstride, int nk, const cd* x, cd* v, float eps);
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -322,8 +321,7 @@ int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_rep
     BIE_LAUNCH(k_rel_diff<<<nk, 256, 0, c->stream>>>(x0, x, N, rel));  // error of the initial guess
     // sensitivity to the FP32 assembly: z = A^{-1} (E x), E a seeded FP32-sized perturbation,
     // by a short GMRES solve; err_est = ||z|| / ||x||
-    dim3 gr((unsigned)((N + 15) / 16), (unsigned)nk);
-    BIE_LAUNCH(k_perturb<<<gr, 512, 0, c->stream>>>(A, (int)N, ld, bstride, x, x0, 6e-8f, 0));
+    BIE_TRY(perturb(c, A, (int)N, ld, bstride, nk, x, x0, 6e-8f));
     BIE_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)nk * N * sizeof(cd), c->stream));
     BIE_TRY(gmres_solve(c, A, nk, (int)N, ld, bstride, x0, z, LUk, lu_bstride, permk, Dk, sel, std::min(m, 20), 1,
                         1e-2, 0.0, gscr, state_e));

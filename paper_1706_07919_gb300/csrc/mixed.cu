@@ -20,11 +20,12 @@ size_t lu_tc_scratch_bytes(int batch, int n, int block);
 int lu_block_for(const bie_ctx* c, int n);
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
-                 int it_max, double tol, cf* D);
+                 int it_max, double tol, cf* D, void* tscratch);
+size_t trsv_scratch_bytes(int nk, int n);
 int64_t diag_inv_stride(int n);
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D);
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch);
 size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est);
@@ -177,7 +178,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(mark(2));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
-                         c->refine_tol, Dinv));
+                         c->refine_tol, Dinv, rowsum));  // the assembly's row sums are free scratch now
     BIE_TRY(mark(3));
     return BIE_OK;
   };
@@ -210,7 +211,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     BIE_TRY(mark(4));
     BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
     BIE_TRY(refine_fp64_system(c, A64, b64, pLU, ld, bstride, pperm, sel_g, ng, (int)N, px, xg, rg, rowabs_g, state_g,
-                               c->refine64_it_max, c->refine64_tol, pD));
+                               c->refine64_it_max, c->refine64_tol, pD, s64));  // the FP64 assembly's scratch
     BIE_TRY(mark(5));
     for (int g = 0; g < ng; ++g) {
       dim3 gs((unsigned)((N + 255) / 256), 1);
@@ -302,7 +303,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
                                                        c->dir[2], known));
         BIE_TRY(rhs_from_known(c, Bk, nk, (int)N, ld, bstride, known, r, b, rowabs, state));
         BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
-                             c->refine_tol, Dinv));
+                             c->refine_tol, Dinv, rowsum));
       }
       BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
       if (d == 0) BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -342,7 +343,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
         BIE_TRY(mark(4));
         BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
         BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
-                                   c->refine64_it_max, c->refine64_tol, Dinv));
+                                   c->refine64_it_max, c->refine64_tol, Dinv, s64));
         BIE_TRY(mark(5));
         BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
         if (timing) {

@@ -229,6 +229,173 @@ __global__ void __launch_bounds__(1024) k_trsv_lu(const cf* __restrict__ LU, int
   }
 }
 
+// ---- the same solves for a few large systems: diagonal super-blocks and wide products ---------
+// k_trsv_lu gives each system one CTA, whose bandwidth (about 180 GB/s) bounds a solve of a few
+// large systems (9 systems of N = 20 544: 9 of 152 SMs busy).  Here the factor is taken in
+// super-blocks of kSuper rows: one CTA per system solves the diagonal super-block (the blocked
+// sweep of k_trsv_lu on that range, with the same diagonal-block inverses), then a launch over all
+// SMs subtracts the super-block's columns times its solved entries from the rows outside it (below
+// it for L, above it for U).  The solution lives in a global FP32 vector y (scaled to O(1) as in
+// k_trsv_lu, the scale kept per system) between the launches.
+constexpr int kSuper = 1024;
+int64_t diag_inv_stride(int n);
+
+// y = P rhs / scale (scale = max |rhs| component), one CTA per system
+__global__ void __launch_bounds__(1024) k_trsv_begin(const int32_t* __restrict__ perm, const cd* __restrict__ rhs,
+                                                     int n, const RefineState* __restrict__ st,
+                                                     const int32_t* __restrict__ sel, cf* __restrict__ y,
+                                                     double* __restrict__ scales) {
+  const int kk = blockIdx.x;
+  if (st && st[kk].done) return;
+  const int fk = sel ? sel[kk] : kk;
+  const int32_t* pm = perm + (int64_t)fk * n;
+  const cd* r = rhs + (int64_t)kk * n;
+  __shared__ double s_scale;
+  if (threadIdx.x == 0) s_scale = 0.0;
+  __syncthreads();
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fmax(fabs(r[i].re), fabs(r[i].im)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&s_scale, __double_as_longlong(mx));
+  __syncthreads();
+  const double sc = s_scale > 0.0 ? s_scale : 1.0;
+  if (threadIdx.x == 0) scales[kk] = sc;
+  cf* yk = y + (int64_t)kk * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cd v = r[pm[i]];
+    yk[i] = {(float)(v.re / sc), (float)(v.im / sc)};
+  }
+}
+
+// diagonal super-block [s0, s1) of system kk's L (LOWER) or U, in place on y; one CTA per system
+template <bool LOWER>
+__global__ void __launch_bounds__(1024) k_trsv_super(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
+                                                     const RefineState* __restrict__ st,
+                                                     const int32_t* __restrict__ sel, cf* __restrict__ y, int s0,
+                                                     int s1, const cf* __restrict__ Dinv, int64_t dstride) {
+  __shared__ cf ys[kSuper];
+  __shared__ cf ytmp[TB];
+  const int kk = blockIdx.x;
+  if (st && st[kk].done) return;
+  const int fk = sel ? sel[kk] : kk;
+  const cf* M = LU + (int64_t)fk * bstride + (int64_t)s0 * ld + s0;
+  cf* yk = y + (int64_t)kk * n;
+  const int m = s1 - s0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = yk[s0 + i];
+  __syncthreads();
+  const cf* Df = Dinv ? Dinv + (int64_t)fk * dstride + (int64_t)(s0 / TB) * 2 * TB * TB : nullptr;
+  trsv_sweep<LOWER>(M, m, ld, ys, Df, ytmp);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) yk[s0 + i] = ys[i];
+}
+
+// rows [r0, r1) of system kk: y[r] -= sum over c in [s0, s1) of F[r][c] y[c]; a warp takes 8 rows,
+// the super-block's entries of y are staged in shared memory.  grid (ceil((r1 - r0) / 64), nk),
+// block 256.
+__global__ void __launch_bounds__(256) k_trsv_gemv(const cf* __restrict__ LU, int n, int64_t ld, int64_t bstride,
+                                                   const RefineState* __restrict__ st,
+                                                   const int32_t* __restrict__ sel, cf* __restrict__ y, int s0, int s1,
+                                                   int r0, int r1) {
+  constexpr int R = 8;
+  __shared__ cf ys[kSuper];
+  const int kk = blockIdx.y;
+  if (st && st[kk].done) return;
+  const int fk = sel ? sel[kk] : kk;
+  cf* yk = y + (int64_t)kk * n;
+  const int m = s1 - s0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = yk[s0 + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = r0 + blockIdx.x * 64 + warp * R;
+  if (i0 >= r1) return;
+  const int nr = min(R, r1 - i0);
+  const cf* F = LU + (int64_t)fk * bstride + (int64_t)i0 * ld + s0;
+  float ar[R], ai[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) ar[u] = ai[u] = 0.f;
+#pragma unroll 2
+  for (int cc = lane; cc < m; cc += 32) {
+    const cf v = ys[cc];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (u < nr) {
+        const cf f = F[(int64_t)u * ld + cc];
+        ar[u] += f.re * v.re - f.im * v.im;
+        ai[u] += f.re * v.im + f.im * v.re;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (u >= nr) break;
+    float a = ar[u], b = ai[u];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      cf& t = yk[i0 + u];
+      t.re -= a;
+      t.im -= b;
+    }
+  }
+}
+
+// out (+)= y * scale
+__global__ void k_trsv_end(const cf* __restrict__ y, const double* __restrict__ scales, int n,
+                           const RefineState* __restrict__ st, cd* __restrict__ out, int accumulate) {
+  const int kk = blockIdx.y;
+  if (st && st[kk].done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double sc = scales[kk];
+  const cf v = y[(int64_t)kk * n + i];
+  cd& o = out[(int64_t)kk * n + i];
+  const cd w = {(double)v.re * sc, (double)v.im * sc};
+  o = accumulate ? cadd(o, w) : w;
+}
+
+size_t trsv_scratch_bytes(int nk, int n) { return 256 + (size_t)nk * n * sizeof(cf) + (size_t)nk * sizeof(double); }
+
+// x (+)= (LU)^{-1} P rhs for nk systems (vectors [nk][n]; factor sel[kk] if sel); systems whose
+// state is done are skipped.  The super-block form when the systems are few and large and
+// `scratch` (trsv_scratch_bytes) is given, otherwise k_trsv_lu.
+int trsv_solve(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t bstride, const int32_t* perm,
+               const cd* rhs, cd* out, int accumulate, const RefineState* st, const int32_t* sel, const cf* D,
+               void* scratch) {
+  const int64_t dstride = diag_inv_stride(n);
+  int nsm = 0;
+  BIE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  if (!scratch || !D || n < 4 * kSuper || 2 * nk > nsm) {
+    BIE_TRY((set_smem_max(k_trsv_lu)));
+    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, (size_t)n * sizeof(cf), c->stream>>>(LU, n, ld, bstride, perm, rhs, out, accumulate,
+                                                                        st, sel, n, 0, n, 0, D, dstride));
+    return BIE_OK;
+  }
+  double* scales = (double*)scratch;
+  cf* y = (cf*)((char*)scratch + (((size_t)nk * sizeof(double) + 255) & ~(size_t)255));
+  BIE_LAUNCH(k_trsv_begin<<<nk, 1024, 0, c->stream>>>(perm, rhs, n, st, sel, y, scales));
+  const int ns = (n + kSuper - 1) / kSuper;
+  for (int b = 0; b < ns; ++b) {  // L: super-blocks in order, then the rows below
+    const int s0 = b * kSuper, s1 = std::min(n, s0 + kSuper);
+    BIE_LAUNCH(k_trsv_super<true><<<nk, 1024, 0, c->stream>>>(LU, n, ld, bstride, st, sel, y, s0, s1, D, dstride));
+    if (s1 < n) {
+      dim3 g((unsigned)((n - s1 + 63) / 64), nk);
+      BIE_LAUNCH(k_trsv_gemv<<<g, 256, 0, c->stream>>>(LU, n, ld, bstride, st, sel, y, s0, s1, s1, n));
+    }
+  }
+  for (int b = ns - 1; b >= 0; --b) {  // U: super-blocks in reverse, then the rows above
+    const int s0 = b * kSuper, s1 = std::min(n, s0 + kSuper);
+    BIE_LAUNCH(k_trsv_super<false><<<nk, 1024, 0, c->stream>>>(LU, n, ld, bstride, st, sel, y, s0, s1, D, dstride));
+    if (s0 > 0) {
+      dim3 g((unsigned)((s0 + 63) / 64), nk);
+      BIE_LAUNCH(k_trsv_gemv<<<g, 256, 0, c->stream>>>(LU, n, ld, bstride, st, sel, y, s0, s1, 0, s0));
+    }
+  }
+  dim3 ge((unsigned)((n + 255) / 256), nk);
+  BIE_LAUNCH(k_trsv_end<<<ge, 256, 0, c->stream>>>(y, scales, n, st, out, accumulate));
+  return BIE_OK;
+}
+
 // ---- residual r = b - A x in float-float; also the row sums of |A| for ||A||_inf ------------
 // grid (ceil(n / 16), batch), block 512: one warp per row, x staged in shared memory as ff.
 __device__ __forceinline__ void ff_acc_prod(float a, float xh, float xl, float& sh, float& sl) {
@@ -288,6 +455,74 @@ __global__ void __launch_bounds__(512) k_residual_ff(const cf* __restrict__ A, i
     r[(int64_t)kk * n + i] = {bi.re - sr, bi.im - si};
     rowabs[(int64_t)kk * n + i] = sa;
   }
+}
+
+// The same residual for large n (x does not fit shared memory with several CTAs per SM): a warp
+// takes 8 rows, so that each FP64 entry of x it reads is split into float-float once for 8 rows
+// (the FP64 conversions of the one-row-per-warp form bounded it on the narrow FP64 pipe).
+// grid (ceil(n / 64), batch), block 256.
+__global__ void __launch_bounds__(256) k_residual_ff_r8(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
+                                                        const cd* __restrict__ b, const cd* __restrict__ x,
+                                                        cd* __restrict__ r, double* __restrict__ rowabs,
+                                                        const RefineState* __restrict__ st) {
+  constexpr int R = 8;
+  const int kk = blockIdx.y;
+  if (st[kk].done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 64 + warp * R;
+  if (i0 >= n) return;
+  const int nr = min(R, n - i0);
+  const cf* A0 = A + (int64_t)kk * bstride + (int64_t)i0 * ld;
+  const cd* xk = x + (int64_t)kk * n;
+  float rh[R], rl[R], ih[R], il[R], ab[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) rh[u] = rl[u] = ih[u] = il[u] = ab[u] = 0.f;
+#pragma unroll 2
+  for (int j = lane; j < n; j += 32) {
+    const ff p = ff_from_double(xk[j].re), q = ff_from_double(xk[j].im);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (u < nr) {
+        const cf a = A0[(int64_t)u * ld + j];
+        ff_acc_prod(a.re, p.hi, p.lo, rh[u], rl[u]);
+        ff_acc_prod(-a.im, q.hi, q.lo, rh[u], rl[u]);
+        ff_acc_prod(a.re, q.hi, q.lo, ih[u], il[u]);
+        ff_acc_prod(a.im, p.hi, p.lo, ih[u], il[u]);
+        ab[u] += fabsf(a.re) + fabsf(a.im);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (u >= nr) break;
+    double sr = (double)rh[u] + (double)rl[u], si = (double)ih[u] + (double)il[u], sa = ab[u];
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    if (lane == 0) {
+      const int64_t t = (int64_t)kk * n + i0 + u;
+      const cd bi = b[t];
+      r[t] = {bi.re - sr, bi.im - si};
+      rowabs[t] = sa;
+    }
+  }
+}
+
+// The residual of nk systems: x staged in shared memory while it fits four CTAs per SM,
+// otherwise 8 rows per warp.
+int residual_ff(bie_ctx* c, const cf* A, int n, int64_t ld, int64_t bstride, int nk, const cd* b, const cd* x, cd* r,
+                double* rowabs, const RefineState* st) {
+  if ((size_t)n * sizeof(float4) <= 48 * 1024) {
+    BIE_TRY((set_smem_max(k_residual_ff)));
+    dim3 gr((unsigned)((n + 15) / 16), nk);
+    BIE_LAUNCH(k_residual_ff<<<gr, 512, (size_t)n * sizeof(float4), c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st, 1));
+  } else {
+    dim3 gr((unsigned)((n + 63) / 64), nk);
+    BIE_LAUNCH(k_residual_ff_r8<<<gr, 256, 0, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st));
+  }
+  return BIE_OK;
 }
 
 // ---- convergence test per system (one CTA each) ----------------------------------------------
@@ -371,6 +606,67 @@ __global__ void __launch_bounds__(512) k_perturb(const cf* __restrict__ A, int n
   if (lane == 0) v[(int64_t)kk * n + i] = {(double)sr, (double)si};
 }
 
+// The same perturbation for large n: a warp takes 8 rows and rounds each entry of x it reads
+// once for all of them (no shared-memory copy of x, which at large n left one CTA per SM).
+// grid (ceil(n / 64), batch), block 256.
+__global__ void __launch_bounds__(256) k_perturb_r8(const cf* __restrict__ A, int n, int64_t ld, int64_t bstride,
+                                                    const cd* __restrict__ x, cd* __restrict__ v, float eps) {
+  constexpr int R = 8;
+  const int kk = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 64 + warp * R;
+  if (i0 >= n) return;
+  const int nr = min(R, n - i0);
+  const cf* A0 = A + (int64_t)kk * bstride + (int64_t)i0 * ld;
+  const cd* xk = x + (int64_t)kk * n;
+  float sr[R], si[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) sr[u] = si[u] = 0.f;
+#pragma unroll 2
+  for (int j = lane; j < n; j += 32) {
+    const float2 xv = make_float2((float)xk[j].re, (float)xk[j].im);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (u < nr) {
+        const int i = i0 + u;
+        const cf a = A0[(int64_t)u * ld + j];
+        const float a2 = a.re * a.re + a.im * a.im;
+        const float m = a2 > 0.f ? eps * (a2 * rsqrtf(a2)) : 0.f;
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)j * 0x85EBCA77u + 0x27D4EB2Fu);
+        h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12;
+        const uint32_t q = (h >> 30) & 3u;
+        const float er = (q == 0) ? m : (q == 2 ? -m : 0.f), ei = (q == 1) ? m : (q == 3 ? -m : 0.f);
+        sr[u] += er * xv.x - ei * xv.y;
+        si[u] += er * xv.y + ei * xv.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (u >= nr) break;
+    float a = sr[u], b2 = si[u];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    }
+    if (lane == 0) v[(int64_t)kk * n + i0 + u] = {(double)a, (double)b2};
+  }
+}
+
+// The perturbation product of nk systems (x rounded once per CTA into shared memory while it
+// fits four CTAs per SM, otherwise 8 rows per warp).
+int perturb(bie_ctx* c, const cf* A, int n, int64_t ld, int64_t bstride, int nk, const cd* x, cd* v, float eps) {
+  if ((size_t)n * sizeof(float2) <= 48 * 1024) {
+    BIE_TRY((set_smem_max(k_perturb)));
+    dim3 gr((unsigned)((n + 15) / 16), nk);
+    BIE_LAUNCH(k_perturb<<<gr, 512, (size_t)n * sizeof(float2), c->stream>>>(A, n, ld, bstride, x, v, eps, 1));
+  } else {
+    dim3 gr((unsigned)((n + 63) / 64), nk);
+    BIE_LAUNCH(k_perturb_r8<<<gr, 256, 0, c->stream>>>(A, n, ld, bstride, x, v, eps));
+  }
+  return BIE_OK;
+}
+
 __global__ void k_err_est(int n, const cd* __restrict__ x, const cd* __restrict__ z, RefineState* __restrict__ st) {
   const int kk = blockIdx.x;
   __shared__ double red[2][32];
@@ -407,35 +703,26 @@ int diag_inverses(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t b
 
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
-                 int it_max, double tol, cf* D) {
+                 int it_max, double tol, cf* D, void* tscratch) {
   RefineState* st = (RefineState*)state_dev;
-  const int64_t dstride = diag_inv_stride(n);
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
   if ((size_t)n * sizeof(int32_t) > 200 * 1024) return fail(BIE_ERR_INVALID_ARG, "N too large for the permutation kernel");
   BIE_TRY((set_smem_max(k_piv_to_perm)));
   BIE_LAUNCH(k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm));
   if (D) BIE_TRY(diag_inverses(c, LU, nk, n, ld, bstride, D));
   const size_t sm_trsv = (size_t)n * sizeof(cf);
-  const int stage = (size_t)n * sizeof(float4) <= 200 * 1024 ? 1 : 0;
-  const size_t sm_res = stage ? (size_t)n * sizeof(float4) : 0;
   if (sm_trsv > 200 * 1024)
     return fail(BIE_ERR_INVALID_ARG, "N too large for the shared-memory triangular solves (N <= 25600)");
-  BIE_TRY((set_smem_max(k_trsv_lu)));
-  BIE_TRY((set_smem_max(k_residual_ff)));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
-  dim3 gr((unsigned)((n + 15) / 16), nk);
+  BIE_TRY(trsv_solve(c, LU, nk, n, ld, bstride, perm, b, x, 0, nullptr, nullptr, D, tscratch));
   for (int it = 0; it <= it_max; ++it) {
-    BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(A, n, ld, bstride, b, x, r, rowabs, st, stage));
+    BIE_TRY(residual_ff(c, A, n, ld, bstride, nk, b, x, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<nk, 256, 0, c->stream>>>(n, b, x, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, x, 1, st, nullptr, n, 0, n, 0, D, dstride));
+    BIE_TRY(trsv_solve(c, LU, nk, n, ld, bstride, perm, r, x, 1, st, nullptr, D, tscratch));
   }
   // assembly-sensitivity estimate (r is free now)
-  const int pstage = (size_t)n * sizeof(float2) <= 200 * 1024 ? 1 : 0;
-  BIE_TRY((set_smem_max(k_perturb)));
-  BIE_LAUNCH(k_perturb<<<gr, 512, pstage ? (size_t)n * sizeof(float2) : 0, c->stream>>>(A, n, ld, bstride, x, r, 6e-8f,
-                                                                                      pstage));
-  BIE_LAUNCH(k_trsv_lu<<<nk, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, n, 0, n, 0, D, dstride));
+  BIE_TRY(perturb(c, A, n, ld, bstride, nk, x, r, 6e-8f));
+  BIE_TRY(trsv_solve(c, LU, nk, n, ld, bstride, perm, r, r, 0, nullptr, nullptr, D, tscratch));
   BIE_LAUNCH(k_err_est<<<nk, 256, 0, c->stream>>>(n, x, r, st));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -451,11 +738,7 @@ int rhs_from_known(bie_ctx* c, const cf* B, int nk, int n, int64_t ld, int64_t b
   RefineState* st = (RefineState*)state_dev;
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, nk * sizeof(RefineState), c->stream));
   BIE_CUDA_TRY(cudaMemsetAsync(zero, 0, (size_t)nk * n * sizeof(cd), c->stream));
-  const int stage = (size_t)n * sizeof(float4) <= 200 * 1024 ? 1 : 0;
-  const size_t sm_res = stage ? (size_t)n * sizeof(float4) : 0;
-  BIE_TRY((set_smem_max(k_residual_ff)));
-  dim3 gr((unsigned)((n + 15) / 16), nk);
-  BIE_LAUNCH(k_residual_ff<<<gr, 512, sm_res, c->stream>>>(B, n, ld, bstride, zero, known, b, rowabs, st, stage));
+  BIE_TRY(residual_ff(c, B, n, ld, bstride, nk, zero, known, b, rowabs, st));
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -518,19 +801,17 @@ __global__ void k_gather_scatter(cd* __restrict__ xb, cd* __restrict__ xg, const
 // rowabs [ng][n], state [ng].
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D) {
-  const int64_t dstride = diag_inv_stride(n);
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch) {
   RefineState* st = (RefineState*)state_dev;
   BIE_CUDA_TRY(cudaMemsetAsync(st, 0, ng * sizeof(RefineState), c->stream));
   dim3 gv((unsigned)((n + 255) / 256), ng);
   BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 1));
-  const size_t sm_trsv = (size_t)n * sizeof(cf);
   dim3 gr((unsigned)((n + 15) / 16), ng);
   for (int it = 0; it <= it_max; ++it) {
     BIE_LAUNCH(k_residual64<<<gr, 512, 0, c->stream>>>(A64, n, b64, xg, r, rowabs, st));
     BIE_LAUNCH(k_refine_check<<<ng, 256, 0, c->stream>>>(n, b64, xg, r, rowabs, st, tol, it < it_max));
     if (it == it_max) break;
-    BIE_LAUNCH(k_trsv_lu<<<ng, 1024, sm_trsv, c->stream>>>(LU, n, ld, bstride, perm, r, xg, 1, st, sel_dev, n, 0, n, 0, D, dstride));
+    BIE_TRY(trsv_solve(c, LU, ng, n, ld, bstride, perm, r, xg, 1, st, sel_dev, D, tscratch));
   }
   BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 0));
   BIE_CUDA_TRY(cudaGetLastError());
