@@ -232,6 +232,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          CTA, tiles of 32 quadrature points, FP32 run sums; 1 the same with 64
  *                          points per CTA and 64-point tiles; 0 groups of 8, 128 points,
  *                          compensated sums per term
+ *   "mixed.reassembly_group" flagged wavenumbers re-assembled and refined together (1..32,
+ *                          default 32; device memory may lower it)
  *   "mixed.reassembly"     system of the flagged wavenumbers: 1 (default) bulk pairs in float-float
  *                          (~48-bit, FP32 pipes), 0 in FP64; near pairs and diagonal are FP64
  *   "assemble.bulk_ff"     bie_assemble's bulk pairs in float-float (1) or FP64 (0, default)
@@ -279,6 +281,27 @@ int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
  * STATE, OOM (scratch larger than free device memory), CUDA. */
 int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, void* surf_out,
                           bie_report* rep);
+
+/* The mixed-precision frequency solves of bie_solve_frequencies (Sec. 3 Eq. BRIEF assembled,
+ * factored and solved per wavenumber as in Sec. 4), stream-ordered: the call returns once its work
+ * is enqueued on the context's stream, so that host work and other contexts' streams overlap it.
+ * Every decision the synchronous call takes on the host runs on the device instead: wavenumbers
+ * flagged by their refinement state or sensitivity estimate are re-assembled in FP64 and refined
+ * against that system with their own TF32 factor, in rounds over the batch's flagged systems.
+ *   k        host f64 [Nk], as bie_solve_frequencies; copied into the launches, free on return
+ *   mode     BIE_MODE_MIXED
+ *   surf_out device c128 [Nk][2][N], written in stream order
+ *   rep      host bie_report [Nk] or NULL: filled by a host function in stream order, valid once
+ *            the stream has completed this call's work (e.g. after cudaStreamSynchronize); the
+ *            array must stay allocated until then
+ * Differences from bie_solve_frequencies: no last-resort full FP64 solve -- a wavenumber whose
+ * re-assembly does not converge, or whose factor met a zero pivot, keeps BIE_FLAG_NOT_CONVERGED;
+ * "mixed.graph" and "mixed.phase_timing" do not apply.  The first solve after bie_set_geometry
+ * builds the mixed path's geometry tables and may synchronise.  Calls on one context share its
+ * workspace and are ordered by its stream.  Errors (before anything is enqueued): as
+ * bie_solve_frequencies; INVALID_ARG for another mode or linear elements. */
+int bie_solve_frequencies_async(bie_ctx* ctx, const double* k, int64_t Nk, int mode, void* surf_out,
+                                bie_report* rep);
 
 /* Frequency solves for several incident plane waves at once (Sec. 5: for a fixed configuration the
  * solution matrix is kept and only the incident wave changes).  Per wavenumber the system matrix

@@ -39,7 +39,8 @@ EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create"
             "bie_mlp_get_params", "bie_mlp_features", "bie_mlp_forward", "bie_mlp_loss_grad", "bie_mlp_adam_step",
             "bie_mlp_train", "bie_mlp_predict", "bie_get_learned_info", "bie_autotune", "bie_sched_create",
             "bie_sched_destroy", "bie_sched_add", "bie_sched_run", "bie_get_phase_times", "bie_measure_peaks",
-            "bie_top_frequencies", "bie_solve_frequencies_multi", "bie_set_geometry_linear"]
+            "bie_top_frequencies", "bie_solve_frequencies_multi", "bie_set_geometry_linear",
+            "bie_solve_frequencies_async"]
 
 
 class BieReport(ctypes.Structure):
@@ -132,6 +133,7 @@ def load(path: str | None = None):
         "bie_top_frequencies": ([vp, vp, i64, i64, i64, vp], i32),
         "bie_solve_frequencies_multi": ([vp, vp, i64, vp, i64, i32, vp, vp], i32),
         "bie_set_geometry_linear": ([vp, vp, i64, vp, i64, vp, vp], i32),
+        "bie_solve_frequencies_async": ([vp, vp, i64, i32, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -222,6 +224,44 @@ def bie_solve_frequencies(ctx: int, k, mode: int, surf_out, reports: bool = True
     _check(load().bie_solve_frequencies(ctx, _hp(k), k.shape[0], mode, _dp(surf_out),
                                         ctypes.cast(rep, ctypes.c_void_p) if rep is not None else None))
     return list(rep)[: k.shape[0]] if rep is not None else None
+
+
+class PendingReports:
+    """Reports of a stream-ordered solve: the host array that the library fills in stream order,
+    with an event recorded on the context's stream after the call.  `reports()` waits for that
+    event; dropping the object also waits for it first, so that the array outlives the library's
+    write into it."""
+
+    def __init__(self, arr, n: int, event):
+        self._arr, self._n, self._ev = arr, n, event
+
+    def done(self) -> bool:
+        return self._ev.query()
+
+    def reports(self):
+        self._ev.synchronize()
+        return list(self._arr)[: self._n] if self._arr is not None else None
+
+    def __del__(self):
+        try:
+            self._ev.synchronize()
+        except Exception:
+            pass
+
+
+def bie_solve_frequencies_async(ctx: int, k, mode: int, surf_out, stream, reports: bool = True) -> PendingReports:
+    """stream: the torch.cuda.Stream the context was created with."""
+    import torch
+
+    k = np.ascontiguousarray(k, np.float64)
+    if _dtype_name(surf_out) != "complex128" or (k.shape[0] and _numel(surf_out) % (2 * k.shape[0])):
+        raise ValueError("surf_out must be complex128 [Nk][2][N]")
+    rep = (BieReport * max(1, k.shape[0]))() if reports else None
+    _check(load().bie_solve_frequencies_async(ctx, _hp(k), k.shape[0], mode, _dp(surf_out),
+                                              ctypes.cast(rep, ctypes.c_void_p) if rep is not None else None))
+    ev = torch.cuda.Event()
+    ev.record(stream)
+    return PendingReports(rep, k.shape[0], ev)
 
 
 def bie_solve_frequencies_multi(ctx: int, k, dirs, mode: int, surf_out, reports: bool = True):

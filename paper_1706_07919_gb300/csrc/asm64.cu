@@ -25,6 +25,7 @@ __global__ void k_known64(const double* __restrict__ nodes, const double* __rest
   int kk = blockIdx.y;
   if (j >= N) return;
   double k = kv[kk];
+  if (k < 0.0) return;  // an idle slot of a re-assembly round (stream-ordered solves)
   double ph = k * (dx * nodes[3 * j] + dy * nodes[3 * j + 1] + dz * nodes[3 * j + 2]);
   double s, c;
   sincos(ph, &s, &c);
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(512) k_asm64_bulk(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kk = blockIdx.y;
   const double k = kv[kk];
+  if (k < 0.0) return;  // an idle slot of a re-assembly round (stream-ordered solves)
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = qshape[t];
   const int64_t i = (int64_t)blockIdx.x * rows + warp;
   if constexpr (GROW) {
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(256) k_asm64_near(
   const int kk = blockIdx.y;
   if (i >= N) return;
   const double k = kv[kk];
+  if (k < 0.0) return;  // an idle slot of a re-assembly round (stream-ordered solves)
   const cd* kn = known + (int64_t)kk * N;
   const double xi[3] = {nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2]};
   const double nui[3] = {normals[3 * i], normals[3 * i + 1], normals[3 * i + 2]};

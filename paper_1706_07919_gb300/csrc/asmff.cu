@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rw = warp / WR, wr = warp % WR, sub = wr % ASMF_W, h = wr / ASMF_W;
   const int kk = blockIdx.y;
+  if (kv[kk] < 0.0) return;  // an idle slot of a re-assembly round (stream-ordered solves)
   const ff k = ff_from_double(kv[kk]);
   const bool kzero = !(kv[kk] > 0.0);  // the zero-frequency term: f takes its limit nu_i.r
   const ff kinv = ff_from_double(kzero ? 0.0 : 1.0 / kv[kk]);

@@ -148,6 +148,7 @@ struct bie_ctx {
   int uniform_bc = -1;               // every element has one condition on all nodes (1), not (0), unknown
   int asm_kb = 2;                    // FP32 bulk assembly: wavenumbers per thread (1, 2), 0 = the
                                      // general kernel (also taken when an element mixes conditions)
+  int reassembly_group = 32;         // FP64 re-assembly slots refined together (1..32; memory may lower it)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph
   int phase_timing = 0;              // time the mixed path's phases with CUDA events (no graphs)
@@ -157,6 +158,8 @@ struct bie_ctx {
   void* pinned = nullptr;            // pinned host staging (wavenumbers of graph replays)
   cudaStream_t cap_stream = nullptr; // private stream on which CUDA graphs are captured
   size_t pinned_bytes = 0;
+  void* rep_pinned = nullptr;        // pinned staging of the stream-ordered solves' reports
+  size_t rep_pinned_bytes = 0;
 
   // learned warm start + Krylov path (BIE_MODE_LEARNED)
   int learned_stride = 8;            // every stride-th wavenumber is solved directly (an anchor)

@@ -124,6 +124,7 @@ int top_frequencies(bie_ctx* c, const cd* S, int64_t P, int nm, int K, int64_t* 
 int solve_fp64_linear(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
 int assemble_linear_one(bie_ctx* c, double k, cd* A_out, cd* b_out);
 int expand_linear(bie_ctx* c, const cd* surf_lin, int nk, cd* surf_q);
+int solve_mixed_async(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
 int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep, cf* lu_keep,
                 int32_t* perm_keep, cf* d_keep, const double* dirs, int ndir);
 int solve_learned(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_report* rep);
@@ -362,6 +363,7 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c, c->work5);
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->rep_pinned) cudaFreeHost(c->rep_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return BIE_OK;
@@ -389,6 +391,9 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value != 0.0 && value != 128.0 && value != 256.0 && value != 512.0)
       return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 0 (by N), 128, 256 or 512");
     c->lu_block = (int)value;
+  } else if (n == "mixed.reassembly_group") {
+    if (value < 1 || value > 32) return fail(BIE_ERR_INVALID_ARG, "mixed.reassembly_group must be in [1, 32]");
+    c->reassembly_group = (int)value;
   } else if (n == "mixed.lu_coop") {
     c->lu_coop = value != 0.0 ? 1 : 0;
   } else if (n == "mixed.lu_tile") {
@@ -546,6 +551,16 @@ int bie_solve_frequencies(bie_ctx* c, const double* k, int64_t Nk, int mode, voi
   if (mode == BIE_MODE_MIXED) return solve_mixed(c, k, Nk, (cd*)surf_out, rep, nullptr, nullptr, nullptr, nullptr, 1);
   if (mode == BIE_MODE_LEARNED) return solve_learned(c, k, Nk, (cd*)surf_out, rep);
   return fail(BIE_ERR_INVALID_ARG, "unknown mode " + std::to_string(mode));
+}
+
+int bie_solve_frequencies_async(bie_ctx* c, const double* k, int64_t Nk, int mode, void* surf_out, bie_report* rep) {
+  BIE_TRY(check_ctx(c, true));
+  BIE_TRY(check_k(k, Nk, true));
+  if (Nk == 0) return BIE_OK;
+  if (!surf_out) return fail(BIE_ERR_INVALID_ARG, "NULL surf_out");
+  if (c->lin_N > 0) return fail(BIE_ERR_INVALID_ARG, "linear elements: bie_solve_frequencies (BIE_MODE_FP64) only");
+  if (mode != BIE_MODE_MIXED) return fail(BIE_ERR_INVALID_ARG, "bie_solve_frequencies_async: BIE_MODE_MIXED only");
+  return solve_mixed_async(c, k, Nk, (cd*)surf_out, rep);
 }
 
 // ---- learned warm start ----------------------------------------------------------------------

@@ -25,7 +25,8 @@ size_t trsv_scratch_bytes(int nk, int n);
 int64_t diag_inv_stride(int n);
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch);
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch,
+                       bool reset_state);
 size_t refine_state_bytes(int nk);
 int refine_read_state(bie_ctx* c, const void* state_dev, int nk, int32_t* done, int32_t* iters, double* berr,
                       double* err_est);
@@ -88,7 +89,8 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
   const size_t fb1 = align256((size_t)N * N * sizeof(cd)) + 7 * vec + align256((size_t)N * 8) + 1024 + pool1;
   size_t free_b = 0;
   BIE_TRY(device_free(c, &free_b));
-  const int G = (int)std::max<size_t>(1, std::min<size_t>(kFallbackGroupMax, (free_b / 8) / fb1));
+  const int G = (int)std::max<size_t>(
+      1, std::min<size_t>(std::min(kFallbackGroupMax, c->reassembly_group), (free_b / 8) / fb1));
   const size_t fb = (size_t)G * fb1 + 4096;
   const size_t avail = free_b > fb ? free_b - fb : 0;
   int64_t kb = std::max<int64_t>(1, std::min<int64_t>(Nk, std::min<int64_t>(c->mixed_batch, (int64_t)((avail / 2) / perk))));
@@ -211,7 +213,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     BIE_TRY(mark(4));
     BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
     BIE_TRY(refine_fp64_system(c, A64, b64, pLU, ld, bstride, pperm, sel_g, ng, (int)N, px, xg, rg, rowabs_g, state_g,
-                               c->refine64_it_max, c->refine64_tol, pD, s64));  // the FP64 assembly's scratch
+                               c->refine64_it_max, c->refine64_tol, pD, s64, true));  // the FP64 assembly's scratch
     BIE_TRY(mark(5));
     for (int g = 0; g < ng; ++g) {
       dim3 gs((unsigned)((N + 255) / 256), 1);
@@ -343,7 +345,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
         BIE_TRY(mark(4));
         BIE_TRY(assemble64(c, kg, ng, A64, b64, s64, c->reassembly_ff != 0));
         BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, ng, (int)N, x, xg, rg, rowabs_g, state_g,
-                                   c->refine64_it_max, c->refine64_tol, Dinv, s64));
+                                   c->refine64_it_max, c->refine64_tol, Dinv, s64, true));
         BIE_TRY(mark(5));
         BIE_TRY(refine_read_state(c, state_g, ng, gd.data(), gi.data(), gb.data(), ge.data()));
         if (timing) {

@@ -791,19 +791,21 @@ __global__ void k_gather_scatter(cd* __restrict__ xb, cd* __restrict__ xg, const
                                  int to_group) {
   const int g = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || sel[g] < 0) return;
   cd* src = to_group ? xb + (int64_t)sel[g] * n : xg + (int64_t)g * n;
   cd* dst = to_group ? xg + (int64_t)g * n : xb + (int64_t)sel[g] * n;
   dst[i] = src[i];
 }
 
 // Refines x[sel[g]] (g < ng) against A64/b64 [ng] with factors LU[sel[g]].  Scratch: xg, r [ng][n],
-// rowabs [ng][n], state [ng].
+// rowabs [ng][n], state [ng] (zeroed here with reset_state; otherwise the caller's: a slot whose
+// state is done, or whose selection is negative, is left alone).
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
-                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch) {
+                       double* rowabs, void* state_dev, int it_max, double tol, const cf* D, void* tscratch,
+                       bool reset_state) {
   RefineState* st = (RefineState*)state_dev;
-  BIE_CUDA_TRY(cudaMemsetAsync(st, 0, ng * sizeof(RefineState), c->stream));
+  if (reset_state) BIE_CUDA_TRY(cudaMemsetAsync(st, 0, ng * sizeof(RefineState), c->stream));
   dim3 gv((unsigned)((n + 255) / 256), ng);
   BIE_LAUNCH(k_gather_scatter<<<gv, 256, 0, c->stream>>>(x, xg, sel_dev, n, 1));
   dim3 gr((unsigned)((n + 15) / 16), ng);

@@ -62,6 +62,16 @@ class Solver:
         rep = B.bie_solve_frequencies(self.ctx, k, mode, surf)
         return surf, rep
 
+    def solve_frequencies_async(self, k, out=None):
+        """Mixed-precision solves enqueued on the context's stream (bie_solve_frequencies_async):
+        returns (surf, pending) at once; pending.reports() waits for the stream's work and returns
+        the reports.  surf is written in stream order: keep it until then too."""
+        k = np.ascontiguousarray(k, np.float64)
+        surf = out if out is not None else torch.empty((k.shape[0], 2, self.N), dtype=torch.complex128,
+                                                       device=self._dev())
+        pending = B.bie_solve_frequencies_async(self.ctx, k, B.BIE_MODE_MIXED, surf, self.stream)
+        return surf, pending
+
     def solve_frequencies_multi(self, k, dirs, mode: int = B.BIE_MODE_MIXED, out=None):
         """Surface solutions [Nk][ndir][2][N] for several incident directions sharing each factor."""
         k = np.ascontiguousarray(k, np.float64)
