@@ -320,16 +320,21 @@ __global__ void __launch_bounds__(256) k_leaf_update(Cx<S>* __restrict__ A, int6
 // a 16-column leaf that fits one CTA's shared memory, one CTA per matrix leaves most SMs idle and
 // has to narrow its leaves to a column or two.  Here `cpm` CTAs share each matrix: CTA j of
 // matrix z holds rows [p0 + j ch, p0 + (j + 1) ch) of a leaf of up to 16 columns in shared memory
-// (column by column), and the CTAs of one matrix agree on every pivot through a per-matrix
-// barrier in global memory, one per column:
+// (column by column), and the CTAs of one matrix agree on every pivot through records in global
+// memory, one exchange per column:
 //   each CTA posts its best candidate row (largest modulus, lowest row on ties) with the
-//   candidate's leaf entries, and the holder of row c posts row c's; after the barrier every CTA
-//   picks the same winner p, the holders of rows c and p exchange them in shared memory, and
-//   every CTA scales column c of its rows and applies the rank-1 update to the rest of its leaf.
+//   candidate's leaf entries (CTA 0 adds row c's), the record's tag written last with release
+//   semantics; one warp of every CTA polls the matrix's tags (acquire) until all carry this
+//   column's, which makes the exchange its own barrier; every CTA picks the same winner p, the
+//   holders of rows c and p exchange them in shared memory, and every CTA scales column c of its
+//   rows and applies the rank-1 update to the rest of its leaf, finding its next candidate on the
+//   way.  The records of consecutive columns alternate between two buffers, which is safe because
+//   no CTA can post column c + 2 before every CTA has posted column c + 1, after reading column c.
 // After a leaf, CTA 0 (its chunk holds the panel's diagonal rows: ch is a multiple of 64) applies
 // the leaf's row interchanges, as one gather of the at most 2 lw rows they touch, to the panel's
 // other columns and solves the leaf's U block L11^{-1} A12 for the panel columns right of the
-// leaf; after a second barrier every CTA updates its rows of those columns, A -= L U (K = lw).
+// leaf; after a barrier (a counter in global memory) every CTA updates its rows of those
+// columns, A -= L U (K = lw).
 // Launched cooperatively, so that all CTAs are resident together.  Every wait is bounded: a CTA
 // whose wait gives up raises the error word (bit 8) and an abort flag on which every other wait
 // ends, and all CTAs leave.  Data written by other CTAs is read with L2-coherent loads.
@@ -339,18 +344,27 @@ constexpr int LWMAX = 16;
 constexpr int WMAX = 64;                 // panel width
 constexpr uint32_t SPIN = 1u << 21;      // polls of one barrier (about a second) before giving up
 struct alignas(16) Cand {                // one CTA's pivot candidate for one column
-  float best;                            // |a|^2 (-1: no row)
-  int idx;                               // its row
-  int pad0, pad1;
-  Cx<float> v[LWMAX];                    // its leaf entries
+  // |a|^2 of the candidate (bits of the float, -1: no row) << 32 | its row << 8 | tag: the column's
+  // place in the panel + 1 (1 .. 64; 0: not written in this launch), stored last with release
+  // semantics, so that one acquire load gives the whole verdict
+  unsigned long long head;
+  int pad[2];
+  Cx<float> v[LWMAX];                    // the candidate's leaf entries
+  Cx<float> d[LWMAX];                    // CTA 0: row c's leaf entries
 };
-// scratch: [nmat] barrier counters, abort flag, [2][grid] candidates, [2][nmat][LWMAX] row c
+// scratch: [nmat] barrier counters, abort flag, [2][grid] candidate records (zeroed before each
+// launch with the counters)
 inline size_t scratch_bytes(int nmat, int grid) {
-  return 256 + (size_t)(nmat + 1) * 4 + 256 + 2 * (size_t)grid * sizeof(Cand) + 2 * (size_t)nmat * LWMAX * 8 + 256;
+  return 256 + (size_t)(nmat + 1) * 4 + 256 + 2 * (size_t)grid * sizeof(Cand) + 256;
 }
 }  // namespace coop
 constexpr int kCoopMaxGrid = 4096;  // CTAs of one cooperative panel launch (at most)
 
+__device__ __forceinline__ unsigned long long ld_acquire_gpu64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -364,13 +378,12 @@ __device__ __forceinline__ Cx<float> ldcg_cx(const Cx<float>* p) {
 __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
     Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0, int w, int lw, int cpm, int ch,
     int32_t* __restrict__ piv, int32_t* __restrict__ info, unsigned* __restrict__ bar, unsigned* abort_flag,
-    coop::Cand* __restrict__ cand, Cx<float>* __restrict__ diag, int32_t* __restrict__ err) {
+    coop::Cand* __restrict__ cand, int32_t* __restrict__ err) {
   using coop::LWMAX;
   using coop::NT;
   extern __shared__ float4 coop_smem[];
   Cx<float>* S = reinterpret_cast<Cx<float>*>(coop_smem);  // [lw][ch]: leaf entry (r, t) at t * ch + r - r_lo
   Cx<float>* Ub = S + (size_t)lw * ch;                     // [LWMAX][WMAX]: the leaf's U block
-  coop::Cand* sc = reinterpret_cast<coop::Cand*>(Ub + LWMAX * coop::WMAX);  // [cpm]: the matrix's candidates
   __shared__ Cx<float> s_u[LWMAX], s_d[LWMAX];             // pivot row, former row c (leaf entries)
   __shared__ float red_v[NT / 32];
   __shared__ int red_i[NT / 32];
@@ -430,6 +443,7 @@ __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
     }
     for (int cc = 0; cc < l; ++cc) {
       const int c = c0 + cc, buf = c & 1;
+      const unsigned tag = (unsigned)(c - p0) + 1u;
       for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -446,47 +460,71 @@ __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         coop::Cand* cd = cand + (int64_t)buf * gridDim.x + blockIdx.x;
-        if (lane == 0) { cd->best = best; cd->idx = bi; }
-        if (lane < l) cd->v[lane] = bi < r_hi ? S[lane * ch + bi - r_lo] : Cx<float>{0.f, 0.f};
-        if (c >= r_lo && c < r_hi && lane < l)
-          diag[((int64_t)buf * nmat + z) * LWMAX + lane] = S[lane * ch + c - r_lo];
-      }
-      if (!barrier()) return;
-      {  // the matrix's candidates and row c, in one round trip
-        const float4* src = reinterpret_cast<const float4*>(cand + (int64_t)buf * gridDim.x + (int64_t)z * cpm);
-        float4* dst = reinterpret_cast<float4*>(sc);
-        constexpr int W4 = (int)(sizeof(coop::Cand) / 16);
-        for (int e = tid; e < cpm * W4; e += NT) dst[e] = __ldcg(src + e);
-        if (tid >= NT - LWMAX && tid - (NT - LWMAX) < l)
-          s_d[tid - (NT - LWMAX)] = ldcg_cx(diag + ((int64_t)buf * nmat + z) * LWMAX + tid - (NT - LWMAX));
-      }
-      __syncthreads();
-      if (warp == 0) {  // the winner among the matrix's CTAs (the same in all of them)
+        if (lane == 0) {  // the whole record from one thread, its head last (release)
+          for (int t = 0; t < l; ++t) cd->v[t] = bi < r_hi ? S[t * ch + bi - r_lo] : Cx<float>{0.f, 0.f};
+          if (c >= r_lo && c < r_hi)
+            for (int t = 0; t < l; ++t) cd->d[t] = S[t * ch + c - r_lo];
+          const unsigned long long head = ((unsigned long long)__float_as_uint(best) << 32) |
+                                          ((unsigned long long)(unsigned)bi << 8) | tag;
+          asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(&cd->head), "l"(head) : "memory");
+        }
+        // wait for every record of this column (bounded; the abort flag, read every 32 polls,
+        // ends it too); the heads carry the candidates
+        const coop::Cand* cb = cand + (int64_t)buf * gridDim.x + (int64_t)z * cpm;
+        bool ok = false;
         float b2 = -1.f;
         int i2 = n, w2 = 0;
-        for (int q = lane; q < cpm; q += 32) {
-          const float bq = sc[q].best;
-          const int iq = sc[q].idx;
-          if (bq > b2 || (bq == b2 && iq < i2)) { b2 = bq; i2 = iq; w2 = q; }
+        for (uint32_t it = 0; it < coop::SPIN; ++it) {
+          bool mine = true;
+          float bl = -1.f;
+          int il = n, wl = 0;
+          for (int q = lane; q < cpm; q += 32) {
+            const unsigned long long h = ld_acquire_gpu64(&cb[q].head);
+            if ((unsigned)(h & 0xffu) != tag) { mine = false; break; }
+            const float bq = __uint_as_float((unsigned)(h >> 32));
+            const int iq = (int)((h >> 8) & 0xffffffu);
+            if (bq > bl || (bq == bl && iq < il)) { bl = bq; il = iq; wl = q; }
+          }
+          if (__all_sync(0xffffffffu, mine)) {
+            ok = true;
+            b2 = bl;
+            i2 = il;
+            w2 = wl;
+            break;
+          }
+          if ((it & 31) == 31 && ld_acquire_gpu(abort_flag)) break;
+          if (it > 16) __nanosleep(32);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, b2, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
-          const int ow = __shfl_xor_sync(0xffffffffu, w2, o);
-          if (ob > b2 || (ob == b2 && oi < i2)) { b2 = ob; i2 = oi; w2 = ow; }
-        }
-        if (i2 >= n) i2 = c;
-        if (lane == 0) {
-          s_p = i2;
-          s_piv[cc] = i2;
-          if (j == 0) {
-            piv[(int64_t)z * n + c] = i2;
-            if (!(b2 > 0) && info) atomicOr(info + z, 1);
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(err, 8);
+            atomicExch(abort_flag, 1u);
+            s_abort = 1;
+          }
+        } else {
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, b2, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
+            const int ow = __shfl_xor_sync(0xffffffffu, w2, o);
+            if (ob > b2 || (ob == b2 && oi < i2)) { b2 = ob; i2 = oi; w2 = ow; }
+          }
+          if (i2 >= n) i2 = c;
+          if (lane == 0) {
+            s_p = i2;
+            s_piv[cc] = i2;
+            if (j == 0) {
+              piv[(int64_t)z * n + c] = i2;
+              if (!(b2 > 0) && info) atomicOr(info + z, 1);
+            }
+          }
+          if (lane < l) {
+            s_u[lane] = ldcg_cx(&cb[w2].v[lane]);
+            s_d[lane] = ldcg_cx(&cb[0].d[lane]);
           }
         }
-        if (lane < l) s_u[lane] = sc[w2].v[lane];
       }
       __syncthreads();
+      if (s_abort) return;
       const int p = s_p;
       // rows c and p exchange (row c takes the pivot row; the thread of row p, below, restores
       // the former row c into it); rows below c are scaled and updated, and each thread keeps its
@@ -494,14 +532,14 @@ __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
       if (p != c && tid < l && c >= r_lo && c < r_hi) S[tid * ch + c - r_lo] = s_u[tid];
       const Cx<float> d = s_u[cc];
       const float dd = d.re * d.re + d.im * d.im;
-      const bool ok = dd > 0.f;
+      const bool okd = dd > 0.f;
       best = -1.f;
       bi = n;
       for (int r = max(a, c + 1) + tid; r < r_hi; r += NT) {
         if (r == p)
           for (int t = 0; t < l; ++t) S[t * ch + r - r_lo] = s_d[t];
         Cx<float> lv = S[cc * ch + r - r_lo];
-        if (ok) lv = cx_div(lv, d);
+        if (okd) lv = cx_div(lv, d);
         S[cc * ch + r - r_lo] = lv;
         for (int t = cc + 1; t < l; ++t) {
           const Cx<float> u = s_u[t];
@@ -514,8 +552,9 @@ __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
           }
         }
       }
-      __syncthreads();
+      // (the next column's first __syncthreads orders these updates before any read of them)
     }
+    __syncthreads();
     for (int e = tid; e < nr * l; e += NT) {
       const int rr = e / l, t = e - rr * l;
       M[(int64_t)(a + rr) * ld + c0 + t] = S[t * ch + a - r_lo + rr];
@@ -885,9 +924,7 @@ static int panel_coop32(bie_ctx* c, Cx<float>* A, int batch, int n, int ld, int6
   BIE_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)k_panel_coop));
   const size_t limit = (size_t)smem_optin() - fa.sharedSizeBytes;
   int lw = coop::LWMAX;
-  auto smem_of = [&](int l) {
-    return ((size_t)l * ch + (size_t)coop::LWMAX * coop::WMAX) * sizeof(Cx<float>) + (size_t)cpm * sizeof(coop::Cand);
-  };
+  auto smem_of = [&](int l) { return ((size_t)l * ch + (size_t)coop::LWMAX * coop::WMAX) * sizeof(Cx<float>); };
   while (lw >= 4 && smem_of(lw) > limit) lw >>= 1;
   if (lw < 4) return BIE_OK;
   lw = std::min(lw, w);
@@ -898,9 +935,9 @@ static int panel_coop32(bie_ctx* c, Cx<float>* A, int batch, int n, int ld, int6
   char* base = (char*)coop + 256;
   unsigned* bar = (unsigned*)base;  // [batch] counters, then the abort flag
   unsigned* abort_flag = bar + batch;
-  coop::Cand* cand = (coop::Cand*)(base + (((size_t)(batch + 1) * 4 + 255) & ~(size_t)255));
-  Cx<float>* diag = (Cx<float>*)(cand + 2 * (size_t)batch * cpm);
-  BIE_CUDA_TRY(cudaMemsetAsync(bar, 0, (size_t)(batch + 1) * 4, c->stream));
+  const size_t cand_off = ((size_t)(batch + 1) * 4 + 255) & ~(size_t)255;
+  coop::Cand* cand = (coop::Cand*)(base + cand_off);
+  BIE_CUDA_TRY(cudaMemsetAsync(bar, 0, cand_off + 2 * (size_t)batch * cpm * sizeof(coop::Cand), c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(batch * cpm));
   cfg.blockDim = dim3(coop::NT);
@@ -913,7 +950,7 @@ static int panel_coop32(bie_ctx* c, Cx<float>* A, int batch, int n, int ld, int6
   cfg.numAttrs = 1;
   count_launch();
   BIE_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_coop, A, bstride, n, ld, p0, w, lw, cpm, ch, piv, info, bar,
-                                  abort_flag, cand, diag, err));
+                                  abort_flag, cand, err));
   *used = true;
   return BIE_OK;
 }

@@ -348,6 +348,29 @@ struct Region {
   int r0, r1, c0, c1, kc0, nchk, ub_c0, ntm, ntn;
 };
 
+// Tile order: per matrix, bands of kBand column tiles, row tiles in order within a band, columns
+// innermost.  The CTAs in flight then share a few bands' U operand and a few row tiles' L operand
+// (at N = 8004, K = 512 the row-major order kept every column tile's U in flight, 62 MB per
+// matrix, which the A22 traffic evicted from L2: 1.5 GB of operand re-reads from DRAM per launch).
+constexpr int kBand = 8;
+__device__ __forceinline__ void tile_coords(int tile, int ntm, int ntn, int& z, int& tm, int& tn) {
+  const int per = ntm * ntn;
+  z = tile / per;
+  const int r = tile - z * per;
+  const int full = ntn / kBand;  // bands of kBand columns; the last band may be narrower
+  const int g = r / (ntm * kBand);
+  if (g < full) {
+    const int w = r - g * ntm * kBand;
+    tm = w / kBand;
+    tn = g * kBand + (w - tm * kBand);
+  } else {
+    const int gw = ntn - full * kBand;
+    const int w = r - full * ntm * kBand;
+    tm = w / gw;
+    tn = full * kBand + (w - tm * gw);
+  }
+}
+
 template <int BNR>
 __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, int batch,
@@ -390,7 +413,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
       uint32_t it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int z = tile / (ntm * ntn), rr = tile % (ntm * ntn), tm = rr / ntn, tn = rr % ntn;
+        int z, tm, tn;
+        tile_coords(tile, ntm, ntn, z, tm, tn);
         for (int ch = 0; ch < nchk && ok; ++ch, ++it) {
           const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
           ok = mbar_wait(baddr(bar.empty[s]), ph ^ 1, err);
@@ -444,7 +468,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_update_tc2(const __grid_constan
     const uint32_t smD = smB + STAGES * B_STAGE;  // 2 x 16 KB, 1024-aligned
     uint32_t ti = 0, nb = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ti) {
-      const int z = tile / (ntm * ntn), rr = tile % (ntm * ntn), tm = rr / ntn, tn = rr % ntn;
+      int z, tm, tn;
+      tile_coords(tile, ntm, ntn, z, tm, tn);
       const uint32_t a = ti & 1, aph = (ti >> 1) & 1;
       // every epilogue warp reaches the named barrier once per tile, then all leave together if
       // any of them gave up waiting (no warp may be left alone at a later barrier)
