@@ -232,6 +232,10 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          CTA, tiles of 32 quadrature points, FP32 run sums; 1 the same with 64
  *                          points per CTA and 64-point tiles; 0 groups of 8, 128 points,
  *                          compensated sums per term
+ *   "asm.windows"          1 (default): at large N, where the mesh's node numbering can be cut
+ *                          into windows of at most 3200 columns that no element straddles (bodies
+ *                          numbered one after the other), the FP32 bulk assembly accumulates each
+ *                          row window by window in shared memory; 0: the rows accumulate in A
  *   "mixed.reassembly_group" flagged wavenumbers re-assembled and refined together (1..32,
  *                          default 32; device memory may lower it)
  *   "mixed.reassembly"     system of the flagged wavenumbers: 1 (default) bulk pairs in float-float

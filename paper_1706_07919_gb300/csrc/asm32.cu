@@ -277,16 +277,22 @@ __global__ void k_known_q32(const int32_t* __restrict__ esort, int64_t E, int Q,
 // a second set of ASM_W warps takes the other half of the same elements' quadrature points, so
 // that the registers of KB = 2 fit 16 warps per SM; the halves add into the row one after the
 // other (barrier of the row's warps in between: fixed order, deterministic sums).
-// grid (ceil(N / rows), ceil(nk / KB)); block 32 * rows * ASM_W * QS; smem rows * KB * N cf, or
-// (GROW, large N) none: the rows then accumulate in A itself, each row owned by one CTA and the
-// row's warps ordered by the same barriers.
-template <int KB, int QS, bool GROW>
+// grid (ceil(N / rows), ceil(nk / KB)); block 32 * rows * ASM_W * QS.  Where a row accumulates:
+//   MODE 0: shared memory, rows * KB * N cf;
+//   MODE 1 (large N): A itself, each row owned by one CTA and the row's warps ordered by the same
+//     barriers (scattered read-modify-writes in L2);
+//   MODE 2 (large N cut into column windows, see build_colouring): shared memory, rows * KB * ws
+//     cf, one window of columns after the other -- the window's elements of every colour, then the
+//     window copied to A -- so that each entry of A is written once.
+template <int KB, int QS, int MODE>
 __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
     const double* __restrict__ nodes, const double* __restrict__ normals, const uint8_t* __restrict__ bc,
     const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q, const float4* __restrict__ qaos,
     const float* __restrict__ qshape, const int32_t* __restrict__ color_off, int ncolors,
     const double* __restrict__ kv, int nk, const cf* __restrict__ kq, cf* __restrict__ A, int64_t lda,
-    double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp, float far_r2) {
+    double* __restrict__ rowsum /* [nk][N][6] */, int rows, TwoPi3 tp, float far_r2,
+    const int32_t* __restrict__ win_lo, const int32_t* __restrict__ wcol_off, int nwin, int ws) {
+  constexpr bool GROW = MODE == 1;
   constexpr int WR = ASM_W * QS;  // warps per row
   extern __shared__ cf acc32[];
   __shared__ float shp[64 * 6];
@@ -309,6 +315,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
   // row j of this CTA's row rw: in shared memory, or (GROW) row i of system k0 + j in A
   auto row_of = [&](int j) -> cf* {
     if constexpr (GROW) return A + ((int64_t)(k0 + j) * N + i) * lda;
+    else if constexpr (MODE == 2) return acc32 + ((int64_t)rw * KB + j) * ws;
     else return acc32 + ((int64_t)rw * KB + j) * N;
   };
   if constexpr (GROW) {
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
         cf* r = row_of(j);
         for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) r[c2] = {0.f, 0.f};
       }
-  } else {
+  } else if constexpr (MODE == 0) {
     for (int64_t t = threadIdx.x; t < (int64_t)rows * KB * N; t += blockDim.x) acc32[t] = {0.f, 0.f};
   }
   __syncthreads();
@@ -328,8 +335,27 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
     nui[d] = ff_from_double(valid ? normals[3 * i + d] : 0.0);
   }
   RowSums S[KB];
+  const int nw = MODE == 2 ? nwin : 1;
+  for (int w = 0; w < nw; ++w) {
+  int w0 = 0;
+  if constexpr (MODE == 2) {  // the row's window accumulator starts at zero
+    w0 = win_lo[w];
+    const int ww = win_lo[w + 1] - w0;
+    for (int j = 0; j < KB; ++j) {
+      cf* r = row_of(j);
+      for (int c2 = wr * 32 + lane; c2 < ww; c2 += 32 * WR) r[c2] = {0.f, 0.f};
+    }
+    bar_named(1 + rw, 32 * WR);
+  }
   for (int col = 0; col < ncolors; ++col) {
-    const int32_t cbeg = color_off[col], cend = color_off[col + 1];
+    int32_t cbeg, cend;
+    if constexpr (MODE == 2) {
+      cbeg = wcol_off[col * (nwin + 1) + w];
+      cend = wcol_off[col * (nwin + 1) + w + 1];
+    } else {
+      cbeg = color_off[col];
+      cend = color_off[col + 1];
+    }
     // the same trip count for all warps of the row (the barriers below are the row's)
     const int iters = valid ? (cend - cbeg + 32 * ASM_W - 1) / (32 * ASM_W) : 0;
     for (int it = 0; it < iters; ++it) {
@@ -437,8 +463,8 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
             cf* row = row_of(j);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
-              row[el[a]].re += ar[j][a];
-              row[el[a]].im += ai[j][a];
+              row[el[a] - w0].re += ar[j][a];
+              row[el[a] - w0].im += ai[j][a];
             }
           }
         }
@@ -447,6 +473,18 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
     }
     if (QS == 1) bar_named(1 + rw, 32 * WR);  // the row's warps finish the colour (rows <= 8: ids 1..8)
   }
+  if constexpr (MODE == 2) {  // the window to A, then its accumulator is free for the next one
+    bar_named(1 + rw, 32 * WR);
+    const int ww = win_lo[w + 1] - w0;
+    if (valid)
+      for (int j = 0; j < nkb; ++j) {
+        const cf* r = row_of(j);
+        cf* Arow = A + ((int64_t)(k0 + j) * N + i) * lda + w0;
+        for (int c2 = wr * 32 + lane; c2 < ww; c2 += 32 * WR) Arow[c2] = r[c2];
+      }
+    bar_named(1 + rw, 32 * WR);
+  }
+  }  // windows
   // reduce the compensated sums across the warp in FP64 (6 values per row and wavenumber)
 #pragma unroll
   for (int j = 0; j < KB; ++j) {
@@ -461,7 +499,7 @@ __global__ void __launch_bounds__(256, 2) k_asm32_bulk_u(
   __syncthreads();
   if (!valid) return;
   for (int j = 0; j < nkb; ++j) {
-    if constexpr (!GROW) {
+    if constexpr (MODE == 0) {
       const cf* row = row_of(j);
       cf* Arow = A + ((int64_t)(k0 + j) * N + i) * lda;
       for (int64_t c2 = wr * 32 + lane; c2 < N; c2 += 32 * WR) Arow[c2] = row[c2];
@@ -721,17 +759,29 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
     if (kb == 2) {
       const int urows = 2;
       const bool grow = (size_t)urows * 2 * N * sizeof(cf) > 100 * 1024;
-      const size_t usmem = grow ? 0 : (size_t)urows * 2 * N * sizeof(cf);
+      // large N: window by window in shared memory where the mesh has column windows
+      // ("asm.windows" 0 keeps the rows in A)
+      const bool win = grow && c->nwin > 1 && c->asm_windows != 0 &&
+                       (size_t)urows * 2 * c->win_max * sizeof(cf) <= 100 * 1024;
+      const size_t usmem = win ? (size_t)urows * 2 * c->win_max * sizeof(cf) : grow ? 0 : (size_t)urows * 2 * N * sizeof(cf);
       dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)((nk + 1) / 2));
-      if (grow) {
-        BIE_LAUNCH(k_asm32_bulk_u<2, 2, true><<<gu, 32 * urows * ASM_W * 2, 0, c->stream>>>(
+      if (win) {
+        BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2, 2>)));
+        BIE_LAUNCH(k_asm32_bulk_u<2, 2, 2><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
             c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2, c->win_lo, c->wcol_off, c->nwin,
+            c->win_max));
+      } else if (grow) {
+        BIE_LAUNCH(k_asm32_bulk_u<2, 2, 1><<<gu, 32 * urows * ASM_W * 2, 0, c->stream>>>(
+            c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2, c->win_lo, c->wcol_off, c->nwin,
+            c->win_max));
       } else {
-        BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2, false>)));
-        BIE_LAUNCH(k_asm32_bulk_u<2, 2, false><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
+        BIE_TRY((set_smem_max(k_asm32_bulk_u<2, 2, 0>)));
+        BIE_LAUNCH(k_asm32_bulk_u<2, 2, 0><<<gu, 32 * urows * ASM_W * 2, usmem, c->stream>>>(
             c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2, c->win_lo, c->wcol_off, c->nwin,
+            c->win_max));
       }
     } else {
       int urows = 4;
@@ -741,14 +791,16 @@ int assemble32(bie_ctx* c, const double* kv, int nk, cf* A, int64_t lda, cd* b, 
       const size_t usmem = grow ? 0 : (size_t)urows * N * sizeof(cf);
       dim3 gu((unsigned)((N + urows - 1) / urows), (unsigned)nk);
       if (grow) {
-        BIE_LAUNCH(k_asm32_bulk_u<1, 1, true><<<gu, 32 * urows * ASM_W, 0, c->stream>>>(
+        BIE_LAUNCH(k_asm32_bulk_u<1, 1, 1><<<gu, 32 * urows * ASM_W, 0, c->stream>>>(
             c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2, c->win_lo, c->wcol_off, c->nwin,
+            c->win_max));
       } else {
-        BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1, false>)));
-        BIE_LAUNCH(k_asm32_bulk_u<1, 1, false><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
+        BIE_TRY((set_smem_max(k_asm32_bulk_u<1, 1, 0>)));
+        BIE_LAUNCH(k_asm32_bulk_u<1, 1, 0><<<gu, 32 * urows * ASM_W, usmem, c->stream>>>(
             c->nodes, c->normals, c->bc, sorted_elems(c), N, E, c->rule.Q, sorted_aos(c), c->qshape32, c->color_off,
-            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2));
+            c->ncolors, kv, nk, kq, A, lda, rowsum, urows, tp, (float)c->far_r2, c->win_lo, c->wcol_off, c->nwin,
+            c->win_max));
       }
     }
   }

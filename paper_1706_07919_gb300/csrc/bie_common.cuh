@@ -116,7 +116,13 @@ struct bie_ctx {
   int ncolors = 0;
   std::vector<int32_t> h_color_off;  // [ncolors+1]
   int32_t* color_off = nullptr;
-  int32_t* elem_perm = nullptr;      // [E] elements ordered by colour
+  int32_t* elem_perm = nullptr;      // [E] elements ordered by colour, then by column window
+  // column windows: node ranges [win_lo[w], win_lo[w + 1]) of at most kWinMax nodes that no element
+  // straddles (0: no such partition; 1: one window, all of [0, N)); within colour col the
+  // elements of window w are [wcol_off[col (nwin + 1) + w], wcol_off[col (nwin + 1) + w + 1])
+  int nwin = 0, win_max = 0;
+  int32_t* win_lo = nullptr;         // [nwin + 1]
+  int32_t* wcol_off = nullptr;       // [ncolors][nwin + 1]
   int32_t* n2e_off = nullptr;        // [N+1] CSR: elements containing node i
   int32_t* n2e = nullptr;            // element * 8 + local index
   int max_n2e = 0;
@@ -148,6 +154,7 @@ struct bie_ctx {
   int uniform_bc = -1;               // every element has one condition on all nodes (1), not (0), unknown
   int asm_kb = 2;                    // FP32 bulk assembly: wavenumbers per thread (1, 2), 0 = the
                                      // general kernel (also taken when an element mixes conditions)
+  int asm_windows = 1;               // FP32 bulk assembly at large N: column windows in shared memory (1) or rows in A (0)
   int reassembly_group = 32;         // FP64 re-assembly slots refined together (1..32; memory may lower it)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph

@@ -144,13 +144,14 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
 static void free_geometry(bie_ctx* c) {
   void* ptrs[] = {c->nodes, c->elems, c->normals, c->bc, c->qgeo, c->ngeo, c->qshape, c->nshape, c->qgeo32,
                   c->qshape32, c->nshape32, c->color_off, c->elem_perm, c->n2e_off, c->n2e, c->d_nnear, c->bc_flip,
-                  c->lin_adj_off, c->lin_adj, c->lin_mid};
+                  c->lin_adj_off, c->lin_adj, c->lin_mid, c->win_lo, c->wcol_off};
   for (void* p : ptrs) dev_free(c, p);
   c->nodes = nullptr; c->elems = nullptr; c->normals = nullptr; c->bc = nullptr;
   c->qgeo = nullptr; c->ngeo = nullptr; c->qshape = nullptr; c->nshape = nullptr;
   c->qgeo32 = nullptr; c->qshape32 = nullptr; c->nshape32 = nullptr; c->color_off = nullptr; c->elem_perm = nullptr;
   c->n2e_off = nullptr; c->n2e = nullptr; c->d_nnear = nullptr; c->bc_flip = nullptr;
   c->lin_adj_off = nullptr; c->lin_adj = nullptr; c->lin_mid = nullptr; c->lin_N = 0;
+  c->win_lo = nullptr; c->wcol_off = nullptr; c->nwin = 0; c->win_max = 0;
   c->far_r2 = 0.0;
   c->uniform_bc = -1;
   c->has_geom = false;
@@ -391,6 +392,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
     if (value != 0.0 && value != 128.0 && value != 256.0 && value != 512.0)
       return fail(BIE_ERR_INVALID_ARG, "mixed.lu_block must be 0 (by N), 128, 256 or 512");
     c->lu_block = (int)value;
+  } else if (n == "asm.windows") {
+    c->asm_windows = value != 0.0 ? 1 : 0;
   } else if (n == "mixed.reassembly_group") {
     if (value < 1 || value > 32) return fail(BIE_ERR_INVALID_ARG, "mixed.reassembly_group must be in [1, 32]");
     c->reassembly_group = (int)value;

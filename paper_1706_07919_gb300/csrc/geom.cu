@@ -224,44 +224,127 @@ int upload_geometry_tables(bie_ctx* c) {
 // one element shares a node with) in conflict, a colour is always free once C > E / cap + D, so
 // the retry loop (C + 1 after a failure) ends.
 constexpr int kColourCap = 64;
+constexpr int64_t kWinMax = 3200;  // nodes of a column window: 2 rows x 2 wavenumbers x 3200 x 8 B = 100 KB
 int build_colouring(bie_ctx* c) {
   const int64_t N = c->N, E = c->E;
   std::vector<std::vector<int32_t>> n2e(N);
   for (int64_t e = 0; e < E; ++e)
     for (int a = 0; a < 6; ++a) n2e[c->h_elems[6 * e + a]].push_back((int32_t)(e * 8 + a));
-  std::vector<int> colour(E, -1);
-  int ncol = (int)std::max<int64_t>(1, (E + kColourCap - 1) / kColourCap);
-  std::vector<int> fill_count, used;
-  for (;;) {
-    std::fill(colour.begin(), colour.end(), -1);
-    fill_count.assign(ncol, 0);
-    used.assign(ncol, -1);
-    bool ok = true;
-    for (int64_t e = 0; e < E && ok; ++e) {
-      for (int a = 0; a < 6; ++a)
-        for (int32_t ea : n2e[c->h_elems[6 * e + a]]) {
-          const int cc = colour[ea / 8];
-          if (cc >= 0) used[cc] = (int)e;
-        }
-      int best = -1;
-      for (int cc = 0; cc < ncol; ++cc)
-        if (used[cc] != (int)e && fill_count[cc] < kColourCap && (best < 0 || fill_count[cc] < fill_count[best]))
-          best = cc;
-      if (best < 0) {
-        ok = false;
-        break;
+  // Column windows: cut the node range where no element straddles the cut (every element's nodes
+  // on one side), greedily into windows of at most kWinMax nodes, so that a bulk kernel can
+  // accumulate a row window by window in shared memory (separate bodies numbered one after the
+  // other give such cuts between bodies).
+  std::vector<int32_t> ewin(E, 0), win_lo(1, 0);
+  {
+    std::vector<int32_t> span(N + 2, 0);
+    for (int64_t e = 0; e < E; ++e) {
+      int32_t mn = c->h_elems[6 * e], mx = mn;
+      for (int a = 1; a < 6; ++a) {
+        mn = std::min(mn, c->h_elems[6 * e + a]);
+        mx = std::max(mx, c->h_elems[6 * e + a]);
       }
-      colour[e] = best;
-      ++fill_count[best];
+      span[mn + 1] += 1;  // cuts x with mn < x <= mx are straddled
+      span[mx + 1] -= 1;
     }
-    if (ok) break;
-    ++ncol;
+    std::vector<int64_t> cuts;  // valid cuts in increasing order, N last
+    int64_t run = 0;
+    for (int64_t x = 1; x < N; ++x) {
+      run += span[x];
+      if (run == 0) cuts.push_back(x);
+    }
+    cuts.push_back(N);
+    bool ok = true;
+    int64_t lo = 0;
+    size_t ci = 0;
+    while (lo < N && ok) {
+      int64_t hi = -1;
+      while (ci < cuts.size() && cuts[ci] - lo <= kWinMax) hi = cuts[ci++];
+      if (hi <= lo) ok = false;
+      else {
+        win_lo.push_back((int32_t)hi);
+        lo = hi;
+      }
+    }
+    if (ok) {
+      for (int64_t e = 0; e < E; ++e) {
+        const int32_t n0 = c->h_elems[6 * e];
+        ewin[e] = (int32_t)(std::upper_bound(win_lo.begin(), win_lo.end(), n0) - win_lo.begin()) - 1;
+      }
+      c->nwin = (int)win_lo.size() - 1;
+      c->win_max = 0;
+      for (int w = 0; w < c->nwin; ++w) c->win_max = std::max(c->win_max, win_lo[w + 1] - win_lo[w]);
+    } else {
+      c->nwin = 0;
+      c->win_max = 0;
+      win_lo.assign(1, 0);
+    }
   }
-  std::vector<int32_t> off(ncol + 1, 0), perm(E);
-  for (int64_t e = 0; e < E; ++e) off[colour[e] + 1]++;
-  for (int i = 0; i < ncol; ++i) off[i + 1] += off[i];
-  std::vector<int32_t> fill(off.begin(), off.end() - 1);
-  for (int64_t e = 0; e < E; ++e) perm[fill[colour[e]]++] = (int32_t)e;
+  // The colouring runs window by window (one window: the whole mesh): elements of different
+  // windows share no node, so colour cc of the mesh is the union of the windows' colours cc and a
+  // window-by-window kernel still finds full colours of up to kColourCap elements in each window.
+  std::vector<int> colour(E, -1);
+  int ncol = 1;
+  {
+    const int nwc = std::max(1, c->nwin);
+    std::vector<std::vector<int32_t>> wel(nwc);
+    for (int64_t e = 0; e < E; ++e) wel[ewin[e]].push_back((int32_t)e);
+    std::vector<int> fill_count, used;
+    for (int w = 0; w < nwc; ++w) {
+      const std::vector<int32_t>& els = wel[w];
+      const int64_t Ew = (int64_t)els.size();
+      int nc = (int)std::max<int64_t>(1, (Ew + kColourCap - 1) / kColourCap);
+      for (;;) {
+        for (int32_t e : els) colour[e] = -1;
+        fill_count.assign(nc, 0);
+        used.assign(nc, -1);
+        bool ok = true;
+        for (int64_t t = 0; t < Ew && ok; ++t) {
+          const int32_t e = els[t];
+          for (int a = 0; a < 6; ++a)
+            for (int32_t ea : n2e[c->h_elems[6 * e + a]]) {
+              const int cc = colour[ea / 8];
+              if (cc >= 0) used[cc] = (int)e;
+            }
+          int best = -1;
+          for (int cc = 0; cc < nc; ++cc)
+            if (used[cc] != (int)e && fill_count[cc] < kColourCap && (best < 0 || fill_count[cc] < fill_count[best]))
+              best = cc;
+          if (best < 0) {
+            ok = false;
+            break;
+          }
+          colour[e] = best;
+          ++fill_count[best];
+        }
+        if (ok) break;
+        ++nc;
+      }
+      ncol = std::max(ncol, nc);
+    }
+  }
+  const int nw = std::max(1, c->nwin);
+  // elements ordered by colour, within a colour by window
+  std::vector<int32_t> woff((size_t)ncol * (nw + 1), 0), perm(E);
+  for (int64_t e = 0; e < E; ++e) woff[(size_t)colour[e] * (nw + 1) + ewin[e] + 1]++;
+  std::vector<int32_t> off(ncol + 1, 0);
+  {
+    int32_t acc = 0;
+    for (int cc = 0; cc < ncol; ++cc) {
+      off[cc] = acc;
+      woff[(size_t)cc * (nw + 1)] = acc;
+      for (int w = 0; w < nw; ++w) {
+        acc += woff[(size_t)cc * (nw + 1) + w + 1];
+        woff[(size_t)cc * (nw + 1) + w + 1] = acc;
+      }
+    }
+    off[ncol] = acc;
+  }
+  {
+    std::vector<int32_t> fill((size_t)ncol * nw);
+    for (int cc = 0; cc < ncol; ++cc)
+      for (int w = 0; w < nw; ++w) fill[(size_t)cc * nw + w] = woff[(size_t)cc * (nw + 1) + w];
+    for (int64_t e = 0; e < E; ++e) perm[fill[(size_t)colour[e] * nw + ewin[e]]++] = (int32_t)e;
+  }
   c->ncolors = ncol;
   c->h_color_off = off;
   std::vector<int32_t> csr_off(N + 1, 0), csr;
@@ -273,6 +356,11 @@ int build_colouring(bie_ctx* c) {
   }
   c->max_n2e = mx;
   BIE_TRY(dev_alloc(c, (void**)&c->color_off, off.size() * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->win_lo, win_lo.size() * sizeof(int32_t)));
+  BIE_TRY(dev_alloc(c, (void**)&c->wcol_off, woff.size() * sizeof(int32_t)));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->win_lo, win_lo.data(), win_lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(cudaMemcpyAsync(c->wcol_off, woff.data(), woff.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               c->stream));
   BIE_TRY(dev_alloc(c, (void**)&c->elem_perm, perm.size() * sizeof(int32_t)));
   BIE_TRY(dev_alloc(c, (void**)&c->n2e_off, csr_off.size() * sizeof(int32_t)));
   BIE_TRY(dev_alloc(c, (void**)&c->n2e, std::max<size_t>(1, csr.size()) * sizeof(int32_t)));
