@@ -755,7 +755,10 @@ def run_case(args):
     runs the learned sweep on 128 spheroid wavenumbers (k = 5.02 .. 7.5, 20 training epochs);
     `field512` evaluates the field of all 512 wavenumbers at all 16 384 points from a constant
     surface solution (the shape of the benchmark's field launch, without its solves);
-    `step` runs one benchmark step once (cold: the geometry tables are built inside it)."""
+    `step` runs one benchmark step once (cold: the geometry tables are built inside it); `lattice`
+    solves one batch of the lattice (k = 0 and 8 wavenumbers, N = 20 544) with phase timing;
+    `lu_n8004` solves two wavenumbers on two spheres of 4002 nodes (N = 8004, deferred block 512,
+    cooperative panels; a few GB on the device)."""
     import torch
 
     import __graft_entry__
@@ -817,6 +820,34 @@ def run_case(args):
         sol.set_option("mixed.batch", 16)
         surf, rep = sol.solve_frequencies(w.k[100:116], B.BIE_MODE_MIXED)
         print("case lu16: refinement corrections", [r.iters for r in rep])
+    elif args.case == "lattice":  # one lattice batch: k = 0 and 8 wavenumbers, N = 20 544, phase timing
+        from workloads import config_lattice_large
+        wl = config_lattice_large()
+        ks = np.concatenate([[0.0], wl.k[np.linspace(0, len(wl.k) - 1, 8).round().astype(np.int64)]])
+        s2 = Solver(0)
+        s2.set_geometry(wl.mesh.nodes, wl.mesh.elems, wl.mesh.normals, wl.mesh.bc)
+        s2.set_incident_plane_wave(wl.direction)
+        s2.set_option("mixed.phase_timing", 1)
+        surf, rep = s2.solve_frequencies(ks, B.BIE_MODE_MIXED)
+        ph = B.bie_get_phase_times(s2.ctx)
+        ph["lu_tflops"] = ph["systems"] * (8.0 / 3.0) * float(wl.mesh.N) ** 3 / (ph["factor_ms"] * 1e-3) / 1e12
+        print("case lattice:", json.dumps(ph), "max backward error", max(r.backward_err for r in rep))
+        s2.close()
+    elif args.case == "lu_n8004":  # two spheres of 4002 nodes, 2 wavenumbers, deferred block 512 (a few GB)
+        from workloads import ico_sphere, merge_meshes, scale_translate
+        s0 = ico_sphere(10)
+        m = merge_meshes([scale_translate(s0, 1.0, (0, 0, -1.05)), scale_translate(s0, 1.0, (0, 0, 1.05))])
+        s2 = Solver(0)
+        s2.set_geometry(m.nodes, m.elems, m.normals, m.bc)
+        s2.set_option("mixed.batch", 2)
+        s2.set_option("mixed.lu_block", 512)
+        s2.set_option("mixed.reassembly_group", 1)
+        s2.set_option("mixed.fallback_err_est", 1.0)
+        s2.set_option("mixed.phase_timing", 1)
+        surf, rep = s2.solve_frequencies(np.array([3.3, 7.7]), B.BIE_MODE_MIXED)
+        ph = B.bie_get_phase_times(s2.ctx)
+        print("case lu_n8004: factor_ms", ph["factor_ms"], "refinement corrections", [r.iters for r in rep])
+        s2.close()
     elif args.case == "field512":
         ks = w.k
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -876,8 +907,8 @@ def main():
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
     ap.add_argument("--uneven-workers", dest="uneven_workers", type=int, default=4)
-    ap.add_argument("--case", choices=["lu", "lu16", "field", "field512", "field_sample", "batch", "learned", "step", "peaks", "phases",
-                                       "uneven_full"],
+    ap.add_argument("--case", choices=["lu", "lu16", "lu_n8004", "lattice", "field", "field512", "field_sample", "batch",
+                                       "learned", "step", "peaks", "phases", "uneven_full"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
