@@ -103,8 +103,9 @@ def test_async_returns_before_the_work_and_overlaps(Solver, B, two_spheres):
         s.set_option("mixed.batch", 8)
     warm = [s.solve_frequencies_async(ks) for s in sols]  # first calls: geometry tables, workspace
     torch.cuda.synchronize()
-    # the call returns while its work is still queued
-    surf, pending = sols[0].solve_frequencies_async(ks)
+    # the call returns while its work is still queued (32 wavenumbers: four batches of GPU work,
+    # far longer than enqueuing them)
+    surf, pending = sols[0].solve_frequencies_async(np.linspace(1.0, 10.0, 32))
     pending_at_return = not pending.done()
     rep = pending.reports()
     assert pending_at_return
