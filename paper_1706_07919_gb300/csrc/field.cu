@@ -667,32 +667,53 @@ int field_mixed(bie_ctx* c, const double* kv, int nk, const cd* surf, const doub
     dim3 gf((unsigned)((M + FT - 1) / FT), nk);
     if (c->field_accurate_phase) {
       const int v = c->field_variant;
-      const int KBv = (v >= 1) ? 16 : FKB;
       std::vector<double> hk(nk);
       BIE_CUDA_TRY(cudaMemcpyAsync(hk.data(), kv, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-      // k = 0 (the zero-frequency term) takes f's limit inside the kernel; launches without it
-      // keep that select out of the inner loop
-      bool zero = false;
-      for (int j = 0; j < nk; ++j) zero |= hk[j] == 0.0;
+      // Segments of the wavenumber list, one launch each: maximal runs of equally spaced
+      // wavenumbers (at least 4) take the phase recurrence inside their groups of KB, the rest
+      // runs without it -- so that a sweep with the zero-frequency term in front (or any
+      // uniform runs inside a list) keeps the recurrence where it applies.
+      std::vector<std::pair<int, int>> segs;  // (start, length); a negative length: no recurrence
       {
-        const int r0 = 0, n = nk;
-        // uniform spacing inside every group of KB wavenumbers enables the phase recurrence
-        int uniform = n > 1 ? 1 : 0;
-        const double dkv = n > 1 ? hk[r0 + 1] - hk[r0] : 0.0;
-        for (int j = 0; j < n && uniform; ++j) {
-          const double expect = hk[r0 + (j / KBv) * KBv] + (j % KBv) * dkv;
-          if (std::fabs(hk[r0 + j] - expect) > 1e-12 * std::fabs(hk[r0 + j]) || !(dkv > 0.0)) uniform = 0;
+        int i = 0, nu_start = -1;
+        while (i < nk) {
+          int L = 1;
+          if (i + 1 < nk) {
+            const double d = hk[i + 1] - hk[i];
+            L = 2;
+            if (!(d > 0.0)) L = 1;
+            else
+              while (i + L < nk && std::fabs(hk[i + L] - (hk[i] + L * d)) <= 1e-12 * std::fabs(hk[i + L])) ++L;
+          }
+          if (L >= 4) {
+            if (nu_start >= 0) { segs.push_back({nu_start, -(i - nu_start)}); nu_start = -1; }
+            segs.push_back({i, L});
+            i += L;
+          } else {
+            if (nu_start < 0) nu_start = i;
+            ++i;
+          }
         }
+        if (nu_start >= 0) segs.push_back({nu_start, -(nk - nu_start)});
+      }
+      for (const auto& sg : segs) {
+        const int r0 = sg.first, n = sg.second > 0 ? sg.second : -sg.second;
+        const int uniform = sg.second > 0 ? 1 : 0;
+        const double dkv = uniform ? hk[r0 + 1] - hk[r0] : 0.0;
+        // k = 0 (the zero-frequency term) takes f's limit inside the kernel; launches without it
+        // keep that select out of the inner loop
+        bool zero_s = false;
+        for (int j = 0; j < n; ++j) zero_s |= hk[r0 + j] == 0.0;
         const ff dkf = ff_from_double(dkv);
         const double* kr = kv + r0;
         const cf *Pqr = Pq + (int64_t)r0 * EQ, *Pnqr = Pnq + (int64_t)r0 * EQ;
         const cd* sr = surf + (int64_t)r0 * 2 * c->N;
         cd* Tr = T + (int64_t)r0 * M;
         if (v == 1) {
-          launch_field32c<16, 64, 4, 64>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero);
+          launch_field32c<16, 64, 4, 64>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero_s);
         } else if (v == 2) {
-          launch_field32c<16, 128, 3, 32>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero);
+          launch_field32c<16, 128, 3, 32>(c, EQ, Pqr, Pnqr, sr, xp, M, foot_elem, foot, kr, n, Tr, tp, uniform, dkf, zero_s);
         } else {
           dim3 gb((unsigned)((M + FT - 1) / FT), (unsigned)((n + FKB - 1) / FKB));
           BIE_LAUNCH(k_field32b<<<gb, FT, 0, c->stream>>>(c->elems, c->N, EQ, c->qgeo32, Pqr, Pnqr, sr, xp, M, foot_elem,

@@ -116,6 +116,30 @@ def test_zero_frequency_uniform_field_group(Solver, B):
             assert rel(T[i], Tr) <= 1e-6, (variant, ks[i])
 
 
+def test_field_segments_zero_term_and_uniform_run(Solver, B):
+    """k = 0 in front of a uniform run, a non-uniform stretch and another uniform run (the field
+    launch is cut into segments: runs of at least 4 equally spaced wavenumbers keep the phase
+    recurrence): one call gives the same mixed fields as the segments called one by one, and the
+    oracle's fields."""
+    m = octa_sphere(2, bc=1)
+    ks = np.concatenate([[0.0], 0.5 + 0.125 * np.arange(19), [3.3, 4.1], 5.0 + 0.2 * np.arange(6)])
+    pts = shell_points(32, 1.2, 3.0, seed=13)
+    s = _solver(Solver, m)
+    xo = torch.tensor(pts, dtype=torch.float64, device="cuda:0")
+    surf, _ = s.solve_frequencies(ks, B.BIE_MODE_FP64)
+    sc = surf.cpu().numpy()
+    for variant in (0, 2):
+        s.set_option("field.variant", variant)
+        T = s.eval_field(xo, ks, surf, B.BIE_MODE_MIXED).cpu().numpy()
+        parts = [s.eval_field(xo, ks[a:b], surf[a:b], B.BIE_MODE_MIXED).cpu().numpy()
+                 for a, b in ((0, 1), (1, 20), (20, 22), (22, 28))]
+        assert np.array_equal(T, np.concatenate(parts)), variant
+        for i in (0, 1, 16, 19, 20, 21, 22, 27):
+            Tr = oracle.field(m, ks[i], sc[i, 0], sc[i, 1], pts)
+            assert rel(T[i], Tr) <= 1e-6, (variant, ks[i], rel(T[i], Tr))
+    s.close()
+
+
 def test_soft_body_space_time_field_includes_zero_frequency(Solver, B):
     """A Gaussian pulse has a non-zero mean; for a soft sphere T(x, 0) = -a/r is not zero, so the
     synthesis over m = 0..Nt/2 must include the k = 0 solve.  FP64 path against the oracle's
