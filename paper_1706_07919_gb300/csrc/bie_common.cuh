@@ -167,6 +167,7 @@ struct bie_ctx {
   size_t pinned_bytes = 0;
   void* rep_pinned = nullptr;        // pinned staging of the stream-ordered solves' reports
   size_t rep_pinned_bytes = 0;
+  std::vector<void*> rep_pinned_old; // outgrown report staging (an earlier call may still use it)
 
   // learned warm start + Krylov path (BIE_MODE_LEARNED)
   int learned_stride = 8;            // every stride-th wavenumber is solved directly (an anchor)

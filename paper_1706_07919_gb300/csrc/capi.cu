@@ -365,6 +365,7 @@ int bie_destroy(bie_ctx* c) {
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->rep_pinned) cudaFreeHost(c->rep_pinned);
+  for (void* q : c->rep_pinned_old) cudaFreeHost(q);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return BIE_OK;

@@ -730,9 +730,23 @@ __global__ void __launch_bounds__(128) k_swap_trsm(Cx<S>* __restrict__ A, int64_
 // the block (unrolled).  Each x_s receives its updates in increasing t, the order of the row-by-row
 // substitution of k_swap_trsm.  (A fully unrolled 64-entry register version ran from the
 // instruction cache's misses.)
+// With bt.ub set, each solved column also goes, rounded to TF32, into the B^T buffer of the
+// tensor-core update (the real embedding: B^T rows 2 (j - bt.cb) and 2 (j - bt.cb) + 1 get, at
+// floats bt.koff + 2 s, [ur, -ui] and [ui, ur]; rows bt.krow floats long, bt.stride per matrix),
+// which saves the separate build pass over U.
+struct BtOut {
+  float* ub;
+  int64_t stride;
+  int krow, koff, cb;
+};
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 constexpr size_t kTrsmSmem = 2 * 64 * 64 * sizeof(Cx<float>);  // L11^T and the solved columns
 __global__ void __launch_bounds__(64) k_trsm64(Cx<float>* __restrict__ A, int64_t bstride, int n, int ld, int p0,
-                                               int j0, int j1) {
+                                               int j0, int j1, BtOut bt) {
   extern __shared__ float4 trsm_smem[];
   Cx<float>* LT = reinterpret_cast<Cx<float>*>(trsm_smem);  // LT[t * 64 + s] = L11[s][t]
   Cx<float>(*X)[64] = reinterpret_cast<Cx<float>(*)[64]>(LT + 64 * 64);  // X[s][thread]: the solved column
@@ -778,6 +792,16 @@ __global__ void __launch_bounds__(64) k_trsm64(Cx<float>* __restrict__ A, int64_
     for (int r = 0; r < 16; ++r) {
       X[b0 + r][tid] = xb[r];
       if (act && (b0 + r) > 0) M[(int64_t)(p0 + b0 + r) * ld + j] = xb[r];
+    }
+  }
+  if (bt.ub && act) {  // this thread's column is complete in X
+    float* o = bt.ub + (int64_t)blockIdx.y * bt.stride + (int64_t)2 * (j - bt.cb) * bt.krow + bt.koff;
+#pragma unroll 4
+    for (int s2 = 0; s2 < 64; s2 += 2) {
+      const Cx<float> u0 = X[s2][tid], u1 = X[s2 + 1][tid];
+      const float a0 = round_tf32(u0.re), b0 = round_tf32(u0.im), a1 = round_tf32(u1.re), b1 = round_tf32(u1.im);
+      *reinterpret_cast<float4*>(o + 2 * s2) = make_float4(a0, -b0, a1, -b1);
+      *reinterpret_cast<float4*>(o + bt.krow + 2 * s2) = make_float4(b0, a0, b1, a1);
     }
   }
 }
@@ -960,7 +984,9 @@ static int panel_coop32(bie_ctx* c, Cx<float>* A, int batch, int n, int ld, int6
 // tensor-core kernels of lu_tc.cu).  coop / err: scratch and error word of the cooperative panel
 // (NULL: one CTA per matrix always).
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info, int tend, void* coop, int32_t* err) {
+                     int32_t* info, int tend, void* coop, int32_t* err, float* ub, int64_t ub_stride, int krow,
+                     int koff, bool* emitted) {
+  if (emitted) *emitted = false;
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   bool used = false;
   BIE_TRY(panel_coop32(c, M, batch, n, ld, bstride, p0, w, piv, info, coop, err, &used));
@@ -971,7 +997,9 @@ int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstrid
     if (tend > p0 + w) {
       BIE_TRY((set_smem_max(k_trsm64)));
       dim3 gt((unsigned)((tend - p0 - w + 63) / 64), batch);
-      BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, p0 + w, tend));
+      const BtOut bt{ub, ub_stride, krow, koff, p0 + w};
+      BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, p0 + w, tend, bt));
+      if (emitted) *emitted = ub != nullptr;
     }
   } else {
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,
@@ -983,14 +1011,18 @@ int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstrid
 
 // U = L11^{-1} A for rows [p0, p0 + w) and the columns [jlo, n), L11 the unit lower diagonal block
 // at (p0, p0) (FP32; no swaps).
-int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo) {
+int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo, float* ub,
+                   int64_t ub_stride, int krow, int koff, bool* emitted) {
+  if (emitted) *emitted = false;
   if (jlo >= n) return BIE_OK;
   Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
   dim3 gs((unsigned)((n - jlo + 127) / 128), batch);
   if (w == 64) {
     BIE_TRY((set_smem_max(k_trsm64)));
     dim3 gt((unsigned)((n - jlo + 63) / 64), batch);
-    BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, jlo, n));
+    const BtOut bt{ub, ub_stride, krow, koff, jlo};
+    BIE_LAUNCH(k_trsm64<<<gt, 64, kTrsmSmem, c->stream>>>(M, bstride, n, ld, p0, jlo, n, bt));
+    if (emitted) *emitted = ub != nullptr;
   }
   else
     BIE_LAUNCH(k_swap_trsm<float><<<gs, 128, (size_t)w * w * sizeof(Cx<float>), c->stream>>>(M, bstride, n, ld, p0, w,

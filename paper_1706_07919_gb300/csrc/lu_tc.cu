@@ -22,9 +22,11 @@
 namespace bie {
 
 int lu_panel_steps32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int32_t* piv,
-                     int32_t* info, int tend, void* coop, int32_t* err);
+                     int32_t* info, int tend, void* coop, int32_t* err, float* ub, int64_t ub_stride, int krow,
+                     int koff, bool* emitted);
 size_t lu_coop_scratch_bytes(int batch);
-int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo);
+int lu_trsm_rows32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int p0, int w, int jlo, float* ub,
+                   int64_t ub_stride, int krow, int koff, bool* emitted);
 
 namespace tc {
 
@@ -651,9 +653,13 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
       const int E = std::min(n, P0 + NBO);
       for (int p0 = P0; p0 < E; p0 += nb) {
         const int w = std::min(nb, E - p0), q = p0 + w;
-        BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E, coop, err));
+        // the U solve of the block's columns right of the panel also writes their B^T (64-row
+        // panels); otherwise the build pass does
+        bool emitted = false;
+        BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, E, coop, err, ub, ub_stride, kr, 0,
+                                 &emitted));
         if (q < E) {  // then w == nb (E - P0 is a multiple of nb unless E == n)
-          BIE_TRY(build(p0, q, E, false, 0, w));
+          if (!emitted) BIE_TRY(build(p0, q, E, false, 0, w));
           BIE_TRY(update(q, n, q, E, p0, w, false, q));
         }
       }
@@ -661,8 +667,9 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
       for (int b = 0; b < NBO / nb; ++b) {
         const int Rb = P0 + b * nb;
         BIE_TRY(update(Rb, Rb + nb, E, n, P0, b * nb, true, E));
-        BIE_TRY(lu_trsm_rows32(c, A, batch, n, ld, bstride, Rb, nb, E));
-        BIE_TRY(build(Rb, E, n, true, 2 * nb * b, nb));
+        bool emitted = false;
+        BIE_TRY(lu_trsm_rows32(c, A, batch, n, ld, bstride, Rb, nb, E, ubo, ubo_stride, 2 * NBO, 2 * nb * b, &emitted));
+        if (!emitted) BIE_TRY(build(Rb, E, n, true, 2 * nb * b, nb));
       }
       BIE_TRY(update(E, n, E, n, P0, NBO, true, E));
     }
@@ -671,7 +678,7 @@ int lu_factor_tc(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, i
   }
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int w = std::min(NB, n - p0);
-    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n, coop, err));
+    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n, coop, err, nullptr, 0, 0, 0, nullptr));
     const int rem = n - p0 - w;
     if (rem <= 0) continue;
     if (ver == 2) {

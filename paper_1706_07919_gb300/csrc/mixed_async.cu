@@ -139,6 +139,17 @@ int solve_mixed_async(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
                       2 * align256a((size_t)N * 4) + align256a(refine_state_bytes(1)) + 64 +
                       align256a(sizeof(bie_report)) + 16;
   const size_t fb1 = align256a((size_t)N * N * sizeof(cd)) + 7 * vec + align256a((size_t)N * 8) + 1024;
+  if (rep && c->rep_pinned_bytes < (size_t)Nk * sizeof(bie_report)) {
+    // report staging, grown before this call enqueues anything; a smaller earlier buffer is
+    // retired, not freed, since an earlier call's host function may still read it (freed with
+    // the context)
+    if (c->rep_pinned) c->rep_pinned_old.push_back(c->rep_pinned);
+    c->rep_pinned = nullptr;
+    c->rep_pinned_bytes = 0;
+    const size_t want = std::max<size_t>((size_t)Nk * sizeof(bie_report), 4096);
+    BIE_CUDA_TRY(cudaMallocHost(&c->rep_pinned, want));
+    c->rep_pinned_bytes = want;
+  }
   size_t free_b = 0;
   BIE_TRY(device_free(c, &free_b));
   const int G = (int)std::max<size_t>(
@@ -224,16 +235,6 @@ int solve_mixed_async(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
   }
   if (rep) {  // reports: device -> pinned staging -> the caller's array, in stream order
     const size_t bytes = (size_t)Nk * sizeof(bie_report);
-    if (c->rep_pinned_bytes < bytes) {
-      if (c->rep_pinned) {  // an earlier call's host copy may still read it
-        BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        cudaFreeHost(c->rep_pinned);
-        c->rep_pinned = nullptr;
-        c->rep_pinned_bytes = 0;
-      }
-      BIE_CUDA_TRY(cudaMallocHost(&c->rep_pinned, bytes));
-      c->rep_pinned_bytes = bytes;
-    }
     BIE_CUDA_TRY(cudaMemcpyAsync(c->rep_pinned, rep_dev, bytes, cudaMemcpyDeviceToHost, c->stream));
     HostCopy* h = new HostCopy{rep, c->rep_pinned, bytes};
     const cudaError_t e = cudaLaunchHostFunc(c->stream, host_copy, h);
