@@ -144,8 +144,8 @@ struct bie_ctx {
   double refine64_tol = 1e-13;       // backward-error target against the FP64 re-assembly
   double refine_tol = 1e-11;         // backward-error target of the refinement
   double fallback_err_est = 3e-7;    // FP64 re-solve above this estimated assembly-induced error (the
-                                     // estimate reads the true error within a factor 0.14 - 2.96 on
-                                     // the two-sphere sweep: 3e-7 keeps the unflagged below 1e-6)
+                                     // true error is 0.14 - 4.4 times the estimate on the two-sphere
+                                     // sweep; at 3e-7 the largest unflagged error there is 4.5e-7)
   int field_accurate_phase = 1;      // mixed field: float-float phases (1) or FP32 phases (0)
   int field_variant = 2;             // mixed field kernel: 2 k_field32c (16 wavenumbers per group,
                                      // 128 points per CTA, 32-point tiles), 1 the same with 64
