@@ -342,7 +342,7 @@ namespace coop {
 constexpr int NT = 512;
 constexpr int LWMAX = 16;
 constexpr int WMAX = 64;                 // panel width
-constexpr uint32_t SPIN = 1u << 21;      // polls of one barrier (about a second) before giving up
+constexpr uint32_t SPIN = 1u << 21;      // polls of one wait (about a second) before giving up
 struct alignas(16) Cand {                // one CTA's pivot candidate for one column
   // |a|^2 of the candidate (bits of the float, -1: no row) << 32 | its row << 8 | tag: the column's
   // place in the panel + 1 (1 .. 64; 0: not written in this launch), stored last with release
@@ -390,7 +390,6 @@ __global__ void __launch_bounds__(coop::NT, 1) k_panel_coop(
   __shared__ int s_p, s_abort, s_m;
   __shared__ int s_piv[LWMAX], s_rows[2 * LWMAX], s_src[2 * LWMAX];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nmat = gridDim.x / cpm;
   const int z = blockIdx.x / cpm, j = blockIdx.x - z * cpm;
   Cx<float>* M = A + (int64_t)z * bstride;
   const int r_lo = p0 + j * ch, r_hi = min(n, r_lo + ch);  // empty when r_lo >= n
