@@ -910,8 +910,8 @@ def main():
     ap.add_argument("--uneven-nk", dest="uneven_nk", type=int, default=8,
                     help="wavenumbers per configuration of the uneven batch sample")
     ap.add_argument("--uneven-workers", dest="uneven_workers", type=int, default=4)
-    ap.add_argument("--case", choices=["lu", "lu16", "lu_n8004", "lattice", "field", "field512", "field_sample", "batch",
-                                       "learned", "step", "peaks", "phases", "uneven_full"],
+    ap.add_argument("--case", choices=["lu", "lu16", "lu_n8004", "lattice", "lattice_full", "field", "field512",
+                                       "field_sample", "batch", "learned", "step", "peaks", "phases", "uneven_full"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
@@ -950,6 +950,50 @@ def main():
         print(json.dumps({"case": "uneven_full", "workload": "uneven_64_configs_N162_to_7976_Nk256",
                           "workers": res[args.uneven_workers], "one_worker": res[1],
                           "speedup": res[1]["wall_s"] / res[args.uneven_workers]["wall_s"]}))
+        return
+    if args.case == "lattice_full":  # the whole lattice workload: k = 0 and 2048 wavenumbers, 8 pulses
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_1706_07919_gb300 import Solver
+        from paper_1706_07919_gb300 import binding as B
+        from workloads import config_lattice_large
+        wl = config_lattice_large()
+        ks = np.concatenate([[0.0], wl.k])
+        midx = np.arange(len(ks), dtype=np.int64)
+        dev = torch.device("cuda", 0)
+        sol = Solver(0)
+        sol.set_geometry(wl.mesh.nodes, wl.mesh.elems, wl.mesh.normals, wl.mesh.bc)
+        sol.set_incident_plane_wave(wl.direction)
+        xo = torch.tensor(wl.xobs, dtype=torch.float64, device=dev)
+        pulses = torch.tensor(wl.pulses, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        surf, rep = sol.solve_frequencies(ks, B.BIE_MODE_MIXED)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        T = sol.eval_field(xo, ks, surf, B.BIE_MODE_MIXED)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        S = sol.pulse_spectrum(pulses)
+        out = sol.synthesize(T, midx, S, wl.Nt, torch.float32)
+        torch.cuda.synchronize(dev)
+        t3 = time.perf_counter()
+        M, P, Nt = wl.xobs.shape[0], wl.pulses.shape[0], wl.Nt
+        ok = [r for r in rep if not r.flags & B.BIE_FLAG_NOT_CONVERGED]
+        print(json.dumps({"case": "lattice_full", "workload": "lattice_4x4x2_soft_N20544_Nk2048_M65536_Nt4096_P8",
+                          "N": int(wl.mesh.N), "wavenumbers": len(ks), "points": M, "pulses": P, "Nt": Nt,
+                          "solve_s": t1 - t0, "field_s": t2 - t1, "spectrum_synthesis_s": t3 - t2,
+                          "solves_per_s": len(ks) / (t1 - t0),
+                          "space_time_pts_per_s": M * Nt * P / ((t2 - t1) + (t3 - t2)),
+                          "field_evals_per_s": M * wl.mesh.E * 16 * len(ks) / (t2 - t1),
+                          "fp64_reassembled": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
+                          "fp64_full_solves": sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64),
+                          "not_converged": len(rep) - len(ok),
+                          "max_backward_err": max(r.backward_err for r in rep),
+                          "output_finite": bool(torch.isfinite(out).all().item()),
+                          "timing": "wall clock around each synchronising phase"}))
+        sol.close()
         return
     if args.case == "peaks":  # the pipe micro-benchmarks alone, as one JSON line
         import torch
