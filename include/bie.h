@@ -60,7 +60,9 @@ extern "C" {
 
 /* Report flags (bie_report.flags). */
 #define BIE_FLAG_NOT_CONVERGED 1u   /* refinement stopped at its iteration cap */
-#define BIE_FLAG_FALLBACK_FP64 2u   /* the frequency was re-solved by the FP64 path */
+#define BIE_FLAG_FALLBACK_FP64 2u   /* the frequency was re-solved by the FP64 path (its report then
+                                       describes that solve: path BIE_MODE_FP64, NOT_CONVERGED
+                                       cleared) */
 #define BIE_FLAG_ZERO_PIVOT 4u      /* an exactly zero pivot was met */
 #define BIE_FLAG_ILL_CONDITIONED 8u /* the FP32 assembly's rounding, pushed through the solve, was
                                        estimated above "mixed.fallback_err_est" (a wavenumber
@@ -78,7 +80,9 @@ typedef struct {
   int32_t path;         /* BIE_MODE_* that produced the result */
   uint32_t flags;       /* BIE_FLAG_* bits */
   int32_t reserved;
-  double backward_err;  /* ||b - A x|| / (||A||_inf ||x|| + ||b||), infinity norms */
+  double backward_err;  /* ||b - A x|| / (||A||_inf ||x|| + ||b||), infinity norms, of the
+                           refinement or Krylov solve; 0 for the FP64 path (a direct solve
+                           with partial pivoting, not measured) */
   double err_est;       /* mixed path: estimated relative L2 error of x caused by the FP32
                            assembly (a seeded FP32-sized perturbation of A solved with the LU) */
 } bie_report;
@@ -226,6 +230,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 3e-7)
+ *   "mixed.refine64_it_max" corrections against the FP64 re-assembly (0..64, default 30); if they
+ *                          do not reach a backward error of 1e-13 the full FP64 path solves it
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
  *   "field.variant"        mixed field kernel: 2 (default) groups of 16 wavenumbers, 128 points per

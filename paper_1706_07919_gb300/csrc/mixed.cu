@@ -398,9 +398,11 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     bie_report r64;
     set_dir(full64_dir[f]);
     BIE_TRY(solve_fp64(c, &full64[f], 1, surf_out + full64_idx[f] * 2 * N, &r64));
-    if (rep) {
-      rep[full64_idx[f]].flags |= BIE_FLAG_FALLBACK_FP64;
-      rep[full64_idx[f]].path = BIE_MODE_FP64;
+    if (rep) {  // the direct FP64 solve replaces the stalled refinement's outcome
+      bie_report& rr = rep[full64_idx[f]];
+      rr.flags = (rr.flags & ~BIE_FLAG_NOT_CONVERGED) | BIE_FLAG_FALLBACK_FP64 | r64.flags;
+      rr.path = BIE_MODE_FP64;
+      rr.backward_err = r64.backward_err;
     }
   }
   BIE_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -161,6 +161,26 @@ def test_fp64_reassembly_path_reaches_fp64_accuracy(Solver, B, ff):
         assert rel(surf[i, 0], P) <= 1e-8, (k, rel(surf[i, 0], P))
 
 
+def test_full_fp64_last_resort_reports(Solver, B):
+    """Every wavenumber flagged and no correction allowed against its FP64 re-assembly: each one
+    ends on the full FP64 path, whose report describes that solve (FALLBACK_FP64, path FP64,
+    NOT_CONVERGED cleared), and whose surface values are the FP64 path's."""
+    w = config_sphere_fp64()
+    ks = w.k[[5, 21, 40]]
+    s = _solver(Solver, w.mesh)
+    s.set_option("mixed.fallback_err_est", 1e-30)
+    s.set_option("mixed.refine64_it_max", 0)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    ref, _ = s.solve_frequencies(ks, B.BIE_MODE_FP64)
+    surf, ref = surf.cpu().numpy(), ref.cpu().numpy()
+    for i in range(len(ks)):
+        assert rep[i].flags & B.BIE_FLAG_FALLBACK_FP64 and rep[i].flags & B.BIE_FLAG_FP64_ASSEMBLY, rep[i].flags
+        assert not rep[i].flags & B.BIE_FLAG_NOT_CONVERGED and rep[i].path == B.BIE_MODE_FP64, rep[i].flags
+        assert rel(surf[i], ref[i]) <= 1e-12, (ks[i], rel(surf[i], ref[i]))
+    with pytest.raises(B.BieError):
+        s.set_option("mixed.refine64_it_max", 65)
+
+
 def test_pooled_reassembly_across_batches(Solver, B):
     """Every wavenumber flagged, 70 wavenumbers in batches of 8: the flagged systems of all batches
     are pooled (factors, permutations, solutions copied aside) and re-assembled and refined in
