@@ -946,6 +946,7 @@ def main():
             res[workers] = {"solves": ns, "wall_s": dt, "solves_per_s": ns / dt, "busy_s": st["busy_ms"] / 1e3,
                             "gpu_util_median_pct": float(np.median(u)) if u else None,
                             "fp64_reassembled": sum(1 for r in reps if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
+                            "fp32_refactored": sum(1 for r in reps if r.flags & B.BIE_FLAG_FP32_REFACTOR),
                             "fp64_full_solves": len(full), "max_backward_err_refined": worst}
         print(json.dumps({"case": "uneven_full", "workload": "uneven_64_configs_N162_to_7976_Nk256",
                           "workers": res[args.uneven_workers], "one_worker": res[1],
@@ -988,6 +989,7 @@ def main():
                           "space_time_pts_per_s": M * Nt * P / ((t2 - t1) + (t3 - t2)),
                           "field_evals_per_s": M * wl.mesh.E * 16 * len(ks) / (t2 - t1),
                           "fp64_reassembled": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP64_ASSEMBLY),
+                          "fp32_refactored": sum(1 for r in rep if r.flags & B.BIE_FLAG_FP32_REFACTOR),
                           "fp64_full_solves": sum(1 for r in rep if r.flags & B.BIE_FLAG_FALLBACK_FP64),
                           "not_converged": len(rep) - len(ok),
                           "max_backward_err": max(r.backward_err for r in rep),

@@ -67,6 +67,9 @@ extern "C" {
 #define BIE_FLAG_ILL_CONDITIONED 8u /* the FP32 assembly's rounding, pushed through the solve, was
                                        estimated above "mixed.fallback_err_est" (a wavenumber
                                        near an interior resonance) */
+#define BIE_FLAG_FP32_REFACTOR 32u  /* the TF32 factor's refinement against the FP64 re-assembly
+                                       stalled; the FP64 system was factored again in FP32 on the
+                                       CUDA cores and refined with that factor (bie_solve_frequencies) */
 #define BIE_FLAG_FP64_ASSEMBLY 16u  /* re-assembled in FP64 and refined against that system with
                                        the low-precision factor (after ILL_CONDITIONED or a stalled
                                        refinement); FALLBACK_FP64 is added if that also stalled */
@@ -231,7 +234,11 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 3e-7)
  *   "mixed.refine64_it_max" corrections against the FP64 re-assembly (0..64, default 30); if they
- *                          do not reach a backward error of 1e-13 the full FP64 path solves it
+ *                          do not reach a backward error of 1e-13, the FP64 system is factored
+ *                          again in FP32 and refined with that factor (up to 30 corrections), and
+ *                          if that also stalls the full FP64 path solves it
+ *   "mixed.refactor32"     1 (default): take the FP32 re-factorisation step above; 0: go from the
+ *                          stalled refinement straight to the full FP64 path
  *   "field.accurate_phase" 1: float-float phases in the mixed field evaluation (default),
  *                          0: FP32 phases with hardware sine/cosine
  *   "field.variant"        mixed field kernel: 2 (default) groups of 16 wavenumbers, 128 points per
@@ -288,7 +295,8 @@ int bie_assemble(bie_ctx* ctx, double k, void* A_out, void* b_out);
  *   surf_out device c128 [Nk][2][N]: scattered P and dP/dn at every node, per k
  *   rep      host bie_report [Nk] or NULL
  * Synchronises the stream before returning (the reports are read back).  Errors: INVALID_ARG,
- * STATE, OOM (scratch larger than free device memory), CUDA. */
+ * STATE, OOM (scratch larger than free device memory), CUDA, TIMEOUT (a bounded wait of the
+ * tensor-core factorisation or of a cooperative panel gave up: that factor is void). */
 int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, void* surf_out,
                           bie_report* rep);
 
@@ -305,7 +313,8 @@ int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, v
  *            the stream has completed this call's work (e.g. after cudaStreamSynchronize); the
  *            array must stay allocated until then
  * Differences from bie_solve_frequencies: no last-resort full FP64 solve -- a wavenumber whose
- * re-assembly does not converge, or whose factor met a zero pivot, keeps BIE_FLAG_NOT_CONVERGED;
+ * re-assembly does not converge, or whose factor met a zero pivot, keeps BIE_FLAG_NOT_CONVERGED
+ * (so does every system of a batch whose factorisation gave up a bounded wait, backward error NaN);
  * "mixed.graph" and "mixed.phase_timing" do not apply.  The first solve after bie_set_geometry
  * builds the mixed path's geometry tables and may synchronise.  Calls on one context share its
  * workspace and are ordered by its stream.  Errors (before anything is enqueued): as

@@ -32,6 +32,7 @@ BIE_FLAG_FALLBACK_FP64 = 2
 BIE_FLAG_ZERO_PIVOT = 4
 BIE_FLAG_ILL_CONDITIONED = 8
 BIE_FLAG_FP64_ASSEMBLY = 16
+BIE_FLAG_FP32_REFACTOR = 32
 
 EXPORTED = ["bie_last_error", "bie_version", "bie_kernel_launches", "bie_create", "bie_destroy", "bie_set_quadrature",
             "bie_set_geometry", "bie_set_incident_plane_wave", "bie_set_option", "bie_assemble", "bie_solve_frequencies",

@@ -155,6 +155,7 @@ struct bie_ctx {
   int asm_kb = 2;                    // FP32 bulk assembly: wavenumbers per thread (1, 2), 0 = the
                                      // general kernel (also taken when an element mixes conditions)
   int asm_windows = 1;               // FP32 bulk assembly at large N: column windows in shared memory (1) or rows in A (0)
+  int refactor32 = 1;                // before the full FP64 path: FP32 re-factorisation of the FP64 system (1)
   int reassembly_group = 32;         // FP64 re-assembly slots refined together (1..32; memory may lower it)
   int reassembly_ff = 1;             // flagged wavenumbers: bulk re-assembly in float-float (1) or FP64 (0)
   int mixed_graph = 1;               // replay full batches of the mixed path from a CUDA graph

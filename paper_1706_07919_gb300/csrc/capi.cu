@@ -415,6 +415,8 @@ int bie_set_option(bie_ctx* c, const char* name, double value) {
   } else if (n == "refine.it_max") {
     if (value < 0 || value > 64) return fail(BIE_ERR_INVALID_ARG, "refine.it_max must be in [0, 64]");
     c->refine_it_max = (int)value;
+  } else if (n == "mixed.refactor32") {
+    c->refactor32 = value != 0.0 ? 1 : 0;
   } else if (n == "mixed.refine64_it_max") {
     if (value < 0 || value > 64) return fail(BIE_ERR_INVALID_ARG, "mixed.refine64_it_max must be in [0, 64]");
     c->refine64_it_max = (int)value;

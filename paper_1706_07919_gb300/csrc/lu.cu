@@ -1040,6 +1040,27 @@ int lu_solve64(bie_ctx* c, const cd* LU, int batch, int n, int ld, int64_t bstri
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
+// FP32 LU without tensor cores for systems the TF32 factor cannot refine: 64-column panels
+// (cooperative for a few tall matrices, see k_panel_coop), their row swaps and U blocks, and the
+// trailing update A22 -= L21 U12 in FP32 on the CUDA cores (k_gemm_update).  coop / err: the
+// cooperative panel's scratch and error word.
+int lu_factor32_panels(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
+                       void* coop, int32_t* err) {
+  Cx<float>* M = reinterpret_cast<Cx<float>*>(A);
+  BIE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
+  for (int p0 = 0; p0 < n; p0 += 64) {
+    const int w = std::min(64, n - p0);
+    BIE_TRY(lu_panel_steps32(c, A, batch, n, ld, bstride, p0, w, piv, info, n, coop, err, nullptr, 0, 0, 0, nullptr));
+    const int rem = n - p0 - w;
+    if (rem > 0) {
+      dim3 gg((unsigned)((rem + 63) / 64), (unsigned)((rem + 63) / 64), batch);
+      BIE_LAUNCH(k_gemm_update<float><<<gg, 256, 0, c->stream>>>(M, bstride, n, ld, p0, w));
+    }
+  }
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 int lu_factor32(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info) {
   return lu_factor_simt<float>(c, reinterpret_cast<Cx<float>*>(A), batch, n, ld, bstride, piv, info, 32);
 }

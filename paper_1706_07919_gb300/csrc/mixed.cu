@@ -22,6 +22,11 @@ int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t l
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
                  int it_max, double tol, cf* D, void* tscratch);
 size_t trsv_scratch_bytes(int nk, int n);
+int lu_tc_error(bie_ctx* c, void* scratch, int32_t* out);
+int lu_factor32_panels(bie_ctx* c, cf* A, int batch, int n, int ld, int64_t bstride, int32_t* piv, int32_t* info,
+                       void* coop, int32_t* err);
+int factor_aux(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t bstride, const int32_t* piv,
+               int32_t* perm, cf* D);
 int64_t diag_inv_stride(int n);
 int refine_fp64_system(bie_ctx* c, const cd* A64, const cd* b64, const cf* LU, int64_t ld, int64_t bstride,
                        const int32_t* perm, const int32_t* sel_dev, int ng, int n, cd* x, cd* xg, cd* r,
@@ -43,6 +48,15 @@ __global__ void k_surface_fields(const uint8_t* __restrict__ bc, int64_t N, cons
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kFallbackGroupMax = 32;  // FP64 systems re-assembled and refined together (at most)
+constexpr int kRefactorItMax = 30;     // corrections with the FP32 re-factorisation
+
+// FP64 matrix [n][n] rounded into an FP32 one [n][ld]; grid (ceil(n / 256), n)
+__global__ void k_cd_to_cf(const cd* __restrict__ A, int64_t n, cf* __restrict__ F, int64_t ld) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= n) return;
+  const cd v = A[i * n + j];
+  F[i * ld + j] = {(float)v.re, (float)v.im};
+}
 
 // lu_keep / perm_keep / d_keep (optional, device): receive the low-precision factor ([Nk][N][ld],
 // ld = N rounded up to 64), row permutation ([Nk][N]) and diagonal-block inverses
@@ -309,6 +323,11 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
       }
       BIE_TRY(refine_read_state(c, state, nk, done.data(), iters.data(), berr.data(), est.data()));
       if (d == 0) BIE_CUDA_TRY(cudaMemcpy(hinfo.data(), info, nk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (d == 0 && c->tc_version > 0) {  // a bounded wait of the factorisation gave up: its factor is void
+        int32_t terr = 0;
+        BIE_TRY(lu_tc_error(c, tcs, &terr));
+        if (terr) return fail(BIE_ERR_TIMEOUT, "LU: a bounded wait in the tensor-core update or a cooperative panel gave up");
+      }
       if (timing && d == 0) {  // the batch has completed (its state was read)
         c->phase.assembly_ms += elapsed(0, 1);
         c->phase.factor_ms += elapsed(1, 2);
@@ -393,8 +412,44 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     set_dir(0);
   }
   BIE_TRY(flush_pool());
+  // Wavenumbers whose TF32 factor could not be refined against the FP64 re-assembly (cond(A)
+  // times the TF32 factor's error near 1): the FP64 system is factored again in FP32 on the CUDA
+  // cores (8000 times smaller factor error than TF32) and refined against itself with that factor;
+  // only if that also stalls does the full FP64 path (an FP64 LU: about 70 times slower on this
+  // GPU's FP64 pipe) solve it.  The batch buffers (slot 0) are free by now.
+  std::vector<int32_t> one{0};
+  for (size_t f = 0; c->refactor32 && f < full64.size(); ++f) {
+    set_dir(full64_dir[f]);
+    BIE_CUDA_TRY(cudaMemcpyAsync(kg, &full64[f], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    BIE_CUDA_TRY(cudaMemcpyAsync(sel_g, one.data(), sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    BIE_TRY(assemble64(c, kg, 1, A64, b64, s64, c->reassembly_ff != 0));
+    BIE_LAUNCH(k_cd_to_cf<<<dim3((unsigned)((N + 255) / 256), (unsigned)N), 256, 0, c->stream>>>(A64, N, LU, ld));
+    BIE_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), c->stream));
+    BIE_TRY(lu_factor32_panels(c, LU, 1, (int)N, (int)ld, bstride, piv, info, (char*)tcs + 256, (int32_t*)tcs));
+    BIE_TRY(factor_aux(c, LU, 1, (int)N, ld, bstride, piv, perm, Dinv));
+    BIE_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)N * sizeof(cd), c->stream));
+    BIE_TRY(refine_fp64_system(c, A64, b64, LU, ld, bstride, perm, sel_g, 1, (int)N, x, xg, rg, rowabs_g, state_g,
+                               kRefactorItMax, c->refine64_tol, Dinv, s64 + N, true));
+    int32_t d1 = 0, it1 = 0, zp = 0, terr = 0;
+    double b1 = 0.0, e1 = 0.0;
+    BIE_TRY(refine_read_state(c, state_g, 1, &d1, &it1, &b1, &e1));
+    BIE_CUDA_TRY(cudaMemcpy(&zp, info, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    BIE_TRY(lu_tc_error(c, tcs, &terr));
+    if (terr) return fail(BIE_ERR_TIMEOUT, "LU: a bounded wait in a cooperative panel gave up");
+    if (!d1 || zp || !std::isfinite(b1)) continue;  // stays for the full FP64 path
+    dim3 gs((unsigned)((N + 255) / 256), 1);
+    BIE_LAUNCH(k_surface_fields<<<gs, 256, 0, c->stream>>>(c->bc, N, x, s64, surf_out + full64_idx[f] * 2 * N, 2 * N));
+    if (rep) {
+      bie_report& rr = rep[full64_idx[f]];
+      rr.flags = (rr.flags & ~BIE_FLAG_NOT_CONVERGED) | BIE_FLAG_FP32_REFACTOR;
+      rr.iters += it1;
+      rr.backward_err = b1;
+    }
+    full64[f] = -1.0;  // done
+  }
   // last resort: the full FP64 path
   for (size_t f = 0; f < full64.size(); ++f) {
+    if (full64[f] < 0.0) continue;
     bie_report r64;
     set_dir(full64_dir[f]);
     BIE_TRY(solve_fp64(c, &full64[f], 1, surf_out + full64_idx[f] * 2 * N, &r64));

@@ -51,10 +51,13 @@ __global__ void k_put_values(ParamVals pv, int n, double* __restrict__ dst) {
 }
 
 // Reports of a batch's nk systems (rep [nk]) and, in order, the indices of the flagged ones
-// (list [nk], *count).  One CTA.
-__global__ void k_async_reports(const RefineState* __restrict__ st, const int32_t* __restrict__ info, int nk,
-                                double thresh, bie_report* __restrict__ rep, int32_t* __restrict__ list,
+// (list [nk], *count).  lu_err: the factorisation's error word (a bounded wait that gave up voids
+// every factor of the batch: all reported NOT_CONVERGED, none re-assembled), or null.  One CTA.
+__global__ void k_async_reports(const RefineState* __restrict__ st, const int32_t* __restrict__ info,
+                                const int32_t* __restrict__ lu_err, int nk, double thresh,
+                                bie_report* __restrict__ rep, int32_t* __restrict__ list,
                                 int32_t* __restrict__ count) {
+  const bool void_factor = lu_err && *lu_err;
   for (int i = threadIdx.x; i < nk; i += blockDim.x) {
     const bool conv = st[i].done && isfinite(st[i].berr);
     const bool sensitive = !(st[i].err_est <= thresh);
@@ -63,9 +66,9 @@ __global__ void k_async_reports(const RefineState* __restrict__ st, const int32_
     r.path = BIE_MODE_MIXED;
     r.flags = (conv ? 0u : BIE_FLAG_NOT_CONVERGED) | (info[i] ? BIE_FLAG_ZERO_PIVOT : 0u) |
               (sensitive ? BIE_FLAG_ILL_CONDITIONED : 0u);
-    if (info[i]) r.flags |= BIE_FLAG_NOT_CONVERGED;  // nothing to refine with
+    if (info[i] || void_factor) r.flags |= BIE_FLAG_NOT_CONVERGED;  // nothing to refine with
     r.reserved = 0;
-    r.backward_err = st[i].berr;
+    r.backward_err = void_factor ? (double)NAN : st[i].berr;
     r.err_est = st[i].err_est;
     rep[i] = r;
   }
@@ -75,7 +78,7 @@ __global__ void k_async_reports(const RefineState* __restrict__ st, const int32_
     for (int i = 0; i < nk; ++i) {
       const bool conv = st[i].done && isfinite(st[i].berr);
       const bool sensitive = !(st[i].err_est <= thresh);
-      if (!info[i] && (!conv || sensitive)) list[n++] = i;
+      if (!info[i] && !void_factor && (!conv || sensitive)) list[n++] = i;
     }
     *count = n;
   }
@@ -217,8 +220,9 @@ int solve_mixed_async(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie
       BIE_TRY(lu_factor32(c, LU, nk, (int)N, (int)ld, bstride, piv, info));
     BIE_TRY(refine_solve(c, A, LU, nk, (int)N, ld, bstride, piv, b, x, r, rowabs, perm, state, c->refine_it_max,
                          c->refine_tol, Dinv, rowsum));
-    BIE_LAUNCH(k_async_reports<<<1, 256, 0, c->stream>>>((const RefineState*)state, info, nk, c->fallback_err_est,
-                                                         rep_dev + k0, list, count));
+    BIE_LAUNCH(k_async_reports<<<1, 256, 0, c->stream>>>((const RefineState*)state, info,
+                                                         c->tc_version > 0 ? (const int32_t*)tcs : nullptr, nk,
+                                                         c->fallback_err_est, rep_dev + k0, list, count));
     const int rounds = std::min(rounds_per_batch, (nk + G - 1) / G);
     for (int rr = 0; rr < rounds; ++rr) {
       BIE_LAUNCH(k_async_round<<<1, ((G + 31) / 32) * 32, 0, c->stream>>>(list, count, rr, G, kdev, kg, sel_g,

@@ -701,6 +701,16 @@ int diag_inverses(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t b
   return BIE_OK;
 }
 
+// The row permutations and diagonal-block inverses of nk factors (what refine_solve forms before
+// its solves), for factors refined by refine_fp64_system directly.
+int factor_aux(bie_ctx* c, const cf* LU, int nk, int n, int64_t ld, int64_t bstride, const int32_t* piv,
+               int32_t* perm, cf* D) {
+  if ((size_t)n * sizeof(int32_t) > 200 * 1024) return fail(BIE_ERR_INVALID_ARG, "N too large for the permutation kernel");
+  BIE_TRY((set_smem_max(k_piv_to_perm)));
+  BIE_LAUNCH(k_piv_to_perm<<<nk, 256, n * sizeof(int32_t), c->stream>>>(piv, n, perm));
+  return diag_inverses(c, LU, nk, n, ld, bstride, D);
+}
+
 int refine_solve(bie_ctx* c, const cf* A, const cf* LU, int nk, int n, int64_t ld, int64_t bstride,
                  const int32_t* piv, const cd* b, cd* x, cd* r, double* rowabs, int32_t* perm, void* state_dev,
                  int it_max, double tol, cf* D, void* tscratch) {

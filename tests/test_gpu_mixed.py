@@ -170,6 +170,7 @@ def test_full_fp64_last_resort_reports(Solver, B):
     s = _solver(Solver, w.mesh)
     s.set_option("mixed.fallback_err_est", 1e-30)
     s.set_option("mixed.refine64_it_max", 0)
+    s.set_option("mixed.refactor32", 0)
     surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
     ref, _ = s.solve_frequencies(ks, B.BIE_MODE_FP64)
     surf, ref = surf.cpu().numpy(), ref.cpu().numpy()
@@ -179,6 +180,38 @@ def test_full_fp64_last_resort_reports(Solver, B):
         assert rel(surf[i], ref[i]) <= 1e-12, (ks[i], rel(surf[i], ref[i]))
     with pytest.raises(B.BieError):
         s.set_option("mixed.refine64_it_max", 65)
+
+
+@pytest.mark.parametrize("mesh", ["sphere", "two_spheres"])
+def test_fp32_refactorisation_before_the_fp64_path(Solver, B, two_spheres, mesh):
+    """Every wavenumber flagged and no correction allowed with the TF32 factor against the FP64
+    re-assembly: the FP64 system is factored again in FP32 on the CUDA cores (64-column panels,
+    cooperative ones for the two spheres' N = 2884) and refined against itself with that factor.
+    Each report carries FP32_REFACTOR on the mixed path (no full FP64 solve), a backward error at
+    the FP64 refinement's tolerance, and surface values equal to the FP64 path's within 1e-9; two
+    incident directions take the same step per direction."""
+    m = config_sphere_fp64().mesh if mesh == "sphere" else two_spheres
+    ks = np.array([1.5, 4.49, 7.0])
+    s = _solver(Solver, m)
+    s.set_option("mixed.fallback_err_est", 1e-30)
+    s.set_option("mixed.refine64_it_max", 0)
+    surf, rep = s.solve_frequencies(ks, B.BIE_MODE_MIXED)
+    ref, _ = s.solve_frequencies(ks, B.BIE_MODE_FP64)
+    surf, ref = surf.cpu().numpy(), ref.cpu().numpy()
+    for i in range(len(ks)):
+        f = rep[i].flags
+        assert f & B.BIE_FLAG_FP32_REFACTOR and f & B.BIE_FLAG_FP64_ASSEMBLY, (ks[i], f)
+        assert not f & (B.BIE_FLAG_FALLBACK_FP64 | B.BIE_FLAG_NOT_CONVERGED) and rep[i].path == B.BIE_MODE_MIXED, (ks[i], f)
+        assert rep[i].backward_err <= 1e-12, (ks[i], rep[i].backward_err)
+        assert rel(surf[i], ref[i]) <= 1e-9, (ks[i], rel(surf[i], ref[i]))
+    if mesh == "sphere":
+        dirs = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8]])
+        sd, rd = s.solve_frequencies_multi(ks, dirs, B.BIE_MODE_MIXED)
+        sr, _ = s.solve_frequencies_multi(ks, dirs, B.BIE_MODE_FP64)
+        sd, sr = sd.cpu().numpy(), sr.cpu().numpy()
+        assert all(r.flags & B.BIE_FLAG_FP32_REFACTOR and not r.flags & B.BIE_FLAG_FALLBACK_FP64 for r in rd), [r.flags for r in rd]
+        assert rel(sd, sr) <= 1e-9, rel(sd, sr)
+    s.close()
 
 
 def test_pooled_reassembly_across_batches(Solver, B):
