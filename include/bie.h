@@ -67,12 +67,13 @@ extern "C" {
 #define BIE_FLAG_ILL_CONDITIONED 8u /* the FP32 assembly's rounding, pushed through the solve, was
                                        estimated above "mixed.fallback_err_est" (a wavenumber
                                        near an interior resonance) */
+#define BIE_FLAG_FP64_ASSEMBLY 16u  /* re-assembled in FP64 and refined against that system with
+                                       the low-precision factor (after ILL_CONDITIONED or a stalled
+                                       refinement); if that also stalls, FP32_REFACTOR or, when
+                                       the re-factorisation stalls too, FALLBACK_FP64 is added */
 #define BIE_FLAG_FP32_REFACTOR 32u  /* the TF32 factor's refinement against the FP64 re-assembly
                                        stalled; the FP64 system was factored again in FP32 on the
                                        CUDA cores and refined with that factor (bie_solve_frequencies) */
-#define BIE_FLAG_FP64_ASSEMBLY 16u  /* re-assembled in FP64 and refined against that system with
-                                       the low-precision factor (after ILL_CONDITIONED or a stalled
-                                       refinement); FALLBACK_FP64 is added if that also stalled */
 
 typedef struct bie_ctx bie_ctx;
 
@@ -314,7 +315,8 @@ int bie_solve_frequencies(bie_ctx* ctx, const double* k, int64_t Nk, int mode, v
  *            array must stay allocated until then
  * Differences from bie_solve_frequencies: no last-resort full FP64 solve -- a wavenumber whose
  * re-assembly does not converge, or whose factor met a zero pivot, keeps BIE_FLAG_NOT_CONVERGED
- * (so does every system of a batch whose factorisation gave up a bounded wait, backward error NaN);
+ * (so does every system of a batch whose factorisation gave up a bounded wait, backward error NaN;
+ * bie_solve_frequencies on those wavenumbers takes the remaining steps);
  * "mixed.graph" and "mixed.phase_timing" do not apply.  The first solve after bie_set_geometry
  * builds the mixed path's geometry tables and may synchronise.  Calls on one context share its
  * workspace and are ordered by its stream.  Errors (before anything is enqueued): as

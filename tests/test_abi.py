@@ -78,3 +78,17 @@ def test_binding_rejects_mismatched_synthesis_buffers_before_launch():
     with pytest.raises(ValueError, match="T_out"):
         B.bie_eval_field(0, torch.zeros((M, 3), dtype=torch.float64), np.ones(Nk), None, 0,
                          torch.zeros((Nk, M - 1), dtype=torch.complex128))
+
+
+def test_binding_constants_match_header():
+    """Every integer constant of include/bie.h (return codes, modes, report flags, the network's
+    parameter count) has the same value in the binding; report flags are distinct bits."""
+    from paper_1706_07919_gb300 import binding as B
+    txt = open(os.path.join(ROOT, "include", "bie.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in
+              re.finditer(r"^#define (BIE_\w+)\s+\(?(-?\d+)u?\)?", txt, flags=re.M)}
+    assert {"BIE_OK", "BIE_ERR_TIMEOUT", "BIE_MODE_MIXED", "BIE_FLAG_FP32_REFACTOR"} <= set(consts)
+    for name, value in consts.items():
+        assert getattr(B, name) == value, name
+    flags = [v for n, v in consts.items() if n.startswith("BIE_FLAG_")]
+    assert all(v & (v - 1) == 0 for v in flags) and len(set(flags)) == len(flags)
