@@ -72,8 +72,9 @@ extern "C" {
                                        refinement); if that also stalls, FP32_REFACTOR or, when
                                        the re-factorisation stalls too, FALLBACK_FP64 is added */
 #define BIE_FLAG_FP32_REFACTOR 32u  /* the TF32 factor's refinement against the FP64 re-assembly
-                                       stalled; the FP64 system was factored again in FP32 on the
-                                       CUDA cores and refined with that factor (bie_solve_frequencies) */
+                                       stalled (or that factor met a zero pivot); the FP64 system
+                                       was factored again in FP32 on the CUDA cores and refined with
+                                       that factor (bie_solve_frequencies; FP64_ASSEMBLY set too) */
 
 typedef struct bie_ctx bie_ctx;
 

@@ -441,7 +441,7 @@ int solve_mixed(bie_ctx* c, const double* k, int64_t Nk, cd* surf_out, bie_repor
     BIE_LAUNCH(k_surface_fields<<<gs, 256, 0, c->stream>>>(c->bc, N, x, s64, surf_out + full64_idx[f] * 2 * N, 2 * N));
     if (rep) {
       bie_report& rr = rep[full64_idx[f]];
-      rr.flags = (rr.flags & ~BIE_FLAG_NOT_CONVERGED) | BIE_FLAG_FP32_REFACTOR;
+      rr.flags = (rr.flags & ~BIE_FLAG_NOT_CONVERGED) | BIE_FLAG_FP32_REFACTOR | BIE_FLAG_FP64_ASSEMBLY;
       rr.iters += it1;
       rr.backward_err = b1;
     }
