@@ -231,7 +231,8 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          shorter pivot chains per leaf, narrower K = 32 updates inside a block)
  *   "mixed.lu_tile"        tile of the tensor-core update (versions 2, 3): 128 rows x 256 real
  *                          columns (default; MMA N = 256) or 128 x 128 (MMA N = 128)
- *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 64)
+ *   "mixed.batch"          wavenumbers factored per batch (>= 1, default 256; at most as many as
+ *                          half the free device memory holds)
  *   "refine.tol"           backward-error target of iterative refinement (default 1e-11)
  *   "refine.it_max"        refinement corrections per wavenumber (0..64, default 10)
  *   "mixed.fallback_err_est" FP64 re-assembly when the estimated error exceeds it (default 3e-7)

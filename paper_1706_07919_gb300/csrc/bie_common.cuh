@@ -138,7 +138,8 @@ struct bie_ctx {
   int lu_coop = 1;                   // several CTAs per matrix in the panels of few tall matrices
   int lu_panel = 64;                 // mixed.tcgen05 3: panel width (32 or 64)
   int lu_tile = 256;                 // mixed.tcgen05 2, 3: update tile width in real columns (256 or 128)
-  int mixed_batch = 64;              // wavenumbers per batch
+  int mixed_batch = 256;             // wavenumbers per batch (capped by free memory; the tuner's
+                                     // choice at N = 2884)
   int refine_it_max = 10;            // refinement corrections per system
   int refine64_it_max = 30;          // corrections against the FP64 re-assembly of flagged systems
   double refine64_tol = 1e-13;       // backward-error target against the FP64 re-assembly
