@@ -866,6 +866,13 @@ def run_case(args):
         xo = torch.tensor(w.xobs[::8], device="cuda")
         T = sol.eval_field(xo, w.k, surf, B.BIE_MODE_MIXED)
         print("case field_sample:", tuple(T.shape))
+    elif args.case == "reassembly4":  # four wavenumbers forced through the FP64 re-assembly (profiler captures)
+        sol.set_incident_plane_wave(w.direction)
+        sol.set_option("mixed.batch", 4)
+        sol.set_option("mixed.reassembly_group", 4)
+        sol.set_option("mixed.fallback_err_est", 1e-30)
+        surf, rep = sol.solve_frequencies(w.k[[100, 200, 300, 400]], B.BIE_MODE_MIXED)
+        print("case reassembly4: flags", [r.flags for r in rep], "backward errors", [r.backward_err for r in rep])
     else:
         ks = w.k[496:504]
         surf = torch.full((len(ks), 2, w.mesh.N), 0.3 + 0.1j, dtype=torch.complex128, device="cuda")
@@ -911,7 +918,8 @@ def main():
                     help="wavenumbers per configuration of the uneven batch sample")
     ap.add_argument("--uneven-workers", dest="uneven_workers", type=int, default=4)
     ap.add_argument("--case", choices=["lu", "lu16", "lu_n8004", "lattice", "lattice_full", "field", "field512",
-                                       "field_sample", "batch", "learned", "step", "peaks", "phases", "uneven_full"],
+                                       "field_sample", "reassembly4", "batch", "learned", "step", "peaks", "phases",
+                                       "uneven_full"],
                     default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()

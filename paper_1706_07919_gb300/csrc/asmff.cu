@@ -68,9 +68,11 @@ __device__ __forceinline__ void cis_ff(ff phi, const FFConst& K, ff& c, ff& s) {
 }
 
 // Same outputs and launch shape as k_asm32_bulk (rows per CTA x ASMF_W warps per row, colours
-// separated by block barriers), with an FP64 row accumulator [rows][N] in shared memory, or for
-// large N (GROW) the output rows of A themselves (each row belongs to one CTA; the elements of a
-// colour share no node, so the row's warps never touch the same entry between barriers).
+// separated by block barriers), with a float-float row accumulator [rows][N] in shared memory, or
+// for large N (GROW) in the output rows of A themselves (each row belongs to one CTA; the elements
+// of a colour share no node, so the row's warps never touch the same entry between barriers),
+// converted to FP64 once the row is complete.  The scatter and the right-hand side's products with
+// the known values (given as float-float) run on the FP32 pipes: no FP64 arithmetic per element.
 // With QS = 2 the quadrature points of an element are split over two sets of ASMF_W warps (four
 // warps per row), so that two rows fit one CTA of 256 threads and two CTAs an SM (16 warps); the
 // halves add into the row one after the other (a barrier of the row's warps in between).
@@ -81,10 +83,11 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     const int32_t* __restrict__ esort, int64_t N, int64_t E, int Q,
     const float4* __restrict__ qaos /* colour-sorted float-float points, 64-byte records [Q][E] */,
     const double* __restrict__ qshape,
-    const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv, const cd* __restrict__ known,
+    const int32_t* __restrict__ color_off, int ncolors, const double* __restrict__ kv,
+    const float4* __restrict__ knf /* [nk][N] known values as float-float: re hi, re lo, im hi, im lo */,
     cd* __restrict__ A, cd* __restrict__ rowsum /* [nk][N][3] */, int rows, FFConst K) {
   constexpr int WR = ASMF_W * QS;  // warps per row
-  extern __shared__ cd accd[];
+  extern __shared__ float4 accf[];
   __shared__ ff shp[64 * 6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rw = warp / WR, wr = warp % WR, sub = wr % ASMF_W, h = wr / ASMF_W;
@@ -96,17 +99,19 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
   for (int t = threadIdx.x; t < Q * 6; t += blockDim.x) shp[t] = ff_from_double(qshape[t]);
   const int64_t i = (int64_t)blockIdx.x * rows + rw;
   const bool valid = i < N;
-  cd* row;
+  // the row accumulates in float-float (re hi, re lo, im hi, im lo: 16 bytes, the size of a cd
+  // entry), in shared memory or (GROW) in the output row itself, converted to FP64 at the end
+  float4* row;
   if constexpr (GROW) {
-    row = A + ((int64_t)kk * N + (valid ? i : 0)) * N;
+    row = reinterpret_cast<float4*>(A + ((int64_t)kk * N + (valid ? i : 0)) * N);
     if (valid)
-      for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) row[j] = {0.0, 0.0};
+      for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) row[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
-    for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accd[t] = {0.0, 0.0};
-    row = accd + (int64_t)rw * N;
+    for (int64_t t = threadIdx.x; t < (int64_t)rows * N; t += blockDim.x) accf[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    row = accf + (int64_t)rw * N;
   }
   __syncthreads();
-  const cd* kn = known + (int64_t)kk * N;
+  const float4* kn = knf + (int64_t)kk * N;
   ff xi[3], nui[3];
   for (int d = 0; d < 3; ++d) {
     xi[d] = ff_from_double(valid ? nodes[3 * i + d] : 0.0);
@@ -173,21 +178,17 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
 #pragma unroll
           for (int a = 0; a < 6; ++a) {
             const int32_t j = el[a];
-            const cd kvj = kn[j];
-            const cd H = {ff_to_double(hr[a]), ff_to_double(hi[a])}, G = {ff_to_double(gr[a]), ff_to_double(gi[a])};
-            if (bc[j] == 0) {  // hard column: A += H, b += Gm P'_known
-              row[j].re += H.re;
-              row[j].im += H.im;
-              const cd t2 = cmul(G, kvj);
-              bsr = ffx_add_f(ffx_add_f(bsr, (float)t2.re), (float)(t2.re - (double)(float)t2.re));
-              bsi = ffx_add_f(ffx_add_f(bsi, (float)t2.im), (float)(t2.im - (double)(float)t2.im));
-            } else {           // soft column: A -= Gm, b -= H P_known
-              row[j].re -= G.re;
-              row[j].im -= G.im;
-              const cd t2 = cmul(H, kvj);
-              bsr = ffx_add_f(ffx_add_f(bsr, -(float)t2.re), -(float)(t2.re - (double)(float)t2.re));
-              bsi = ffx_add_f(ffx_add_f(bsi, -(float)t2.im), -(float)(t2.im - (double)(float)t2.im));
-            }
+            const float4 k4 = kn[j];
+            const ff kr = {k4.x, k4.y}, ki = {k4.z, k4.w};
+            // hard column: A += H, b += Gm P'_known; soft column: A -= Gm, b -= H P_known
+            const bool hard = bc[j] == 0;
+            const ff ar = hard ? hr[a] : ff_neg(gr[a]), ai = hard ? hi[a] : ff_neg(gi[a]);
+            const ff br = hard ? gr[a] : ff_neg(hr[a]), bi = hard ? gi[a] : ff_neg(hi[a]);
+            float4 v = row[j];
+            const ff nr = ff_add(ff{v.x, v.y}, ar), ni = ff_add(ff{v.z, v.w}, ai);
+            row[j] = make_float4(nr.hi, nr.lo, ni.hi, ni.lo);
+            bsr = ff_add(bsr, ff_sub(ff_mul(br, kr), ff_mul(bi, ki)));
+            bsi = ff_add(bsi, ff_add(ff_mul(br, ki), ff_mul(bi, kr)));
           }
         }
         if (QS > 1) bar_named(1 + rw, 32 * WR);
@@ -206,9 +207,11 @@ __global__ void __launch_bounds__(256, 2) k_asmff_bulk(
     for (int u = 0; u < 6; ++u) part[rw][wr][u] = v[u];
   __syncthreads();
   if (valid) {
-    if constexpr (!GROW) {
-      cd* Arow = A + ((int64_t)kk * N + i) * N;
-      for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) Arow[j] = row[j];
+    // the row to FP64: from shared memory, or (GROW) in place, each entry by the thread that reads it
+    cd* Arow = A + ((int64_t)kk * N + i) * N;
+    for (int64_t j = wr * 32 + lane; j < N; j += 32 * WR) {
+      const float4 v = row[j];
+      Arow[j] = {ff_to_double(ff{v.x, v.y}), ff_to_double(ff{v.z, v.w})};
     }
     if (wr == 0 && lane == 0) {
       double w[6] = {0, 0, 0, 0, 0, 0};
@@ -262,10 +265,22 @@ int ensure_mixed_tables(bie_ctx* c);
 const float4* sorted_aos_ptr(bie_ctx* c);
 const int32_t* sorted_elems_ptr(bie_ctx* c);
 
+// known values [n] (FP64) split into float-float: re hi, re lo, im hi, im lo
+__global__ void k_known_ff(const cd* __restrict__ known, int64_t n, float4* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const cd v = known[t];
+  const ff r = ff_from_double(v.re), i = ff_from_double(v.im);
+  out[t] = make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
 // Bulk part of the FP64 system in float-float (the replacement of k_asm64_bulk in assemble64).
 int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* known, cd* rowsum) {
   const int64_t N = c->N;
   BIE_TRY(ensure_mixed_tables(c));
+  BIE_TRY(ensure_buf(c, c->work6, (size_t)nk * N * sizeof(float4)));
+  float4* knf = (float4*)c->work6.p;
+  BIE_LAUNCH(k_known_ff<<<(unsigned)((nk * N + 255) / 256), 256, 0, c->stream>>>(known, nk * N, knf));
   // 2 rows x 4 warps (quadrature halves) when two such CTAs fit an SM, else 4 rows x 2 warps
   // shrunk to fit shared memory, else (large N) the rows accumulate in A itself
   const bool split = (size_t)2 * N * sizeof(cd) <= 100 * 1024;
@@ -280,17 +295,17 @@ int assemble_ff_bulk(bie_ctx* c, const double* kv, int nk, cd* A, const cd* know
   if (grow) {
     BIE_LAUNCH(k_asmff_bulk<true, 1><<<gb, 32 * rows * ASMF_W, 0, c->stream>>>(
         c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->qshape, c->color_off, c->ncolors, kv, knf, A, rowsum, rows, K));
   } else if (split) {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 2>)));
     BIE_LAUNCH(k_asmff_bulk<false, 2><<<gb, 32 * rows * ASMF_W * 2, smem, c->stream>>>(
         c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->qshape, c->color_off, c->ncolors, kv, knf, A, rowsum, rows, K));
   } else {
     BIE_TRY((set_smem_max(k_asmff_bulk<false, 1>)));
     BIE_LAUNCH(k_asmff_bulk<false, 1><<<gb, 32 * rows * ASMF_W, smem, c->stream>>>(
         c->nodes, c->normals, c->bc, sorted_elems_ptr(c), N, c->E, c->rule.Q, sorted_aos_ptr(c),
-        c->qshape, c->color_off, c->ncolors, kv, known, A, rowsum, rows, K));
+        c->qshape, c->color_off, c->ncolors, kv, knf, A, rowsum, rows, K));
   }
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

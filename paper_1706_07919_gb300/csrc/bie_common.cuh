@@ -192,6 +192,7 @@ struct bie_ctx {
   bie::DeviceBuf work3;  // foot points, field scratch, synthesis indices
   bie::DeviceBuf work4;  // learned mode: the anchors' factors, permutations and solutions
   bie::DeviceBuf work5;  // linear elements: surface values interpolated onto the flat quadratic image
+  bie::DeviceBuf work6;  // float-float re-assembly: known values split into float-float
 };
 
 namespace bie {

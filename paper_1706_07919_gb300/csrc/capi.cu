@@ -362,6 +362,7 @@ int bie_destroy(bie_ctx* c) {
   free_buf(c, c->work3);
   free_buf(c, c->work4);
   free_buf(c, c->work5);
+  free_buf(c, c->work6);
   mlp_free(c);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->rep_pinned) cudaFreeHost(c->rep_pinned);
