@@ -248,6 +248,9 @@ int bie_set_incident_plane_wave(bie_ctx* ctx, const double* dir);
  *                          CTA, tiles of 32 quadrature points, FP32 run sums; 1 the same with 64
  *                          points per CTA and 64-point tiles; 0 groups of 8, 128 points,
  *                          compensated sums per term
+ *   "mixed.asm_kb"         FP32 bulk assembly on meshes whose elements carry one boundary
+ *                          condition each: 2 (default) wavenumbers per thread, 1, or 0 (the general
+ *                          kernel, one wavenumber per thread, both nodal sums per element)
  *   "asm.windows"          1 (default): at large N, where the mesh's node numbering can be cut
  *                          into windows of at most 3200 columns that no element straddles (bodies
  *                          numbered one after the other), the FP32 bulk assembly accumulates each

@@ -92,3 +92,14 @@ def test_binding_constants_match_header():
         assert getattr(B, name) == value, name
     flags = [v for n, v in consts.items() if n.startswith("BIE_FLAG_")]
     assert all(v & (v - 1) == 0 for v in flags) and len(set(flags)) == len(flags)
+
+
+def test_every_option_is_documented():
+    """Every name bie_set_option accepts is documented in include/bie.h and vice versa (the option
+    table of the header against the names compared in the implementation; CPU only)."""
+    src = open(os.path.join(ROOT, "paper_1706_07919_gb300", "csrc", "capi.cu")).read()
+    accepted = set(re.findall(r'n == "([a-z0-9_.]+)"', src))
+    hdr = open(os.path.join(ROOT, "include", "bie.h")).read()
+    documented = set(re.findall(r'^ \*   "([a-z0-9_.]+)"', hdr, flags=re.M))
+    documented |= set(re.findall(r'^ \*   "[a-z0-9_.]+", "([a-z0-9_.]+)"', hdr, flags=re.M))
+    assert accepted and accepted == documented, (accepted - documented, documented - accepted)
